@@ -1,0 +1,185 @@
+"""ctypes wrapper around the FP64 CPU oracle (wb_oracle.cpp).
+
+TEST INFRASTRUCTURE: only the tests, the smoke check and the benchmark's
+CPU-baseline leg may import this module.  It does not import the CUDA library
+and the CUDA library does not import it.
+
+Arrays cross this wrapper in the library's layouts (q, qd, qdd, tau as [d][B];
+poses [B][n][12]; spheres [B][S][3]) and are converted to the oracle's
+config-major float64 layout here.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "wb_oracle.cpp")
+_OUT = os.path.join(_HERE, "_build", "libwb_oracle.so")
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (OpenMP across configurations)."""
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+        os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+        tmp = _OUT + ".tmp%d" % os.getpid()
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fopenmp", "-shared", "-fPIC",
+                               _SRC, "-o", tmp])
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+class _Robot(C.Structure):
+    _fields_ = [("n", C.c_int), ("d", C.c_int), ("S", C.c_int), ("P", C.c_int),
+                ("n_pm", C.c_int),
+                ("parent", C.c_void_p), ("jtype", C.c_void_p), ("axis", C.c_void_p),
+                ("T_fixed", C.c_void_p), ("jidx", C.c_void_p), ("mimic_mult", C.c_void_p),
+                ("mimic_off", C.c_void_p), ("gravity", C.c_void_p), ("sph_link", C.c_void_p),
+                ("sph_c", C.c_void_p), ("sph_r", C.c_void_p), ("pairs", C.c_void_p),
+                ("mass", C.c_void_p), ("com", C.c_void_p), ("Icom", C.c_void_p),
+                ("pm_link", C.c_void_p), ("pm_mass", C.c_void_p), ("pm_pos", C.c_void_p)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        p = C.c_void_p
+        _lib.or_eval.argtypes = [C.POINTER(_Robot), C.c_int, p, p, p, p, p, p, p, p, p, p, C.c_int]
+        _lib.or_grad.argtypes = [C.POINTER(_Robot), C.c_int, p, p, p, p, p, p, p, p, p, p, p,
+                                 C.c_int]
+        _lib.or_bspline.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, p, p, p, p]
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+class OracleRobot:
+    """Holds contiguous float64/int32 copies of a synthetic Robot."""
+
+    def __init__(self, robot):
+        self.robot = robot
+        self._keep = {}
+
+        def keep(name, a, dt):
+            a = np.ascontiguousarray(a, dtype=dt)
+            self._keep[name] = a
+            return a.ctypes.data
+
+        r = robot
+        s = _Robot()
+        s.n, s.d, s.S, s.P, s.n_pm = r.n, r.dof, r.S, r.P, len(r.pm_link)
+        s.parent = keep("parent", r.parent, np.int32)
+        s.jtype = keep("jtype", r.jtype, np.int32)
+        s.axis = keep("axis", r.axis, np.float64)
+        s.T_fixed = keep("T", r.T_fixed, np.float64)
+        s.jidx = keep("jidx", r.jidx, np.int32)
+        s.mimic_mult = keep("mm", r.mimic_mult, np.float64)
+        s.mimic_off = keep("mo", r.mimic_off, np.float64)
+        s.gravity = keep("g", r.gravity, np.float64)
+        s.sph_link = keep("sl", r.sph_link, np.int32)
+        s.sph_c = keep("sc", r.sph_c, np.float64)
+        s.sph_r = keep("sr", r.sph_r, np.float64)
+        s.pairs = keep("pairs", r.pairs.reshape(-1, 2) if r.P else np.zeros((1, 2)), np.int32)
+        s.mass = keep("mass", r.mass, np.float64)
+        s.com = keep("com", r.com, np.float64)
+        s.Icom = keep("Icom", r.Icom, np.float64)
+        s.pm_link = keep("pml", r.pm_link if len(r.pm_link) else np.zeros(1), np.int32)
+        s.pm_mass = keep("pmm", r.pm_mass if len(r.pm_mass) else np.zeros(1), np.float64)
+        s.pm_pos = keep("pmp", r.pm_pos if len(r.pm_pos) else np.zeros((1, 3)), np.float64)
+        self.s = s
+
+
+def _cm(x, d):
+    """[d][B] (library layout) -> contiguous float64 [B][d]."""
+    return np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(d, -1).T)
+
+
+def evaluate(robot, q, qd=None, qdd=None, fext=None, want=("pose", "sph", "dmin", "tau"),
+             nthreads: int = 0):
+    """Forward evaluation.  q, qd, qdd in [d][B].  Returns a dict with
+    pose [B][n][12], sph [B][S][3], dmin [B], worst [B], collide [B][P] uint8,
+    tau [d][B] (each only if in `want`)."""
+    orob = robot if isinstance(robot, OracleRobot) else OracleRobot(robot)
+    r = orob.robot
+    d = r.dof
+    q = _cm(q, d)
+    B = q.shape[0]
+    need_tau = "tau" in want
+    qd = _cm(qd, d) if qd is not None else np.zeros_like(q)
+    qdd = _cm(qdd, d) if qdd is not None else np.zeros_like(q)
+    out = {}
+    pose = np.zeros((B, r.n, 12)) if "pose" in want else None
+    sph = np.zeros((B, r.S, 3)) if "sph" in want else None
+    need_pair = "dmin" in want or "worst" in want or "collide" in want
+    dmin = np.zeros(B) if need_pair else None
+    worst = np.zeros(B, np.int32) if need_pair else None
+    collide = np.zeros((B, max(r.P, 1)), np.uint8) if "collide" in want else None
+    tau = np.zeros((B, d)) if need_tau else None
+    fe = None if fext is None else np.ascontiguousarray(fext, dtype=np.float64)
+    lib().or_eval(C.byref(orob.s), B, _ptr(q), _ptr(qd), _ptr(qdd), _ptr(fe), _ptr(pose),
+                  _ptr(sph), _ptr(dmin), _ptr(worst), _ptr(collide), _ptr(tau), nthreads)
+    if pose is not None:
+        out["pose"] = pose
+    if sph is not None:
+        out["sph"] = sph
+    if need_pair:
+        out["dmin"] = dmin
+        out["worst"] = worst
+    if collide is not None:
+        out["collide"] = collide[:, :r.P]
+    if tau is not None:
+        out["tau"] = np.ascontiguousarray(tau.T)
+    return out
+
+
+def gradient(robot, q, qd, qdd, g_pose=None, g_sph=None, g_dmin=None, g_tau=None, fext=None,
+             nthreads: int = 0):
+    """Exact (dual-number) gradient of <g_pose,pose> + <g_sph,sph> +
+    g_dmin*d_min + <g_tau,tau> w.r.t. q, qd, qdd.  Inputs in library layouts;
+    returns (gq, gqd, gqdd) each [d][B]."""
+    orob = robot if isinstance(robot, OracleRobot) else OracleRobot(robot)
+    r = orob.robot
+    d = r.dof
+    q = _cm(q, d)
+    B = q.shape[0]
+    qd = _cm(qd, d)
+    qdd = _cm(qdd, d)
+    gp = None if g_pose is None else np.ascontiguousarray(g_pose, dtype=np.float64)
+    gs = None if g_sph is None else np.ascontiguousarray(g_sph, dtype=np.float64)
+    gm = None if g_dmin is None else np.ascontiguousarray(g_dmin, dtype=np.float64)
+    gt = None if g_tau is None else _cm(g_tau, d)
+    fe = None if fext is None else np.ascontiguousarray(fext, dtype=np.float64)
+    gq = np.zeros((B, d))
+    gqd = np.zeros((B, d))
+    gqdd = np.zeros((B, d))
+    lib().or_grad(C.byref(orob.s), B, _ptr(q), _ptr(qd), _ptr(qdd), _ptr(fe), _ptr(gp),
+                  _ptr(gs), _ptr(gm), _ptr(gt), _ptr(gq), _ptr(gqd), _ptr(gqdd), nthreads)
+    return (np.ascontiguousarray(gq.T), np.ascontiguousarray(gqd.T),
+            np.ascontiguousarray(gqdd.T))
+
+
+def bspline(U, T: int, dt: float):
+    """Uniform cubic B-spline states from control points U [n_traj][d][K].
+    Returns q, qd, qdd in [d][n_traj*T]."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    n_traj, d, K = U.shape
+    B = n_traj * T
+    q = np.zeros((B, d))
+    qd = np.zeros((B, d))
+    qdd = np.zeros((B, d))
+    rc = lib().or_bspline(n_traj, d, K, T, dt, _ptr(U), _ptr(q), _ptr(qd), _ptr(qdd))
+    if rc != 0:
+        raise ValueError("or_bspline: bad sizes")
+    return (np.ascontiguousarray(q.T), np.ascontiguousarray(qd.T), np.ascontiguousarray(qdd.T))
+
+
+def max_threads() -> int:
+    return int(lib().or_max_threads())

@@ -1,0 +1,444 @@
+"""Pins of the FP64 oracle to things other than itself: closed forms,
+invariants, an independent Lagrangian formulation, library routines and finite
+differences.  CPU only."""
+import numpy as np
+import pytest
+from scipy.spatial.distance import cdist
+
+from synthetic import robots as R
+from synthetic import inputs as I
+
+
+def states(robot, B, seed):
+    return I.uniform_states(robot.dof, B, seed)
+
+
+def ev(O, robot, q, qd=None, qdd=None, **kw):
+    return O.evaluate(robot, np.asarray(q, float).reshape(robot.dof, -1),
+                      None if qd is None else np.asarray(qd, float).reshape(robot.dof, -1),
+                      None if qdd is None else np.asarray(qdd, float).reshape(robot.dof, -1),
+                      nthreads=1, **kw)
+
+
+def tau_of(O, robot, q, qd, qdd):
+    return ev(O, robot, q, qd, qdd, want=("tau",))["tau"][:, 0]
+
+
+# ---------------------------------------------------------------------------
+# forward kinematics
+# ---------------------------------------------------------------------------
+
+def test_planar_2link_closed_form(oracle_lib):
+    """Sec. 6.1.1 FK on the 2-link planar arm: x = l1 cos q1 + l2 cos(q1+q2),
+    y = l1 sin q1 + l2 sin(q1+q2), z = 0."""
+    O = oracle_lib
+    l1, l2 = 0.5, 0.25
+    rob = R.planar_2link(l1, l2)
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        q1, q2 = rng.uniform(-np.pi, np.pi, 2)
+        o = ev(O, rob, [q1, q2])
+        tip = o["sph"][0, 1]
+        assert np.allclose(tip, [l1 * np.cos(q1) + l2 * np.cos(q1 + q2),
+                                 l1 * np.sin(q1) + l2 * np.sin(q1 + q2), 0.0], atol=1e-14)
+        p2 = o["pose"][0, 1, 9:]
+        assert np.allclose(p2, [l1 * np.cos(q1), l1 * np.sin(q1), 0], atol=1e-14)
+        R2 = o["pose"][0, 1, :9].reshape(3, 3)
+        c, s = np.cos(q1 + q2), np.sin(q1 + q2)
+        assert np.allclose(R2, [[c, -s, 0], [s, c, 0], [0, 0, 1]], atol=1e-14)
+
+
+def _homog(T12):
+    H = np.eye(4)
+    H[:3, :3] = np.asarray(T12[:9]).reshape(3, 3)
+    H[:3, 3] = T12[9:]
+    return H
+
+
+@pytest.mark.parametrize("mk", [R.r7, R.r48, R.mixed_joint_tree])
+def test_zero_config_is_product_of_fixed_transforms(oracle_lib, mk):
+    """At q = 0 (and zero mimic offsets) each world pose is the product of the
+    fixed transforms along the chain."""
+    O = oracle_lib
+    rob = mk()
+    rob.mimic_off[:] = 0.0
+    o = ev(O, rob, np.zeros(rob.dof))
+    for k in range(rob.n):
+        H = np.eye(4)
+        chain = []
+        j = k
+        while j >= 0:
+            chain.append(j)
+            j = rob.parent[j]
+        for j in reversed(chain):
+            H = H @ _homog(rob.T_fixed[j])
+        got = _homog(o["pose"][0, k])
+        assert np.allclose(got, H, atol=1e-13)
+
+
+@pytest.mark.parametrize("mk", [R.r7, R.r48, R.mixed_joint_tree])
+def test_rotations_orthonormal_and_offsets_preserved(oracle_lib, mk):
+    O = oracle_lib
+    rob = mk()
+    q, _, _ = states(rob, 32, 5)
+    o = O.evaluate(rob, q, want=("pose",), nthreads=1)
+    Rm = o["pose"][:, :, :9].reshape(-1, rob.n, 3, 3)
+    eye = np.einsum("bkji,bkjl->bkil", Rm, Rm)
+    # fixed rotations are float32-rounded: the invariant holds up to their own
+    # deviation from orthonormality, accumulated along the chain
+    Rf = rob.T_fixed[:, :9].reshape(-1, 3, 3)
+    dev = np.abs(np.einsum("kji,kjl->kil", Rf, Rf) - np.eye(3)).max()
+    tol = 1e-12 + 3 * (rob.depth().max() + 1) * dev
+    assert np.abs(eye - np.eye(3)).max() <= tol
+    assert np.abs(np.linalg.det(Rm) - 1).max() <= tol
+    p = o["pose"][:, :, 9:]
+    for k in range(rob.n):
+        pa = rob.parent[k]
+        if pa >= 0 and rob.jtype[k] == R.REVOLUTE:
+            dist = np.linalg.norm(p[:, k] - p[:, pa], axis=1)
+            assert np.allclose(dist, np.linalg.norm(rob.T_fixed[k, 9:]), atol=1e-13)
+
+
+def test_prismatic_moves_along_axis(oracle_lib):
+    """A prismatic joint translates its link by q along the joint axis
+    (expressed in the parent through the fixed rotation)."""
+    O = oracle_lib
+    rob = R.mixed_joint_tree()
+    k = 1
+    assert rob.jtype[k] == R.PRISMATIC
+    rng = np.random.default_rng(1)
+    q = rng.uniform(-1, 1, rob.dof)
+    o0 = ev(O, rob, q)
+    q2 = q.copy()
+    q2[rob.jidx[k]] += 0.3
+    o1 = ev(O, rob, q2)
+    Rpa = o0["pose"][0, rob.parent[k], :9].reshape(3, 3)
+    Rf = rob.T_fixed[k, :9].reshape(3, 3)
+    step = Rpa @ Rf @ (rob.axis[k] / np.linalg.norm(rob.axis[k])) * 0.3
+    assert np.allclose(o1["pose"][0, k, 9:] - o0["pose"][0, k, 9:], step, atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# spheres and self-collision
+# ---------------------------------------------------------------------------
+
+def _slider_robot(radii):
+    """Prismatic sliders along x from the world origin, one sphere each: the
+    sphere centres are exactly (q_k, 0, 0)."""
+    n = len(radii)
+    return R._plain("sliders", [-1] * n, [R.PRISMATIC] * n, [[1, 0, 0]] * n,
+                    [R._Tp(0, 0, 0)] * n, mass=[1.0] * n, com=np.zeros((n, 3)),
+                    Icom=[[0.1, 0.1, 0.1, 0, 0, 0]] * n, sph_link=list(range(n)),
+                    sph_c=np.zeros((n, 3)), sph_r=radii,
+                    pairs=[[i, j] for i in range(n) for j in range(i + 1, n)])
+
+
+def test_hand_built_sphere_cases(oracle_lib):
+    """Three spheres at known positions: distances |xi-xj| - ri - rj; exactly
+    touching spheres (d = 0) are not colliding under the strict test."""
+    O = oracle_lib
+    rob = _slider_robot([0.25, 0.125, 0.5])
+    # sphere 0 at 0, sphere 1 at 0.375 (touching 0), sphere 2 at 2.0
+    o = ev(O, rob, [0.0, 0.375, 2.0], want=("dmin", "collide"))
+    assert o["dmin"][0] == 0.0 and o["worst"][0] == 0
+    assert list(o["collide"][0]) == [0, 0, 0]
+    # move sphere 2 to 0.5: pair (1,2) = 0.125 - 0.625 = -0.5, (0,2) = 0.5 - 0.75
+    o = ev(O, rob, [0.0, 0.375, 0.5], want=("dmin", "collide"))
+    assert o["dmin"][0] == -0.5 and o["worst"][0] == 2
+    assert list(o["collide"][0]) == [0, 1, 1]
+    # exact tie between pair 0 (0,1) and pair 2 (1,2): the smaller index wins
+    o = ev(O, rob, [0.0, 0.375, 1.0], want=("dmin",))
+    assert o["dmin"][0] == 0.0 and o["worst"][0] == 0
+
+
+@pytest.mark.parametrize("mk", [R.r7, R.r23, R.r48])
+def test_pairs_match_library_distance_matrix(oracle_lib, mk):
+    """d_min / worst / collide against scipy's cdist over the masked pairs."""
+    O = oracle_lib
+    rob = mk()
+    q, _, _ = states(rob, 8, 11)
+    o = O.evaluate(rob, q, want=("sph", "dmin", "collide"), nthreads=1)
+    i, j = rob.pairs[:, 0], rob.pairs[:, 1]
+    for b in range(q.shape[1]):
+        D = cdist(o["sph"][b], o["sph"][b])[i, j] - rob.sph_r[i] - rob.sph_r[j]
+        assert abs(o["dmin"][b] - D.min()) <= 1e-13
+        assert abs(D[o["worst"][b]] - D.min()) <= 1e-13
+        assert np.array_equal(o["collide"][b].astype(bool), D < 0)
+
+
+def test_pair_permutation_invariance(oracle_lib):
+    O = oracle_lib
+    rob = R.r23()
+    q, _, _ = states(rob, 16, 12)
+    base = O.evaluate(rob, q, want=("dmin",), nthreads=1)
+    perm = np.random.default_rng(3).permutation(rob.P)
+    shuf = rob.with_pairs(rob.pairs[perm])
+    o = O.evaluate(shuf, q, want=("dmin",), nthreads=1)
+    assert np.array_equal(o["dmin"], base["dmin"])
+    assert np.array_equal(perm[o["worst"]], base["worst"])
+
+
+# ---------------------------------------------------------------------------
+# inverse dynamics
+# ---------------------------------------------------------------------------
+
+def test_single_pendulum_closed_form(oracle_lib):
+    """tau = (Ixx + m l^2) qdd + m g l cos q, velocity terms exactly 0."""
+    O = oracle_lib
+    rob = R.pendulum(2.0, 0.75, 0.05)
+    # the parameters as stored (float32-representable values)
+    m, l, Ixx, g = rob.mass[0], rob.com[0, 1], rob.Icom[0, 0], -rob.gravity[2]
+    rng = np.random.default_rng(2)
+    for _ in range(20):
+        q, qd, qdd = rng.uniform(-3, 3, 3)
+        t = tau_of(O, rob, [q], [qd], [qdd])[0]
+        ref = (Ixx + m * l * l) * qdd + m * g * l * np.cos(q)
+        assert abs(t - ref) <= 1e-12 * max(1.0, abs(ref))
+        assert abs(tau_of(O, rob, [q], [qd], [0.0])[0] - tau_of(O, rob, [q], [0.0], [0.0])[0]) \
+            <= 1e-12
+
+
+def _world_com(rob, pose):
+    """World CoM of every link from the oracle's poses [n][12]."""
+    Rm = pose[:, :9].reshape(-1, 3, 3)
+    return np.einsum("kij,kj->ki", Rm, rob.com) + pose[:, 9:]
+
+
+def _potential(O, rob, q):
+    pose = ev(O, rob, q, want=("pose",))["pose"][0]
+    c = _world_com(rob, pose)
+    V = -np.sum(rob.mass[:, None] * c * rob.gravity[None, :])
+    if len(rob.pm_link):
+        Rm = pose[:, :9].reshape(-1, 3, 3)
+        x = np.einsum("kij,kj->ki", Rm[rob.pm_link], rob.pm_pos) + pose[rob.pm_link, 9:]
+        V -= np.sum(rob.pm_mass[:, None] * x * rob.gravity[None, :])
+    return V
+
+
+@pytest.mark.parametrize("mk", [R.r7, R.mixed_joint_tree, R.r23,
+                                lambda: I.hand_payload(R.r48())])
+def test_gravity_torque_is_potential_gradient(oracle_lib, mk):
+    """tau(q, 0, 0) = dV/dq, V = -sum m g.c(q), by central differences."""
+    O = oracle_lib
+    rob = mk()
+    q, _, _ = states(rob, 2, 21)
+    h = 1e-6
+    for b in range(2):
+        qb = q[:, b].astype(float)
+        tg = tau_of(O, rob, qb, np.zeros(rob.dof), np.zeros(rob.dof))
+        fd = np.zeros(rob.dof)
+        for j in range(rob.dof):
+            e = np.zeros(rob.dof)
+            e[j] = h
+            fd[j] = (_potential(O, rob, qb + e) - _potential(O, rob, qb - e)) / (2 * h)
+        assert np.abs(tg - fd).max() <= 1e-7 * max(1.0, np.abs(tg).max())
+
+
+def test_axes_parallel_to_gravity_have_no_static_torque(oracle_lib):
+    O = oracle_lib
+    rob = R.chain_along_gravity()
+    q, _, _ = states(rob, 4, 8)
+    o = O.evaluate(rob, q, np.zeros_like(q), np.zeros_like(q), want=("tau",), nthreads=1)
+    assert np.abs(o["tau"]).max() <= 1e-12
+
+
+def _jacobian_mass_matrix(O, rob, q, h=1e-6):
+    """M(q) = sum_k m_k Jv^T Jv + Jw^T (R Ic R^T) Jw from geometric Jacobians,
+    the Jacobians taken by central differences of forward kinematics alone."""
+    d = rob.dof
+
+    def kin(qq):
+        pose = ev(O, rob, qq, want=("pose",))["pose"][0]
+        return pose[:, :9].reshape(-1, 3, 3), _world_com(rob, pose), pose
+
+    R0, c0, pose0 = kin(q)
+    Jv = np.zeros((rob.n, 3, d))
+    Jw = np.zeros((rob.n, 3, d))
+    Jp = np.zeros((len(rob.pm_link), 3, d))
+    for j in range(d):
+        e = np.zeros(d)
+        e[j] = h
+        Rp, cp, pp = kin(q + e)
+        Rm_, cm, pm = kin(q - e)
+        Jv[:, :, j] = (cp - cm) / (2 * h)
+        dR = (Rp - Rm_) / (2 * h)
+        W = np.einsum("kij,klj->kil", dR, R0)   # dR R^T = [w]^
+        Jw[:, :, j] = np.stack([W[:, 2, 1], W[:, 0, 2], W[:, 1, 0]], axis=1)
+        for m, l in enumerate(rob.pm_link):
+            xp = pp[l, :9].reshape(3, 3) @ rob.pm_pos[m] + pp[l, 9:]
+            xm = pm[l, :9].reshape(3, 3) @ rob.pm_pos[m] + pm[l, 9:]
+            Jp[m, :, j] = (xp - xm) / (2 * h)
+    M = np.zeros((d, d))
+    for k in range(rob.n):
+        ic = rob.Icom[k]
+        Ic = np.array([[ic[0], ic[3], ic[4]], [ic[3], ic[1], ic[5]], [ic[4], ic[5], ic[2]]])
+        Iw = R0[k] @ Ic @ R0[k].T
+        M += rob.mass[k] * Jv[k].T @ Jv[k] + Jw[k].T @ Iw @ Jw[k]
+    for m in range(len(rob.pm_link)):
+        M += rob.pm_mass[m] * Jp[m].T @ Jp[m]
+    return M
+
+
+def _rnea_mass_matrix(O, rob, q):
+    d = rob.dof
+    z = np.zeros(d)
+    t0 = tau_of(O, rob, q, z, z)
+    return np.stack([tau_of(O, rob, q, z, np.eye(d)[j]) - t0 for j in range(d)], axis=1)
+
+
+@pytest.mark.parametrize("mk", [R.r7, R.mixed_joint_tree, R.r23,
+                                lambda: I.hand_payload(R.r48())])
+def test_lagrangian_mass_matrix(oracle_lib, mk):
+    """tau(q,0,qdd) - tau(q,0,0) = M(q) qdd with M from geometric Jacobians;
+    M symmetric positive definite."""
+    O = oracle_lib
+    rob = mk()
+    q, _, _ = states(rob, 1, 31)
+    q = q[:, 0].astype(float)
+    Mj = _jacobian_mass_matrix(O, rob, q)
+    Mr = _rnea_mass_matrix(O, rob, q)
+    scale = np.abs(Mj).max()
+    assert np.abs(Mr - Mj).max() <= 1e-7 * scale
+    assert np.abs(Mr - Mr.T).max() <= 1e-12 * scale
+    assert np.linalg.eigvalsh(0.5 * (Mr + Mr.T)).min() > 0
+
+
+@pytest.mark.parametrize("mk", [R.r7, R.mixed_joint_tree])
+def test_coriolis_from_christoffel_symbols(oracle_lib, mk):
+    """tau(q,qd,0) - tau(q,0,0) = sum_jk Gamma_ijk qd_j qd_k with Gamma from
+    central differences of M(q)."""
+    O = oracle_lib
+    rob = mk()
+    q, qd, _ = states(rob, 1, 41)
+    q = q[:, 0].astype(float)
+    qd = qd[:, 0].astype(float)
+    d = rob.dof
+    h = 1e-5
+    dM = np.zeros((d, d, d))  # dM[i, j, k] = dM_ij / dq_k
+    for k in range(d):
+        e = np.zeros(d)
+        e[k] = h
+        dM[:, :, k] = (_rnea_mass_matrix(O, rob, q + e) - _rnea_mass_matrix(O, rob, q - e)) / (2 * h)
+    G = 0.5 * (dM + dM.transpose(0, 2, 1) - dM.transpose(2, 0, 1))  # [i,j,k]: dM_jk/dq_i last
+    c = np.einsum("ijk,j,k->i", G, qd, qd)
+    z = np.zeros(d)
+    got = tau_of(O, rob, q, qd, z) - tau_of(O, rob, q, z, z)
+    assert np.abs(got - c).max() <= 1e-6 * max(1.0, np.abs(c).max())
+
+
+def test_power_balance_along_smooth_trajectory(oracle_lib):
+    """qd^T (tau - g(q)) = d/dt (1/2 qd^T M qd) along q(t) = a + b t + c t^2."""
+    O = oracle_lib
+    rob = R.mixed_joint_tree()
+    d = rob.dof
+    rng = np.random.default_rng(5)
+    a, b, c = rng.uniform(-1, 1, (3, d))
+
+    def state(t):
+        return a + b * t + c * t * t, b + 2 * c * t, 2 * c
+
+    def kinetic(t):
+        qq, vv, _ = state(t)
+        return 0.5 * vv @ _rnea_mass_matrix(O, rob, qq) @ vv
+
+    t0, h = 0.3, 1e-5
+    qq, vv, aa = state(t0)
+    z = np.zeros(d)
+    power = vv @ (tau_of(O, rob, qq, vv, aa) - tau_of(O, rob, qq, z, z))
+    dK = (kinetic(t0 + h) - kinetic(t0 - h)) / (2 * h)
+    assert abs(power - dK) <= 1e-7 * max(1.0, abs(power))
+
+
+def test_tau_affine_in_qdd(oracle_lib):
+    O = oracle_lib
+    rob = R.r48()
+    q, qd, qdd = states(rob, 3, 51)
+    q, qd = q[:, 0].astype(float), qd[:, 0].astype(float)
+    a1, a2 = qdd[:, 1].astype(float), qdd[:, 2].astype(float)
+    z = np.zeros(rob.dof)
+    lhs = tau_of(O, rob, q, qd, a1 + a2) - tau_of(O, rob, q, qd, a1)
+    rhs = tau_of(O, rob, q, qd, a2) - tau_of(O, rob, q, qd, z)
+    assert np.abs(lhs - rhs).max() <= 1e-10 * max(1.0, np.abs(lhs).max())
+
+
+def test_point_payload_adds_its_gravity_torque(oracle_lib):
+    """A point mass m at x on a link adds m (w_j x (x - o_j)) . (-g) to the
+    static torque of every ancestor joint j."""
+    O = oracle_lib
+    base = R.r48()
+    loaded = I.hand_payload(base)
+    q, _, _ = states(base, 2, 61)
+    z = np.zeros(base.dof)
+    for b in range(2):
+        qb = q[:, b].astype(float)
+        dt = tau_of(O, loaded, qb, z, z) - tau_of(O, base, qb, z, z)
+        pose = ev(O, base, qb, want=("pose",))["pose"][0]
+        ref = np.zeros(base.dof)
+        for l, m, pp in zip(loaded.pm_link, loaded.pm_mass, loaded.pm_pos):
+            x = pose[l, :9].reshape(3, 3) @ pp + pose[l, 9:]
+            k = l
+            while k >= 0:
+                if base.jtype[k] == R.REVOLUTE:
+                    w = pose[k, :9].reshape(3, 3) @ (base.axis[k] / np.linalg.norm(base.axis[k]))
+                    ref[base.jidx[k]] += m * np.cross(w, x - pose[k, 9:]) @ (-base.gravity)
+                k = base.parent[k]
+        assert np.abs(dt - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max())
+
+
+# ---------------------------------------------------------------------------
+# gradients
+# ---------------------------------------------------------------------------
+
+def _loss(O, rob, q, qd, qdd, gp, gs, gm, gt):
+    o = O.evaluate(rob, q[:, None], qd[:, None], qdd[:, None], nthreads=1)
+    return (np.sum(gp * o["pose"][0]) + np.sum(gs * o["sph"][0]) + gm * o["dmin"][0]
+            + np.sum(gt * o["tau"][:, 0]))
+
+
+@pytest.mark.parametrize("mk", [R.r7, R.mixed_joint_tree, R.r23])
+def test_dual_gradient_matches_central_differences(oracle_lib, mk):
+    O = oracle_lib
+    rob = mk()
+    B = 2
+    q, qd, qdd = states(rob, B, 71)
+    gp, gs, gm, gt = I.upstream_grads(rob, B, 72)
+    gq, gqd, gqdd = O.gradient(rob, q, qd, qdd, gp, gs, gm, gt, nthreads=1)
+    h = 1e-6
+    for b in range(B):
+        args = [x[:, b].astype(float) for x in (q, qd, qdd)]
+        ups = (gp[b].astype(float), gs[b].astype(float), float(gm[b]), gt[:, b].astype(float))
+        for which, g in enumerate((gq, gqd, gqdd)):
+            fd = np.zeros(rob.dof)
+            for j in range(rob.dof):
+                ap = [a.copy() for a in args]
+                am = [a.copy() for a in args]
+                ap[which][j] += h
+                am[which][j] -= h
+                fd[j] = (_loss(O, rob, *ap, *ups) - _loss(O, rob, *am, *ups)) / (2 * h)
+            assert np.abs(g[:, b] - fd).max() <= 1e-7 * max(1.0, np.abs(fd).max())
+
+
+# ---------------------------------------------------------------------------
+# B-spline (Sec. 4)
+# ---------------------------------------------------------------------------
+
+def test_bspline_reproduces_polynomials(oracle_lib):
+    """Uniform cubic B-splines reproduce constants and lines exactly, and for
+    control points u_i = i^2 give (i+1+alpha)^2 + 1/3; derivatives scale by
+    1/dt per order."""
+    O = oracle_lib
+    K, T, dt = 16, 64, 0.25
+    idx = np.arange(K, dtype=float)
+    U = np.stack([np.full(K, 0.7), 0.3 + 0.5 * idx, idx ** 2])[None]
+    q, qd, qdd = O.bspline(U, T, dt)
+    nseg = K - 3
+    t = np.arange(T) * nseg / (T - 1)
+    k = np.minimum(np.floor(t), nseg - 1)
+    alpha = t - k
+    x = k + 1 + alpha
+    assert np.allclose(q[0], 0.7, atol=1e-14) and np.allclose(qd[0], 0, atol=1e-13)
+    assert np.allclose(q[1], 0.3 + 0.5 * x, atol=1e-13)
+    assert np.allclose(qd[1], 0.5 / dt, atol=1e-12) and np.allclose(qdd[1], 0, atol=1e-11)
+    assert np.allclose(q[2], x ** 2 + 1.0 / 3.0, atol=1e-12)
+    assert np.allclose(qd[2], 2 * x / dt, atol=1e-11)
+    assert np.allclose(qdd[2], 2 / dt ** 2, atol=1e-10)
