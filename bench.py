@@ -1,0 +1,368 @@
+"""Benchmark of the whole-body evaluation (forward + backward) on GB300.
+
+A step is one forward evaluation (FK, sphere placement, self-collision
+map-reduce, RNEA) plus one backward pass (the VJP of all four with upstream
+gradients on poses, spheres, d_min and torques) over one batch of synthetic
+configurations of the 48-DoF humanoid-shaped tree (1024 seeds x 32 timesteps
+= 32768 configurations).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--kernel fused|plain] [--batch B] [--skip-cpu]
+
+--impl reference times the FP64 CPU oracle on the host cores instead.
+Under torchrun (N > 1) every rank evaluates its own batch (weak scaling);
+the step time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synthetic import configs as CF  # noqa: E402
+from synthetic import inputs as I  # noqa: E402
+from synthetic import robots as R  # noqa: E402
+
+METRIC = "whole-body evals/s (FK+self-coll+RNEA, fwd+bwd) at 48 DoF"
+L2_FLUSH_BYTES = 512 << 20
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per evaluation (flops; FMA = 2) and bytes
+# ---------------------------------------------------------------------------
+def work_per_eval(desc):
+    n = desc.n
+    nm = int((desc.jtype != R.FIXED).sum())
+    S, P, d = desc.S, desc.P, desc.dof
+    fwd = 150 * nm + 18 * S + 11 * P + 330 * n
+    bwd = 150 * nm + 330 * n + 660 * n + 60 * n + 15 * S
+    fwd_bytes = 4 * (3 * d + 12 * n + 3 * S + 1 + 1 + d)
+    bwd_bytes = 4 * (3 * d + 1 + 12 * n + 3 * S + 1 + d + 3 * d)
+    return {"fwd_flops": fwd, "bwd_flops": bwd, "fwd_bytes": fwd_bytes, "bwd_bytes": bwd_bytes}
+
+
+def fp32_peak_tflops(num_sms, mhz):
+    """FP32 FMA peak: SMs x 128 lanes x 2 flops x clock."""
+    return num_sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in self.rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in self.rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+def time_oracle(desc, target_s=15.0, seed=CF.HUMANOID48.seed):
+    """Forward + exact (dual-number) gradient of the FP64 oracle on the host
+    cores, on a sample sized to take about target_s seconds."""
+    from oracle import oracle as O
+    orob = O.OracleRobot(desc)
+    cores = O.max_threads()
+    n_cal = max(cores, 8)
+    q, qd, qdd = I.uniform_states(desc.dof, n_cal, seed)
+    gp, gs, gm, gt = I.upstream_grads(desc, n_cal, seed + 1)
+    t0 = time.perf_counter()
+    O.evaluate(orob, q, qd, qdd)
+    O.gradient(orob, q, qd, qdd, gp, gs, gm, gt)
+    per = (time.perf_counter() - t0) / n_cal
+    n = int(max(n_cal, min(200000, target_s / max(per, 1e-9))))
+    q, qd, qdd = I.uniform_states(desc.dof, n, seed + 7)
+    gp, gs, gm, gt = I.upstream_grads(desc, n, seed + 8)
+    t0 = time.perf_counter()
+    O.evaluate(orob, q, qd, qdd)
+    O.gradient(orob, q, qd, qdd, gp, gs, gm, gt)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "evals/s", "cores": cores, "kind": "oracle",
+            "sample": "%d configurations of the %s workload (FP64 forward + dual-number "
+                      "gradient, OpenMP over configurations), %.1f s" % (n, desc.name, dt)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    desc = R.r48()
+    steps = []
+    for _ in range(args.warmup):
+        time_oracle(desc, target_s=2.0)
+    for _ in range(args.steps):
+        steps.append(time_oracle(desc, target_s=args.ref_step_s))
+    vals = [s["value"] for s in steps]
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * CF.HUMANOID48.batch / value, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "humanoid48: 48-DoF tree, 200 spheres, 15392 pairs, "
+                               "1024 x 32 configurations, fwd + bwd",
+                   "batch": CF.HUMANOID48.batch},
+        "cpu_baseline": dict(steps[-1], value=value),
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the GPU benchmark
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2603_05493_gb300 import build
+    build()
+    from paper_2603_05493_gb300 import wbe
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    desc = R.r48()
+    B = args.batch or CF.HUMANOID48.batch
+    rob = wbe.Robot(desc, device=local_rank)
+    tune = wbe.PLAIN if args.kernel == "plain" else wbe.Tune()
+    seed = CF.HUMANOID48.seed + 101 * rank
+    q, qd, qdd = I.uniform_states(desc.dof, B, seed)
+    gp, gs, gm, gt = I.upstream_grads(desc, B, seed + 1)
+    h_in = [torch.from_numpy(x).pin_memory() for x in (q, qd, qdd, gp, gs, gm, gt)]
+    d_in = [x.to(dev) for x in h_in]
+    tq, tqd, tqdd, tgp, tgs, tgm, tgt = d_in
+    out = rob.empty_outputs(B)
+    gout = tuple(torch.empty((desc.dof, B), device=dev) for _ in range(3))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        rob.eval(tq, tqd, tqdd, tune=tune, out=out)
+        rob.eval_backward(tq, tqd, tqdd, out["worst"], tgp, tgs, tgm, tgt, tune=tune, out=gout)
+
+    for _ in range(max(args.warmup, 3) if args.warmup >= 0 else 3):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    for i in range(args.steps):
+        flush.fill_(float(i))  # evict L2 between timed steps (outside the events)
+        e0, e1, e2 = ev[i]
+        e0.record(stream)
+        rob.eval(tq, tqd, tqdd, tune=tune, out=out)
+        e1.record(stream)
+        rob.eval_backward(tq, tqd, tqdd, out["worst"], tgp, tgs, tgm, tgt, tune=tune, out=gout)
+        e2.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    fwd_ms = [a.elapsed_time(b) for a, b, _ in ev]
+    bwd_ms = [b.elapsed_time(c) for _, b, c in ev]
+    step_ms = float(np.sum(fwd_ms) + np.sum(bwd_ms)) / args.steps
+
+    # end to end through the C ABI: pinned host inputs -> device, forward,
+    # backward, results -> pinned host, every step
+    h_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
+             for k, v in out.items() if v is not None}
+    h_gout = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in gout]
+    torch.cuda.synchronize()
+    e2e_steps = max(3, min(args.steps, 20))
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(e2e_steps):
+        for dst, src in zip(d_in, h_in):
+            dst.copy_(src, non_blocking=True)
+        step()
+        for k, v in h_out.items():
+            v.copy_(out[k], non_blocking=True)
+        for hv, dv in zip(h_gout, gout):
+            hv.copy_(dv, non_blocking=True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clocks.stop()
+    e2e_ms = t0.elapsed_time(t1) / e2e_steps
+    h2d = int(sum(x.numel() * x.element_size() for x in h_in))
+    d2h = int(sum(v.numel() * v.element_size() for v in h_out.values()) +
+              sum(x.numel() * x.element_size() for x in h_gout))
+
+    if world > 1:
+        t = torch.tensor([step_ms, e2e_ms, float(np.mean(fwd_ms)), float(np.mean(bwd_ms))],
+                         device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms, e2e_ms, fwd_mean, bwd_mean = [float(x) for x in t.tolist()]
+    else:
+        fwd_mean, bwd_mean = float(np.mean(fwd_ms)), float(np.mean(bwd_ms))
+    if rank != 0:
+        return
+    value = world * B / (step_ms * 1e-3)
+    e2e_value = world * B / (e2e_ms * 1e-3)
+    w = work_per_eval(desc)
+    peaks = measured_peaks()
+    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    peak = fp32_peak_tflops(num_sms, sm_max)
+    dom_is_fwd = fwd_mean >= bwd_mean
+    dom_ms = fwd_mean if dom_is_fwd else bwd_mean
+    dom_flops = (w["fwd_flops"] if dom_is_fwd else w["bwd_flops"]) * B
+    achieved = dom_flops / (dom_ms * 1e-3) / 1e12
+    cpu = None if args.skip_cpu else time_oracle(desc, target_s=args.cpu_s)
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "humanoid48: 48-DoF tree, 200 spheres, 15392 pairs, "
+                               "1024 x 32 configurations, fwd + bwd (upstream grads on "
+                               "poses, spheres, d_min, tau)",
+                   "batch_per_gpu": B, "kernel": args.kernel,
+                   "l2": "flushed between timed steps (512 MB write outside the events)"},
+        "fwd_ms": fwd_mean, "bwd_ms": bwd_mean,
+        "roofline": {"kernel": "fused_fwd_kernel" if dom_is_fwd else "fused_bwd_kernel",
+                     "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_basis": "FP32 FMA: %d SMs x 128 x 2 x %.0f MHz (max SM clock)"
+                                   % (num_sms, sm_max),
+                     "flops_per_eval": w["fwd_flops"] if dom_is_fwd else w["bwd_flops"]},
+        "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks.summary(),
+        "cpu_baseline": cpu,
+    }
+    if args.kernel == "fused" and not args.skip_plain:
+        # the plain one-thread-per-configuration kernels on the same inputs
+        for _ in range(2):
+            rob.eval(tq, tqd, tqdd, tune=wbe.PLAIN, out=out)
+            rob.eval_backward(tq, tqd, tqdd, out["worst"], tgp, tgs, tgm, tgt, tune=wbe.PLAIN,
+                              out=gout)
+        torch.cuda.synchronize()
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        pf, pb = [], []
+        for i in range(3):
+            flush.fill_(float(i))
+            a.record(stream)
+            rob.eval(tq, tqd, tqdd, tune=wbe.PLAIN, out=out)
+            b.record(stream)
+            rob.eval_backward(tq, tqd, tqdd, out["worst"], tgp, tgs, tgm, tgt, tune=wbe.PLAIN,
+                              out=gout)
+            c.record(stream)
+            torch.cuda.synchronize()
+            pf.append(a.elapsed_time(b))
+            pb.append(b.elapsed_time(c))
+        line["plain"] = {"value": B / ((np.mean(pf) + np.mean(pb)) * 1e-3), "unit": "evals/s",
+                         "fwd_ms": float(np.mean(pf)), "bwd_ms": float(np.mean(pb))}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--kernel", choices=["fused", "plain"], default="fused")
+    ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--cpu-s", type=float, default=15.0)
+    ap.add_argument("--ref-step-s", type=float, default=10.0)
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

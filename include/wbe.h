@@ -1,0 +1,212 @@
+/*
+ * wbe.h -- C ABI of the GB300 whole-body evaluation library (libwbe.so).
+ *
+ * One whole-body evaluation of a robot configuration (Sec. 6 of the paper)
+ * is, in order:
+ *   1. forward kinematics over the kinematic tree (Sec. 6.1.1),
+ *   2. collision-sphere placement (Sec. 6.1.1),
+ *   3. self-collision signed distance over the masked sphere pairs reduced
+ *      to the minimum and the worst pair (Sec. 6.2, Fig. self_collision),
+ *   4. joint torques by recursive Newton-Euler inverse dynamics (Sec. 6.3,
+ *      Alg. 4),
+ * and the backward pass is the vector-Jacobian product of all four (Alg. 1,
+ * Alg. 5, Sec. 6.3 "VJP-based backward pass").
+ *
+ * Conventions
+ *   - All device buffers are owned by the caller, live on the robot's
+ *     device, are contiguous and 16-byte aligned.  The library keeps no
+ *     pointer to them after a call returns.
+ *   - Every call that takes a stream enqueues its work on that stream
+ *     (a cudaStream_t passed as void*; NULL = the legacy default stream),
+ *     returns without synchronising, performs no device allocation and is
+ *     safe to capture in a CUDA graph.
+ *   - Batched per-configuration arrays use two layouts:
+ *       joint-major   [d][B]     (q, qd, qdd, tau and their gradients)
+ *       config-major  [B][...]   (link poses, sphere centres, pair bits)
+ *     where B is the number of configurations and d the number of actuated
+ *     joints.
+ *   - A link pose is 12 floats: the world rotation R (row-major 3x3) then
+ *     the world position p, so that x_world = R x_link + p.
+ *   - Every function returns WB_OK (0) or a negative WB_E* code;
+ *     wb_last_error() returns a message for the calling thread's last error.
+ */
+#ifndef WBE_H
+#define WBE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WB_OK 0
+#define WB_EINVAL (-1)   /* null required pointer, B < 0, misaligned buffer, non-unit axis */
+#define WB_ETOPO (-2)    /* parent[k] >= k, bad joint index, bad joint type */
+#define WB_ERANGE (-3)   /* pair or link index out of range, duplicate pair, i >= j */
+#define WB_ETOOBIG (-4)  /* robot larger than the kernels' limits */
+#define WB_EDEVICE (-5)  /* pointer not on the robot's device */
+#define WB_ECUDA (-6)    /* CUDA runtime error (allocation, copy or launch) */
+#define WB_ETIMEOUT (-7) /* a bounded device wait expired */
+
+/* limits of the kernels (checked at load) */
+#define WB_MAX_LINKS 255
+#define WB_MAX_SPHERES 1020
+
+typedef struct wb_robot wb_robot; /* opaque, owned by the library */
+typedef struct wb_batch wb_batch; /* opaque, owned by the library */
+
+/* Kinematic tree (Sec. 6.1, Fig. fk_comparison).  Host arrays, read during
+ * the call only.
+ *   parent[k]      -1 for the world, otherwise < k (topological order)
+ *   joint_type[k]  0 fixed, 1 revolute, 2 prismatic
+ *   axis[k][3]     joint axis in the link frame; |axis| must be 1 within 1e-5
+ *                  (it is renormalised in double before rounding to float)
+ *   T_fixed[k][12] pose of link k's joint frame in its parent frame:
+ *                  rotation (row-major, orthonormal within 1e-5), translation
+ *   joint_index[k] actuated joint of link k in [0, d), -1 iff fixed
+ *   mimic_mult[k], mimic_offset[k]  (nullable: 1 and 0) the joint variable of
+ *                  link k is mimic_mult*q[joint_index] + mimic_offset (the
+ *                  mimic joints of Fig. fk_comparison(b) and Alg. 4)
+ *   gravity[3]     (nullable: (0, 0, -9.81)) world gravity; it enters the
+ *                  dynamics as the base acceleration -gravity            */
+typedef struct {
+  int32_t n_links;
+  const int32_t* parent;
+  const int32_t* joint_type;
+  const double* axis;
+  const double* T_fixed;
+  const int32_t* joint_index;
+  const double* mimic_mult;
+  const double* mimic_offset;
+  const double* gravity;
+} wb_tree;
+
+/* Collision spheres (Sec. 6.1.1): sphere s sits on link[s] at center[s] in
+ * that link's frame, radius[s] >= 0. */
+typedef struct {
+  int32_t n_spheres;
+  const int32_t* link;
+  const double* center;
+  const double* radius;
+} wb_spheres;
+
+/* Self-collision pair mask (Sec. 6.2).  Either an explicit list of n_pairs
+ * pairs (i, j) with i < j (mask == NULL), or a dense S x S uint8 mask whose
+ * strict upper triangle is read (pairs == NULL).  The library sorts the pairs
+ * row-major: the pair index reported by wb_eval is the rank of (i, j) in
+ * lexicographic order. */
+typedef struct {
+  int32_t n_pairs;
+  const int32_t* pairs;
+  const uint8_t* mask;
+} wb_pairs;
+
+/* Inertials (Sec. 6.3, Tab. rnea_comparison "runtime payload").  Per link:
+ * mass[k], com[k][3] in the link frame, inertia[k][6] = (xx, yy, zz, xy, xz,
+ * yz) about the CoM in link axes.  Optional point masses (payloads):
+ * point_mass[m] kg rigidly attached to link point_link[m] at point_pos[m][3]
+ * (link frame); their spatial inertia is added to the link's. */
+typedef struct {
+  const double* mass;
+  const double* com;
+  const double* inertia;
+  int32_t n_points;
+  const int32_t* point_link;
+  const double* point_mass;
+  const double* point_pos;
+} wb_inertial;
+
+/* Kernel selection and launch shape (all zero = automatic). */
+#define WB_KERNEL_AUTO 0
+#define WB_KERNEL_PLAIN 1 /* one thread per configuration, baseline */
+#define WB_KERNEL_FUSED 2 /* one thread group per configuration, tiled */
+typedef struct {
+  int32_t kernel;            /* WB_KERNEL_* */
+  int32_t lanes_per_config;  /* fused: 4, 8, 16 or 32 (0 = robot default) */
+  int32_t configs_per_block; /* fused: configurations per CTA (0 = default) */
+  int32_t blocks_per_sm;     /* grid = blocks_per_sm * SMs (0 = occupancy) */
+} wb_tune;
+
+typedef struct {
+  int32_t n_links, dof, n_spheres, n_pairs, n_levels, max_level_width;
+  int32_t n_pair_blocks; /* 4x4 sphere-group blocks holding the pairs */
+  int32_t device;
+} wb_robot_info;
+
+/* Load and validate a robot; builds the topology cache (levels, children,
+ * per-joint link lists; Sec. 6.1.2 "topology cache"), the sorted pair list
+ * and its 4x4 block plan, compact float inertials, and copies them to
+ * `device`.  *out receives a handle owned by the library (free with
+ * wb_free_robot).  Errors: WB_EINVAL, WB_ETOPO, WB_ERANGE, WB_ETOOBIG,
+ * WB_ECUDA. */
+int wb_load_robot(const wb_tree* tree, const wb_spheres* spheres, const wb_pairs* pairs,
+                  const wb_inertial* inertial, int device, wb_robot** out);
+
+/* Replace the inertials (and point masses) of a loaded robot, e.g. to add a
+ * payload at run time (Tab. rnea_comparison).  The upload is enqueued on
+ * `stream`: work enqueued later on that stream sees the new values.  Calls
+ * on other streams must be ordered by the caller.  Not graph-capturable
+ * (it copies from host memory).  Errors: WB_EINVAL, WB_ERANGE, WB_ECUDA. */
+int wb_set_inertials(wb_robot* robot, const wb_inertial* inertial, void* stream);
+
+int wb_robot_info_get(const wb_robot* robot, wb_robot_info* out);
+
+/* Validate a descriptor and plan it exactly as wb_load_robot would, without
+ * touching any GPU: fills *out (device = -1) and, if sched_rounds is not
+ * NULL, sched_rounds[t] = rounds of the per-lane pair-block schedule for
+ * 4 << t lanes per configuration (t = 0..3).  Same errors as wb_load_robot
+ * except WB_EDEVICE / WB_ECUDA. */
+int wb_plan_info(const wb_tree* tree, const wb_spheres* spheres, const wb_pairs* pairs,
+                 const wb_inertial* inertial, wb_robot_info* out, int32_t* sched_rounds);
+
+/* Forward whole-body evaluation of B configurations (Sec. 6, Alg. 4).
+ *   q, qd, qdd   [d][B] joint positions, velocities, accelerations
+ *                (qd, qdd may be NULL only if tau == NULL)
+ * Outputs (device, written fully; NULL = not wanted):
+ *   link_pose    [B][n][12] world poses (NULL skips the store, not FK)
+ *   sphere       [B][S][3]  world sphere centres
+ *   d_min        [B]        min over masked pairs of |c_i-c_j| - r_i - r_j
+ *                           (+inf when the robot has no pairs)
+ *   worst_pair   [B]        index of the pair attaining d_min (smallest index
+ *                           among exact float ties; -1 when no pairs).
+ *                           Required when d_min is given.
+ *   tau          [d][B]     joint torques (NULL skips the dynamics)
+ *   pair_bits    [B][ceil(P/32)] bit p of word p/32 set iff pair p has
+ *                           |c_i-c_j| < r_i + r_j (colliding, strict)
+ * B == 0 is a no-op.  Errors: WB_EINVAL (null robot/q, B < 0, misaligned
+ * pointer, d_min without worst_pair, tau without qd/qdd), WB_EDEVICE,
+ * WB_ETOOBIG (launch shape does not fit), WB_ECUDA (launch failure). */
+int wb_eval(wb_robot* robot, int64_t B, const float* q, const float* qd, const float* qdd,
+            float* link_pose, float* sphere, float* d_min, int32_t* worst_pair, float* tau,
+            uint32_t* pair_bits, const wb_tune* tune, void* stream);
+
+/* Backward pass: the gradient of
+ *   L = <g_pose, link_pose> + <g_sphere, sphere> + sum_b g_dmin[b] d_min[b]
+ *       + <g_tau, tau>
+ * with respect to q, qd, qdd (Alg. 1 for the kinematic terms, Alg. 5 for the
+ * torque terms; the d_min term flows through worst_pair only).  Link
+ * transforms and the dynamics forward sweep are recomputed, not stored.
+ *   q, qd, qdd   [d][B] the inputs of the forward call
+ *   worst_pair   [B] from the forward call (required iff g_dmin != NULL)
+ *   g_pose [B][n][12], g_sphere [B][S][3], g_dmin [B], g_tau [d][B]
+ *                upstream gradients, each nullable (= zero)
+ *   gq, gqd, gqdd [d][B] outputs, overwritten (not accumulated)
+ * Errors as wb_eval. */
+int wb_eval_backward(wb_robot* robot, int64_t B, const float* q, const float* qd,
+                     const float* qdd, const int32_t* worst_pair, const float* g_pose,
+                     const float* g_sphere, const float* g_dmin, const float* g_tau, float* gq,
+                     float* gqd, float* gqdd, const wb_tune* tune, void* stream);
+
+void wb_free_robot(wb_robot* robot);
+
+/* Message describing the calling thread's most recent error ("" if none). */
+const char* wb_last_error(void);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int wb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WBE_H */

@@ -1,0 +1,105 @@
+"""ctypes declarations of the C ABI in include/wbe.h (argument marshalling
+only).  Loading fails loudly if libwbe.so has not been built: there is no
+fallback implementation."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libwbe.so")
+
+WB_OK = 0
+WB_EINVAL = -1
+WB_ETOPO = -2
+WB_ERANGE = -3
+WB_ETOOBIG = -4
+WB_EDEVICE = -5
+WB_ECUDA = -6
+WB_ETIMEOUT = -7
+ERRNAMES = {0: "WB_OK", -1: "WB_EINVAL", -2: "WB_ETOPO", -3: "WB_ERANGE", -4: "WB_ETOOBIG",
+            -5: "WB_EDEVICE", -6: "WB_ECUDA", -7: "WB_ETIMEOUT"}
+
+WB_KERNEL_AUTO = 0
+WB_KERNEL_PLAIN = 1
+WB_KERNEL_FUSED = 2
+
+p = C.c_void_p
+
+
+class wb_tree(C.Structure):
+    _fields_ = [("n_links", C.c_int32), ("parent", p), ("joint_type", p), ("axis", p),
+                ("T_fixed", p), ("joint_index", p), ("mimic_mult", p), ("mimic_offset", p),
+                ("gravity", p)]
+
+
+class wb_spheres(C.Structure):
+    _fields_ = [("n_spheres", C.c_int32), ("link", p), ("center", p), ("radius", p)]
+
+
+class wb_pairs(C.Structure):
+    _fields_ = [("n_pairs", C.c_int32), ("pairs", p), ("mask", p)]
+
+
+class wb_inertial(C.Structure):
+    _fields_ = [("mass", p), ("com", p), ("inertia", p), ("n_points", C.c_int32),
+                ("point_link", p), ("point_mass", p), ("point_pos", p)]
+
+
+class wb_tune(C.Structure):
+    _fields_ = [("kernel", C.c_int32), ("lanes_per_config", C.c_int32),
+                ("configs_per_block", C.c_int32), ("blocks_per_sm", C.c_int32)]
+
+
+class wb_robot_info(C.Structure):
+    _fields_ = [("n_links", C.c_int32), ("dof", C.c_int32), ("n_spheres", C.c_int32),
+                ("n_pairs", C.c_int32), ("n_levels", C.c_int32), ("max_level_width", C.c_int32),
+                ("n_pair_blocks", C.c_int32), ("device", C.c_int32)]
+
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "wb_version": (C.c_int, []),
+    "wb_last_error": (C.c_char_p, []),
+    "wb_load_robot": (C.c_int, [C.POINTER(wb_tree), C.POINTER(wb_spheres), C.POINTER(wb_pairs),
+                                C.POINTER(wb_inertial), C.c_int, C.POINTER(p)]),
+    "wb_set_inertials": (C.c_int, [p, C.POINTER(wb_inertial), p]),
+    "wb_robot_info_get": (C.c_int, [p, C.POINTER(wb_robot_info)]),
+    "wb_plan_info": (C.c_int, [C.POINTER(wb_tree), C.POINTER(wb_spheres), C.POINTER(wb_pairs),
+                               C.POINTER(wb_inertial), C.POINTER(wb_robot_info),
+                               C.POINTER(C.c_int32)]),
+    "wb_eval": (C.c_int, [p, C.c_int64, p, p, p, p, p, p, p, p, p, C.POINTER(wb_tune), p]),
+    "wb_eval_backward": (C.c_int, [p, C.c_int64, p, p, p, p, p, p, p, p, p, p, p,
+                                   C.POINTER(wb_tune), p]),
+    "wb_free_robot": (None, [p]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libwbe.so (raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(
+                "libwbe.so not found at %s: build it first "
+                "(python -c 'import __graft_entry__ as g; g.build()')" % path)
+        lib = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class WbError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__("%s failed: %s (%s)" % (where, msg, ERRNAMES.get(code, code)))
+        self.code = code
+
+
+def check(code: int, where: str):
+    if code != WB_OK:
+        raise WbError(code, where, load().wb_last_error().decode(errors="replace"))

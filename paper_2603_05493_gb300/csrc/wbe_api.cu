@@ -1,0 +1,749 @@
+// wbe_api.cu -- host side of libwbe.so: the C ABI declared in include/wbe.h.
+//
+// wb_load_robot validates the descriptor and builds, once per robot:
+//   * the topology cache of Sec. 6.1.2: tree levels (links of equal depth),
+//     children lists, the links driven by each joint (mimic joints, Alg. 1
+//     "jointMap"), the spheres of each link;
+//   * compact float parameters: fixed transforms (R, p), unit axes, the
+//     10-float spatial inertia (m, m c, inertia about the link origin) with
+//     payload point masses added (spatial inertias are additive);
+//   * the row-major sorted pair list, its 4x4 sphere-group blocks and a
+//     per-lane block schedule for each fused launch width;
+// and copies them to the device in one allocation.
+#include "../../include/wbe.h"
+#include "wbe_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace wbe;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+static int cuda_fail(cudaError_t e, const char* what) {
+  return fail(WB_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Runs with the robot's device current and restores the caller's device.
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+      changed = cudaSetDevice(dev) == cudaSuccess;
+    }
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// the robot handle
+// ---------------------------------------------------------------------------
+struct wb_robot {
+  int device = 0;
+  int num_sms = 0;
+  DevRobot dev{};
+  void* dmem = nullptr;
+  size_t dbytes = 0;
+  float* d_inert = nullptr;   // device inertia array (inside dmem)
+  PairSchedule sched[4]{};    // G = 4, 8, 16, 32
+  wb_robot_info info{};
+  // host copies needed by set_inertials
+  int n = 0, S = 0;
+  float* h_stage = nullptr;   // pinned staging buffer for inertia uploads
+  cudaEvent_t stage_evt = nullptr;
+  bool stage_pending = false;
+};
+
+static int sched_slot(int G) { return G == 4 ? 0 : G == 8 ? 1 : G == 16 ? 2 : G == 32 ? 3 : -1; }
+
+// Sub-allocator for the single device block.
+struct Packer {
+  std::vector<char> host;
+  struct Item {
+    size_t off;
+    const void** slot;
+  };
+  std::vector<Item> items;
+  size_t add(const void* src, size_t bytes, const void** slot) {
+    size_t off = (host.size() + 255) & ~size_t(255);
+    host.resize(off + std::max<size_t>(bytes, 16));
+    if (bytes) std::memcpy(host.data() + off, src, bytes);
+    items.push_back({off, slot});
+    return off;
+  }
+  template <class T>
+  size_t add_vec(const std::vector<T>& v, const T** slot) {
+    return add(v.data(), v.size() * sizeof(T), reinterpret_cast<const void**>(slot));
+  }
+};
+
+// 10-float compact spatial inertia at the link origin, point masses added
+static int compact_inertia(const wb_inertial* in, int n, std::vector<float>& out) {
+  if (!in || !in->mass || !in->com || !in->inertia)
+    return fail(WB_EINVAL, "inertial: mass, com and inertia are required");
+  std::vector<double> acc(10 * (size_t)n, 0.0);
+  auto add_body = [&](int k, double m, const double* c, const double* Ic) {
+    double* o = &acc[10 * (size_t)k];
+    const double cc = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+    o[0] += m;
+    o[1] += m * c[0];
+    o[2] += m * c[1];
+    o[3] += m * c[2];
+    // Io = Ic + m (|c|^2 I - c c^T)
+    o[4] += (Ic ? Ic[0] : 0.0) + m * (cc - c[0] * c[0]);
+    o[5] += (Ic ? Ic[1] : 0.0) + m * (cc - c[1] * c[1]);
+    o[6] += (Ic ? Ic[2] : 0.0) + m * (cc - c[2] * c[2]);
+    o[7] += (Ic ? Ic[3] : 0.0) - m * c[0] * c[1];
+    o[8] += (Ic ? Ic[4] : 0.0) - m * c[0] * c[2];
+    o[9] += (Ic ? Ic[5] : 0.0) - m * c[1] * c[2];
+  };
+  for (int k = 0; k < n; ++k) {
+    const double m = in->mass[k];
+    if (!std::isfinite(m) || m < 0) return fail(WB_EINVAL, "inertial: bad mass at link %d", k);
+    for (int i = 0; i < 3; ++i)
+      if (!std::isfinite(in->com[3 * k + i])) return fail(WB_EINVAL, "inertial: bad com %d", k);
+    for (int i = 0; i < 6; ++i)
+      if (!std::isfinite(in->inertia[6 * k + i]))
+        return fail(WB_EINVAL, "inertial: bad inertia at link %d", k);
+    add_body(k, m, in->com + 3 * k, in->inertia + 6 * k);
+  }
+  if (in->n_points < 0) return fail(WB_EINVAL, "inertial: n_points < 0");
+  if (in->n_points > 0 && (!in->point_link || !in->point_mass || !in->point_pos))
+    return fail(WB_EINVAL, "inertial: point mass arrays are required when n_points > 0");
+  for (int m = 0; m < in->n_points; ++m) {
+    const int l = in->point_link[m];
+    if (l < 0 || l >= n) return fail(WB_ERANGE, "inertial: point mass %d on link %d", m, l);
+    if (!std::isfinite(in->point_mass[m]) || in->point_mass[m] < 0)
+      return fail(WB_EINVAL, "inertial: bad point mass %d", m);
+    add_body(l, in->point_mass[m], in->point_pos + 3 * m, nullptr);
+  }
+  out.resize(acc.size());
+  for (size_t i = 0; i < acc.size(); ++i) out[i] = (float)acc[i];
+  return WB_OK;
+}
+
+// Deal the pair blocks of one launch width G to the lanes.  Blocks of column
+// class gj mod C (C = min(G, 8)) go to the lanes l with l mod C == class, so
+// that the 8 lanes of a shared-memory phase read distinct bank groups; each
+// class is sorted by row group gi (a lane reloads its row spheres only when
+// gi changes) and cut into equal contiguous runs.
+static void build_schedule(int G, const std::vector<uint32_t>& bx, std::vector<uint2>& ent,
+                           int& rounds) {
+  const int C = std::min(G, 8);
+  const int per = G / C;
+  std::vector<std::vector<int>> lanes(G);
+  for (int c = 0; c < C; ++c) {
+    std::vector<int> cls;
+    for (int b = 0; b < (int)bx.size(); ++b)
+      if ((int)((bx[b] >> 8) & 0xFF) % C == c) cls.push_back(b);
+    std::stable_sort(cls.begin(), cls.end(), [&](int a, int b) {
+      return (bx[a] & 0xFFFF) < (bx[b] & 0xFFFF);
+    });
+    const size_t m = cls.size();
+    for (int t = 0; t < per; ++t) {
+      const size_t lo = m * t / per, hi = m * (t + 1) / per;
+      for (size_t i = lo; i < hi; ++i) lanes[c + t * C].push_back(cls[i]);
+    }
+  }
+  // even out lanes whose class is larger than average: move the tail of the
+  // longest lane to the shortest until the spread is at most one block
+  for (int it = 0; it < 100000; ++it) {
+    int lo = 0, hi = 0;
+    for (int l = 1; l < G; ++l) {
+      if (lanes[l].size() < lanes[lo].size()) lo = l;
+      if (lanes[l].size() > lanes[hi].size()) hi = l;
+    }
+    if (lanes[hi].size() <= lanes[lo].size() + 1) break;
+    lanes[lo].push_back(lanes[hi].back());
+    lanes[hi].pop_back();
+  }
+  rounds = 0;
+  for (int l = 0; l < G; ++l) rounds = std::max(rounds, (int)lanes[l].size());
+  ent.assign((size_t)std::max(rounds, 1) * G, uint2{0u, 0u});
+  for (int l = 0; l < G; ++l)
+    for (size_t i = 0; i < lanes[l].size(); ++i) {
+      const int b = lanes[l][i];
+      ent[i * G + l] = uint2{bx[b], (uint32_t)b};
+    }
+}
+
+extern "C" {
+
+int wb_version(void) { return 100; }
+
+const char* wb_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"
+
+// Everything wb_load_robot computes on the host, before touching a device.
+struct HostPlan {
+  int n = 0, d = 0, S = 0, P = 0, nlev = 0, maxw = 0, Sg = 0;
+  float g[3];
+  double reach = 0.0;
+  std::vector<int16_t> parent, jidx, lev_start, lev_links, child_start, children, jl_start,
+      jl_links, ls_start, ls_sph, sph_link;
+  std::vector<int8_t> jtype, rot_id;
+  std::vector<float> axis, Tf, mimic, inert;
+  std::vector<float4> sp, grp_rad;
+  std::vector<int2> pairs_dev;
+  std::vector<uint32_t> bx;
+  std::vector<int32_t> blk_pidx;
+};
+
+static int plan_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs* pairs,
+                      const wb_inertial* inertial, HostPlan& H) {
+  if (!tree || !sph || !pairs || !inertial) return fail(WB_EINVAL, "NULL descriptor");
+  const int n = tree->n_links;
+  if (n <= 0) return fail(WB_EINVAL, "n_links must be positive");
+  if (n > WB_MAX_LINKS) return fail(WB_ETOOBIG, "n_links %d > %d", n, WB_MAX_LINKS);
+  if (!tree->parent || !tree->joint_type || !tree->axis || !tree->T_fixed || !tree->joint_index)
+    return fail(WB_EINVAL, "tree: parent, joint_type, axis, T_fixed, joint_index are required");
+
+  // ---- tree ----
+  std::vector<int16_t> parent(n), jidx(n);
+  std::vector<int8_t> jtype(n), rot_id(n);
+  std::vector<float> axis(4 * (size_t)n, 0.0f), Tf(12 * (size_t)n), mimic(2 * (size_t)n);
+  int d = 0;
+  for (int k = 0; k < n; ++k) {
+    const int pa = tree->parent[k];
+    if (pa < -1 || pa >= k) return fail(WB_ETOPO, "parent[%d] = %d must be in [-1, %d)", k, pa, k);
+    parent[k] = (int16_t)pa;
+    const int jt = tree->joint_type[k];
+    if (jt < 0 || jt > 2) return fail(WB_ETOPO, "joint_type[%d] = %d", k, jt);
+    jtype[k] = (int8_t)jt;
+    const int j = tree->joint_index[k];
+    if (jt == 0 && j != -1) return fail(WB_ETOPO, "fixed link %d has joint_index %d", k, j);
+    if (jt != 0 && (j < 0 || j >= n))
+      return fail(WB_ETOPO, "joint_index[%d] = %d out of range", k, j);
+    jidx[k] = (int16_t)j;
+    d = std::max(d, j + 1);
+    const double* ax = tree->axis + 3 * k;
+    if (jt != 0) {
+      const double nrm = std::sqrt(ax[0] * ax[0] + ax[1] * ax[1] + ax[2] * ax[2]);
+      if (!std::isfinite(nrm) || std::fabs(nrm - 1.0) > 1e-5)
+        return fail(WB_EINVAL, "axis of link %d is not unit (|a| = %g)", k, nrm);
+      for (int i = 0; i < 3; ++i) axis[4 * k + i] = (float)(ax[i] / nrm);
+    }
+    const double* T = tree->T_fixed + 12 * k;
+    for (int i = 0; i < 12; ++i)
+      if (!std::isfinite(T[i])) return fail(WB_EINVAL, "T_fixed of link %d not finite", k);
+    double dev = 0.0;
+    for (int i = 0; i < 3; ++i)
+      for (int jj = 0; jj < 3; ++jj) {
+        double s = 0.0;
+        for (int m = 0; m < 3; ++m) s += T[3 * m + i] * T[3 * m + jj];
+        dev = std::max(dev, std::fabs(s - (i == jj ? 1.0 : 0.0)));
+      }
+    if (dev > 1e-5) return fail(WB_EINVAL, "T_fixed rotation of link %d not orthonormal", k);
+    bool ident = true;
+    for (int i = 0; i < 9; ++i) {
+      Tf[12 * k + i] = (float)T[i];
+      if (T[i] != ((i % 4 == 0) ? 1.0 : 0.0)) ident = false;
+    }
+    for (int i = 9; i < 12; ++i) Tf[12 * k + i] = (float)T[i];
+    rot_id[k] = ident ? 1 : 0;
+    mimic[2 * k] = tree->mimic_mult ? (float)tree->mimic_mult[k] : 1.0f;
+    mimic[2 * k + 1] = tree->mimic_offset ? (float)tree->mimic_offset[k] : 0.0f;
+    if (!std::isfinite(mimic[2 * k]) || !std::isfinite(mimic[2 * k + 1]))
+      return fail(WB_EINVAL, "mimic parameters of link %d not finite", k);
+  }
+  // every joint must drive at least one link
+  std::vector<std::vector<int16_t>> jl(d);
+  for (int k = 0; k < n; ++k)
+    if (jidx[k] >= 0) jl[jidx[k]].push_back((int16_t)k);
+  for (int j = 0; j < d; ++j)
+    if (jl[j].empty()) return fail(WB_ETOPO, "joint %d drives no link", j);
+  float g[3] = {0.0f, 0.0f, -9.81f};
+  if (tree->gravity)
+    for (int i = 0; i < 3; ++i) g[i] = (float)tree->gravity[i];
+
+  // levels, children
+  std::vector<int> depth(n);
+  int nlev = 0;
+  for (int k = 0; k < n; ++k) {
+    depth[k] = parent[k] < 0 ? 0 : depth[parent[k]] + 1;
+    nlev = std::max(nlev, depth[k] + 1);
+  }
+  std::vector<int16_t> lev_start(nlev + 1, 0), lev_links;
+  int maxw = 0;
+  for (int l = 0; l < nlev; ++l) {
+    lev_start[l] = (int16_t)lev_links.size();
+    for (int k = 0; k < n; ++k)
+      if (depth[k] == l) lev_links.push_back((int16_t)k);
+    maxw = std::max(maxw, (int)lev_links.size() - lev_start[l]);
+  }
+  lev_start[nlev] = (int16_t)lev_links.size();
+  std::vector<int16_t> child_start(n + 1, 0), children;
+  for (int k = 0; k < n; ++k) {
+    child_start[k] = (int16_t)children.size();
+    for (int c = k + 1; c < n; ++c)
+      if (parent[c] == k) children.push_back((int16_t)c);
+  }
+  child_start[n] = (int16_t)children.size();
+  std::vector<int16_t> jl_start(d + 1, 0), jl_links;
+  for (int j = 0; j < d; ++j) {
+    jl_start[j] = (int16_t)jl_links.size();
+    jl_links.insert(jl_links.end(), jl[j].begin(), jl[j].end());
+  }
+  jl_start[d] = (int16_t)jl_links.size();
+
+  // ---- spheres ----
+  const int S = sph->n_spheres;
+  if (S < 0) return fail(WB_EINVAL, "n_spheres < 0");
+  if (S > WB_MAX_SPHERES) return fail(WB_ETOOBIG, "n_spheres %d > %d", S, WB_MAX_SPHERES);
+  if (S > 0 && (!sph->link || !sph->center || !sph->radius))
+    return fail(WB_EINVAL, "spheres: link, center, radius are required");
+  std::vector<float4> sp(std::max(S, 1));
+  std::vector<int16_t> sph_link(std::max(S, 1), 0);
+  double max_c = 0.0, max_r = 0.0;
+  for (int s = 0; s < S; ++s) {
+    const int l = sph->link[s];
+    if (l < 0 || l >= n) return fail(WB_ERANGE, "sphere %d on link %d", s, l);
+    const double* c = sph->center + 3 * s;
+    const double rr = sph->radius[s];
+    if (!std::isfinite(c[0]) || !std::isfinite(c[1]) || !std::isfinite(c[2]) ||
+        !std::isfinite(rr) || rr < 0)
+      return fail(WB_EINVAL, "sphere %d: bad centre or radius", s);
+    sp[s] = make_float4((float)c[0], (float)c[1], (float)c[2], (float)rr);
+    sph_link[s] = (int16_t)l;
+    max_c = std::max(max_c, std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]));
+    max_r = std::max(max_r, rr);
+  }
+  std::vector<int16_t> ls_start(n + 1, 0), ls_sph;
+  for (int k = 0; k < n; ++k) {
+    ls_start[k] = (int16_t)ls_sph.size();
+    for (int s = 0; s < S; ++s)
+      if (sph_link[s] == k) ls_sph.push_back((int16_t)s);
+  }
+  ls_start[n] = (int16_t)ls_sph.size();
+  if (ls_sph.empty()) ls_sph.push_back(0);
+
+  // ---- pairs: sort row-major, validate ----
+  std::vector<std::pair<int, int>> pl;
+  if (pairs->mask && pairs->pairs) return fail(WB_EINVAL, "pairs: give a list or a mask, not both");
+  if (pairs->mask) {
+    for (int i = 0; i < S; ++i)
+      for (int j = i + 1; j < S; ++j)
+        if (pairs->mask[(size_t)i * S + j]) pl.emplace_back(i, j);
+  } else {
+    if (pairs->n_pairs < 0) return fail(WB_EINVAL, "n_pairs < 0");
+    if (pairs->n_pairs > 0 && !pairs->pairs) return fail(WB_EINVAL, "pairs: list is NULL");
+    for (int p = 0; p < pairs->n_pairs; ++p) {
+      const int i = pairs->pairs[2 * p], j = pairs->pairs[2 * p + 1];
+      if (i < 0 || j < 0 || i >= S || j >= S)
+        return fail(WB_ERANGE, "pair %d = (%d, %d) out of range (S = %d)", p, i, j, S);
+      if (i >= j) return fail(WB_ERANGE, "pair %d = (%d, %d) must have i < j", p, i, j);
+      pl.emplace_back(i, j);
+    }
+    std::sort(pl.begin(), pl.end());
+    for (size_t p = 1; p < pl.size(); ++p)
+      if (pl[p] == pl[p - 1])
+        return fail(WB_ERANGE, "duplicate pair (%d, %d)", pl[p].first, pl[p].second);
+  }
+  const int P = (int)pl.size();
+  std::vector<int2> pairs_dev(std::max(P, 1), int2{0, 0});
+  for (int p = 0; p < P; ++p) pairs_dev[p] = int2{pl[p].first, pl[p].second};
+
+  // ---- 4x4 group blocks ----
+  const int Sg = std::max((S + 3) / 4, 1);
+  std::vector<float4> grp_rad(Sg, make_float4(0, 0, 0, 0));
+  for (int s = 0; s < S; ++s) (&grp_rad[s / 4].x)[s % 4] = sp[s].w;
+  std::vector<int> blk_of((size_t)Sg * Sg, -1);
+  std::vector<uint32_t> bx;  // gi | gj << 8 | mask << 16
+  std::vector<int32_t> blk_pidx;
+  for (int p = 0; p < P; ++p) {
+    const int i = pl[p].first, j = pl[p].second;
+    const int gi = i / 4, gj = j / 4;
+    int& b = blk_of[(size_t)gi * Sg + gj];
+    if (b < 0) {
+      b = (int)bx.size();
+      bx.push_back((uint32_t)gi | ((uint32_t)gj << 8));
+      blk_pidx.insert(blk_pidx.end(), 16, -1);
+    }
+    const int bit = 4 * (i % 4) + (j % 4);
+    bx[b] |= 1u << (16 + bit);
+    blk_pidx[16 * (size_t)b + bit] = p;
+  }
+  if (blk_pidx.empty()) blk_pidx.assign(16, -1);
+
+  // ---- inertia ----
+  std::vector<float> inert;
+  int rc = compact_inertia(inertial, n, inert);
+  if (rc != WB_OK) return rc;
+
+  // pair filter margin: a bound on the float rounding of the squared-distance
+  // test, scaled with the robot's reach
+  double reach = 0.0;
+  {
+    std::vector<double> rk(n, 0.0);
+    for (int k = 0; k < n; ++k) {
+      const double* T = tree->T_fixed + 12 * k;
+      const double len = std::sqrt(T[9] * T[9] + T[10] * T[10] + T[11] * T[11]);
+      rk[k] = (parent[k] < 0 ? 0.0 : rk[parent[k]]) + len;
+      reach = std::max(reach, rk[k]);
+    }
+    reach += max_c + max_r;
+  }
+
+  H.n = n;
+  H.d = d;
+  H.S = S;
+  H.P = P;
+  H.nlev = nlev;
+  H.maxw = maxw;
+  H.Sg = Sg;
+  for (int i = 0; i < 3; ++i) H.g[i] = g[i];
+  H.reach = reach;
+  H.parent.swap(parent);
+  H.jidx.swap(jidx);
+  H.lev_start.swap(lev_start);
+  H.lev_links.swap(lev_links);
+  H.child_start.swap(child_start);
+  if (children.empty()) children.push_back(0);
+  H.children.swap(children);
+  H.jl_start.swap(jl_start);
+  if (jl_links.empty()) jl_links.push_back(0);
+  H.jl_links.swap(jl_links);
+  H.ls_start.swap(ls_start);
+  H.ls_sph.swap(ls_sph);
+  H.sph_link.swap(sph_link);
+  H.jtype.swap(jtype);
+  H.rot_id.swap(rot_id);
+  H.axis.swap(axis);
+  H.Tf.swap(Tf);
+  H.mimic.swap(mimic);
+  H.inert.swap(inert);
+  H.sp.swap(sp);
+  H.grp_rad.swap(grp_rad);
+  H.pairs_dev.swap(pairs_dev);
+  H.bx.swap(bx);
+  H.blk_pidx.swap(blk_pidx);
+  return WB_OK;
+}
+
+static void fill_info(const HostPlan& H, int device, wb_robot_info* info) {
+  info->n_links = H.n;
+  info->dof = H.d;
+  info->n_spheres = H.S;
+  info->n_pairs = H.P;
+  info->n_levels = H.nlev;
+  info->max_level_width = H.maxw;
+  info->n_pair_blocks = (int)H.bx.size();
+  info->device = device;
+}
+
+extern "C" {
+
+int wb_plan_info(const wb_tree* tree, const wb_spheres* spheres, const wb_pairs* pairs,
+                 const wb_inertial* inertial, wb_robot_info* out, int32_t* sched_rounds) {
+  g_err.clear();
+  if (!out) return fail(WB_EINVAL, "out is NULL");
+  HostPlan H;
+  int rc = plan_robot(tree, spheres, pairs, inertial, H);
+  if (rc != WB_OK) return rc;
+  fill_info(H, -1, out);
+  if (sched_rounds)
+    for (int t = 0; t < 4; ++t) {
+      std::vector<uint2> ent;
+      int rounds = 0;
+      build_schedule(4 << t, H.bx, ent, rounds);
+      sched_rounds[t] = H.bx.empty() ? 0 : rounds;
+    }
+  return WB_OK;
+}
+
+int wb_load_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs* pairs,
+                  const wb_inertial* inertial, int device, wb_robot** out) {
+  g_err.clear();
+  if (!out) return fail(WB_EINVAL, "out is NULL");
+  *out = nullptr;
+  HostPlan H;
+  int rc = plan_robot(tree, sph, pairs, inertial, H);
+  if (rc != WB_OK) return rc;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return fail(WB_EDEVICE, "device %d not available (%d devices)", device, ndev);
+  }
+  const int n = H.n;
+  wb_robot* R = new wb_robot();
+  R->device = device;
+  R->n = n;
+  R->S = H.S;
+  DeviceGuard guard(device);
+  cudaDeviceGetAttribute(&R->num_sms, cudaDevAttrMultiProcessorCount, device);
+
+  DevRobot& D = R->dev;
+  D.n = n;
+  D.d = H.d;
+  D.S = H.S;
+  D.P = H.P;
+  D.nlev = H.nlev;
+  D.maxw = H.maxw;
+  D.Sg = H.Sg;
+  D.nblk = (int)H.bx.size();
+  D.margin = (float)std::max(std::ldexp(1.0, -16), H.reach * std::ldexp(1.0, -20));
+  for (int i = 0; i < 3; ++i) D.abase[i] = -H.g[i];
+
+  Packer pk;
+  pk.add_vec(H.parent, &D.parent);
+  pk.add_vec(H.jtype, &D.jtype);
+  pk.add_vec(H.rot_id, &D.rot_id);
+  pk.add_vec(H.jidx, &D.jidx);
+  pk.add_vec(H.mimic, &D.mimic);
+  pk.add_vec(H.axis, &D.axis);
+  pk.add_vec(H.Tf, &D.Tf);
+  const size_t inert_off = pk.add_vec(H.inert, &D.inert);
+  pk.add_vec(H.lev_start, &D.lev_start);
+  pk.add_vec(H.lev_links, &D.lev_links);
+  pk.add_vec(H.child_start, &D.child_start);
+  pk.add_vec(H.children, &D.children);
+  pk.add_vec(H.jl_start, &D.jl_start);
+  pk.add_vec(H.jl_links, &D.jl_links);
+  pk.add_vec(H.ls_start, &D.ls_start);
+  pk.add_vec(H.ls_sph, &D.ls_sph);
+  pk.add_vec(H.sp, &D.sph);
+  pk.add_vec(H.sph_link, &D.sph_link);
+  pk.add_vec(H.pairs_dev, &D.pairs);
+  pk.add_vec(H.grp_rad, &D.grp_rad);
+  pk.add_vec(H.blk_pidx, &D.blk_pidx);
+  std::vector<uint2> ents[4];
+  for (int t = 0; t < 4; ++t) {
+    const int G = 4 << t;
+    int rounds = 0;
+    build_schedule(G, H.bx, ents[t], rounds);
+    R->sched[t].G = G;
+    R->sched[t].rounds = H.bx.empty() ? 0 : rounds;
+    pk.add_vec(ents[t], &R->sched[t].ent);
+  }
+  cudaError_t e = cudaMalloc(&R->dmem, pk.host.size());
+  if (e != cudaSuccess) {
+    delete R;
+    return cuda_fail(e, "cudaMalloc(robot)");
+  }
+  R->dbytes = pk.host.size();
+  e = cudaMemcpy(R->dmem, pk.host.data(), pk.host.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(R->dmem);
+    delete R;
+    return cuda_fail(e, "cudaMemcpy(robot)");
+  }
+  for (auto& it : pk.items) *it.slot = static_cast<char*>(R->dmem) + it.off;
+  R->d_inert = reinterpret_cast<float*>(static_cast<char*>(R->dmem) + inert_off);
+  e = cudaMallocHost(reinterpret_cast<void**>(&R->h_stage), H.inert.size() * sizeof(float));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&R->stage_evt, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    wb_free_robot(R);
+    return cuda_fail(e, "robot staging buffer");
+  }
+  fill_info(H, device, &R->info);
+  *out = R;
+  return WB_OK;
+}
+
+int wb_robot_info_get(const wb_robot* robot, wb_robot_info* out) {
+  if (!robot || !out) return fail(WB_EINVAL, "NULL argument");
+  *out = robot->info;
+  return WB_OK;
+}
+
+int wb_set_inertials(wb_robot* robot, const wb_inertial* inertial, void* stream) {
+  g_err.clear();
+  if (!robot) return fail(WB_EINVAL, "robot is NULL");
+  std::vector<float> inert;
+  int rc = compact_inertia(inertial, robot->n, inert);
+  if (rc != WB_OK) return rc;
+  DeviceGuard guard(robot->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (robot->stage_pending) {
+    cudaError_t e = cudaEventSynchronize(robot->stage_evt);
+    if (e != cudaSuccess) return cuda_fail(e, "wait for previous inertia upload");
+  }
+  std::memcpy(robot->h_stage, inert.data(), inert.size() * sizeof(float));
+  cudaError_t e = cudaMemcpyAsync(robot->d_inert, robot->h_stage, inert.size() * sizeof(float),
+                                  cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "inertia upload");
+  e = cudaEventRecord(robot->stage_evt, s);
+  if (e != cudaSuccess) return cuda_fail(e, "inertia upload event");
+  robot->stage_pending = true;
+  return WB_OK;
+}
+
+void wb_free_robot(wb_robot* robot) {
+  if (!robot) return;
+  {
+    DeviceGuard guard(robot->device);
+    if (robot->stage_pending) cudaEventSynchronize(robot->stage_evt);
+    if (robot->stage_evt) cudaEventDestroy(robot->stage_evt);
+    if (robot->h_stage) cudaFreeHost(robot->h_stage);
+    if (robot->dmem) cudaFree(robot->dmem);
+  }
+  delete robot;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// launch helpers
+// ---------------------------------------------------------------------------
+static int check_ptr(const wb_robot* R, const void* p, const char* name, bool required) {
+  if (!p) return required ? fail(WB_EINVAL, "%s is NULL", name) : WB_OK;
+  if (reinterpret_cast<uintptr_t>(p) & 15u)
+    return fail(WB_EINVAL, "%s is not 16-byte aligned", name);
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(WB_EDEVICE, "%s: not a CUDA pointer", name);
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+    return fail(WB_EDEVICE, "%s is not device memory", name);
+  if (at.type == cudaMemoryTypeDevice && at.device != R->device)
+    return fail(WB_EDEVICE, "%s lives on device %d, robot on device %d", name, at.device,
+                R->device);
+  return WB_OK;
+}
+
+static int default_G(const DevRobot& r) { return (r.n >= 24 || r.P >= 2048) ? 32 : 8; }
+
+// Pick configurations per CTA and grid for a fused launch.
+static int fused_shape(const wb_robot* R, bool fwd, bool bits, const wb_tune* t, int64_t B,
+                       FusedShape& sh) {
+  const DevRobot& D = R->dev;
+  int G = (t && t->lanes_per_config) ? t->lanes_per_config : default_G(D);
+  if (sched_slot(G) < 0) return fail(WB_EINVAL, "lanes_per_config must be 4, 8, 16 or 32");
+  const size_t per = fwd ? fused_fwd_smem_per_config(D, G, bits) : fused_bwd_smem_per_config(D, G);
+  const int step = 32 / G;  // configurations per warp
+  int cpb = (t && t->configs_per_block) ? t->configs_per_block : 0;
+  if (cpb) {
+    if (cpb % step) return fail(WB_EINVAL, "configs_per_block must be a multiple of %d", step);
+    if (cpb * G > 256) return fail(WB_EINVAL, "configs_per_block * lanes must be <= 256");
+  } else {
+    cpb = 256 / G;
+    const size_t cap = 100 * 1024;  // leave room for two CTAs per SM
+    while (cpb > step && per * cpb > cap) cpb -= step;
+  }
+  const size_t smem = per * cpb;
+  if (smem > 227 * 1024)
+    return fail(WB_ETOOBIG, "robot needs %zu bytes of shared memory per CTA", smem);
+  int bps = (t && t->blocks_per_sm) ? t->blocks_per_sm : 0;
+  if (!bps) {
+    cudaError_t e = fwd ? fused_fwd_max_blocks_per_sm(G, cpb, smem, &bps)
+                        : fused_bwd_max_blocks_per_sm(G, cpb, smem, &bps);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    if (bps < 1) return fail(WB_ETOOBIG, "fused kernel does not fit on an SM");
+  }
+  const int64_t ntiles = (B + cpb - 1) / cpb;
+  sh.G = G;
+  sh.cpb = cpb;
+  sh.smem = smem;
+  sh.grid = (int)std::min<int64_t>(ntiles, (int64_t)bps * R->num_sms);
+  return WB_OK;
+}
+
+static bool plain_fits(const DevRobot& D) { return D.n <= 64 && D.S <= 256; }
+
+extern "C" {
+
+int wb_eval(wb_robot* robot, int64_t B, const float* q, const float* qd, const float* qdd,
+            float* link_pose, float* sphere, float* d_min, int32_t* worst_pair, float* tau,
+            uint32_t* pair_bits, const wb_tune* tune, void* stream) {
+  g_err.clear();
+  if (!robot) return fail(WB_EINVAL, "robot is NULL");
+  if (B < 0) return fail(WB_EINVAL, "B < 0");
+  if (B == 0) return WB_OK;
+  if (B > (int64_t)1 << 40) return fail(WB_EINVAL, "B too large");
+  int rc;
+  if ((rc = check_ptr(robot, q, "q", true))) return rc;
+  if ((rc = check_ptr(robot, qd, "qd", tau != nullptr))) return rc;
+  if ((rc = check_ptr(robot, qdd, "qdd", tau != nullptr))) return rc;
+  if ((rc = check_ptr(robot, link_pose, "link_pose", false))) return rc;
+  if ((rc = check_ptr(robot, sphere, "sphere", false))) return rc;
+  if ((rc = check_ptr(robot, d_min, "d_min", false))) return rc;
+  if ((rc = check_ptr(robot, worst_pair, "worst_pair", d_min != nullptr))) return rc;
+  if ((rc = check_ptr(robot, tau, "tau", false))) return rc;
+  if ((rc = check_ptr(robot, pair_bits, "pair_bits", false))) return rc;
+  if (!d_min && worst_pair) return fail(WB_EINVAL, "worst_pair without d_min");
+  DeviceGuard guard(robot->device);
+  FwdArgs a{B, q, qd, qdd, link_pose, sphere, d_min, worst_pair, tau, pair_bits};
+  const int kernel = tune ? tune->kernel : WB_KERNEL_AUTO;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (kernel == WB_KERNEL_PLAIN) {
+    if (!plain_fits(robot->dev))
+      return fail(WB_ETOOBIG, "plain kernel supports at most 64 links and 256 spheres");
+    e = launch_plain_fwd(robot->dev, a, 128, s);
+  } else if (kernel == WB_KERNEL_AUTO || kernel == WB_KERNEL_FUSED) {
+    FusedShape sh;
+    if ((rc = fused_shape(robot, true, pair_bits != nullptr, tune, B, sh))) return rc;
+    e = launch_fused_fwd(robot->dev, robot->sched[sched_slot(sh.G)], a, sh, s);
+  } else {
+    return fail(WB_EINVAL, "unknown kernel %d", kernel);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "wb_eval launch");
+  return WB_OK;
+}
+
+int wb_eval_backward(wb_robot* robot, int64_t B, const float* q, const float* qd,
+                     const float* qdd, const int32_t* worst_pair, const float* g_pose,
+                     const float* g_sphere, const float* g_dmin, const float* g_tau, float* gq,
+                     float* gqd, float* gqdd, const wb_tune* tune, void* stream) {
+  g_err.clear();
+  if (!robot) return fail(WB_EINVAL, "robot is NULL");
+  if (B < 0) return fail(WB_EINVAL, "B < 0");
+  if (B == 0) return WB_OK;
+  if (B > (int64_t)1 << 40) return fail(WB_EINVAL, "B too large");
+  int rc;
+  if ((rc = check_ptr(robot, q, "q", true))) return rc;
+  if ((rc = check_ptr(robot, qd, "qd", true))) return rc;
+  if ((rc = check_ptr(robot, qdd, "qdd", true))) return rc;
+  if ((rc = check_ptr(robot, worst_pair, "worst_pair", g_dmin != nullptr))) return rc;
+  if ((rc = check_ptr(robot, g_pose, "g_pose", false))) return rc;
+  if ((rc = check_ptr(robot, g_sphere, "g_sphere", false))) return rc;
+  if ((rc = check_ptr(robot, g_dmin, "g_dmin", false))) return rc;
+  if ((rc = check_ptr(robot, g_tau, "g_tau", false))) return rc;
+  if ((rc = check_ptr(robot, gq, "gq", true))) return rc;
+  if ((rc = check_ptr(robot, gqd, "gqd", true))) return rc;
+  if ((rc = check_ptr(robot, gqdd, "gqdd", true))) return rc;
+  DeviceGuard guard(robot->device);
+  BwdArgs a{B, q, qd, qdd, worst_pair, g_pose, g_sphere, g_dmin, g_tau, gq, gqd, gqdd};
+  const int kernel = tune ? tune->kernel : WB_KERNEL_AUTO;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (kernel == WB_KERNEL_PLAIN) {
+    if (!plain_fits(robot->dev))
+      return fail(WB_ETOOBIG, "plain kernel supports at most 64 links and 256 spheres");
+    e = launch_plain_bwd(robot->dev, a, 128, s);
+  } else if (kernel == WB_KERNEL_AUTO || kernel == WB_KERNEL_FUSED) {
+    FusedShape sh;
+    if ((rc = fused_shape(robot, false, false, tune, B, sh))) return rc;
+    e = launch_fused_bwd(robot->dev, a, sh, s);
+  } else {
+    return fail(WB_EINVAL, "unknown kernel %d", kernel);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "wb_eval_backward launch");
+  return WB_OK;
+}
+
+}  // extern "C"

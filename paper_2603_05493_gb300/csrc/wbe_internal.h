@@ -1,0 +1,110 @@
+// wbe_internal.h -- device-side robot layout shared by the host loader and
+// the kernels of libwbe.so (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wbe {
+
+// Device copy of a robot: everything a kernel needs, as device pointers.
+// Passed to kernels by value.  All per-link arrays are indexed by link id
+// (topological order, parent[k] < k).
+struct DevRobot {
+  int n;       // links (including fixed ones)
+  int d;       // actuated joints
+  int S;       // spheres
+  int P;       // masked pairs
+  int nlev;    // tree levels (depth 0 = links whose parent is the world)
+  int maxw;    // widest level
+  int Sg;      // sphere groups of 4 (S padded up to a multiple of 4)
+  int nblk;    // 4x4 group blocks holding at least one pair
+  float margin;              // pair filter margin (metres), see the pair stage
+  float abase[3];            // base acceleration = -gravity
+
+  // per link
+  const int16_t* parent;     // [n] -1 = world
+  const int8_t* jtype;       // [n] 0 fixed, 1 revolute, 2 prismatic
+  const int8_t* rot_id;      // [n] 1 if the fixed rotation is the identity
+  const int16_t* jidx;       // [n] actuated joint or -1
+  const float* mimic;        // [n][2] multiplier, offset
+  const float* axis;         // [n][4] unit axis (xyz, pad)
+  const float* Tf;           // [n][12] fixed transform R (row-major), p
+  const float* inert;        // [n][10] m, h = m*c (3), Io (xx yy zz xy xz yz) about origin
+  // topology cache (Sec. 6.1.2)
+  const int16_t* lev_start;  // [nlev+1]
+  const int16_t* lev_links;  // [n] links grouped by level
+  const int16_t* child_start;// [n+1]
+  const int16_t* children;   // [n]
+  const int16_t* jl_start;   // [d+1] links driven by each joint (mimic)
+  const int16_t* jl_links;   // [#driven links]
+  const int16_t* ls_start;   // [n+1] spheres of each link
+  const int16_t* ls_sph;     // [S]
+  // spheres and pairs
+  const float4* sph;         // [S] centre in link frame (xyz), radius (w)
+  const int16_t* sph_link;   // [S]
+  const int2* pairs;         // [P] sorted row-major
+  const float4* grp_rad;     // [Sg] radii of the 4 spheres of a group (0 pad)
+  const int32_t* blk_pidx;   // [nblk][16] pair index of (4gi+a, 4gj+b) or -1
+};
+
+// A per-lane schedule of pair blocks for the fused kernel with G lanes per
+// configuration: entry [r][l] is the block lane l processes in round r.
+// x = gi | gj << 8 | mask << 16 (mask bit a*4+b = pair (4gi+a, 4gj+b) is
+// masked in), y = block id (row of blk_pidx); mask 0 = no work.
+struct PairSchedule {
+  int G;
+  int rounds;
+  const uint2* ent;          // [rounds][G]
+};
+
+// Kernel-side launch configuration of the fused kernels.
+struct FusedShape {
+  int G;                     // lanes per configuration (4, 8, 16, 32)
+  int cpb;                   // configurations per CTA
+  int grid;                  // CTAs
+  size_t smem;               // dynamic shared memory per CTA
+};
+
+struct FwdArgs {
+  int64_t B;
+  const float* q;
+  const float* qd;
+  const float* qdd;
+  float* pose;
+  float* sph;
+  float* dmin;
+  int32_t* worst;
+  float* tau;
+  uint32_t* bits;
+};
+
+struct BwdArgs {
+  int64_t B;
+  const float* q;
+  const float* qd;
+  const float* qdd;
+  const int32_t* worst;
+  const float* g_pose;
+  const float* g_sph;
+  const float* g_dmin;
+  const float* g_tau;
+  float* gq;
+  float* gqd;
+  float* gqdd;
+};
+
+// launchers (return cudaGetLastError())
+cudaError_t launch_plain_fwd(const DevRobot& r, const FwdArgs& a, int threads, cudaStream_t s);
+cudaError_t launch_plain_bwd(const DevRobot& r, const BwdArgs& a, int threads, cudaStream_t s);
+
+size_t fused_fwd_smem_per_config(const DevRobot& r, int G, bool bits);
+size_t fused_bwd_smem_per_config(const DevRobot& r, int G);
+cudaError_t launch_fused_fwd(const DevRobot& r, const PairSchedule& ps, const FwdArgs& a,
+                             const FusedShape& sh, cudaStream_t s);
+cudaError_t launch_fused_bwd(const DevRobot& r, const BwdArgs& a, const FusedShape& sh,
+                             cudaStream_t s);
+cudaError_t fused_fwd_max_blocks_per_sm(int G, int cpb, size_t smem, int* out);
+cudaError_t fused_bwd_max_blocks_per_sm(int G, int cpb, size_t smem, int* out);
+
+}  // namespace wbe

@@ -1,0 +1,226 @@
+"""Python binding of the whole-body evaluation library.
+
+Every computation runs in libwbe.so's CUDA kernels; this module only builds
+the C descriptors, hands device pointers of torch tensors and the current
+stream across the C ABI, and wraps the pair of calls in a
+torch.autograd.Function.
+
+Tensor layouts (float32 unless noted, on the robot's CUDA device):
+  q, qd, qdd, tau, grads   (d, B)     joint-major
+  link_pose                (B, n, 12) world R (row-major) then p
+  sphere                   (B, S, 3)
+  d_min                    (B,)
+  worst                    (B,) int32
+  pair_bits                (B, ceil(P/32)) int32 holding uint32 bit words
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _arr(a, dtype):
+    return np.ascontiguousarray(np.asarray(a), dtype=dtype)
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+@dataclass
+class Tune:
+    """Kernel choice and launch shape (zeros = automatic)."""
+    kernel: int = L.WB_KERNEL_AUTO
+    lanes_per_config: int = 0
+    configs_per_block: int = 0
+    blocks_per_sm: int = 0
+
+    def c(self):
+        return L.wb_tune(self.kernel, self.lanes_per_config, self.configs_per_block,
+                         self.blocks_per_sm)
+
+
+PLAIN = Tune(kernel=L.WB_KERNEL_PLAIN)
+FUSED = Tune(kernel=L.WB_KERNEL_FUSED)
+
+
+def _inertial_struct(keep, mass, com, inertia, pm_link=None, pm_mass=None, pm_pos=None):
+    def k(a, dt):
+        a = _arr(a, dt)
+        keep.append(a)
+        return a.ctypes.data
+    npm = 0 if pm_link is None else len(pm_link)
+    return L.wb_inertial(k(mass, np.float64), k(com, np.float64), k(inertia, np.float64), npm,
+                         k(pm_link, np.int32) if npm else None,
+                         k(pm_mass, np.float64) if npm else None,
+                         k(pm_pos, np.float64) if npm else None)
+
+
+def descriptors(desc, keep):
+    """C descriptor structs for a robot description (see Robot); the numpy
+    buffers they point to are appended to `keep`."""
+    def k(a, dt):
+        a = _arr(a, dt)
+        keep.append(a)
+        return a.ctypes.data
+
+    n = len(desc.parent)
+    tree = L.wb_tree(n, k(desc.parent, np.int32), k(desc.jtype, np.int32),
+                     k(desc.axis, np.float64), k(desc.T_fixed, np.float64),
+                     k(desc.jidx, np.int32), k(desc.mimic_mult, np.float64),
+                     k(desc.mimic_off, np.float64), k(desc.gravity, np.float64))
+    S = len(desc.sph_r)
+    sph = L.wb_spheres(S, k(desc.sph_link, np.int32), k(desc.sph_c, np.float64),
+                       k(desc.sph_r, np.float64))
+    pr = _arr(desc.pairs, np.int32).reshape(-1, 2)
+    keep.append(pr)
+    pairs = L.wb_pairs(pr.shape[0], pr.ctypes.data if pr.size else None, None)
+    pm = getattr(desc, "pm_link", None)
+    inert = _inertial_struct(keep, desc.mass, desc.com, desc.Icom,
+                             pm if pm is not None and len(pm) else None,
+                             getattr(desc, "pm_mass", None), getattr(desc, "pm_pos", None))
+    return tree, sph, pairs, inert
+
+
+def plan_info(desc):
+    """Validate and plan a robot on the host only (no GPU needed).  Returns
+    (info dict, pair-schedule rounds for 4/8/16/32 lanes per configuration)."""
+    lib = L.load()
+    keep = []
+    tree, sph, pairs, inert = descriptors(desc, keep)
+    info = L.wb_robot_info()
+    rounds = (C.c_int32 * 4)()
+    L.check(lib.wb_plan_info(C.byref(tree), C.byref(sph), C.byref(pairs), C.byref(inert),
+                             C.byref(info), rounds), "wb_plan_info")
+    d = {f: getattr(info, f) for f, _ in L.wb_robot_info._fields_}
+    return d, list(rounds)
+
+
+class Robot:
+    """A robot loaded into libwbe on one CUDA device.
+
+    `desc` is any object with the descriptor arrays: parent, jtype, axis,
+    T_fixed, jidx, mimic_mult, mimic_off, gravity, sph_link, sph_c, sph_r,
+    pairs (P, 2), mass, com, Icom and optionally pm_link, pm_mass, pm_pos
+    (payload point masses)."""
+
+    def __init__(self, desc, device=None):
+        self.lib = L.load()
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = torch.device("cuda", int(device))
+        keep = []
+        tree, sph, pairs, inert = descriptors(desc, keep)
+        h = C.c_void_p()
+        L.check(self.lib.wb_load_robot(C.byref(tree), C.byref(sph), C.byref(pairs),
+                                       C.byref(inert), int(self.device.index), C.byref(h)),
+                "wb_load_robot")
+        self.handle = h
+        info = L.wb_robot_info()
+        L.check(self.lib.wb_robot_info_get(self.handle, C.byref(info)), "wb_robot_info_get")
+        self.n, self.dof, self.S, self.P = info.n_links, info.dof, info.n_spheres, info.n_pairs
+        self.n_levels = info.n_levels
+        self.max_level_width = info.max_level_width
+        self.n_pair_blocks = info.n_pair_blocks
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            self.lib.wb_free_robot(h)
+            self.handle = None
+
+    @property
+    def pair_words(self) -> int:
+        return (self.P + 31) // 32
+
+    def set_inertials(self, mass, com, inertia, pm_link=None, pm_mass=None, pm_pos=None,
+                      stream=None):
+        keep = []
+        inert = _inertial_struct(keep, mass, com, inertia, pm_link, pm_mass, pm_pos)
+        L.check(self.lib.wb_set_inertials(self.handle, C.byref(inert), _stream(stream)),
+                "wb_set_inertials")
+
+    # ------------------------------------------------------------------
+    def empty_outputs(self, B, pose=True, sphere=True, dmin=True, tau=True, bits=False):
+        dev = self.device
+        f = dict(device=dev, dtype=torch.float32)
+        return {
+            "pose": torch.empty((B, self.n, 12), **f) if pose else None,
+            "sphere": torch.empty((B, self.S, 3), **f) if sphere else None,
+            "dmin": torch.empty((B,), **f) if dmin else None,
+            "worst": torch.empty((B,), device=dev, dtype=torch.int32) if dmin else None,
+            "tau": torch.empty((self.dof, B), **f) if tau else None,
+            "bits": torch.empty((B, max(self.pair_words, 1)), device=dev, dtype=torch.int32)
+            if bits else None,
+        }
+
+    def eval(self, q, qd=None, qdd=None, *, pose=True, sphere=True, dmin=True, tau=True,
+             bits=False, tune: Tune | None = None, out=None, stream=None):
+        """Forward whole-body evaluation; returns a dict of output tensors."""
+        B = q.shape[1]
+        o = out if out is not None else self.empty_outputs(B, pose, sphere, dmin, tau, bits)
+        t = (tune or Tune()).c()
+        L.check(self.lib.wb_eval(self.handle, B, _ptr(q), _ptr(qd), _ptr(qdd), _ptr(o["pose"]),
+                                 _ptr(o["sphere"]), _ptr(o["dmin"]), _ptr(o["worst"]),
+                                 _ptr(o["tau"]), _ptr(o["bits"]), C.byref(t), _stream(stream)),
+                "wb_eval")
+        return o
+
+    def eval_backward(self, q, qd, qdd, worst=None, g_pose=None, g_sphere=None, g_dmin=None,
+                      g_tau=None, *, tune: Tune | None = None, out=None, stream=None):
+        """Gradient of <g_pose,pose> + <g_sphere,sphere> + g_dmin.d_min +
+        <g_tau,tau> w.r.t. (q, qd, qdd)."""
+        B = q.shape[1]
+        if out is None:
+            out = tuple(torch.empty((self.dof, B), device=self.device, dtype=torch.float32)
+                        for _ in range(3))
+        gq, gqd, gqdd = out
+        t = (tune or Tune()).c()
+        L.check(self.lib.wb_eval_backward(self.handle, B, _ptr(q), _ptr(qd), _ptr(qdd),
+                                          _ptr(worst), _ptr(g_pose), _ptr(g_sphere),
+                                          _ptr(g_dmin), _ptr(g_tau), _ptr(gq), _ptr(gqd),
+                                          _ptr(gqdd), C.byref(t), _stream(stream)),
+                "wb_eval_backward")
+        return gq, gqd, gqdd
+
+
+def _c(t):
+    return None if t is None else t.contiguous()
+
+
+class WholeBodyEval(torch.autograd.Function):
+    """(q, qd, qdd) -> (link_pose, sphere, d_min, tau) with the hand-written
+    adjoint kernel as backward.  Saves q, qd, qdd and the worst pair, not the
+    transforms (they are recomputed)."""
+
+    @staticmethod
+    def forward(ctx, robot: Robot, q, qd, qdd, tune=None):
+        q, qd, qdd = q.contiguous(), qd.contiguous(), qdd.contiguous()
+        o = robot.eval(q, qd, qdd, tune=tune)
+        ctx.robot = robot
+        ctx.tune = tune
+        ctx.save_for_backward(q, qd, qdd, o["worst"])
+        ctx.mark_non_differentiable(o["worst"])
+        return o["pose"], o["sphere"], o["dmin"], o["tau"], o["worst"]
+
+    @staticmethod
+    def backward(ctx, g_pose, g_sph, g_dmin, g_tau, _g_worst):
+        q, qd, qdd, worst = ctx.saved_tensors
+        gq, gqd, gqdd = ctx.robot.eval_backward(q, qd, qdd, worst, _c(g_pose), _c(g_sph),
+                                                _c(g_dmin), _c(g_tau), tune=ctx.tune)
+        return None, gq, gqd, gqdd, None
+
+
+def whole_body_eval(robot: Robot, q, qd, qdd, tune=None):
+    """Differentiable evaluation: returns (link_pose, sphere, d_min, tau, worst)."""
+    return WholeBodyEval.apply(robot, q, qd, qdd, tune)

@@ -1,0 +1,263 @@
+"""GPU parity: the CUDA kernels against the FP64 oracle, element by element,
+through the C ABI.  Sizes span several CTA tiles with a ragged tail; the
+full-size workloads are checked on sampled configurations."""
+import numpy as np
+import pytest
+import torch
+
+from synthetic import configs as CF
+from synthetic import inputs as I
+from synthetic import robots as R
+from tests import parity as PY
+
+pytestmark = pytest.mark.gpu
+
+ROBOTS = {"R7": R.r7, "R23": R.r23, "R48": R.r48, "mixed": R.mixed_joint_tree}
+
+
+@pytest.fixture(scope="module")
+def W():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2603_05493_gb300 import build
+    build()
+    from paper_2603_05493_gb300 import wbe
+    return wbe
+
+
+@pytest.fixture(scope="module")
+def O():
+    from oracle import oracle
+    oracle.build()
+    return oracle
+
+
+def kernels(W):
+    return {"plain": W.PLAIN,
+            "fused4": W.Tune(kernel=2, lanes_per_config=4),
+            "fused8": W.Tune(kernel=2, lanes_per_config=8),
+            "fused16": W.Tune(kernel=2, lanes_per_config=16),
+            "fused32": W.Tune(kernel=2, lanes_per_config=32)}
+
+
+KERNEL_NAMES = ["plain", "fused4", "fused8", "fused16", "fused32"]
+
+_robots = {}
+
+
+def robot(W, name):
+    if name not in _robots:
+        _robots[name] = (ROBOTS[name](), W.Robot(ROBOTS[name](), device=0))
+    return _robots[name]
+
+
+def cuda(x):
+    return None if x is None else torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def host(o):
+    return {k: (None if v is None else v.cpu().numpy()) for k, v in o.items()}
+
+
+def run_fwd(rob, q, qd, qdd, tune, bits=False):
+    o = rob.eval(cuda(q), cuda(qd), cuda(qdd), tune=tune, bits=bits)
+    torch.cuda.synchronize()
+    return host(o)
+
+
+@pytest.mark.parametrize("rname", list(ROBOTS))
+@pytest.mark.parametrize("kname", KERNEL_NAMES)
+def test_forward_parity(W, O, rname, kname):
+    desc, rob = robot(W, rname)
+    B = 203 if rname != "R48" else 77  # several tiles and a ragged tail
+    q, qd, qdd = I.uniform_states(desc.dof, B, seed=hash((rname, 1)) % 1000)
+    got = run_fwd(rob, q, qd, qdd, kernels(W)[kname], bits=True)
+    ref = O.evaluate(desc, q, qd, qdd)
+    PY.check_forward(desc, got, ref)
+
+
+@pytest.mark.parametrize("rname", list(ROBOTS))
+@pytest.mark.parametrize("kname", KERNEL_NAMES)
+def test_backward_parity(W, O, rname, kname):
+    desc, rob = robot(W, rname)
+    B = 19 if rname == "R48" else 45
+    q, qd, qdd = I.uniform_states(desc.dof, B, seed=hash((rname, 2)) % 1000)
+    gp, gs, gm, gt = I.upstream_grads(desc, B, seed=3)
+    tune = kernels(W)[kname]
+    o = rob.eval(cuda(q), cuda(qd), cuda(qdd), tune=tune)
+    g = rob.eval_backward(cuda(q), cuda(qd), cuda(qdd), o["worst"], cuda(gp), cuda(gs),
+                          cuda(gm), cuda(gt), tune=tune)
+    torch.cuda.synchronize()
+    ref = O.evaluate(desc, q, want=("dmin",))
+    gref = O.gradient(desc, q, qd, qdd, gp, gs, gm, gt)
+    same = o["worst"].cpu().numpy() == ref["worst"]
+    assert same.mean() >= 0.9
+    PY.check_gradient([x.cpu().numpy() for x in g], gref, mask=same)
+
+
+@pytest.mark.parametrize("kname", KERNEL_NAMES)
+@pytest.mark.parametrize("which", ["pose", "sph", "dmin", "tau"])
+def test_backward_each_output_alone(W, O, kname, which):
+    """Each upstream gradient on its own (the others NULL)."""
+    desc, rob = robot(W, "mixed")
+    B = 33
+    q, qd, qdd = I.uniform_states(desc.dof, B, seed=9)
+    gp, gs, gm, gt = I.upstream_grads(desc, B, seed=10, pose=which == "pose",
+                                      sph=which == "sph", dmin=which == "dmin",
+                                      tau=which == "tau")
+    tune = kernels(W)[kname]
+    o = rob.eval(cuda(q), cuda(qd), cuda(qdd), tune=tune)
+    g = rob.eval_backward(cuda(q), cuda(qd), cuda(qdd), o["worst"], cuda(gp), cuda(gs),
+                          cuda(gm), cuda(gt), tune=tune)
+    torch.cuda.synchronize()
+    gref = O.gradient(desc, q, qd, qdd, gp, gs, gm, gt)
+    ref = O.evaluate(desc, q, want=("dmin",))
+    same = o["worst"].cpu().numpy() == ref["worst"]
+    PY.check_gradient([x.cpu().numpy() for x in g], gref, mask=same)
+
+
+def test_small7_workload(W, O):
+    """7-DoF chain, batch 64, forward FK + self-collision + RNEA."""
+    desc, rob = robot(W, "R7")
+    q, qd, qdd = I.uniform_states(desc.dof, CF.SMALL7.batch, CF.SMALL7.seed)
+    for tune in kernels(W).values():
+        got = run_fwd(rob, q, qd, qdd, tune, bits=True)
+        PY.check_forward(desc, got, O.evaluate(desc, q, qd, qdd))
+
+
+def _sample(B, k, seed):
+    rng = np.random.default_rng(seed)
+    s = np.unique(np.concatenate([[0, B - 1], rng.choice(B, k, replace=False)]))
+    return s
+
+
+def test_arm7_full_size_sampled(W, O):
+    """7-DoF chain, 4096 x 32 configurations, default launch; sampled parity."""
+    desc, rob = robot(W, "R7")
+    B = CF.ARM7.batch
+    q, qd, qdd = I.uniform_states(desc.dof, B, CF.ARM7.seed)
+    got = run_fwd(rob, q, qd, qdd, None)
+    s = _sample(B, 256, 1)
+    ref = O.evaluate(desc, q[:, s], qd[:, s], qdd[:, s])
+    PY.check_forward(desc, got, ref, sample=s)
+    assert np.isfinite(got["tau"]).all() and np.isfinite(got["dmin"]).all()
+
+
+def test_humanoid48_full_size_sampled(W, O):
+    """48-DoF tree, 1024 x 32 configurations, forward + backward with the
+    default launch; sampled parity."""
+    desc, rob = robot(W, "R48")
+    B = CF.HUMANOID48.batch
+    q, qd, qdd = I.uniform_states(desc.dof, B, CF.HUMANOID48.seed)
+    gp, gs, gm, gt = I.upstream_grads(desc, B, seed=CF.HUMANOID48.seed + 1)
+    tq, tqd, tqdd = cuda(q), cuda(qd), cuda(qdd)
+    o = rob.eval(tq, tqd, tqdd)
+    g = rob.eval_backward(tq, tqd, tqdd, o["worst"], cuda(gp), cuda(gs), cuda(gm), cuda(gt))
+    torch.cuda.synchronize()
+    got = host(o)
+    s = _sample(B, 40, 2)
+    ref = O.evaluate(desc, q[:, s], qd[:, s], qdd[:, s])
+    PY.check_forward(desc, got, ref, sample=s)
+    gref = O.gradient(desc, q[:, s], qd[:, s], qdd[:, s], gp[s], gs[s], gm[s], gt[:, s])
+    same = got["worst"][s] == ref["worst"]
+    PY.check_gradient([x.cpu().numpy()[:, s] for x in g], gref, mask=same)
+    for x in g:
+        assert torch.isfinite(x).all()
+
+
+def test_payload_via_set_inertials(W, O):
+    """Runtime payload: 3 kg on each hand through wb_set_inertials."""
+    desc = R.r48()
+    loaded = I.hand_payload(desc)
+    rob = W.Robot(desc, device=0)
+    rob.set_inertials(loaded.mass, loaded.com, loaded.Icom, loaded.pm_link, loaded.pm_mass,
+                      loaded.pm_pos)
+    q, qd, qdd = I.uniform_states(desc.dof, 40, 77)
+    got = run_fwd(rob, q, qd, qdd, None)
+    PY.check_forward(loaded, got, O.evaluate(loaded, q, qd, qdd))
+    base = O.evaluate(desc, q, qd, qdd, want=("tau",))
+    assert np.abs(base["tau"] - got["tau"]).max() > 1.0  # the payload mattered
+
+
+def test_edge_cases(W, O):
+    desc, rob = robot(W, "R7")
+    # B = 0 is a no-op
+    z = torch.zeros((desc.dof, 0), device="cuda")
+    o = rob.eval(z, z, z)
+    assert o["dmin"].numel() == 0
+    # B = 1
+    q, qd, qdd = I.uniform_states(desc.dof, 1, 4)
+    for tune in kernels(W).values():
+        PY.check_forward(desc, run_fwd(rob, q, qd, qdd, tune, bits=True),
+                         O.evaluate(desc, q, qd, qdd))
+    # no pairs: d_min = +inf, worst = -1; forward without dynamics
+    nop = desc.with_pairs(np.zeros((0, 2), np.int32))
+    r0 = W.Robot(nop, device=0)
+    q, qd, qdd = I.uniform_states(desc.dof, 50, 5)
+    for tune in kernels(W).values():
+        o = host(r0.eval(cuda(q), tau=False, tune=tune))
+        assert np.isinf(o["dmin"]).all() and (o["worst"] == -1).all()
+        PY.check_forward(nop, o, O.evaluate(nop, q, want=("pose", "sph")))
+
+
+def test_exact_touching_and_ties(W, O):
+    """Sliders with exact dyadic positions: touching spheres are not
+    colliding, exact ties pick the smallest pair index."""
+    n = 3
+    desc = R._plain("sliders", [-1] * n, [R.PRISMATIC] * n, [[1, 0, 0]] * n,
+                    [R._Tp(0, 0, 0)] * n, mass=[1.0] * n, com=np.zeros((n, 3)),
+                    Icom=[[0.1, 0.1, 0.1, 0, 0, 0]] * n, sph_link=list(range(n)),
+                    sph_c=np.zeros((n, 3)), sph_r=[0.25, 0.125, 0.5],
+                    pairs=[[0, 1], [0, 2], [1, 2]])
+    rob = W.Robot(desc, device=0)
+    q = np.array([[0.0, 0.0, 0.0], [0.375, 0.375, 0.375], [2.0, 0.5, 1.0]], np.float32)
+    for tune in kernels(W).values():
+        o = host(rob.eval(cuda(q), cuda(np.zeros_like(q)), cuda(np.zeros_like(q)), tune=tune,
+                          bits=True))
+        assert list(o["dmin"]) == [0.0, -0.5, 0.0]
+        assert list(o["worst"]) == [0, 2, 0]
+        assert list(o["bits"][:, 0]) == [0, 0b110, 0]
+
+
+def test_errors_are_reported(W):
+    from paper_2603_05493_gb300 import _lib as L
+    desc, rob = robot(W, "R7")
+    q = torch.zeros((desc.dof, 8), device="cuda")
+    with pytest.raises(L.WbError) as e:
+        rob.eval(q.cpu(), tau=False)
+    assert e.value.code == L.WB_EDEVICE
+    big = torch.zeros(desc.dof * 8 + 1, device="cuda")
+    with pytest.raises(L.WbError) as e:
+        rob.eval(big[1:].view(desc.dof, 8), tau=False)
+    assert e.value.code == L.WB_EINVAL
+    with pytest.raises(L.WbError) as e:
+        rob.eval(q, None, None, tau=True)
+    assert e.value.code == L.WB_EINVAL
+    with pytest.raises(L.WbError) as e:
+        rob.eval(q, q, q, tune=W.Tune(kernel=2, lanes_per_config=5))
+    assert e.value.code == L.WB_EINVAL
+
+
+def test_autograd_function(W, O):
+    desc, rob = robot(W, "R23")
+    B = 24
+    q, qd, qdd = I.uniform_states(desc.dof, B, 31)
+    gp, gs, gm, gt = I.upstream_grads(desc, B, 32)
+    tq, tqd, tqdd = (cuda(x).requires_grad_(True) for x in (q, qd, qdd))
+    pose, sph, dmin, tau, worst = W.whole_body_eval(rob, tq, tqd, tqdd)
+    loss = (pose * cuda(gp)).sum() + (sph * cuda(gs)).sum() + (dmin * cuda(gm)).sum() + \
+        (tau * cuda(gt)).sum()
+    loss.backward()
+    gref = O.gradient(desc, q, qd, qdd, gp, gs, gm, gt)
+    same = worst.cpu().numpy() == O.evaluate(desc, q, want=("dmin",))["worst"]
+    PY.check_gradient([tq.grad.cpu().numpy(), tqd.grad.cpu().numpy(), tqdd.grad.cpu().numpy()],
+                      gref, mask=same)
+
+
+def test_deterministic(W):
+    desc, rob = robot(W, "R48")
+    q, qd, qdd = I.uniform_states(desc.dof, 300, 8)
+    a = run_fwd(rob, q, qd, qdd, None)
+    b = run_fwd(rob, q, qd, qdd, None)
+    for k in a:
+        if a[k] is not None:
+            assert np.array_equal(a[k], b[k]), k
