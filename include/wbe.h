@@ -120,8 +120,12 @@ typedef struct {
 #define WB_KERNEL_AUTO 0
 #define WB_KERNEL_PLAIN 1 /* one thread per configuration, baseline */
 #define WB_KERNEL_FUSED 2 /* one thread group per configuration, tiled */
+#define WB_KERNEL_TREE 3  /* depth-first sweep kernels (one thread per configuration)
+                             for FK, RNEA and the backward, plus a warp-per-
+                             configuration sphere/pair kernel; needs link_pose
+                             when spheres or pairs are wanted */
 typedef struct {
-  int32_t kernel;            /* WB_KERNEL_* */
+  int32_t kernel;            /* WB_KERNEL_* (AUTO: TREE when it applies, else FUSED) */
   int32_t lanes_per_config;  /* fused: 4, 8, 16 or 32 (0 = robot default) */
   int32_t configs_per_block; /* fused: configurations per CTA (0 = default) */
   int32_t blocks_per_sm;     /* grid = blocks_per_sm * SMs (0 = occupancy) */

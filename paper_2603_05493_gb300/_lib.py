@@ -23,6 +23,7 @@ ERRNAMES = {0: "WB_OK", -1: "WB_EINVAL", -2: "WB_ETOPO", -3: "WB_ERANGE", -4: "W
 WB_KERNEL_AUTO = 0
 WB_KERNEL_PLAIN = 1
 WB_KERNEL_FUSED = 2
+WB_KERNEL_TREE = 3
 
 p = C.c_void_p
 

@@ -157,9 +157,9 @@ static void build_schedule(int G, const std::vector<uint32_t>& bx, std::vector<u
     std::vector<int> cls;
     for (int b = 0; b < (int)bx.size(); ++b)
       if ((int)((bx[b] >> 8) & 0xFF) % C == c) cls.push_back(b);
-    std::stable_sort(cls.begin(), cls.end(), [&](int a, int b) {
-      return (bx[a] & 0xFFFF) < (bx[b] & 0xFFFF);
-    });
+    // row group gi first, then column group gj
+    auto key = [&](int b) { return ((bx[b] & 0xFF) << 8) | ((bx[b] >> 8) & 0xFF); };
+    std::stable_sort(cls.begin(), cls.end(), [&](int a, int b) { return key(a) < key(b); });
     const size_t m = cls.size();
     for (int t = 0; t < per; ++t) {
       const size_t lo = m * t / per, hi = m * (t + 1) / per;
@@ -180,7 +180,8 @@ static void build_schedule(int G, const std::vector<uint32_t>& bx, std::vector<u
   }
   rounds = 0;
   for (int l = 0; l < G; ++l) rounds = std::max(rounds, (int)lanes[l].size());
-  ent.assign((size_t)std::max(rounds, 1) * G, uint2{0u, 0u});
+  // one extra all-null round: kernels may prefetch round r + 1 unguarded
+  ent.assign((size_t)(rounds + 1) * G, uint2{0u, 0u});
   for (int l = 0; l < G; ++l)
     for (size_t i = 0; i < lanes[l].size(); ++i) {
       const int b = lanes[l][i];
@@ -209,6 +210,12 @@ struct HostPlan {
   std::vector<int2> pairs_dev;
   std::vector<uint32_t> bx;
   std::vector<int32_t> blk_pidx;
+  std::vector<int4> lvm;
+  std::vector<int2> dfs;
+  std::vector<int16_t> chain_start, chain;
+  int maxdepth = 0;
+  int mimic_shared = 0;
+  double r_max = 0.0;
 };
 
 static int plan_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs* pairs,
@@ -415,6 +422,37 @@ static int plan_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs
   H.Sg = Sg;
   for (int i = 0; i < 3; ++i) H.g[i] = g[i];
   H.reach = reach;
+  H.r_max = max_r;
+  H.lvm.resize(n);
+  for (int i = 0; i < n; ++i) {
+    const int k = lev_links[i];
+    const int meta = (jidx[k] + 1) | ((int)jtype[k] << 16) | ((int)rot_id[k] << 24);
+    H.lvm[i] = make_int4(k, parent[k], meta, child_start[k] | (child_start[k + 1] << 16));
+  }
+  // depth-first pre-order (children in index order) and ancestor chains
+  {
+    std::vector<int> stack;
+    for (int k = n - 1; k >= 0; --k)
+      if (parent[k] < 0) stack.push_back(k);
+    while (!stack.empty()) {
+      const int k = stack.back();
+      stack.pop_back();
+      H.dfs.push_back(make_int2(k, depth[k]));
+      for (int c = n - 1; c > k; --c)
+        if (parent[c] == k) stack.push_back(c);
+    }
+    H.maxdepth = nlev;
+    H.chain_start.assign(n + 1, 0);
+    for (int k = 0; k < n; ++k) {
+      H.chain_start[k] = (int16_t)H.chain.size();
+      std::vector<int16_t> up;
+      for (int a = k; a >= 0; a = parent[a]) up.push_back((int16_t)a);
+      H.chain.insert(H.chain.end(), up.rbegin(), up.rend());
+    }
+    H.chain_start[n] = (int16_t)H.chain.size();
+    for (int j = 0; j < d; ++j)
+      if (jl[j].size() > 1) H.mimic_shared = 1;
+  }
   H.parent.swap(parent);
   H.jidx.swap(jidx);
   H.lev_start.swap(lev_start);
@@ -504,6 +542,10 @@ int wb_load_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs* pa
   D.Sg = H.Sg;
   D.nblk = (int)H.bx.size();
   D.margin = (float)std::max(std::ldexp(1.0, -16), H.reach * std::ldexp(1.0, -20));
+  // bound on the float rounding of the expanded squared-distance filter,
+  // 128 ulp of (reach + r_max + 1 cm)^2 (see the pair stage of k_fused.cu)
+  D.etol = (float)(128.0 * std::ldexp(1.0, -24) * (H.reach + H.r_max + 0.01) *
+                   (H.reach + H.r_max + 0.01));
   for (int i = 0; i < 3; ++i) D.abase[i] = -H.g[i];
 
   Packer pk;
@@ -517,6 +559,21 @@ int wb_load_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs* pa
   const size_t inert_off = pk.add_vec(H.inert, &D.inert);
   pk.add_vec(H.lev_start, &D.lev_start);
   pk.add_vec(H.lev_links, &D.lev_links);
+  pk.add_vec(H.lvm, &D.lvm);
+  pk.add_vec(H.dfs, &D.dfs);
+  pk.add_vec(H.chain_start, &D.chain_start);
+  pk.add_vec(H.chain, &D.chain);
+  D.maxdepth = H.maxdepth;
+  {
+    float rmin = 0.0f;
+    for (int s2 = 0; s2 < H.S; ++s2) rmin = s2 == 0 ? H.sp[s2].w : std::min(rmin, H.sp[s2].w);
+    D.rmin = rmin;
+    int full = 1;
+    for (uint32_t x : H.bx)
+      if ((x >> 16) != 0xFFFFu) full = 0;
+    D.all_full = full;
+  }
+  D.mimic_shared = H.mimic_shared;
   pk.add_vec(H.child_start, &D.child_start);
   pk.add_vec(H.children, &D.children);
   pk.add_vec(H.jl_start, &D.jl_start);
@@ -634,17 +691,31 @@ static int fused_shape(const wb_robot* R, bool fwd, bool bits, const wb_tune* t,
   int G = (t && t->lanes_per_config) ? t->lanes_per_config : default_G(D);
   if (sched_slot(G) < 0) return fail(WB_EINVAL, "lanes_per_config must be 4, 8, 16 or 32");
   const size_t per = fwd ? fused_fwd_smem_per_config(D, G, bits) : fused_bwd_smem_per_config(D, G);
+  const size_t cta = fused_cta_smem(D);
   const int step = 32 / G;  // configurations per warp
   int cpb = (t && t->configs_per_block) ? t->configs_per_block : 0;
   if (cpb) {
     if (cpb % step) return fail(WB_EINVAL, "configs_per_block must be a multiple of %d", step);
     if (cpb * G > 256) return fail(WB_EINVAL, "configs_per_block * lanes must be <= 256");
   } else {
-    cpb = 256 / G;
-    const size_t cap = 100 * 1024;  // leave room for two CTAs per SM
-    while (cpb > step && per * cpb > cap) cpb -= step;
+    // most resident warps per SM: try every CTA size, keep the best
+    cpb = step;
+    int best_warps = -1;
+    for (int c = step; c * G <= 256; c += step) {
+      const size_t sm = cta + per * c;
+      if (sm > 227 * 1024) break;
+      int nb = 0;
+      cudaError_t e = fwd ? fused_fwd_max_blocks_per_sm(G, c, sm, &nb)
+                          : fused_bwd_max_blocks_per_sm(G, c, sm, &nb);
+      if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+      const int warps = nb * c * G / 32;
+      if (warps > best_warps) {
+        best_warps = warps;
+        cpb = c;
+      }
+    }
   }
-  const size_t smem = per * cpb;
+  const size_t smem = cta + per * cpb;
   if (smem > 227 * 1024)
     return fail(WB_ETOOBIG, "robot needs %zu bytes of shared memory per CTA", smem);
   int bps = (t && t->blocks_per_sm) ? t->blocks_per_sm : 0;
@@ -687,14 +758,34 @@ int wb_eval(wb_robot* robot, int64_t B, const float* q, const float* qd, const f
   if (!d_min && worst_pair) return fail(WB_EINVAL, "worst_pair without d_min");
   DeviceGuard guard(robot->device);
   FwdArgs a{B, q, qd, qdd, link_pose, sphere, d_min, worst_pair, tau, pair_bits};
-  const int kernel = tune ? tune->kernel : WB_KERNEL_AUTO;
+  int kernel = tune ? tune->kernel : WB_KERNEL_AUTO;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool pairs_wanted = d_min || sphere || pair_bits;
+  const bool tree_ok = robot->dev.maxdepth <= tree_max_depth();
+  if (kernel == WB_KERNEL_AUTO)
+    kernel = (tree_ok && (link_pose || !pairs_wanted)) ? WB_KERNEL_TREE : WB_KERNEL_FUSED;
   cudaError_t e;
   if (kernel == WB_KERNEL_PLAIN) {
     if (!plain_fits(robot->dev))
       return fail(WB_ETOOBIG, "plain kernel supports at most 64 links and 256 spheres");
     e = launch_plain_fwd(robot->dev, a, 128, s);
-  } else if (kernel == WB_KERNEL_AUTO || kernel == WB_KERNEL_FUSED) {
+  } else if (kernel == WB_KERNEL_TREE) {
+    if (!tree_ok) return fail(WB_ETOOBIG, "tree deeper than %d levels", tree_max_depth());
+    if (pairs_wanted && !link_pose)
+      return fail(WB_EINVAL, "the tree kernel needs link_pose when spheres or pairs are wanted");
+    e = launch_tree_fwd(robot->dev, a, 128, s);
+    if (e == cudaSuccess && pairs_wanted) {
+      const int warps = 8;
+      int bps = 0;
+      e = pair_max_blocks_per_sm(robot->dev, warps, pair_bits != nullptr, &bps);
+      if (e == cudaSuccess) {
+        if (bps < 1) return fail(WB_ETOOBIG, "pair kernel does not fit on an SM");
+        const int64_t need = (B + warps - 1) / warps;
+        const int grid = (int)std::min<int64_t>(need, (int64_t)bps * robot->num_sms);
+        e = launch_pair(robot->dev, robot->sched[sched_slot(32)], a, grid, warps, s);
+      }
+    }
+  } else if (kernel == WB_KERNEL_FUSED) {
     FusedShape sh;
     if ((rc = fused_shape(robot, true, pair_bits != nullptr, tune, B, sh))) return rc;
     e = launch_fused_fwd(robot->dev, robot->sched[sched_slot(sh.G)], a, sh, s);
@@ -728,14 +819,19 @@ int wb_eval_backward(wb_robot* robot, int64_t B, const float* q, const float* qd
   if ((rc = check_ptr(robot, gqdd, "gqdd", true))) return rc;
   DeviceGuard guard(robot->device);
   BwdArgs a{B, q, qd, qdd, worst_pair, g_pose, g_sphere, g_dmin, g_tau, gq, gqd, gqdd};
-  const int kernel = tune ? tune->kernel : WB_KERNEL_AUTO;
+  int kernel = tune ? tune->kernel : WB_KERNEL_AUTO;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool tree_ok = robot->dev.maxdepth <= tree_max_depth();
+  if (kernel == WB_KERNEL_AUTO) kernel = tree_ok ? WB_KERNEL_TREE : WB_KERNEL_FUSED;
   cudaError_t e;
   if (kernel == WB_KERNEL_PLAIN) {
     if (!plain_fits(robot->dev))
       return fail(WB_ETOOBIG, "plain kernel supports at most 64 links and 256 spheres");
     e = launch_plain_bwd(robot->dev, a, 128, s);
-  } else if (kernel == WB_KERNEL_AUTO || kernel == WB_KERNEL_FUSED) {
+  } else if (kernel == WB_KERNEL_TREE) {
+    if (!tree_ok) return fail(WB_ETOOBIG, "tree deeper than %d levels", tree_max_depth());
+    e = launch_tree_bwd(robot->dev, a, 128, s);
+  } else if (kernel == WB_KERNEL_FUSED) {
     FusedShape sh;
     if ((rc = fused_shape(robot, false, false, tune, B, sh))) return rc;
     e = launch_fused_bwd(robot->dev, a, sh, s);

@@ -20,6 +20,9 @@ struct DevRobot {
   int Sg;      // sphere groups of 4 (S padded up to a multiple of 4)
   int nblk;    // 4x4 group blocks holding at least one pair
   float margin;              // pair filter margin (metres), see the pair stage
+  float etol;                // pair filter tolerance on the squared form (m^2)
+  float rmin;                // smallest sphere radius
+  int all_full;              // every pair block holds all 16 pairs
   float abase[3];            // base acceleration = -gravity
 
   // per link
@@ -34,6 +37,14 @@ struct DevRobot {
   // topology cache (Sec. 6.1.2)
   const int16_t* lev_start;  // [nlev+1]
   const int16_t* lev_links;  // [n] links grouped by level
+  const int2* dfs;           // [n] depth-first pre-order: link, depth
+  int maxdepth;              // deepest link depth + 1
+  int mimic_shared;          // 1 if some joint drives more than one link
+  const int16_t* chain_start;// [n+1] ancestor chains (Alg. 1 "linkChain")
+  const int16_t* chain;      // root -> link, link included
+  const int4* lvm;           // [n] per level-ordered slot: link, parent,
+                             //   (jidx+1) | jtype << 16 | rot_id << 24,
+                             //   child_start | child_end << 16
   const int16_t* child_start;// [n+1]
   const int16_t* children;   // [n]
   const int16_t* jl_start;   // [d+1] links driven by each joint (mimic)
@@ -95,11 +106,19 @@ struct BwdArgs {
 };
 
 // launchers (return cudaGetLastError())
+cudaError_t launch_tree_fwd(const DevRobot& r, const FwdArgs& a, int threads, cudaStream_t s);
+cudaError_t launch_tree_bwd(const DevRobot& r, const BwdArgs& a, int threads, cudaStream_t s);
+int tree_max_depth();
+size_t pair_smem(const DevRobot& r, int warps, bool bits);
+cudaError_t launch_pair(const DevRobot& r, const PairSchedule& ps, const FwdArgs& a, int grid,
+                        int warps, cudaStream_t s);
+cudaError_t pair_max_blocks_per_sm(const DevRobot& r, int warps, bool bits, int* out);
 cudaError_t launch_plain_fwd(const DevRobot& r, const FwdArgs& a, int threads, cudaStream_t s);
 cudaError_t launch_plain_bwd(const DevRobot& r, const BwdArgs& a, int threads, cudaStream_t s);
 
 size_t fused_fwd_smem_per_config(const DevRobot& r, int G, bool bits);
 size_t fused_bwd_smem_per_config(const DevRobot& r, int G);
+size_t fused_cta_smem(const DevRobot& r);  // robot metadata cached per CTA
 cudaError_t launch_fused_fwd(const DevRobot& r, const PairSchedule& ps, const FwdArgs& a,
                              const FusedShape& sh, cudaStream_t s);
 cudaError_t launch_fused_bwd(const DevRobot& r, const BwdArgs& a, const FusedShape& sh,

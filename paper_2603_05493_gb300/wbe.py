@@ -52,6 +52,7 @@ class Tune:
 
 PLAIN = Tune(kernel=L.WB_KERNEL_PLAIN)
 FUSED = Tune(kernel=L.WB_KERNEL_FUSED)
+TREE = Tune(kernel=L.WB_KERNEL_TREE)
 
 
 def _inertial_struct(keep, mass, com, inertia, pm_link=None, pm_mass=None, pm_pos=None):

@@ -33,13 +33,14 @@ def O():
 
 def kernels(W):
     return {"plain": W.PLAIN,
+            "tree": W.TREE,
             "fused4": W.Tune(kernel=2, lanes_per_config=4),
             "fused8": W.Tune(kernel=2, lanes_per_config=8),
             "fused16": W.Tune(kernel=2, lanes_per_config=16),
             "fused32": W.Tune(kernel=2, lanes_per_config=32)}
 
 
-KERNEL_NAMES = ["plain", "fused4", "fused8", "fused16", "fused32"]
+KERNEL_NAMES = ["plain", "tree", "fused4", "fused8", "fused16", "fused32"]
 
 _robots = {}
 
@@ -235,6 +236,13 @@ def test_errors_are_reported(W):
     with pytest.raises(L.WbError) as e:
         rob.eval(q, q, q, tune=W.Tune(kernel=2, lanes_per_config=5))
     assert e.value.code == L.WB_EINVAL
+    # the tree path needs link_pose when spheres or pairs are wanted
+    with pytest.raises(L.WbError) as e:
+        rob.eval(q, q, q, pose=False, tune=W.TREE)
+    assert e.value.code == L.WB_EINVAL
+    # automatic choice falls back to the fused kernels then
+    o = host(rob.eval(q, q, q, pose=False))
+    assert np.isfinite(o["dmin"]).all()
 
 
 def test_autograd_function(W, O):
