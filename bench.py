@@ -7,7 +7,7 @@ configurations of the 48-DoF humanoid-shaped tree (1024 seeds x 32 timesteps
 = 32768 configurations).  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--kernel fused|plain] [--batch B] [--skip-cpu]
+                  [--kernel tree|fused|plain] [--batch B] [--skip-cpu] [--skip-plain]
 
 --impl reference times the FP64 CPU oracle on the host cores instead.
 Under torchrun (N > 1) every rank evaluates its own batch (weak scaling);
@@ -40,14 +40,45 @@ L2_FLUSH_BYTES = 512 << 20
 # algorithmic work per evaluation (flops; FMA = 2) and bytes
 # ---------------------------------------------------------------------------
 def work_per_eval(desc):
+    """Algorithmic flops (FMA = 2) and HBM bytes per evaluation for each kernel
+    of the step: the forward tree sweep (FK + RNEA), the sphere/pair kernel
+    and the backward tree sweep."""
     n = desc.n
     nm = int((desc.jtype != R.FIXED).sum())
     S, P, d = desc.S, desc.P, desc.dof
-    fwd = 150 * nm + 18 * S + 11 * P + 330 * n
-    bwd = 150 * nm + 330 * n + 660 * n + 60 * n + 15 * S
-    fwd_bytes = 4 * (3 * d + 12 * n + 3 * S + 1 + 1 + d)
-    bwd_bytes = 4 * (3 * d + 1 + 12 * n + 3 * S + 1 + d + 3 * d)
-    return {"fwd_flops": fwd, "bwd_flops": bwd, "fwd_bytes": fwd_bytes, "bwd_bytes": bwd_bytes}
+    return {
+        "tree_fwd": {"flops": 150 * nm + 330 * n, "bytes": 4 * (3 * d + 12 * n + d)},
+        "pair": {"flops": 18 * S + 11 * P, "bytes": 4 * (12 * n + 3 * S + 2)},
+        "tree_bwd": {"flops": 150 * nm + 330 * n + 660 * n + 60 * n + 15 * S,
+                     "bytes": 4 * (3 * d + 12 * n + 3 * S + 2 + d + 3 * d)},
+    }
+
+
+# DRAM traffic (read + write) per evaluation from one ncu capture of each
+# kernel (24576 configurations of the humanoid48 workload; traffic scales with
+# the batch).  Keyed by the source file's hash: a changed kernel reads null.
+MEASURED_TRAFFIC = {
+    "tree_fwd": {"src": "paper_2603_05493_gb300/csrc/k_tree.cu",
+                 "sha256": "ee3c59c2eabc8680a652d20c440e662a472e0a2857edf9adbb133af8c0bdbe36",
+                 "bytes_per_eval": (20.451584e6 + 108.546816e6) / 24576},
+    "pair": {"src": "paper_2603_05493_gb300/csrc/k_pair.cu",
+             "sha256": "8f70c86db1727a3df545a52676fd2f5f18fb7b379a8b5cf8ef9a170227063291",
+             "bytes_per_eval": (57.902848e6 + 15.621888e6) / 24576},
+    "tree_bwd": {"src": "paper_2603_05493_gb300/csrc/k_tree.cu",
+                 "sha256": "ee3c59c2eabc8680a652d20c440e662a472e0a2857edf9adbb133af8c0bdbe36",
+                 "bytes_per_eval": (215.058688e6 + 189.910272e6) / 24576},
+}
+
+
+def traffic_per_eval(name):
+    import hashlib
+    t = MEASURED_TRAFFIC.get(name)
+    if not t:
+        return None
+    with open(os.path.join(ROOT, t["src"]), "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != t["sha256"]:
+            return None
+    return t["bytes_per_eval"]
 
 
 def fp32_peak_tflops(num_sms, mhz):
@@ -194,7 +225,7 @@ def run_ours(args, rank, world, local_rank):
     desc = R.r48()
     B = args.batch or CF.HUMANOID48.batch
     rob = wbe.Robot(desc, device=local_rank)
-    tune = wbe.PLAIN if args.kernel == "plain" else wbe.Tune()
+    tune = {"plain": wbe.PLAIN, "fused": wbe.FUSED, "tree": wbe.TREE}[args.kernel]
     seed = CF.HUMANOID48.seed + 101 * rank
     q, qd, qdd = I.uniform_states(desc.dof, B, seed)
     gp, gs, gm, gt = I.upstream_grads(desc, B, seed + 1)
@@ -206,36 +237,52 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step():
-        rob.eval(tq, tqd, tqdd, tune=tune, out=out)
+    fwd_out = {"pose": out["pose"], "sphere": None, "dmin": None, "worst": None,
+               "tau": out["tau"], "bits": None}
+    pair_out = {"sphere": out["sphere"], "dmin": out["dmin"], "worst": out["worst"],
+                "bits": None}
+
+    def step(events=None):
+        # forward: FK + RNEA sweep, then spheres + self-collision; backward
+        if args.kernel != "tree":  # one forward launch
+            rob.eval(tq, tqd, tqdd, tune=tune, out=out)
+            if events:
+                events[1].record(stream)
+                events[2].record(stream)
+        else:
+            rob.eval(tq, tqd, tqdd, tune=tune, out=fwd_out, dmin=False, sphere=False)
+            if events:
+                events[1].record(stream)
+            rob.self_collision(out["pose"], out=pair_out)
+            if events:
+                events[2].record(stream)
         rob.eval_backward(tq, tqd, tqdd, out["worst"], tgp, tgs, tgm, tgt, tune=tune, out=gout)
 
-    for _ in range(max(args.warmup, 3) if args.warmup >= 0 else 3):
+    for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clocks = ClockSampler(local_rank)
     clocks.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     for i in range(args.steps):
         flush.fill_(float(i))  # evict L2 between timed steps (outside the events)
-        e0, e1, e2 = ev[i]
-        e0.record(stream)
-        rob.eval(tq, tqd, tqdd, tune=tune, out=out)
-        e1.record(stream)
-        rob.eval_backward(tq, tqd, tqdd, out["worst"], tgp, tgs, tgm, tgt, tune=tune, out=gout)
-        e2.record(stream)
+        ev[i][0].record(stream)
+        step(ev[i])
+        ev[i][3].record(stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    fwd_ms = [a.elapsed_time(b) for a, b, _ in ev]
-    bwd_ms = [b.elapsed_time(c) for _, b, c in ev]
-    step_ms = float(np.sum(fwd_ms) + np.sum(bwd_ms)) / args.steps
+    k_ms = {"tree_fwd": [e[0].elapsed_time(e[1]) for e in ev],
+            "pair": [e[1].elapsed_time(e[2]) for e in ev],
+            "tree_bwd": [e[2].elapsed_time(e[3]) for e in ev]}
+    step_ms = float(np.mean([e[0].elapsed_time(e[3]) for e in ev]))
+    fwd_ms = [a + b for a, b in zip(k_ms["tree_fwd"], k_ms["pair"])]
+    bwd_ms = k_ms["tree_bwd"]
 
     # end to end through the C ABI: pinned host inputs -> device, forward,
     # backward, results -> pinned host, every step
@@ -263,26 +310,45 @@ def run_ours(args, rank, world, local_rank):
     d2h = int(sum(v.numel() * v.element_size() for v in h_out.values()) +
               sum(x.numel() * x.element_size() for x in h_gout))
 
+    kmean = {k: float(np.mean(v)) for k, v in k_ms.items()}
     if world > 1:
-        t = torch.tensor([step_ms, e2e_ms, float(np.mean(fwd_ms)), float(np.mean(bwd_ms))],
+        t = torch.tensor([step_ms, e2e_ms] + [kmean[k] for k in ("tree_fwd", "pair", "tree_bwd")],
                          device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms, e2e_ms, fwd_mean, bwd_mean = [float(x) for x in t.tolist()]
-    else:
-        fwd_mean, bwd_mean = float(np.mean(fwd_ms)), float(np.mean(bwd_ms))
+        vals = [float(x) for x in t.tolist()]
+        step_ms, e2e_ms = vals[0], vals[1]
+        kmean = dict(zip(("tree_fwd", "pair", "tree_bwd"), vals[2:]))
+    fwd_mean, bwd_mean = kmean["tree_fwd"] + kmean["pair"], kmean["tree_bwd"]
     if rank != 0:
         return
     value = world * B / (step_ms * 1e-3)
     e2e_value = world * B / (e2e_ms * 1e-3)
-    w = work_per_eval(desc)
+    work = work_per_eval(desc)
     peaks = measured_peaks()
     num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    peak = fp32_peak_tflops(num_sms, sm_max)
-    dom_is_fwd = fwd_mean >= bwd_mean
-    dom_ms = fwd_mean if dom_is_fwd else bwd_mean
-    dom_flops = (w["fwd_flops"] if dom_is_fwd else w["bwd_flops"]) * B
-    achieved = dom_flops / (dom_ms * 1e-3) / 1e12
+    alu_peak = fp32_peak_tflops(num_sms, sm_max)
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    ridge = alu_peak * 1e12 / (hbm_peak * 1e9)
+    kernels = {}
+    for name, ms in kmean.items():
+        w = work[name]
+        if ms <= 0:
+            continue
+        if w["flops"] / w["bytes"] >= ridge:
+            ach = w["flops"] * B / (ms * 1e-3) / 1e12
+            kernels[name] = {"bound": "alu", "achieved": ach, "peak": alu_peak,
+                             "unit": "TFLOP/s", "frac": ach / alu_peak}
+        else:
+            ach = w["bytes"] * B / (ms * 1e-3) / 1e9
+            kernels[name] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": ach / hbm_peak}
+        tr = traffic_per_eval(name)
+        kernels[name].update({"ms": ms, "flops_per_eval": w["flops"],
+                              "bytes_per_eval": w["bytes"],
+                              "traffic": None if tr is None else tr * B})
+    kmean = {k: v for k, v in kmean.items() if v > 0}
+    dom = max(kmean, key=kmean.get)
     cpu = None if args.skip_cpu else time_oracle(desc, target_s=args.cpu_s)
     line = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
@@ -295,19 +361,19 @@ def run_ours(args, rank, world, local_rank):
                    "batch_per_gpu": B, "kernel": args.kernel,
                    "l2": "flushed between timed steps (512 MB write outside the events)"},
         "fwd_ms": fwd_mean, "bwd_ms": bwd_mean,
-        "roofline": {"kernel": "fused_fwd_kernel" if dom_is_fwd else "fused_bwd_kernel",
-                     "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "peak_basis": "FP32 FMA: %d SMs x 128 x 2 x %.0f MHz (max SM clock)"
-                                   % (num_sms, sm_max),
-                     "flops_per_eval": w["fwd_flops"] if dom_is_fwd else w["bwd_flops"]},
+        "roofline": dict(kernel=dom + "_kernel", **{k: kernels[dom][k] for k in
+                         ("bound", "achieved", "peak", "unit", "frac", "traffic")},
+                         peak_basis=("FP32 FMA: %d SMs x 128 x 2 x %.0f MHz (max SM clock)"
+                                     % (num_sms, sm_max)) if kernels[dom]["bound"] == "alu"
+                         else "HBM copy bandwidth of measured"),
+        "kernels": kernels,
         "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": (3 if args.kernel == "tree" else 2) * args.steps,
         "clocks": clocks.summary(),
         "cpu_baseline": cpu,
     }
-    if args.kernel == "fused" and not args.skip_plain:
+    if args.kernel == "tree" and not args.skip_plain:
         # the plain one-thread-per-configuration kernels on the same inputs
         for _ in range(2):
             rob.eval(tq, tqd, tqdd, tune=wbe.PLAIN, out=out)
@@ -338,7 +404,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--kernel", choices=["fused", "plain"], default="fused")
+    ap.add_argument("--kernel", choices=["tree", "fused", "plain"], default="tree")
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")

@@ -184,6 +184,17 @@ int wb_eval(wb_robot* robot, int64_t B, const float* q, const float* qd, const f
             float* link_pose, float* sphere, float* d_min, int32_t* worst_pair, float* tau,
             uint32_t* pair_bits, const wb_tune* tune, void* stream);
 
+/* Sphere placement and self-collision from given world link poses: the
+ * second half of the split forward of Sec. 6.1.1 (a first kernel writes the
+ * link transforms, a second reads them and places the spheres) followed by
+ * the pair map-reduce of Sec. 6.2.
+ *   link_pose    [B][n][12] world poses (as written by wb_eval), required
+ *   sphere, d_min, worst_pair, pair_bits  as in wb_eval (nullable; d_min
+ *                and worst_pair go together)
+ * Errors as wb_eval. */
+int wb_self_collision(wb_robot* robot, int64_t B, const float* link_pose, float* sphere,
+                      float* d_min, int32_t* worst_pair, uint32_t* pair_bits, void* stream);
+
 /* Backward pass: the gradient of
  *   L = <g_pose, link_pose> + <g_sphere, sphere> + sum_b g_dmin[b] d_min[b]
  *       + <g_tau, tau>

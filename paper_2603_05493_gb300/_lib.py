@@ -70,6 +70,7 @@ SIGNATURES = {
                                C.POINTER(wb_inertial), C.POINTER(wb_robot_info),
                                C.POINTER(C.c_int32)]),
     "wb_eval": (C.c_int, [p, C.c_int64, p, p, p, p, p, p, p, p, p, C.POINTER(wb_tune), p]),
+    "wb_self_collision": (C.c_int, [p, C.c_int64, p, p, p, p, p, p]),
     "wb_eval_backward": (C.c_int, [p, C.c_int64, p, p, p, p, p, p, p, p, p, p, p,
                                    C.POINTER(wb_tune), p]),
     "wb_free_robot": (None, [p]),

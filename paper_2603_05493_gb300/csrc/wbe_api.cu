@@ -67,6 +67,7 @@ struct wb_robot {
   size_t dbytes = 0;
   float* d_inert = nullptr;   // device inertia array (inside dmem)
   PairSchedule sched[4]{};    // G = 4, 8, 16, 32
+  PairSchedule32 sched32{};   // the pair kernel's (byte-offset encoding)
   wb_robot_info info{};
   // host copies needed by set_inertials
   int n = 0, S = 0;
@@ -393,6 +394,7 @@ static int plan_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs
     blk_pidx[16 * (size_t)b + bit] = p;
   }
   if (blk_pidx.empty()) blk_pidx.assign(16, -1);
+  if (bx.size() > 65535) return fail(WB_ETOOBIG, "%zu pair blocks > 65535", bx.size());
 
   // ---- inertia ----
   std::vector<float> inert;
@@ -594,6 +596,13 @@ int wb_load_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs* pa
     R->sched[t].rounds = H.bx.empty() ? 0 : rounds;
     pk.add_vec(ents[t], &R->sched[t].ent);
   }
+  std::vector<uint2> ent32(ents[3]);
+  for (auto& e : ent32) {
+    const uint32_t gi = e.x & 0xFF, gj = (e.x >> 8) & 0xFF, mask = e.x >> 16;
+    e = uint2{(16u * gi) | ((16u * gj) << 16), (mask << 16) | (e.y & 0xFFFF)};
+  }
+  R->sched32.rounds = R->sched[3].rounds;
+  pk.add_vec(ent32, &R->sched32.ent);
   cudaError_t e = cudaMalloc(&R->dmem, pk.host.size());
   if (e != cudaSuccess) {
     delete R;
@@ -782,7 +791,7 @@ int wb_eval(wb_robot* robot, int64_t B, const float* q, const float* qd, const f
         if (bps < 1) return fail(WB_ETOOBIG, "pair kernel does not fit on an SM");
         const int64_t need = (B + warps - 1) / warps;
         const int grid = (int)std::min<int64_t>(need, (int64_t)bps * robot->num_sms);
-        e = launch_pair(robot->dev, robot->sched[sched_slot(32)], a, grid, warps, s);
+        e = launch_pair(robot->dev, robot->sched32, a, grid, warps, s);
       }
     }
   } else if (kernel == WB_KERNEL_FUSED) {
@@ -793,6 +802,35 @@ int wb_eval(wb_robot* robot, int64_t B, const float* q, const float* qd, const f
     return fail(WB_EINVAL, "unknown kernel %d", kernel);
   }
   if (e != cudaSuccess) return cuda_fail(e, "wb_eval launch");
+  return WB_OK;
+}
+
+int wb_self_collision(wb_robot* robot, int64_t B, const float* link_pose, float* sphere,
+                      float* d_min, int32_t* worst_pair, uint32_t* pair_bits, void* stream) {
+  g_err.clear();
+  if (!robot) return fail(WB_EINVAL, "robot is NULL");
+  if (B < 0) return fail(WB_EINVAL, "B < 0");
+  if (B == 0) return WB_OK;
+  int rc;
+  if ((rc = check_ptr(robot, link_pose, "link_pose", true))) return rc;
+  if ((rc = check_ptr(robot, sphere, "sphere", false))) return rc;
+  if ((rc = check_ptr(robot, d_min, "d_min", false))) return rc;
+  if ((rc = check_ptr(robot, worst_pair, "worst_pair", d_min != nullptr))) return rc;
+  if ((rc = check_ptr(robot, pair_bits, "pair_bits", false))) return rc;
+  if (!d_min && worst_pair) return fail(WB_EINVAL, "worst_pair without d_min");
+  if (!d_min && !sphere && !pair_bits) return WB_OK;
+  DeviceGuard guard(robot->device);
+  FwdArgs a{B, nullptr, nullptr, nullptr, const_cast<float*>(link_pose), sphere, d_min,
+            worst_pair, nullptr, pair_bits};
+  const int warps = 8;
+  int bps = 0;
+  cudaError_t e = pair_max_blocks_per_sm(robot->dev, warps, pair_bits != nullptr, &bps);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+  if (bps < 1) return fail(WB_ETOOBIG, "pair kernel does not fit on an SM");
+  const int64_t need = (B + warps - 1) / warps;
+  const int grid = (int)std::min<int64_t>(need, (int64_t)bps * robot->num_sms);
+  e = launch_pair(robot->dev, robot->sched32, a, grid, warps, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "wb_self_collision launch");
   return WB_OK;
 }
 

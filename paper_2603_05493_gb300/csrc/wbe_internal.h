@@ -69,6 +69,15 @@ struct PairSchedule {
   const uint2* ent;          // [rounds][G]
 };
 
+// The same blocks dealt to 32 lanes for the warp-per-configuration pair
+// kernel, encoded with byte offsets: x = 16 gi | (16 gj) << 16 (offsets of
+// the row / column group within one per-warp sphere array), y = mask << 16 |
+// block id; mask 0 = no work.
+struct PairSchedule32 {
+  int rounds;
+  const uint2* ent;          // [rounds + 1][32], the last round all null
+};
+
 // Kernel-side launch configuration of the fused kernels.
 struct FusedShape {
   int G;                     // lanes per configuration (4, 8, 16, 32)
@@ -110,7 +119,7 @@ cudaError_t launch_tree_fwd(const DevRobot& r, const FwdArgs& a, int threads, cu
 cudaError_t launch_tree_bwd(const DevRobot& r, const BwdArgs& a, int threads, cudaStream_t s);
 int tree_max_depth();
 size_t pair_smem(const DevRobot& r, int warps, bool bits);
-cudaError_t launch_pair(const DevRobot& r, const PairSchedule& ps, const FwdArgs& a, int grid,
+cudaError_t launch_pair(const DevRobot& r, const PairSchedule32& ps, const FwdArgs& a, int grid,
                         int warps, cudaStream_t s);
 cudaError_t pair_max_blocks_per_sm(const DevRobot& r, int warps, bool bits, int* out);
 cudaError_t launch_plain_fwd(const DevRobot& r, const FwdArgs& a, int threads, cudaStream_t s);

@@ -177,6 +177,19 @@ class Robot:
                 "wb_eval")
         return o
 
+    def self_collision(self, link_pose, *, sphere=True, dmin=True, bits=False, out=None,
+                       stream=None):
+        """Spheres and the pair map-reduce from given world link poses
+        (B, n, 12); returns a dict with sphere, dmin, worst, bits."""
+        B = link_pose.shape[0]
+        o = out if out is not None else self.empty_outputs(B, pose=False, sphere=sphere,
+                                                           dmin=dmin, tau=False, bits=bits)
+        L.check(self.lib.wb_self_collision(self.handle, B, _ptr(link_pose), _ptr(o.get("sphere")),
+                                           _ptr(o.get("dmin")), _ptr(o.get("worst")),
+                                           _ptr(o.get("bits")), _stream(stream)),
+                "wb_self_collision")
+        return o
+
     def eval_backward(self, q, qd, qdd, worst=None, g_pose=None, g_sphere=None, g_dmin=None,
                       g_tau=None, *, tune: Tune | None = None, out=None, stream=None):
         """Gradient of <g_pose,pose> + <g_sphere,sphere> + g_dmin.d_min +

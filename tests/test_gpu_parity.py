@@ -269,3 +269,18 @@ def test_deterministic(W):
     for k in a:
         if a[k] is not None:
             assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("rname", ["R48", "mixed"])
+def test_self_collision_from_poses(W, O, rname):
+    """Spheres and the pair map-reduce from given link poses (the split
+    forward): same results as the oracle, bits included."""
+    desc, rob = robot(W, rname)
+    B = 131
+    q, qd, qdd = I.uniform_states(desc.dof, B, seed=21)
+    o = rob.eval(cuda(q), cuda(qd), cuda(qdd), sphere=False, dmin=False, tau=False,
+                 tune=W.TREE)
+    sc = host(rob.self_collision(o["pose"], bits=True))
+    torch.cuda.synchronize()
+    sc["pose"] = o["pose"].cpu().numpy()
+    PY.check_forward(desc, sc, O.evaluate(desc, q, want=("pose", "sph", "dmin")))
