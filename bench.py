@@ -398,6 +398,89 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_uneven(args):
+    """Uneven batch: 256 x R7 + 256 x R23 + 256 x R48 problems with horizons
+    U{16..64}, forward (FK + RNEA, spheres + self-collision) and backward in
+    one persistent launch per pass, captured once in a CUDA graph and
+    replayed.  Value = configurations per second (sum of horizons / step)."""
+    import torch
+    from paper_2603_05493_gb300 import build
+    build()
+    from paper_2603_05493_gb300 import wbe
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    mix = I.uneven_mix()
+    robs = [wbe.Robot(d, device=0) for d in mix.robots]
+    problems = list(zip(mix.robot_of.tolist(), mix.horizon.tolist()))
+    batch = wbe.Batch(robs, problems)
+    total = int(mix.horizon.sum())
+
+    def packed(kind, make, dtype=torch.float32):
+        out = batch.empty(kind, dtype)
+        for p, (ri, H) in enumerate(problems):
+            x = make(mix.robots[ri], H, 7000 + p)
+            o = int(batch.offsets[kind][p])
+            t = torch.from_numpy(np.ascontiguousarray(x)).reshape(-1).to(dev)
+            out[o:o + t.numel()] = t
+        return out
+    q = packed("joint", lambda d, H, s: I.uniform_states(d.dof, H, s)[0])
+    qd = packed("joint", lambda d, H, s: I.uniform_states(d.dof, H, s)[1])
+    qdd = packed("joint", lambda d, H, s: I.uniform_states(d.dof, H, s)[2])
+    gp = packed("pose", lambda d, H, s: I.upstream_grads(d, H, s)[0])
+    gs = packed("sphere", lambda d, H, s: I.upstream_grads(d, H, s)[1])
+    gm = packed("config", lambda d, H, s: I.upstream_grads(d, H, s)[2])
+    gt = packed("joint", lambda d, H, s: I.upstream_grads(d, H, s)[3])
+    pose, sph, dmin, tau = batch.empty("pose"), batch.empty("sphere"), batch.empty("config"), \
+        batch.empty("joint")
+    worst = batch.empty("config", torch.int32)
+    g = [batch.empty("joint") for _ in range(3)]
+
+    def step():
+        batch.eval(q, qd, qdd, pose, sph, dmin, worst, tau)
+        batch.eval_backward(q, qd, qdd, worst, gp, gs, gm, gt, *g)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            step()
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
+    for _ in range(max(args.warmup, 3)):
+        graph.replay()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ts = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        graph.replay()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    clocks.stop()
+    ms = float(np.mean(ts))
+    tunes = {}
+    for d, rob in zip(mix.robots, robs):
+        f, bw, fm, bm = rob.autotune(2048)
+        tunes[d.name] = {"fwd": f.__dict__, "bwd": bw.__dict__, "fwd_ms_2048": fm,
+                         "bwd_ms_2048": bm}
+    print(json.dumps({
+        "metric": "uneven-batch evals/s (R7/R23/R48 problems, fwd+bwd, one graph)",
+        "value": total / (ms * 1e-3), "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "uneven: 256 x R7 + 256 x R23 + 256 x R48, horizons U{16..64}",
+                   "configurations": total, "problems": len(problems),
+                   "l2": "flushed between timed steps"},
+        "gpu_launches": 3 * args.steps, "clocks": clocks.summary(),
+        "autotune_single_robot_b2048": tunes}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -410,12 +493,16 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--cpu-s", type=float, default=15.0)
     ap.add_argument("--ref-step-s", type=float, default=10.0)
+    ap.add_argument("--workload", choices=["humanoid48", "uneven"], default="humanoid48")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "uneven":
+        run_uneven(args)
         return
     if world > 1:
         import torch

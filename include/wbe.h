@@ -127,8 +127,10 @@ typedef struct {
 typedef struct {
   int32_t kernel;            /* WB_KERNEL_* (AUTO: TREE when it applies, else FUSED) */
   int32_t lanes_per_config;  /* fused: 4, 8, 16 or 32 (0 = robot default) */
-  int32_t configs_per_block; /* fused: configurations per CTA (0 = default) */
-  int32_t blocks_per_sm;     /* grid = blocks_per_sm * SMs (0 = occupancy) */
+  int32_t configs_per_block; /* fused: configurations per CTA; tree: threads per block
+                                of the sweep kernels (32..256); 0 = default */
+  int32_t blocks_per_sm;     /* fused: grid = blocks_per_sm * SMs (0 = occupancy);
+                                tree: warps per block of the pair kernel (0 = 8) */
 } wb_tune;
 
 typedef struct {
@@ -212,7 +214,58 @@ int wb_eval_backward(wb_robot* robot, int64_t B, const float* q, const float* qd
                      const float* g_sphere, const float* g_dmin, const float* g_tau, float* gq,
                      float* gqd, float* gqdd, const wb_tune* tune, void* stream);
 
+/* Autotuner (a setup-time call: it allocates scratch buffers for B
+ * configurations, synchronises the device and must not be captured).  Times
+ * every applicable kernel family and launch shape -- depth-first sweep kernels
+ * with 64 / 128 / 256 threads per block and 4 / 8 warps per pair block, fused
+ * kernels with 4, 8, 16 and 32 lanes per configuration, the plain kernels --
+ * on random states with all outputs (forward) and all upstream gradients
+ * (backward), and returns the fastest choice for each pass with its median
+ * time (ms, nullable). */
+int wb_autotune(wb_robot* robot, int64_t B, wb_tune* fwd, wb_tune* bwd, float* fwd_ms,
+                float* bwd_ms);
+
 void wb_free_robot(wb_robot* robot);
+
+/* ---------------------------------------------------------------------------
+ * Uneven batches (several robots, uneven horizons) in one persistent launch
+ * per pass.  A problem is (robot index, horizon H); problem p owns slices of
+ * packed arrays:
+ *   joint-major  [d_p][H_p]       q, qd, qdd, tau, gradients (offset joint[p])
+ *   poses        [H_p][n_p][12]   (offset pose[p])
+ *   spheres      [H_p][S_p][3]    (offset sphere[p])
+ *   per config   [H_p]            d_min, worst pair, g_dmin (offset config[p])
+ * (offsets in elements, from wb_batch_offsets).  Work items are sorted by cost
+ * and pulled by the warps of a persistent grid through an atomic counter held
+ * by the batch object (cleared on the stream before each launch): calls on
+ * one batch object must not overlap on the GPU; use one object per stream.
+ * Forward and backward are graph-capturable.  Robots must stay alive while
+ * the batch exists. */
+typedef struct {
+  int32_t robot;   /* index into the robots array of wb_batch_create */
+  int32_t horizon; /* configurations of this problem, >= 0 */
+} wb_problem;
+
+typedef struct {
+  int64_t joint_elems, pose_elems, sphere_elems, configs; /* packed array lengths */
+  int32_t n_problems, n_robots;
+} wb_batch_sizes;
+
+int wb_batch_create(wb_robot* const* robots, int32_t n_robots, const wb_problem* problems,
+                    int32_t n_problems, wb_batch** out);
+int wb_batch_sizes_get(const wb_batch* batch, wb_batch_sizes* out);
+/* per-problem offsets into the packed arrays (host arrays of n_problems) */
+int wb_batch_offsets(const wb_batch* batch, int64_t* joint, int64_t* pose, int64_t* sphere,
+                     int64_t* config);
+/* link_pose is required when sphere or d_min is wanted (the pair pass reads it) */
+int wb_batch_eval(wb_batch* batch, const float* q, const float* qd, const float* qdd,
+                  float* link_pose, float* sphere, float* d_min, int32_t* worst_pair, float* tau,
+                  void* stream);
+int wb_batch_eval_backward(wb_batch* batch, const float* q, const float* qd, const float* qdd,
+                           const int32_t* worst_pair, const float* g_pose, const float* g_sphere,
+                           const float* g_dmin, const float* g_tau, float* gq, float* gqd,
+                           float* gqdd, void* stream);
+void wb_free_batch(wb_batch* batch);
 
 /* Message describing the calling thread's most recent error ("" if none). */
 const char* wb_last_error(void);

@@ -52,6 +52,16 @@ class wb_tune(C.Structure):
                 ("configs_per_block", C.c_int32), ("blocks_per_sm", C.c_int32)]
 
 
+class wb_problem(C.Structure):
+    _fields_ = [("robot", C.c_int32), ("horizon", C.c_int32)]
+
+
+class wb_batch_sizes(C.Structure):
+    _fields_ = [("joint_elems", C.c_int64), ("pose_elems", C.c_int64),
+                ("sphere_elems", C.c_int64), ("configs", C.c_int64),
+                ("n_problems", C.c_int32), ("n_robots", C.c_int32)]
+
+
 class wb_robot_info(C.Structure):
     _fields_ = [("n_links", C.c_int32), ("dof", C.c_int32), ("n_spheres", C.c_int32),
                 ("n_pairs", C.c_int32), ("n_levels", C.c_int32), ("max_level_width", C.c_int32),
@@ -74,6 +84,15 @@ SIGNATURES = {
     "wb_eval_backward": (C.c_int, [p, C.c_int64, p, p, p, p, p, p, p, p, p, p, p,
                                    C.POINTER(wb_tune), p]),
     "wb_free_robot": (None, [p]),
+    "wb_autotune": (C.c_int, [p, C.c_int64, C.POINTER(wb_tune), C.POINTER(wb_tune),
+                              C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+    "wb_batch_create": (C.c_int, [C.POINTER(p), C.c_int32, C.POINTER(wb_problem), C.c_int32,
+                                  C.POINTER(p)]),
+    "wb_batch_sizes_get": (C.c_int, [p, C.POINTER(wb_batch_sizes)]),
+    "wb_batch_offsets": (C.c_int, [p, p, p, p, p]),
+    "wb_batch_eval": (C.c_int, [p, p, p, p, p, p, p, p, p, p]),
+    "wb_batch_eval_backward": (C.c_int, [p, p, p, p, p, p, p, p, p, p, p, p, p]),
+    "wb_free_batch": (None, [p]),
 }
 
 _lib = None

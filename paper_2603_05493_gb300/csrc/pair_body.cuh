@@ -1,0 +1,288 @@
+// pair_body.cuh -- sphere placement and the self-collision map-reduce
+// (Sec. 6.2), one warp per configuration (device code shared by the
+// single-robot and the batched pair kernels).
+//
+// A warp stages its configuration's world link poses (config-major, written by
+// the tree kernel) into shared memory with vector loads, places the spheres
+// (c_s = R_l c_local + p_l, Sec. 6.1.1) as SoA arrays -- column copies x, y,
+// z, N = |c|^2 - r^2 and row copies pre-scaled by -2 -- and writes the
+// sphere output.  The pair blocks (4x4 sphere groups, dealt by the host so
+// that the 8 lanes of a shared-memory phase read distinct bank groups, rows
+// kept per lane in runs) are then screened with
+//   e = |c_i - c_j|^2 - t^2,  t = T_i + r_j,  T_i = max(best + r_i + margin, -r_min),
+// expanded as (|c_i|^2 - T_i^2) + (|c_j|^2 - r_j^2) - 2 c_i . c_j - 2 T_i r_j
+// (one add and four fused multiply-adds per pair); e < 0 exactly when
+// |c_i - c_j| < t.  Raising T_i to -r_min only widens the screen, and keeps
+// t >= 0 so that t^2 is monotone.
+// best is the warp-wide running minimum, refreshed every two rounds with one
+// integer min-reduction over an order-preserving key, so the exact path --
+// sqrt distance, pair index, lexicographic (d, index) compare -- only runs
+// for screened-in pairs, one candidate at a time.  The screen fires on
+// e < etol, a host bound on the float rounding of the expanded form, so it
+// never drops a pair the exact path would keep.  A 5-step shuffle reduction
+// of (d, index) finishes the configuration: one configuration never spans
+// more than one warp, so the paper's second reduce kernel becomes a register
+// reduction.
+#pragma once
+
+#include "spatial.cuh"
+
+#include <climits>
+
+namespace wbe {
+
+__host__ __device__ constexpr int a32(int x) { return (x + 31) & ~31; }
+
+struct PairPlan {  // per warp, 32-bit words
+  int xr, yr, zr, xc, yc, zc, nn, bits, total;
+  __host__ __device__ PairPlan(int n, int Sg, int P, bool with_bits) {
+    const int m = a32(4 * Sg);
+    const int ra = 3 * m > a32(12 * n) ? 3 * m : a32(12 * n);  // rows; poses while staging
+    xr = 0;
+    yr = m;
+    zr = 2 * m;
+    xc = ra;
+    yc = ra + m;
+    zc = ra + 2 * m;
+    nn = ra + 3 * m;
+    bits = ra + 4 * m;
+    total = bits + (with_bits ? a32((P + 31) / 32) : 0);
+  }
+};
+
+inline size_t pair_smem(const DevRobot& r, int warps, bool bits) {
+  return sizeof(float) *
+         ((size_t)a32(4 * r.Sg) + (size_t)warps * PairPlan(r.n, r.Sg, r.P, bits).total);
+}
+
+// order-preserving map of a float to a signed int (and back)
+__device__ __forceinline__ int fkey(float f) {
+  const int i = __float_as_int(f);
+  return i < 0 ? i ^ 0x7FFFFFFF : i;
+}
+__device__ __forceinline__ float fkey_inv(int k) { return __int_as_float(k < 0 ? k ^ 0x7FFFFFFF : k); }
+
+__device__ __forceinline__ float4 lds4(const char* base, uint32_t off) {
+  return *reinterpret_cast<const float4*>(base + off);
+}
+__device__ __forceinline__ float pick(const float4& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+template <bool FULL, bool BITS>
+__device__ __forceinline__ void pair_one(const DevRobot& r, const PairSchedule32& ps,
+                                         const FwdArgs& A, int64_t b, float* ws,
+                                         const float4* radw, int lane) {
+  const PairPlan pl(r.n, r.Sg, r.P, BITS);
+  float* xr = ws + pl.xr;
+  float* yr = ws + pl.yr;
+  float* zr = ws + pl.zr;
+  float* xc = ws + pl.xc;
+  float* yc = ws + pl.yc;
+  float* zc = ws + pl.zc;
+  float* nn = ws + pl.nn;
+  uint32_t* bm = reinterpret_cast<uint32_t*>(ws + pl.bits);
+  const char* cxr = reinterpret_cast<const char*>(xr);
+  const char* cyr = reinterpret_cast<const char*>(yr);
+  const char* czr = reinterpret_cast<const char*>(zr);
+  const char* cxc = reinterpret_cast<const char*>(xc);
+  const char* cyc = reinterpret_cast<const char*>(yc);
+  const char* czc = reinterpret_cast<const char*>(zc);
+  const char* cnn = reinterpret_cast<const char*>(nn);
+  const char* crad = reinterpret_cast<const char*>(radw);
+  const int n = r.n, S = r.S;
+  const int W = (r.P + 31) >> 5;
+  const float margin = r.margin, etol = r.etol, nrmin = -r.rmin;
+  const int rounds = ps.rounds;
+  // ---- stage the link poses (contiguous), then place the spheres ----
+  {
+    const float4* src = reinterpret_cast<const float4*>(A.pose + b * (int64_t)n * 12);
+    float4* dst = reinterpret_cast<float4*>(xr);
+#pragma unroll 4
+    for (int i = lane; i < 3 * n; i += 32) dst[i] = __ldg(src + i);
+  }
+  __syncwarp();
+  for (int s = lane; s < 4 * r.Sg; s += 32) {
+    float c[3] = {0.0f, 0.0f, 0.0f};
+    float rs = 0.0f;
+    if (s < S) {
+      const float4 sp = __ldg(r.sph + s);
+      const float* P = xr + 12 * __ldg(r.sph_link + s);
+      const float cl[3] = {sp.x, sp.y, sp.z};
+      rot(P, cl, c);
+      c[0] += P[9];
+      c[1] += P[10];
+      c[2] += P[11];
+      rs = sp.w;
+      if (A.sph) {
+        float* o = A.sph + (b * S + s) * 3;
+        o[0] = c[0];
+        o[1] = c[1];
+        o[2] = c[2];
+      }
+    }
+    xc[s] = c[0];
+    yc[s] = c[1];
+    zc[s] = c[2];
+    nn[s] = fmaf(-rs, rs, fmaf(c[2], c[2], fmaf(c[1], c[1], c[0] * c[0])));  // |c|^2 - r^2
+  }
+  __syncwarp();
+  for (int s = lane; s < 4 * r.Sg; s += 32) {  // row copies, pre-scaled by -2
+    xr[s] = -2.0f * xc[s];
+    yr[s] = -2.0f * yc[s];
+    zr[s] = -2.0f * zc[s];
+  }
+  if (BITS)
+    for (int w = lane; w < W; w += 32) bm[w] = 0u;
+  __syncwarp();
+  if (!A.dmin && !BITS) return;  // sphere placement only
+  if (rounds == 0) {
+    if (lane == 0 && A.dmin) {
+      A.dmin[b] = __int_as_float(0x7f800000);
+      A.worst[b] = -1;
+    }
+    if (BITS)
+      for (int w = lane; w < W; w += 32) A.bits[b * (int64_t)W + w] = 0u;
+    return;
+  }
+  float best = 1e15f;
+  int bidx = INT_MAX;
+  uint2 nxt = __ldg(ps.ent + lane);
+  // seed: the exact distance of one pair of the lane's first block
+  if (FULL && (nxt.y >> 16) != 0u) {
+    const uint32_t ro = nxt.x & 0xFFFF, co = nxt.x >> 16;
+    const float* pi = reinterpret_cast<const float*>(cxc + ro);
+    const float* pj = reinterpret_cast<const float*>(cxc + co);
+    const float d2 = dist2(pi[0], *reinterpret_cast<const float*>(cyc + ro),
+                           *reinterpret_cast<const float*>(czc + ro), pj[0],
+                           *reinterpret_cast<const float*>(cyc + co),
+                           *reinterpret_cast<const float*>(czc + co));
+    best = sqrtf(d2) - (lds4(crad, ro).x + lds4(crad, co).x);
+    bidx = 16 * (nxt.y & 0xFFFF);
+  }
+  float gbest = fkey_inv(__reduce_min_sync(0xffffffffu, fkey(best)));
+  uint32_t cur = 0xFFFFFFFFu;
+  float4 XR = {}, YR = {}, ZR = {}, RR = {}, CC = {};
+  float Ai[4], ti2[4];
+  auto set_row = [&]() {
+    const float bb = fminf(best, gbest) + margin;
+    const float T0 = fmaxf(bb + RR.x, nrmin), T1 = fmaxf(bb + RR.y, nrmin);
+    const float T2 = fmaxf(bb + RR.z, nrmin), T3 = fmaxf(bb + RR.w, nrmin);
+    Ai[0] = fmaf(-T0, T0, CC.x);
+    Ai[1] = fmaf(-T1, T1, CC.y);
+    Ai[2] = fmaf(-T2, T2, CC.z);
+    Ai[3] = fmaf(-T3, T3, CC.w);
+    ti2[0] = -2.0f * T0;
+    ti2[1] = -2.0f * T1;
+    ti2[2] = -2.0f * T2;
+    ti2[3] = -2.0f * T3;
+  };
+  for (int rr = 0; rr < rounds; ++rr) {
+    const uint2 e = nxt;
+    nxt = __ldg(ps.ent + (rr + 1) * 32 + lane);  // the schedule has a null round at the end
+    const uint32_t ro = e.x & 0xFFFF, co = e.x >> 16;
+    const uint32_t mask = e.y >> 16;
+    if (ro != cur) {
+      cur = ro;
+      XR = lds4(cxr, ro);
+      YR = lds4(cyr, ro);
+      ZR = lds4(czr, ro);
+      RR = lds4(crad, ro);
+      const float4 N = lds4(cnn, ro);
+      CC = make_float4(fmaf(RR.x, RR.x, N.x), fmaf(RR.y, RR.y, N.y), fmaf(RR.z, RR.z, N.z),
+                       fmaf(RR.w, RR.w, N.w));  // |c_i|^2
+      set_row();
+    }
+    const float4 X = lds4(cxc, co), Y = lds4(cyc, co), Z = lds4(czc, co), N = lds4(cnn, co),
+                 Rc = lds4(crad, co);
+    const float xr4[4] = {XR.x, XR.y, XR.z, XR.w}, yr4[4] = {YR.x, YR.y, YR.z, YR.w},
+                zr4[4] = {ZR.x, ZR.y, ZR.z, ZR.w};
+    const float xj[4] = {X.x, X.y, X.z, X.w}, yj[4] = {Y.x, Y.y, Y.z, Y.w},
+                zj[4] = {Z.x, Z.y, Z.z, Z.w}, nj[4] = {N.x, N.y, N.z, N.w},
+                rj[4] = {Rc.x, Rc.y, Rc.z, Rc.w};
+    // e(a, c) = |c_a - c_c|^2 - t^2 with t = T_a + r_c, expanded
+    auto screen = [&](int a, int c) {
+      return fmaf(ti2[a], rj[c],
+                  fmaf(zr4[a], zj[c], fmaf(yr4[a], yj[c], fmaf(xr4[a], xj[c], Ai[a] + nj[c]))));
+    };
+    float m;
+    if (FULL) {
+      float m4[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+        m4[a] = fminf(fminf(screen(a, 0), screen(a, 1)), fminf(screen(a, 2), screen(a, 3)));
+      m = fminf(fminf(m4[0], m4[1]), fminf(m4[2], m4[3]));
+      m = mask ? m : __int_as_float(0x7f800000);  // null entries at the schedule's tail
+    } else {
+      m = __int_as_float(0x7f800000);
+#pragma unroll
+      for (int t = 0; t < 16; ++t)
+        if ((mask >> t) & 1u) m = fminf(m, screen(t >> 2, t & 3));
+    }
+    if (m < etol) {
+      // candidates of this block, then the exact path one at a time
+      uint32_t cand = 0u;
+#pragma unroll
+      for (int t = 0; t < 16; ++t) cand |= (screen(t >> 2, t & 3) < etol ? 1u : 0u) << t;
+      cand &= mask;
+      while (cand) {
+        const int t = __ffs(cand) - 1;
+        cand &= cand - 1u;
+        const int a = t >> 2, c = t & 3;
+        const float d2 = dist2(-0.5f * pick(XR, a), -0.5f * pick(YR, a), -0.5f * pick(ZR, a),
+                               pick(X, c), pick(Y, c), pick(Z, c));
+        const float dd = sqrtf(d2) - (pick(RR, a) + pick(Rc, c));
+        const int slot = 16 * (e.y & 0xFFFF) + t;  // row of blk_pidx: resolved at the end
+        if (dd < best) {
+          best = dd;
+          bidx = slot;
+        } else if (dd == best && bidx != INT_MAX &&
+                   __ldg(r.blk_pidx + slot) < __ldg(r.blk_pidx + bidx)) {
+          bidx = slot;  // exact tie: the smaller pair index wins
+        }
+      }
+      set_row();
+    }
+    if (BITS && mask) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if ((mask >> (4 * a + c)) & 1u) {
+            const float d2 = dist2(-0.5f * xr4[a], -0.5f * yr4[a], -0.5f * zr4[a], xj[c], yj[c],
+                                   zj[c]);
+            if (sqrtf(d2) - (pick(RR, a) + rj[c]) < 0.0f) {
+              const int pidx = __ldg(r.blk_pidx + 16 * (e.y & 0xFFFF) + 4 * a + c);
+              atomicOr(bm + (pidx >> 5), 1u << (pidx & 31));
+            }
+          }
+        }
+    }
+    if (rr & 1) {  // group-wide best, every two rounds
+      gbest = fminf(gbest, fkey_inv(__reduce_min_sync(0xffffffffu, fkey(best))));
+      set_row();
+    }
+  }
+  bidx = bidx == INT_MAX ? INT_MAX : __ldg(r.blk_pidx + bidx);  // slot -> pair index
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, bidx, off);
+    if (ob < best || (ob == best && oi < bidx)) {
+      best = ob;
+      bidx = oi;
+    }
+  }
+  if (lane == 0 && A.dmin) {
+    const bool none = bidx == INT_MAX;
+    A.dmin[b] = none ? __int_as_float(0x7f800000) : best;
+    A.worst[b] = none ? -1 : bidx;
+  }
+  if (BITS) {
+    __syncwarp();
+    for (int w = lane; w < W; w += 32) A.bits[b * (int64_t)W + w] = bm[w];
+  }
+  __syncwarp();
+}
+
+}  // namespace wbe

@@ -782,9 +782,13 @@ int wb_eval(wb_robot* robot, int64_t B, const float* q, const float* qd, const f
     if (!tree_ok) return fail(WB_ETOOBIG, "tree deeper than %d levels", tree_max_depth());
     if (pairs_wanted && !link_pose)
       return fail(WB_EINVAL, "the tree kernel needs link_pose when spheres or pairs are wanted");
-    e = launch_tree_fwd(robot->dev, a, 128, s);
+    const int tpb = (tune && tune->configs_per_block) ? tune->configs_per_block : 128;
+    if (tpb < 32 || tpb > 256 || tpb % 32)
+      return fail(WB_EINVAL, "tree threads per block must be a multiple of 32 in [32, 256]");
+    const int warps = (tune && tune->blocks_per_sm) ? tune->blocks_per_sm : 8;
+    if (warps < 1 || warps > 8) return fail(WB_EINVAL, "pair warps per block must be in [1, 8]");
+    e = launch_tree_fwd(robot->dev, a, tpb, s);
     if (e == cudaSuccess && pairs_wanted) {
-      const int warps = 8;
       int bps = 0;
       e = pair_max_blocks_per_sm(robot->dev, warps, pair_bits != nullptr, &bps);
       if (e == cudaSuccess) {
@@ -868,7 +872,10 @@ int wb_eval_backward(wb_robot* robot, int64_t B, const float* q, const float* qd
     e = launch_plain_bwd(robot->dev, a, 128, s);
   } else if (kernel == WB_KERNEL_TREE) {
     if (!tree_ok) return fail(WB_ETOOBIG, "tree deeper than %d levels", tree_max_depth());
-    e = launch_tree_bwd(robot->dev, a, 128, s);
+    const int tpb = (tune && tune->configs_per_block) ? tune->configs_per_block : 128;
+    if (tpb < 32 || tpb > 256 || tpb % 32)
+      return fail(WB_EINVAL, "tree threads per block must be a multiple of 32 in [32, 256]");
+    e = launch_tree_bwd(robot->dev, a, tpb, s);
   } else if (kernel == WB_KERNEL_FUSED) {
     FusedShape sh;
     if ((rc = fused_shape(robot, false, false, tune, B, sh))) return rc;
@@ -881,3 +888,352 @@ int wb_eval_backward(wb_robot* robot, int64_t B, const float* q, const float* qd
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// uneven batches
+// ---------------------------------------------------------------------------
+struct wb_batch {
+  int device = 0;
+  int num_sms = 0;
+  std::vector<wb_robot*> robots;
+  std::vector<BatchProblemDev> probs;
+  void* dmem = nullptr;
+  const DevRobot* d_robots = nullptr;
+  const PairSchedule32* d_scheds = nullptr;
+  const BatchProblemDev* d_probs = nullptr;
+  const int4* d_titems = nullptr;
+  const int2* d_pitems = nullptr;
+  const int* d_counters = nullptr;
+  int n_titems = 0, n_pitems = 0;
+  int ws_words = 0, rad_words = 0;
+  wb_batch_sizes sizes{};
+};
+
+extern "C" {
+
+int wb_batch_create(wb_robot* const* robots, int32_t n_robots, const wb_problem* problems,
+                    int32_t n_problems, wb_batch** out) {
+  g_err.clear();
+  if (!out) return fail(WB_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!robots || n_robots <= 0) return fail(WB_EINVAL, "no robots");
+  if (n_problems < 0 || (n_problems > 0 && !problems)) return fail(WB_EINVAL, "bad problems");
+  const int dev = robots[0] ? robots[0]->device : -1;
+  for (int i = 0; i < n_robots; ++i) {
+    if (!robots[i]) return fail(WB_EINVAL, "robot %d is NULL", i);
+    if (robots[i]->device != dev) return fail(WB_EDEVICE, "robots on different devices");
+    if (robots[i]->dev.maxdepth > tree_max_depth())
+      return fail(WB_ETOOBIG, "robot %d deeper than %d levels", i, tree_max_depth());
+  }
+  wb_batch* Bt = new wb_batch();
+  Bt->device = dev;
+  Bt->num_sms = robots[0]->num_sms;
+  Bt->robots.assign(robots, robots + n_robots);
+  int64_t jo = 0, po = 0, so = 0, co = 0;
+  std::vector<int4> titems;
+  std::vector<int2> pitems;
+  for (int p = 0; p < n_problems; ++p) {
+    const int ri = problems[p].robot, H = problems[p].horizon;
+    if (ri < 0 || ri >= n_robots) {
+      delete Bt;
+      return fail(WB_ERANGE, "problem %d: robot %d out of range", p, ri);
+    }
+    if (H < 0) {
+      delete Bt;
+      return fail(WB_EINVAL, "problem %d: horizon %d < 0", p, H);
+    }
+    const DevRobot& D = robots[ri]->dev;
+    Bt->probs.push_back(BatchProblemDev{ri, H, jo, po, so, co});
+    jo += (int64_t)D.d * H;
+    po += (int64_t)H * D.n * 12;
+    so += (int64_t)H * D.S * 3;
+    co += H;
+    for (int c = 0; c < H; c += 32) titems.push_back(make_int4(p, c, std::min(32, H - c), ri));
+    for (int c = 0; c < H; ++c) pitems.push_back(make_int2(p, c));
+    Bt->ws_words = std::max(Bt->ws_words, pair_plan_words(D));
+    Bt->rad_words = std::max(Bt->rad_words, (4 * D.Sg + 31) & ~31);
+  }
+  // longest work first
+  auto tcost = [&](const int4& w) { return robots[w.w]->dev.n; };
+  std::stable_sort(titems.begin(), titems.end(),
+                   [&](const int4& a, const int4& b) { return tcost(a) > tcost(b); });
+  auto pcost = [&](const int2& w) { return robots[Bt->probs[w.x].robot]->dev.P; };
+  std::stable_sort(pitems.begin(), pitems.end(),
+                   [&](const int2& a, const int2& b) { return pcost(a) > pcost(b); });
+  std::vector<DevRobot> drs;
+  std::vector<PairSchedule32> dss;
+  for (int i = 0; i < n_robots; ++i) {
+    drs.push_back(robots[i]->dev);
+    dss.push_back(robots[i]->sched32);
+  }
+  std::vector<int> counters(4, 0);
+  if (titems.empty()) titems.push_back(make_int4(0, 0, 0, 0));
+  if (pitems.empty()) pitems.push_back(make_int2(0, 0));
+  std::vector<BatchProblemDev> probs_dev = Bt->probs;
+  if (probs_dev.empty()) probs_dev.push_back(BatchProblemDev{0, 0, 0, 0, 0, 0});
+  Bt->n_titems = n_problems ? (int)titems.size() : 0;
+  Bt->n_pitems = co > 0 ? (int)pitems.size() : 0;
+  if (co == 0) Bt->n_titems = 0;
+  Packer pk;
+  pk.add_vec(drs, &Bt->d_robots);
+  pk.add_vec(dss, &Bt->d_scheds);
+  pk.add_vec(probs_dev, &Bt->d_probs);
+  pk.add_vec(titems, &Bt->d_titems);
+  pk.add_vec(pitems, &Bt->d_pitems);
+  pk.add_vec(counters, &Bt->d_counters);
+  DeviceGuard guard(dev);
+  cudaError_t e = cudaMalloc(&Bt->dmem, pk.host.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(Bt->dmem, pk.host.data(), pk.host.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (Bt->dmem) cudaFree(Bt->dmem);
+    delete Bt;
+    return cuda_fail(e, "batch upload");
+  }
+  for (auto& it : pk.items) *it.slot = static_cast<char*>(Bt->dmem) + it.off;
+  Bt->sizes = wb_batch_sizes{jo, po, so, co, n_problems, n_robots};
+  *out = Bt;
+  return WB_OK;
+}
+
+int wb_batch_sizes_get(const wb_batch* batch, wb_batch_sizes* out) {
+  if (!batch || !out) return fail(WB_EINVAL, "NULL argument");
+  *out = batch->sizes;
+  return WB_OK;
+}
+
+int wb_batch_offsets(const wb_batch* batch, int64_t* joint, int64_t* pose, int64_t* sphere,
+                     int64_t* config) {
+  if (!batch) return fail(WB_EINVAL, "batch is NULL");
+  for (size_t p = 0; p < batch->probs.size(); ++p) {
+    if (joint) joint[p] = batch->probs[p].jo;
+    if (pose) pose[p] = batch->probs[p].po;
+    if (sphere) sphere[p] = batch->probs[p].so;
+    if (config) config[p] = batch->probs[p].co;
+  }
+  return WB_OK;
+}
+
+void wb_free_batch(wb_batch* batch) {
+  if (!batch) return;
+  {
+    DeviceGuard guard(batch->device);
+    if (batch->dmem) cudaFree(batch->dmem);
+  }
+  delete batch;
+}
+
+static int batch_grid_tree(const wb_batch* Bt, bool fwd, int* grid) {
+  int bps = 0;
+  cudaError_t e = batch_tree_max_blocks_per_sm(fwd, &bps);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+  const int need = (Bt->n_titems + 3) / 4;  // 4 warps per block
+  *grid = std::max(1, std::min(need, std::max(bps, 1) * Bt->num_sms));
+  return WB_OK;
+}
+
+int wb_batch_eval(wb_batch* batch, const float* q, const float* qd, const float* qdd,
+                  float* link_pose, float* sphere, float* d_min, int32_t* worst_pair, float* tau,
+                  void* stream) {
+  g_err.clear();
+  if (!batch) return fail(WB_EINVAL, "batch is NULL");
+  if (batch->sizes.configs == 0) return WB_OK;
+  const wb_robot* R0 = batch->robots[0];
+  int rc;
+  if ((rc = check_ptr(R0, q, "q", true))) return rc;
+  if ((rc = check_ptr(R0, qd, "qd", tau != nullptr))) return rc;
+  if ((rc = check_ptr(R0, qdd, "qdd", tau != nullptr))) return rc;
+  const bool pairs = d_min || sphere;
+  if ((rc = check_ptr(R0, link_pose, "link_pose", pairs))) return rc;
+  if ((rc = check_ptr(R0, sphere, "sphere", false))) return rc;
+  if ((rc = check_ptr(R0, d_min, "d_min", false))) return rc;
+  if ((rc = check_ptr(R0, worst_pair, "worst_pair", d_min != nullptr))) return rc;
+  if ((rc = check_ptr(R0, tau, "tau", false))) return rc;
+  if (!d_min && worst_pair) return fail(WB_EINVAL, "worst_pair without d_min");
+  DeviceGuard guard(batch->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  BatchIO io{q, qd, qdd, link_pose, sphere, d_min, worst_pair, tau,
+             nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int* counters = const_cast<int*>(batch->d_counters);
+  cudaError_t e = cudaSuccess;
+  if (link_pose || tau) {
+    int grid = 1;
+    if ((rc = batch_grid_tree(batch, true, &grid))) return rc;
+    e = launch_batch_tree_fwd(batch->d_robots, batch->d_probs, batch->d_titems, batch->n_titems,
+                              counters, io, grid, s);
+    if (e != cudaSuccess) return cuda_fail(e, "wb_batch_eval launch");
+  }
+  if (pairs && batch->n_pitems > 0) {
+    const int warps = 8;
+    int bps = 0;
+    e = batch_pair_max_blocks_per_sm(warps, batch->ws_words, batch->rad_words, &bps);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    if (bps < 1) return fail(WB_ETOOBIG, "batch pair kernel does not fit on an SM");
+    const int need = (batch->n_pitems + warps - 1) / warps;
+    const int grid = std::min(need, bps * batch->num_sms);
+    e = launch_batch_pair(batch->d_robots, batch->d_scheds, batch->d_probs, batch->d_pitems,
+                          batch->n_pitems, counters + 1, io, grid, warps, batch->ws_words,
+                          batch->rad_words, s);
+    if (e != cudaSuccess) return cuda_fail(e, "wb_batch_eval launch");
+  }
+  return WB_OK;
+}
+
+int wb_batch_eval_backward(wb_batch* batch, const float* q, const float* qd, const float* qdd,
+                           const int32_t* worst_pair, const float* g_pose, const float* g_sphere,
+                           const float* g_dmin, const float* g_tau, float* gq, float* gqd,
+                           float* gqdd, void* stream) {
+  g_err.clear();
+  if (!batch) return fail(WB_EINVAL, "batch is NULL");
+  if (batch->sizes.configs == 0) return WB_OK;
+  const wb_robot* R0 = batch->robots[0];
+  int rc;
+  if ((rc = check_ptr(R0, q, "q", true))) return rc;
+  if ((rc = check_ptr(R0, qd, "qd", true))) return rc;
+  if ((rc = check_ptr(R0, qdd, "qdd", true))) return rc;
+  if ((rc = check_ptr(R0, worst_pair, "worst_pair", g_dmin != nullptr))) return rc;
+  if ((rc = check_ptr(R0, g_pose, "g_pose", false))) return rc;
+  if ((rc = check_ptr(R0, g_sphere, "g_sphere", false))) return rc;
+  if ((rc = check_ptr(R0, g_dmin, "g_dmin", false))) return rc;
+  if ((rc = check_ptr(R0, g_tau, "g_tau", false))) return rc;
+  if ((rc = check_ptr(R0, gq, "gq", true))) return rc;
+  if ((rc = check_ptr(R0, gqd, "gqd", true))) return rc;
+  if ((rc = check_ptr(R0, gqdd, "gqdd", true))) return rc;
+  DeviceGuard guard(batch->device);
+  BatchIO io{q, qd, qdd, nullptr, nullptr, nullptr, const_cast<int32_t*>(worst_pair), nullptr,
+             g_pose, g_sphere, g_dmin, g_tau, gq, gqd, gqdd};
+  int grid = 1;
+  if ((rc = batch_grid_tree(batch, false, &grid))) return rc;
+  cudaError_t e = launch_batch_tree_bwd(batch->d_robots, batch->d_probs, batch->d_titems,
+                                        batch->n_titems, const_cast<int*>(batch->d_counters) + 2,
+                                        io, grid, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "wb_batch_eval_backward launch");
+  return WB_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// autotuner
+// ---------------------------------------------------------------------------
+namespace {
+struct Scratch {
+  std::vector<void*> bufs;
+  ~Scratch() {
+    for (void* p : bufs) cudaFree(p);
+  }
+  template <class T>
+  T* get(size_t n) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) return nullptr;
+    bufs.push_back(p);
+    return static_cast<T*>(p);
+  }
+};
+
+float median3(std::vector<float> v) {
+  std::sort(v.begin(), v.end());
+  return v[v.size() / 2];
+}
+}  // namespace
+
+extern "C" int wb_autotune(wb_robot* robot, int64_t B, wb_tune* fwd, wb_tune* bwd, float* fwd_ms,
+                           float* bwd_ms) {
+  g_err.clear();
+  if (!robot || !fwd || !bwd) return fail(WB_EINVAL, "NULL argument");
+  if (B <= 0) return fail(WB_EINVAL, "B must be positive");
+  DeviceGuard guard(robot->device);
+  const DevRobot& D = robot->dev;
+  Scratch sc;
+  const size_t nj = (size_t)D.d * B;
+  float* q = sc.get<float>(nj);
+  float* qd = sc.get<float>(nj);
+  float* qdd = sc.get<float>(nj);
+  float* pose = sc.get<float>((size_t)B * D.n * 12);
+  float* sph = sc.get<float>((size_t)B * D.S * 3);
+  float* dmin = sc.get<float>(B);
+  int32_t* worst = sc.get<int32_t>(B);
+  float* tau = sc.get<float>(nj);
+  float* gpose = sc.get<float>((size_t)B * D.n * 12);
+  float* gsph = sc.get<float>((size_t)B * D.S * 3);
+  float* gdmin = sc.get<float>(B);
+  float* gtau = sc.get<float>(nj);
+  float* gq = sc.get<float>(nj);
+  float* gqd = sc.get<float>(nj);
+  float* gqdd = sc.get<float>(nj);
+  if (!gqdd || !q || !pose || !sph || !gpose || !gsph) return fail(WB_ECUDA, "autotune scratch");
+  {  // deterministic states: q in [-pi, pi], rates in [-2, 2], grads in [-1, 1]
+    std::vector<float> h(std::max(nj, (size_t)B * std::max(D.n * 12, D.S * 3)));
+    uint64_t st = 0x9E3779B97F4A7C15ull;
+    auto uni = [&]() {
+      st = st * 6364136223846793005ull + 1442695040888963407ull;
+      return (float)((st >> 40) * (1.0 / 16777216.0)) * 2.0f - 1.0f;
+    };
+    auto fill = [&](float* dst, size_t n, float scale) {
+      for (size_t i = 0; i < n; ++i) h[i] = scale * uni();
+      return cudaMemcpy(dst, h.data(), n * sizeof(float), cudaMemcpyHostToDevice);
+    };
+    cudaError_t e = fill(q, nj, 3.14159265f);
+    if (e == cudaSuccess) e = fill(qd, nj, 2.0f);
+    if (e == cudaSuccess) e = fill(qdd, nj, 5.0f);
+    if (e == cudaSuccess) e = fill(gpose, (size_t)B * D.n * 12, 1.0f);
+    if (e == cudaSuccess) e = fill(gsph, (size_t)B * D.S * 3, 1.0f);
+    if (e == cudaSuccess) e = fill(gdmin, B, 1.0f);
+    if (e == cudaSuccess) e = fill(gtau, nj, 1.0f);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune inputs");
+  }
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(WB_ECUDA, "autotune stream/events");
+  std::vector<wb_tune> cands;
+  if (D.maxdepth <= tree_max_depth())
+    for (int tpb : {64, 128, 256})
+      for (int pw : {4, 8}) cands.push_back(wb_tune{WB_KERNEL_TREE, 0, tpb, pw});
+  for (int G : {4, 8, 16, 32}) cands.push_back(wb_tune{WB_KERNEL_FUSED, G, 0, 0});
+  if (plain_fits(D)) cands.push_back(wb_tune{WB_KERNEL_PLAIN, 0, 0, 0});
+  float best_f = 1e30f, best_b = 1e30f;
+  wb_tune bf = cands[0], bb = cands[0];
+  for (const wb_tune& t : cands) {
+    for (int pass = 0; pass < 2; ++pass) {
+      if (pass == 1 && t.kernel == WB_KERNEL_TREE && t.blocks_per_sm != 8) continue;
+      auto run = [&]() {
+        return pass == 0 ? wb_eval(robot, B, q, qd, qdd, pose, sph, dmin, worst, tau, nullptr,
+                                   &t, s)
+                         : wb_eval_backward(robot, B, q, qd, qdd, worst, gpose, gsph, gdmin,
+                                            gtau, gq, gqd, gqdd, &t, s);
+      };
+      if (run() != WB_OK) continue;  // shape not applicable to this robot
+      std::vector<float> ts;
+      for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(e0, s);
+        run();
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ts.push_back(ms);
+      }
+      const float m = median3(ts);
+      if (pass == 0 && m < best_f) {
+        best_f = m;
+        bf = t;
+      }
+      if (pass == 1 && m < best_b) {
+        best_b = m;
+        bb = t;
+      }
+    }
+  }
+  cudaStreamSynchronize(s);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  g_err.clear();
+  *fwd = bf;
+  *bwd = bb;
+  if (fwd_ms) *fwd_ms = best_f;
+  if (bwd_ms) *bwd_ms = best_b;
+  return WB_OK;
+}

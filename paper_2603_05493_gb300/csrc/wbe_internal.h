@@ -114,6 +114,46 @@ struct BwdArgs {
   float* gqdd;
 };
 
+// One problem of an uneven batch: robot index and horizon, and the offsets
+// (in elements) of its slices of the packed arrays.
+struct BatchProblemDev {
+  int robot;
+  int H;
+  int64_t jo, po, so, co;  // joint-major, pose, sphere, per-configuration
+};
+
+struct BatchIO {
+  const float* q;
+  const float* qd;
+  const float* qdd;
+  float* pose;
+  float* sph;
+  float* dmin;
+  int32_t* worst;
+  float* tau;
+  const float* g_pose;
+  const float* g_sph;
+  const float* g_dmin;
+  const float* g_tau;
+  float* gq;
+  float* gqd;
+  float* gqdd;
+};
+
+cudaError_t launch_batch_tree_fwd(const DevRobot* robots, const BatchProblemDev* probs,
+                                  const int4* items, int n_items, int* counter, const BatchIO& io,
+                                  int grid, cudaStream_t s);
+cudaError_t launch_batch_tree_bwd(const DevRobot* robots, const BatchProblemDev* probs,
+                                  const int4* items, int n_items, int* counter, const BatchIO& io,
+                                  int grid, cudaStream_t s);
+cudaError_t launch_batch_pair(const DevRobot* robots, const PairSchedule32* scheds,
+                              const BatchProblemDev* probs, const int2* items, int n_items,
+                              int* counter, const BatchIO& io, int grid, int warps, int ws_words,
+                              int rad_words, cudaStream_t s);
+cudaError_t batch_pair_max_blocks_per_sm(int warps, int ws_words, int rad_words, int* out);
+cudaError_t batch_tree_max_blocks_per_sm(bool fwd, int* out);
+int pair_plan_words(const DevRobot& r);
+
 // launchers (return cudaGetLastError())
 cudaError_t launch_tree_fwd(const DevRobot& r, const FwdArgs& a, int threads, cudaStream_t s);
 cudaError_t launch_tree_bwd(const DevRobot& r, const BwdArgs& a, int threads, cudaStream_t s);

@@ -151,6 +151,16 @@ class Robot:
         L.check(self.lib.wb_set_inertials(self.handle, C.byref(inert), _stream(stream)),
                 "wb_set_inertials")
 
+    def autotune(self, B):
+        """Time the kernel families / launch shapes on this robot for batch B;
+        returns (forward Tune, backward Tune, forward ms, backward ms)."""
+        f, b = L.wb_tune(), L.wb_tune()
+        fm, bm = C.c_float(), C.c_float()
+        L.check(self.lib.wb_autotune(self.handle, int(B), C.byref(f), C.byref(b), C.byref(fm),
+                                     C.byref(bm)), "wb_autotune")
+        mk = lambda t: Tune(t.kernel, t.lanes_per_config, t.configs_per_block, t.blocks_per_sm)
+        return mk(f), mk(b), fm.value, bm.value
+
     # ------------------------------------------------------------------
     def empty_outputs(self, B, pose=True, sphere=True, dmin=True, tau=True, bits=False):
         dev = self.device
@@ -206,6 +216,107 @@ class Robot:
                                           _ptr(gqdd), C.byref(t), _stream(stream)),
                 "wb_eval_backward")
         return gq, gqd, gqdd
+
+
+class Batch:
+    """An uneven batch: problems (robot index, horizon) over several loaded
+    robots, evaluated by one persistent launch per pass.  Packed arrays are
+    flat float32 / int32 tensors of the lengths in `sizes`; problem p's slices
+    start at the offsets in `offsets` (see include/wbe.h)."""
+
+    def __init__(self, robots, problems):
+        self.lib = L.load()
+        self.robots = list(robots)
+        self.device = self.robots[0].device
+        arr = (C.c_void_p * len(self.robots))(*[r.handle.value for r in self.robots])
+        probs = (L.wb_problem * len(problems))(*[L.wb_problem(int(a), int(h))
+                                                 for a, h in problems])
+        h = C.c_void_p()
+        L.check(self.lib.wb_batch_create(arr, len(self.robots), probs, len(problems),
+                                         C.byref(h)), "wb_batch_create")
+        self.handle = h
+        sz = L.wb_batch_sizes()
+        L.check(self.lib.wb_batch_sizes_get(self.handle, C.byref(sz)), "wb_batch_sizes_get")
+        self.sizes = {f: getattr(sz, f) for f, _ in L.wb_batch_sizes._fields_}
+        n = len(problems)
+        offs = [np.zeros(n, np.int64) for _ in range(4)]
+        L.check(self.lib.wb_batch_offsets(self.handle, *[o.ctypes.data for o in offs]),
+                "wb_batch_offsets")
+        self.offsets = {"joint": offs[0], "pose": offs[1], "sphere": offs[2], "config": offs[3]}
+        self.problems = [(int(a), int(h)) for a, h in problems]
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            self.lib.wb_free_batch(h)
+            self.handle = None
+
+    def empty(self, kind, dtype=torch.float32):
+        n = {"joint": "joint_elems", "pose": "pose_elems", "sphere": "sphere_elems",
+             "config": "configs"}[kind]
+        return torch.empty(max(self.sizes[n], 1), device=self.device, dtype=dtype)
+
+    def pack_joint(self, per_problem):
+        """Concatenate per-problem [d][H] arrays into the packed joint layout."""
+        out = self.empty("joint")
+        for p, x in enumerate(per_problem):
+            o = int(self.offsets["joint"][p])
+            out[o:o + x.numel()] = torch.as_tensor(x, device=self.device).reshape(-1)
+        return out
+
+    def view(self, packed, kind, p, shape):
+        o = int(self.offsets[kind][p])
+        n = int(np.prod(shape))
+        return packed[o:o + n].view(*shape)
+
+    def eval(self, q, qd, qdd, pose, sphere=None, dmin=None, worst=None, tau=None, stream=None):
+        L.check(self.lib.wb_batch_eval(self.handle, _ptr(q), _ptr(qd), _ptr(qdd), _ptr(pose),
+                                       _ptr(sphere), _ptr(dmin), _ptr(worst), _ptr(tau),
+                                       _stream(stream)), "wb_batch_eval")
+
+    def eval_backward(self, q, qd, qdd, worst, g_pose, g_sphere, g_dmin, g_tau, gq, gqd, gqdd,
+                      stream=None):
+        L.check(self.lib.wb_batch_eval_backward(self.handle, _ptr(q), _ptr(qd), _ptr(qdd),
+                                                _ptr(worst), _ptr(g_pose), _ptr(g_sphere),
+                                                _ptr(g_dmin), _ptr(g_tau), _ptr(gq), _ptr(gqd),
+                                                _ptr(gqdd), _stream(stream)),
+                "wb_batch_eval_backward")
+
+
+def descriptor_hash(desc) -> str:
+    """Content hash of a robot description (the autotune cache key)."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("parent", "jtype", "axis", "T_fixed", "jidx", "mimic_mult", "mimic_off",
+                 "gravity", "sph_link", "sph_c", "sph_r", "pairs", "mass", "com", "Icom"):
+        h.update(np.ascontiguousarray(getattr(desc, name)).tobytes())
+    return h.hexdigest()[:32]
+
+
+def autotune_cached(robot: Robot, desc, B: int, path: str | None = None):
+    """Autotune once per (robot description, GPU, batch size); results persist
+    in a JSON file (default ~/.cache/wbe/autotune.json)."""
+    import json
+    import os
+    path = path or os.path.join(os.path.expanduser("~"), ".cache", "wbe", "autotune.json")
+    key = "%s|%s|%d" % (descriptor_hash(desc), torch.cuda.get_device_name(robot.device), B)
+    cache = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            cache = json.load(f)
+    if key in cache:
+        e = cache[key]
+        return Tune(*e["fwd"]), Tune(*e["bwd"]), e["fwd_ms"], e["bwd_ms"]
+    f, b, fm, bm = robot.autotune(B)
+    cache[key] = {"fwd": [f.kernel, f.lanes_per_config, f.configs_per_block, f.blocks_per_sm],
+                  "bwd": [b.kernel, b.lanes_per_config, b.configs_per_block, b.blocks_per_sm],
+                  "fwd_ms": fm, "bwd_ms": bm}
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + ".tmp%d" % os.getpid()
+    with open(tmp, "w") as fh:
+        json.dump(cache, fh, indent=1)
+    os.replace(tmp, path)
+    return f, b, fm, bm
 
 
 def _c(t):

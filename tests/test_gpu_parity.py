@@ -284,3 +284,25 @@ def test_self_collision_from_poses(W, O, rname):
     torch.cuda.synchronize()
     sc["pose"] = o["pose"].cpu().numpy()
     PY.check_forward(desc, sc, O.evaluate(desc, q, want=("pose", "sph", "dmin")))
+
+
+@pytest.mark.parametrize("rname", ["R7", "R48"])
+def test_autotune_choice_is_valid_and_exact(W, O, rname, tmp_path):
+    desc, rob = robot(W, rname)
+    f, b, fm, bm = W.autotune_cached(rob, desc, 2048, path=str(tmp_path / "tune.json"))
+    assert fm > 0 and bm > 0
+    # cached on the second call
+    f2, b2, _, _ = W.autotune_cached(rob, desc, 2048, path=str(tmp_path / "tune.json"))
+    assert (f2, b2) == (f, b)
+    B = 97
+    q, qd, qdd = I.uniform_states(desc.dof, B, seed=61)
+    gp, gs, gm, gt = I.upstream_grads(desc, B, seed=62)
+    got = run_fwd(rob, q, qd, qdd, f)
+    PY.check_forward(desc, got, O.evaluate(desc, q, qd, qdd))
+    o = rob.eval(cuda(q), cuda(qd), cuda(qdd), tune=f)
+    g = rob.eval_backward(cuda(q), cuda(qd), cuda(qdd), o["worst"], cuda(gp), cuda(gs), cuda(gm),
+                          cuda(gt), tune=b)
+    torch.cuda.synchronize()
+    gref = O.gradient(desc, q, qd, qdd, gp, gs, gm, gt)
+    same = o["worst"].cpu().numpy() == O.evaluate(desc, q, want=("dmin",))["worst"]
+    PY.check_gradient([x.cpu().numpy() for x in g], gref, mask=same)
