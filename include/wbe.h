@@ -267,6 +267,62 @@ int wb_batch_eval_backward(wb_batch* batch, const float* q, const float* qd, con
                            float* gqdd, void* stream);
 void wb_free_batch(wb_batch* batch);
 
+/* ---------------------------------------------------------------------------
+ * Forward evaluation of an uneven batch without any device allocation.  The
+ * paper has no counterpart to this entry point.
+ *
+ * Who needs it: a caller whose mix of problems (which robots, which horizons)
+ * changes from call to call, e.g. a planner or controller that checks a fresh
+ * set of candidate trajectories every cycle.  With wb_batch_create it would
+ * create and free a batch object per call, and that allocates and releases
+ * device memory (cudaMalloc / cudaFree), which can synchronise the whole
+ * device and take unbounded time: a fixed-period control loop cannot afford
+ * that, and a process whose device memory is held by another allocator (a
+ * framework's caching allocator) may not be able to allocate at all.  This
+ * call allocates nothing, on the device or through any library.
+ *
+ * Arguments and packed layouts are those of wb_batch_create + wb_batch_eval:
+ * problem p's slices start at the prefix sums, in problem order, of d_p*H_p
+ * (joint-major arrays), H_p*n_p*12 (poses), H_p*S_p*3 (spheres) and H_p (per
+ * configuration); wb_batch_offsets of a batch built from the same problems
+ * gives the same offsets.  Outputs are identical to wb_batch_eval's.
+ *
+ * Scratch: the work tables and counters live in one device array inside the
+ * library, about 0.6 MiB per device, reserved when the library's device code
+ * is loaded on that device.  Limits: at most WB_NOALLOC_MAX_ROBOTS robots,
+ * WB_NOALLOC_MAX_PROBLEMS problems and WB_NOALLOC_MAX_CONFIGS configurations
+ * (sum of horizons) per call; larger calls fail with WB_ETOOBIG and change
+ * nothing.  Each call rebuilds the tables on `stream` (one setup kernel) before
+ * the passes read them.  What must start at zero: the work counter of each
+ * pass; the call clears it itself on `stream` (cudaMemsetAsync) before the
+ * pass.
+ *
+ * Setup: the first call on a device looks up the scratch array's device
+ * address (cudaGetSymbolAddress, with that device current), which may load
+ * the library's device code there; make that first call on each device before
+ * any stream capture begins, e.g. as a warm-up.
+ *
+ * The statement on graph capture in the conventions at the top of this file
+ * does not cover this call.
+ *
+ * The scratch is shared by all calls on a device: calls whose GPU work may
+ * overlap (different streams without ordering between them, or several host
+ * threads) race on it and give wrong results.  Order them on one stream or
+ * with events.  Robots must stay alive until the call's work has finished.
+ *
+ * Errors: WB_EINVAL (null robots or q, horizon < 0, misaligned pointer,
+ * d_min without worst_pair, tau without qd/qdd, sphere or d_min without
+ * link_pose), WB_ERANGE (robot index out of range), WB_EDEVICE (robots or
+ * buffers on different devices), WB_ETOOBIG (a limit above exceeded, robot
+ * deeper than the sweep kernels' limit), WB_ECUDA (lookup or launch failure). */
+#define WB_NOALLOC_MAX_ROBOTS 8
+#define WB_NOALLOC_MAX_PROBLEMS 1024
+#define WB_NOALLOC_MAX_CONFIGS 65536
+int wb_batch_eval_noalloc(wb_robot* const* robots, int32_t n_robots, const wb_problem* problems,
+                          int32_t n_problems, const float* q, const float* qd, const float* qdd,
+                          float* link_pose, float* sphere, float* d_min, int32_t* worst_pair,
+                          float* tau, void* stream);
+
 /* Message describing the calling thread's most recent error ("" if none). */
 const char* wb_last_error(void);
 

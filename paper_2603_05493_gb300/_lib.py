@@ -93,6 +93,7 @@ SIGNATURES = {
     "wb_batch_eval": (C.c_int, [p, p, p, p, p, p, p, p, p, p]),
     "wb_batch_eval_backward": (C.c_int, [p, p, p, p, p, p, p, p, p, p, p, p, p]),
     "wb_free_batch": (None, [p]),
+    "wb_batch_eval_noalloc": (C.c_int, [p, C.c_int32, p, C.c_int32, p, p, p, p, p, p, p, p, p]),
 }
 
 _lib = None

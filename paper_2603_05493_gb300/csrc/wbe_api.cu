@@ -1111,6 +1111,127 @@ int wb_batch_eval_backward(wb_batch* batch, const float* q, const float* qd, con
   return WB_OK;
 }
 
+// The work tables of wb_batch_create, rebuilt per call in the library's static
+// scratch (k_noalloc.cu) instead of device memory allocated per batch.  The
+// host fills the setup kernel's launch parameters (NoAllocPlan, on this
+// stack) and chooses the same longest-first order of work items.
+int wb_batch_eval_noalloc(wb_robot* const* robots, int32_t n_robots, const wb_problem* problems,
+                          int32_t n_problems, const float* q, const float* qd, const float* qdd,
+                          float* link_pose, float* sphere, float* d_min, int32_t* worst_pair,
+                          float* tau, void* stream) {
+  g_err.clear();
+  if (!robots || n_robots <= 0) return fail(WB_EINVAL, "no robots");
+  if (n_problems < 0 || (n_problems > 0 && !problems)) return fail(WB_EINVAL, "bad problems");
+  if (n_robots > WB_NOALLOC_MAX_ROBOTS)
+    return fail(WB_ETOOBIG, "%d robots: at most %d per call", n_robots, WB_NOALLOC_MAX_ROBOTS);
+  if (n_problems > WB_NOALLOC_MAX_PROBLEMS)
+    return fail(WB_ETOOBIG, "%d problems: at most %d per call", n_problems,
+                WB_NOALLOC_MAX_PROBLEMS);
+  static_assert(WB_NOALLOC_MAX_ROBOTS == NA_MAX_ROBOTS &&
+                    WB_NOALLOC_MAX_PROBLEMS == NA_MAX_PROBLEMS &&
+                    WB_NOALLOC_MAX_CONFIGS == NA_MAX_CONFIGS,
+                "public and internal limits differ");
+  const int dev = robots[0] ? robots[0]->device : -1;
+  for (int i = 0; i < n_robots; ++i) {
+    if (!robots[i]) return fail(WB_EINVAL, "robot %d is NULL", i);
+    if (robots[i]->device != dev) return fail(WB_EDEVICE, "robots on different devices");
+    if (robots[i]->dev.maxdepth > tree_max_depth())
+      return fail(WB_ETOOBIG, "robot %d deeper than %d levels", i, tree_max_depth());
+  }
+  int64_t configs = 0;
+  for (int p = 0; p < n_problems; ++p) {
+    const int ri = problems[p].robot, H = problems[p].horizon;
+    if (ri < 0 || ri >= n_robots) return fail(WB_ERANGE, "problem %d: robot %d out of range", p, ri);
+    if (H < 0) return fail(WB_EINVAL, "problem %d: horizon %d < 0", p, H);
+    configs += H;
+    if (configs > WB_NOALLOC_MAX_CONFIGS)
+      return fail(WB_ETOOBIG, "more than %d configurations per call", WB_NOALLOC_MAX_CONFIGS);
+  }
+  const wb_robot* R0 = robots[0];
+  int rc;
+  if ((rc = check_ptr(R0, q, "q", configs > 0))) return rc;
+  if ((rc = check_ptr(R0, qd, "qd", configs > 0 && tau != nullptr))) return rc;
+  if ((rc = check_ptr(R0, qdd, "qdd", configs > 0 && tau != nullptr))) return rc;
+  const bool pairs = d_min || sphere;
+  if ((rc = check_ptr(R0, link_pose, "link_pose", configs > 0 && pairs))) return rc;
+  if ((rc = check_ptr(R0, sphere, "sphere", false))) return rc;
+  if ((rc = check_ptr(R0, d_min, "d_min", false))) return rc;
+  if ((rc = check_ptr(R0, worst_pair, "worst_pair", configs > 0 && d_min != nullptr))) return rc;
+  if ((rc = check_ptr(R0, tau, "tau", false))) return rc;
+  if (!d_min && worst_pair) return fail(WB_EINVAL, "worst_pair without d_min");
+  if (configs == 0) return WB_OK;
+
+  NoAllocPlan plan;
+  plan.n_robots = n_robots;
+  plan.n_problems = n_problems;
+  plan.n_configs = (int)configs;
+  int ws_words = 0, rad_words = 0;
+  for (int i = 0; i < n_robots; ++i) {
+    plan.robots[i] = robots[i]->dev;
+    plan.scheds[i] = robots[i]->sched32;
+  }
+  for (int p = 0; p < n_problems; ++p) {
+    const DevRobot& D = robots[problems[p].robot]->dev;
+    plan.prob[p] = problems[p].robot << 24 | problems[p].horizon;
+    ws_words = std::max(ws_words, pair_plan_words(D));
+    rad_words = std::max(rad_words, (4 * D.Sg + 31) & ~31);
+  }
+  // longest work first: robots by cost (stable), problems in order within one
+  int n_titems = 0, n_pitems = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    int order[NA_MAX_ROBOTS];
+    for (int i = 0; i < n_robots; ++i) order[i] = i;
+    auto cost = [&](int i) { return pass == 0 ? robots[i]->dev.n : robots[i]->dev.P; };
+    std::stable_sort(order, order + n_robots, [&](int a, int b) { return cost(a) > cost(b); });
+    int next = 0;
+    for (int k = 0; k < n_robots; ++k)
+      for (int p = 0; p < n_problems; ++p) {
+        if (problems[p].robot != order[k]) continue;
+        const int H = problems[p].horizon;
+        if (pass == 0) {
+          plan.tstart[p] = next;
+          next += (H + 31) / 32;
+        } else {
+          plan.pstart[p] = next;
+          next += H;
+        }
+      }
+    (pass == 0 ? n_titems : n_pitems) = next;
+  }
+
+  DeviceGuard guard(dev);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned char* base = nullptr;
+  cudaError_t e = noalloc_scratch(dev, &base);
+  if (e != cudaSuccess) return cuda_fail(e, "scratch address lookup");
+  const NoAllocTables T = noalloc_tables(base);
+  const int setup_grid = std::max(1, std::min((n_pitems + 1023) / 1024, R0->num_sms));
+  e = launch_noalloc_setup(plan, base, setup_grid, s);
+  if (e != cudaSuccess) return cuda_fail(e, "wb_batch_eval_noalloc setup launch");
+  BatchIO io{q, qd, qdd, link_pose, sphere, d_min, worst_pair, tau,
+             nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  if (link_pose || tau) {
+    int bps = 0;
+    e = batch_tree_max_blocks_per_sm(true, &bps);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    const int grid = std::max(1, std::min((n_titems + 3) / 4, std::max(bps, 1) * R0->num_sms));
+    e = launch_batch_tree_fwd(T.robots, T.probs, T.titems, n_titems, T.counters, io, grid, s);
+    if (e != cudaSuccess) return cuda_fail(e, "wb_batch_eval_noalloc launch");
+  }
+  if (pairs) {
+    const int warps = 8;
+    int bps = 0;
+    e = batch_pair_max_blocks_per_sm(warps, ws_words, rad_words, &bps);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    if (bps < 1) return fail(WB_ETOOBIG, "batch pair kernel does not fit on an SM");
+    const int grid = std::min((n_pitems + warps - 1) / warps, bps * R0->num_sms);
+    e = launch_batch_pair(T.robots, T.scheds, T.probs, T.pitems, n_pitems, T.counters + 1, io, grid,
+                          warps, ws_words, rad_words, s);
+    if (e != cudaSuccess) return cuda_fail(e, "wb_batch_eval_noalloc launch");
+  }
+  return WB_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

@@ -151,6 +151,34 @@ cudaError_t launch_batch_pair(const DevRobot* robots, const PairSchedule32* sche
                               int* counter, const BatchIO& io, int grid, int warps, int ws_words,
                               int rad_words, cudaStream_t s);
 cudaError_t batch_pair_max_blocks_per_sm(int warps, int ws_words, int rad_words, int* out);
+
+// Forward batch evaluation on tables in a file-scope device array
+// (k_noalloc.cu).  The limits equal the public WB_NOALLOC_MAX_* values.
+constexpr int NA_MAX_ROBOTS = 8;
+constexpr int NA_MAX_PROBLEMS = 1024;
+constexpr int NA_MAX_CONFIGS = 65536;
+constexpr int NA_MAX_DEVICES = 64;
+struct NoAllocPlan {  // launch parameters of the setup kernel
+  int n_robots, n_problems, n_configs;
+  DevRobot robots[NA_MAX_ROBOTS];
+  PairSchedule32 scheds[NA_MAX_ROBOTS];
+  int prob[NA_MAX_PROBLEMS];    // robot << 24 | horizon
+  int tstart[NA_MAX_PROBLEMS];  // first sweep item of the problem, in cost order
+  int pstart[NA_MAX_PROBLEMS];  // first pair item of the problem, in cost order
+};
+struct NoAllocTables {
+  DevRobot* robots;
+  PairSchedule32* scheds;
+  BatchProblemDev* probs;
+  int4* titems;
+  int2* pitems;
+  int* counters;
+};
+size_t noalloc_scratch_bytes();
+__host__ __device__ NoAllocTables noalloc_tables(unsigned char* base);
+cudaError_t noalloc_scratch(int device, unsigned char** out);
+cudaError_t launch_noalloc_setup(const NoAllocPlan& plan, unsigned char* base, int grid,
+                                 cudaStream_t s);
 cudaError_t batch_tree_max_blocks_per_sm(bool fwd, int* out);
 int pair_plan_words(const DevRobot& r);
 

@@ -283,6 +283,26 @@ class Batch:
                 "wb_batch_eval_backward")
 
 
+def batch_eval_noalloc(robots, problems, q, qd, qdd, pose, sphere=None, dmin=None, worst=None,
+                       tau=None, stream=None):
+    """wb_batch_eval_noalloc: forward evaluation of an uneven batch without any
+    device allocation, for callers whose problem mix changes every call and
+    who cannot afford (or are not allowed) to allocate device memory per call.
+    Buffers are packed as for `Batch` built from the same problems; all of
+    them are the caller's.  Calls on one device must not overlap on the GPU
+    (they share the library's scratch), and the first call on a device does a
+    one-time setup (include/wbe.h)."""
+    lib = L.load()
+    robots = list(robots)
+    arr = (C.c_void_p * len(robots))(*[r.handle.value for r in robots])
+    probs = (L.wb_problem * max(len(problems), 1))(*[L.wb_problem(int(a), int(h))
+                                                     for a, h in problems])
+    L.check(lib.wb_batch_eval_noalloc(arr, len(robots), probs, len(problems), _ptr(q), _ptr(qd),
+                                      _ptr(qdd), _ptr(pose), _ptr(sphere), _ptr(dmin),
+                                      _ptr(worst), _ptr(tau), _stream(stream)),
+            "wb_batch_eval_noalloc")
+
+
 def descriptor_hash(desc) -> str:
     """Content hash of a robot description (the autotune cache key)."""
     import hashlib
