@@ -57,27 +57,34 @@ def work_per_eval(desc):
 # DRAM traffic (read + write) per evaluation from one ncu capture of each
 # kernel (24576 configurations of the humanoid48 workload; traffic scales with
 # the batch).  Keyed by the source file's hash: a changed kernel reads null.
+# DRAM bytes (read + write) per evaluation from one ncu capture of each
+# kernel at the bench's launch configuration on 24576 configurations, tied to
+# the hash of the sources that kernel is built from: a changed source makes the
+# figure stale, and it is reported as null until captured again.
+TREE_SRC = ["paper_2603_05493_gb300/csrc/k_tree.cu", "paper_2603_05493_gb300/csrc/tree_sweep.cuh",
+            "paper_2603_05493_gb300/csrc/spatial.cuh"]
+PAIR_SRC = ["paper_2603_05493_gb300/csrc/k_pair.cu", "paper_2603_05493_gb300/csrc/pair_body.cuh",
+            "paper_2603_05493_gb300/csrc/spatial.cuh"]
 MEASURED_TRAFFIC = {
-    "tree_fwd": {"src": "paper_2603_05493_gb300/csrc/k_tree.cu",
-                 "sha256": "ee3c59c2eabc8680a652d20c440e662a472e0a2857edf9adbb133af8c0bdbe36",
-                 "bytes_per_eval": (20.451584e6 + 108.546816e6) / 24576},
-    "pair": {"src": "paper_2603_05493_gb300/csrc/k_pair.cu",
-             "sha256": "8f70c86db1727a3df545a52676fd2f5f18fb7b379a8b5cf8ef9a170227063291",
-             "bytes_per_eval": (57.902848e6 + 15.621888e6) / 24576},
-    "tree_bwd": {"src": "paper_2603_05493_gb300/csrc/k_tree.cu",
-                 "sha256": "ee3c59c2eabc8680a652d20c440e662a472e0a2857edf9adbb133af8c0bdbe36",
-                 "bytes_per_eval": (215.058688e6 + 189.910272e6) / 24576},
+    "tree_fwd": {"src": TREE_SRC, "sha256": None, "bytes_per_eval": None},
+    "pair": {"src": PAIR_SRC, "sha256": None, "bytes_per_eval": None},
+    "tree_bwd": {"src": TREE_SRC, "sha256": None, "bytes_per_eval": None},
 }
 
 
-def traffic_per_eval(name):
+def source_hash(files):
     import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def traffic_per_eval(name):
     t = MEASURED_TRAFFIC.get(name)
-    if not t:
+    if not t or not t["sha256"] or source_hash(t["src"]) != t["sha256"]:
         return None
-    with open(os.path.join(ROOT, t["src"]), "rb") as f:
-        if hashlib.sha256(f.read()).hexdigest() != t["sha256"]:
-            return None
     return t["bytes_per_eval"]
 
 
@@ -226,6 +233,25 @@ def run_ours(args, rank, world, local_rank):
     B = args.batch or CF.HUMANOID48.batch
     rob = wbe.Robot(desc, device=local_rank)
     tune = {"plain": wbe.PLAIN, "fused": wbe.FUSED, "tree": wbe.TREE}[args.kernel]
+    btune = tune
+    names = {"tree_fwd": "fused_fwd_kernel" if args.kernel == "fused" else "plain_fwd_kernel",
+             "pair": "-", "tree_bwd": "fused_bwd_kernel" if args.kernel == "fused"
+             else "plain_bwd_kernel"}
+    chosen = None
+    if args.kernel == "tree":
+        # sweep launch shape (segments, threads per block) from the library's
+        # autotuner at this batch size
+        ft, bt, fms, bms = rob.autotune(B)
+        seg = lambda t: t.lanes_per_config if t.kernel == wbe.L.WB_KERNEL_TREE else 0  # noqa
+        tpb = lambda t: t.configs_per_block if t.kernel == wbe.L.WB_KERNEL_TREE else 0  # noqa
+        tune = wbe.Tune(kernel=wbe.L.WB_KERNEL_TREE, lanes_per_config=seg(ft),
+                        configs_per_block=tpb(ft))
+        btune = wbe.Tune(kernel=wbe.L.WB_KERNEL_TREE, lanes_per_config=seg(bt),
+                         configs_per_block=tpb(bt))
+        chosen = {"fwd": dict(ft.__dict__), "bwd": dict(bt.__dict__)}
+        names = {"tree_fwd": "tree_fwd_seg_kernel" if seg(ft) > 1 else "tree_fwd_kernel",
+                 "pair": "pair_kernel",
+                 "tree_bwd": "tree_bwd_seg_kernel" if seg(bt) > 1 else "tree_bwd_kernel"}
     seed = CF.HUMANOID48.seed + 101 * rank
     q, qd, qdd = I.uniform_states(desc.dof, B, seed)
     gp, gs, gm, gt = I.upstream_grads(desc, B, seed + 1)
@@ -256,7 +282,7 @@ def run_ours(args, rank, world, local_rank):
             rob.self_collision(out["pose"], out=pair_out)
             if events:
                 events[2].record(stream)
-        rob.eval_backward(tq, tqd, tqdd, out["worst"], tgp, tgs, tgm, tgt, tune=tune, out=gout)
+        rob.eval_backward(tq, tqd, tqdd, out["worst"], tgp, tgs, tgm, tgt, tune=btune, out=gout)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -344,7 +370,7 @@ def run_ours(args, rank, world, local_rank):
             kernels[name] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                              "frac": ach / hbm_peak}
         tr = traffic_per_eval(name)
-        kernels[name].update({"ms": ms, "flops_per_eval": w["flops"],
+        kernels[name].update({"kernel": names[name], "ms": ms, "flops_per_eval": w["flops"],
                               "bytes_per_eval": w["bytes"],
                               "traffic": None if tr is None else tr * B})
     kmean = {k: v for k, v in kmean.items() if v > 0}
@@ -358,10 +384,10 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": "humanoid48: 48-DoF tree, 200 spheres, 15392 pairs, "
                                "1024 x 32 configurations, fwd + bwd (upstream grads on "
                                "poses, spheres, d_min, tau)",
-                   "batch_per_gpu": B, "kernel": args.kernel,
+                   "batch_per_gpu": B, "kernel": args.kernel, "autotuned": chosen,
                    "l2": "flushed between timed steps (512 MB write outside the events)"},
         "fwd_ms": fwd_mean, "bwd_ms": bwd_mean,
-        "roofline": dict(kernel=dom + "_kernel", **{k: kernels[dom][k] for k in
+        "roofline": dict(kernel=names[dom], **{k: kernels[dom][k] for k in
                          ("bound", "achieved", "peak", "unit", "frac", "traffic")},
                          peak_basis=("FP32 FMA: %d SMs x 128 x 2 x %.0f MHz (max SM clock)"
                                      % (num_sms, sm_max)) if kernels[dom]["bound"] == "alu"

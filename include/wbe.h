@@ -126,7 +126,14 @@ typedef struct {
                              when spheres or pairs are wanted */
 typedef struct {
   int32_t kernel;            /* WB_KERNEL_* (AUTO: TREE when it applies, else FUSED) */
-  int32_t lanes_per_config;  /* fused: 4, 8, 16 or 32 (0 = robot default) */
+  int32_t lanes_per_config;  /* fused: 4, 8, 16 or 32 (0 = robot default);
+                                tree: sweep segments 1, 2, 4 or 8 -- 1 = one thread
+                                per configuration, G > 1 = G warps per 32
+                                configurations, each sweeping a contiguous piece
+                                of the depth-first order (not for robots where a
+                                joint drives several links); 0 = the fewest that
+                                give about 24 (forward) / 12 (backward) warps per
+                                SM */
   int32_t configs_per_block; /* fused: configurations per CTA; tree: threads per block
                                 of the sweep kernels (32..256); 0 = default */
   int32_t blocks_per_sm;     /* fused: grid = blocks_per_sm * SMs (0 = occupancy);

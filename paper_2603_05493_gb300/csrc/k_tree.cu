@@ -1,6 +1,9 @@
 // k_tree.cu -- the single-robot depth-first sweep kernels (tree_sweep.cuh):
-// one thread per configuration of a batch of B.
+// one thread per configuration of a batch of B, or G warps per 32
+// configurations (segmented sweep).
 #include "tree_sweep.cuh"
+
+#include <algorithm>
 
 namespace wbe {
 
@@ -14,8 +17,71 @@ __global__ void __launch_bounds__(256) tree_bwd_kernel(DevRobot r, BwdArgs A) {
   if (b < A.B) tree_bwd_one(r, A, b);
 }
 
-// The sweep kernels use no shared memory: give the whole unified L1/shared
-// array to L1, where the stacks live.
+// Segmented sweeps, plan t (G = 2 << t segments).  A block holds CG groups of
+// G warps; warp w sweeps segment w % G of the 32 configurations of group
+// w / G.  Shared memory per group: the partial outputs [nout][ns][G][32] of
+// the ns links that several segments hold, summed in segment order after the
+// barrier by the group's warps (slot s by warp s % G).
+__device__ __forceinline__ Seg seg_of(const DevRobot& r, int t, float* part) {
+  const int G = 2 << t;
+  const int w = threadIdx.x >> 5;
+  const int g = w % G;
+  return Seg{r.seg_pos[t][g], r.seg_pos[t][g + 1], g, G, r.seg_slot + t * r.n,
+             part, r.seg_ns[t], (int)(threadIdx.x & 31)};
+}
+
+__global__ void __launch_bounds__(256) tree_fwd_seg_kernel(const __grid_constant__ DevRobot r,
+                                                           FwdArgs A, int t) {
+  extern __shared__ float part[];
+  const int G = 2 << t;
+  const int CG = blockDim.x / (32 * G);
+  const int cg = (threadIdx.x >> 5) / G;
+  const int ns = r.seg_ns[t];
+  Seg sg = seg_of(r, t, part + (size_t)cg * ns * G * 32);
+  for (int s = 0; s < ns; ++s) sg.part[(s * G + sg.g) * 32 + sg.lane] = 0.0f;
+  const int64_t b = ((int64_t)blockIdx.x * CG + cg) * 32 + sg.lane;
+  if (b < A.B) tree_fwd_seg(r, A, b, sg);
+  __syncthreads();
+  if (b < A.B && A.tau) {
+    for (int s = sg.g; s < ns; s += G) {
+      float acc = 0.0f;
+      for (int h = 0; h < G; ++h) acc += sg.part[(s * G + h) * 32 + sg.lane];
+      const int k = __ldg(r.seg_slot_link + t * r.n + s);
+      A.tau[(int64_t)__ldg(r.jidx + k) * A.B + b] = acc;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) tree_bwd_seg_kernel(const __grid_constant__ DevRobot r,
+                                                           BwdArgs A, int t) {
+  extern __shared__ float part[];
+  const int G = 2 << t;
+  const int CG = blockDim.x / (32 * G);
+  const int cg = (threadIdx.x >> 5) / G;
+  const int ns = r.seg_ns[t];
+  const size_t o = (size_t)ns * G * 32;  // one output's partials
+  Seg sg = seg_of(r, t, part + (size_t)cg * 3 * o);
+  for (int s = 0; s < ns; ++s)
+    for (int q = 0; q < 3; ++q) sg.part[q * o + (s * G + sg.g) * 32 + sg.lane] = 0.0f;
+  const int64_t b = ((int64_t)blockIdx.x * CG + cg) * 32 + sg.lane;
+  if (b < A.B) tree_bwd_seg(r, A, b, sg);
+  __syncthreads();
+  if (b < A.B) {
+    for (int s = sg.g; s < ns; s += G) {
+      float acc[3] = {0.0f, 0.0f, 0.0f};
+      for (int h = 0; h < G; ++h)
+        for (int q = 0; q < 3; ++q) acc[q] += sg.part[q * o + (s * G + h) * 32 + sg.lane];
+      const int k = __ldg(r.seg_slot_link + t * r.n + s);
+      const int64_t at = (int64_t)__ldg(r.jidx + k) * A.B + b;
+      A.gq[at] = acc[0];
+      A.gqd[at] = acc[1];
+      A.gqdd[at] = acc[2];
+    }
+  }
+}
+
+// The one-thread sweep kernels use no shared memory: give the whole unified
+// L1/shared array to L1, where the stacks live.
 static void prefer_l1() {
   static bool done = false;
   if (!done) {
@@ -25,17 +91,45 @@ static void prefer_l1() {
   }
 }
 
-cudaError_t launch_tree_fwd(const DevRobot& r, const FwdArgs& a, int threads, cudaStream_t s) {
-  prefer_l1();
+static int seg_plan(int segments) { return segments == 2 ? 0 : segments == 4 ? 1 : 2; }
+static int seg_groups(int segments, int threads) { return std::max(1, threads / (32 * segments)); }
+
+size_t tree_seg_smem(const DevRobot& r, int segments, int threads, bool fwd) {
+  const int t = seg_plan(segments);
+  return (size_t)seg_groups(segments, threads) * (fwd ? 1 : 3) * r.seg_ns[t] * segments * 32 *
+         sizeof(float);
+}
+
+template <class Args>
+static cudaError_t launch_seg(void (*kern)(DevRobot, Args, int), const DevRobot& r, const Args& a,
+                              int threads, int segments, bool fwd, cudaStream_t s) {
+  const int t = seg_plan(segments);
+  const int CG = seg_groups(segments, threads);
+  const size_t smem = tree_seg_smem(r, segments, threads, fwd);
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t groups = (a.B + 31) / 32;
+  const int64_t grid = (groups + CG - 1) / CG;
+  kern<<<(unsigned)grid, 32 * segments * CG, smem, s>>>(r, a, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tree_fwd(const DevRobot& r, const FwdArgs& a, int threads, int segments,
+                            cudaStream_t s) {
   if (threads <= 0) threads = 128;
+  if (segments > 1) return launch_seg(tree_fwd_seg_kernel, r, a, threads, segments, true, s);
+  prefer_l1();
   const int64_t grid = (a.B + threads - 1) / threads;
   tree_fwd_kernel<<<(unsigned)grid, threads, 0, s>>>(r, a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tree_bwd(const DevRobot& r, const BwdArgs& a, int threads, cudaStream_t s) {
-  prefer_l1();
+cudaError_t launch_tree_bwd(const DevRobot& r, const BwdArgs& a, int threads, int segments,
+                            cudaStream_t s) {
   if (threads <= 0) threads = 128;
+  if (segments > 1) return launch_seg(tree_bwd_seg_kernel, r, a, threads, segments, false, s);
+  prefer_l1();
   const int64_t grid = (a.B + threads - 1) / threads;
   tree_bwd_kernel<<<(unsigned)grid, threads, 0, s>>>(r, a);
   return cudaGetLastError();

@@ -34,6 +34,20 @@
 // general formula; the v-dependence of a_k through v_k x_m (S qd) enters as
 // the crf(S qd) abar term.  Both are derived from Alg. 4 by reverse-mode
 // differentiation.
+//
+// Segmented sweeps.  A tree with few links per level but many links in total
+// leaves one thread per configuration with a long serial chain and, at a few
+// tens of thousands of configurations, few warps per SM.  The DFS order can
+// instead be cut into G contiguous segments, one warp per segment over the
+// same 32 configurations.  The warp of segment g first replays the ancestors
+// of its first link (pre-order data only: poses, v, a, Fbar; its own force,
+// adjoint and wrench contributions are zero), then sweeps its links.  Every
+// post-order quantity above is linear in the accumulated F, abar, vbar, W
+// given the pre-order data, so the outputs of a link that several segments
+// hold (an ancestor of a segment's first link) are the sums of the
+// segments' partial outputs.  Those partials go to shared-memory slots and
+// the kernel adds them in segment order (deterministic) after a barrier; all
+// other outputs are written directly by the one segment that owns the link.
 #pragma once
 
 #include "spatial.cuh"
@@ -41,6 +55,35 @@
 namespace wbe {
 
 constexpr int TMAXD = 32;  // deepest tree the sweep kernels accept
+
+// One segment of a segmented sweep (see above).  slot == nullptr: the whole
+// DFS order, outputs written directly.
+struct Seg {
+  int p0, p1;          // DFS positions this segment owns
+  int g, G;            // segment index, segments per configuration
+  const int16_t* slot; // [n] shared output slot of a link or -1; nullptr = none
+  float* part;         // partial outputs of this group: [nout][ns][G][32]
+  int ns;              // shared slots
+  int lane;
+};
+
+__device__ __forceinline__ Seg whole_sweep(const DevRobot& r) {
+  return Seg{0, r.n, 0, 1, nullptr, nullptr, 0, 0};
+}
+
+// L2 prefetch hint for a global input of the next link, so that its DRAM
+// latency overlaps the current link's arithmetic (measured on the 48-DoF
+// humanoid: 11 % off the one-thread sweeps; an L1 hint gives the same).
+// Only called on addresses inside the caller's buffers.
+__device__ __forceinline__ void pf(const void* p) { asm volatile("prefetch.L2 [%0];" ::"l"(p)); }
+
+// where the partial output o of link k goes, or nullptr for a direct write
+__device__ __forceinline__ float* seg_part(const Seg& sg, int k, int o) {
+  if (!sg.slot) return nullptr;
+  const int s = __ldg(sg.slot + k);
+  if (s < 0) return nullptr;
+  return sg.part + ((size_t)(o * sg.ns + s) * sg.G + sg.g) * 32 + sg.lane;
+}
 
 __device__ __forceinline__ void motion_S6t(int jt, const float* ax, float* S) {
   S[0] = S[1] = S[2] = S[3] = S[4] = S[5] = 0.0f;
@@ -78,14 +121,16 @@ __device__ __forceinline__ void link_local(const DevRobot& r, int k, const float
 // ---------------------------------------------------------------------------
 // forward: FK + RNEA
 // ---------------------------------------------------------------------------
+// Per-depth stack entry.  The local transform is not kept: post-order
+// recomputes it from q (cheaper than a round trip through local memory).
 struct FEnt {
-  float L[12];  // local transform
   float W[12];  // world pose
   float v[6], a[6], F[6];
   int k;
 };
 
-__device__ __forceinline__ void tree_fwd_one(const DevRobot& r, const FwdArgs& A, int64_t b) {
+__device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A, int64_t b,
+                                             const Seg& sg) {
   const int64_t B = A.B;
   const int n = r.n;
   const bool dyn = A.tau != nullptr;
@@ -102,33 +147,36 @@ __device__ __forceinline__ void tree_fwd_one(const DevRobot& r, const FwdArgs& A
       const float ax[3] = {a4.x, a4.y, a4.z};
       const float mm = __ldg(reinterpret_cast<const float2*>(r.mimic) + k).x;
       const float t = mm * St_dot(__ldg(r.jtype + k), ax, E.F);
-      float* dst = A.tau + (int64_t)j * B + b;
-      *dst = r.mimic_shared ? *dst + t : t;
+      float* pt = seg_part(sg, k, 0);
+      if (pt) {
+        *pt = t;
+      } else {
+        float* dst = A.tau + (int64_t)j * B + b;
+        *dst = r.mimic_shared ? *dst + t : t;
+      }
     }
     if (e > 0) {
-      float up[6];
-      xf_force_T(E.L, E.L + 9, E.F, up);
+      float L[12], up[6];
+      link_local(r, k, A.q, B, b, L);
+      xf_force_T(L, L + 9, E.F, up);
 #pragma unroll
       for (int i = 0; i < 6; ++i) stk[e - 1].F[i] += up[i];
     }
   };
 
-  int sp = 0;
-  for (int pos = 0; pos < n; ++pos) {
-    const int2 kd = __ldg(r.dfs + pos);
-    const int k = kd.x, dep = kd.y;
-    if (dyn)
-      while (sp > dep) close(--sp);
-    sp = dep + 1;
+  // pre-order of link k at depth dep; own = false replays an ancestor of
+  // the segment (pose, v, a only; no output, no force of its own)
+  auto push = [&](int k, int dep, bool own) {
     FEnt& E = stk[dep];
     E.k = k;
-    link_local(r, k, A.q, B, b, E.L);
+    float L[12];
+    link_local(r, k, A.q, B, b, L);
     if (dep > 0)
-      compose(stk[dep - 1].W, E.L, E.W);
+      compose(stk[dep - 1].W, L, E.W);
     else
 #pragma unroll
-      for (int i = 0; i < 12; ++i) E.W[i] = E.L[i];
-    if (A.pose) {
+      for (int i = 0; i < 12; ++i) E.W[i] = L[i];
+    if (own && A.pose) {
       float4* dst = reinterpret_cast<float4*>(A.pose + (b * n + k) * 12);
       dst[0] = make_float4(E.W[0], E.W[1], E.W[2], E.W[3]);
       dst[1] = make_float4(E.W[4], E.W[5], E.W[6], E.W[7]);
@@ -155,23 +203,59 @@ __device__ __forceinline__ void tree_fwd_one(const DevRobot& r, const FwdArgs& A
       const float mm = __ldg(reinterpret_cast<const float2*>(r.mimic) + k).x;
       const float vq = j >= 0 ? mm * __ldg(A.qd + (int64_t)j * B + b) : 0.0f;
       const float aq = j >= 0 ? mm * __ldg(A.qdd + (int64_t)j * B + b) : 0.0f;
-      rnea_va(E.L, E.L + 9, vp, ap, __ldg(r.jtype + k), ax, vq, aq, E.v, E.a);
-      float I[10];
-      load_inertia(r, k, I);
-      rnea_force(I, E.v, E.a, E.F);
+      rnea_va(L, L + 9, vp, ap, __ldg(r.jtype + k), ax, vq, aq, E.v, E.a);
+      if (own) {
+        float I[10];
+        load_inertia(r, k, I);
+        rnea_force(I, E.v, E.a, E.F);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) E.F[i] = 0.0f;
+      }
     }
+  };
+
+  int sp = 0;
+  if (sg.p0 > 0) {  // replay the proper ancestors of the first link
+    const int k0 = __ldg(r.dfs + sg.p0).x;
+    const int c0 = __ldg(r.chain_start + k0), c1 = __ldg(r.chain_start + k0 + 1);
+    for (int c = c0; c < c1 - 1; ++c) push(__ldg(r.chain + c), c - c0, false);
+    sp = c1 - 1 - c0;
+  }
+  for (int pos = sg.p0; pos < sg.p1; ++pos) {
+    const int2 kd = __ldg(r.dfs + pos);
+    const int dep = kd.y;
+    if (pos + 1 < sg.p1) {  // the next link's joint inputs
+      const int jn = __ldg(r.jidx + __ldg(r.dfs + pos + 1).x);
+      if (jn >= 0) {
+        pf(A.q + (int64_t)jn * B + b);
+        if (dyn) {
+          pf(A.qd + (int64_t)jn * B + b);
+          pf(A.qdd + (int64_t)jn * B + b);
+        }
+      }
+    }
+    if (dyn)
+      while (sp > dep) close(--sp);
+    sp = dep + 1;
+    push(kd.x, dep, true);
   }
   if (dyn)
     while (sp > 0) close(--sp);
 }
 
+__device__ __forceinline__ void tree_fwd_one(const DevRobot& r, const FwdArgs& A, int64_t b) {
+  tree_fwd_seg(r, A, b, whole_sweep(r));
+}
+
 // ---------------------------------------------------------------------------
 // backward: the whole adjoint in one sweep
 // ---------------------------------------------------------------------------
+// Per-depth stack entry.  The local transform X_k and X_k Fbar_pa are not
+// kept: post-order recomputes them from q and the parent's Fbar.
 struct BEnt {
-  float L[12], W[12];
+  float W[12];
   float v[6], a[6], F[6];
-  float XF[6];   // X_k Fbar_pa
   float Fb[6];   // Fbar_k
   float ab[6], vb[6], Wr[6];
   int k;
@@ -209,7 +293,8 @@ __device__ __forceinline__ void point_wrench(const float* R, float4 sp, const fl
   w[5] += f[2];
 }
 
-__device__ __forceinline__ void tree_bwd_one(const DevRobot& r, const BwdArgs& A, int64_t b) {
+__device__ __forceinline__ void tree_bwd_seg(const DevRobot& r, const BwdArgs& A, int64_t b,
+                                             const Seg& sg) {
   const int64_t B = A.B;
   const int n = r.n;
   BEnt stk[TMAXD];
@@ -219,7 +304,13 @@ __device__ __forceinline__ void tree_bwd_one(const DevRobot& r, const BwdArgs& A
       A.gqd[(int64_t)j * B + b] = 0.0f;
       A.gqdd[(int64_t)j * B + b] = 0.0f;
     }
-  // the worst pair's gradient: u = g_dmin (c_i - c_j) / |c_i - c_j|
+  // the worst pair's gradient: u = g_dmin (c_i - c_j) / |c_i - c_j|, needed
+  // only by the segment that owns one of the pair's links
+  auto owned = [&](int k) {
+    if (!sg.slot) return true;
+    const int p = __ldg(r.dfs_pos + k);
+    return p >= sg.p0 && p < sg.p1;
+  };
   int pl1 = -1, pl2 = -1, ps1 = 0, ps2 = 0;
   float u[3] = {0.0f, 0.0f, 0.0f};
   if (A.g_dmin) {
@@ -227,25 +318,28 @@ __device__ __forceinline__ void tree_bwd_one(const DevRobot& r, const BwdArgs& A
     const float gd = A.g_dmin[b];
     if (wp >= 0 && wp < r.P && gd != 0.0f) {
       const int2 ij = __ldg(r.pairs + wp);
-      ps1 = ij.x;
-      ps2 = ij.y;
-      pl1 = __ldg(r.sph_link + ps1);
-      pl2 = __ldg(r.sph_link + ps2);
-      float P1[12], P2[12], c1[3], c2[3];
-      chain_pose(r, pl1, A.q, B, b, P1);
-      chain_pose(r, pl2, A.q, B, b, P2);
-      const float4 s1 = __ldg(r.sph + ps1), s2 = __ldg(r.sph + ps2);
-      const float l1[3] = {s1.x, s1.y, s1.z}, l2[3] = {s2.x, s2.y, s2.z};
-      rot(P1, l1, c1);
-      rot(P2, l2, c2);
-      const float dx = (c1[0] + P1[9]) - (c2[0] + P2[9]);
-      const float dy = (c1[1] + P1[10]) - (c2[1] + P2[10]);
-      const float dz = (c1[2] + P1[11]) - (c2[2] + P2[11]);
-      const float nrm = sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
-      const float sc = nrm > 0.0f ? gd / nrm : 0.0f;
-      u[0] = dx * sc;
-      u[1] = dy * sc;
-      u[2] = dz * sc;
+      const int l1 = __ldg(r.sph_link + ij.x), l2 = __ldg(r.sph_link + ij.y);
+      if (owned(l1) || owned(l2)) {
+        ps1 = ij.x;
+        ps2 = ij.y;
+        pl1 = l1;
+        pl2 = l2;
+        float P1[12], P2[12], c1[3], c2[3];
+        chain_pose(r, pl1, A.q, B, b, P1);
+        chain_pose(r, pl2, A.q, B, b, P2);
+        const float4 s1 = __ldg(r.sph + ps1), s2 = __ldg(r.sph + ps2);
+        const float q1[3] = {s1.x, s1.y, s1.z}, q2[3] = {s2.x, s2.y, s2.z};
+        rot(P1, q1, c1);
+        rot(P2, q2, c2);
+        const float dx = (c1[0] + P1[9]) - (c2[0] + P2[9]);
+        const float dy = (c1[1] + P1[10]) - (c2[1] + P2[10]);
+        const float dz = (c1[2] + P1[11]) - (c2[2] + P2[11]);
+        const float nrm = sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+        const float sc = nrm > 0.0f ? gd / nrm : 0.0f;
+        u[0] = dx * sc;
+        u[1] = dy * sc;
+        u[2] = dz * sc;
+      }
     }
   }
 
@@ -260,6 +354,14 @@ __device__ __forceinline__ void tree_bwd_one(const DevRobot& r, const BwdArgs& A
     motion_S6t(jt, ax, S);
     const float mm = __ldg(reinterpret_cast<const float2*>(r.mimic) + k).x;
     const float vq = j >= 0 ? mm * __ldg(A.qd + (int64_t)j * B + b) : 0.0f;
+    float L[12];
+    link_local(r, k, A.q, B, b, L);
+    float XF[6];  // X_k Fbar_pa
+    if (e > 0) {
+      xf_motion(L, L + 9, stk[e - 1].Fb, XF);
+    } else {
+      XF[0] = XF[1] = XF[2] = XF[3] = XF[4] = XF[5] = 0.0f;
+    }
     float ab[6], vb[6], t[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
@@ -267,7 +369,7 @@ __device__ __forceinline__ void tree_bwd_one(const DevRobot& r, const BwdArgs& A
       vb[i] = E.vb[i];
     }
     crf(S, E.F, t);
-    float gq = dot6t(E.XF, t);
+    float gq = dot6t(XF, t);
     crf(S, ab, t);
 #pragma unroll
     for (int i = 0; i < 6; ++i) vb[i] = fmaf(vq, t[i], vb[i]);
@@ -289,58 +391,64 @@ __device__ __forceinline__ void tree_bwd_one(const DevRobot& r, const BwdArgs& A
       ap[5] = r.abase[2];
     }
     float Xa[6], Xv[6], c6[6];
-    xf_motion(E.L, E.L + 9, ap, Xa);
-    xf_motion(E.L, E.L + 9, vp, Xv);
+    xf_motion(L, L + 9, ap, Xa);
+    xf_motion(L, L + 9, vp, Xv);
     crm(S, Xa, c6);
     gq -= dot6t(ab, c6);
     crm(S, Xv, c6);
     gq -= dot6t(vb, c6);
     gq += dot6t(S, E.Wr);
     if (j >= 0) {
-      float* o0 = A.gq + (int64_t)j * B + b;
-      float* o1 = A.gqd + (int64_t)j * B + b;
-      float* o2 = A.gqdd + (int64_t)j * B + b;
-      if (r.mimic_shared) {
-        *o0 += mm * gq;
-        *o1 += mm * gqd;
-        *o2 += mm * gqdd;
+      float* p0 = seg_part(sg, k, 0);
+      if (p0) {
+        const size_t o = (size_t)sg.ns * sg.G * 32;
+        p0[0] = mm * gq;
+        p0[o] = mm * gqd;
+        p0[2 * o] = mm * gqdd;
       } else {
-        *o0 = mm * gq;
-        *o1 = mm * gqd;
-        *o2 = mm * gqdd;
+        float* o0 = A.gq + (int64_t)j * B + b;
+        float* o1 = A.gqd + (int64_t)j * B + b;
+        float* o2 = A.gqdd + (int64_t)j * B + b;
+        if (r.mimic_shared) {
+          *o0 += mm * gq;
+          *o1 += mm * gqd;
+          *o2 += mm * gqdd;
+        } else {
+          *o0 = mm * gq;
+          *o1 = mm * gqd;
+          *o2 = mm * gqdd;
+        }
       }
     }
     if (e > 0) {
       BEnt& P = stk[e - 1];
       float up[6];
-      xf_force_T(E.L, E.L + 9, E.F, up);
+      xf_force_T(L, L + 9, E.F, up);
 #pragma unroll
       for (int i = 0; i < 6; ++i) P.F[i] += up[i];
-      xf_force_T(E.L, E.L + 9, ab, up);
+      xf_force_T(L, L + 9, ab, up);
 #pragma unroll
       for (int i = 0; i < 6; ++i) P.ab[i] += up[i];
-      xf_force_T(E.L, E.L + 9, vb, up);
+      xf_force_T(L, L + 9, vb, up);
 #pragma unroll
       for (int i = 0; i < 6; ++i) P.vb[i] += up[i];
-      xf_force_T(E.L, E.L + 9, E.Wr, up);
+      xf_force_T(L, L + 9, E.Wr, up);
 #pragma unroll
       for (int i = 0; i < 6; ++i) P.Wr[i] += up[i];
     }
   };
 
-  int sp = 0;
-  for (int pos = 0; pos < n; ++pos) {
-    const int2 kd = __ldg(r.dfs + pos);
-    const int k = kd.x, dep = kd.y;
-    while (sp > dep) close(--sp);
-    sp = dep + 1;
+  // pre-order of link k at depth dep; own = false replays an ancestor of
+  // the segment (pose, v, a, Fbar only; its own contributions are zero)
+  auto push = [&](int k, int dep, bool own) {
     BEnt& E = stk[dep];
     E.k = k;
-    link_local(r, k, A.q, B, b, E.L);
+    float L[12];
+    link_local(r, k, A.q, B, b, L);
     float vp[6], ap[6], Fbp[6];
     if (dep > 0) {
       const BEnt& P = stk[dep - 1];
-      compose(P.W, E.L, E.W);
+      compose(P.W, L, E.W);
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
         vp[i] = P.v[i];
@@ -349,7 +457,7 @@ __device__ __forceinline__ void tree_bwd_one(const DevRobot& r, const BwdArgs& A
       }
     } else {
 #pragma unroll
-      for (int i = 0; i < 12; ++i) E.W[i] = E.L[i];
+      for (int i = 0; i < 12; ++i) E.W[i] = L[i];
       vp[0] = vp[1] = vp[2] = vp[3] = vp[4] = vp[5] = 0.0f;
       ap[0] = ap[1] = ap[2] = 0.0f;
       ap[3] = r.abase[0];
@@ -364,18 +472,24 @@ __device__ __forceinline__ void tree_bwd_one(const DevRobot& r, const BwdArgs& A
     const float mm = __ldg(reinterpret_cast<const float2*>(r.mimic) + k).x;
     const float vq = j >= 0 ? mm * __ldg(A.qd + (int64_t)j * B + b) : 0.0f;
     const float aq = j >= 0 ? mm * __ldg(A.qdd + (int64_t)j * B + b) : 0.0f;
-    // dynamics forward: v, a, f
-    rnea_va(E.L, E.L + 9, vp, ap, jt, ax, vq, aq, E.v, E.a);
-    float I[10];
-    load_inertia(r, k, I);
-    rnea_force(I, E.v, E.a, E.F);
+    // dynamics forward: v, a (and f when the link is this segment's)
+    rnea_va(L, L + 9, vp, ap, jt, ax, vq, aq, E.v, E.a);
     // adjoint of the force sweep: Fbar_k = S m taubar + X Fbar_pa
     float S[6];
     motion_S6t(jt, ax, S);
     const float tb = (j >= 0 && A.g_tau) ? mm * __ldg(A.g_tau + (int64_t)j * B + b) : 0.0f;
-    xf_motion(E.L, E.L + 9, Fbp, E.XF);
+    float XF[6];
+    xf_motion(L, L + 9, Fbp, XF);
 #pragma unroll
-    for (int i = 0; i < 6; ++i) E.Fb[i] = fmaf(S[i], tb, E.XF[i]);
+    for (int i = 0; i < 6; ++i) E.Fb[i] = fmaf(S[i], tb, XF[i]);
+    if (!own) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) E.F[i] = E.ab[i] = E.vb[i] = E.Wr[i] = 0.0f;
+      return;
+    }
+    float I[10];
+    load_inertia(r, k, I);
+    rnea_force(I, E.v, E.a, E.F);
     // adjoint of the per-link force: abar, vbar
     {
       float Iv[6], t1[6], t2[6], t3[6];
@@ -421,9 +535,49 @@ __device__ __forceinline__ void tree_bwd_one(const DevRobot& r, const BwdArgs& A
     }
 #pragma unroll
     for (int i = 0; i < 6; ++i) E.Wr[i] = w[i];
+  };
+
+  int sp = 0;
+  if (sg.p0 > 0) {  // replay the proper ancestors of the first link
+    const int k0 = __ldg(r.dfs + sg.p0).x;
+    const int c0 = __ldg(r.chain_start + k0), c1 = __ldg(r.chain_start + k0 + 1);
+    for (int c = c0; c < c1 - 1; ++c) push(__ldg(r.chain + c), c - c0, false);
+    sp = c1 - 1 - c0;
+  }
+  for (int pos = sg.p0; pos < sg.p1; ++pos) {
+    const int2 kd = __ldg(r.dfs + pos);
+    const int dep = kd.y;
+    if (pos + 1 < sg.p1) {  // the next link's inputs
+      const int kn = __ldg(r.dfs + pos + 1).x;
+      const int jn = __ldg(r.jidx + kn);
+      if (jn >= 0) {
+        pf(A.q + (int64_t)jn * B + b);
+        pf(A.qd + (int64_t)jn * B + b);
+        pf(A.qdd + (int64_t)jn * B + b);
+        if (A.g_tau) pf(A.g_tau + (int64_t)jn * B + b);
+      }
+      if (A.g_pose) {
+        const float* gpn = A.g_pose + (b * n + kn) * 12;
+        pf(gpn);
+        pf(gpn + 11);
+      }
+      if (A.g_sph) {
+        const int e0 = __ldg(r.ls_start + kn), e1 = __ldg(r.ls_start + kn + 1);
+        if (e1 > e0) {
+          pf(A.g_sph + (b * r.S + __ldg(r.ls_sph + e0)) * 3);
+          pf(A.g_sph + (b * r.S + __ldg(r.ls_sph + e1 - 1)) * 3 + 2);
+        }
+      }
+    }
+    while (sp > dep) close(--sp);
+    sp = dep + 1;
+    push(kd.x, dep, true);
   }
   while (sp > 0) close(--sp);
 }
 
+__device__ __forceinline__ void tree_bwd_one(const DevRobot& r, const BwdArgs& A, int64_t b) {
+  tree_bwd_seg(r, A, b, whole_sweep(r));
+}
 
 }  // namespace wbe

@@ -217,7 +217,59 @@ struct HostPlan {
   int maxdepth = 0;
   int mimic_shared = 0;
   double r_max = 0.0;
+  // segmented-sweep plans (G = 2, 4, 8)
+  std::vector<int16_t> dfs_pos, seg_slot, seg_slot_link;
+  int seg_ok = 0;
+  int seg_ns[3] = {0, 0, 0};
+  int16_t seg_pos[3][9] = {};
 };
+
+// Cut the DFS order into G contiguous segments minimising the largest
+// segment cost = owned links + 0.7 x replayed ancestors (the depth of the
+// segment's first link): a replayed link does the pre-order without the
+// link's own force / adjoint terms, then a full post-order.  Links held by
+// more than one segment (the proper ancestors of a segment's first link)
+// that drive a joint get an output slot.
+static void plan_segments(HostPlan& H, int t) {
+  const int n = H.n, G = 2 << t;
+  if (H.mimic_shared || n < G) return;
+  const double kInf = 1e300;
+  auto cost = [&](int s, int e) { return (e - s) + 0.7 * H.dfs[s].y; };
+  std::vector<double> best((size_t)(G + 1) * (n + 1), kInf);
+  std::vector<int> arg((size_t)(G + 1) * (n + 1), 0);
+  auto at = [&](int g, int e) { return (size_t)g * (n + 1) + e; };
+  best[at(0, 0)] = 0.0;
+  for (int g = 1; g <= G; ++g)
+    for (int e = g; e <= n; ++e)
+      for (int s0 = g - 1; s0 < e; ++s0) {
+        const double v = std::max(best[at(g - 1, s0)], cost(s0, e));
+        if (v < best[at(g, e)]) {
+          best[at(g, e)] = v;
+          arg[at(g, e)] = s0;
+        }
+      }
+  int e = n;
+  H.seg_pos[t][G] = (int16_t)n;
+  for (int g = G; g >= 1; --g) {
+    e = arg[at(g, e)];
+    H.seg_pos[t][g - 1] = (int16_t)e;
+  }
+  int16_t* slot = &H.seg_slot[(size_t)t * n];
+  int16_t* link = &H.seg_slot_link[(size_t)t * n];
+  int ns = 0;
+  for (int g = 1; g < G; ++g) {
+    const int k0 = H.dfs[H.seg_pos[t][g]].x;
+    for (int c = H.chain_start[k0]; c < H.chain_start[k0 + 1] - 1; ++c) {
+      const int a = H.chain[c];
+      if (H.jidx[a] >= 0 && slot[a] < 0) {
+        slot[a] = (int16_t)ns;
+        link[ns++] = (int16_t)a;
+      }
+    }
+  }
+  H.seg_ns[t] = ns;
+  H.seg_ok |= 1 << t;
+}
 
 static int plan_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs* pairs,
                       const wb_inertial* inertial, HostPlan& H) {
@@ -457,6 +509,11 @@ static int plan_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs
   }
   H.parent.swap(parent);
   H.jidx.swap(jidx);
+  H.dfs_pos.assign(n, 0);
+  for (int p = 0; p < n; ++p) H.dfs_pos[H.dfs[p].x] = (int16_t)p;
+  H.seg_slot.assign(3 * (size_t)n, -1);
+  H.seg_slot_link.assign(3 * (size_t)n, 0);
+  for (int t = 0; t < 3; ++t) plan_segments(H, t);
   H.lev_start.swap(lev_start);
   H.lev_links.swap(lev_links);
   H.child_start.swap(child_start);
@@ -566,6 +623,14 @@ int wb_load_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs* pa
   pk.add_vec(H.chain_start, &D.chain_start);
   pk.add_vec(H.chain, &D.chain);
   D.maxdepth = H.maxdepth;
+  pk.add_vec(H.dfs_pos, &D.dfs_pos);
+  pk.add_vec(H.seg_slot, &D.seg_slot);
+  pk.add_vec(H.seg_slot_link, &D.seg_slot_link);
+  D.seg_ok = H.seg_ok;
+  for (int t = 0; t < 3; ++t) {
+    D.seg_ns[t] = H.seg_ns[t];
+    for (int g = 0; g < 9; ++g) D.seg_pos[t][g] = H.seg_pos[t][g];
+  }
   {
     float rmin = 0.0f;
     for (int s2 = 0; s2 < H.S; ++s2) rmin = s2 == 0 ? H.sp[s2].w : std::min(rmin, H.sp[s2].w);
@@ -744,6 +809,35 @@ static int fused_shape(const wb_robot* R, bool fwd, bool bits, const wb_tune* t,
 
 static bool plain_fits(const DevRobot& D) { return D.n <= 64 && D.S <= 256; }
 
+// Segments of the sweep kernels (wb_tune.lanes_per_config for TREE): 1, 2, 4
+// or 8; 0 = the fewest of the robot's plans that give about 24 (forward) or
+// 12 (backward, whose larger stack entries thrash L1 sooner) warps per SM --
+// measured on the 48-DoF humanoid at 32768 configurations: forward best at 4,
+// backward at 2, 8 slower than 1 for both.
+static int tree_segments(const wb_robot* R, const wb_tune* tune, int64_t B, int threads,
+                         bool fwd, int* out) {
+  const int req = tune ? tune->lanes_per_config : 0;
+  const int ok = R->dev.seg_ok;
+  int G = 1;
+  if (req > 0) {
+    const int t = req == 2 ? 0 : req == 4 ? 1 : req == 8 ? 2 : -1;
+    if (req != 1 && t < 0) return fail(WB_EINVAL, "tree segments must be 1, 2, 4 or 8");
+    if (t >= 0 && !(ok >> t & 1))
+      return fail(WB_EINVAL, "no %d-segment sweep for this robot (fewer links, or a joint "
+                  "driving several links)", req);
+    G = req;
+  } else {
+    const int64_t warps = (B + 31) / 32;
+    const int64_t target = (fwd ? 24LL : 12LL) * R->num_sms;
+    for (int t = 0; t < 3 && warps * G < target; ++t)
+      if (ok >> t & 1) G = 2 << t;
+  }
+  if (G > 1 && tree_seg_smem(R->dev, G, threads, fwd) > 227 * 1024)
+    return fail(WB_ETOOBIG, "segmented sweep needs too much shared memory");
+  *out = G;
+  return WB_OK;
+}
+
 extern "C" {
 
 int wb_eval(wb_robot* robot, int64_t B, const float* q, const float* qd, const float* qdd,
@@ -787,7 +881,9 @@ int wb_eval(wb_robot* robot, int64_t B, const float* q, const float* qd, const f
       return fail(WB_EINVAL, "tree threads per block must be a multiple of 32 in [32, 256]");
     const int warps = (tune && tune->blocks_per_sm) ? tune->blocks_per_sm : 8;
     if (warps < 1 || warps > 8) return fail(WB_EINVAL, "pair warps per block must be in [1, 8]");
-    e = launch_tree_fwd(robot->dev, a, tpb, s);
+    int G = 1;
+    if ((rc = tree_segments(robot, tune, B, tpb, true, &G))) return rc;
+    e = launch_tree_fwd(robot->dev, a, tpb, G, s);
     if (e == cudaSuccess && pairs_wanted) {
       int bps = 0;
       e = pair_max_blocks_per_sm(robot->dev, warps, pair_bits != nullptr, &bps);
@@ -875,7 +971,9 @@ int wb_eval_backward(wb_robot* robot, int64_t B, const float* q, const float* qd
     const int tpb = (tune && tune->configs_per_block) ? tune->configs_per_block : 128;
     if (tpb < 32 || tpb > 256 || tpb % 32)
       return fail(WB_EINVAL, "tree threads per block must be a multiple of 32 in [32, 256]");
-    e = launch_tree_bwd(robot->dev, a, tpb, s);
+    int G = 1;
+    if ((rc = tree_segments(robot, tune, B, tpb, false, &G))) return rc;
+    e = launch_tree_bwd(robot->dev, a, tpb, G, s);
   } else if (kernel == WB_KERNEL_FUSED) {
     FusedShape sh;
     if ((rc = fused_shape(robot, false, false, tune, B, sh))) return rc;
@@ -1310,8 +1408,11 @@ extern "C" int wb_autotune(wb_robot* robot, int64_t B, wb_tune* fwd, wb_tune* bw
     return fail(WB_ECUDA, "autotune stream/events");
   std::vector<wb_tune> cands;
   if (D.maxdepth <= tree_max_depth())
-    for (int tpb : {64, 128, 256})
-      for (int pw : {4, 8}) cands.push_back(wb_tune{WB_KERNEL_TREE, 0, tpb, pw});
+    for (int seg : {1, 2, 4, 8})
+      for (int tpb : {64, 128, 256})
+        for (int pw : {4, 8})
+          if (seg == 1 || (tpb >= 128 && (D.seg_ok >> (seg == 2 ? 0 : seg == 4 ? 1 : 2) & 1)))
+            cands.push_back(wb_tune{WB_KERNEL_TREE, seg, tpb, pw});
   for (int G : {4, 8, 16, 32}) cands.push_back(wb_tune{WB_KERNEL_FUSED, G, 0, 0});
   if (plain_fits(D)) cands.push_back(wb_tune{WB_KERNEL_PLAIN, 0, 0, 0});
   float best_f = 1e30f, best_b = 1e30f;

@@ -42,6 +42,13 @@ struct DevRobot {
   int mimic_shared;          // 1 if some joint drives more than one link
   const int16_t* chain_start;// [n+1] ancestor chains (Alg. 1 "linkChain")
   const int16_t* chain;      // root -> link, link included
+  const int16_t* dfs_pos;    // [n] DFS position of each link
+  // segmented sweeps with G = 2 << t segments, t = 0, 1, 2 (tree_sweep.cuh)
+  int seg_ok;                // bit t set: plan t exists
+  int seg_ns[3];             // shared output slots of plan t
+  int16_t seg_pos[3][9];     // first DFS position of each segment; [G] = n
+  const int16_t* seg_slot;   // [3][n] shared output slot of a link, -1 = none
+  const int16_t* seg_slot_link; // [3][n] link of each slot
   const int4* lvm;           // [n] per level-ordered slot: link, parent,
                              //   (jidx+1) | jtype << 16 | rot_id << 24,
                              //   child_start | child_end << 16
@@ -183,8 +190,13 @@ cudaError_t batch_tree_max_blocks_per_sm(bool fwd, int* out);
 int pair_plan_words(const DevRobot& r);
 
 // launchers (return cudaGetLastError())
-cudaError_t launch_tree_fwd(const DevRobot& r, const FwdArgs& a, int threads, cudaStream_t s);
-cudaError_t launch_tree_bwd(const DevRobot& r, const BwdArgs& a, int threads, cudaStream_t s);
+// segments: 1 = one thread per configuration; 2, 4, 8 = segmented sweep
+// (requires the robot's plan for it, bit log2(segments) - 1 of seg_ok)
+cudaError_t launch_tree_fwd(const DevRobot& r, const FwdArgs& a, int threads, int segments,
+                            cudaStream_t s);
+cudaError_t launch_tree_bwd(const DevRobot& r, const BwdArgs& a, int threads, int segments,
+                            cudaStream_t s);
+size_t tree_seg_smem(const DevRobot& r, int segments, int threads, bool fwd);
 int tree_max_depth();
 size_t pair_smem(const DevRobot& r, int warps, bool bits);
 cudaError_t launch_pair(const DevRobot& r, const PairSchedule32& ps, const FwdArgs& a, int grid,

@@ -306,3 +306,48 @@ def test_autotune_choice_is_valid_and_exact(W, O, rname, tmp_path):
     gref = O.gradient(desc, q, qd, qdd, gp, gs, gm, gt)
     same = o["worst"].cpu().numpy() == O.evaluate(desc, q, want=("dmin",))["worst"]
     PY.check_gradient([x.cpu().numpy() for x in g], gref, mask=same)
+
+
+def _segments_available(desc, G):
+    """The sweep kernels cut the depth-first order into G segments unless the
+    robot has fewer links or a joint driving several links."""
+    ji = [j for j in np.asarray(desc.jidx).tolist() if j >= 0]
+    return G == 1 or (len(desc.parent) >= G and len(ji) == len(set(ji)))
+
+
+@pytest.mark.parametrize("rname", list(ROBOTS))
+@pytest.mark.parametrize("G", [1, 2, 4, 8])
+def test_tree_segments_parity(W, O, rname, G):
+    """Segmented depth-first sweeps (G warps per 32 configurations, shared
+    ancestors' outputs summed across segments) against the oracle, forward
+    and backward, on a ragged batch."""
+    desc, rob = robot(W, rname)
+    tune = W.Tune(kernel=3, lanes_per_config=G)
+    B = 77 if rname == "R48" else 203
+    q, qd, qdd = I.uniform_states(desc.dof, B, seed=hash((rname, 5, G)) % 1000)
+    if not _segments_available(desc, G):
+        with pytest.raises(W.L.WbError) as ei:
+            rob.eval(cuda(q), cuda(qd), cuda(qdd), tune=tune)
+        assert ei.value.code == W.L.WB_EINVAL
+        return
+    got = run_fwd(rob, q, qd, qdd, tune)
+    PY.check_forward(desc, got, O.evaluate(desc, q, qd, qdd))
+    Bb = 45
+    q, qd, qdd = q[:, :Bb].copy(), qd[:, :Bb].copy(), qdd[:, :Bb].copy()
+    gp, gs, gm, gt = I.upstream_grads(desc, Bb, seed=G + 11)
+    o = rob.eval(cuda(q), cuda(qd), cuda(qdd), tune=tune)
+    g = rob.eval_backward(cuda(q), cuda(qd), cuda(qdd), o["worst"], cuda(gp), cuda(gs),
+                          cuda(gm), cuda(gt), tune=tune)
+    torch.cuda.synchronize()
+    ref = O.evaluate(desc, q, want=("dmin",))
+    gref = O.gradient(desc, q, qd, qdd, gp, gs, gm, gt)
+    same = o["worst"].cpu().numpy() == ref["worst"]
+    assert same.mean() >= 0.9
+    PY.check_gradient([x.cpu().numpy() for x in g], gref, mask=same)
+    # the same configurations through one thread per configuration: the
+    # segments only change the order of the shared ancestors' sums
+    g1 = rob.eval_backward(cuda(q), cuda(qd), cuda(qdd), o["worst"], cuda(gp), cuda(gs),
+                           cuda(gm), cuda(gt), tune=W.Tune(kernel=3, lanes_per_config=1))
+    torch.cuda.synchronize()
+    for a, b in zip(g, g1):
+        torch.testing.assert_close(a, b, rtol=1e-4, atol=1e-4 * float(b.abs().max()))
