@@ -54,6 +54,8 @@ def lib():
         _lib.or_grad.argtypes = [C.POINTER(_Robot), C.c_int, p, p, p, p, p, p, p, p, p, p, p,
                                  C.c_int]
         _lib.or_bspline.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, p, p, p, p]
+        _lib.or_bspline_vjp.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, p, p, p,
+                                        p]
     return _lib
 
 
@@ -179,6 +181,64 @@ def bspline(U, T: int, dt: float):
     if rc != 0:
         raise ValueError("or_bspline: bad sizes")
     return (np.ascontiguousarray(q.T), np.ascontiguousarray(qd.T), np.ascontiguousarray(qdd.T))
+
+
+def bspline_vjp(gq, gqd, gqdd, n_traj: int, K: int, T: int, dt: float):
+    """Control-point gradient of a scalar with upstream gradients gq, gqd,
+    gqdd [d][n_traj*T] on the B-spline states (Eq. backward_grad; each may be
+    None).  Returns Ubar [n_traj][d][K]."""
+    g = [None if x is None else np.ascontiguousarray(np.asarray(x, np.float64).T)
+         for x in (gq, gqd, gqdd)]
+    d = next(x.shape[1] for x in g if x is not None)
+    Ub = np.zeros((n_traj, d, K))
+    rc = lib().or_bspline_vjp(n_traj, d, K, T, dt, _ptr(g[0]), _ptr(g[1]), _ptr(g[2]), _ptr(Ub))
+    if rc != 0:
+        raise ValueError("or_bspline_vjp: bad sizes")
+    return Ub
+
+
+def trajopt_cost(tau, dmin, tau_lo, tau_hi, w_coll):
+    """Per-configuration cost of the trajectory-optimisation workload and its
+    upstream gradients (torque-limit hinges per joint plus the self-collision
+    hinge on the worst pair):
+        cost_b = sum_j [max(0, tau_jb - hi_j) + max(0, lo_j - tau_jb)]
+                 + w max(0, -dmin_b),
+        dL/dtau_jb = [tau_jb > hi_j] - [tau_jb < lo_j],
+        dL/ddmin_b = -w [dmin_b < 0]
+    (a kink takes the zero one-sided derivative).  tau [d][B], dmin [B],
+    limits [d].  Returns cost [B], g_tau [d][B], g_dmin [B] in float64."""
+    tau = np.asarray(tau, np.float64)
+    dmin = np.asarray(dmin, np.float64)
+    lo = np.asarray(tau_lo, np.float64)[:, None]
+    hi = np.asarray(tau_hi, np.float64)[:, None]
+    over = np.maximum(0.0, tau - hi)
+    under = np.maximum(0.0, lo - tau)
+    cost = (over + under).sum(axis=0) + w_coll * np.maximum(0.0, -dmin)
+    g_tau = (tau > hi).astype(np.float64) - (tau < lo).astype(np.float64)
+    g_dmin = -w_coll * (dmin < 0).astype(np.float64)
+    return cost, g_tau, g_dmin
+
+
+def trajopt_value(robot, U, T: int, dt: float, tau_lo, tau_hi, w_coll):
+    """Total cost L(U) = sum_b cost_b over every sample of every trajectory:
+    B-spline states -> whole-body evaluation -> cost."""
+    q, qd, qdd = bspline(U, T, dt)
+    ev = evaluate(robot, q, qd, qdd, want=("dmin", "tau"))
+    cost, _, _ = trajopt_cost(ev["tau"], ev["dmin"], tau_lo, tau_hi, w_coll)
+    return float(cost.sum()), ev
+
+
+def trajopt_gradient(robot, U, T: int, dt: float, tau_lo, tau_hi, w_coll):
+    """dL/dU by the chain of the pieces above: cost gradients -> VJP of the
+    whole-body evaluation (dual numbers) -> VJP of the B-spline.  Returns
+    (Ubar [n_traj][d][K], per-configuration cost [B], evaluation dict)."""
+    U = np.asarray(U, np.float64)
+    n_traj, d, K = U.shape
+    q, qd, qdd = bspline(U, T, dt)
+    ev = evaluate(robot, q, qd, qdd, want=("dmin", "tau"))
+    cost, g_tau, g_dmin = trajopt_cost(ev["tau"], ev["dmin"], tau_lo, tau_hi, w_coll)
+    gq, gqd, gqdd = gradient(robot, q, qd, qdd, g_dmin=g_dmin, g_tau=g_tau)
+    return bspline_vjp(gq, gqd, gqdd, n_traj, K, T, dt), cost, ev
 
 
 def max_threads() -> int:

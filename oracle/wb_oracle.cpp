@@ -21,7 +21,8 @@
 //      (one pass per input coordinate); d_min differentiates through the
 //      selected worst pair.
 //   6. the uniform cubic B-spline of Sec. 4 (Eq. bspline-cubic), used to make
-//      joint trajectories from control points.
+//      joint trajectories from control points, and its vector-Jacobian
+//      product with respect to the control points (Eq. backward_grad).
 //
 // Readings where the paper is silent: gravity enters as a fictitious base
 // acceleration a_base = [0; -g]; a fixed joint has an empty motion subspace;
@@ -600,6 +601,47 @@ int or_bspline(int n_traj, int d, int K, int T, double dt, const double* U, doub
         q[b * d + j] = out[0];
         qd[b * d + j] = out[1];
         qdd[b * d + j] = out[2];
+      }
+    }
+  return 0;
+}
+
+// Vector-Jacobian product of or_bspline (Eq. backward_grad): every sample adds
+// B(alpha)^T g to the four control points of its window, B = T P(alpha) C with
+// the rows for theta, theta_dot, theta_ddot.  gq, gqd, gqdd [n_traj*T][d]
+// (each may be NULL = zero); Ubar [n_traj][d][K] is overwritten.
+int or_bspline_vjp(int n_traj, int d, int K, int T, double dt, const double* gq,
+                   const double* gqd, const double* gqdd, double* Ubar) {
+  if (K < 4 || T < 2) return -1;
+  const double C[4][4] = {{-1.0 / 6, 3.0 / 6, -3.0 / 6, 1.0 / 6},
+                          {3.0 / 6, -6.0 / 6, 3.0 / 6, 0.0},
+                          {-3.0 / 6, 0.0, 3.0 / 6, 0.0},
+                          {1.0 / 6, 4.0 / 6, 1.0 / 6, 0.0}};
+  const int nseg = K - 3;
+  std::fill(Ubar, Ubar + (size_t)n_traj * d * K, 0.0);
+  for (int tr = 0; tr < n_traj; ++tr)
+    for (int s = 0; s < T; ++s) {
+      double t = (double)s * nseg / (double)(T - 1);
+      int k = (int)std::floor(t);
+      if (k > nseg - 1) k = nseg - 1;
+      double al = t - k;
+      double P[3][4] = {{al * al * al, al * al, al, 1.0},
+                        {3 * al * al / dt, 2 * al / dt, 1.0 / dt, 0.0},
+                        {6 * al / (dt * dt), 2.0 / (dt * dt), 0.0, 0.0}};
+      double Bm[3][4];
+      for (int row = 0; row < 3; ++row)
+        for (int l = 0; l < 4; ++l) {
+          double acc = 0.0;
+          for (int m = 0; m < 4; ++m) acc += P[row][m] * C[m][l];
+          Bm[row][l] = acc;
+        }
+      const size_t b = (size_t)tr * T + s;
+      for (int j = 0; j < d; ++j) {
+        const double g[3] = {gq ? gq[b * d + j] : 0.0, gqd ? gqd[b * d + j] : 0.0,
+                             gqdd ? gqdd[b * d + j] : 0.0};
+        double* u = Ubar + ((size_t)tr * d + j) * K + k;
+        for (int l = 0; l < 4; ++l)
+          u[l] += Bm[0][l] * g[0] + Bm[1][l] * g[1] + Bm[2][l] * g[2];
       }
     }
   return 0;

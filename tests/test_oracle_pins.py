@@ -442,3 +442,106 @@ def test_bspline_reproduces_polynomials(oracle_lib):
     assert np.allclose(q[2], x ** 2 + 1.0 / 3.0, atol=1e-12)
     assert np.allclose(qd[2], 2 * x / dt, atol=1e-11)
     assert np.allclose(qdd[2], 2 / dt ** 2, atol=1e-10)
+
+
+def test_bspline_vjp_is_the_adjoint(oracle_lib):
+    """The B-spline map U -> (q, qd, qdd) is linear, so its VJP must satisfy
+    <bspline(U), g> = <U, vjp(g)> for every U and g (Eq. backward_grad is the
+    transpose of Eq. bspline-cubic)."""
+    O = oracle_lib
+    rng = np.random.default_rng(31)
+    n_traj, d, K, T, dt = 3, 4, 9, 23, 0.3
+    U = rng.normal(size=(n_traj, d, K))
+    g = [rng.normal(size=(d, n_traj * T)) for _ in range(3)]
+    q, qd, qdd = O.bspline(U, T, dt)
+    lhs = sum(float((a * b).sum()) for a, b in zip((q, qd, qdd), g))
+    Ub = O.bspline_vjp(*g, n_traj, K, T, dt)
+    assert abs(lhs - float((U * Ub).sum())) <= 1e-11 * max(1.0, abs(lhs))
+    # each upstream array alone, the others absent
+    for i in range(3):
+        gi = [g[k] if k == i else None for k in range(3)]
+        Ui = O.bspline_vjp(*gi, n_traj, K, T, dt)
+        lhs_i = float(((q, qd, qdd)[i] * g[i]).sum())
+        assert abs(lhs_i - float((U * Ui).sum())) <= 1e-11 * max(1.0, abs(lhs_i))
+
+
+def test_bspline_vjp_local_support_is_the_textbook_basis(oracle_lib):
+    """A unit gradient on one sample's position reaches only the four control
+    points of its window, with the uniform cubic B-spline basis values
+    (1-a)^3/6, (3a^3-6a^2+4)/6, (-3a^3+3a^2+3a+1)/6, a^3/6 (partition of
+    unity); on its velocity, their derivatives / dt."""
+    O = oracle_lib
+    K, T, dt = 10, 19, 0.2
+    nseg = K - 3
+    for s in (0, 5, 11, T - 1):
+        t = s * nseg / (T - 1)
+        k = min(int(np.floor(t)), nseg - 1)
+        a = t - k
+        g = np.zeros((1, T))
+        g[0, s] = 1.0
+        Ub = O.bspline_vjp(g, None, None, 1, K, T, dt)[0, 0]
+        basis = np.array([(1 - a) ** 3, 3 * a ** 3 - 6 * a ** 2 + 4,
+                          -3 * a ** 3 + 3 * a ** 2 + 3 * a + 1, a ** 3]) / 6
+        ref = np.zeros(K)
+        ref[k:k + 4] = basis
+        assert np.allclose(Ub, ref, atol=1e-14)
+        assert abs(basis.sum() - 1.0) < 1e-14
+        Ubd = O.bspline_vjp(None, g, None, 1, K, T, dt)[0, 0]
+        dbasis = np.array([-3 * (1 - a) ** 2, 9 * a ** 2 - 12 * a, -9 * a ** 2 + 6 * a + 3,
+                           3 * a ** 2]) / 6 / dt
+        refd = np.zeros(K)
+        refd[k:k + 4] = dbasis
+        assert np.allclose(Ubd, refd, atol=1e-13)
+
+
+def test_trajopt_cost_closed_form(oracle_lib):
+    """Hinges on hand-made torques and distances: only the parts beyond the
+    limits count, gradients are +-1 there, and the collision hinge is
+    -w dmin for penetration only."""
+    O = oracle_lib
+    tau = np.array([[35.0, 10.0, -31.0], [-40.0, 29.9, 0.0]])  # [d=2][B=3]
+    dmin = np.array([0.2, -0.05, 0.0])
+    lo, hi = np.array([-30.0, -30.0]), np.array([30.0, 30.0])
+    cost, g_tau, g_dmin = O.trajopt_cost(tau, dmin, lo, hi, 2.0)
+    assert np.allclose(cost, [5.0 + 10.0, 0.0 + 2.0 * 0.05, 1.0 + 0.0], atol=1e-12)
+    assert np.array_equal(g_tau, [[1.0, 0.0, -1.0], [-1.0, 0.0, 0.0]])
+    assert np.array_equal(g_dmin, [0.0, -2.0, 0.0])
+
+
+def test_trajopt_chain_gradient_matches_finite_differences(oracle_lib):
+    """dL/dU through cost -> whole-body VJP -> B-spline VJP equals central
+    differences of the total cost, at control points where no hinge and no
+    worst pair switches within the step (torque limits at the median |tau|,
+    sphere radii scaled so that some samples penetrate and some do not)."""
+    import dataclasses
+    O = oracle_lib
+    base = R.r7()
+    rob = dataclasses.replace(base, sph_r=base.sph_r * 0.7)
+    rng = np.random.default_rng(5)
+    n_traj, K, T, dt = 2, 6, 9, 0.25
+    U = rng.uniform(-1.5, 1.5, size=(n_traj, rob.dof, K))
+    _, ev = O.trajopt_value(rob, U, T, dt, -np.ones(rob.dof), np.ones(rob.dof), 1.0)
+    lim = float(np.median(np.abs(ev["tau"])))
+    lo, hi, w = -lim * np.ones(rob.dof), lim * np.ones(rob.dof), 1.5
+    assert (ev["dmin"] < 0).any() and (ev["dmin"] > 0).any()
+    Ub, cost, ev = O.trajopt_gradient(rob, U, T, dt, lo, hi, w)
+    assert ((np.abs(ev["tau"]) > lim).mean()) > 0.2
+    h = 1e-6
+    checked = 0
+    for flat in rng.choice(U.size, size=16, replace=False):
+        idx = np.unravel_index(flat, U.shape)
+        Up, Um = U.copy(), U.copy()
+        Up[idx] += h
+        Um[idx] -= h
+        vp, evp = O.trajopt_value(rob, Up, T, dt, lo, hi, w)
+        vm, evm = O.trajopt_value(rob, Um, T, dt, lo, hi, w)
+        same = all(np.array_equal(a["tau"] > hi[:, None], ev["tau"] > hi[:, None]) and
+                   np.array_equal(a["tau"] < lo[:, None], ev["tau"] < lo[:, None]) and
+                   np.array_equal(a["dmin"] < 0, ev["dmin"] < 0) and
+                   np.array_equal(a["worst"], ev["worst"]) for a in (evp, evm))
+        if not same:
+            continue
+        fd = (vp - vm) / (2 * h)
+        assert abs(fd - Ub[idx]) <= 1e-6 * max(1.0, abs(Ub[idx])), (idx, fd, Ub[idx])
+        checked += 1
+    assert checked >= 8
