@@ -54,9 +54,6 @@ def work_per_eval(desc):
     }
 
 
-# DRAM traffic (read + write) per evaluation from one ncu capture of each
-# kernel (24576 configurations of the humanoid48 workload; traffic scales with
-# the batch).  Keyed by the source file's hash: a changed kernel reads null.
 # DRAM bytes (read + write) per evaluation from one ncu capture of each
 # kernel at the bench's launch configuration on 24576 configurations, tied to
 # the hash of the sources that kernel is built from: a changed source makes the
@@ -424,6 +421,163 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def trajopt_work(desc, K, T):
+    """Algorithmic flops and HBM bytes per configuration for the kernels of the
+    trajectory-optimisation step (no pose or sphere gradients flow back; the
+    pair kernel stores no sphere centres)."""
+    n = desc.n
+    nm = int((desc.jtype != R.FIXED).sum())
+    S, P, d = desc.S, desc.P, desc.dof
+    return {
+        "bspline_fwd": {"flops": 84 * d, "bytes": 4 * 3 * d + 4 * d * K // T},
+        "tree_fwd": {"flops": 150 * nm + 330 * n, "bytes": 4 * (3 * d + 12 * n + d)},
+        "pair": {"flops": 18 * S + 11 * P, "bytes": 4 * (12 * n + 2)},
+        "cost": {"flops": 6 * d + 3, "bytes": 4 * (2 * d + 3)},
+        "tree_bwd": {"flops": 150 * nm + 330 * n + 660 * n + 60 * n,
+                     "bytes": 4 * (3 * d + 2 + d + 3 * d)},
+        "bspline_bwd": {"flops": 24 * d, "bytes": 4 * 3 * d + 4 * d * K // T},
+    }
+
+
+def run_trajopt(args):
+    """Trajectory-optimisation gradient step on the 48-DoF humanoid with 3 kg
+    hand payloads: 512 seeds x 16 control points per joint -> 64 B-spline
+    samples each (32768 configurations) -> FK + RNEA sweep -> self-collision
+    -> torque-limit + collision hinge cost -> adjoint sweep -> dL/dU.
+    Value = configurations per second."""
+    import torch
+    from paper_2603_05493_gb300 import build
+    build()
+    from paper_2603_05493_gb300 import wbe
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    desc = I.hand_payload(R.r48())
+    rob = wbe.Robot(desc, device=0)
+    n_traj, K, T, dt = CF.TRAJOPT_SEEDS, CF.TRAJOPT_KNOTS, CF.TRAJOPT_STEPS, CF.TRAJOPT_DT
+    B, d = n_traj * T, desc.dof
+    ft, bt, _, _ = rob.autotune(B)
+    seg = lambda t: t.lanes_per_config if t.kernel == wbe.L.WB_KERNEL_TREE else 0  # noqa
+    tpb = lambda t: t.configs_per_block if t.kernel == wbe.L.WB_KERNEL_TREE else 0  # noqa
+    ftune = wbe.Tune(kernel=wbe.L.WB_KERNEL_TREE, lanes_per_config=seg(ft),
+                     configs_per_block=tpb(ft))
+    btune = wbe.Tune(kernel=wbe.L.WB_KERNEL_TREE, lanes_per_config=seg(bt),
+                     configs_per_block=tpb(bt))
+    hU = torch.from_numpy(I.bspline_controls(d, n_traj, K, seed=CF.TRAJOPT48.seed)).pin_memory()
+    U = hU.to(dev)
+    lo = torch.full((d,), -CF.TORQUE_LIMIT, device=dev)
+    hi = torch.full((d,), CF.TORQUE_LIMIT, device=dev)
+    q, qd, qdd = (torch.empty((d, B), device=dev) for _ in range(3))
+    out = rob.empty_outputs(B, sphere=False)
+    fwd_out = {"pose": out["pose"], "sphere": None, "dmin": None, "worst": None,
+               "tau": out["tau"], "bits": None}
+    pair_out = {"sphere": None, "dmin": out["dmin"], "worst": out["worst"], "bits": None}
+    cost = torch.empty((B,), device=dev)
+    g_tau = torch.empty((d, B), device=dev)
+    g_dmin = torch.empty((B,), device=dev)
+    gout = tuple(torch.empty((d, B), device=dev) for _ in range(3))
+    gU = torch.empty((n_traj, d, K), device=dev)
+    stream = torch.cuda.current_stream()
+    names = ["bspline_fwd", "tree_fwd", "pair", "cost", "tree_bwd", "bspline_bwd"]
+
+    def step(ev=None):
+        mark = (lambda i: ev[i].record(stream)) if ev else (lambda i: None)
+        wbe.bspline_eval(U, T, dt, q, qd, qdd)
+        mark(1)
+        rob.eval(q, qd, qdd, tune=ftune, out=fwd_out, dmin=False, sphere=False)
+        mark(2)
+        rob.self_collision(out["pose"], out=pair_out)
+        mark(3)
+        wbe.trajopt_cost(out["tau"], out["dmin"], lo, hi, CF.COLLISION_WEIGHT, cost, g_tau,
+                         g_dmin)
+        mark(4)
+        rob.eval_backward(q, qd, qdd, out["worst"], None, None, g_dmin, g_tau, tune=btune,
+                          out=gout)
+        mark(5)
+        wbe.bspline_backward(*gout, n_traj, K, T, dt, gU)
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        evs[i][0].record(stream)
+        step(evs[i])
+        evs[i][6].record(stream)
+    torch.cuda.synchronize()
+    step_ms = float(np.mean([e[0].elapsed_time(e[6]) for e in evs]))
+    k_ms = {nm: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in evs]))
+            for i, nm in enumerate(names)}
+    # end to end: control points in from pinned host memory, dL/dU and the
+    # per-configuration cost back, every step
+    hgU = torch.empty(gU.shape, pin_memory=True)
+    hcost = torch.empty(cost.shape, pin_memory=True)
+    e2e_steps = max(3, min(args.steps, 20))
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(e2e_steps):
+        U.copy_(hU, non_blocking=True)
+        step()
+        hgU.copy_(gU, non_blocking=True)
+        hcost.copy_(cost, non_blocking=True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clocks.stop()
+    e2e_ms = t0.elapsed_time(t1) / e2e_steps
+    work = trajopt_work(desc, K, T)
+    peaks = measured_peaks()
+    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = fp32_peak_tflops(num_sms, peaks.get("sm_max_mhz", 2070.0))
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    ridge = alu_peak * 1e12 / (hbm_peak * 1e9)
+    kernels = {}
+    kn = {"bspline_fwd": "bspline_fwd_kernel", "pair": "pair_kernel",
+          "tree_fwd": "tree_fwd_seg_kernel" if seg(ft) > 1 else "tree_fwd_kernel",
+          "cost": "trajopt_cost_kernel",
+          "tree_bwd": "tree_bwd_seg_kernel" if seg(bt) > 1 else "tree_bwd_kernel",
+          "bspline_bwd": "bspline_bwd_kernel"}
+    for nm, ms in k_ms.items():
+        w = work[nm]
+        if w["flops"] / w["bytes"] >= ridge:
+            ach = w["flops"] * B / (ms * 1e-3) / 1e12
+            kernels[nm] = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
+                           "frac": ach / alu_peak}
+        else:
+            ach = w["bytes"] * B / (ms * 1e-3) / 1e9
+            kernels[nm] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                           "frac": ach / hbm_peak}
+        kernels[nm].update({"kernel": kn[nm], "ms": ms, "flops_per_eval": w["flops"],
+                            "bytes_per_eval": w["bytes"], "traffic": None})
+    dom = max(k_ms, key=k_ms.get)
+    line = {
+        "metric": "trajopt48 evals/s (B-spline -> FK+self-coll+RNEA -> hinge cost -> "
+                  "adjoint -> dL/dU)",
+        "value": B / (step_ms * 1e-3), "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "trajopt48: 48-DoF tree + 3 kg hand payloads, 512 seeds x 64 "
+                               "B-spline samples (16 control points / joint, dt 0.25 s), "
+                               "torque limits +-30 N m, collision weight 1",
+                   "configurations": B,
+                   "autotuned": {"fwd": dict(ft.__dict__), "bwd": dict(bt.__dict__)},
+                   "l2": "flushed between timed steps (512 MB write outside the events)"},
+        "roofline": dict(kernel=kn[dom], **{k: kernels[dom][k] for k in
+                         ("bound", "achieved", "peak", "unit", "frac", "traffic")}),
+        "kernels": kernels,
+        "active_torque_hinges": float((out["tau"].abs() > CF.TORQUE_LIMIT).float().mean()),
+        "penetrating_configurations": float((out["dmin"] < 0).float().mean()),
+        "e2e": {"value": B / (e2e_ms * 1e-3), "unit": "evals/s",
+                "h2d_bytes_per_step": int(hU.numel() * 4),
+                "d2h_bytes_per_step": int(hgU.numel() * 4 + hcost.numel() * 4)},
+        "gpu_launches": 6 * args.steps,
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_uneven(args):
     """Uneven batch: 256 x R7 + 256 x R23 + 256 x R48 problems with horizons
     U{16..64}, forward (FK + RNEA, spheres + self-collision) and backward in
@@ -519,7 +673,8 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--cpu-s", type=float, default=15.0)
     ap.add_argument("--ref-step-s", type=float, default=10.0)
-    ap.add_argument("--workload", choices=["humanoid48", "uneven"], default="humanoid48")
+    ap.add_argument("--workload", choices=["humanoid48", "uneven", "trajopt48"],
+                    default="humanoid48")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -529,6 +684,9 @@ def main():
         return
     if args.workload == "uneven":
         run_uneven(args)
+        return
+    if args.workload == "trajopt48":
+        run_trajopt(args)
         return
     if world > 1:
         import torch

@@ -275,6 +275,49 @@ int wb_batch_eval_backward(wb_batch* batch, const float* q, const float* qd, con
 void wb_free_batch(wb_batch* batch);
 
 /* ---------------------------------------------------------------------------
+ * Trajectory-optimisation ends of the evaluation.  These calls take no robot:
+ * every buffer must live on one device (the first non-NULL buffer fixes it),
+ * be 16-byte aligned and caller-owned.
+ *
+ * Joint states from uniform cubic B-spline control points (Sec. 4,
+ * Eq. bspline-cubic): U [n_traj][d][K] control points per trajectory and
+ * joint; each trajectory is sampled at T points uniformly spaced over its K-3
+ * segments, t_s = s (K-3) / (T-1), segment k = min(floor(t_s), K-4),
+ * alpha = t_s - k, window u_k .. u_k+3, state = T P(alpha) C window with the
+ * time scaling 1/dt per derivative order.  Outputs q, qd, qdd (each nullable)
+ * joint-major [d][n_traj*T], configuration b = traj*T + s.
+ * Limits: 4 <= K <= 4096, 2 <= T <= 4096, dt > 0.
+ * Errors: WB_EINVAL, WB_EDEVICE, WB_ECUDA. */
+int wb_bspline_eval(int64_t n_traj, int32_t d, int32_t K, int32_t T, float dt, const float* U,
+                    float* q, float* qd, float* qdd, void* stream);
+
+/* Control-point gradient (Eq. backward_grad): gU [n_traj][d][K] (overwritten)
+ * = sum over samples of B(alpha)^T (gq, gqd, gqdd) for the four control
+ * points of each sample's window; upstream gradients [d][n_traj*T], each
+ * nullable (= zero).  Deterministic (no atomics).  Errors as wb_bspline_eval. */
+int wb_bspline_backward(int64_t n_traj, int32_t d, int32_t K, int32_t T, float dt,
+                        const float* gq, const float* gqd, const float* gqdd, float* gU,
+                        void* stream);
+
+/* Per-configuration cost of trajectory optimisation and its upstream
+ * gradients:
+ *   cost[b]     = sum_j max(0, tau[j][b] - tau_hi[j]) + max(0, tau_lo[j] - tau[j][b])
+ *                 + w_coll * max(0, -d_min[b])
+ *   g_tau[j][b] = [tau > tau_hi] - [tau < tau_lo]      (d cost / d tau)
+ *   g_dmin[b]   = -w_coll * [d_min < 0]                (d cost / d d_min)
+ * i.e. torque-limit hinges and the self-collision hinge on the worst pair
+ * (the constraint C_robot <= 0 of the paper's problem statement turned into
+ * a penalty); a kink takes the zero one-sided derivative.  tau, g_tau [d][B];
+ * d_min, cost, g_dmin [B]; tau_lo, tau_hi [d] device arrays (required with
+ * tau).  Any of tau / d_min may be NULL (its terms vanish); any output may be
+ * NULL.  Feed g_tau and g_dmin (with the forward's worst pair) to
+ * wb_eval_backward and the result to wb_bspline_backward for dL/dU.
+ * Errors: WB_EINVAL, WB_EDEVICE, WB_ECUDA. */
+int wb_trajopt_cost(int64_t B, int32_t d, const float* tau, const float* d_min,
+                    const float* tau_lo, const float* tau_hi, float w_coll, float* cost,
+                    float* g_tau, float* g_dmin, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Forward evaluation of an uneven batch without any device allocation.  The
  * paper has no counterpart to this entry point.
  *

@@ -94,6 +94,11 @@ SIGNATURES = {
     "wb_batch_eval_backward": (C.c_int, [p, p, p, p, p, p, p, p, p, p, p, p, p]),
     "wb_free_batch": (None, [p]),
     "wb_batch_eval_noalloc": (C.c_int, [p, C.c_int32, p, C.c_int32, p, p, p, p, p, p, p, p, p]),
+    "wb_bspline_eval": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_float, p, p, p,
+                                  p, p]),
+    "wb_bspline_backward": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_float, p,
+                                      p, p, p, p]),
+    "wb_trajopt_cost": (C.c_int, [C.c_int64, C.c_int32, p, p, p, p, C.c_float, p, p, p, p]),
 }
 
 _lib = None

@@ -1209,6 +1209,101 @@ int wb_batch_eval_backward(wb_batch* batch, const float* q, const float* qd, con
   return WB_OK;
 }
 
+// ---------------------------------------------------------------------------
+// trajectory-optimisation ends
+// ---------------------------------------------------------------------------
+// A device buffer of the call: NULL only when optional, 16-byte aligned,
+// device memory; the first one fixes the call's device (-1 = not yet known).
+static int check_buf(const void* p, const char* name, bool required, int* device) {
+  if (!p) return required ? fail(WB_EINVAL, "%s is NULL", name) : WB_OK;
+  if (reinterpret_cast<uintptr_t>(p) & 15u)
+    return fail(WB_EINVAL, "%s is not 16-byte aligned", name);
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(WB_EDEVICE, "%s: not a CUDA pointer", name);
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+    return fail(WB_EDEVICE, "%s is not device memory", name);
+  if (at.type == cudaMemoryTypeDevice) {
+    if (*device < 0) *device = at.device;
+    else if (at.device != *device)
+      return fail(WB_EDEVICE, "%s lives on device %d, other buffers on device %d", name,
+                  at.device, *device);
+  }
+  return WB_OK;
+}
+
+static int check_spline(int64_t n_traj, int32_t d, int32_t K, int32_t T, float dt) {
+  if (n_traj < 0 || d < 1 || d > WB_MAX_LINKS) return fail(WB_EINVAL, "bad n_traj or d");
+  if (K < 4 || K > 4096)
+    return fail(WB_EINVAL, "K = %d outside [4, 4096] (a cubic B-spline needs 4 control points)", K);
+  if (T < 2 || T > 4096) return fail(WB_EINVAL, "T = %d outside [2, 4096]", T);
+  if (!(dt > 0.0f) || !std::isfinite(dt)) return fail(WB_EINVAL, "dt must be positive");
+  if (n_traj * T * (int64_t)d > ((int64_t)1 << 40)) return fail(WB_EINVAL, "too many samples");
+  return WB_OK;
+}
+
+int wb_bspline_eval(int64_t n_traj, int32_t d, int32_t K, int32_t T, float dt, const float* U,
+                    float* q, float* qd, float* qdd, void* stream) {
+  g_err.clear();
+  int rc, dev = -1;
+  if ((rc = check_spline(n_traj, d, K, T, dt))) return rc;
+  if ((rc = check_buf(U, "U", n_traj > 0, &dev))) return rc;
+  if ((rc = check_buf(q, "q", false, &dev))) return rc;
+  if ((rc = check_buf(qd, "qd", false, &dev))) return rc;
+  if ((rc = check_buf(qdd, "qdd", false, &dev))) return rc;
+  if (n_traj == 0 || (!q && !qd && !qdd)) return WB_OK;
+  DeviceGuard guard(dev);
+  cudaError_t e = launch_bspline_fwd(n_traj, d, K, T, dt, U, q, qd, qdd,
+                                     static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "wb_bspline_eval launch");
+  return WB_OK;
+}
+
+int wb_bspline_backward(int64_t n_traj, int32_t d, int32_t K, int32_t T, float dt,
+                        const float* gq, const float* gqd, const float* gqdd, float* gU,
+                        void* stream) {
+  g_err.clear();
+  int rc, dev = -1;
+  if ((rc = check_spline(n_traj, d, K, T, dt))) return rc;
+  if ((rc = check_buf(gU, "gU", n_traj > 0, &dev))) return rc;
+  if ((rc = check_buf(gq, "gq", false, &dev))) return rc;
+  if ((rc = check_buf(gqd, "gqd", false, &dev))) return rc;
+  if ((rc = check_buf(gqdd, "gqdd", false, &dev))) return rc;
+  if (n_traj == 0) return WB_OK;
+  DeviceGuard guard(dev);
+  cudaError_t e = launch_bspline_bwd(n_traj, d, K, T, dt, gq, gqd, gqdd, gU,
+                                     static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "wb_bspline_backward launch");
+  return WB_OK;
+}
+
+int wb_trajopt_cost(int64_t B, int32_t d, const float* tau, const float* d_min,
+                    const float* tau_lo, const float* tau_hi, float w_coll, float* cost,
+                    float* g_tau, float* g_dmin, void* stream) {
+  g_err.clear();
+  int rc, dev = -1;
+  if (B < 0 || d < 0 || d > WB_MAX_LINKS) return fail(WB_EINVAL, "bad B or d");
+  if (B * (int64_t)std::max(d, 1) > ((int64_t)1 << 40)) return fail(WB_EINVAL, "B too large");
+  if (!std::isfinite(w_coll)) return fail(WB_EINVAL, "w_coll must be finite");
+  if ((rc = check_buf(tau, "tau", false, &dev))) return rc;
+  if ((rc = check_buf(d_min, "d_min", false, &dev))) return rc;
+  if ((rc = check_buf(tau_lo, "tau_lo", tau != nullptr, &dev))) return rc;
+  if ((rc = check_buf(tau_hi, "tau_hi", tau != nullptr, &dev))) return rc;
+  if ((rc = check_buf(cost, "cost", false, &dev))) return rc;
+  if ((rc = check_buf(g_tau, "g_tau", false, &dev))) return rc;
+  if ((rc = check_buf(g_dmin, "g_dmin", false, &dev))) return rc;
+  if (g_tau && !tau) return fail(WB_EINVAL, "g_tau without tau");
+  if (g_dmin && !d_min) return fail(WB_EINVAL, "g_dmin without d_min");
+  if (B == 0 || dev < 0) return WB_OK;
+  DeviceGuard guard(dev);
+  cudaError_t e = launch_trajopt_cost(B, d, tau, d_min, tau_lo, tau_hi, w_coll, cost, g_tau,
+                                      g_dmin, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "wb_trajopt_cost launch");
+  return WB_OK;
+}
+
 // The work tables of wb_batch_create, rebuilt per call in the library's static
 // scratch (k_noalloc.cu) instead of device memory allocated per batch.  The
 // host fills the setup kernel's launch parameters (NoAllocPlan, on this

@@ -283,6 +283,52 @@ class Batch:
                 "wb_batch_eval_backward")
 
 
+def bspline_eval(U, T: int, dt: float, q=None, qd=None, qdd=None, stream=None):
+    """Joint states [d][n_traj*T] from B-spline control points U
+    [n_traj][d][K] (wb_bspline_eval); allocates the outputs it is not given."""
+    lib = L.load()
+    n_traj, d, K = U.shape
+    B = n_traj * T
+    mk = lambda t: t if t is not None else torch.empty((d, B), device=U.device)  # noqa: E731
+    q, qd, qdd = mk(q), mk(qd), mk(qdd)
+    L.check(lib.wb_bspline_eval(n_traj, d, K, int(T), float(dt), _ptr(U), _ptr(q), _ptr(qd),
+                                _ptr(qdd), _stream(stream)), "wb_bspline_eval")
+    return q, qd, qdd
+
+
+def bspline_backward(gq, gqd, gqdd, n_traj: int, K: int, T: int, dt: float, gU=None,
+                     stream=None):
+    """Control-point gradient [n_traj][d][K] from upstream gradients on the
+    states (wb_bspline_backward; any of gq, gqd, gqdd may be None)."""
+    lib = L.load()
+    ref = next(t for t in (gq, gqd, gqdd) if t is not None)
+    d = ref.shape[0]
+    if gU is None:
+        gU = torch.empty((n_traj, d, K), device=ref.device)
+    L.check(lib.wb_bspline_backward(n_traj, d, K, int(T), float(dt), _ptr(gq), _ptr(gqd),
+                                    _ptr(gqdd), _ptr(gU), _stream(stream)),
+            "wb_bspline_backward")
+    return gU
+
+
+def trajopt_cost(tau, d_min, tau_lo, tau_hi, w_coll: float, cost=None, g_tau=None, g_dmin=None,
+                 stream=None):
+    """Per-configuration cost and upstream gradients (wb_trajopt_cost);
+    allocates the outputs it is not given.  Returns (cost, g_tau, g_dmin)."""
+    lib = L.load()
+    ref = tau if tau is not None else d_min
+    d, B = tau.shape if tau is not None else (0, d_min.shape[0])
+    cost = cost if cost is not None else torch.empty((B,), device=ref.device)
+    if g_tau is None and tau is not None:
+        g_tau = torch.empty((d, B), device=ref.device)
+    if g_dmin is None and d_min is not None:
+        g_dmin = torch.empty((B,), device=ref.device)
+    L.check(lib.wb_trajopt_cost(B, d, _ptr(tau), _ptr(d_min), _ptr(tau_lo), _ptr(tau_hi),
+                                float(w_coll), _ptr(cost), _ptr(g_tau), _ptr(g_dmin),
+                                _stream(stream)), "wb_trajopt_cost")
+    return cost, g_tau, g_dmin
+
+
 def batch_eval_noalloc(robots, problems, q, qd, qdd, pose, sphere=None, dmin=None, worst=None,
                        tau=None, stream=None):
     """wb_batch_eval_noalloc: forward evaluation of an uneven batch without any

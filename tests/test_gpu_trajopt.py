@@ -1,0 +1,175 @@
+"""GPU parity of the trajectory-optimisation ends: B-spline states and their
+control-point gradient, the per-configuration cost, and the whole chain
+U -> states -> whole-body evaluation -> cost -> dL/dU on the 48-DoF humanoid
+with 3 kg hand payloads, against the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+from synthetic import configs as CF
+from synthetic import inputs as I
+from synthetic import robots as R
+from tests import parity as PY
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def W():
+    assert torch.cuda.is_available()
+    from paper_2603_05493_gb300 import build
+    build()
+    from paper_2603_05493_gb300 import wbe
+    return wbe
+
+
+@pytest.fixture(scope="module")
+def O():
+    from oracle import oracle
+    oracle.build()
+    return oracle
+
+
+def cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+
+
+@pytest.mark.parametrize("n_traj,d,K,T,dt", [(5, 7, 16, 64, 0.25), (3, 5, 6, 9, 0.3),
+                                             (2, 3, 4, 2, 0.1), (1, 48, 40, 301, 0.05),
+                                             (0, 4, 8, 16, 0.25)])
+def test_bspline_forward_and_vjp(W, O, n_traj, d, K, T, dt):
+    rng = np.random.default_rng(K * 100 + T)
+    U = rng.uniform(-np.pi / 2, np.pi / 2, size=(n_traj, d, K)).astype(np.float32)
+    q, qd, qdd = W.bspline_eval(cuda(U), T, dt)
+    torch.cuda.synchronize()
+    if n_traj == 0:
+        return
+    ref = O.bspline(U.astype(np.float64), T, dt)
+    for got, r, order in zip((q, qd, qdd), ref, range(3)):
+        scale = np.pi / dt ** order
+        assert np.abs(got.cpu().numpy() - r).max() <= 2e-6 * scale
+    g = [rng.normal(size=(d, n_traj * T)).astype(np.float32) for _ in range(3)]
+    gU = W.bspline_backward(*[cuda(x) for x in g], n_traj, K, T, dt)
+    torch.cuda.synchronize()
+    Uref = O.bspline_vjp(*[x.astype(np.float64) for x in g], n_traj, K, T, dt)
+    got = gU.cpu().numpy()
+    for tr in range(n_traj):
+        for j in range(d):
+            e = np.abs(got[tr, j] - Uref[tr, j]).max()
+            assert e <= 1e-5 * max(1.0, np.abs(Uref[tr, j]).max()) * (1 + T / K), (tr, j, e)
+    # adjoint identity on the GPU's own results
+    lhs = sum(float((a.double() * cuda(b).double()).sum()) for a, b in zip((q, qd, qdd), g))
+    rhs = float((cuda(U).double() * gU.double()).sum())
+    assert abs(lhs - rhs) <= 1e-5 * (abs(lhs) + np.abs(got).sum())
+    # one upstream gradient alone
+    gq_only = W.bspline_backward(cuda(g[0]), None, None, n_traj, K, T, dt)
+    ref_q = O.bspline_vjp(g[0].astype(np.float64), None, None, n_traj, K, T, dt)
+    assert np.abs(gq_only.cpu().numpy() - ref_q).max() <= 1e-5 * max(1.0, np.abs(ref_q).max()) * T
+
+
+def test_bspline_backward_is_deterministic(W):
+    rng = np.random.default_rng(3)
+    n_traj, d, K, T = 64, 48, 16, 64
+    g = [cuda(rng.normal(size=(d, n_traj * T))) for _ in range(3)]
+    a = W.bspline_backward(*g, n_traj, K, T, 0.25)
+    b = W.bspline_backward(*g, n_traj, K, T, 0.25)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+def test_trajopt_cost_matches_oracle_on_the_same_inputs(W, O):
+    """Same float32 torques and distances on both sides: the hinge decisions
+    and gradients are identical, the cost agrees to float rounding."""
+    rng = np.random.default_rng(8)
+    d, B = 48, 1000
+    tau = rng.normal(scale=30.0, size=(d, B)).astype(np.float32)
+    tau[0, :5] = [30.0, -30.0, 30.000002, -30.000002, 0.0]  # on and just past the limits
+    dmin = rng.normal(scale=0.05, size=B).astype(np.float32)
+    dmin[:3] = [0.0, -0.0, 1e-9]
+    lo = np.full(d, -30.0, np.float32)
+    hi = np.full(d, 30.0, np.float32)
+    hi[3] = 25.0
+    cost, g_tau, g_dmin = W.trajopt_cost(cuda(tau), cuda(dmin), cuda(lo), cuda(hi), 2.5)
+    torch.cuda.synchronize()
+    rc, rg, rm = O.trajopt_cost(tau, dmin, lo, hi, 2.5)
+    assert np.array_equal(g_tau.cpu().numpy(), rg)
+    assert np.array_equal(g_dmin.cpu().numpy(), rm)
+    assert np.allclose(cost.cpu().numpy(), rc, rtol=2e-6, atol=1e-4)
+    # distances only / torques only
+    c2, _, gm2 = W.trajopt_cost(cuda(tau), None, cuda(lo), cuda(hi), 2.5)
+    c3, _, _ = W.trajopt_cost(cuda(tau[:, :0]), None, cuda(lo), cuda(hi), 2.5)
+    torch.cuda.synchronize()
+    assert np.allclose(c2.cpu().numpy(), O.trajopt_cost(tau, np.ones(B), lo, hi, 0.0)[0],
+                       rtol=2e-6, atol=1e-4)
+
+
+def _chain(W, rob, desc, U, T, dt, lo, hi, w):
+    """The GPU chain; returns (gU, cost, eval outputs)."""
+    n_traj, d, K = U.shape
+    q, qd, qdd = W.bspline_eval(U, T, dt)
+    o = rob.eval(q, qd, qdd)
+    cost, g_tau, g_dmin = W.trajopt_cost(o["tau"], o["dmin"], lo, hi, w)
+    gq, gqd, gqdd = rob.eval_backward(q, qd, qdd, o["worst"], None, None, g_dmin, g_tau)
+    gU = W.bspline_backward(gq, gqd, gqdd, n_traj, K, T, dt)
+    torch.cuda.synchronize()
+    return gU, cost, o
+
+
+def _compare_chain(O, desc, U, T, dt, lim, w, gU, cost, o, trajs):
+    d = desc.dof
+    lo, hi = -lim * np.ones(d), lim * np.ones(d)
+    Uref, cref, ev = O.trajopt_gradient(desc, U.astype(np.float64), T, dt, lo, hi, w)
+    tau, dmin, worst = ev["tau"], ev["dmin"], ev["worst"]
+    got_worst = o["worst"].cpu().numpy()
+    got_cost = cost.cpu().numpy()
+    gUn = gU.cpu().numpy()
+    kept = 0
+    for i, tr in enumerate(trajs):
+        sl = slice(i * T, (i + 1) * T)
+        gsl = slice(tr * T, (tr + 1) * T)
+        # torques agree to 1e-4 relative per joint, so the hinge sums do too
+        tol = 1e-4 * np.maximum(np.abs(tau[:, sl]), 1.0).sum(axis=0) + 1e-5
+        assert (np.abs(got_cost[gsl] - cref[sl]) <= tol).all()
+        near = (np.abs(np.abs(tau[:, sl]) - lim) < 1e-3).any() or \
+            (np.abs(dmin[sl]) < 1e-4).any() or not np.array_equal(got_worst[gsl], worst[sl])
+        if near:  # a hinge or the worst pair may switch between FP32 and FP64
+            continue
+        e = np.linalg.norm(gUn[tr] - Uref[i])
+        assert e <= PY.GRAD_REL * max(np.linalg.norm(Uref[i]), 1e-6), (tr, e)
+        kept += 1
+    return kept
+
+
+def test_trajopt_chain_matches_oracle(W, O):
+    """U -> B-spline -> FK + spheres + self-collision + RNEA -> cost ->
+    adjoint -> dL/dU, 48-DoF humanoid with 3 kg hand payloads, torque limits
+    +-30 N m, collision weight 1."""
+    desc = I.hand_payload(R.r48())
+    rob = W.Robot(desc, device=0)
+    n_traj, K, T, dt = 6, CF.TRAJOPT_KNOTS, CF.TRAJOPT_STEPS, CF.TRAJOPT_DT
+    U = I.bspline_controls(desc.dof, n_traj, K, seed=CF.TRAJOPT48.seed)
+    lim, w = CF.TORQUE_LIMIT, CF.COLLISION_WEIGHT
+    lo = cuda(-lim * np.ones(desc.dof))
+    hi = cuda(lim * np.ones(desc.dof))
+    gU, cost, o = _chain(W, rob, desc, cuda(U), T, dt, lo, hi, w)
+    tau = o["tau"].cpu().numpy()
+    assert (np.abs(tau) > lim).mean() > 0.01  # the torque hinge is active
+    kept = _compare_chain(O, desc, U, T, dt, lim, w, gU, cost, o, list(range(n_traj)))
+    assert kept >= n_traj - 2
+
+
+def test_trajopt48_full_size_sampled(W, O):
+    """The full 512 x 64 launch; three trajectories checked against the
+    oracle (each trajectory's dL/dU depends on its own samples only)."""
+    desc = I.hand_payload(R.r48())
+    rob = W.Robot(desc, device=0)
+    n_traj, K, T, dt = CF.TRAJOPT_SEEDS, CF.TRAJOPT_KNOTS, CF.TRAJOPT_STEPS, CF.TRAJOPT_DT
+    U = I.bspline_controls(desc.dof, n_traj, K, seed=CF.TRAJOPT48.seed)
+    lim, w = CF.TORQUE_LIMIT, CF.COLLISION_WEIGHT
+    lo = cuda(-lim * np.ones(desc.dof))
+    hi = cuda(lim * np.ones(desc.dof))
+    gU, cost, o = _chain(W, rob, desc, cuda(U), T, dt, lo, hi, w)
+    assert torch.isfinite(gU).all() and torch.isfinite(cost).all()
+    trajs = [0, 257, n_traj - 1]
+    kept = _compare_chain(O, desc, U[trajs], T, dt, lim, w, gU, cost, o, trajs)
+    assert kept >= 2
