@@ -365,7 +365,8 @@ def autotune_cached(robot: Robot, desc, B: int, path: str | None = None):
     import json
     import os
     path = path or os.path.join(os.path.expanduser("~"), ".cache", "wbe", "autotune.json")
-    key = "%s|%s|%d" % (descriptor_hash(desc), torch.cuda.get_device_name(robot.device), B)
+    key = "%s|%s|%d|%d" % (descriptor_hash(desc), torch.cuda.get_device_name(robot.device), B,
+                           L.load().wb_version())
     cache = {}
     if os.path.exists(path):
         with open(path) as f:
@@ -374,9 +375,9 @@ def autotune_cached(robot: Robot, desc, B: int, path: str | None = None):
         e = cache[key]
         return Tune(*e["fwd"]), Tune(*e["bwd"]), e["fwd_ms"], e["bwd_ms"]
     f, b, fm, bm = robot.autotune(B)
-    cache[key] = {"fwd": [f.kernel, f.lanes_per_config, f.configs_per_block, f.blocks_per_sm],
-                  "bwd": [b.kernel, b.lanes_per_config, b.configs_per_block, b.blocks_per_sm],
-                  "fwd_ms": fm, "bwd_ms": bm}
+    fields = lambda t: [t.kernel, t.lanes_per_config, t.configs_per_block,  # noqa: E731
+                        t.blocks_per_sm]
+    cache[key] = {"fwd": fields(f), "bwd": fields(b), "fwd_ms": fm, "bwd_ms": bm}
     os.makedirs(os.path.dirname(path), exist_ok=True)
     tmp = path + ".tmp%d" % os.getpid()
     with open(tmp, "w") as fh:
