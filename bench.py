@@ -88,6 +88,38 @@ def traffic_per_eval(name):
     return t["bytes_per_eval"]
 
 
+# ---------------------------------------------------------------------------
+# multi-rank host logic: one process per GPU, each evaluating its own batch
+# (weak scaling); no collective touches the data path, only the timing
+# ---------------------------------------------------------------------------
+def rank_seed(base, rank):
+    """Each rank draws its own inputs."""
+    return base + 101 * rank
+
+
+def reduce_max(values, world, device):
+    """Element-wise maximum over ranks (the slowest rank sets the time)."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_value(world, units_per_rank, ms):
+    """Whole-job throughput: the units every rank processed / the slowest
+    rank's time."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
 def fp32_peak_tflops(num_sms, mhz):
     """FP32 FMA peak: SMs x 128 lanes x 2 flops x clock."""
     return num_sms * 128 * 2 * mhz * 1e6 / 1e12
@@ -252,7 +284,7 @@ def run_ours(args, rank, world, local_rank):
         names = {"tree_fwd": "tree_fwd_seg_kernel" if seg(ft) > 1 else "tree_fwd_kernel",
                  "pair": "pair_kernel",
                  "tree_bwd": "tree_bwd_seg_kernel" if seg(bt) > 1 else "tree_bwd_kernel"}
-    seed = CF.HUMANOID48.seed + 101 * rank
+    seed = rank_seed(CF.HUMANOID48.seed, rank)
     q, qd, qdd = I.uniform_states(desc.dof, B, seed)
     gp, gs, gm, gt = I.upstream_grads(desc, B, seed + 1)
     h_in = [torch.from_numpy(x).pin_memory() for x in (q, qd, qdd, gp, gs, gm, gt)]
@@ -339,18 +371,15 @@ def run_ours(args, rank, world, local_rank):
               sum(x.numel() * x.element_size() for x in h_gout))
 
     kmean = {k: float(np.mean(v)) for k, v in k_ms.items()}
-    if world > 1:
-        t = torch.tensor([step_ms, e2e_ms] + [kmean[k] for k in ("tree_fwd", "pair", "tree_bwd")],
-                         device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        vals = [float(x) for x in t.tolist()]
-        step_ms, e2e_ms = vals[0], vals[1]
-        kmean = dict(zip(("tree_fwd", "pair", "tree_bwd"), vals[2:]))
+    keys = ("tree_fwd", "pair", "tree_bwd")
+    vals = reduce_max([step_ms, e2e_ms] + [kmean[k] for k in keys], world, dev)
+    step_ms, e2e_ms = vals[0], vals[1]
+    kmean = dict(zip(keys, vals[2:]))
     fwd_mean, bwd_mean = kmean["tree_fwd"] + kmean["pair"], kmean["tree_bwd"]
     if rank != 0:
         return
-    value = world * B / (step_ms * 1e-3)
-    e2e_value = world * B / (e2e_ms * 1e-3)
+    value = job_value(world, B, step_ms)
+    e2e_value = job_value(world, B, e2e_ms)
     work = work_per_eval(desc)
     peaks = measured_peaks()
     num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -444,7 +473,7 @@ def trajopt_work(desc, K, T):
     }
 
 
-def run_trajopt(args):
+def run_trajopt(args, rank=0, world=1, local_rank=0):
     """Trajectory-optimisation gradient step on the 48-DoF humanoid with 3 kg
     hand payloads: 512 seeds x 16 control points per joint -> 64 B-spline
     samples each (32768 configurations) -> FK + RNEA sweep -> self-collision
@@ -454,10 +483,10 @@ def run_trajopt(args):
     from paper_2603_05493_gb300 import build
     build()
     from paper_2603_05493_gb300 import wbe
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     desc = I.hand_payload(R.r48())
-    rob = wbe.Robot(desc, device=0)
+    rob = wbe.Robot(desc, device=local_rank)
     n_traj, K, T, dt = CF.TRAJOPT_SEEDS, CF.TRAJOPT_KNOTS, CF.TRAJOPT_STEPS, CF.TRAJOPT_DT
     B, d = n_traj * T, desc.dof
     ft, bt, _, _ = rob.autotune(B)
@@ -467,7 +496,8 @@ def run_trajopt(args):
                      configs_per_block=tpb(ft))
     btune = wbe.Tune(kernel=wbe.L.WB_KERNEL_TREE, lanes_per_config=seg(bt),
                      configs_per_block=tpb(bt))
-    hU = torch.from_numpy(I.bspline_controls(d, n_traj, K, seed=CF.TRAJOPT48.seed)).pin_memory()
+    hU = torch.from_numpy(I.bspline_controls(d, n_traj, K, seed=rank_seed(CF.TRAJOPT48.seed, rank)))
+    hU = hU.pin_memory()
     U = hU.to(dev)
     lo = torch.full((d,), -CF.TORQUE_LIMIT, device=dev)
     hi = torch.full((d,), CF.TORQUE_LIMIT, device=dev)
@@ -504,7 +534,8 @@ def run_trajopt(args):
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
-    clocks = ClockSampler(0)
+    barrier(world)
+    clocks = ClockSampler(local_rank)
     clocks.start()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
     torch.cuda.nvtx.range_push("timed")
@@ -515,6 +546,7 @@ def run_trajopt(args):
         evs[i][6].record(stream)
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
+    barrier(world)
     step_ms = float(np.mean([e[0].elapsed_time(e[6]) for e in evs]))
     k_ms = {nm: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in evs]))
             for i, nm in enumerate(names)}
@@ -534,6 +566,11 @@ def run_trajopt(args):
     torch.cuda.synchronize()
     clocks.stop()
     e2e_ms = t0.elapsed_time(t1) / e2e_steps
+    vals = reduce_max([step_ms, e2e_ms] + [k_ms[nm] for nm in names], world, dev)
+    step_ms, e2e_ms = vals[0], vals[1]
+    k_ms = dict(zip(names, vals[2:]))
+    if rank != 0:
+        return
     work = trajopt_work(desc, K, T)
     peaks = measured_peaks()
     num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -562,7 +599,8 @@ def run_trajopt(args):
     line = {
         "metric": "trajopt48 evals/s (B-spline -> FK+self-coll+RNEA -> hinge cost -> "
                   "adjoint -> dL/dU)",
-        "value": B / (step_ms * 1e-3), "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
+        "value": job_value(world, B, step_ms), "unit": "evals/s", "n_gpus": world,
+        "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "trajopt48: 48-DoF tree + 3 kg hand payloads, 512 seeds x 64 "
@@ -576,16 +614,16 @@ def run_trajopt(args):
         "kernels": kernels,
         "active_torque_hinges": float((out["tau"].abs() > CF.TORQUE_LIMIT).float().mean()),
         "penetrating_configurations": float((out["dmin"] < 0).float().mean()),
-        "e2e": {"value": B / (e2e_ms * 1e-3), "unit": "evals/s",
-                "h2d_bytes_per_step": int(hU.numel() * 4),
-                "d2h_bytes_per_step": int(hgU.numel() * 4 + hcost.numel() * 4)},
-        "gpu_launches": 6 * args.steps,
+        "e2e": {"value": job_value(world, B, e2e_ms), "unit": "evals/s",
+                "h2d_bytes_per_step": world * int(hU.numel() * 4),
+                "d2h_bytes_per_step": world * int(hgU.numel() * 4 + hcost.numel() * 4)},
+        "gpu_launches": 6 * args.steps * world,
         "clocks": clocks.summary(),
     }
     print(json.dumps(line), flush=True)
 
 
-def run_uneven(args):
+def run_uneven(args, rank=0, world=1, local_rank=0):
     """Uneven batch: 256 x R7 + 256 x R23 + 256 x R48 problems with horizons
     U{16..64}, forward (FK + RNEA, spheres + self-collision) and backward in
     one persistent launch per pass, captured once in a CUDA graph and
@@ -594,10 +632,10 @@ def run_uneven(args):
     from paper_2603_05493_gb300 import build
     build()
     from paper_2603_05493_gb300 import wbe
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    mix = I.uneven_mix()
-    robs = [wbe.Robot(d, device=0) for d in mix.robots]
+    mix = I.uneven_mix()  # the same problem mix on every rank; states differ
+    robs = [wbe.Robot(d, device=local_rank) for d in mix.robots]
     problems = list(zip(mix.robot_of.tolist(), mix.horizon.tolist()))
     batch = wbe.Batch(robs, problems)
     total = int(mix.horizon.sum())
@@ -605,7 +643,7 @@ def run_uneven(args):
     def packed(kind, make, dtype=torch.float32):
         out = batch.empty(kind, dtype)
         for p, (ri, H) in enumerate(problems):
-            x = make(mix.robots[ri], H, 7000 + p)
+            x = make(mix.robots[ri], H, 7000 + p + 100000 * rank)
             o = int(batch.offsets[kind][p])
             t = torch.from_numpy(np.ascontiguousarray(x)).reshape(-1).to(dev)
             out[o:o + t.numel()] = t
@@ -638,7 +676,8 @@ def run_uneven(args):
     for _ in range(max(args.warmup, 3)):
         graph.replay()
     torch.cuda.synchronize()
-    clocks = ClockSampler(0)
+    barrier(world)
+    clocks = ClockSampler(local_rank)
     clocks.start()
     ts = []
     torch.cuda.nvtx.range_push("timed")
@@ -652,7 +691,10 @@ def run_uneven(args):
         ts.append(a.elapsed_time(b))
     torch.cuda.nvtx.range_pop()
     clocks.stop()
-    ms = float(np.mean(ts))
+    barrier(world)
+    ms = reduce_max([float(np.mean(ts))], world, dev)[0]
+    if rank != 0:
+        return
     tunes = {}
     for d, rob in zip(mix.robots, robs):
         f, bw, fm, bm = rob.autotune(2048)
@@ -660,13 +702,14 @@ def run_uneven(args):
                          "bwd_ms_2048": bm}
     print(json.dumps({
         "metric": "uneven-batch evals/s (R7/R23/R48 problems, fwd+bwd, one graph)",
-        "value": total / (ms * 1e-3), "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
+        "value": job_value(world, total, ms), "unit": "evals/s", "n_gpus": world,
+        "steps": args.steps, "scaling": "weak",
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": "uneven: 256 x R7 + 256 x R23 + 256 x R48, horizons U{16..64}",
                    "configurations": total, "problems": len(problems),
                    "l2": "flushed between timed steps"},
-        "gpu_launches": 3 * args.steps, "clocks": clocks.summary(),
+        "gpu_launches": 3 * args.steps * world, "clocks": clocks.summary(),
         "autotune_single_robot_b2048": tunes}), flush=True)
 
 
@@ -691,19 +734,14 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    if args.workload == "uneven":
-        run_uneven(args)
-        return
-    if args.workload == "trajopt48":
-        run_trajopt(args)
-        return
     if world > 1:
         import torch
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     try:
-        run_ours(args, rank, world, local_rank)
+        run = {"humanoid48": run_ours, "uneven": run_uneven, "trajopt48": run_trajopt}
+        run[args.workload](args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch.distributed as dist

@@ -1,0 +1,62 @@
+"""The multi-rank host logic of bench.py on CPU: two gloo ranks on
+127.0.0.1, each with its own batch (weak scaling).  The slowest rank's time
+sets the step, the whole-job value counts every rank's configurations, and
+the ranks draw different inputs.  No GPU, no collective on the data path."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import bench
+        from synthetic import configs as CF
+        from synthetic import inputs as I
+        from synthetic import robots as R
+        seed = bench.rank_seed(CF.HUMANOID48.seed, rank)
+        q, _, _ = I.uniform_states(R.r7().dof, 16, seed)
+        # rank r takes (r + 1) ms per step and 2 (r + 1) ms end to end
+        step, e2e = bench.reduce_max([1.0 + rank, 2.0 * (1 + rank)], world, "cpu")
+        bench.barrier(world)
+        out.put((rank, seed, q.sum(), step, e2e, bench.job_value(world, 32768, step)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_weak_scaling():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(out.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (_, s0, q0, st0, e0, v0), (_, s1, q1, st1, e1, v1) = res
+    assert s0 != s1 and q0 != q1             # each rank evaluates its own configurations
+    assert st0 == st1 == 2.0                 # max over ranks
+    assert e0 == e1 == 4.0
+    assert v0 == v1 == pytest.approx(2 * 32768 / 2e-3)   # all ranks' work / slowest time
+
+
+def test_single_rank_needs_no_process_group():
+    import bench
+    assert bench.reduce_max([3.0, 1.5], 1, "cpu") == [3.0, 1.5]
+    assert bench.job_value(1, 1000, 2.0) == pytest.approx(5e5)
+    assert bench.rank_seed(7, 0) == 7
+    assert len({bench.rank_seed(7, r) for r in range(8)}) == 8
+    assert np.isfinite(bench.job_value(8, 32768, 0.8))
