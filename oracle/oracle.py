@@ -219,6 +219,33 @@ def trajopt_cost(tau, dmin, tau_lo, tau_hi, w_coll):
     return cost, g_tau, g_dmin
 
 
+def pair_hinge(robot, q, eta: float, w: float):
+    """All-pairs summed self-collision hinge with activation distance eta:
+        cost_b = w sum_p max(0, eta - d_p),  d_p = |c_i - c_j| - r_i - r_j
+    over every masked pair p = (i, j), and its gradient with respect to the
+    sphere centres: a pair with d_p < eta adds -w u to dcost/dc_i and +w u to
+    dcost/dc_j, u = (c_i - c_j) / |c_i - c_j| (a pair exactly at eta, or with
+    coincident centres, adds nothing).  q [d][B].  Returns cost [B] and
+    g_sph [B][S][3] in float64."""
+    r = robot
+    c = evaluate(r, q, want=("sph",))["sph"]            # [B][S][3]
+    P = np.asarray(r.pairs, dtype=np.int64).reshape(-1, 2)
+    rad = np.asarray(r.sph_r, dtype=np.float64)
+    diff = c[:, P[:, 0]] - c[:, P[:, 1]]                  # [B][P][3]
+    nrm = np.sqrt((diff * diff).sum(axis=2))
+    d = nrm - rad[P[:, 0]] - rad[P[:, 1]]
+    act = d < eta
+    cost = w * np.where(act, eta - d, 0.0).sum(axis=1)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        u = np.where(nrm[..., None] > 0, diff / nrm[..., None], 0.0)
+    gu = w * u * act[..., None]
+    g = np.zeros_like(c)
+    for k in range(P.shape[0]):  # plain accumulation, pair by pair
+        g[:, P[k, 0]] -= gu[:, k]
+        g[:, P[k, 1]] += gu[:, k]
+    return cost, g
+
+
 def trajopt_value(robot, U, T: int, dt: float, tau_lo, tau_hi, w_coll):
     """Total cost L(U) = sum_b cost_b over every sample of every trajectory:
     B-spline states -> whole-body evaluation -> cost."""

@@ -545,3 +545,50 @@ def test_trajopt_chain_gradient_matches_finite_differences(oracle_lib):
         assert abs(fd - Ub[idx]) <= 1e-6 * max(1.0, abs(Ub[idx])), (idx, fd, Ub[idx])
         checked += 1
     assert checked >= 8
+
+
+def test_pair_hinge_hand_built(oracle_lib):
+    """Three slider spheres (centres (q_k, 0, 0)): every pair closer than the
+    activation distance adds w (eta - d); the gradient pushes each sphere of
+    an active pair away from its partner with weight w; since each slider
+    moves its sphere along x, the joint gradient is the x component."""
+    O = oracle_lib
+    rob = _slider_robot([0.25, 0.125, 0.5])
+    q = np.array([[0.0], [0.375], [0.5]])
+    eta, w = 0.1, 2.0
+    # d01 = 0.375 - 0.375 = 0, d02 = 0.5 - 0.75 = -0.25, d12 = 0.125 - 0.625 = -0.5
+    cost, g = O.pair_hinge(rob, q, eta, w)
+    assert cost[0] == pytest.approx(w * (0.1 + 0.35 + 0.6), abs=1e-15)
+    # sphere 0 is left of both partners, sphere 2 right of both, sphere 1 between
+    assert np.allclose(g[0, :, 0], [w * 2, w * (-1 + 1), -w * 2], atol=1e-15)
+    assert np.allclose(g[0, :, 1:], 0.0)
+    gq, _, _ = O.gradient(rob, q, np.zeros_like(q), np.zeros_like(q), g_sph=g)
+    assert np.allclose(gq[:, 0], g[0, :, 0], atol=1e-14)
+    # move sphere 2 far away: only pair (0, 1) stays active; at d = eta exactly
+    # nothing is added
+    cost, g = O.pair_hinge(rob, np.array([[0.0], [0.375], [5.0]]), eta, w)
+    assert cost[0] == pytest.approx(w * 0.1) and np.allclose(g[0, 2], 0.0)
+    cost, g = O.pair_hinge(rob, np.array([[0.0], [0.5], [5.0]]), 0.125, w)  # d01 = 0.125 exactly
+    assert cost[0] == 0.0 and np.allclose(g, 0.0)
+
+
+def test_pair_hinge_gradient_matches_finite_differences(oracle_lib):
+    """d(cost)/dq through the sphere gradient and the whole-body VJP equals
+    central differences of the summed hinge on the 7-DoF chain, at
+    configurations where no pair crosses the activation distance within the
+    step."""
+    O = oracle_lib
+    rob = R.r7()
+    rng = np.random.default_rng(12)
+    q = rng.uniform(-np.pi, np.pi, size=(rob.dof, 6))
+    eta, w, h = 0.05, 1.7, 1e-6
+    cost, g = O.pair_hinge(rob, q, eta, w)
+    assert (cost > 0).all()
+    gq, _, _ = O.gradient(rob, q, np.zeros_like(q), np.zeros_like(q), g_sph=g)
+    fd = np.zeros_like(q)
+    for j in range(rob.dof):
+        qp, qm = q.copy(), q.copy()
+        qp[j] += h
+        qm[j] -= h
+        fd[j] = (O.pair_hinge(rob, qp, eta, w)[0] - O.pair_hinge(rob, qm, eta, w)[0]) / (2 * h)
+    assert np.allclose(gq, fd, rtol=1e-6, atol=1e-6)
