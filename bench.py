@@ -470,6 +470,8 @@ def trajopt_work(desc, K, T):
         "tree_bwd": {"flops": 150 * nm + 330 * n + 660 * n + 60 * n,
                      "bytes": 4 * (3 * d + 2 + d + 3 * d)},
         "bspline_bwd": {"flops": 24 * d, "bytes": 4 * 3 * d + 4 * d * K // T},
+        # summed hinge: every pair screened from both spheres (sqrt-free, 8 flops)
+        "hinge": {"flops": 18 * S + 16 * P, "bytes": 4 * (12 * n + 3 * S + 1)},
     }
 
 
@@ -512,7 +514,11 @@ def run_trajopt(args, rank=0, world=1, local_rank=0):
     gout = tuple(torch.empty((d, B), device=dev) for _ in range(3))
     gU = torch.empty((n_traj, d, K), device=dev)
     stream = torch.cuda.current_stream()
-    names = ["bspline_fwd", "tree_fwd", "pair", "cost", "tree_bwd", "bspline_bwd"]
+    hinge = args.collision == "hinge"
+    names = ["bspline_fwd", "tree_fwd", "hinge" if hinge else "pair", "cost", "tree_bwd",
+             "bspline_bwd"]
+    hinge_cost = torch.empty((B,), device=dev)
+    g_sph = torch.empty((B, desc.S, 3), device=dev) if hinge else None
 
     def step(ev=None):
         mark = (lambda i: ev[i].record(stream)) if ev else (lambda i: None)
@@ -520,13 +526,20 @@ def run_trajopt(args, rank=0, world=1, local_rank=0):
         mark(1)
         rob.eval(q, qd, qdd, tune=ftune, out=fwd_out, dmin=False, sphere=False)
         mark(2)
-        rob.self_collision(out["pose"], out=pair_out)
+        if hinge:  # every pair within the activation distance
+            rob.self_collision_hinge(out["pose"], CF.ACTIVATION_DISTANCE, CF.COLLISION_WEIGHT,
+                                     cost=hinge_cost, g_sphere=g_sph)
+        else:  # the worst pair
+            rob.self_collision(out["pose"], out=pair_out)
         mark(3)
-        wbe.trajopt_cost(out["tau"], out["dmin"], lo, hi, CF.COLLISION_WEIGHT, cost, g_tau,
-                         g_dmin)
+        wbe.trajopt_cost(out["tau"], None if hinge else out["dmin"], lo, hi,
+                         CF.COLLISION_WEIGHT, cost, g_tau, None if hinge else g_dmin)
         mark(4)
-        rob.eval_backward(q, qd, qdd, out["worst"], None, None, g_dmin, g_tau, tune=btune,
-                          out=gout)
+        if hinge:
+            rob.eval_backward(q, qd, qdd, None, None, g_sph, None, g_tau, tune=btune, out=gout)
+        else:
+            rob.eval_backward(q, qd, qdd, out["worst"], None, None, g_dmin, g_tau, tune=btune,
+                              out=gout)
         mark(5)
         wbe.bspline_backward(*gout, n_traj, K, T, dt, gU)
 
@@ -578,7 +591,7 @@ def run_trajopt(args, rank=0, world=1, local_rank=0):
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     ridge = alu_peak * 1e12 / (hbm_peak * 1e9)
     kernels = {}
-    kn = {"bspline_fwd": "bspline_fwd_kernel", "pair": "pair_kernel",
+    kn = {"bspline_fwd": "bspline_fwd_kernel", "pair": "pair_kernel", "hinge": "hinge_kernel",
           "tree_fwd": "tree_fwd_seg_kernel" if seg(ft) > 1 else "tree_fwd_kernel",
           "cost": "trajopt_cost_kernel",
           "tree_bwd": "tree_bwd_seg_kernel" if seg(bt) > 1 else "tree_bwd_kernel",
@@ -605,7 +618,9 @@ def run_trajopt(args, rank=0, world=1, local_rank=0):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "trajopt48: 48-DoF tree + 3 kg hand payloads, 512 seeds x 64 "
                                "B-spline samples (16 control points / joint, dt 0.25 s), "
-                               "torque limits +-30 N m, collision weight 1",
+                               "torque limits +-30 N m, collision weight 1, " +
+                               ("summed hinge over all pairs, activation distance %.3g m"
+                                % CF.ACTIVATION_DISTANCE if hinge else "worst-pair hinge"),
                    "configurations": B,
                    "autotuned": {"fwd": dict(ft.__dict__), "bwd": dict(bt.__dict__)},
                    "l2": "flushed between timed steps (512 MB write outside the events)"},
@@ -613,7 +628,7 @@ def run_trajopt(args, rank=0, world=1, local_rank=0):
                          ("bound", "achieved", "peak", "unit", "frac", "traffic")}),
         "kernels": kernels,
         "active_torque_hinges": float((out["tau"].abs() > CF.TORQUE_LIMIT).float().mean()),
-        "penetrating_configurations": float((out["dmin"] < 0).float().mean()),
+        "penetrating_configurations": None if hinge else float((out["dmin"] < 0).float().mean()),
         "e2e": {"value": job_value(world, B, e2e_ms), "unit": "evals/s",
                 "h2d_bytes_per_step": world * int(hU.numel() * 4),
                 "d2h_bytes_per_step": world * int(hgU.numel() * 4 + hcost.numel() * 4)},
@@ -727,6 +742,8 @@ def main():
     ap.add_argument("--ref-step-s", type=float, default=10.0)
     ap.add_argument("--workload", choices=["humanoid48", "uneven", "trajopt48"],
                     default="humanoid48")
+    ap.add_argument("--collision", choices=["worst", "hinge"], default="worst",
+                    help="trajopt48 collision cost: worst-pair hinge or summed hinge")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -204,6 +204,20 @@ int wb_eval(wb_robot* robot, int64_t B, const float* q, const float* qd, const f
 int wb_self_collision(wb_robot* robot, int64_t B, const float* link_pose, float* sphere,
                       float* d_min, int32_t* worst_pair, uint32_t* pair_bits, void* stream);
 
+/* All-pairs summed self-collision hinge with activation distance eta (the
+ * constraint C_robot <= 0 of the paper's problem statement with a margin, as
+ * a penalty over every masked pair rather than the worst one):
+ *   cost[b] = w * sum_p max(0, eta - d_p),  d_p = |c_i - c_j| - r_i - r_j
+ * and, in g_sphere [B][S][3], its gradient with respect to the sphere centres
+ * (a pair with d_p < eta adds -w u at sphere i and +w u at sphere j,
+ * u = (c_i - c_j) / |c_i - c_j|; coincident centres add nothing).  Pass
+ * g_sphere to wb_eval_backward as its sphere gradient for dcost/dq.  Spheres
+ * are placed from link_pose [B][n][12] (from wb_eval).  cost [B] and g_sphere
+ * are each nullable.  Deterministic (no atomics).  A pair exactly at eta adds
+ * nothing.  Errors: WB_EINVAL, WB_EDEVICE, WB_ETOOBIG, WB_ECUDA. */
+int wb_self_collision_hinge(wb_robot* robot, int64_t B, const float* link_pose, float eta,
+                            float w, float* cost, float* g_sphere, void* stream);
+
 /* Backward pass: the gradient of
  *   L = <g_pose, link_pose> + <g_sphere, sphere> + sum_b g_dmin[b] d_min[b]
  *       + <g_tau, tau>

@@ -209,6 +209,8 @@ struct HostPlan {
   std::vector<float> axis, Tf, mimic, inert;
   std::vector<float4> sp, grp_rad;
   std::vector<int2> pairs_dev;
+  std::vector<int32_t> adj_start;
+  std::vector<int16_t> adj;
   std::vector<uint32_t> bx;
   std::vector<int32_t> blk_pidx;
   std::vector<int4> lvm;
@@ -424,6 +426,24 @@ static int plan_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs
   const int P = (int)pl.size();
   std::vector<int2> pairs_dev(std::max(P, 1), int2{0, 0});
   for (int p = 0; p < P; ++p) pairs_dev[p] = int2{pl[p].first, pl[p].second};
+  {  // adjacency: partners of every sphere, ascending
+    std::vector<std::vector<int16_t>> nb(S);
+    for (int p = 0; p < P; ++p) {
+      nb[pl[p].first].push_back((int16_t)pl[p].second);
+      nb[pl[p].second].push_back((int16_t)pl[p].first);
+    }
+    // each list padded to a multiple of 4 with the sentinel S (a sphere the
+    // hinge kernel places far away), so partners load four at a time
+    H.adj_start.assign(S + 1, 0);
+    for (int s2 = 0; s2 < S; ++s2) {
+      std::sort(nb[s2].begin(), nb[s2].end());
+      H.adj_start[s2] = (int32_t)H.adj.size();
+      H.adj.insert(H.adj.end(), nb[s2].begin(), nb[s2].end());
+      while (H.adj.size() % 4) H.adj.push_back((int16_t)S);
+    }
+    H.adj_start[S] = (int32_t)H.adj.size();
+    while (H.adj.size() < 4) H.adj.push_back((int16_t)S);
+  }
 
   // ---- 4x4 group blocks ----
   const int Sg = std::max((S + 3) / 4, 1);
@@ -650,6 +670,8 @@ int wb_load_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs* pa
   pk.add_vec(H.sp, &D.sph);
   pk.add_vec(H.sph_link, &D.sph_link);
   pk.add_vec(H.pairs_dev, &D.pairs);
+  pk.add_vec(H.adj_start, &D.adj_start);
+  pk.add_vec(H.adj, &D.adj);
   pk.add_vec(H.grp_rad, &D.grp_rad);
   pk.add_vec(H.blk_pidx, &D.blk_pidx);
   std::vector<uint2> ents[4];
@@ -931,6 +953,31 @@ int wb_self_collision(wb_robot* robot, int64_t B, const float* link_pose, float*
   const int grid = (int)std::min<int64_t>(need, (int64_t)bps * robot->num_sms);
   e = launch_pair(robot->dev, robot->sched32, a, grid, warps, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "wb_self_collision launch");
+  return WB_OK;
+}
+
+int wb_self_collision_hinge(wb_robot* robot, int64_t B, const float* link_pose, float eta,
+                            float w, float* cost, float* g_sphere, void* stream) {
+  g_err.clear();
+  if (!robot) return fail(WB_EINVAL, "robot is NULL");
+  if (B < 0) return fail(WB_EINVAL, "B < 0");
+  if (!std::isfinite(eta) || !std::isfinite(w)) return fail(WB_EINVAL, "eta and w must be finite");
+  if (B == 0 || (!cost && !g_sphere)) return WB_OK;
+  int rc;
+  if ((rc = check_ptr(robot, link_pose, "link_pose", true))) return rc;
+  if ((rc = check_ptr(robot, cost, "cost", false))) return rc;
+  if ((rc = check_ptr(robot, g_sphere, "g_sphere", false))) return rc;
+  DeviceGuard guard(robot->device);
+  const int warps = 8;
+  int bps = 0;
+  cudaError_t e = hinge_max_blocks_per_sm(robot->dev, warps, &bps);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+  if (bps < 1) return fail(WB_ETOOBIG, "hinge kernel does not fit on an SM");
+  const int64_t need = (B + warps - 1) / warps;
+  const int grid = (int)std::min<int64_t>(need, (int64_t)bps * robot->num_sms);
+  HingeArgs a{B, link_pose, eta, w, cost, g_sphere};
+  e = launch_hinge(robot->dev, a, grid, warps, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "wb_self_collision_hinge launch");
   return WB_OK;
 }
 

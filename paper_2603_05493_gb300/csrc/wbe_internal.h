@@ -64,6 +64,11 @@ struct DevRobot {
   const int2* pairs;         // [P] sorted row-major
   const float4* grp_rad;     // [Sg] radii of the 4 spheres of a group (0 pad)
   const int32_t* blk_pidx;   // [nblk][16] pair index of (4gi+a, 4gj+b) or -1
+  // sphere adjacency of the masked pairs (each pair listed at both spheres,
+  // partners ascending, each list padded to a multiple of 4 with S): the
+  // summed collision hinge walks it per sphere
+  const int32_t* adj_start;  // [S+1], multiples of 4
+  const int16_t* adj;
 };
 
 // A per-lane schedule of pair blocks for the fused kernel with G lanes per
@@ -190,6 +195,19 @@ cudaError_t batch_tree_max_blocks_per_sm(bool fwd, int* out);
 int pair_plan_words(const DevRobot& r);
 
 // launchers (return cudaGetLastError())
+// all-pairs summed collision hinge (k_hinge.cu)
+struct HingeArgs {
+  int64_t B;
+  const float* pose;  // [B][n][12]
+  float eta, w;       // activation distance, weight
+  float* cost;        // [B] or nullptr
+  float* g_sph;       // [B][S][3] or nullptr
+};
+size_t hinge_smem_per_warp(const DevRobot& r);
+cudaError_t launch_hinge(const DevRobot& r, const HingeArgs& a, int grid, int warps,
+                         cudaStream_t s);
+cudaError_t hinge_max_blocks_per_sm(const DevRobot& r, int warps, int* out);
+
 // trajectory-optimisation ends (k_traj.cu)
 cudaError_t launch_bspline_fwd(int64_t n_traj, int d, int K, int T, float dt, const float* U,
                                float* q, float* qd, float* qdd, cudaStream_t s);

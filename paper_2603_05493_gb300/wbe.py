@@ -200,6 +200,22 @@ class Robot:
                 "wb_self_collision")
         return o
 
+    def self_collision_hinge(self, link_pose, eta: float, w: float = 1.0, *, cost=None,
+                             g_sphere=None, want_grad=True, stream=None):
+        """All-pairs summed collision hinge w * sum max(0, eta - d) per
+        configuration and its sphere-centre gradient (wb_self_collision_hinge);
+        returns (cost [B], g_sphere [B][S][3] or None)."""
+        B = link_pose.shape[0]
+        f = dict(device=link_pose.device, dtype=torch.float32)
+        cost = cost if cost is not None else torch.empty((B,), **f)
+        if g_sphere is None and want_grad:
+            g_sphere = torch.empty((B, self.S, 3), **f)
+        L.check(self.lib.wb_self_collision_hinge(self.handle, B, _ptr(link_pose), float(eta),
+                                                 float(w), _ptr(cost), _ptr(g_sphere),
+                                                 _stream(stream)),
+                "wb_self_collision_hinge")
+        return cost, g_sphere
+
     def eval_backward(self, q, qd, qdd, worst=None, g_pose=None, g_sphere=None, g_dmin=None,
                       g_tau=None, *, tune: Tune | None = None, out=None, stream=None):
         """Gradient of <g_pose,pose> + <g_sphere,sphere> + g_dmin.d_min +

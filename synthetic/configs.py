@@ -31,3 +31,4 @@ TRAJOPT_KNOTS = 16
 TRAJOPT_DT = 0.25
 TORQUE_LIMIT = 30.0
 COLLISION_WEIGHT = 1.0
+ACTIVATION_DISTANCE = 0.02  # m, summed collision hinge of the trajopt48 variant

@@ -75,3 +75,10 @@ def check_gradient(got, ref, mask=None):
         nrm = np.maximum(np.linalg.norm(r, axis=0), 1e-6)
         worst = (err / nrm).max() if err.size else 0.0
         assert worst <= GRAD_REL, "grad %s rel error %g" % (name, worst)
+
+
+def stable_seed(*parts) -> int:
+    """A seed in [0, 1000) from test parameters, the same in every process
+    (Python's str hash is salted per process)."""
+    import zlib
+    return zlib.crc32(repr(parts).encode()) % 1000
