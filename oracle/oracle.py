@@ -56,6 +56,8 @@ def lib():
         _lib.or_bspline.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, p, p, p, p]
         _lib.or_bspline_vjp.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, p, p, p,
                                         p]
+        _lib.or_kinematics.argtypes = [C.POINTER(_Robot), C.c_int, p, C.c_int, p, p, p, p,
+                                       C.c_int]
     return _lib
 
 
@@ -217,6 +219,27 @@ def trajopt_cost(tau, dmin, tau_lo, tau_hi, w_coll):
     g_tau = (tau > hi).astype(np.float64) - (tau < lo).astype(np.float64)
     g_dmin = -w_coll * (dmin < 0).astype(np.float64)
     return cost, g_tau, g_dmin
+
+
+def kinematics(robot, q, targets, nthreads: int = 0):
+    """Jacobians of the target links and the centre of mass by dual-number
+    differentiation of the forward kinematics.  q [d][B].  Returns
+    J [B][nt][6][d] (rows: world origin velocity, then angular velocity),
+    com [B][3], Jcom [B][3][d]."""
+    orob = robot if isinstance(robot, OracleRobot) else OracleRobot(robot)
+    r = orob.robot
+    d = r.dof
+    qc = _cm(q, d)
+    B = qc.shape[0]
+    tg = np.ascontiguousarray(targets, dtype=np.int32)
+    J = np.zeros((B, len(tg), 6, d))
+    com = np.zeros((B, 3))
+    Jc = np.zeros((B, 3, d))
+    rc = lib().or_kinematics(C.byref(orob.s), B, _ptr(qc), len(tg), _ptr(tg), _ptr(J), _ptr(com),
+                             _ptr(Jc), nthreads)
+    if rc != 0:
+        raise ValueError("or_kinematics: target out of range")
+    return J, com, Jc
 
 
 def pair_hinge(robot, q, eta: float, w: float):

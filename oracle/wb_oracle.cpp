@@ -22,7 +22,9 @@
 //      selected worst pair.
 //   6. the uniform cubic B-spline of Sec. 4 (Eq. bspline-cubic), used to make
 //      joint trajectories from control points, and its vector-Jacobian
-//      product with respect to the control points (Eq. backward_grad).
+//      product with respect to the control points (Eq. backward_grad);
+//   7. kinematic Jacobians of chosen links and the whole-body centre of mass
+//      with its Jacobian, by dual-number differentiation of step 1.
 //
 // Readings where the paper is silent: gravity enters as a fictitious base
 // acceleration a_base = [0; -g]; a fixed joint has an empty motion subspace;
@@ -603,6 +605,75 @@ int or_bspline(int n_traj, int d, int K, int T, double dt, const double* U, doub
         qdd[b * d + j] = out[2];
       }
     }
+  return 0;
+}
+
+// Kinematic Jacobians and the centre of mass (Sec. 6.1.1 "centers of mass,
+// and Jacobians"; Alg. 2 gives their column structure), by forward-mode
+// differentiation of the forward kinematics: one dual pass per joint j seeds
+// dq_j = 1.  For target link e, column j of J [B][nt][6][d] holds the
+// derivative of e's world origin (rows 0-2) and the angular velocity of its
+// frame, vee(dR_e/dq_j R_e^T) (rows 3-5).  com [B][3] is the mass-weighted mean
+// of the link centres of mass and the payload point masses; Jcom [B][3][d] its
+// derivative.  Each output may be NULL.
+int or_kinematics(const or_robot* r, int B, const double* q, int nt, const int* targets,
+                  double* J, double* com, double* Jcom, int nthreads) {
+  const int d = r->d, n = r->n;
+  for (int t = 0; t < nt; ++t)
+    if (targets[t] < 0 || targets[t] >= n) return -1;
+  double M = 0.0;
+  for (int k = 0; k < n; ++k) M += r->mass[k];
+  for (int m = 0; m < r->n_pm; ++m) M += r->pm_mass[m];
+  int nthr = threads_for(nthreads);
+#pragma omp parallel for num_threads(nthr) schedule(dynamic, 1)
+  for (int b = 0; b < B; ++b) {
+    const double* qb = q + (size_t)b * d;
+    // centre of mass of the configuration, with derivative along seed j
+    auto com_of = [&](const std::vector<M3<Dual>>& Rw, const std::vector<Dual>& pw, Dual* c) {
+      c[0] = c[1] = c[2] = Dual(0.0);
+      auto add_point = [&](int k, const double* x, double m) {
+        Dual cl[3] = {Dual(x[0]), Dual(x[1]), Dual(x[2])}, wc[3];
+        m3_vec(Rw[k], cl, wc);
+        for (int i = 0; i < 3; ++i) c[i] += Dual(m) * (wc[i] + pw[3 * k + i]);
+      };
+      for (int k = 0; k < n; ++k) add_point(k, r->com + 3 * k, r->mass[k]);
+      for (int m = 0; m < r->n_pm; ++m) add_point(r->pm_link[m], r->pm_pos + 3 * m, r->pm_mass[m]);
+      for (int i = 0; i < 3; ++i) c[i] = c[i] / Dual(M);
+    };
+    for (int j = 0; j < std::max(d, 1); ++j) {
+      std::vector<Dual> qd(d);
+      for (int i = 0; i < d; ++i) qd[i] = Dual(qb[i], i == j ? 1.0 : 0.0);
+      std::vector<M3<Dual>> Rw;
+      std::vector<Dual> pw;
+      fk(*r, qd.data(), Rw, pw);
+      if (d == 0) break;
+      for (int t = 0; t < nt; ++t) {
+        const int e = targets[t];
+        double* col = J ? J + (((size_t)b * nt + t) * 6) * d + j : nullptr;
+        if (!col) break;
+        for (int i = 0; i < 3; ++i) col[(size_t)i * d] = pw[3 * e + i].d;
+        // W = dR R^T is skew; its axial vector is the angular velocity
+        double Wm[3][3];
+        for (int i = 0; i < 3; ++i)
+          for (int k = 0; k < 3; ++k) {
+            double acc = 0.0;
+            for (int l = 0; l < 3; ++l) acc += Rw[e].a[i][l].d * Rw[e].a[k][l].v;
+            Wm[i][k] = acc;
+          }
+        col[3 * (size_t)d] = 0.5 * (Wm[2][1] - Wm[1][2]);
+        col[4 * (size_t)d] = 0.5 * (Wm[0][2] - Wm[2][0]);
+        col[5 * (size_t)d] = 0.5 * (Wm[1][0] - Wm[0][1]);
+      }
+      if (com || Jcom) {
+        Dual c[3];
+        com_of(Rw, pw, c);
+        if (com && j == 0)
+          for (int i = 0; i < 3; ++i) com[3 * (size_t)b + i] = c[i].v;
+        if (Jcom)
+          for (int i = 0; i < 3; ++i) Jcom[((size_t)b * 3 + i) * d + j] = c[i].d;
+      }
+    }
+  }
   return 0;
 }
 

@@ -592,3 +592,66 @@ def test_pair_hinge_gradient_matches_finite_differences(oracle_lib):
         qm[j] -= h
         fd[j] = (O.pair_hinge(rob, qp, eta, w)[0] - O.pair_hinge(rob, qm, eta, w)[0]) / (2 * h)
     assert np.allclose(gq, fd, rtol=1e-6, atol=1e-6)
+
+
+def test_jacobian_and_com_planar_closed_form(oracle_lib):
+    """2-link planar arm (axes z, link 2 at (l1, 0, 0), unit masses with CoMs
+    at the link midpoints (l1/2, 0, 0) and (l2/2, 0, 0)): link 2's origin
+    (l1 c1, l1 s1) moves with (-l1 s1, l1 c1) under q1 and not under q2; both
+    columns turn about z; the CoM is the mean of the two link CoMs."""
+    O = oracle_lib
+    l1, l2 = 0.5, 0.25
+    rob = R.planar_2link(l1, l2)
+    q1, q2 = 0.3, 0.5
+    J, com, Jc = O.kinematics(rob, np.array([[q1], [q2]]), [0, 1])
+    c1, s1, c12, s12 = np.cos(q1), np.sin(q1), np.cos(q1 + q2), np.sin(q1 + q2)
+    ref1 = np.array([[-l1 * s1, 0], [l1 * c1, 0], [0, 0], [0, 0], [0, 0], [1, 1]])
+    assert np.allclose(J[0, 1], ref1, atol=1e-14)
+    assert np.allclose(J[0, 0], [[0, 0]] * 5 + [[1, 0]], atol=1e-14)  # link 1 at the origin
+    m1 = np.array([l1 / 2 * c1, l1 / 2 * s1, 0.0])
+    m2 = np.array([l1 * c1 + l2 / 2 * c12, l1 * s1 + l2 / 2 * s12, 0.0])
+    assert np.allclose(com[0], (m1 + m2) / 2, atol=1e-15)
+    dm1 = np.array([[-l1 / 2 * s1, 0], [l1 / 2 * c1, 0], [0, 0]])
+    dm2 = np.array([[-l1 * s1 - l2 / 2 * s12, -l2 / 2 * s12],
+                    [l1 * c1 + l2 / 2 * c12, l2 / 2 * c12], [0, 0]])
+    assert np.allclose(Jc[0], (dm1 + dm2) / 2, atol=1e-15)
+
+
+def test_jacobian_and_com_match_finite_differences(oracle_lib):
+    """On the humanoid with hand payloads: linear rows = central differences
+    of the link origins, angular rows = vee(dR R^T) by central differences of
+    the rotations; the CoM equals the mass-weighted sum over link CoMs and
+    point masses from the poses, and its Jacobian its central differences."""
+    O = oracle_lib
+    rob = I.hand_payload(R.r48())
+    rng = np.random.default_rng(21)
+    q = rng.uniform(-np.pi, np.pi, size=(rob.dof, 2))
+    targets = [0, 11, 27, rob.n - 1]
+    J, com, Jc = O.kinematics(rob, q, targets)
+
+    def poses(qq):
+        return O.evaluate(rob, qq, want=("pose",))["pose"]
+
+    def com_from(P):
+        m = np.concatenate([rob.mass, rob.pm_mass])
+        links = np.concatenate([np.arange(rob.n), rob.pm_link])
+        loc = np.concatenate([rob.com, rob.pm_pos])
+        R3 = P[:, links, :9].reshape(-1, len(links), 3, 3)
+        x = np.einsum("blij,lj->bli", R3, loc) + P[:, links, 9:]
+        return (m[None, :, None] * x).sum(axis=1) / m.sum()
+    P0 = poses(q)
+    assert np.allclose(com, com_from(P0), atol=1e-13)
+    h = 1e-6
+    for j in range(0, rob.dof, 7):
+        qp, qm = q.copy(), q.copy()
+        qp[j] += h
+        qm[j] -= h
+        Pp, Pm = poses(qp), poses(qm)
+        for t, e in enumerate(targets):
+            lin = (Pp[:, e, 9:] - Pm[:, e, 9:]) / (2 * h)
+            assert np.allclose(J[:, t, :3, j], lin, atol=1e-7)
+            dR = (Pp[:, e, :9] - Pm[:, e, :9]).reshape(-1, 3, 3) / (2 * h)
+            Wm = dR @ P0[:, e, :9].reshape(-1, 3, 3).transpose(0, 2, 1)
+            ang = np.stack([Wm[:, 2, 1], Wm[:, 0, 2], Wm[:, 1, 0]], axis=1)
+            assert np.allclose(J[:, t, 3:, j], ang, atol=1e-7)
+        assert np.allclose(Jc[:, :, j], (com_from(Pp) - com_from(Pm)) / (2 * h), atol=1e-7)
