@@ -204,6 +204,21 @@ int wb_eval(wb_robot* robot, int64_t B, const float* q, const float* qd, const f
 int wb_self_collision(wb_robot* robot, int64_t B, const float* link_pose, float* sphere,
                       float* d_min, int32_t* worst_pair, uint32_t* pair_bits, void* stream);
 
+/* Kinematic Jacobians of chosen links and the whole-body centre of mass,
+ * from world link poses [B][n][12] (from wb_eval): the second-kernel outputs
+ * of the split forward kinematics (Sec. 6.1.1), columns as in Alg. 2 (a joint
+ * driving several links -- mimic -- sums their contributions).
+ *   jac     [B][n_targets][6][d]  per target link e, column j = d/dq_j of
+ *           e's world origin (rows 0-2) and e's angular velocity (rows 3-5),
+ *           world coordinates; zero for joints not on e's chain
+ *   com     [B][3]                centre of mass (links + payload point masses)
+ *   jac_com [B][3][d]             its Jacobian
+ * targets is a HOST array of n_targets link indices (0 <= n_targets <= 64);
+ * each output is nullable.  Errors: WB_EINVAL, WB_ERANGE (target out of
+ * range), WB_EDEVICE, WB_ETOOBIG, WB_ECUDA. */
+int wb_kinematics(wb_robot* robot, int64_t B, const float* link_pose, int32_t n_targets,
+                  const int32_t* targets, float* jac, float* com, float* jac_com, void* stream);
+
 /* All-pairs summed self-collision hinge with activation distance eta (the
  * constraint C_robot <= 0 of the paper's problem statement with a margin, as
  * a penalty over every masked pair rather than the worst one):

@@ -220,7 +220,7 @@ struct HostPlan {
   int mimic_shared = 0;
   double r_max = 0.0;
   // segmented-sweep plans (G = 2, 4, 8)
-  std::vector<int16_t> dfs_pos, seg_slot, seg_slot_link;
+  std::vector<int16_t> dfs_pos, dfs_end, seg_slot, seg_slot_link;
   int seg_ok = 0;
   int seg_ns[3] = {0, 0, 0};
   int16_t seg_pos[3][9] = {};
@@ -531,6 +531,15 @@ static int plan_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs
   H.jidx.swap(jidx);
   H.dfs_pos.assign(n, 0);
   for (int p = 0; p < n; ++p) H.dfs_pos[H.dfs[p].x] = (int16_t)p;
+  // a subtree is the contiguous DFS range up to the next position at the
+  // same or a smaller depth
+  H.dfs_end.assign(n, (int16_t)n);
+  for (int p = 0; p < n; ++p)
+    for (int p2 = p + 1; p2 < n; ++p2)
+      if (H.dfs[p2].y <= H.dfs[p].y) {
+        H.dfs_end[H.dfs[p].x] = (int16_t)p2;
+        break;
+      }
   H.seg_slot.assign(3 * (size_t)n, -1);
   H.seg_slot_link.assign(3 * (size_t)n, 0);
   for (int t = 0; t < 3; ++t) plan_segments(H, t);
@@ -644,6 +653,7 @@ int wb_load_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs* pa
   pk.add_vec(H.chain, &D.chain);
   D.maxdepth = H.maxdepth;
   pk.add_vec(H.dfs_pos, &D.dfs_pos);
+  pk.add_vec(H.dfs_end, &D.dfs_end);
   pk.add_vec(H.seg_slot, &D.seg_slot);
   pk.add_vec(H.seg_slot_link, &D.seg_slot_link);
   D.seg_ok = H.seg_ok;
@@ -953,6 +963,46 @@ int wb_self_collision(wb_robot* robot, int64_t B, const float* link_pose, float*
   const int grid = (int)std::min<int64_t>(need, (int64_t)bps * robot->num_sms);
   e = launch_pair(robot->dev, robot->sched32, a, grid, warps, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "wb_self_collision launch");
+  return WB_OK;
+}
+
+int wb_kinematics(wb_robot* robot, int64_t B, const float* link_pose, int32_t n_targets,
+                  const int32_t* targets, float* jac, float* com, float* jac_com, void* stream) {
+  g_err.clear();
+  if (!robot) return fail(WB_EINVAL, "robot is NULL");
+  if (B < 0) return fail(WB_EINVAL, "B < 0");
+  if (n_targets < 0 || n_targets > KIN_MAX_TARGETS)
+    return fail(WB_EINVAL, "n_targets must be in [0, %d]", KIN_MAX_TARGETS);
+  if (n_targets > 0 && !targets) return fail(WB_EINVAL, "targets is NULL");
+  KinArgs a{};
+  for (int t = 0; t < n_targets; ++t) {
+    if (targets[t] < 0 || targets[t] >= robot->dev.n)
+      return fail(WB_ERANGE, "target %d = link %d out of range", t, targets[t]);
+    a.targets[t] = targets[t];
+  }
+  if (jac && n_targets == 0) jac = nullptr;
+  if (B == 0 || (!jac && !com && !jac_com)) return WB_OK;
+  int rc;
+  if ((rc = check_ptr(robot, link_pose, "link_pose", true))) return rc;
+  if ((rc = check_ptr(robot, jac, "jac", false))) return rc;
+  if ((rc = check_ptr(robot, com, "com", false))) return rc;
+  if ((rc = check_ptr(robot, jac_com, "jac_com", false))) return rc;
+  DeviceGuard guard(robot->device);
+  const int warps = 8;
+  int bps = 0;
+  cudaError_t e = kin_max_blocks_per_sm(robot->dev, warps, &bps);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+  if (bps < 1) return fail(WB_ETOOBIG, "kinematics kernel does not fit on an SM");
+  const int64_t need = (B + warps - 1) / warps;
+  const int grid = (int)std::min<int64_t>(need, (int64_t)bps * robot->num_sms);
+  a.B = B;
+  a.pose = link_pose;
+  a.nt = n_targets;
+  a.jac = jac;
+  a.com = com;
+  a.jac_com = jac_com;
+  e = launch_kin(robot->dev, a, grid, warps, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "wb_kinematics launch");
   return WB_OK;
 }
 

@@ -43,6 +43,7 @@ struct DevRobot {
   const int16_t* chain_start;// [n+1] ancestor chains (Alg. 1 "linkChain")
   const int16_t* chain;      // root -> link, link included
   const int16_t* dfs_pos;    // [n] DFS position of each link
+  const int16_t* dfs_end;    // [n] one past the last DFS position of its subtree
   // segmented sweeps with G = 2 << t segments, t = 0, 1, 2 (tree_sweep.cuh)
   int seg_ok;                // bit t set: plan t exists
   int seg_ns[3];             // shared output slots of plan t
@@ -195,6 +196,20 @@ cudaError_t batch_tree_max_blocks_per_sm(bool fwd, int* out);
 int pair_plan_words(const DevRobot& r);
 
 // launchers (return cudaGetLastError())
+// link Jacobians and the centre of mass (k_kin.cu)
+constexpr int KIN_MAX_TARGETS = 64;
+struct KinArgs {
+  int64_t B;
+  const float* pose;  // [B][n][12]
+  int nt;
+  int targets[KIN_MAX_TARGETS];
+  float* jac;         // [B][nt][6][d] or nullptr
+  float* com;         // [B][3] or nullptr
+  float* jac_com;     // [B][3][d] or nullptr
+};
+cudaError_t launch_kin(const DevRobot& r, const KinArgs& a, int grid, int warps, cudaStream_t s);
+cudaError_t kin_max_blocks_per_sm(const DevRobot& r, int warps, int* out);
+
 // all-pairs summed collision hinge (k_hinge.cu)
 struct HingeArgs {
   int64_t B;

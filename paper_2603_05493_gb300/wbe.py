@@ -200,6 +200,23 @@ class Robot:
                 "wb_self_collision")
         return o
 
+    def kinematics(self, link_pose, targets=(), *, jac=None, com=True, jac_com=True,
+                   stream=None):
+        """Jacobians of the target links [B][nt][6][d], centre of mass [B][3]
+        and its Jacobian [B][3][d] from world link poses (wb_kinematics);
+        pass False to skip an output."""
+        B = link_pose.shape[0]
+        f = dict(device=link_pose.device, dtype=torch.float32)
+        tg = (C.c_int32 * max(len(targets), 1))(*[int(t) for t in targets])
+        if jac is None and len(targets):
+            jac = torch.empty((B, len(targets), 6, self.dof), **f)
+        com = torch.empty((B, 3), **f) if com is True else (com or None)
+        jac_com = torch.empty((B, 3, self.dof), **f) if jac_com is True else (jac_com or None)
+        L.check(self.lib.wb_kinematics(self.handle, B, _ptr(link_pose), len(targets), tg,
+                                       _ptr(jac), _ptr(com), _ptr(jac_com), _stream(stream)),
+                "wb_kinematics")
+        return jac, com, jac_com
+
     def self_collision_hinge(self, link_pose, eta: float, w: float = 1.0, *, cost=None,
                              g_sphere=None, want_grad=True, stream=None):
         """All-pairs summed collision hinge w * sum max(0, eta - d) per
