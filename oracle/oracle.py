@@ -221,6 +221,27 @@ def trajopt_cost(tau, dmin, tau_lo, tau_hi, w_coll):
     return cost, g_tau, g_dmin
 
 
+def fext_gradient(robot, q, qd, qdd, fext, g_tau):
+    """d<g_tau, tau>/d f_ext [B][n][6]: tau is affine in the external forces
+    (f_k = I a + v x* I v - f_ext,k, link coordinates, moment then force), so
+    each component is <g_tau, tau(f_ext + e) - tau(f_ext)> for a unit e."""
+    r = robot
+    d = r.dof
+    q = np.asarray(q, np.float64)
+    B = q.shape[1]
+    fe = np.zeros((B, r.n, 6)) if fext is None else np.asarray(fext, np.float64)
+    base = evaluate(r, q, qd, qdd, fext=fe, want=("tau",))["tau"]
+    gt = np.asarray(g_tau, np.float64)
+    g = np.zeros((B, r.n, 6))
+    for k in range(r.n):
+        for i in range(6):
+            f2 = fe.copy()
+            f2[:, k, i] += 1.0
+            t2 = evaluate(r, q, qd, qdd, fext=f2, want=("tau",))["tau"]
+            g[:, k, i] = ((t2 - base) * gt).sum(axis=0)
+    return g
+
+
 def kinematics(robot, q, targets, nthreads: int = 0):
     """Jacobians of the target links and the centre of mass by dual-number
     differentiation of the forward kinematics.  q [d][B].  Returns

@@ -655,3 +655,59 @@ def test_jacobian_and_com_match_finite_differences(oracle_lib):
             ang = np.stack([Wm[:, 2, 1], Wm[:, 0, 2], Wm[:, 1, 0]], axis=1)
             assert np.allclose(J[:, t, 3:, j], ang, atol=1e-7)
         assert np.allclose(Jc[:, :, j], (com_from(Pp) - com_from(Pm)) / (2 * h), atol=1e-7)
+
+
+def _support_forces(rob, P):
+    """Per link, the wrench (link coordinates, moment then force, about the
+    link origin) that holds its mass and payload point masses against
+    gravity: force m R^T (-g) at each mass point."""
+    B = P.shape[0]
+    f = np.zeros((B, rob.n, 6))
+    pts = [(k, rob.mass[k], rob.com[k]) for k in range(rob.n)]
+    pts += [(int(l), m, x) for l, m, x in zip(rob.pm_link, rob.pm_mass, rob.pm_pos)]
+    g = np.asarray(rob.gravity, float)
+    for k, m, x in pts:
+        Rk = P[:, k, :9].reshape(B, 3, 3)
+        F = m * np.einsum("bji,j->bi", Rk, -g)
+        f[:, k, 3:] += F
+        f[:, k, :3] += np.cross(np.broadcast_to(x, F.shape), F)
+    return f
+
+
+def test_external_support_forces_cancel_gravity(oracle_lib):
+    """External forces that hold every link up against gravity leave zero
+    joint torque at rest, in any configuration (sign, frame and moment-first
+    ordering of f_ext)."""
+    O = oracle_lib
+    rob = I.hand_payload(R.r48())
+    rng = np.random.default_rng(8)
+    q = rng.uniform(-np.pi, np.pi, size=(rob.dof, 3))
+    P = O.evaluate(rob, q, want=("pose",))["pose"]
+    z = np.zeros_like(q)
+    tau0 = O.evaluate(rob, q, z, z, want=("tau",))["tau"]
+    assert np.abs(tau0).max() > 10.0
+    tau = O.evaluate(rob, q, z, z, fext=_support_forces(rob, P), want=("tau",))["tau"]
+    assert np.abs(tau).max() < 1e-10
+
+
+def test_fext_gradient_is_minus_the_link_frame_jacobian(oracle_lib):
+    """d tau_j / d f_ext,k = -(link k's origin Jacobian column j in link k's
+    coordinates, angular then linear): the transpose of the kinematics that
+    maps joint rates to link k's twist."""
+    O = oracle_lib
+    rob = R.r23()
+    rng = np.random.default_rng(4)
+    B = 2
+    q, qd, qdd = (rng.uniform(-2, 2, size=(rob.dof, B)) for _ in range(3))
+    fext = rng.normal(size=(B, rob.n, 6))
+    J, _, _ = O.kinematics(rob, q, list(range(rob.n)))
+    P = O.evaluate(rob, q, want=("pose",))["pose"]
+    for j in (0, 5, rob.dof - 1):
+        gt = np.zeros((rob.dof, B))
+        gt[j] = 1.0
+        g = O.fext_gradient(rob, q, qd, qdd, fext, gt)
+        for k in range(rob.n):
+            Rk = P[:, k, :9].reshape(B, 3, 3)
+            ang = np.einsum("bji,bj->bi", Rk, J[:, k, 3:, j])
+            lin = np.einsum("bji,bj->bi", Rk, J[:, k, :3, j])
+            assert np.allclose(g[:, k], -np.concatenate([ang, lin], axis=1), atol=1e-9)
