@@ -250,6 +250,23 @@ int wb_eval_backward(wb_robot* robot, int64_t B, const float* q, const float* qd
                      const float* g_sphere, const float* g_dmin, const float* g_tau, float* gq,
                      float* gqd, float* gqdd, const wb_tune* tune, void* stream);
 
+/* wb_eval / wb_eval_backward with external link wrenches (Alg. 4's f_ext):
+ * f_ext [B][n][6], link coordinates, moment then force about the link
+ * origin, enters every link force as f_k = I a + v x* I v - f_ext,k (it
+ * changes tau only).  The backward also returns g_fext [B][n][6] =
+ * dL/df_ext = -fbar_k, the adjoint of the link force (Sec. 6.3).  Both are
+ * nullable; the fused kernels reject them (WB_EINVAL), the tree and plain
+ * kernels take them. */
+int wb_eval_ext(wb_robot* robot, int64_t B, const float* q, const float* qd, const float* qdd,
+                const float* f_ext, float* link_pose, float* sphere, float* d_min,
+                int32_t* worst_pair, float* tau, uint32_t* pair_bits, const wb_tune* tune,
+                void* stream);
+int wb_eval_backward_ext(wb_robot* robot, int64_t B, const float* q, const float* qd,
+                         const float* qdd, const float* f_ext, const int32_t* worst_pair,
+                         const float* g_pose, const float* g_sphere, const float* g_dmin,
+                         const float* g_tau, float* gq, float* gqd, float* gqdd, float* g_fext,
+                         const wb_tune* tune, void* stream);
+
 /* Autotuner (a setup-time call: it allocates scratch buffers for B
  * configurations, synchronises the device and must not be captured).  Times
  * every applicable kernel family and launch shape -- depth-first sweep kernels

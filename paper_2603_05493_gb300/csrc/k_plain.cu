@@ -126,6 +126,8 @@ __global__ void __launch_bounds__(128) plain_fwd_kernel(DevRobot r, FwdArgs A) {
       float I[10];
       load_inertia(r, k, I);
       rnea_force(I, v[k], a[k], f[k]);
+      if (A.fext)
+        for (int i = 0; i < 6; ++i) f[k][i] -= A.fext[(b * n + k) * 6 + i];
     }
     for (int j = 0; j < r.d; ++j) A.tau[j * B + b] = 0.0f;
     for (int k = n - 1; k >= 0; --k) {
@@ -258,6 +260,8 @@ __global__ void __launch_bounds__(128) plain_bwd_kernel(DevRobot r, BwdArgs A) {
     float I[10];
     load_inertia(r, k, I);
     rnea_force(I, v[k], a[k], F[k]);
+    if (A.fext)
+      for (int i = 0; i < 6; ++i) F[k][i] -= A.fext[(b * n + k) * 6 + i];
   }
   for (int k = n - 1; k >= 0; --k) {
     const int pa = r.parent[k];
@@ -286,6 +290,8 @@ __global__ void __launch_bounds__(128) plain_bwd_kernel(DevRobot r, BwdArgs A) {
     crf(S, F[k], cS);
     qb[k] = dot6(XF, cS);
     for (int i = 0; i < 6; ++i) Fb[k][i] = fmaf(S[i], tb, XF[i]);
+    if (A.g_fext)  // dL/df_ext,k = -Fbar_k
+      for (int i = 0; i < 6; ++i) A.g_fext[(b * n + k) * 6 + i] = -Fb[k][i];
   }
   // ---- adjoint of the per-link force ----
   for (int k = 0; k < n; ++k) {

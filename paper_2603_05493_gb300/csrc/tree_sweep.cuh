@@ -208,6 +208,11 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
         float I[10];
         load_inertia(r, k, I);
         rnea_force(I, E.v, E.a, E.F);
+        if (A.fext) {  // f_k = I a + v x* I v - f_ext,k
+          const float* fe = A.fext + (b * n + k) * 6;
+#pragma unroll
+          for (int i = 0; i < 6; ++i) E.F[i] -= __ldg(fe + i);
+        }
       } else {
 #pragma unroll
         for (int i = 0; i < 6; ++i) E.F[i] = 0.0f;
@@ -490,6 +495,16 @@ __device__ __forceinline__ void tree_bwd_seg(const DevRobot& r, const BwdArgs& A
     float I[10];
     load_inertia(r, k, I);
     rnea_force(I, E.v, E.a, E.F);
+    if (A.fext) {
+      const float* fe = A.fext + (b * n + k) * 6;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) E.F[i] -= __ldg(fe + i);
+    }
+    if (A.g_fext) {  // dL/df_ext,k = -Fbar_k
+      float* o = A.g_fext + (b * n + k) * 6;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) o[i] = -E.Fb[i];
+    }
     // adjoint of the per-link force: abar, vbar
     {
       float Iv[6], t1[6], t2[6], t3[6];

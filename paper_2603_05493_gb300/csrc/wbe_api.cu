@@ -875,6 +875,14 @@ extern "C" {
 int wb_eval(wb_robot* robot, int64_t B, const float* q, const float* qd, const float* qdd,
             float* link_pose, float* sphere, float* d_min, int32_t* worst_pair, float* tau,
             uint32_t* pair_bits, const wb_tune* tune, void* stream) {
+  return wb_eval_ext(robot, B, q, qd, qdd, nullptr, link_pose, sphere, d_min, worst_pair, tau,
+                     pair_bits, tune, stream);
+}
+
+int wb_eval_ext(wb_robot* robot, int64_t B, const float* q, const float* qd, const float* qdd,
+                const float* f_ext, float* link_pose, float* sphere, float* d_min,
+                int32_t* worst_pair, float* tau, uint32_t* pair_bits, const wb_tune* tune,
+                void* stream) {
   g_err.clear();
   if (!robot) return fail(WB_EINVAL, "robot is NULL");
   if (B < 0) return fail(WB_EINVAL, "B < 0");
@@ -890,9 +898,11 @@ int wb_eval(wb_robot* robot, int64_t B, const float* q, const float* qd, const f
   if ((rc = check_ptr(robot, worst_pair, "worst_pair", d_min != nullptr))) return rc;
   if ((rc = check_ptr(robot, tau, "tau", false))) return rc;
   if ((rc = check_ptr(robot, pair_bits, "pair_bits", false))) return rc;
+  if ((rc = check_ptr(robot, f_ext, "f_ext", false))) return rc;
   if (!d_min && worst_pair) return fail(WB_EINVAL, "worst_pair without d_min");
   DeviceGuard guard(robot->device);
   FwdArgs a{B, q, qd, qdd, link_pose, sphere, d_min, worst_pair, tau, pair_bits};
+  a.fext = tau ? f_ext : nullptr;
   int kernel = tune ? tune->kernel : WB_KERNEL_AUTO;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bool pairs_wanted = d_min || sphere || pair_bits;
@@ -927,6 +937,7 @@ int wb_eval(wb_robot* robot, int64_t B, const float* q, const float* qd, const f
       }
     }
   } else if (kernel == WB_KERNEL_FUSED) {
+    if (a.fext) return fail(WB_EINVAL, "the fused kernels take no external forces");
     FusedShape sh;
     if ((rc = fused_shape(robot, true, pair_bits != nullptr, tune, B, sh))) return rc;
     e = launch_fused_fwd(robot->dev, robot->sched[sched_slot(sh.G)], a, sh, s);
@@ -1035,6 +1046,15 @@ int wb_eval_backward(wb_robot* robot, int64_t B, const float* q, const float* qd
                      const float* qdd, const int32_t* worst_pair, const float* g_pose,
                      const float* g_sphere, const float* g_dmin, const float* g_tau, float* gq,
                      float* gqd, float* gqdd, const wb_tune* tune, void* stream) {
+  return wb_eval_backward_ext(robot, B, q, qd, qdd, nullptr, worst_pair, g_pose, g_sphere,
+                              g_dmin, g_tau, gq, gqd, gqdd, nullptr, tune, stream);
+}
+
+int wb_eval_backward_ext(wb_robot* robot, int64_t B, const float* q, const float* qd,
+                         const float* qdd, const float* f_ext, const int32_t* worst_pair,
+                         const float* g_pose, const float* g_sphere, const float* g_dmin,
+                         const float* g_tau, float* gq, float* gqd, float* gqdd, float* g_fext,
+                         const wb_tune* tune, void* stream) {
   g_err.clear();
   if (!robot) return fail(WB_EINVAL, "robot is NULL");
   if (B < 0) return fail(WB_EINVAL, "B < 0");
@@ -1052,8 +1072,18 @@ int wb_eval_backward(wb_robot* robot, int64_t B, const float* q, const float* qd
   if ((rc = check_ptr(robot, gq, "gq", true))) return rc;
   if ((rc = check_ptr(robot, gqd, "gqd", true))) return rc;
   if ((rc = check_ptr(robot, gqdd, "gqdd", true))) return rc;
+  if ((rc = check_ptr(robot, f_ext, "f_ext", false))) return rc;
+  if ((rc = check_ptr(robot, g_fext, "g_fext", false))) return rc;
   DeviceGuard guard(robot->device);
   BwdArgs a{B, q, qd, qdd, worst_pair, g_pose, g_sphere, g_dmin, g_tau, gq, gqd, gqdd};
+  a.fext = f_ext;
+  a.g_fext = g_fext;
+  if (g_fext && !g_tau) {  // nothing depends on the external forces but tau
+    cudaError_t e0 = cudaMemsetAsync(g_fext, 0, sizeof(float) * 6 * robot->dev.n * B,
+                                     static_cast<cudaStream_t>(stream));
+    if (e0 != cudaSuccess) return cuda_fail(e0, "g_fext clear");
+    a.g_fext = nullptr;
+  }
   int kernel = tune ? tune->kernel : WB_KERNEL_AUTO;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bool tree_ok = robot->dev.maxdepth <= tree_max_depth();
@@ -1072,6 +1102,7 @@ int wb_eval_backward(wb_robot* robot, int64_t B, const float* q, const float* qd
     if ((rc = tree_segments(robot, tune, B, tpb, false, &G))) return rc;
     e = launch_tree_bwd(robot->dev, a, tpb, G, s);
   } else if (kernel == WB_KERNEL_FUSED) {
+    if (a.fext || a.g_fext) return fail(WB_EINVAL, "the fused kernels take no external forces");
     FusedShape sh;
     if ((rc = fused_shape(robot, false, false, tune, B, sh))) return rc;
     e = launch_fused_bwd(robot->dev, a, sh, s);

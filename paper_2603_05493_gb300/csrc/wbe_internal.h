@@ -110,6 +110,7 @@ struct FwdArgs {
   int32_t* worst;
   float* tau;
   uint32_t* bits;
+  const float* fext = nullptr;  // [B][n][6] external link wrenches, link coordinates
 };
 
 struct BwdArgs {
@@ -125,6 +126,8 @@ struct BwdArgs {
   float* gq;
   float* gqd;
   float* gqdd;
+  const float* fext = nullptr;  // [B][n][6]
+  float* g_fext = nullptr;      // [B][n][6]: -Fbar_k
 };
 
 // One problem of an uneven batch: robot index and horizon, and the offsets

@@ -176,14 +176,16 @@ class Robot:
         }
 
     def eval(self, q, qd=None, qdd=None, *, pose=True, sphere=True, dmin=True, tau=True,
-             bits=False, tune: Tune | None = None, out=None, stream=None):
-        """Forward whole-body evaluation; returns a dict of output tensors."""
+             bits=False, tune: Tune | None = None, out=None, f_ext=None, stream=None):
+        """Forward whole-body evaluation; returns a dict of output tensors.
+        f_ext: optional external link wrenches [B][n][6] (wb_eval_ext)."""
         B = q.shape[1]
         o = out if out is not None else self.empty_outputs(B, pose, sphere, dmin, tau, bits)
         t = (tune or Tune()).c()
-        L.check(self.lib.wb_eval(self.handle, B, _ptr(q), _ptr(qd), _ptr(qdd), _ptr(o["pose"]),
-                                 _ptr(o["sphere"]), _ptr(o["dmin"]), _ptr(o["worst"]),
-                                 _ptr(o["tau"]), _ptr(o["bits"]), C.byref(t), _stream(stream)),
+        L.check(self.lib.wb_eval_ext(self.handle, B, _ptr(q), _ptr(qd), _ptr(qdd), _ptr(f_ext),
+                                     _ptr(o["pose"]), _ptr(o["sphere"]), _ptr(o["dmin"]),
+                                     _ptr(o["worst"]), _ptr(o["tau"]), _ptr(o["bits"]),
+                                     C.byref(t), _stream(stream)),
                 "wb_eval")
         return o
 
@@ -234,19 +236,23 @@ class Robot:
         return cost, g_sphere
 
     def eval_backward(self, q, qd, qdd, worst=None, g_pose=None, g_sphere=None, g_dmin=None,
-                      g_tau=None, *, tune: Tune | None = None, out=None, stream=None):
+                      g_tau=None, *, tune: Tune | None = None, out=None, f_ext=None,
+                      g_fext=None, stream=None):
         """Gradient of <g_pose,pose> + <g_sphere,sphere> + g_dmin.d_min +
-        <g_tau,tau> w.r.t. (q, qd, qdd)."""
+        <g_tau,tau> w.r.t. (q, qd, qdd); with f_ext given (the forward's
+        external wrenches) and a g_fext buffer [B][n][6], also w.r.t. f_ext
+        (wb_eval_backward_ext)."""
         B = q.shape[1]
         if out is None:
             out = tuple(torch.empty((self.dof, B), device=self.device, dtype=torch.float32)
                         for _ in range(3))
         gq, gqd, gqdd = out
         t = (tune or Tune()).c()
-        L.check(self.lib.wb_eval_backward(self.handle, B, _ptr(q), _ptr(qd), _ptr(qdd),
-                                          _ptr(worst), _ptr(g_pose), _ptr(g_sphere),
-                                          _ptr(g_dmin), _ptr(g_tau), _ptr(gq), _ptr(gqd),
-                                          _ptr(gqdd), C.byref(t), _stream(stream)),
+        L.check(self.lib.wb_eval_backward_ext(self.handle, B, _ptr(q), _ptr(qd), _ptr(qdd),
+                                              _ptr(f_ext), _ptr(worst), _ptr(g_pose),
+                                              _ptr(g_sphere), _ptr(g_dmin), _ptr(g_tau),
+                                              _ptr(gq), _ptr(gqd), _ptr(gqdd), _ptr(g_fext),
+                                              C.byref(t), _stream(stream)),
                 "wb_eval_backward")
         return gq, gqd, gqdd
 
