@@ -638,6 +638,86 @@ def run_trajopt(args, rank=0, world=1, local_rank=0):
     print(json.dumps(line), flush=True)
 
 
+def run_kinematics(args, rank=0, world=1, local_rank=0):
+    """Split forward kinematics on the 48-DoF humanoid with hand payloads,
+    32768 configurations: the forward sweep writes the link poses, then one
+    kernel computes the world Jacobians of the two hands and two feet, the
+    centre of mass and its Jacobian.  Value = configurations per second."""
+    import torch
+    from paper_2603_05493_gb300 import build
+    build()
+    from paper_2603_05493_gb300 import wbe
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    desc = I.hand_payload(R.r48())
+    rob = wbe.Robot(desc, device=local_rank)
+    B, d, n = CF.HUMANOID48.batch, desc.dof, desc.n
+    targets = list(R.hand_links(desc)) + [n - 1, n - 7]
+    q, qd, qdd = (torch.from_numpy(x).to(dev) for x in
+                  I.uniform_states(d, B, rank_seed(CF.HUMANOID48.seed, rank)))
+    out = rob.empty_outputs(B, sphere=False, dmin=False, tau=False)
+    jac = torch.empty((B, len(targets), 6, d), device=dev)
+    com = torch.empty((B, 3), device=dev)
+    jac_com = torch.empty((B, 3, d), device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        rob.eval(q, tune=wbe.TREE, out=out, sphere=False, dmin=False, tau=False)
+        if ev:
+            ev[1].record(stream)
+        rob.kinematics(out["pose"], targets, jac=jac, com=com, jac_com=jac_com)
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    torch.cuda.nvtx.range_push("timed")
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        evs[i][0].record(stream)
+        step(evs[i])
+        evs[i][2].record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    clocks.stop()
+    barrier(world)
+    step_ms = float(np.mean([e[0].elapsed_time(e[2]) for e in evs]))
+    fk_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
+    kin_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
+    step_ms, fk_ms, kin_ms = reduce_max([step_ms, fk_ms, kin_ms], world, dev)
+    if rank != 0:
+        return
+    # kinematics kernel: reads the poses, writes the Jacobians, CoM and its
+    # Jacobian (HBM-bound); per configuration ~(12 per driven link + 30 per
+    # target-column) flops on the chain joints, ~60 per link for the moments
+    nt = len(targets)
+    kin_bytes = 4 * (12 * n + nt * 6 * d + 3 + 3 * d)
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    ach = kin_bytes * B / (kin_ms * 1e-3) / 1e9
+    print(json.dumps({
+        "metric": "split FK + link Jacobians + CoM evals/s (48-DoF humanoid + payloads)",
+        "value": job_value(world, B, step_ms), "unit": "evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "kinematics: 48-DoF tree + 3 kg hand payloads, 32768 "
+                               "configurations, Jacobians of 4 links, CoM and its Jacobian",
+                   "targets": targets, "l2": "flushed between timed steps"},
+        "kernels": {"tree_fwd": {"kernel": "tree_fwd_seg_kernel or tree_fwd_kernel (poses only)",
+                                 "ms": fk_ms},
+                    "kinematics": {"kernel": "kin_kernel", "ms": kin_ms, "bound": "hbm",
+                                   "bytes_per_eval": kin_bytes, "achieved": ach,
+                                   "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak}},
+        "roofline": {"kernel": "kin_kernel", "bound": "hbm", "achieved": ach, "peak": hbm_peak,
+                     "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None},
+        "gpu_launches": 2 * args.steps * world, "clocks": clocks.summary()}), flush=True)
+
+
 def run_uneven(args, rank=0, world=1, local_rank=0):
     """Uneven batch: 256 x R7 + 256 x R23 + 256 x R48 problems with horizons
     U{16..64}, forward (FK + RNEA, spheres + self-collision) and backward in
@@ -740,7 +820,7 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--cpu-s", type=float, default=15.0)
     ap.add_argument("--ref-step-s", type=float, default=10.0)
-    ap.add_argument("--workload", choices=["humanoid48", "uneven", "trajopt48"],
+    ap.add_argument("--workload", choices=["humanoid48", "uneven", "trajopt48", "kinematics"],
                     default="humanoid48")
     ap.add_argument("--collision", choices=["worst", "hinge"], default="worst",
                     help="trajopt48 collision cost: worst-pair hinge or summed hinge")
@@ -757,7 +837,8 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     try:
-        run = {"humanoid48": run_ours, "uneven": run_uneven, "trajopt48": run_trajopt}
+        run = {"humanoid48": run_ours, "uneven": run_uneven, "trajopt48": run_trajopt,
+               "kinematics": run_kinematics}
         run[args.workload](args, rank, world, local_rank)
     finally:
         if world > 1:

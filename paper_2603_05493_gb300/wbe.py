@@ -212,8 +212,14 @@ class Robot:
         tg = (C.c_int32 * max(len(targets), 1))(*[int(t) for t in targets])
         if jac is None and len(targets):
             jac = torch.empty((B, len(targets), 6, self.dof), **f)
-        com = torch.empty((B, 3), **f) if com is True else (com or None)
-        jac_com = torch.empty((B, 3, self.dof), **f) if jac_com is True else (jac_com or None)
+        if com is True:
+            com = torch.empty((B, 3), **f)
+        elif com is False:
+            com = None
+        if jac_com is True:
+            jac_com = torch.empty((B, 3, self.dof), **f)
+        elif jac_com is False:
+            jac_com = None
         L.check(self.lib.wb_kinematics(self.handle, B, _ptr(link_pose), len(targets), tg,
                                        _ptr(jac), _ptr(com), _ptr(jac_com), _stream(stream)),
                 "wb_kinematics")
