@@ -132,8 +132,7 @@ typedef struct {
                                 configurations, each sweeping a contiguous piece
                                 of the depth-first order (not for robots where a
                                 joint drives several links); 0 = the fewest that
-                                give about 24 (forward) / 12 (backward) warps per
-                                SM */
+                                give about 12 warps per SM */
   int32_t configs_per_block; /* fused: configurations per CTA; tree: threads per block
                                 of the sweep kernels (32..256); 0 = default */
   int32_t blocks_per_sm;     /* fused: grid = blocks_per_sm * SMs (0 = occupancy);

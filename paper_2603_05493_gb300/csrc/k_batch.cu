@@ -48,7 +48,8 @@ __global__ void __launch_bounds__(128) batch_tree_fwd_kernel(const DevRobot* rob
   }
 }
 
-__global__ void __launch_bounds__(128) batch_tree_bwd_kernel(const DevRobot* robots,
+// capped at 128 registers, as the single-robot backward sweeps
+__global__ void __launch_bounds__(128, 4) batch_tree_bwd_kernel(const DevRobot* robots,
                                                              const BatchProblemDev* probs,
                                                              const int4* items, int n_items,
                                                              int* counter, BatchIO io) {

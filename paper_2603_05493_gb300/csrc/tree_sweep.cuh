@@ -137,16 +137,34 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
   FEnt stk[TMAXD];
   if (dyn && r.mimic_shared)
     for (int j = 0; j < r.d; ++j) A.tau[(int64_t)j * B + b] = 0.0f;
+  // Register copies that spare most stack loads: the pre-order data of the
+  // last pushed entry (never changes while the entry is on the stack; a link
+  // pushed right after its parent reads it from here), and the accumulated
+  // force of the entry that the post-order closes next (an unwinding chain
+  // passes it on in registers; it is stored when a push interrupts).
+  float cW[12], cv[6], ca[6];
+  int cdep = -1;
+  float pF[6];
+  int pdep = -1;
 
   auto close = [&](int e) {
     FEnt& E = stk[e];
     const int k = E.k;
+    float F[6];
+    if (pdep == e) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) F[i] = pF[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) F[i] = E.F[i];
+    }
+    pdep = -1;
     const int j = __ldg(r.jidx + k);
     if (j >= 0) {
       const float4 a4 = __ldg(reinterpret_cast<const float4*>(r.axis) + k);
       const float ax[3] = {a4.x, a4.y, a4.z};
       const float mm = __ldg(reinterpret_cast<const float2*>(r.mimic) + k).x;
-      const float t = mm * St_dot(__ldg(r.jtype + k), ax, E.F);
+      const float t = mm * St_dot(__ldg(r.jtype + k), ax, F);
       float* pt = seg_part(sg, k, 0);
       if (pt) {
         *pt = t;
@@ -158,9 +176,17 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
     if (e > 0) {
       float L[12], up[6];
       link_local(r, k, A.q, B, b, L);
-      xf_force_T(L, L + 9, E.F, up);
+      xf_force_T(L, L + 9, F, up);
 #pragma unroll
-      for (int i = 0; i < 6; ++i) stk[e - 1].F[i] += up[i];
+      for (int i = 0; i < 6; ++i) pF[i] = stk[e - 1].F[i] + up[i];
+      pdep = e - 1;
+    }
+  };
+  auto flush = [&]() {  // the pending force goes back to its stack entry
+    if (pdep >= 0) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) stk[pdep].F[i] = pF[i];
+      pdep = -1;
     }
   };
 
@@ -168,54 +194,75 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
   // the segment (pose, v, a only; no output, no force of its own)
   auto push = [&](int k, int dep, bool own) {
     FEnt& E = stk[dep];
-    E.k = k;
     float L[12];
     link_local(r, k, A.q, B, b, L);
-    if (dep > 0)
-      compose(stk[dep - 1].W, L, E.W);
-    else
+    float PW[12], vp[6], ap[6];
+    if (dep > 0) {
+      if (dep == cdep + 1) {
 #pragma unroll
-      for (int i = 0; i < 12; ++i) E.W[i] = L[i];
-    if (own && A.pose) {
-      float4* dst = reinterpret_cast<float4*>(A.pose + (b * n + k) * 12);
-      dst[0] = make_float4(E.W[0], E.W[1], E.W[2], E.W[3]);
-      dst[1] = make_float4(E.W[4], E.W[5], E.W[6], E.W[7]);
-      dst[2] = make_float4(E.W[8], E.W[9], E.W[10], E.W[11]);
-    }
-    if (dyn) {
-      float vp[6], ap[6];
-      if (dep > 0) {
+        for (int i = 0; i < 12; ++i) PW[i] = cW[i];
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
-          vp[i] = stk[dep - 1].v[i];
-          ap[i] = stk[dep - 1].a[i];
+          vp[i] = cv[i];
+          ap[i] = ca[i];
         }
       } else {
-        vp[0] = vp[1] = vp[2] = vp[3] = vp[4] = vp[5] = 0.0f;
-        ap[0] = ap[1] = ap[2] = 0.0f;
-        ap[3] = r.abase[0];
-        ap[4] = r.abase[1];
-        ap[5] = r.abase[2];
+        const FEnt& P = stk[dep - 1];
+#pragma unroll
+        for (int i = 0; i < 12; ++i) PW[i] = P.W[i];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+          vp[i] = P.v[i];
+          ap[i] = P.a[i];
+        }
       }
+      compose(PW, L, cW);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 12; ++i) cW[i] = L[i];
+      vp[0] = vp[1] = vp[2] = vp[3] = vp[4] = vp[5] = 0.0f;
+      ap[0] = ap[1] = ap[2] = 0.0f;
+      ap[3] = r.abase[0];
+      ap[4] = r.abase[1];
+      ap[5] = r.abase[2];
+    }
+    cdep = dep;
+    E.k = k;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) E.W[i] = cW[i];
+    if (own && A.pose) {
+      float4* dst = reinterpret_cast<float4*>(A.pose + (b * n + k) * 12);
+      dst[0] = make_float4(cW[0], cW[1], cW[2], cW[3]);
+      dst[1] = make_float4(cW[4], cW[5], cW[6], cW[7]);
+      dst[2] = make_float4(cW[8], cW[9], cW[10], cW[11]);
+    }
+    if (dyn) {
       const int j = __ldg(r.jidx + k);
       const float4 a4 = __ldg(reinterpret_cast<const float4*>(r.axis) + k);
       const float ax[3] = {a4.x, a4.y, a4.z};
       const float mm = __ldg(reinterpret_cast<const float2*>(r.mimic) + k).x;
       const float vq = j >= 0 ? mm * __ldg(A.qd + (int64_t)j * B + b) : 0.0f;
       const float aq = j >= 0 ? mm * __ldg(A.qdd + (int64_t)j * B + b) : 0.0f;
-      rnea_va(L, L + 9, vp, ap, __ldg(r.jtype + k), ax, vq, aq, E.v, E.a);
+      rnea_va(L, L + 9, vp, ap, __ldg(r.jtype + k), ax, vq, aq, cv, ca);
+      float F[6];
       if (own) {
         float I[10];
         load_inertia(r, k, I);
-        rnea_force(I, E.v, E.a, E.F);
+        rnea_force(I, cv, ca, F);
         if (A.fext) {  // f_k = I a + v x* I v - f_ext,k
           const float* fe = A.fext + (b * n + k) * 6;
 #pragma unroll
-          for (int i = 0; i < 6; ++i) E.F[i] -= __ldg(fe + i);
+          for (int i = 0; i < 6; ++i) F[i] -= __ldg(fe + i);
         }
       } else {
 #pragma unroll
-        for (int i = 0; i < 6; ++i) E.F[i] = 0.0f;
+        for (int i = 0; i < 6; ++i) F[i] = 0.0f;
+      }
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        E.v[i] = cv[i];
+        E.a[i] = ca[i];
+        E.F[i] = F[i];
       }
     }
   };
@@ -240,13 +287,17 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
         }
       }
     }
-    if (dyn)
+    if (dyn) {
       while (sp > dep) close(--sp);
+      flush();
+    }
     sp = dep + 1;
     push(kd.x, dep, true);
   }
-  if (dyn)
+  if (dyn) {
     while (sp > 0) close(--sp);
+    flush();
+  }
 }
 
 __device__ __forceinline__ void tree_fwd_one(const DevRobot& r, const FwdArgs& A, int64_t b) {
@@ -348,9 +399,45 @@ __device__ __forceinline__ void tree_bwd_seg(const DevRobot& r, const BwdArgs& A
     }
   }
 
+  // Register copies that spare most stack loads (see tree_fwd_seg): the
+  // pre-order data of the last pushed entry (W, v, a, Fbar), the pending
+  // accumulators (F, abar, vbar, W) of the entry the post-order closes next,
+  // and the v of that entry, loaded by the close of its child.
+  float cW[12], cv[6], ca[6], cFb[6];
+  int cdep = -1;
+  float pF[6], pab[6], pvb[6], pWr[6], qv[6];
+  int pdep = -1, qdep = -1;
+
   auto close = [&](int e) {
     BEnt& E = stk[e];
     const int k = E.k;
+    float F[6], ab[6], vb[6], Wr[6], v[6];
+    if (pdep == e) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        F[i] = pF[i];
+        ab[i] = pab[i];
+        vb[i] = pvb[i];
+        Wr[i] = pWr[i];
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        F[i] = E.F[i];
+        ab[i] = E.ab[i];
+        vb[i] = E.vb[i];
+        Wr[i] = E.Wr[i];
+      }
+    }
+    if (qdep == e) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) v[i] = qv[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) v[i] = E.v[i];
+    }
+    pdep = -1;
+    qdep = -1;
     const int j = __ldg(r.jidx + k);
     const int jt = __ldg(r.jtype + k);
     const float4 a4 = __ldg(reinterpret_cast<const float4*>(r.axis) + k);
@@ -361,40 +448,34 @@ __device__ __forceinline__ void tree_bwd_seg(const DevRobot& r, const BwdArgs& A
     const float vq = j >= 0 ? mm * __ldg(A.qd + (int64_t)j * B + b) : 0.0f;
     float L[12];
     link_local(r, k, A.q, B, b, L);
-    float XF[6];  // X_k Fbar_pa
+    float XF[6], vp[6], ap[6];  // X_k Fbar_pa, and the parent's v, a
     if (e > 0) {
-      xf_motion(L, L + 9, stk[e - 1].Fb, XF);
-    } else {
-      XF[0] = XF[1] = XF[2] = XF[3] = XF[4] = XF[5] = 0.0f;
-    }
-    float ab[6], vb[6], t[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      ab[i] = E.ab[i];
-      vb[i] = E.vb[i];
-    }
-    crf(S, E.F, t);
-    float gq = dot6t(XF, t);
-    crf(S, ab, t);
-#pragma unroll
-    for (int i = 0; i < 6; ++i) vb[i] = fmaf(vq, t[i], vb[i]);
-    const float gqdd = dot6t(S, ab);
-    crf(E.v, ab, t);
-    const float gqd = dot6t(S, vb) - dot6t(S, t);
-    float vp[6], ap[6];
-    if (e > 0) {
+      const BEnt& P = stk[e - 1];
+      float Fbp[6];
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
-        vp[i] = stk[e - 1].v[i];
-        ap[i] = stk[e - 1].a[i];
+        Fbp[i] = P.Fb[i];
+        vp[i] = P.v[i];
+        ap[i] = P.a[i];
       }
+      xf_motion(L, L + 9, Fbp, XF);
     } else {
+      XF[0] = XF[1] = XF[2] = XF[3] = XF[4] = XF[5] = 0.0f;
       vp[0] = vp[1] = vp[2] = vp[3] = vp[4] = vp[5] = 0.0f;
       ap[0] = ap[1] = ap[2] = 0.0f;
       ap[3] = r.abase[0];
       ap[4] = r.abase[1];
       ap[5] = r.abase[2];
     }
+    float t[6];
+    crf(S, F, t);
+    float gq = dot6t(XF, t);
+    crf(S, ab, t);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) vb[i] = fmaf(vq, t[i], vb[i]);
+    const float gqdd = dot6t(S, ab);
+    crf(v, ab, t);
+    const float gqd = dot6t(S, vb) - dot6t(S, t);
     float Xa[6], Xv[6], c6[6];
     xf_motion(L, L + 9, ap, Xa);
     xf_motion(L, L + 9, vp, Xv);
@@ -402,7 +483,7 @@ __device__ __forceinline__ void tree_bwd_seg(const DevRobot& r, const BwdArgs& A
     gq -= dot6t(ab, c6);
     crm(S, Xv, c6);
     gq -= dot6t(vb, c6);
-    gq += dot6t(S, E.Wr);
+    gq += dot6t(S, Wr);
     if (j >= 0) {
       float* p0 = seg_part(sg, k, 0);
       if (p0) {
@@ -426,43 +507,73 @@ __device__ __forceinline__ void tree_bwd_seg(const DevRobot& r, const BwdArgs& A
       }
     }
     if (e > 0) {
-      BEnt& P = stk[e - 1];
+      const BEnt& P = stk[e - 1];
       float up[6];
-      xf_force_T(L, L + 9, E.F, up);
+      xf_force_T(L, L + 9, F, up);
 #pragma unroll
-      for (int i = 0; i < 6; ++i) P.F[i] += up[i];
+      for (int i = 0; i < 6; ++i) pF[i] = P.F[i] + up[i];
       xf_force_T(L, L + 9, ab, up);
 #pragma unroll
-      for (int i = 0; i < 6; ++i) P.ab[i] += up[i];
+      for (int i = 0; i < 6; ++i) pab[i] = P.ab[i] + up[i];
       xf_force_T(L, L + 9, vb, up);
 #pragma unroll
-      for (int i = 0; i < 6; ++i) P.vb[i] += up[i];
-      xf_force_T(L, L + 9, E.Wr, up);
+      for (int i = 0; i < 6; ++i) pvb[i] = P.vb[i] + up[i];
+      xf_force_T(L, L + 9, Wr, up);
 #pragma unroll
-      for (int i = 0; i < 6; ++i) P.Wr[i] += up[i];
+      for (int i = 0; i < 6; ++i) pWr[i] = P.Wr[i] + up[i];
+      pdep = e - 1;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) qv[i] = vp[i];
+      qdep = e - 1;
     }
+  };
+  auto flush = [&]() {  // the pending accumulators go back to their entry
+    if (pdep >= 0) {
+      BEnt& P = stk[pdep];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        P.F[i] = pF[i];
+        P.ab[i] = pab[i];
+        P.vb[i] = pvb[i];
+        P.Wr[i] = pWr[i];
+      }
+      pdep = -1;
+    }
+    qdep = -1;
   };
 
   // pre-order of link k at depth dep; own = false replays an ancestor of
   // the segment (pose, v, a, Fbar only; its own contributions are zero)
   auto push = [&](int k, int dep, bool own) {
     BEnt& E = stk[dep];
-    E.k = k;
     float L[12];
     link_local(r, k, A.q, B, b, L);
-    float vp[6], ap[6], Fbp[6];
+    float PW[12], vp[6], ap[6], Fbp[6];
     if (dep > 0) {
-      const BEnt& P = stk[dep - 1];
-      compose(P.W, L, E.W);
+      if (dep == cdep + 1) {
 #pragma unroll
-      for (int i = 0; i < 6; ++i) {
-        vp[i] = P.v[i];
-        ap[i] = P.a[i];
-        Fbp[i] = P.Fb[i];
+        for (int i = 0; i < 12; ++i) PW[i] = cW[i];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+          vp[i] = cv[i];
+          ap[i] = ca[i];
+          Fbp[i] = cFb[i];
+        }
+      } else {
+        const BEnt& P = stk[dep - 1];
+#pragma unroll
+        for (int i = 0; i < 12; ++i) PW[i] = P.W[i];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+          vp[i] = P.v[i];
+          ap[i] = P.a[i];
+          Fbp[i] = P.Fb[i];
+        }
       }
+      compose(PW, L, cW);
     } else {
 #pragma unroll
-      for (int i = 0; i < 12; ++i) E.W[i] = L[i];
+      for (int i = 0; i < 12; ++i) cW[i] = L[i];
       vp[0] = vp[1] = vp[2] = vp[3] = vp[4] = vp[5] = 0.0f;
       ap[0] = ap[1] = ap[2] = 0.0f;
       ap[3] = r.abase[0];
@@ -470,6 +581,7 @@ __device__ __forceinline__ void tree_bwd_seg(const DevRobot& r, const BwdArgs& A
       ap[5] = r.abase[2];
       Fbp[0] = Fbp[1] = Fbp[2] = Fbp[3] = Fbp[4] = Fbp[5] = 0.0f;
     }
+    cdep = dep;
     const int j = __ldg(r.jidx + k);
     const int jt = __ldg(r.jtype + k);
     const float4 a4 = __ldg(reinterpret_cast<const float4*>(r.axis) + k);
@@ -478,7 +590,7 @@ __device__ __forceinline__ void tree_bwd_seg(const DevRobot& r, const BwdArgs& A
     const float vq = j >= 0 ? mm * __ldg(A.qd + (int64_t)j * B + b) : 0.0f;
     const float aq = j >= 0 ? mm * __ldg(A.qdd + (int64_t)j * B + b) : 0.0f;
     // dynamics forward: v, a (and f when the link is this segment's)
-    rnea_va(L, L + 9, vp, ap, jt, ax, vq, aq, E.v, E.a);
+    rnea_va(L, L + 9, vp, ap, jt, ax, vq, aq, cv, ca);
     // adjoint of the force sweep: Fbar_k = S m taubar + X Fbar_pa
     float S[6];
     motion_S6t(jt, ax, S);
@@ -486,35 +598,45 @@ __device__ __forceinline__ void tree_bwd_seg(const DevRobot& r, const BwdArgs& A
     float XF[6];
     xf_motion(L, L + 9, Fbp, XF);
 #pragma unroll
-    for (int i = 0; i < 6; ++i) E.Fb[i] = fmaf(S[i], tb, XF[i]);
+    for (int i = 0; i < 6; ++i) cFb[i] = fmaf(S[i], tb, XF[i]);
+    E.k = k;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) E.W[i] = cW[i];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      E.v[i] = cv[i];
+      E.a[i] = ca[i];
+      E.Fb[i] = cFb[i];
+    }
     if (!own) {
 #pragma unroll
       for (int i = 0; i < 6; ++i) E.F[i] = E.ab[i] = E.vb[i] = E.Wr[i] = 0.0f;
       return;
     }
-    float I[10];
+    float I[10], F[6];
     load_inertia(r, k, I);
-    rnea_force(I, E.v, E.a, E.F);
+    rnea_force(I, cv, ca, F);
     if (A.fext) {
       const float* fe = A.fext + (b * n + k) * 6;
 #pragma unroll
-      for (int i = 0; i < 6; ++i) E.F[i] -= __ldg(fe + i);
+      for (int i = 0; i < 6; ++i) F[i] -= __ldg(fe + i);
     }
     if (A.g_fext) {  // dL/df_ext,k = -Fbar_k
       float* o = A.g_fext + (b * n + k) * 6;
 #pragma unroll
-      for (int i = 0; i < 6; ++i) o[i] = -E.Fb[i];
+      for (int i = 0; i < 6; ++i) o[i] = -cFb[i];
     }
     // adjoint of the per-link force: abar, vbar
+    float abk[6], vbk[6];
     {
       float Iv[6], t1[6], t2[6], t3[6];
-      inertia_mul(I, E.Fb, E.ab);
-      inertia_mul(I, E.v, Iv);
-      crf(E.Fb, Iv, t1);
-      crm(E.v, E.Fb, t2);
+      inertia_mul(I, cFb, abk);
+      inertia_mul(I, cv, Iv);
+      crf(cFb, Iv, t1);
+      crm(cv, cFb, t2);
       inertia_mul(I, t2, t3);
 #pragma unroll
-      for (int i = 0; i < 6; ++i) E.vb[i] = -t1[i] - t3[i];
+      for (int i = 0; i < 6; ++i) vbk[i] = -t1[i] - t3[i];
     }
     // gradient wrench of the kinematic outputs, link frame
     float w[6] = {0, 0, 0, 0, 0, 0};
@@ -522,7 +644,7 @@ __device__ __forceinline__ void tree_bwd_seg(const DevRobot& r, const BwdArgs& A
       const float4* g4 = reinterpret_cast<const float4*>(A.g_pose + (b * n + k) * 12);
       const float4 x0 = __ldg(g4), x1 = __ldg(g4 + 1), x2 = __ldg(g4 + 2);
       const float gg[12] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w, x2.x, x2.y, x2.z, x2.w};
-      const float* R = E.W;
+      const float* R = cW;
       float Gm[9];  // R^T Rbar
 #pragma unroll
       for (int ii = 0; ii < 3; ++ii)
@@ -540,16 +662,21 @@ __device__ __forceinline__ void tree_bwd_seg(const DevRobot& r, const BwdArgs& A
         const int s = __ldg(r.ls_sph + e);
         const float* g = A.g_sph + (b * r.S + s) * 3;
         const float gg[3] = {__ldg(g), __ldg(g + 1), __ldg(g + 2)};
-        point_wrench(E.W, __ldg(r.sph + s), gg, w);
+        point_wrench(cW, __ldg(r.sph + s), gg, w);
       }
     }
-    if (k == pl1) point_wrench(E.W, __ldg(r.sph + ps1), u, w);
+    if (k == pl1) point_wrench(cW, __ldg(r.sph + ps1), u, w);
     if (k == pl2) {
       const float mu[3] = {-u[0], -u[1], -u[2]};
-      point_wrench(E.W, __ldg(r.sph + ps2), mu, w);
+      point_wrench(cW, __ldg(r.sph + ps2), mu, w);
     }
 #pragma unroll
-    for (int i = 0; i < 6; ++i) E.Wr[i] = w[i];
+    for (int i = 0; i < 6; ++i) {
+      E.F[i] = F[i];
+      E.ab[i] = abk[i];
+      E.vb[i] = vbk[i];
+      E.Wr[i] = w[i];
+    }
   };
 
   int sp = 0;
@@ -585,10 +712,12 @@ __device__ __forceinline__ void tree_bwd_seg(const DevRobot& r, const BwdArgs& A
       }
     }
     while (sp > dep) close(--sp);
+    flush();
     sp = dep + 1;
     push(kd.x, dep, true);
   }
   while (sp > 0) close(--sp);
+  flush();
 }
 
 __device__ __forceinline__ void tree_bwd_one(const DevRobot& r, const BwdArgs& A, int64_t b) {

@@ -842,10 +842,10 @@ static int fused_shape(const wb_robot* R, bool fwd, bool bits, const wb_tune* t,
 static bool plain_fits(const DevRobot& D) { return D.n <= 64 && D.S <= 256; }
 
 // Segments of the sweep kernels (wb_tune.lanes_per_config for TREE): 1, 2, 4
-// or 8; 0 = the fewest of the robot's plans that give about 24 (forward) or
-// 12 (backward, whose larger stack entries thrash L1 sooner) warps per SM --
-// measured on the 48-DoF humanoid at 32768 configurations: forward best at 4,
-// backward at 2, 8 slower than 1 for both.
+// or 8; 0 = the fewest of the robot's plans that give about 12 warps per SM --
+// measured on the 48-DoF humanoid at 32768 configurations: both passes best
+// at 2 segments (the register copies of the stack top make each warp
+// faster, so fewer segments suffice), 8 slower than 1.
 static int tree_segments(const wb_robot* R, const wb_tune* tune, int64_t B, int threads,
                          bool fwd, int* out) {
   const int req = tune ? tune->lanes_per_config : 0;
@@ -860,7 +860,7 @@ static int tree_segments(const wb_robot* R, const wb_tune* tune, int64_t B, int 
     G = req;
   } else {
     const int64_t warps = (B + 31) / 32;
-    const int64_t target = (fwd ? 24LL : 12LL) * R->num_sms;
+    const int64_t target = 12LL * R->num_sms;
     for (int t = 0; t < 3 && warps * G < target; ++t)
       if (ok >> t & 1) G = 2 << t;
   }
