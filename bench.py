@@ -344,6 +344,24 @@ def run_ours(args, rank, world, local_rank):
     fwd_ms = [a + b for a, b in zip(k_ms["tree_fwd"], k_ms["pair"])]
     bwd_ms = k_ms["tree_bwd"]
 
+    # the pair stage's full map-reduce (every block screened, no culling) on
+    # the same poses, for comparison with the default culled kernel
+    brute_ms = None
+    if args.kernel == "tree":
+        bout = {"sphere": None, "dmin": torch.empty_like(out["dmin"]),
+                "worst": torch.empty_like(out["worst"]), "bits": None}
+        tb = []
+        for i in range(max(5, min(args.steps, 20))):
+            flush.fill_(float(i))
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            rob.self_collision(out["pose"], out=bout, tune=wbe.TREE_NOCULL)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            tb.append(a0.elapsed_time(a1))
+        brute_ms = float(np.mean(tb[2:]))
+        assert torch.equal(bout["dmin"], out["dmin"]) and torch.equal(bout["worst"], out["worst"])
+
     # end to end through the C ABI: pinned host inputs -> device, forward,
     # backward, results -> pinned host, every step
     h_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
@@ -424,6 +442,7 @@ def run_ours(args, rank, world, local_rank):
                                      % (num_sms, sm_max)) if kernels[dom]["bound"] == "alu"
                          else "HBM copy bandwidth of measured"),
         "kernels": kernels,
+        "pair_full_map_reduce_ms": brute_ms,
         "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": (3 if args.kernel == "tree" else 2) * args.steps,

@@ -124,6 +124,9 @@ typedef struct {
                              for FK, RNEA and the backward, plus a warp-per-
                              configuration sphere/pair kernel; needs link_pose
                              when spheres or pairs are wanted */
+#define WB_KERNEL_TREE_NOCULL 4 /* TREE with the pair stage's full map-reduce: every
+                                   block screened, no bounding-sphere culling (the
+                                   results are identical; for comparison) */
 typedef struct {
   int32_t kernel;            /* WB_KERNEL_* (AUTO: TREE when it applies, else FUSED) */
   int32_t lanes_per_config;  /* fused: 4, 8, 16 or 32 (0 = robot default);
@@ -202,6 +205,14 @@ int wb_eval(wb_robot* robot, int64_t B, const float* q, const float* qd, const f
  * Errors as wb_eval. */
 int wb_self_collision(wb_robot* robot, int64_t B, const float* link_pose, float* sphere,
                       float* d_min, int32_t* worst_pair, uint32_t* pair_bits, void* stream);
+/* wb_self_collision with a launch choice: tune->kernel TREE (or AUTO, or a
+ * NULL tune) culls 4x4 sphere-group blocks whose bounding-sphere lower bound
+ * exceeds an exact upper bound on d_min (the default); TREE_NOCULL screens
+ * every block.  tune->blocks_per_sm = warps per block (0 = 8).  Same outputs,
+ * same tie rule. */
+int wb_self_collision_tuned(wb_robot* robot, int64_t B, const float* link_pose, float* sphere,
+                            float* d_min, int32_t* worst_pair, uint32_t* pair_bits,
+                            const wb_tune* tune, void* stream);
 
 /* Kinematic Jacobians of chosen links and the whole-body centre of mass,
  * from world link poses [B][n][12] (from wb_eval): the second-kernel outputs

@@ -24,6 +24,7 @@ WB_KERNEL_AUTO = 0
 WB_KERNEL_PLAIN = 1
 WB_KERNEL_FUSED = 2
 WB_KERNEL_TREE = 3
+WB_KERNEL_TREE_NOCULL = 4
 
 p = C.c_void_p
 
@@ -101,6 +102,7 @@ SIGNATURES = {
     "wb_trajopt_cost": (C.c_int, [C.c_int64, C.c_int32, p, p, p, p, C.c_float, p, p, p, p]),
     "wb_self_collision_hinge": (C.c_int, [p, C.c_int64, p, C.c_float, C.c_float, p, p, p]),
     "wb_kinematics": (C.c_int, [p, C.c_int64, p, C.c_int32, p, p, p, p, p]),
+    "wb_self_collision_tuned": (C.c_int, [p, C.c_int64, p, p, p, p, p, C.POINTER(wb_tune), p]),
     "wb_eval_ext": (C.c_int, [p, C.c_int64, p, p, p, p, p, p, p, p, p, p, C.POINTER(wb_tune), p]),
     "wb_eval_backward_ext": (C.c_int, [p, C.c_int64, p, p, p, p, p, p, p, p, p, p, p, p, p,
                                        C.POINTER(wb_tune), p]),

@@ -107,9 +107,9 @@ __global__ void __launch_bounds__(256, 3) batch_pair_kernel(const DevRobot* robo
               io.worst ? io.worst + pb.co : nullptr,
               nullptr, nullptr};
     if (r.all_full)
-      pair_one<true, false>(r, scheds[pb.robot], A, w.y, ws, radw, lane);
+      pair_one_culled<true, false>(r, scheds[pb.robot], A, w.y, ws, radw, lane);
     else
-      pair_one<false, false>(r, scheds[pb.robot], A, w.y, ws, radw, lane);
+      pair_one_culled<false, false>(r, scheds[pb.robot], A, w.y, ws, radw, lane);
   }
 }
 

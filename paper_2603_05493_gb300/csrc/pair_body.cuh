@@ -34,7 +34,7 @@ namespace wbe {
 __host__ __device__ constexpr int a32(int x) { return (x + 31) & ~31; }
 
 struct PairPlan {  // per warp, 32-bit words
-  int xr, yr, zr, xc, yc, zc, nn, bits, total;
+  int xr, yr, zr, xc, yc, zc, nn, gb, q, bits, total;
   __host__ __device__ PairPlan(int n, int Sg, int P, bool with_bits) {
     const int m = a32(4 * Sg);
     const int ra = 3 * m > a32(12 * n) ? 3 * m : a32(12 * n);  // rows; poses while staging
@@ -45,7 +45,9 @@ struct PairPlan {  // per warp, 32-bit words
     yc = ra + m;
     zc = ra + 2 * m;
     nn = ra + 3 * m;
-    bits = ra + 4 * m;
+    gb = ra + 4 * m;  // group bounding spheres (float4 per group), culling only
+    q = gb + m;       // queue of surviving schedule entries (64), culling only
+    bits = q + 64;
     total = bits + (with_bits ? a32((P + 31) / 32) : 0);
   }
 };
@@ -263,6 +265,277 @@ __device__ __forceinline__ void pair_one(const DevRobot& r, const PairSchedule32
       set_row();
     }
   }
+  bidx = bidx == INT_MAX ? INT_MAX : __ldg(r.blk_pidx + bidx);  // slot -> pair index
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, bidx, off);
+    if (ob < best || (ob == best && oi < bidx)) {
+      best = ob;
+      bidx = oi;
+    }
+  }
+  if (lane == 0 && A.dmin) {
+    const bool none = bidx == INT_MAX;
+    A.dmin[b] = none ? __int_as_float(0x7f800000) : best;
+    A.worst[b] = none ? -1 : bidx;
+  }
+  if (BITS) {
+    __syncwarp();
+    for (int w = lane; w < W; w += 32) A.bits[b * (int64_t)W + w] = bm[w];
+  }
+  __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// The same map-reduce with whole blocks culled by group bounding spheres.
+//
+// Every 4-sphere group gets a bounding sphere (C_g, R_g): the mean of its
+// centres and the largest |c - C_g| + r, widened for float rounding.  For any
+// pair (a in group i, b in group j), d_ab >= |C_i - C_j| - R_i - R_j =: lb, so
+// a block whose lb exceeds an upper bound on d_min holds no candidate for the
+// minimum (nor, with lb >= 0, a colliding pair).  Pass 1 finds the block of
+// smallest lb and the exact minimum of its pairs, a real pair distance and
+// so an upper bound on d_min; pass 2 walks the schedule again, keeps the
+// blocks with lb within the margin of the current bound (or below 0 when
+// the pair bits are wanted), queues them warp-wide (ballot + prefix count)
+// and screens 32 queued blocks at a time with the usual screen and exact
+// path.  The result -- d_min, the worst pair with its tie rule, the bits --
+// is that of the full map-reduce; only blocks that cannot affect it are
+// skipped.
+template <bool FULL, bool BITS>
+__device__ __forceinline__ void pair_one_culled(const DevRobot& r, const PairSchedule32& ps,
+                                                const FwdArgs& A, int64_t b, float* ws,
+                                                const float4* radw, int lane) {
+  const PairPlan pl(r.n, r.Sg, r.P, BITS);
+  float* xr = ws + pl.xr;
+  float* yr = ws + pl.yr;
+  float* zr = ws + pl.zr;
+  float* xc = ws + pl.xc;
+  float* yc = ws + pl.yc;
+  float* zc = ws + pl.zc;
+  float* nn = ws + pl.nn;
+  float4* gb = reinterpret_cast<float4*>(ws + pl.gb);
+  uint32_t* qu = reinterpret_cast<uint32_t*>(ws + pl.q);
+  uint32_t* bm = reinterpret_cast<uint32_t*>(ws + pl.bits);
+  const char* cxr = reinterpret_cast<const char*>(xr);
+  const char* cyr = reinterpret_cast<const char*>(yr);
+  const char* czr = reinterpret_cast<const char*>(zr);
+  const char* cxc = reinterpret_cast<const char*>(xc);
+  const char* cyc = reinterpret_cast<const char*>(yc);
+  const char* czc = reinterpret_cast<const char*>(zc);
+  const char* cnn = reinterpret_cast<const char*>(nn);
+  const char* crad = reinterpret_cast<const char*>(radw);
+  const int n = r.n, S = r.S, Sg = r.Sg;
+  const int W = (r.P + 31) >> 5;
+  const float margin = r.margin, etol = r.etol, nrmin = -r.rmin;
+  const int rounds = ps.rounds;
+  // ---- stage the link poses (contiguous), then place the spheres ----
+  {
+    const float4* src = reinterpret_cast<const float4*>(A.pose + b * (int64_t)n * 12);
+    float4* dst = reinterpret_cast<float4*>(xr);
+#pragma unroll 4
+    for (int i = lane; i < 3 * n; i += 32) dst[i] = __ldg(src + i);
+  }
+  __syncwarp();
+  for (int s = lane; s < 4 * Sg; s += 32) {
+    float c[3] = {0.0f, 0.0f, 0.0f};
+    float rs = 0.0f;
+    if (s < S) {
+      const float4 sp = __ldg(r.sph + s);
+      const float* P = xr + 12 * __ldg(r.sph_link + s);
+      const float cl[3] = {sp.x, sp.y, sp.z};
+      rot(P, cl, c);
+      c[0] += P[9];
+      c[1] += P[10];
+      c[2] += P[11];
+      rs = sp.w;
+      if (A.sph) {
+        float* o = A.sph + (b * S + s) * 3;
+        o[0] = c[0];
+        o[1] = c[1];
+        o[2] = c[2];
+      }
+    }
+    xc[s] = c[0];
+    yc[s] = c[1];
+    zc[s] = c[2];
+    nn[s] = fmaf(-rs, rs, fmaf(c[2], c[2], fmaf(c[1], c[1], c[0] * c[0])));  // |c|^2 - r^2
+  }
+  __syncwarp();
+  for (int s = lane; s < 4 * Sg; s += 32) {  // row copies, pre-scaled by -2
+    xr[s] = -2.0f * xc[s];
+    yr[s] = -2.0f * yc[s];
+    zr[s] = -2.0f * zc[s];
+  }
+  for (int g = lane; g < Sg; g += 32) {  // group bounding spheres
+    const int s0 = 4 * g, s1 = min(S, s0 + 4);
+    float cx = 0.0f, cy = 0.0f, cz = 0.0f;
+    for (int s = s0; s < s1; ++s) {
+      cx += xc[s];
+      cy += yc[s];
+      cz += zc[s];
+    }
+    const float inv = 1.0f / (float)max(s1 - s0, 1);
+    cx *= inv;
+    cy *= inv;
+    cz *= inv;
+    const float4 rad = radw[g];
+    float R = 0.0f;
+    for (int s = s0; s < s1; ++s)
+      R = fmaxf(R, sqrtf(dist2(cx, cy, cz, xc[s], yc[s], zc[s])) + pick(rad, s - s0));
+    gb[g] = make_float4(cx, cy, cz, fmaf(R, 1e-6f, R) + 1e-6f);  // widened for rounding
+  }
+  if (BITS)
+    for (int w = lane; w < W; w += 32) bm[w] = 0u;
+  __syncwarp();
+  if (!A.dmin && !BITS) return;  // sphere placement only
+  if (rounds == 0) {
+    if (lane == 0 && A.dmin) {
+      A.dmin[b] = __int_as_float(0x7f800000);
+      A.worst[b] = -1;
+    }
+    if (BITS)
+      for (int w = lane; w < W; w += 32) A.bits[b * (int64_t)W + w] = 0u;
+    return;
+  }
+  const float inf = __int_as_float(0x7f800000);
+  // ---- pass 1: the block of smallest lower bound (approximately: any block
+  // gives a valid bound), and the exact minimum of its pairs ----
+  float lbmin = inf;
+  uint2 ebest = make_uint2(0u, 0u);
+  for (int rr = 0; rr < rounds; ++rr) {
+    const uint2 e = __ldg(ps.ent + rr * 32 + lane);
+    if ((e.y >> 16) == 0u) continue;  // null entry
+    const float4 P4 = gb[(e.x & 0xFFFF) >> 4], Q4 = gb[(e.x >> 16) >> 4];
+    const float D2 = fmaxf(dist2(P4.x, P4.y, P4.z, Q4.x, Q4.y, Q4.z), 1e-30f);
+    const float lb = D2 * rsqrtf(D2) - (P4.w + Q4.w);  // approximate square root
+    if (lb < lbmin) {
+      lbmin = lb;
+      ebest = e;
+    }
+  }
+  float gbest;
+  {
+    const int kmin = __reduce_min_sync(0xffffffffu, fkey(lbmin));
+    const int src = __ffs(__ballot_sync(0xffffffffu, fkey(lbmin) == kmin)) - 1;
+    const uint2 e = make_uint2(__shfl_sync(0xffffffffu, ebest.x, src),
+                               __shfl_sync(0xffffffffu, ebest.y, src));
+    float d = inf;
+    const int t = lane & 15, a = t >> 2, c = t & 3;
+    if (lane < 16 && ((e.y >> 16) >> t) & 1u) {
+      const uint32_t ro = e.x & 0xFFFF, co = e.x >> 16;
+      const float* pi = reinterpret_cast<const float*>(cxc + ro);
+      const float* pyi = reinterpret_cast<const float*>(cyc + ro);
+      const float* pzi = reinterpret_cast<const float*>(czc + ro);
+      const float* pj = reinterpret_cast<const float*>(cxc + co);
+      const float* pyj = reinterpret_cast<const float*>(cyc + co);
+      const float* pzj = reinterpret_cast<const float*>(czc + co);
+      d = sqrtf(dist2(pi[a], pyi[a], pzi[a], pj[c], pyj[c], pzj[c])) -
+          (pick(lds4(crad, ro), a) + pick(lds4(crad, co), c));
+    }
+    gbest = fkey_inv(__reduce_min_sync(0xffffffffu, fkey(d)));  // a real pair: d_min <= gbest
+  }
+  // ---- pass 2: queue the surviving blocks, screen 32 at a time ----
+  float best = 1e15f;
+  int bidx = INT_MAX;
+  int qn = 0;  // warp-uniform queue length
+  // a block survives when its lower bound is within the screen's reach of
+  // the current bound (or below zero when every colliding pair is wanted)
+  const float reach_tol = 2.0f * margin;
+  auto screen_block = [&](uint2 e) {
+    const uint32_t ro = e.x & 0xFFFF, co = e.x >> 16;
+    const uint32_t mask = e.y >> 16;
+    const float4 XR = lds4(cxr, ro), YR = lds4(cyr, ro), ZR = lds4(czr, ro);
+    const float4 RR = lds4(crad, ro), NI = lds4(cnn, ro);
+    const float4 CC = make_float4(fmaf(RR.x, RR.x, NI.x), fmaf(RR.y, RR.y, NI.y),
+                                  fmaf(RR.z, RR.z, NI.z), fmaf(RR.w, RR.w, NI.w));  // |c_i|^2
+    const float bb = fminf(best, gbest) + margin;
+    const float T[4] = {fmaxf(bb + RR.x, nrmin), fmaxf(bb + RR.y, nrmin),
+                        fmaxf(bb + RR.z, nrmin), fmaxf(bb + RR.w, nrmin)};
+    const float C4[4] = {CC.x, CC.y, CC.z, CC.w};
+    const float xr4[4] = {XR.x, XR.y, XR.z, XR.w}, yr4[4] = {YR.x, YR.y, YR.z, YR.w},
+                zr4[4] = {ZR.x, ZR.y, ZR.z, ZR.w};
+    const float4 X = lds4(cxc, co), Y = lds4(cyc, co), Z = lds4(czc, co), N = lds4(cnn, co),
+                 Rc = lds4(crad, co);
+    const float xj[4] = {X.x, X.y, X.z, X.w}, yj[4] = {Y.x, Y.y, Y.z, Y.w},
+                zj[4] = {Z.x, Z.y, Z.z, Z.w}, nj[4] = {N.x, N.y, N.z, N.w},
+                rj[4] = {Rc.x, Rc.y, Rc.z, Rc.w};
+    auto screen = [&](int a, int c) {
+      const float Ai = fmaf(-T[a], T[a], C4[a]);
+      return fmaf(-2.0f * T[a], rj[c],
+                  fmaf(zr4[a], zj[c], fmaf(yr4[a], yj[c], fmaf(xr4[a], xj[c], Ai + nj[c]))));
+    };
+    uint32_t cand = 0u;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) cand |= (screen(t >> 2, t & 3) < etol ? 1u : 0u) << t;
+    cand &= mask;
+    while (cand) {
+      const int t = __ffs(cand) - 1;
+      cand &= cand - 1u;
+      const int a = t >> 2, c = t & 3;
+      const float d2 = dist2(-0.5f * xr4[a], -0.5f * yr4[a], -0.5f * zr4[a], xj[c], yj[c], zj[c]);
+      const float dd = sqrtf(d2) - (pick(RR, a) + rj[c]);
+      const int slot = 16 * (e.y & 0xFFFF) + t;  // row of blk_pidx: resolved at the end
+      if (dd < best) {
+        best = dd;
+        bidx = slot;
+      } else if (dd == best && bidx != INT_MAX &&
+                 __ldg(r.blk_pidx + slot) < __ldg(r.blk_pidx + bidx)) {
+        bidx = slot;  // exact tie: the smaller pair index wins
+      }
+    }
+    if (BITS && mask) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if ((mask >> (4 * a + c)) & 1u) {
+            const float d2 = dist2(-0.5f * xr4[a], -0.5f * yr4[a], -0.5f * zr4[a], xj[c], yj[c],
+                                   zj[c]);
+            if (sqrtf(d2) - (pick(RR, a) + rj[c]) < 0.0f) {
+              const int pidx = __ldg(r.blk_pidx + 16 * (e.y & 0xFFFF) + 4 * a + c);
+              atomicOr(bm + (pidx >> 5), 1u << (pidx & 31));
+            }
+          }
+        }
+    }
+  };
+  auto drain = [&](int count) {  // screen queue entries [0, count), one per lane
+    const uint2 e = lane < count ? __ldg(ps.ent + qu[lane]) : make_uint2(0u, 0u);
+    __syncwarp();
+    if ((e.y >> 16) != 0u) screen_block(e);
+    gbest = fminf(gbest, fkey_inv(__reduce_min_sync(0xffffffffu, fkey(best))));
+  };
+  for (int rr = 0; rr < rounds; ++rr) {
+    const int idx = rr * 32 + lane;
+    const uint2 e = __ldg(ps.ent + idx);
+    // lb <= bound + tol  <=>  |C_i - C_j| <= t := bound + tol + R_i + R_j,
+    // tested on squares (t >= 0); the tolerance covers the float rounding
+    bool keep = false;
+    if ((e.y >> 16) != 0u) {
+      const float4 P4 = gb[(e.x & 0xFFFF) >> 4], Q4 = gb[(e.x >> 16) >> 4];
+      const float D2 = dist2(P4.x, P4.y, P4.z, Q4.x, Q4.y, Q4.z);
+      const float RR2 = P4.w + Q4.w + reach_tol;
+      const float t = fminf(best, gbest) + RR2;
+      keep = (t >= 0.0f && D2 <= t * t) || (BITS && RR2 >= 0.0f && D2 <= RR2 * RR2);
+    }
+    const uint32_t ball = __ballot_sync(0xffffffffu, keep);
+    if (keep) qu[qn + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)idx;
+    qn += __popc(ball);
+    if (qn >= 32) {
+      __syncwarp();
+      drain(32);
+      __syncwarp();
+      const uint32_t moved = lane + 32 < qn ? qu[lane + 32] : 0u;  // at most 31 left
+      __syncwarp();
+      if (lane + 32 < qn) qu[lane] = moved;
+      qn -= 32;
+      __syncwarp();
+    }
+  }
+  __syncwarp();
+  if (qn > 0) drain(qn);
   bidx = bidx == INT_MAX ? INT_MAX : __ldg(r.blk_pidx + bidx);  // slot -> pair index
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {

@@ -910,6 +910,8 @@ int wb_eval_ext(wb_robot* robot, int64_t B, const float* q, const float* qd, con
   if (kernel == WB_KERNEL_AUTO)
     kernel = (tree_ok && (link_pose || !pairs_wanted)) ? WB_KERNEL_TREE : WB_KERNEL_FUSED;
   cudaError_t e;
+  const bool cull = kernel != WB_KERNEL_TREE_NOCULL;
+  if (kernel == WB_KERNEL_TREE_NOCULL) kernel = WB_KERNEL_TREE;
   if (kernel == WB_KERNEL_PLAIN) {
     if (!plain_fits(robot->dev))
       return fail(WB_ETOOBIG, "plain kernel supports at most 64 links and 256 spheres");
@@ -933,7 +935,7 @@ int wb_eval_ext(wb_robot* robot, int64_t B, const float* q, const float* qd, con
         if (bps < 1) return fail(WB_ETOOBIG, "pair kernel does not fit on an SM");
         const int64_t need = (B + warps - 1) / warps;
         const int grid = (int)std::min<int64_t>(need, (int64_t)bps * robot->num_sms);
-        e = launch_pair(robot->dev, robot->sched32, a, grid, warps, s);
+        e = launch_pair(robot->dev, robot->sched32, a, grid, warps, s, cull);
       }
     }
   } else if (kernel == WB_KERNEL_FUSED) {
@@ -950,6 +952,13 @@ int wb_eval_ext(wb_robot* robot, int64_t B, const float* q, const float* qd, con
 
 int wb_self_collision(wb_robot* robot, int64_t B, const float* link_pose, float* sphere,
                       float* d_min, int32_t* worst_pair, uint32_t* pair_bits, void* stream) {
+  return wb_self_collision_tuned(robot, B, link_pose, sphere, d_min, worst_pair, pair_bits,
+                                 nullptr, stream);
+}
+
+int wb_self_collision_tuned(wb_robot* robot, int64_t B, const float* link_pose, float* sphere,
+                            float* d_min, int32_t* worst_pair, uint32_t* pair_bits,
+                            const wb_tune* tune, void* stream) {
   g_err.clear();
   if (!robot) return fail(WB_EINVAL, "robot is NULL");
   if (B < 0) return fail(WB_EINVAL, "B < 0");
@@ -965,14 +974,19 @@ int wb_self_collision(wb_robot* robot, int64_t B, const float* link_pose, float*
   DeviceGuard guard(robot->device);
   FwdArgs a{B, nullptr, nullptr, nullptr, const_cast<float*>(link_pose), sphere, d_min,
             worst_pair, nullptr, pair_bits};
-  const int warps = 8;
+  const int kernel = tune ? tune->kernel : WB_KERNEL_AUTO;
+  if (kernel != WB_KERNEL_AUTO && kernel != WB_KERNEL_TREE && kernel != WB_KERNEL_TREE_NOCULL)
+    return fail(WB_EINVAL, "the pair kernel takes TREE (culled) or TREE_NOCULL");
+  const int warps = (tune && tune->blocks_per_sm) ? tune->blocks_per_sm : 8;
+  if (warps < 1 || warps > 8) return fail(WB_EINVAL, "pair warps per block must be in [1, 8]");
   int bps = 0;
   cudaError_t e = pair_max_blocks_per_sm(robot->dev, warps, pair_bits != nullptr, &bps);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
   if (bps < 1) return fail(WB_ETOOBIG, "pair kernel does not fit on an SM");
   const int64_t need = (B + warps - 1) / warps;
   const int grid = (int)std::min<int64_t>(need, (int64_t)bps * robot->num_sms);
-  e = launch_pair(robot->dev, robot->sched32, a, grid, warps, static_cast<cudaStream_t>(stream));
+  e = launch_pair(robot->dev, robot->sched32, a, grid, warps, static_cast<cudaStream_t>(stream),
+                  kernel != WB_KERNEL_TREE_NOCULL);
   if (e != cudaSuccess) return cuda_fail(e, "wb_self_collision launch");
   return WB_OK;
 }
@@ -1088,6 +1102,7 @@ int wb_eval_backward_ext(wb_robot* robot, int64_t B, const float* q, const float
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bool tree_ok = robot->dev.maxdepth <= tree_max_depth();
   if (kernel == WB_KERNEL_AUTO) kernel = tree_ok ? WB_KERNEL_TREE : WB_KERNEL_FUSED;
+  if (kernel == WB_KERNEL_TREE_NOCULL) kernel = WB_KERNEL_TREE;  // no pair stage here
   cudaError_t e;
   if (kernel == WB_KERNEL_PLAIN) {
     if (!plain_fits(robot->dev))

@@ -246,7 +246,7 @@ size_t tree_seg_smem(const DevRobot& r, int segments, int threads, bool fwd);
 int tree_max_depth();
 size_t pair_smem(const DevRobot& r, int warps, bool bits);
 cudaError_t launch_pair(const DevRobot& r, const PairSchedule32& ps, const FwdArgs& a, int grid,
-                        int warps, cudaStream_t s);
+                        int warps, cudaStream_t s, bool cull = true);
 cudaError_t pair_max_blocks_per_sm(const DevRobot& r, int warps, bool bits, int* out);
 cudaError_t launch_plain_fwd(const DevRobot& r, const FwdArgs& a, int threads, cudaStream_t s);
 cudaError_t launch_plain_bwd(const DevRobot& r, const BwdArgs& a, int threads, cudaStream_t s);

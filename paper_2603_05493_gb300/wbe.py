@@ -53,6 +53,7 @@ class Tune:
 PLAIN = Tune(kernel=L.WB_KERNEL_PLAIN)
 FUSED = Tune(kernel=L.WB_KERNEL_FUSED)
 TREE = Tune(kernel=L.WB_KERNEL_TREE)
+TREE_NOCULL = Tune(kernel=L.WB_KERNEL_TREE_NOCULL)
 
 
 def _inertial_struct(keep, mass, com, inertia, pm_link=None, pm_mass=None, pm_pos=None):
@@ -190,15 +191,18 @@ class Robot:
         return o
 
     def self_collision(self, link_pose, *, sphere=True, dmin=True, bits=False, out=None,
-                       stream=None):
+                       tune: Tune | None = None, stream=None):
         """Spheres and the pair map-reduce from given world link poses
-        (B, n, 12); returns a dict with sphere, dmin, worst, bits."""
+        (B, n, 12); returns a dict with sphere, dmin, worst, bits.  tune:
+        TREE (default, culled blocks) or Tune(kernel=TREE_NOCULL)."""
         B = link_pose.shape[0]
         o = out if out is not None else self.empty_outputs(B, pose=False, sphere=sphere,
                                                            dmin=dmin, tau=False, bits=bits)
-        L.check(self.lib.wb_self_collision(self.handle, B, _ptr(link_pose), _ptr(o.get("sphere")),
-                                           _ptr(o.get("dmin")), _ptr(o.get("worst")),
-                                           _ptr(o.get("bits")), _stream(stream)),
+        t = (tune or Tune()).c()
+        L.check(self.lib.wb_self_collision_tuned(self.handle, B, _ptr(link_pose),
+                                                 _ptr(o.get("sphere")), _ptr(o.get("dmin")),
+                                                 _ptr(o.get("worst")), _ptr(o.get("bits")),
+                                                 C.byref(t), _stream(stream)),
                 "wb_self_collision")
         return o
 

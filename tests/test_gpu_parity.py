@@ -34,13 +34,14 @@ def O():
 def kernels(W):
     return {"plain": W.PLAIN,
             "tree": W.TREE,
+            "tree_nocull": W.TREE_NOCULL,
             "fused4": W.Tune(kernel=2, lanes_per_config=4),
             "fused8": W.Tune(kernel=2, lanes_per_config=8),
             "fused16": W.Tune(kernel=2, lanes_per_config=16),
             "fused32": W.Tune(kernel=2, lanes_per_config=32)}
 
 
-KERNEL_NAMES = ["plain", "tree", "fused4", "fused8", "fused16", "fused32"]
+KERNEL_NAMES = ["plain", "tree", "tree_nocull", "fused4", "fused8", "fused16", "fused32"]
 
 _robots = {}
 
