@@ -63,12 +63,12 @@ TREE_SRC = ["paper_2603_05493_gb300/csrc/k_tree.cu", "paper_2603_05493_gb300/csr
 PAIR_SRC = ["paper_2603_05493_gb300/csrc/k_pair.cu", "paper_2603_05493_gb300/csrc/pair_body.cuh",
             "paper_2603_05493_gb300/csrc/spatial.cuh"]
 MEASURED_TRAFFIC = {  # profiles/humanoid48_kernel_traffic.md
-    "tree_fwd": {"src": TREE_SRC, "sha256": "de3587a342b3abe969f82aecc98fa0d002148da2427bb892d7ef64eba0043037",
-                 "bytes_per_eval": (48.0e6 + 212.4e6) / 24576},
-    "pair": {"src": PAIR_SRC, "sha256": "f39839b5d1204aadc8880251ed0d2c25fb5d647d0f01814ee912cdbbd20e7aa8",
-             "bytes_per_eval": (58.0e6 + 12.0e6) / 24576},
-    "tree_bwd": {"src": TREE_SRC, "sha256": "de3587a342b3abe969f82aecc98fa0d002148da2427bb892d7ef64eba0043037",
-                 "bytes_per_eval": (295.5e6 + 272.7e6) / 24576},
+    "tree_fwd": {"src": TREE_SRC, "sha256": "dfdf529911cb14f0da1b79df668c911c732b8f4127c735f8e49a8259739e5e6b",
+                 "bytes_per_eval": (46.8e6 + 196.1e6) / 24576},
+    "pair": {"src": PAIR_SRC, "sha256": "c0f00e126b5027b8eb78ef9b1137c99d21bc21025fc0afc751da0f1a59bdc3b1",
+             "bytes_per_eval": (58.8e6 + 21.4e6) / 24576},
+    "tree_bwd": {"src": TREE_SRC, "sha256": "dfdf529911cb14f0da1b79df668c911c732b8f4127c735f8e49a8259739e5e6b",
+                 "bytes_per_eval": (304.5e6 + 259.5e6) / 24576},
 }
 
 
