@@ -362,31 +362,38 @@ def run_ours(args, rank, world, local_rank):
         brute_ms = float(np.mean(tb[2:]))
         assert torch.equal(bout["dmin"], out["dmin"]) and torch.equal(bout["worst"], out["worst"])
 
-    # end to end through the C ABI: pinned host inputs -> device, forward,
-    # backward, results -> pinned host, every step
-    h_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
-             for k, v in out.items() if v is not None}
-    h_gout = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in gout]
+    # end to end through the public API: every step copies the inputs in from
+    # pinned host memory and every output back; wbe.StreamedStep cuts the
+    # batch into chunks so that both copy directions and the kernels overlap
+    e2e_chunks = 2 if args.kernel == "tree" else 1  # measured best on GB300 (4 and 8 slower)
+    Bc = B // e2e_chunks
+    pipe = wbe.StreamedStep(rob, Bc, e2e_chunks, fwd_tune=tune, bwd_tune=btune)
+    h_in, h_out = pipe.host_buffers()
+    src = {"q": q, "qd": qd, "qdd": qdd, "g_pose": gp, "g_sphere": gs, "g_dmin": gm,
+           "g_tau": gt}
+    for c in range(e2e_chunks):
+        sl = slice(c * Bc, (c + 1) * Bc)
+        for k, x in src.items():
+            part = x[:, sl] if k in ("q", "qd", "qdd", "g_tau") else x[sl]
+            h_in[c][k].copy_(torch.from_numpy(np.ascontiguousarray(part)))
+    for _ in range(2):
+        pipe.step(h_in, h_out)
     torch.cuda.synchronize()
     e2e_steps = max(3, min(args.steps, 20))
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
     for _ in range(e2e_steps):
-        for dst, src in zip(d_in, h_in):
-            dst.copy_(src, non_blocking=True)
-        step()
-        for k, v in h_out.items():
-            v.copy_(out[k], non_blocking=True)
-        for hv, dv in zip(h_gout, gout):
-            hv.copy_(dv, non_blocking=True)
+        pipe.step(h_in, h_out)
     t1.record(stream)
     torch.cuda.synchronize()
     clocks.stop()
     e2e_ms = t0.elapsed_time(t1) / e2e_steps
-    h2d = int(sum(x.numel() * x.element_size() for x in h_in))
-    d2h = int(sum(v.numel() * v.element_size() for v in h_out.values()) +
-              sum(x.numel() * x.element_size() for x in h_gout))
+    h2d = int(sum(v.numel() * v.element_size() for c in h_in for v in c.values()))
+    d2h = int(sum(v.numel() * v.element_size() for c in h_out for v in c.values()))
+    # the chunked step computes what the whole-batch step computed
+    ref_chunk = out["dmin"][:Bc].cpu()
+    assert torch.equal(h_out[0]["dmin"], ref_chunk)
 
     kmean = {k: float(np.mean(v)) for k, v in k_ms.items()}
     keys = ("tree_fwd", "pair", "tree_bwd")
@@ -444,7 +451,9 @@ def run_ours(args, rank, world, local_rank):
         "kernels": kernels,
         "pair_full_map_reduce_ms": brute_ms,
         "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "chunks": e2e_chunks,
+                "note": "wbe.StreamedStep: copies in, kernels and copies out of different "
+                        "chunks overlap on three streams"},
         "gpu_launches": (3 if args.kernel == "tree" else 2) * args.steps,
         "clocks": clocks.summary(),
         "cpu_baseline": cpu,

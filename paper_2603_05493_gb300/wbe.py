@@ -398,6 +398,86 @@ def batch_eval_noalloc(robots, problems, q, qd, qdd, pose, sphere=None, dmin=Non
             "wb_batch_eval_noalloc")
 
 
+class StreamedStep:
+    """Forward + backward over a batch whose inputs and outputs live in pinned
+    host memory.  The batch is cut into chunks with their own device buffers;
+    the host-to-device copies of one chunk, the kernels of another and the
+    device-to-host copies of a third run on three streams, so transfers in
+    both directions overlap each other and the evaluation.  Per step and
+    chunk c: inputs host_in[c] = dict(q, qd, qdd [d][Bc], g_pose [Bc][n][12],
+    g_sphere [Bc][S][3], g_dmin [Bc], g_tau [d][Bc]) copied in; outputs
+    host_out[c] = dict(pose, sphere, dmin, worst, tau, gq, gqd, gqdd) copied
+    out.  Events per chunk order consecutive steps (a chunk's inputs are not
+    overwritten before its kernels ran, nor its outputs before they were
+    copied out).  step() enqueues and returns; the caller's current stream
+    waits for the last copy."""
+
+    IN = ("q", "qd", "qdd", "g_pose", "g_sphere", "g_dmin", "g_tau")
+    OUT = ("pose", "sphere", "dmin", "worst", "tau", "gq", "gqd", "gqdd")
+
+    def __init__(self, robot: Robot, chunk: int, n_chunks: int, fwd_tune: Tune | None = None,
+                 bwd_tune: Tune | None = None, run_streams: int = 1):
+        self.rob, self.Bc, self.K = robot, int(chunk), int(n_chunks)
+        self.ft, self.bt = fwd_tune or TREE, bwd_tune or TREE
+        dev, d, n, S, Bc = robot.device, robot.dof, robot.n, robot.S, self.Bc
+        f = dict(device=dev, dtype=torch.float32)
+        self.din, self.dout = [], []
+        for _ in range(self.K):
+            self.din.append({"q": torch.empty((d, Bc), **f), "qd": torch.empty((d, Bc), **f),
+                             "qdd": torch.empty((d, Bc), **f),
+                             "g_pose": torch.empty((Bc, n, 12), **f),
+                             "g_sphere": torch.empty((Bc, S, 3), **f),
+                             "g_dmin": torch.empty((Bc,), **f),
+                             "g_tau": torch.empty((d, Bc), **f)})
+            o = robot.empty_outputs(Bc)
+            o.update(gq=torch.empty((d, Bc), **f), gqd=torch.empty((d, Bc), **f),
+                     gqdd=torch.empty((d, Bc), **f))
+            self.dout.append(o)
+        self.s_in, self.s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        # chunks alternate over run_streams compute streams, so that the kernels
+        # of consecutive chunks may share the GPU
+        self.s_runs = [torch.cuda.Stream(dev) for _ in range(max(1, int(run_streams)))]
+        self.ev_in = [torch.cuda.Event() for _ in range(self.K)]
+        self.ev_run = [torch.cuda.Event() for _ in range(self.K)]
+        self.ev_out = [torch.cuda.Event() for _ in range(self.K)]
+
+    def host_buffers(self):
+        """Pinned host inputs and outputs shaped for step()."""
+        hin = [{k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in c.items()}
+               for c in self.din]
+        hout = [{k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
+                 for k, v in c.items() if k in self.OUT and v is not None} for c in self.dout]
+        return hin, hout
+
+    def step(self, host_in, host_out):
+        rob = self.rob
+        for c in range(self.K):
+            di, do = self.din[c], self.dout[c]
+            self.s_in.wait_event(self.ev_run[c])  # the last step's kernels read di
+            with torch.cuda.stream(self.s_in):
+                for k in self.IN:
+                    di[k].copy_(host_in[c][k], non_blocking=True)
+                self.ev_in[c].record(self.s_in)
+            sr = self.s_runs[c % len(self.s_runs)]
+            sr.wait_event(self.ev_in[c])
+            sr.wait_event(self.ev_out[c])  # the last step's copies read do
+            with torch.cuda.stream(sr):
+                fwd = {"pose": do["pose"], "sphere": None, "dmin": None, "worst": None,
+                       "tau": do["tau"], "bits": None}  # the sweep; pairs follow
+                rob.eval(di["q"], di["qd"], di["qdd"], tune=self.ft, out=fwd, stream=sr)
+                rob.self_collision(do["pose"], out=do, stream=sr)
+                rob.eval_backward(di["q"], di["qd"], di["qdd"], do["worst"], di["g_pose"],
+                                  di["g_sphere"], di["g_dmin"], di["g_tau"], tune=self.bt,
+                                  out=(do["gq"], do["gqd"], do["gqdd"]), stream=sr)
+                self.ev_run[c].record(sr)
+            self.s_out.wait_event(self.ev_run[c])
+            with torch.cuda.stream(self.s_out):
+                for k, v in host_out[c].items():
+                    v.copy_(do[k], non_blocking=True)
+                self.ev_out[c].record(self.s_out)
+        torch.cuda.current_stream().wait_event(self.ev_out[self.K - 1])  # s_out is in order
+
+
 def descriptor_hash(desc) -> str:
     """Content hash of a robot description (the autotune cache key)."""
     import hashlib

@@ -121,3 +121,37 @@ def test_batch_graph_capture_and_replay(W):
         assert torch.equal(a, b)
     # and the earlier (pre-capture) results differ from the replayed ones
     assert not torch.equal(ref_o["dmin"], go["dmin"])
+
+
+def test_streamed_step_matches_direct_calls(W):
+    """wbe.StreamedStep (chunks, three streams, pinned host buffers) gives
+    the same outputs as the direct calls on the whole batch, twice in a row."""
+    desc = R.r23()
+    rob = W.Robot(desc, device=0)
+    K, Bc = 3, 40
+    B = K * Bc
+    q, qd, qdd = I.uniform_states(desc.dof, B, seed=31)
+    gp, gs, gm, gt = I.upstream_grads(desc, B, seed=32)
+    tune = W.Tune(kernel=3, lanes_per_config=1)
+    cuda = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()  # noqa: E731
+    o = rob.eval(cuda(q), cuda(qd), cuda(qdd), tune=tune)
+    g = rob.eval_backward(cuda(q), cuda(qd), cuda(qdd), o["worst"], cuda(gp), cuda(gs),
+                          cuda(gm), cuda(gt), tune=tune)
+    pipe = W.StreamedStep(rob, Bc, K, fwd_tune=tune, bwd_tune=tune, run_streams=2)
+    hin, hout = pipe.host_buffers()
+    src = {"q": q, "qd": qd, "qdd": qdd, "g_pose": gp, "g_sphere": gs, "g_dmin": gm, "g_tau": gt}
+    for c in range(K):
+        sl = slice(c * Bc, (c + 1) * Bc)
+        for k, x in src.items():
+            part = x[:, sl] if k in ("q", "qd", "qdd", "g_tau") else x[sl]
+            hin[c][k].copy_(torch.from_numpy(np.ascontiguousarray(part)))
+    for _ in range(2):
+        pipe.step(hin, hout)
+        torch.cuda.synchronize()
+        for c in range(K):
+            sl = slice(c * Bc, (c + 1) * Bc)
+            ref = {"pose": o["pose"][sl], "sphere": o["sphere"][sl], "dmin": o["dmin"][sl],
+                   "worst": o["worst"][sl], "tau": o["tau"][:, sl], "gq": g[0][:, sl],
+                   "gqd": g[1][:, sl], "gqdd": g[2][:, sl]}
+            for k, v in ref.items():
+                assert torch.equal(hout[c][k], v.cpu()), (c, k)
