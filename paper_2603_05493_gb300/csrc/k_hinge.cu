@@ -8,22 +8,26 @@
 //
 // One warp per configuration (persistent grid): the warp stages the
 // configuration's link poses into shared memory, places its spheres
-// (Sec. 6.1.1), then each lane walks the partner lists of its spheres
-// (s = lane, lane + 32, ...; partners ascending).  A sphere accumulates its
-// own gradient over all its partners in list order, and the cost counts each
-// pair once, at its lower sphere, in the same order, then a fixed shuffle
-// tree adds the lanes: no atomics, the same result on every run.  Pairs are
-// first screened without a square root, |c_i - c_j|^2 < (eta + r_i + r_j)^2
-// widened by a rounding margin, and the exact distance decides.
+// (Sec. 6.1.1) and bounds every group of 4 with a sphere (C_g, R_g), then each
+// lane walks the partner groups of its spheres (s = lane, lane + 32, ...;
+// groups ascending).  A partner group whose bound is farther than eta,
+// |c_s - C_g| - r_s - R_g >= eta (every partner in it then has d >= eta),
+// is skipped after one test; otherwise its partners (a 4-bit mask) are tested
+// -- without a square root, |c_s - c_p|^2 < (eta + r_s + r_p)^2 widened by a
+// rounding margin -- and the exact distance decides.  A sphere sums its own
+// gradient over its partners in list order, the cost counts each pair once,
+// at its lower sphere, in the same order, and a fixed shuffle tree adds the
+// lanes: no atomics, the same result on every run.
 #include "spatial.cuh"
 
 namespace wbe {
 
-// per warp: link poses, then one float4 (x, y, z, r) per sphere plus the
-// sentinel sphere S that pads the partner lists
+// per warp: link poses, one float4 (x, y, z, r) per sphere (padded to whole
+// groups), one float4 (C, R) per group
 static __host__ __device__ int hinge_words(int n, int S) {
   const int p = (12 * n + 31) & ~31;
-  return p + 4 * (((S + 1) + 7) & ~7);
+  const int s4 = (S + 3) & ~3;
+  return p + 4 * ((s4 + 7) & ~7) + 4 * (((s4 / 4) + 7) & ~7);
 }
 
 size_t hinge_smem_per_warp(const DevRobot& r) { return sizeof(float) * hinge_words(r.n, r.S); }
@@ -34,35 +38,60 @@ __global__ void __launch_bounds__(256) hinge_kernel(DevRobot r, HingeArgs A) {
   const int n = r.n, S = r.S;
   float* ws = smem + (size_t)warp * hinge_words(n, S);
   float* P = ws;  // link poses
+  const int s4 = (S + 3) & ~3, Sg = s4 / 4;
   float4* cs = reinterpret_cast<float4*>(ws + ((12 * n + 31) & ~31));  // spheres
+  float4* gb = cs + ((s4 + 7) & ~7);                                  // group bounds
   const float eta = A.eta, w = A.w;
   for (int64_t b = (int64_t)blockIdx.x * wpb + warp; b < A.B; b += (int64_t)gridDim.x * wpb) {
     const float4* src = reinterpret_cast<const float4*>(A.pose + b * (int64_t)n * 12);
     float4* dst = reinterpret_cast<float4*>(P);
     for (int i = lane; i < 3 * n; i += 32) dst[i] = __ldg(src + i);
     __syncwarp();
-    for (int s = lane; s < S; s += 32) {
-      const float4 sp = __ldg(r.sph + s);
-      const float* T = P + 12 * __ldg(r.sph_link + s);
-      const float cl[3] = {sp.x, sp.y, sp.z};
-      float c[3];
-      rot(T, cl, c);
-      cs[s] = make_float4(c[0] + T[9], c[1] + T[10], c[2] + T[11], sp.w);
+    for (int s = lane; s < s4; s += 32) {
+      if (s < S) {
+        const float4 sp = __ldg(r.sph + s);
+        const float* T = P + 12 * __ldg(r.sph_link + s);
+        const float cl[3] = {sp.x, sp.y, sp.z};
+        float c[3];
+        rot(T, cl, c);
+        cs[s] = make_float4(c[0] + T[9], c[1] + T[10], c[2] + T[11], sp.w);
+      } else {
+        cs[s] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // padding, never a partner
+      }
     }
-    if (lane == 0) cs[S] = make_float4(1e18f, 1e18f, 1e18f, 0.0f);  // the padding sentinel
+    __syncwarp();
+    for (int g = lane; g < Sg; g += 32) {  // group bounding spheres
+      const int s1 = min(S, 4 * g + 4);
+      float cx = 0.0f, cy = 0.0f, cz = 0.0f;
+      for (int s = 4 * g; s < s1; ++s) {
+        cx += cs[s].x;
+        cy += cs[s].y;
+        cz += cs[s].z;
+      }
+      const float inv = 1.0f / (float)max(s1 - 4 * g, 1);
+      cx *= inv;
+      cy *= inv;
+      cz *= inv;
+      float R = 0.0f;
+      for (int s = 4 * g; s < s1; ++s)
+        R = fmaxf(R, sqrtf(dist2(cx, cy, cz, cs[s].x, cs[s].y, cs[s].z)) + cs[s].w);
+      gb[g] = make_float4(cx, cy, cz, fmaf(R, 1e-6f, R) + 1e-6f);  // widened for rounding
+    }
     __syncwarp();
     float cost = 0.0f;
     for (int s = lane; s < S; s += 32) {
       const float4 me = cs[s];
       float gx = 0.0f, gy = 0.0f, gz = 0.0f;
-      const int e0 = __ldg(r.adj_start + s), e1 = __ldg(r.adj_start + s + 1);
-      const ushort4* a4 = reinterpret_cast<const ushort4*>(r.adj);
-      for (int e = e0; e < e1; e += 4) {
-        const ushort4 pq = __ldg(a4 + (e >> 2));
-        const int ps[4] = {pq.x, pq.y, pq.z, pq.w};
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int p = ps[u];
+      const int e1 = __ldg(r.adj_start + s + 1);
+      for (int e = __ldg(r.adj_start + s); e < e1; ++e) {
+        const int ent = __ldg(r.adj + e);
+        const int g = ent & 0xFF;
+        const float4 B4 = gb[g];
+        const float tg = eta + me.w + B4.w;  // skip the group when |c_s - C_g| >= tg
+        const float tgm = fmaf(tg, 1e-5f, tg) + 1e-6f;
+        if (tg <= -1e-6f || dist2(me.x, me.y, me.z, B4.x, B4.y, B4.z) >= tgm * tgm) continue;
+        for (int m = ent >> 8; m; m &= m - 1) {
+          const int p = 4 * g + __ffs(m) - 1;
           const float4 o = cs[p];
           const float dx = me.x - o.x, dy = me.y - o.y, dz = me.z - o.z;
           const float n2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));

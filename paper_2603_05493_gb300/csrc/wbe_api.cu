@@ -426,23 +426,26 @@ static int plan_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs
   const int P = (int)pl.size();
   std::vector<int2> pairs_dev(std::max(P, 1), int2{0, 0});
   for (int p = 0; p < P; ++p) pairs_dev[p] = int2{pl[p].first, pl[p].second};
-  {  // adjacency: partners of every sphere, ascending
-    std::vector<std::vector<int16_t>> nb(S);
+  {  // adjacency: per sphere, its partner groups of 4 (ascending) with a
+     // 4-bit mask of the partners in the group: entry = group | mask << 8
+    std::vector<std::vector<int>> nb(S);
     for (int p = 0; p < P; ++p) {
-      nb[pl[p].first].push_back((int16_t)pl[p].second);
-      nb[pl[p].second].push_back((int16_t)pl[p].first);
+      nb[pl[p].first].push_back(pl[p].second);
+      nb[pl[p].second].push_back(pl[p].first);
     }
-    // each list padded to a multiple of 4 with the sentinel S (a sphere the
-    // hinge kernel places far away), so partners load four at a time
     H.adj_start.assign(S + 1, 0);
     for (int s2 = 0; s2 < S; ++s2) {
       std::sort(nb[s2].begin(), nb[s2].end());
       H.adj_start[s2] = (int32_t)H.adj.size();
-      H.adj.insert(H.adj.end(), nb[s2].begin(), nb[s2].end());
-      while (H.adj.size() % 4) H.adj.push_back((int16_t)S);
+      for (size_t i = 0; i < nb[s2].size();) {
+        const int g = nb[s2][i] >> 2;
+        int mask = 0;
+        while (i < nb[s2].size() && (nb[s2][i] >> 2) == g) mask |= 1 << (nb[s2][i++] & 3);
+        H.adj.push_back((int16_t)(g | mask << 8));
+      }
     }
     H.adj_start[S] = (int32_t)H.adj.size();
-    while (H.adj.size() < 4) H.adj.push_back((int16_t)S);
+    if (H.adj.empty()) H.adj.push_back(0);
   }
 
   // ---- 4x4 group blocks ----

@@ -65,10 +65,11 @@ struct DevRobot {
   const int2* pairs;         // [P] sorted row-major
   const float4* grp_rad;     // [Sg] radii of the 4 spheres of a group (0 pad)
   const int32_t* blk_pidx;   // [nblk][16] pair index of (4gi+a, 4gj+b) or -1
-  // sphere adjacency of the masked pairs (each pair listed at both spheres,
-  // partners ascending, each list padded to a multiple of 4 with S): the
+  // sphere adjacency of the masked pairs, by partner group of 4: per sphere
+  // (each pair listed at both spheres), entries group | mask << 8 with
+  // ascending groups and bit a of mask = sphere 4 group + a is a partner; the
   // summed collision hinge walks it per sphere
-  const int32_t* adj_start;  // [S+1], multiples of 4
+  const int32_t* adj_start;  // [S+1]
   const int16_t* adj;
 };
 
