@@ -199,16 +199,24 @@ def bspline_vjp(gq, gqd, gqdd, n_traj: int, K: int, T: int, dt: float):
     return Ub
 
 
-def trajopt_cost(tau, dmin, tau_lo, tau_hi, w_coll):
+def trajopt_cost(tau, dmin, tau_lo, tau_hi, w_coll, qd=None, qdd=None, smooth=0.0,
+                 length=0.0, energy=0.0, dt=1.0):
     """Per-configuration cost of the trajectory-optimisation workload and its
-    upstream gradients (torque-limit hinges per joint plus the self-collision
-    hinge on the worst pair):
-        cost_b = sum_j [max(0, tau_jb - hi_j) + max(0, lo_j - tau_jb)]
+    gradients: the motion terms of the problem's loss, smooth ||qdd||^2,
+    length ||qd||^2 and energy ||(qd . tau) dt||^2 with their weights, plus
+    the torque-limit hinges per joint and the self-collision hinge on the
+    worst pair:
+        cost_b = smooth |qdd_b|^2 + length |qd_b|^2
+                 + energy dt^2 sum_j (qd_jb tau_jb)^2
+                 + sum_j [max(0, tau_jb - hi_j) + max(0, lo_j - tau_jb)]
                  + w max(0, -dmin_b),
-        dL/dtau_jb = [tau_jb > hi_j] - [tau_jb < lo_j],
-        dL/ddmin_b = -w [dmin_b < 0]
-    (a kink takes the zero one-sided derivative).  tau [d][B], dmin [B],
-    limits [d].  Returns cost [B], g_tau [d][B], g_dmin [B] in float64."""
+        dL/dtau_jb  = 2 energy dt^2 qd_jb^2 tau_jb + [tau_jb > hi_j] - [tau_jb < lo_j],
+        dL/ddmin_b  = -w [dmin_b < 0],
+        dL/dqd_jb   = 2 length qd_jb + 2 energy dt^2 qd_jb tau_jb^2   (direct),
+        dL/dqdd_jb  = 2 smooth qdd_jb                                 (direct)
+    (a kink takes the zero one-sided derivative).  tau, qd, qdd [d][B],
+    dmin [B], limits [d].  Returns cost [B], g_tau [d][B], g_dmin [B] and,
+    when qd / qdd are given, g_qd, g_qdd [d][B], all float64."""
     tau = np.asarray(tau, np.float64)
     dmin = np.asarray(dmin, np.float64)
     lo = np.asarray(tau_lo, np.float64)[:, None]
@@ -218,7 +226,17 @@ def trajopt_cost(tau, dmin, tau_lo, tau_hi, w_coll):
     cost = (over + under).sum(axis=0) + w_coll * np.maximum(0.0, -dmin)
     g_tau = (tau > hi).astype(np.float64) - (tau < lo).astype(np.float64)
     g_dmin = -w_coll * (dmin < 0).astype(np.float64)
-    return cost, g_tau, g_dmin
+    if qd is None and qdd is None:
+        return cost, g_tau, g_dmin
+    qd = np.zeros_like(tau) if qd is None else np.asarray(qd, np.float64)
+    qdd = np.zeros_like(tau) if qdd is None else np.asarray(qdd, np.float64)
+    e = energy * dt * dt
+    cost = cost + smooth * (qdd ** 2).sum(axis=0) + length * (qd ** 2).sum(axis=0) \
+        + e * ((qd * tau) ** 2).sum(axis=0)
+    g_tau = g_tau + 2.0 * e * qd ** 2 * tau
+    g_qd = 2.0 * length * qd + 2.0 * e * qd * tau ** 2
+    g_qdd = 2.0 * smooth * qdd
+    return cost, g_tau, g_dmin, g_qd, g_qdd
 
 
 def fext_gradient(robot, q, qd, qdd, fext, g_tau):
@@ -290,26 +308,34 @@ def pair_hinge(robot, q, eta: float, w: float):
     return cost, g
 
 
-def trajopt_value(robot, U, T: int, dt: float, tau_lo, tau_hi, w_coll):
+def trajopt_value(robot, U, T: int, dt: float, tau_lo, tau_hi, w_coll, smooth=0.0,
+                  length=0.0, energy=0.0):
     """Total cost L(U) = sum_b cost_b over every sample of every trajectory:
-    B-spline states -> whole-body evaluation -> cost."""
+    B-spline states -> whole-body evaluation -> cost (the energy term uses
+    the sample spacing of the B-spline, dt (K-3) / (T-1))."""
     q, qd, qdd = bspline(U, T, dt)
     ev = evaluate(robot, q, qd, qdd, want=("dmin", "tau"))
-    cost, _, _ = trajopt_cost(ev["tau"], ev["dmin"], tau_lo, tau_hi, w_coll)
+    K = np.asarray(U).shape[2]
+    cost = trajopt_cost(ev["tau"], ev["dmin"], tau_lo, tau_hi, w_coll, qd, qdd, smooth, length,
+                        energy, dt * (K - 3) / (T - 1))[0]
     return float(cost.sum()), ev
 
 
-def trajopt_gradient(robot, U, T: int, dt: float, tau_lo, tau_hi, w_coll):
+def trajopt_gradient(robot, U, T: int, dt: float, tau_lo, tau_hi, w_coll, smooth=0.0,
+                     length=0.0, energy=0.0):
     """dL/dU by the chain of the pieces above: cost gradients -> VJP of the
-    whole-body evaluation (dual numbers) -> VJP of the B-spline.  Returns
-    (Ubar [n_traj][d][K], per-configuration cost [B], evaluation dict)."""
+    whole-body evaluation (dual numbers) plus the cost's direct qd / qdd
+    gradients -> VJP of the B-spline.  Returns (Ubar [n_traj][d][K],
+    per-configuration cost [B], evaluation dict)."""
     U = np.asarray(U, np.float64)
     n_traj, d, K = U.shape
     q, qd, qdd = bspline(U, T, dt)
     ev = evaluate(robot, q, qd, qdd, want=("dmin", "tau"))
-    cost, g_tau, g_dmin = trajopt_cost(ev["tau"], ev["dmin"], tau_lo, tau_hi, w_coll)
+    cost, g_tau, g_dmin, d_qd, d_qdd = trajopt_cost(ev["tau"], ev["dmin"], tau_lo, tau_hi,
+                                                    w_coll, qd, qdd, smooth, length, energy,
+                                                    dt * (K - 3) / (T - 1))
     gq, gqd, gqdd = gradient(robot, q, qd, qdd, g_dmin=g_dmin, g_tau=g_tau)
-    return bspline_vjp(gq, gqd, gqdd, n_traj, K, T, dt), cost, ev
+    return bspline_vjp(gq, gqd + d_qd, gqdd + d_qdd, n_traj, K, T, dt), cost, ev
 
 
 def max_threads() -> int:

@@ -711,3 +711,48 @@ def test_fext_gradient_is_minus_the_link_frame_jacobian(oracle_lib):
             ang = np.einsum("bji,bj->bi", Rk, J[:, k, 3:, j])
             lin = np.einsum("bji,bj->bi", Rk, J[:, k, :3, j])
             assert np.allclose(g[:, k], -np.concatenate([ang, lin], axis=1), atol=1e-9)
+
+
+def test_motion_cost_terms_closed_form(oracle_lib):
+    """smooth |qdd|^2 + length |qd|^2 + energy ||(qd . tau) dt||^2 on hand
+    numbers, with their tau / qd / qdd gradients."""
+    O = oracle_lib
+    tau = np.array([[2.0], [-3.0]])
+    qd = np.array([[0.5], [4.0]])
+    qdd = np.array([[1.0], [-2.0]])
+    lo, hi = np.array([-10.0, -10.0]), np.array([10.0, 10.0])
+    cost, g_tau, g_dmin, g_qd, g_qdd = O.trajopt_cost(tau, np.array([1.0]), lo, hi, 1.0, qd, qdd,
+                                                      smooth=0.5, length=0.25, energy=2.0,
+                                                      dt=0.1)
+    # smooth 0.5 (1 + 4) = 2.5; length 0.25 (0.25 + 16) = 4.0625;
+    # energy 2 * 0.01 * ((0.5 * 2)^2 + (4 * -3)^2) = 0.02 * 145 = 2.9
+    assert cost[0] == pytest.approx(2.5 + 4.0625 + 2.9, abs=1e-12)
+    e = 2.0 * 0.01
+    assert np.allclose(g_tau[:, 0], [2 * e * 0.25 * 2.0, 2 * e * 16.0 * -3.0], atol=1e-12)
+    assert np.allclose(g_qd[:, 0], [2 * 0.25 * 0.5 + 2 * e * 0.5 * 4.0,
+                                    2 * 0.25 * 4.0 + 2 * e * 4.0 * 9.0], atol=1e-12)
+    assert np.allclose(g_qdd[:, 0], [1.0, -2.0], atol=1e-12)
+    assert g_dmin[0] == 0.0
+
+
+def test_trajopt_chain_with_motion_terms_matches_finite_differences(oracle_lib):
+    """The chain gradient with smooth, length and energy terms (their direct
+    qd / qdd gradients added before the B-spline VJP) equals central
+    differences of the total cost."""
+    O = oracle_lib
+    rob = R.r7()
+    rng = np.random.default_rng(9)
+    n_traj, K, T, dt = 2, 6, 9, 0.25
+    U = rng.uniform(-1.0, 1.0, size=(n_traj, rob.dof, K))
+    lo, hi = -1e3 * np.ones(rob.dof), 1e3 * np.ones(rob.dof)  # hinges inactive
+    kw = dict(smooth=0.01, length=0.1, energy=0.05)
+    Ub, _, _ = O.trajopt_gradient(rob, U, T, dt, lo, hi, 0.0, **kw)
+    h = 1e-6
+    for flat in rng.choice(U.size, size=10, replace=False):
+        idx = np.unravel_index(flat, U.shape)
+        Up, Um = U.copy(), U.copy()
+        Up[idx] += h
+        Um[idx] -= h
+        fd = (O.trajopt_value(rob, Up, T, dt, lo, hi, 0.0, **kw)[0] -
+              O.trajopt_value(rob, Um, T, dt, lo, hi, 0.0, **kw)[0]) / (2 * h)
+        assert abs(fd - Ub[idx]) <= 1e-6 * max(1.0, abs(Ub[idx])), (idx, fd, Ub[idx])
