@@ -494,10 +494,13 @@ def trajopt_work(desc, K, T):
         "bspline_fwd": {"flops": 84 * d, "bytes": 4 * 3 * d + 4 * d * K // T},
         "tree_fwd": {"flops": 150 * nm + 330 * n, "bytes": 4 * (3 * d + 12 * n + d)},
         "pair": {"flops": 18 * S + 11 * P, "bytes": 4 * (12 * n + 2)},
-        "cost": {"flops": 6 * d + 3, "bytes": 4 * (2 * d + 3)},
+        # hinges and motion terms: tau, qd, qdd, d_min in; cost, g_tau, g_qd,
+        # g_qdd, g_dmin out
+        "cost": {"flops": 22 * d + 3, "bytes": 4 * (6 * d + 3)},
         "tree_bwd": {"flops": 150 * nm + 330 * n + 660 * n + 60 * n,
                      "bytes": 4 * (3 * d + 2 + d + 3 * d)},
-        "bspline_bwd": {"flops": 24 * d, "bytes": 4 * 3 * d + 4 * d * K // T},
+        # five upstream gradients (three of the sweep, two direct ones of the cost)
+        "bspline_bwd": {"flops": 26 * d, "bytes": 4 * 5 * d + 4 * d * K // T},
         # summed hinge: every pair screened from both spheres (sqrt-free, 8 flops)
         "hinge": {"flops": 18 * S + 16 * P, "bytes": 4 * (12 * n + 3 * S + 1)},
     }
@@ -507,8 +510,10 @@ def run_trajopt(args, rank=0, world=1, local_rank=0):
     """Trajectory-optimisation gradient step on the 48-DoF humanoid with 3 kg
     hand payloads: 512 seeds x 16 control points per joint -> 64 B-spline
     samples each (32768 configurations) -> FK + RNEA sweep -> self-collision
-    -> torque-limit + collision hinge cost -> adjoint sweep -> dL/dU.
-    Value = configurations per second."""
+    -> torque-limit + collision hinges and the smooth / length / energy
+    terms -> adjoint sweep -> dL/dU (the cost's direct qd / qdd gradients
+    join the sweep's in the B-spline adjoint).  Value = configurations per
+    second."""
     import torch
     from paper_2603_05493_gb300 import build
     build()
@@ -539,7 +544,10 @@ def run_trajopt(args, rank=0, world=1, local_rank=0):
     cost = torch.empty((B,), device=dev)
     g_tau = torch.empty((d, B), device=dev)
     g_dmin = torch.empty((B,), device=dev)
+    g_qd, g_qdd = torch.empty((d, B), device=dev), torch.empty((d, B), device=dev)
     gout = tuple(torch.empty((d, B), device=dev) for _ in range(3))
+    # the energy term's dt: the time between consecutive samples
+    dt_sample = dt * (K - 3) / (T - 1)
     gU = torch.empty((n_traj, d, K), device=dev)
     stream = torch.cuda.current_stream()
     hinge = args.collision == "hinge"
@@ -560,8 +568,10 @@ def run_trajopt(args, rank=0, world=1, local_rank=0):
         else:  # the worst pair
             rob.self_collision(out["pose"], out=pair_out)
         mark(3)
-        wbe.trajopt_cost(out["tau"], None if hinge else out["dmin"], lo, hi,
-                         CF.COLLISION_WEIGHT, cost, g_tau, None if hinge else g_dmin)
+        wbe.trajopt_cost_ext(out["tau"], None if hinge else out["dmin"], qd, qdd, lo, hi,
+                             CF.COLLISION_WEIGHT, CF.SMOOTH_WEIGHT, CF.LENGTH_WEIGHT,
+                             CF.ENERGY_WEIGHT, dt_sample,
+                             out=(cost, g_tau, None if hinge else g_dmin, g_qd, g_qdd))
         mark(4)
         if hinge:
             rob.eval_backward(q, qd, qdd, None, None, g_sph, None, g_tau, tune=btune, out=gout)
@@ -569,7 +579,7 @@ def run_trajopt(args, rank=0, world=1, local_rank=0):
             rob.eval_backward(q, qd, qdd, out["worst"], None, None, g_dmin, g_tau, tune=btune,
                               out=gout)
         mark(5)
-        wbe.bspline_backward(*gout, n_traj, K, T, dt, gU)
+        wbe.bspline_backward(*gout, n_traj, K, T, dt, gU, gqd_add=g_qd, gqdd_add=g_qdd)
 
     flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
     for _ in range(max(args.warmup, 3)):
@@ -638,15 +648,17 @@ def run_trajopt(args, rank=0, world=1, local_rank=0):
                             "bytes_per_eval": w["bytes"], "traffic": None})
     dom = max(k_ms, key=k_ms.get)
     line = {
-        "metric": "trajopt48 evals/s (B-spline -> FK+self-coll+RNEA -> hinge cost -> "
-                  "adjoint -> dL/dU)",
+        "metric": "trajopt48 evals/s (B-spline -> FK+self-coll+RNEA -> hinge + motion cost "
+                  "-> adjoint -> dL/dU)",
         "value": job_value(world, B, step_ms), "unit": "evals/s", "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "trajopt48: 48-DoF tree + 3 kg hand payloads, 512 seeds x 64 "
                                "B-spline samples (16 control points / joint, dt 0.25 s), "
-                               "torque limits +-30 N m, collision weight 1, " +
+                               "torque limits +-30 N m, collision weight 1, smooth / "
+                               "length / energy weights %g / %g / %g, "
+                               % (CF.SMOOTH_WEIGHT, CF.LENGTH_WEIGHT, CF.ENERGY_WEIGHT) +
                                ("summed hinge over all pairs, activation distance %.3g m"
                                 % CF.ACTIVATION_DISTANCE if hinge else "worst-pair hinge"),
                    "configurations": B,

@@ -355,6 +355,16 @@ int wb_bspline_backward(int64_t n_traj, int32_t d, int32_t K, int32_t T, float d
                         const float* gq, const float* gqd, const float* gqdd, float* gU,
                         void* stream);
 
+/* As wb_bspline_backward, with two more upstream gradients gqd_add and
+ * gqdd_add [d][n_traj*T] (nullable) that add to gqd and gqdd before the
+ * transpose: the direct state gradients of a cost (wb_trajopt_cost_ext)
+ * join those of the dynamics without a separate addition pass.
+ * Deterministic.  Errors as wb_bspline_eval. */
+int wb_bspline_backward_ext(int64_t n_traj, int32_t d, int32_t K, int32_t T, float dt,
+                            const float* gq, const float* gqd, const float* gqdd,
+                            const float* gqd_add, const float* gqdd_add, float* gU,
+                            void* stream);
+
 /* Per-configuration cost of trajectory optimisation and its upstream
  * gradients:
  *   cost[b]     = sum_j max(0, tau[j][b] - tau_hi[j]) + max(0, tau_lo[j] - tau[j][b])
@@ -372,6 +382,34 @@ int wb_bspline_backward(int64_t n_traj, int32_t d, int32_t K, int32_t T, float d
 int wb_trajopt_cost(int64_t B, int32_t d, const float* tau, const float* d_min,
                     const float* tau_lo, const float* tau_hi, float w_coll, float* cost,
                     float* g_tau, float* g_dmin, void* stream);
+
+/* Weights of the cost terms of wb_trajopt_cost_ext. */
+typedef struct {
+  float collision; /* w_coll of the worst-pair hinge */
+  float smooth;    /* weight of |qdd|^2 */
+  float length;    /* weight of |qd|^2 */
+  float energy;    /* weight of sum_j (qd_j tau_j dt)^2 */
+  float dt;        /* time between consecutive samples (the energy term's dt) */
+} wb_cost_weights;
+
+/* wb_trajopt_cost with the motion terms of the problem's loss (Sec. 3,
+ * Eq. cost_motion_opt: the smooth, length and energy terms):
+ *   cost[b]     = (wb_trajopt_cost's terms with w_coll = w->collision)
+ *                 + smooth |qdd_b|^2 + length |qd_b|^2
+ *                 + energy dt^2 sum_j (qd[j][b] tau[j][b])^2
+ *   g_tau[j][b] = [tau > tau_hi] - [tau < tau_lo] + 2 energy dt^2 qd^2 tau
+ *   g_dmin[b]   = -w->collision [d_min < 0]
+ *   g_qd[j][b]  = 2 length qd + 2 energy dt^2 qd tau^2   (direct gradient)
+ *   g_qdd[j][b] = 2 smooth qdd                           (direct gradient)
+ * qd, qdd, g_qd, g_qdd [d][B], each nullable (a NULL state is zero, its
+ * terms vanish; a NULL output is not written).  w is a host pointer, read
+ * before the call returns, all five weights finite and dt > 0.  Pass g_qd
+ * and g_qdd to wb_bspline_backward_ext as gqd_add and gqdd_add.
+ * Errors: WB_EINVAL, WB_EDEVICE, WB_ECUDA. */
+int wb_trajopt_cost_ext(int64_t B, int32_t d, const float* tau, const float* d_min,
+                        const float* qd, const float* qdd, const float* tau_lo,
+                        const float* tau_hi, const wb_cost_weights* w, float* cost,
+                        float* g_tau, float* g_dmin, float* g_qd, float* g_qdd, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Forward evaluation of an uneven batch without any device allocation.  The

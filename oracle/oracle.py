@@ -202,7 +202,8 @@ def bspline_vjp(gq, gqd, gqdd, n_traj: int, K: int, T: int, dt: float):
 def trajopt_cost(tau, dmin, tau_lo, tau_hi, w_coll, qd=None, qdd=None, smooth=0.0,
                  length=0.0, energy=0.0, dt=1.0):
     """Per-configuration cost of the trajectory-optimisation workload and its
-    gradients: the motion terms of the problem's loss, smooth ||qdd||^2,
+    gradients: the motion terms of the problem's loss (Sec. 3,
+    Eq. cost_motion_opt), smooth ||qdd||^2,
     length ||qd||^2 and energy ||(qd . tau) dt||^2 with their weights, plus
     the torque-limit hinges per joint and the self-collision hinge on the
     worst pair:

@@ -53,6 +53,11 @@ class wb_tune(C.Structure):
                 ("configs_per_block", C.c_int32), ("blocks_per_sm", C.c_int32)]
 
 
+class wb_cost_weights(C.Structure):
+    _fields_ = [("collision", C.c_float), ("smooth", C.c_float), ("length", C.c_float),
+                ("energy", C.c_float), ("dt", C.c_float)]
+
+
 class wb_problem(C.Structure):
     _fields_ = [("robot", C.c_int32), ("horizon", C.c_int32)]
 
@@ -100,6 +105,10 @@ SIGNATURES = {
     "wb_bspline_backward": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_float, p,
                                       p, p, p, p]),
     "wb_trajopt_cost": (C.c_int, [C.c_int64, C.c_int32, p, p, p, p, C.c_float, p, p, p, p]),
+    "wb_bspline_backward_ext": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_float,
+                                          p, p, p, p, p, p, p]),
+    "wb_trajopt_cost_ext": (C.c_int, [C.c_int64, C.c_int32, p, p, p, p, p, p,
+                                      C.POINTER(wb_cost_weights), p, p, p, p, p, p]),
     "wb_self_collision_hinge": (C.c_int, [p, C.c_int64, p, C.c_float, C.c_float, p, p, p]),
     "wb_kinematics": (C.c_int, [p, C.c_int64, p, C.c_int32, p, p, p, p, p]),
     "wb_self_collision_tuned": (C.c_int, [p, C.c_int64, p, p, p, p, p, C.POINTER(wb_tune), p]),

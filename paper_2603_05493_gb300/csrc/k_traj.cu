@@ -79,6 +79,8 @@ __global__ void __launch_bounds__(256) bspline_bwd_kernel(int64_t n_traj, int d,
                                                           float dt, const float* __restrict__ gq,
                                                           const float* __restrict__ gqd,
                                                           const float* __restrict__ gqdd,
+                                                          const float* __restrict__ gqd2,
+                                                          const float* __restrict__ gqdd2,
                                                           float* gU) {
   extern __shared__ float tab[];  // [T][12] basis rows, then [K-2] first samples
   int* first = reinterpret_cast<int*>(tab + (size_t)T * 12);
@@ -116,39 +118,64 @@ __global__ void __launch_bounds__(256) bspline_bwd_kernel(int64_t n_traj, int d,
       const float* Bs = tab + s * 12;
       float c = 0.0f;
       if (gq) c = fmaf(Bs[l], __ldg(gq + base + s), c);
-      if (gqd) c = fmaf(Bs[4 + l], __ldg(gqd + base + s), c);
-      if (gqdd) c = fmaf(Bs[8 + l], __ldg(gqdd + base + s), c);
+      float gv = gqd ? __ldg(gqd + base + s) : 0.0f;  // the two qd gradients add
+      if (gqd2) gv += __ldg(gqd2 + base + s);
+      c = fmaf(Bs[4 + l], gv, c);
+      float ga = gqdd ? __ldg(gqdd + base + s) : 0.0f;
+      if (gqdd2) ga += __ldg(gqdd2 + base + s);
+      c = fmaf(Bs[8 + l], ga, c);
       acc += c;
     }
   }
   gU[idx] = acc;
 }
 
-// One thread per configuration.
+// One thread per configuration.  The motion terms of the loss (smooth |qdd|^2,
+// length |qd|^2, energy ||(qd . tau) dt||^2 with e = energy dt^2) and the
+// hinges; g_qd / g_qdd are the cost's direct qd / qdd gradients.
 __global__ void __launch_bounds__(256) trajopt_cost_kernel(int64_t B, int d,
                                                            const float* __restrict__ tau,
                                                            const float* __restrict__ d_min,
+                                                           const float* __restrict__ qd,
+                                                           const float* __restrict__ qdd,
                                                            const float* __restrict__ lo,
                                                            const float* __restrict__ hi,
-                                                           float w, float* cost, float* g_tau,
-                                                           float* g_dmin) {
+                                                           float w, float smooth, float length,
+                                                           float e, float* cost, float* g_tau,
+                                                           float* g_dmin, float* g_qd,
+                                                           float* g_qdd) {
   const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (b >= B) return;
   float c = 0.0f;
-  if (tau) {
-    // loads issued eight joints at a time so that their latencies overlap
-    for (int j0 = 0; j0 < d; j0 += 8) {
-      float t[8];
+  // loads issued eight joints at a time so that their latencies overlap
+  for (int j0 = 0; j0 < d; j0 += 8) {
+    float t[8], v[8], a[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) t[u] = j0 + u < d ? __ldg(tau + (int64_t)(j0 + u) * B + b) : 0.0f;
+    for (int u = 0; u < 8; ++u) {
+      const int64_t at = (int64_t)(j0 + u) * B + b;
+      const bool in = j0 + u < d;
+      t[u] = in && tau ? __ldg(tau + at) : 0.0f;
+      v[u] = in && qd ? __ldg(qd + at) : 0.0f;
+      a[u] = in && qdd ? __ldg(qdd + at) : 0.0f;
+    }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int j = j0 + u;
-        if (j >= d) break;
+    for (int u = 0; u < 8; ++u) {
+      const int j = j0 + u;
+      if (j >= d) break;
+      const int64_t at = (int64_t)j * B + b;
+      const float vt = v[u] * t[u];
+      c = fmaf(smooth * a[u], a[u], c);
+      c = fmaf(length * v[u], v[u], c);
+      c = fmaf(e * vt, vt, c);
+      float gt = 2.0f * e * v[u] * vt;
+      if (tau) {
         const float l = __ldg(lo + j), h = __ldg(hi + j);
         c += fmaxf(0.0f, t[u] - h) + fmaxf(0.0f, l - t[u]);
-        if (g_tau) g_tau[(int64_t)j * B + b] = (t[u] > h ? 1.0f : 0.0f) - (t[u] < l ? 1.0f : 0.0f);
+        gt += (t[u] > h ? 1.0f : 0.0f) - (t[u] < l ? 1.0f : 0.0f);
       }
+      if (g_tau) g_tau[at] = gt;
+      if (g_qd) g_qd[at] = 2.0f * (length * v[u] + e * vt * t[u]);
+      if (g_qdd) g_qdd[at] = 2.0f * smooth * a[u];
     }
   }
   if (d_min) {
@@ -175,22 +202,25 @@ size_t bspline_bwd_smem(int K, int T) {
 }
 
 cudaError_t launch_bspline_bwd(int64_t n_traj, int d, int K, int T, float dt, const float* gq,
-                               const float* gqd, const float* gqdd, float* gU, cudaStream_t s) {
+                               const float* gqd, const float* gqdd, const float* gqd2,
+                               const float* gqdd2, float* gU, cudaStream_t s) {
   const size_t smem = bspline_bwd_smem(K, T);
   cudaError_t e = cudaFuncSetAttribute(bspline_bwd_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t n = n_traj * d * K;
   bspline_bwd_kernel<<<(unsigned)((n + 255) / 256), 256, smem, s>>>(n_traj, d, K, T, dt, gq, gqd,
-                                                                   gqdd, gU);
+                                                                   gqdd, gqd2, gqdd2, gU);
   return cudaGetLastError();
 }
 
 cudaError_t launch_trajopt_cost(int64_t B, int d, const float* tau, const float* d_min,
-                                const float* lo, const float* hi, float w, float* cost,
-                                float* g_tau, float* g_dmin, cudaStream_t s) {
-  trajopt_cost_kernel<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(B, d, tau, d_min, lo, hi, w,
-                                                                  cost, g_tau, g_dmin);
+                                const float* qd, const float* qdd, const float* lo,
+                                const float* hi, float w, float smooth, float length, float e,
+                                float* cost, float* g_tau, float* g_dmin, float* g_qd,
+                                float* g_qdd, cudaStream_t s) {
+  trajopt_cost_kernel<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(
+      B, d, tau, d_min, qd, qdd, lo, hi, w, smooth, length, e, cost, g_tau, g_dmin, g_qd, g_qdd);
   return cudaGetLastError();
 }
 

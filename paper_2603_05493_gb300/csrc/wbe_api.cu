@@ -1407,9 +1407,10 @@ int wb_bspline_eval(int64_t n_traj, int32_t d, int32_t K, int32_t T, float dt, c
   return WB_OK;
 }
 
-int wb_bspline_backward(int64_t n_traj, int32_t d, int32_t K, int32_t T, float dt,
-                        const float* gq, const float* gqd, const float* gqdd, float* gU,
-                        void* stream) {
+int wb_bspline_backward_ext(int64_t n_traj, int32_t d, int32_t K, int32_t T, float dt,
+                            const float* gq, const float* gqd, const float* gqdd,
+                            const float* gqd_add, const float* gqdd_add, float* gU,
+                            void* stream) {
   g_err.clear();
   int rc, dev = -1;
   if ((rc = check_spline(n_traj, d, K, T, dt))) return rc;
@@ -1417,37 +1418,65 @@ int wb_bspline_backward(int64_t n_traj, int32_t d, int32_t K, int32_t T, float d
   if ((rc = check_buf(gq, "gq", false, &dev))) return rc;
   if ((rc = check_buf(gqd, "gqd", false, &dev))) return rc;
   if ((rc = check_buf(gqdd, "gqdd", false, &dev))) return rc;
+  if ((rc = check_buf(gqd_add, "gqd_add", false, &dev))) return rc;
+  if ((rc = check_buf(gqdd_add, "gqdd_add", false, &dev))) return rc;
   if (n_traj == 0) return WB_OK;
   DeviceGuard guard(dev);
-  cudaError_t e = launch_bspline_bwd(n_traj, d, K, T, dt, gq, gqd, gqdd, gU,
+  cudaError_t e = launch_bspline_bwd(n_traj, d, K, T, dt, gq, gqd, gqdd, gqd_add, gqdd_add, gU,
                                      static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "wb_bspline_backward launch");
+  return WB_OK;
+}
+
+int wb_bspline_backward(int64_t n_traj, int32_t d, int32_t K, int32_t T, float dt,
+                        const float* gq, const float* gqd, const float* gqdd, float* gU,
+                        void* stream) {
+  return wb_bspline_backward_ext(n_traj, d, K, T, dt, gq, gqd, gqdd, nullptr, nullptr, gU,
+                                 stream);
+}
+
+int wb_trajopt_cost_ext(int64_t B, int32_t d, const float* tau, const float* d_min,
+                        const float* qd, const float* qdd, const float* tau_lo,
+                        const float* tau_hi, const wb_cost_weights* w, float* cost,
+                        float* g_tau, float* g_dmin, float* g_qd, float* g_qdd, void* stream) {
+  g_err.clear();
+  int rc, dev = -1;
+  if (!w) return fail(WB_EINVAL, "weights are NULL");
+  const wb_cost_weights W = *w;
+  if (B < 0 || d < 0 || d > WB_MAX_LINKS) return fail(WB_EINVAL, "bad B or d");
+  if (B * (int64_t)std::max(d, 1) > ((int64_t)1 << 40)) return fail(WB_EINVAL, "B too large");
+  if (!std::isfinite(W.collision) || !std::isfinite(W.smooth) || !std::isfinite(W.length) ||
+      !std::isfinite(W.energy) || !std::isfinite(W.dt) || !(W.dt > 0.0f) ||
+      !std::isfinite(W.energy * W.dt * W.dt))
+    return fail(WB_EINVAL, "weights must be finite and dt > 0");
+  if ((rc = check_buf(tau, "tau", false, &dev))) return rc;
+  if ((rc = check_buf(d_min, "d_min", false, &dev))) return rc;
+  if ((rc = check_buf(qd, "qd", false, &dev))) return rc;
+  if ((rc = check_buf(qdd, "qdd", false, &dev))) return rc;
+  if ((rc = check_buf(tau_lo, "tau_lo", tau != nullptr, &dev))) return rc;
+  if ((rc = check_buf(tau_hi, "tau_hi", tau != nullptr, &dev))) return rc;
+  if ((rc = check_buf(cost, "cost", false, &dev))) return rc;
+  if ((rc = check_buf(g_tau, "g_tau", false, &dev))) return rc;
+  if ((rc = check_buf(g_dmin, "g_dmin", false, &dev))) return rc;
+  if ((rc = check_buf(g_qd, "g_qd", false, &dev))) return rc;
+  if ((rc = check_buf(g_qdd, "g_qdd", false, &dev))) return rc;
+  if (g_tau && !tau) return fail(WB_EINVAL, "g_tau without tau");
+  if (g_dmin && !d_min) return fail(WB_EINVAL, "g_dmin without d_min");
+  if (B == 0 || dev < 0) return WB_OK;
+  DeviceGuard guard(dev);
+  cudaError_t e = launch_trajopt_cost(B, d, tau, d_min, qd, qdd, tau_lo, tau_hi, W.collision,
+                                      W.smooth, W.length, W.energy * W.dt * W.dt, cost, g_tau,
+                                      g_dmin, g_qd, g_qdd, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "wb_trajopt_cost launch");
   return WB_OK;
 }
 
 int wb_trajopt_cost(int64_t B, int32_t d, const float* tau, const float* d_min,
                     const float* tau_lo, const float* tau_hi, float w_coll, float* cost,
                     float* g_tau, float* g_dmin, void* stream) {
-  g_err.clear();
-  int rc, dev = -1;
-  if (B < 0 || d < 0 || d > WB_MAX_LINKS) return fail(WB_EINVAL, "bad B or d");
-  if (B * (int64_t)std::max(d, 1) > ((int64_t)1 << 40)) return fail(WB_EINVAL, "B too large");
-  if (!std::isfinite(w_coll)) return fail(WB_EINVAL, "w_coll must be finite");
-  if ((rc = check_buf(tau, "tau", false, &dev))) return rc;
-  if ((rc = check_buf(d_min, "d_min", false, &dev))) return rc;
-  if ((rc = check_buf(tau_lo, "tau_lo", tau != nullptr, &dev))) return rc;
-  if ((rc = check_buf(tau_hi, "tau_hi", tau != nullptr, &dev))) return rc;
-  if ((rc = check_buf(cost, "cost", false, &dev))) return rc;
-  if ((rc = check_buf(g_tau, "g_tau", false, &dev))) return rc;
-  if ((rc = check_buf(g_dmin, "g_dmin", false, &dev))) return rc;
-  if (g_tau && !tau) return fail(WB_EINVAL, "g_tau without tau");
-  if (g_dmin && !d_min) return fail(WB_EINVAL, "g_dmin without d_min");
-  if (B == 0 || dev < 0) return WB_OK;
-  DeviceGuard guard(dev);
-  cudaError_t e = launch_trajopt_cost(B, d, tau, d_min, tau_lo, tau_hi, w_coll, cost, g_tau,
-                                      g_dmin, static_cast<cudaStream_t>(stream));
-  if (e != cudaSuccess) return cuda_fail(e, "wb_trajopt_cost launch");
-  return WB_OK;
+  const wb_cost_weights w = {w_coll, 0.0f, 0.0f, 0.0f, 1.0f};
+  return wb_trajopt_cost_ext(B, d, tau, d_min, nullptr, nullptr, tau_lo, tau_hi, &w, cost, g_tau,
+                             g_dmin, nullptr, nullptr, stream);
 }
 
 // The work tables of wb_batch_create, rebuilt per call in the library's static

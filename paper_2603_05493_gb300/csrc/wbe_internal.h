@@ -232,10 +232,13 @@ cudaError_t launch_bspline_fwd(int64_t n_traj, int d, int K, int T, float dt, co
                                float* q, float* qd, float* qdd, cudaStream_t s);
 size_t bspline_bwd_smem(int K, int T);
 cudaError_t launch_bspline_bwd(int64_t n_traj, int d, int K, int T, float dt, const float* gq,
-                               const float* gqd, const float* gqdd, float* gU, cudaStream_t s);
+                               const float* gqd, const float* gqdd, const float* gqd2,
+                               const float* gqdd2, float* gU, cudaStream_t s);
 cudaError_t launch_trajopt_cost(int64_t B, int d, const float* tau, const float* d_min,
-                                const float* lo, const float* hi, float w, float* cost,
-                                float* g_tau, float* g_dmin, cudaStream_t s);
+                                const float* qd, const float* qdd, const float* lo,
+                                const float* hi, float w, float smooth, float length, float e,
+                                float* cost, float* g_tau, float* g_dmin, float* g_qd,
+                                float* g_qdd, cudaStream_t s);
 
 // segments: 1 = one thread per configuration; 2, 4, 8 = segmented sweep
 // (requires the robot's plan for it, bit log2(segments) - 1 of seg_ok)

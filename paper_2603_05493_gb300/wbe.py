@@ -346,17 +346,24 @@ def bspline_eval(U, T: int, dt: float, q=None, qd=None, qdd=None, stream=None):
 
 
 def bspline_backward(gq, gqd, gqdd, n_traj: int, K: int, T: int, dt: float, gU=None,
-                     stream=None):
+                     stream=None, gqd_add=None, gqdd_add=None):
     """Control-point gradient [n_traj][d][K] from upstream gradients on the
-    states (wb_bspline_backward; any of gq, gqd, gqdd may be None)."""
+    states (wb_bspline_backward; any of gq, gqd, gqdd may be None).  With
+    gqd_add / gqdd_add (wb_bspline_backward_ext) those add to gqd / gqdd."""
     lib = L.load()
-    ref = next(t for t in (gq, gqd, gqdd) if t is not None)
+    ref = next(t for t in (gq, gqd, gqdd, gqd_add, gqdd_add) if t is not None)
     d = ref.shape[0]
     if gU is None:
         gU = torch.empty((n_traj, d, K), device=ref.device)
-    L.check(lib.wb_bspline_backward(n_traj, d, K, int(T), float(dt), _ptr(gq), _ptr(gqd),
-                                    _ptr(gqdd), _ptr(gU), _stream(stream)),
-            "wb_bspline_backward")
+    if gqd_add is None and gqdd_add is None:
+        L.check(lib.wb_bspline_backward(n_traj, d, K, int(T), float(dt), _ptr(gq), _ptr(gqd),
+                                        _ptr(gqdd), _ptr(gU), _stream(stream)),
+                "wb_bspline_backward")
+    else:
+        L.check(lib.wb_bspline_backward_ext(n_traj, d, K, int(T), float(dt), _ptr(gq),
+                                            _ptr(gqd), _ptr(gqdd), _ptr(gqd_add),
+                                            _ptr(gqdd_add), _ptr(gU), _stream(stream)),
+                "wb_bspline_backward_ext")
     return gU
 
 
@@ -376,6 +383,30 @@ def trajopt_cost(tau, d_min, tau_lo, tau_hi, w_coll: float, cost=None, g_tau=Non
                                 float(w_coll), _ptr(cost), _ptr(g_tau), _ptr(g_dmin),
                                 _stream(stream)), "wb_trajopt_cost")
     return cost, g_tau, g_dmin
+
+
+def trajopt_cost_ext(tau, d_min, qd, qdd, tau_lo, tau_hi, w_coll: float, smooth: float = 0.0,
+                     length: float = 0.0, energy: float = 0.0, dt: float = 1.0, out=None,
+                     stream=None):
+    """The cost with its motion terms (wb_trajopt_cost_ext): smooth |qdd|^2,
+    length |qd|^2 and energy sum_j (qd_j tau_j dt)^2 on top of the hinges.
+    ``out`` may hold preallocated (cost, g_tau, g_dmin, g_qd, g_qdd); the
+    ones missing are allocated.  Returns (cost, g_tau, g_dmin, g_qd, g_qdd)."""
+    lib = L.load()
+    ref = next(t for t in (tau, qd, qdd, d_min) if t is not None)
+    d, B = ref.shape if ref.dim() == 2 else (0, ref.shape[0])
+    cost, g_tau, g_dmin, g_qd, g_qdd = out if out is not None else (None,) * 5
+    mk = lambda t, src, shape: t if t is not None or src is None else \
+        torch.empty(shape, device=ref.device)  # noqa: E731
+    cost = mk(cost, ref, (B,))
+    g_tau, g_dmin = mk(g_tau, tau, (d, B)), mk(g_dmin, d_min, (B,))
+    g_qd, g_qdd = mk(g_qd, qd, (d, B)), mk(g_qdd, qdd, (d, B))
+    w = L.wb_cost_weights(float(w_coll), float(smooth), float(length), float(energy), float(dt))
+    L.check(lib.wb_trajopt_cost_ext(B, d, _ptr(tau), _ptr(d_min), _ptr(qd), _ptr(qdd),
+                                    _ptr(tau_lo), _ptr(tau_hi), C.byref(w), _ptr(cost),
+                                    _ptr(g_tau), _ptr(g_dmin), _ptr(g_qd), _ptr(g_qdd),
+                                    _stream(stream)), "wb_trajopt_cost_ext")
+    return cost, g_tau, g_dmin, g_qd, g_qdd
 
 
 def batch_eval_noalloc(robots, problems, q, qd, qdd, pose, sphere=None, dmin=None, worst=None,

@@ -32,3 +32,9 @@ TRAJOPT_DT = 0.25
 TORQUE_LIMIT = 30.0
 COLLISION_WEIGHT = 1.0
 ACTIVATION_DISTANCE = 0.02  # m, summed collision hinge of the trajopt48 variant
+# motion terms of the trajopt48 loss (smooth |qdd|^2, length |qd|^2, energy
+# sum (qd tau dt)^2), weighted so that each is of the order of a few hundred
+# on the workload's states, like the torque hinges
+SMOOTH_WEIGHT = 0.01
+LENGTH_WEIGHT = 1.0
+ENERGY_WEIGHT = 0.01

@@ -103,22 +103,92 @@ def test_trajopt_cost_matches_oracle_on_the_same_inputs(W, O):
                        rtol=2e-6, atol=1e-4)
 
 
-def _chain(W, rob, desc, U, T, dt, lo, hi, w):
-    """The GPU chain; returns (gU, cost, eval outputs)."""
+def test_trajopt_cost_motion_terms_match_oracle(W, O):
+    """wb_trajopt_cost_ext on the same float32 states and torques as the
+    oracle: the smooth, length and energy terms and their direct gradients
+    agree to float rounding, the hinge decisions are unchanged."""
+    rng = np.random.default_rng(21)
+    d, B = 48, 777
+    tau = rng.normal(scale=30.0, size=(d, B)).astype(np.float32)
+    qd = rng.normal(scale=3.0, size=(d, B)).astype(np.float32)
+    qdd = rng.normal(scale=20.0, size=(d, B)).astype(np.float32)
+    dmin = rng.normal(scale=0.05, size=B).astype(np.float32)
+    lo, hi = np.full(d, -30.0, np.float32), np.full(d, 30.0, np.float32)
+    kw = dict(smooth=0.01, length=1.0, energy=0.01, dt=0.05)
+    got = W.trajopt_cost_ext(cuda(tau), cuda(dmin), cuda(qd), cuda(qdd), cuda(lo), cuda(hi), 2.5,
+                             **kw)
+    torch.cuda.synchronize()
+    ref = O.trajopt_cost(tau, dmin, lo, hi, 2.5, qd, qdd, **kw)
+    got = [g.cpu().numpy().astype(np.float64) for g in got]
+    # each term is a sum of d float products: relative 1e-5 of its size
+    mag = (kw["smooth"] * qdd.astype(np.float64) ** 2 + kw["length"] * qd.astype(np.float64) ** 2
+           + kw["energy"] * kw["dt"] ** 2 * (qd.astype(np.float64) * tau) ** 2
+           + np.abs(tau)).sum(axis=0) + 2.5 * np.abs(dmin)
+    assert (np.abs(got[0] - ref[0]) <= 1e-5 * mag + 1e-5).all()
+    for g, r in zip(got[1:], ref[1:]):
+        assert np.allclose(g, r, rtol=1e-5, atol=1e-5 * np.abs(r).max())
+    assert np.array_equal(got[2], ref[2])  # the collision hinge is untouched
+    # zero motion weights: the plain cost, bit for bit
+    c0 = W.trajopt_cost_ext(cuda(tau), cuda(dmin), cuda(qd), cuda(qdd), cuda(lo), cuda(hi), 2.5)
+    c1 = W.trajopt_cost(cuda(tau), cuda(dmin), cuda(lo), cuda(hi), 2.5)
+    torch.cuda.synchronize()
+    for a, b in zip(c0[:3], c1):
+        assert torch.equal(a, b)
+    assert not c0[3].any() and not c0[4].any()
+    # states only (no torques, no distances): motion terms alone
+    m = W.trajopt_cost_ext(None, None, cuda(qd), cuda(qdd), None, None, 0.0, **kw)
+    torch.cuda.synchronize()
+    assert m[1] is None and m[2] is None
+    rm = O.trajopt_cost(np.zeros((d, B)), np.ones(B), lo, hi, 0.0, qd, qdd, **kw)
+    assert np.allclose(m[0].cpu().numpy(), rm[0], rtol=1e-5)
+    assert np.allclose(m[3].cpu().numpy(), 2.0 * kw["length"] * qd, rtol=1e-6)
+
+
+def test_trajopt_cost_ext_rejects_bad_weights(W):
+    x = cuda(np.ones((3, 4)))
+    for bad in (dict(dt=0.0), dict(dt=-1.0), dict(smooth=float("nan")),
+                dict(energy=float("inf"))):
+        with pytest.raises(W.L.WbError):
+            W.trajopt_cost_ext(x, None, x, x, cuda(-np.ones(3)), cuda(np.ones(3)), 1.0, **bad)
+
+
+def test_bspline_backward_ext_adds_before_the_transpose(W):
+    """gqd + gqd_add through the adjoint equals the plain adjoint of the float
+    sum: the kernel adds in the same float order as the caller would."""
+    rng = np.random.default_rng(5)
+    n_traj, d, K, T = 9, 13, 11, 33
+    g = [cuda(rng.normal(size=(d, n_traj * T))) for _ in range(5)]
+    a = W.bspline_backward(g[0], g[1], g[2], n_traj, K, T, 0.2, gqd_add=g[3], gqdd_add=g[4])
+    b = W.bspline_backward(g[0], g[1] + g[3], g[2] + g[4], n_traj, K, T, 0.2)
+    c = W.bspline_backward(None, None, None, n_traj, K, T, 0.2, gqd_add=g[3])
+    e = W.bspline_backward(None, g[3], None, n_traj, K, T, 0.2)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b) and torch.equal(c, e)
+
+
+def _chain(W, rob, desc, U, T, dt, lo, hi, w, motion=None):
+    """The GPU chain; returns (gU, cost, eval outputs).  ``motion`` holds the
+    smooth / length / energy weights of the cost's motion terms."""
     n_traj, d, K = U.shape
     q, qd, qdd = W.bspline_eval(U, T, dt)
     o = rob.eval(q, qd, qdd)
-    cost, g_tau, g_dmin = W.trajopt_cost(o["tau"], o["dmin"], lo, hi, w)
+    if motion:
+        cost, g_tau, g_dmin, g_qd, g_qdd = W.trajopt_cost_ext(
+            o["tau"], o["dmin"], qd, qdd, lo, hi, w, dt=dt * (K - 3) / (T - 1), **motion)
+    else:
+        cost, g_tau, g_dmin = W.trajopt_cost(o["tau"], o["dmin"], lo, hi, w)
+        g_qd = g_qdd = None
     gq, gqd, gqdd = rob.eval_backward(q, qd, qdd, o["worst"], None, None, g_dmin, g_tau)
-    gU = W.bspline_backward(gq, gqd, gqdd, n_traj, K, T, dt)
+    gU = W.bspline_backward(gq, gqd, gqdd, n_traj, K, T, dt, gqd_add=g_qd, gqdd_add=g_qdd)
     torch.cuda.synchronize()
     return gU, cost, o
 
 
-def _compare_chain(O, desc, U, T, dt, lim, w, gU, cost, o, trajs):
+def _compare_chain(O, desc, U, T, dt, lim, w, gU, cost, o, trajs, motion=None):
     d = desc.dof
     lo, hi = -lim * np.ones(d), lim * np.ones(d)
-    Uref, cref, ev = O.trajopt_gradient(desc, U.astype(np.float64), T, dt, lo, hi, w)
+    Uref, cref, ev = O.trajopt_gradient(desc, U.astype(np.float64), T, dt, lo, hi, w,
+                                        **(motion or {}))
     tau, dmin, worst = ev["tau"], ev["dmin"], ev["worst"]
     got_worst = o["worst"].cpu().numpy()
     got_cost = cost.cpu().numpy()
@@ -129,6 +199,8 @@ def _compare_chain(O, desc, U, T, dt, lim, w, gU, cost, o, trajs):
         gsl = slice(tr * T, (tr + 1) * T)
         # torques agree to 1e-4 relative per joint, so the hinge sums do too
         tol = 1e-4 * np.maximum(np.abs(tau[:, sl]), 1.0).sum(axis=0) + 1e-5
+        if motion:  # the energy term is quadratic in the torques: 2e-4 relative
+            tol = tol + 2e-4 * np.abs(cref[sl])
         assert (np.abs(got_cost[gsl] - cref[sl]) <= tol).all()
         near = (np.abs(np.abs(tau[:, sl]) - lim) < 1e-3).any() or \
             (np.abs(dmin[sl]) < 1e-4).any() or not np.array_equal(got_worst[gsl], worst[sl])
@@ -173,3 +245,20 @@ def test_trajopt48_full_size_sampled(W, O):
     trajs = [0, 257, n_traj - 1]
     kept = _compare_chain(O, desc, U[trajs], T, dt, lim, w, gU, cost, o, trajs)
     assert kept >= 2
+
+
+def test_trajopt_chain_with_motion_terms_matches_oracle(W, O):
+    """The chain with the smooth, length and energy terms of the loss at the
+    trajopt48 weights: the cost's direct qd / qdd gradients join the sweep's
+    in the B-spline adjoint."""
+    desc = I.hand_payload(R.r48())
+    rob = W.Robot(desc, device=0)
+    n_traj, K, T, dt = 6, CF.TRAJOPT_KNOTS, CF.TRAJOPT_STEPS, CF.TRAJOPT_DT
+    U = I.bspline_controls(desc.dof, n_traj, K, seed=CF.TRAJOPT48.seed + 1)
+    lim, w = CF.TORQUE_LIMIT, CF.COLLISION_WEIGHT
+    motion = dict(smooth=CF.SMOOTH_WEIGHT, length=CF.LENGTH_WEIGHT, energy=CF.ENERGY_WEIGHT)
+    lo = cuda(-lim * np.ones(desc.dof))
+    hi = cuda(lim * np.ones(desc.dof))
+    gU, cost, o = _chain(W, rob, desc, cuda(U), T, dt, lo, hi, w, motion)
+    kept = _compare_chain(O, desc, U, T, dt, lim, w, gU, cost, o, list(range(n_traj)), motion)
+    assert kept >= n_traj - 2
