@@ -63,12 +63,12 @@ TREE_SRC = ["paper_2603_05493_gb300/csrc/k_tree.cu", "paper_2603_05493_gb300/csr
 PAIR_SRC = ["paper_2603_05493_gb300/csrc/k_pair.cu", "paper_2603_05493_gb300/csrc/pair_body.cuh",
             "paper_2603_05493_gb300/csrc/spatial.cuh"]
 MEASURED_TRAFFIC = {  # profiles/humanoid48_kernel_traffic.md
-    "tree_fwd": {"src": TREE_SRC, "sha256": "dfdf529911cb14f0da1b79df668c911c732b8f4127c735f8e49a8259739e5e6b",
-                 "bytes_per_eval": (46.8e6 + 196.1e6) / 24576},
+    "tree_fwd": {"src": TREE_SRC, "sha256": "d40e87d7413845bf5b8a8bd156dac5947de2c5667d1fc5911aca8281d2f208e4",
+                 "bytes_per_eval": (17.09e6 + 41.61e6) / 24576},
     "pair": {"src": PAIR_SRC, "sha256": "c0f00e126b5027b8eb78ef9b1137c99d21bc21025fc0afc751da0f1a59bdc3b1",
              "bytes_per_eval": (58.8e6 + 21.4e6) / 24576},
-    "tree_bwd": {"src": TREE_SRC, "sha256": "dfdf529911cb14f0da1b79df668c911c732b8f4127c735f8e49a8259739e5e6b",
-                 "bytes_per_eval": (304.5e6 + 259.5e6) / 24576},
+    "tree_bwd": {"src": TREE_SRC, "sha256": "d40e87d7413845bf5b8a8bd156dac5947de2c5667d1fc5911aca8281d2f208e4",
+                 "bytes_per_eval": (213.98e6 + 93.85e6) / 24576},
 }
 
 

@@ -123,10 +123,12 @@ __device__ __forceinline__ void link_local(const DevRobot& r, int k, const float
 // ---------------------------------------------------------------------------
 // Per-depth stack entry.  The local transform is not kept: post-order
 // recomputes it from q (cheaper than a round trip through local memory).
+// W, v and a are read only by the push of a second or later child, so only
+// links with two or more children store them; F (own force plus the
+// children's) is stored when a child's push interrupts it.
 struct FEnt {
   float W[12];  // world pose
   float v[6], a[6], F[6];
-  int k;
 };
 
 __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A, int64_t b,
@@ -146,10 +148,11 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
   int cdep = -1;
   float pF[6];
   int pdep = -1;
+  int lastk = 0;  // last pushed link; the stack holds its ancestor chain
 
   auto close = [&](int e) {
     FEnt& E = stk[e];
-    const int k = E.k;
+    const int k = __ldg(r.chain + __ldg(r.chain_start + lastk) + e);
     float F[6];
     if (pdep == e) {
 #pragma unroll
@@ -193,6 +196,7 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
   // pre-order of link k at depth dep; own = false replays an ancestor of
   // the segment (pose, v, a only; no output, no force of its own)
   auto push = [&](int k, int dep, bool own) {
+    if (dyn) flush();  // the parent's force, when it is still pending
     FEnt& E = stk[dep];
     float L[12];
     link_local(r, k, A.q, B, b, L);
@@ -227,9 +231,12 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
       ap[5] = r.abase[2];
     }
     cdep = dep;
-    E.k = k;
+    lastk = k;
+    const int nch = __ldg(r.child_start + k + 1) - __ldg(r.child_start + k);
+    if (nch > 1) {
 #pragma unroll
-    for (int i = 0; i < 12; ++i) E.W[i] = cW[i];
+      for (int i = 0; i < 12; ++i) E.W[i] = cW[i];
+    }
     if (own && A.pose) {
       float4* dst = reinterpret_cast<float4*>(A.pose + (b * n + k) * 12);
       dst[0] = make_float4(cW[0], cW[1], cW[2], cW[3]);
@@ -258,12 +265,17 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
 #pragma unroll
         for (int i = 0; i < 6; ++i) F[i] = 0.0f;
       }
+      if (nch > 1) {
 #pragma unroll
-      for (int i = 0; i < 6; ++i) {
-        E.v[i] = cv[i];
-        E.a[i] = ca[i];
-        E.F[i] = F[i];
+        for (int i = 0; i < 6; ++i) {
+          E.v[i] = cv[i];
+          E.a[i] = ca[i];
+        }
       }
+      // the force waits in the pending registers; a child's push stores it
+#pragma unroll
+      for (int i = 0; i < 6; ++i) pF[i] = F[i];
+      pdep = dep;
     }
   };
 
@@ -307,14 +319,23 @@ __device__ __forceinline__ void tree_fwd_one(const DevRobot& r, const FwdArgs& A
 // ---------------------------------------------------------------------------
 // backward: the whole adjoint in one sweep
 // ---------------------------------------------------------------------------
-// Per-depth stack entry.  The local transform X_k and X_k Fbar_pa are not
-// kept: post-order recomputes them from q and the parent's Fbar.
+// Per-depth stack entry.  Only what a later step reads is stored:
+//   v, a, Fbar  -- read by the close of every child (not stored for a leaf,
+//                  whose close follows its push and takes them from registers);
+//   Wr          -- the link's own gradient wrench, stored only when some
+//                  kinematic output of the link has a gradient;
+//   W           -- world pose, read by the push of a second or later child
+//                  (stored only for links with two or more children);
+//   acc         -- the children's sums of F, abar, vbar, W, stored only when
+//                  the push of a sibling subtree interrupts them.
+// The link's own F, abar and vbar are recomputed at its close from v, a and
+// Fbar (a few hundred flops) instead of a round trip through local memory,
+// and X_k, X_k Fbar_pa from q and the parent's Fbar.
 struct BEnt {
+  float v[6], a[6], Fb[6];
+  float Wr[6];
   float W[12];
-  float v[6], a[6], F[6];
-  float Fb[6];   // Fbar_k
-  float ab[6], vb[6], Wr[6];
-  int k;
+  float aF[6], aab[6], avb[6], aWr[6];
 };
 
 // world pose of link l by composing its ancestor chain (topology cache)
@@ -399,45 +420,94 @@ __device__ __forceinline__ void tree_bwd_seg(const DevRobot& r, const BwdArgs& A
     }
   }
 
-  // Register copies that spare most stack loads (see tree_fwd_seg): the
-  // pre-order data of the last pushed entry (W, v, a, Fbar), the pending
-  // accumulators (F, abar, vbar, W) of the entry the post-order closes next,
-  // and the v of that entry, loaded by the close of its child.
+  // Register copies that spare most stack traffic:
+  //   c*: pre-order data of the last pushed entry (W, v, a, Fbar);
+  //   p*: the accumulated children's sums (F, abar, vbar, W) of the entry the
+  //       post-order closes next (an unwinding chain passes them on in
+  //       registers; they are stored when a push interrupts).
+  // Caching the parent's pre-order data as well was measured slower: at the
+  // 128 registers that two 256-thread blocks per SM allow, the extra copies
+  // spill, and more registers per thread cost more in occupancy than they
+  // save.
   float cW[12], cv[6], ca[6], cFb[6];
   int cdep = -1;
-  float pF[6], pab[6], pvb[6], pWr[6], qv[6];
-  int pdep = -1, qdep = -1;
+  float pF[6], pab[6], pvb[6], pWr[6];
+  int pdep = -1;
+  // bit e: entry e is an ancestor replayed for this segment (no own terms),
+  // its acc holds children's sums, its Wr was stored
+  uint32_t replayed = 0u, accv = 0u, wrv = 0u;
+  int lastk = 0;  // last pushed link; the stack holds its ancestor chain
+  const bool kin_grad = A.g_pose != nullptr || A.g_sph != nullptr;
 
   auto close = [&](int e) {
     BEnt& E = stk[e];
-    const int k = E.k;
-    float F[6], ab[6], vb[6], Wr[6], v[6];
+    const int k = __ldg(r.chain + __ldg(r.chain_start + lastk) + e);
+    float v[6], a[6], Fb[6];
+    if (cdep == e) {  // a leaf (or a segment's last link), closed right after its push
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        v[i] = cv[i];
+        a[i] = ca[i];
+        Fb[i] = cFb[i];
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        v[i] = E.v[i];
+        a[i] = E.a[i];
+        Fb[i] = E.Fb[i];
+      }
+    }
+    // own terms: f = I a + v x* I v - f_ext, abar = I Fbar,
+    // vbar = -crf(Fbar) I v - I crm(v) Fbar, and the stored wrench
+    float F[6], ab[6], vb[6], Wr[6];
+    if (!((replayed >> e) & 1u)) {
+      float I[10];
+      load_inertia(r, k, I);
+      rnea_force(I, v, a, F);
+      if (A.fext) {
+        const float* fe = A.fext + (b * n + k) * 6;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) F[i] -= __ldg(fe + i);
+      }
+      float Iv[6], t1[6], t2[6], t3[6];
+      inertia_mul(I, Fb, ab);
+      inertia_mul(I, v, Iv);
+      crf(Fb, Iv, t1);
+      crm(v, Fb, t2);
+      inertia_mul(I, t2, t3);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) vb[i] = -t1[i] - t3[i];
+      if ((wrv >> e) & 1u) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) Wr[i] = E.Wr[i];
+      } else {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) Wr[i] = 0.0f;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) F[i] = ab[i] = vb[i] = Wr[i] = 0.0f;
+    }
+    // plus the children's sums
     if (pdep == e) {
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
-        F[i] = pF[i];
-        ab[i] = pab[i];
-        vb[i] = pvb[i];
-        Wr[i] = pWr[i];
+        F[i] += pF[i];
+        ab[i] += pab[i];
+        vb[i] += pvb[i];
+        Wr[i] += pWr[i];
       }
-    } else {
+    } else if ((accv >> e) & 1u) {
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
-        F[i] = E.F[i];
-        ab[i] = E.ab[i];
-        vb[i] = E.vb[i];
-        Wr[i] = E.Wr[i];
+        F[i] += E.aF[i];
+        ab[i] += E.aab[i];
+        vb[i] += E.avb[i];
+        Wr[i] += E.aWr[i];
       }
     }
-    if (qdep == e) {
-#pragma unroll
-      for (int i = 0; i < 6; ++i) v[i] = qv[i];
-    } else {
-#pragma unroll
-      for (int i = 0; i < 6; ++i) v[i] = E.v[i];
-    }
     pdep = -1;
-    qdep = -1;
     const int j = __ldg(r.jidx + k);
     const int jt = __ldg(r.jtype + k);
     const float4 a4 = __ldg(reinterpret_cast<const float4*>(r.axis) + k);
@@ -448,10 +518,9 @@ __device__ __forceinline__ void tree_bwd_seg(const DevRobot& r, const BwdArgs& A
     const float vq = j >= 0 ? mm * __ldg(A.qd + (int64_t)j * B + b) : 0.0f;
     float L[12];
     link_local(r, k, A.q, B, b, L);
-    float XF[6], vp[6], ap[6];  // X_k Fbar_pa, and the parent's v, a
+    float XF[6], vp[6], ap[6], Fbp[6];  // X_k Fbar_pa, and the parent's v, a, Fbar
     if (e > 0) {
       const BEnt& P = stk[e - 1];
-      float Fbp[6];
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
         Fbp[i] = P.Fb[i];
@@ -508,38 +577,38 @@ __device__ __forceinline__ void tree_bwd_seg(const DevRobot& r, const BwdArgs& A
     }
     if (e > 0) {
       const BEnt& P = stk[e - 1];
+      const bool has = (accv >> (e - 1)) & 1u;
+      accv &= ~(1u << (e - 1));  // taken over by the pending registers
       float up[6];
       xf_force_T(L, L + 9, F, up);
 #pragma unroll
-      for (int i = 0; i < 6; ++i) pF[i] = P.F[i] + up[i];
+      for (int i = 0; i < 6; ++i) pF[i] = has ? P.aF[i] + up[i] : up[i];
       xf_force_T(L, L + 9, ab, up);
 #pragma unroll
-      for (int i = 0; i < 6; ++i) pab[i] = P.ab[i] + up[i];
+      for (int i = 0; i < 6; ++i) pab[i] = has ? P.aab[i] + up[i] : up[i];
       xf_force_T(L, L + 9, vb, up);
 #pragma unroll
-      for (int i = 0; i < 6; ++i) pvb[i] = P.vb[i] + up[i];
+      for (int i = 0; i < 6; ++i) pvb[i] = has ? P.avb[i] + up[i] : up[i];
       xf_force_T(L, L + 9, Wr, up);
 #pragma unroll
-      for (int i = 0; i < 6; ++i) pWr[i] = P.Wr[i] + up[i];
+      for (int i = 0; i < 6; ++i) pWr[i] = has ? P.aWr[i] + up[i] : up[i];
       pdep = e - 1;
-#pragma unroll
-      for (int i = 0; i < 6; ++i) qv[i] = vp[i];
-      qdep = e - 1;
     }
+    if (cdep == e) cdep = -1;
   };
-  auto flush = [&]() {  // the pending accumulators go back to their entry
+  auto flush = [&]() {  // the pending children's sums go to their entry
     if (pdep >= 0) {
       BEnt& P = stk[pdep];
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
-        P.F[i] = pF[i];
-        P.ab[i] = pab[i];
-        P.vb[i] = pvb[i];
-        P.Wr[i] = pWr[i];
+        P.aF[i] = pF[i];
+        P.aab[i] = pab[i];
+        P.avb[i] = pvb[i];
+        P.aWr[i] = pWr[i];
       }
+      accv |= 1u << pdep;
       pdep = -1;
     }
-    qdep = -1;
   };
 
   // pre-order of link k at depth dep; own = false replays an ancestor of
@@ -559,7 +628,7 @@ __device__ __forceinline__ void tree_bwd_seg(const DevRobot& r, const BwdArgs& A
           ap[i] = ca[i];
           Fbp[i] = cFb[i];
         }
-      } else {
+      } else {  // a second or later child: the parent stored its pose
         const BEnt& P = stk[dep - 1];
 #pragma unroll
         for (int i = 0; i < 12; ++i) PW[i] = P.W[i];
@@ -582,6 +651,11 @@ __device__ __forceinline__ void tree_bwd_seg(const DevRobot& r, const BwdArgs& A
       Fbp[0] = Fbp[1] = Fbp[2] = Fbp[3] = Fbp[4] = Fbp[5] = 0.0f;
     }
     cdep = dep;
+    lastk = k;
+    const uint32_t bit = 1u << dep;
+    accv &= ~bit;
+    wrv &= ~bit;
+    replayed = own ? (replayed & ~bit) : (replayed | bit);
     const int j = __ldg(r.jidx + k);
     const int jt = __ldg(r.jtype + k);
     const float4 a4 = __ldg(reinterpret_cast<const float4*>(r.axis) + k);
@@ -589,7 +663,7 @@ __device__ __forceinline__ void tree_bwd_seg(const DevRobot& r, const BwdArgs& A
     const float mm = __ldg(reinterpret_cast<const float2*>(r.mimic) + k).x;
     const float vq = j >= 0 ? mm * __ldg(A.qd + (int64_t)j * B + b) : 0.0f;
     const float aq = j >= 0 ? mm * __ldg(A.qdd + (int64_t)j * B + b) : 0.0f;
-    // dynamics forward: v, a (and f when the link is this segment's)
+    // dynamics forward: v, a
     rnea_va(L, L + 9, vp, ap, jt, ax, vq, aq, cv, ca);
     // adjoint of the force sweep: Fbar_k = S m taubar + X Fbar_pa
     float S[6];
@@ -599,46 +673,27 @@ __device__ __forceinline__ void tree_bwd_seg(const DevRobot& r, const BwdArgs& A
     xf_motion(L, L + 9, Fbp, XF);
 #pragma unroll
     for (int i = 0; i < 6; ++i) cFb[i] = fmaf(S[i], tb, XF[i]);
-    E.k = k;
+    const int nch = __ldg(r.child_start + k + 1) - __ldg(r.child_start + k);
+    if (nch > 0) {
 #pragma unroll
-    for (int i = 0; i < 12; ++i) E.W[i] = cW[i];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      E.v[i] = cv[i];
-      E.a[i] = ca[i];
-      E.Fb[i] = cFb[i];
+      for (int i = 0; i < 6; ++i) {
+        E.v[i] = cv[i];
+        E.a[i] = ca[i];
+        E.Fb[i] = cFb[i];
+      }
     }
-    if (!own) {
+    if (nch > 1) {
 #pragma unroll
-      for (int i = 0; i < 6; ++i) E.F[i] = E.ab[i] = E.vb[i] = E.Wr[i] = 0.0f;
-      return;
+      for (int i = 0; i < 12; ++i) E.W[i] = cW[i];
     }
-    float I[10], F[6];
-    load_inertia(r, k, I);
-    rnea_force(I, cv, ca, F);
-    if (A.fext) {
-      const float* fe = A.fext + (b * n + k) * 6;
-#pragma unroll
-      for (int i = 0; i < 6; ++i) F[i] -= __ldg(fe + i);
-    }
+    if (!own) return;
     if (A.g_fext) {  // dL/df_ext,k = -Fbar_k
       float* o = A.g_fext + (b * n + k) * 6;
 #pragma unroll
       for (int i = 0; i < 6; ++i) o[i] = -cFb[i];
     }
-    // adjoint of the per-link force: abar, vbar
-    float abk[6], vbk[6];
-    {
-      float Iv[6], t1[6], t2[6], t3[6];
-      inertia_mul(I, cFb, abk);
-      inertia_mul(I, cv, Iv);
-      crf(cFb, Iv, t1);
-      crm(cv, cFb, t2);
-      inertia_mul(I, t2, t3);
-#pragma unroll
-      for (int i = 0; i < 6; ++i) vbk[i] = -t1[i] - t3[i];
-    }
     // gradient wrench of the kinematic outputs, link frame
+    if (!kin_grad && k != pl1 && k != pl2) return;
     float w[6] = {0, 0, 0, 0, 0, 0};
     if (A.g_pose) {
       const float4* g4 = reinterpret_cast<const float4*>(A.g_pose + (b * n + k) * 12);
@@ -671,12 +726,8 @@ __device__ __forceinline__ void tree_bwd_seg(const DevRobot& r, const BwdArgs& A
       point_wrench(cW, __ldg(r.sph + ps2), mu, w);
     }
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      E.F[i] = F[i];
-      E.ab[i] = abk[i];
-      E.vb[i] = vbk[i];
-      E.Wr[i] = w[i];
-    }
+    for (int i = 0; i < 6; ++i) E.Wr[i] = w[i];
+    wrv |= bit;
   };
 
   int sp = 0;
