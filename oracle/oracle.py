@@ -199,6 +199,66 @@ def bspline_vjp(gq, gqd, gqdd, n_traj: int, K: int, T: int, dt: float):
     return Ub
 
 
+def ghost_knots(start, dt: float):
+    """The three fictitious control points that anchor a spline to a
+    non-static initial state (Sec. 4.2, Eqs. fixed_3, fixed_2, fixed_1):
+    start [n_traj][d][3] holds theta_0, thetadot_0, thetaddot_0 per joint;
+    returns [n_traj][d][3] = u_-3, u_-2, u_-1 with
+        u_-3 = theta_0 - thetaddot_0 dt^2 / 6,
+        u_-2 = theta_0 + thetadot_0 dt + thetaddot_0 dt^2 / 3,
+        u_-1 = theta_0 + 2 thetadot_0 dt + 11 thetaddot_0 dt^2 / 6."""
+    st = np.asarray(start, np.float64)
+    th, v, a = st[..., 0], st[..., 1], st[..., 2]
+    return np.stack([th - a * dt * dt / 6.0,
+                     th + v * dt + a * dt * dt / 3.0,
+                     th + 2.0 * v * dt + 11.0 * a * dt * dt / 6.0], axis=-1)
+
+
+def extended_knots(U, start=None, end_static=False, dt: float = 1.0):
+    """The knot sequence a boundary-conditioned spline is evaluated on: the
+    ghost knots of a non-static start prepended (Sec. 4.2), and for a static
+    goal the final control point repeated so that it appears four times
+    (Sec. 4.2: the repeated knot makes velocity and acceleration vanish at
+    the end, Eq. stop-constraint)."""
+    U = np.asarray(U, np.float64)
+    parts = []
+    if start is not None:
+        parts.append(ghost_knots(start, dt))
+    parts.append(U)
+    if end_static:
+        parts.append(np.repeat(U[..., -1:], 3, axis=-1))
+    return np.concatenate(parts, axis=-1)
+
+
+def bspline_bc(U, T: int, dt: float, start=None, end_static=False):
+    """B-spline states with boundary conditions: Eq. bspline-cubic evaluated
+    on the extended knot sequence (T samples over its segments).  Returns q,
+    qd, qdd [d][n_traj*T]."""
+    return bspline(extended_knots(U, start, end_static, dt), T, dt)
+
+
+def bspline_bc_vjp(gq, gqd, gqdd, n_traj: int, K: int, T: int, dt: float, has_start=False,
+                   end_static=False):
+    """Gradients of a scalar through bspline_bc: the control-point gradient
+    [n_traj][d][K] (the VJP on the extended sequence, with the repeated final
+    knots folded onto the last control point) and, with a start state, the
+    start-state gradient [n_traj][d][3] through the ghost knots (the
+    transpose of ghost_knots' linear map)."""
+    Kx = K + (3 if has_start else 0) + (3 if end_static else 0)
+    gx = bspline_vjp(gq, gqd, gqdd, n_traj, Kx, T, dt)
+    o = 3 if has_start else 0
+    gU = gx[..., o:o + K].copy()
+    if end_static:
+        gU[..., -1] += gx[..., o + K:].sum(axis=-1)
+    gstart = None
+    if has_start:
+        g3, g2, g1 = gx[..., 0], gx[..., 1], gx[..., 2]
+        gstart = np.stack([g3 + g2 + g1,
+                           dt * g2 + 2.0 * dt * g1,
+                           dt * dt * (-g3 / 6.0 + g2 / 3.0 + 11.0 * g1 / 6.0)], axis=-1)
+    return gU, gstart
+
+
 def trajopt_cost(tau, dmin, tau_lo, tau_hi, w_coll, qd=None, qdd=None, smooth=0.0,
                  length=0.0, energy=0.0, dt=1.0):
     """Per-configuration cost of the trajectory-optimisation workload and its

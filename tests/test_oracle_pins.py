@@ -494,6 +494,81 @@ def test_bspline_vjp_local_support_is_the_textbook_basis(oracle_lib):
         assert np.allclose(Ubd, refd, atol=1e-13)
 
 
+def test_bspline_ghost_knots_continue_the_start_state(oracle_lib):
+    """With a non-static start (Sec. 4.2) the first sampled window is
+    [u_-3, u_-2, u_-1, u_0]; its state at alpha = 0 depends on the ghost
+    knots only and is the start state carried one knot interval forward with
+    zero jerk: q = th0 + v dt + a dt^2 / 2, qd = v + a dt, qdd = a, whatever
+    the optimised control points.  Three equations in the three ghost knots,
+    so a wrong coefficient in any of them shows here."""
+    O = oracle_lib
+    rng = np.random.default_rng(41)
+    n_traj, d, K, T, dt = 3, 5, 8, 12, 0.3
+    start = rng.normal(size=(n_traj, d, 3))
+    th, v, a = start[..., 0], start[..., 1], start[..., 2]
+    for seed in (1, 2):
+        U = np.random.default_rng(seed).normal(size=(n_traj, d, K))
+        for end in (False, True):
+            q, qd, qdd = O.bspline_bc(U, T, dt, start=start, end_static=end)
+            first = np.arange(n_traj) * T  # sample 0 of each trajectory
+            assert np.allclose(q[:, first].T, th + v * dt + a * dt * dt / 2, atol=1e-13)
+            assert np.allclose(qd[:, first].T, v + a * dt, atol=1e-12)
+            assert np.allclose(qdd[:, first].T, a, atol=1e-11)
+
+
+def test_bspline_static_goal_stops_at_the_last_control_point(oracle_lib):
+    """Repeating the final control point until it appears four times (Sec.
+    4.2) makes the last segment constant: the final sample is at u_K-1 with
+    zero velocity and acceleration (Eq. stop-constraint), and so is every
+    sample of that segment."""
+    O = oracle_lib
+    rng = np.random.default_rng(42)
+    n_traj, d, K, T, dt = 2, 4, 9, 25, 0.2
+    U = rng.normal(size=(n_traj, d, K))
+    for start in (None, rng.normal(size=(n_traj, d, 3))):
+        q, qd, qdd = O.bspline_bc(U, T, dt, start=start, end_static=True)
+        nseg = K + 3 + (3 if start is not None else 0) - 3
+        t = np.arange(T) * nseg / (T - 1)
+        last = t >= nseg - 1  # samples inside the final segment
+        assert last.sum() >= 2
+        for tr in range(n_traj):
+            sl = np.arange(tr * T, (tr + 1) * T)[last]
+            assert np.allclose(q[:, sl], U[tr, :, -1:], atol=1e-13)
+            assert np.allclose(qd[:, sl], 0.0, atol=1e-12)
+            assert np.allclose(qdd[:, sl], 0.0, atol=1e-11)
+
+
+def test_bspline_boundary_vjp_is_the_adjoint(oracle_lib):
+    """q, qd, qdd are linear in (U, start state) together, so the VJP with the
+    repeated final knots folded onto u_K-1 and the start-state gradient
+    through the ghost knots must satisfy <g, states> = <gU, U> + <gs, start>;
+    and a unit gradient on the first sample's position reaches the start
+    state only, as d q / d (th0, v, a) = (1, dt, dt^2 / 2)."""
+    O = oracle_lib
+    rng = np.random.default_rng(43)
+    n_traj, d, K, T, dt = 3, 4, 7, 17, 0.25
+    U = rng.normal(size=(n_traj, d, K))
+    start = rng.normal(size=(n_traj, d, 3))
+    g = [rng.normal(size=(d, n_traj * T)) for _ in range(3)]
+    for has_start in (False, True):
+        for end in (False, True):
+            st = start if has_start else None
+            states = O.bspline_bc(U, T, dt, start=st, end_static=end)
+            lhs = sum(float((a * b).sum()) for a, b in zip(states, g))
+            gU, gs = O.bspline_bc_vjp(*g, n_traj, K, T, dt, has_start=has_start,
+                                      end_static=end)
+            rhs = float((U * gU).sum()) + (float((start * gs).sum()) if has_start else 0.0)
+            assert abs(lhs - rhs) <= 1e-11 * max(1.0, abs(lhs)), (has_start, end)
+            assert (gs is None) == (not has_start)
+    g0 = np.zeros((d, n_traj * T))
+    g0[2, T] = 1.0  # joint 2, trajectory 1, sample 0
+    gU, gs = O.bspline_bc_vjp(g0, None, None, n_traj, K, T, dt, has_start=True)
+    assert np.allclose(gU, 0.0, atol=1e-15)
+    ref = np.zeros((n_traj, d, 3))
+    ref[1, 2] = [1.0, dt, dt * dt / 2]
+    assert np.allclose(gs, ref, atol=1e-14)
+
+
 def test_trajopt_cost_closed_form(oracle_lib):
     """Hinges on hand-made torques and distances: only the parts beyond the
     limits count, gradients are +-1 there, and the collision hinge is
