@@ -355,6 +355,39 @@ int wb_bspline_backward(int64_t n_traj, int32_t d, int32_t K, int32_t T, float d
                         const float* gq, const float* gqd, const float* gqdd, float* gU,
                         void* stream);
 
+/* Boundary conditions (Sec. 4.2).  The spline is evaluated on an extended
+ * sequence of Kx = K + 3 [start] + 3 [end_static] knots:
+ *   - start (nullable) [n_traj][d][3] holds theta_0, thetadot_0, thetaddot_0
+ *     per trajectory and joint; the ghost knots of Eqs. fixed_3, fixed_2,
+ *     fixed_1 come first,
+ *       u_-3 = th0 - a0 dt^2 / 6,  u_-2 = th0 + v0 dt + a0 dt^2 / 3,
+ *       u_-1 = th0 + 2 v0 dt + 11 a0 dt^2 / 6,
+ *     so the first sample is the start state carried one knot interval
+ *     forward with zero jerk;
+ *   - end_static != 0 repeats the last control point three more times, so the
+ *     last segment holds it at rest (Eq. stop-constraint).
+ * The T samples spread over the Kx - 3 segments as in wb_bspline_eval.
+ * Limits: 1 <= K <= 4096 and Kx >= 4; T, dt as wb_bspline_eval.  start is a
+ * caller-owned device buffer on the device of U.  With start == NULL and
+ * end_static == 0 this is wb_bspline_eval.
+ * Errors: WB_EINVAL, WB_EDEVICE, WB_ECUDA. */
+int wb_bspline_eval_bc(int64_t n_traj, int32_t d, int32_t K, int32_t T, float dt, const float* U,
+                       const float* start, int32_t end_static, float* q, float* qd, float* qdd,
+                       void* stream);
+
+/* Gradients through wb_bspline_eval_bc (Eq. backward_grad on the extended
+ * sequence): gU [n_traj][d][K] (overwritten; with end_static the last
+ * control point also receives the gradients of its three repeats) and, when
+ * has_start != 0 and g_start != NULL, the start-state gradient g_start
+ * [n_traj][d][3] (the transpose of the ghost knots' linear map applied to
+ * their gradients).  Upstream gradients gq, gqd, gqdd and the additive
+ * gqd_add, gqdd_add [d][n_traj*T], each nullable.  g_start without
+ * has_start is an error.  Deterministic.  Errors as wb_bspline_eval_bc. */
+int wb_bspline_backward_bc(int64_t n_traj, int32_t d, int32_t K, int32_t T, float dt,
+                           int32_t has_start, int32_t end_static, const float* gq,
+                           const float* gqd, const float* gqdd, const float* gqd_add,
+                           const float* gqdd_add, float* gU, float* g_start, void* stream);
+
 /* As wb_bspline_backward, with two more upstream gradients gqd_add and
  * gqdd_add [d][n_traj*T] (nullable) that add to gqd and gqdd before the
  * transpose: the direct state gradients of a cost (wb_trajopt_cost_ext)

@@ -1,6 +1,7 @@
 // k_traj.cu -- the trajectory-optimisation ends of the whole-body evaluation:
 // joint states from uniform cubic B-spline control points (Sec. 4,
-// Eq. bspline-cubic), the control-point gradient (Eq. backward_grad), and the
+// Eq. bspline-cubic) with the boundary conditions of Sec. 4.2, the
+// control-point gradient (Eq. backward_grad), and the
 // per-configuration cost (torque-limit hinges and the self-collision hinge on
 // the worst pair) with its upstream gradients.
 //
@@ -43,10 +44,38 @@ __device__ __forceinline__ void bs_basis(float a, float dt, float Bm[3][4]) {
   }
 }
 
+// Boundary conditions (Sec. 4.2).  The spline is evaluated on an extended
+// knot sequence of Kx = K + 3 hs + 3 es knots: with a start state (hs = 1)
+// the ghost knots u_-3, u_-2, u_-1 of Eqs. fixed_3, fixed_2, fixed_1 come
+// first,
+//   u_-3 = th0 - a0 dt^2 / 6,  u_-2 = th0 + v0 dt + a0 dt^2 / 3,
+//   u_-1 = th0 + 2 v0 dt + 11 a0 dt^2 / 6,
+// and for a static goal (es = 1) the last control point is repeated three
+// more times.  Samples spread over the Kx - 3 segments of the extended
+// sequence; with hs = es = 0 it is U itself.
+struct Knots {
+  const float* u;   // the K control points of one (trajectory, joint)
+  const float* st;  // theta_0, thetadot_0, thetaddot_0 of it, or nullptr
+  int K, hs;
+  float dt;
+  __device__ __forceinline__ float operator()(int x) const {
+    const int r = x - 3 * hs;
+    if (r >= K) return __ldg(u + K - 1);
+    if (r >= 0) return __ldg(u + r);
+    const float th = __ldg(st), v = __ldg(st + 1), a = __ldg(st + 2);
+    const float a2 = a * dt * dt;
+    if (r == -3) return fmaf(-1.0f / 6.0f, a2, th);
+    if (r == -2) return fmaf(1.0f / 3.0f, a2, fmaf(v, dt, th));
+    return fmaf(11.0f / 6.0f, a2, fmaf(2.0f * v, dt, th));
+  }
+};
+
 // one thread per (joint, configuration); b fastest so that stores coalesce
 __global__ void __launch_bounds__(256) bspline_fwd_kernel(int64_t n_traj, int d, int K, int T,
                                                           float dt, const float* __restrict__ U,
-                                                          float* q, float* qd, float* qdd) {
+                                                          const float* __restrict__ start,
+                                                          int es, float* q, float* qd,
+                                                          float* qdd) {
   const int64_t B = n_traj * T;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= B * d) return;
@@ -54,13 +83,15 @@ __global__ void __launch_bounds__(256) bspline_fwd_kernel(int64_t n_traj, int d,
   const int64_t b = idx - (int64_t)j * B;
   const int64_t tr = b / T;
   const int s = (int)(b - tr * T);
+  const int hs = start != nullptr;
+  const int Kx = K + 3 * hs + 3 * es;
   int k;
   float a;
-  bs_sample(s, K, T, k, a);
+  bs_sample(s, Kx, T, k, a);
   float Bm[3][4];
   bs_basis(a, dt, Bm);
-  const float* u = U + (tr * d + j) * K + k;
-  const float u0 = __ldg(u), u1 = __ldg(u + 1), u2 = __ldg(u + 2), u3 = __ldg(u + 3);
+  const Knots kn{U + (tr * d + j) * K, hs ? start + (tr * d + j) * 3 : nullptr, K, hs, dt};
+  const float u0 = kn(k), u1 = kn(k + 1), u2 = kn(k + 2), u3 = kn(k + 3);
   float out[3];
 #pragma unroll
   for (int r = 0; r < 3; ++r)
@@ -71,24 +102,57 @@ __global__ void __launch_bounds__(256) bspline_fwd_kernel(int64_t n_traj, int d,
   if (qdd) qdd[o] = out[2];
 }
 
-// One thread per control point (trajectory, joint, k): it sums
-// B(alpha_s)^T g_s over the samples of segments k-3 .. k in sample order (no
-// atomics, deterministic).  The basis rows and segment of every sample and
-// the first sample of every segment are tabled in shared memory per block.
-__global__ void __launch_bounds__(256) bspline_bwd_kernel(int64_t n_traj, int d, int K, int T,
-                                                          float dt, const float* __restrict__ gq,
-                                                          const float* __restrict__ gqd,
-                                                          const float* __restrict__ gqdd,
-                                                          const float* __restrict__ gqd2,
-                                                          const float* __restrict__ gqdd2,
-                                                          float* gU) {
-  extern __shared__ float tab[];  // [T][12] basis rows, then [K-2] first samples
+// Gradient of extended knot x of one (trajectory, joint): the sum of
+// B(alpha_s)^T g_s over the samples of segments x-3 .. x in sample order.
+struct KnotGrad {
+  const float* tab;  // [T][12] basis rows
+  const int* first;  // [nseg + 1] first sample of each segment
+  int nseg;
+  const float *gq, *gqd, *gqdd, *gqd2, *gqdd2;  // already offset to (joint, trajectory)
+  __device__ __forceinline__ float operator()(int x) const {
+    const int m0 = max(x - 3, 0), m1 = min(x, nseg - 1);
+    float acc = 0.0f;
+    if (m0 <= m1) {
+      int m = m0;
+      for (int s = first[m0]; s < first[m1 + 1]; ++s) {
+        while (s >= first[m + 1]) ++m;  // segment of sample s
+        const int l = x - m;            // this knot's place in the window
+        const float* Bs = tab + s * 12;
+        float c = 0.0f;
+        if (gq) c = fmaf(Bs[l], __ldg(gq + s), c);
+        float gv = gqd ? __ldg(gqd + s) : 0.0f;  // the two qd gradients add
+        if (gqd2) gv += __ldg(gqd2 + s);
+        c = fmaf(Bs[4 + l], gv, c);
+        float ga = gqdd ? __ldg(gqdd + s) : 0.0f;
+        if (gqdd2) ga += __ldg(gqdd2 + s);
+        c = fmaf(Bs[8 + l], ga, c);
+        acc += c;
+      }
+    }
+    return acc;
+  }
+};
+
+// One thread per control point (trajectory, joint, k), plus with a start
+// state one per (trajectory, joint) for the start-state gradient (no atomics,
+// deterministic).  The basis rows and segment of every sample and the first
+// sample of every segment are tabled in shared memory per block.  With a
+// static goal the last control point also sums the gradients of its three
+// repeats; the start-state gradient is the transpose of the ghost knots'
+// linear map applied to their three gradients.
+__global__ void __launch_bounds__(256) bspline_bwd_kernel(
+    int64_t n_traj, int d, int K, int T, float dt, int hs, int es, const float* __restrict__ gq,
+    const float* __restrict__ gqd, const float* __restrict__ gqdd,
+    const float* __restrict__ gqd2, const float* __restrict__ gqdd2, float* gU,
+    float* gstart) {
+  extern __shared__ float tab[];  // [T][12] basis rows, then [Kx-2] first samples
   int* first = reinterpret_cast<int*>(tab + (size_t)T * 12);
-  const int nseg = K - 3;
+  const int Kx = K + 3 * hs + 3 * es;
+  const int nseg = Kx - 3;
   for (int s = threadIdx.x; s < T; s += blockDim.x) {
     int k;
     float a;
-    bs_sample(s, K, T, k, a);
+    bs_sample(s, Kx, T, k, a);
     float Bm[3][4];
     bs_basis(a, dt, Bm);
 #pragma unroll
@@ -101,33 +165,33 @@ __global__ void __launch_bounds__(256) bspline_bwd_kernel(int64_t n_traj, int d,
     first[m] = m == nseg ? T : (m * (T - 1) + nseg - 1) / nseg;
   __syncthreads();
   const int64_t B = n_traj * T;
+  const int per = K + hs;  // threads per (trajectory, joint)
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= n_traj * d * K) return;
-  const int64_t tj = idx / K;  // trajectory * d + joint
-  const int k = (int)(idx - tj * K);
+  if (idx >= n_traj * d * per) return;
+  const int64_t tj = idx / per;  // trajectory * d + joint
+  const int t = (int)(idx - tj * per);
   const int64_t tr = tj / d;
   const int j = (int)(tj - tr * d);
   const int64_t base = (int64_t)j * B + tr * T;
-  const int m0 = max(k - 3, 0), m1 = min(k, nseg - 1);
-  float acc = 0.0f;
-  if (m0 <= m1) {
-    int m = m0;
-    for (int s = first[m0]; s < first[m1 + 1]; ++s) {
-      while (s >= first[m + 1]) ++m;  // segment of sample s
-      const int l = k - m;            // this control point's place in the window
-      const float* Bs = tab + s * 12;
-      float c = 0.0f;
-      if (gq) c = fmaf(Bs[l], __ldg(gq + base + s), c);
-      float gv = gqd ? __ldg(gqd + base + s) : 0.0f;  // the two qd gradients add
-      if (gqd2) gv += __ldg(gqd2 + base + s);
-      c = fmaf(Bs[4 + l], gv, c);
-      float ga = gqdd ? __ldg(gqdd + base + s) : 0.0f;
-      if (gqdd2) ga += __ldg(gqdd2 + base + s);
-      c = fmaf(Bs[8 + l], ga, c);
-      acc += c;
+  const KnotGrad kg{tab, first, nseg, gq ? gq + base : nullptr, gqd ? gqd + base : nullptr,
+                    gqdd ? gqdd + base : nullptr, gqd2 ? gqd2 + base : nullptr,
+                    gqdd2 ? gqdd2 + base : nullptr};
+  if (t < hs) {  // the start-state gradient through u_-3, u_-2, u_-1
+    const float g3 = kg(0), g2 = kg(1), g1 = kg(2);
+    if (gstart) {
+      float* o = gstart + tj * 3;
+      o[0] = g3 + g2 + g1;
+      o[1] = dt * fmaf(2.0f, g1, g2);
+      o[2] = dt * dt * fmaf(11.0f / 6.0f, g1, fmaf(1.0f / 3.0f, g2, (-1.0f / 6.0f) * g3));
     }
+    return;
   }
-  gU[idx] = acc;
+  const int k = t - hs;
+  const int x = k + 3 * hs;
+  float acc = kg(x);
+  if (es && k == K - 1)
+    for (int r = 1; r <= 3; ++r) acc += kg(x + r);
+  gU[tj * K + k] = acc;
 }
 
 // One thread per configuration.  The motion terms of the loss (smooth |qdd|^2,
@@ -190,27 +254,30 @@ __global__ void __launch_bounds__(256) trajopt_cost_kernel(int64_t B, int d,
 // launchers
 // ---------------------------------------------------------------------------
 cudaError_t launch_bspline_fwd(int64_t n_traj, int d, int K, int T, float dt, const float* U,
-                               float* q, float* qd, float* qdd, cudaStream_t s) {
+                               const float* start, int end_static, float* q, float* qd,
+                               float* qdd, cudaStream_t s) {
   const int64_t n = n_traj * T * d;
-  bspline_fwd_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n_traj, d, K, T, dt, U, q, qd,
-                                                                 qdd);
+  bspline_fwd_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n_traj, d, K, T, dt, U, start,
+                                                                 end_static ? 1 : 0, q, qd, qdd);
   return cudaGetLastError();
 }
 
-size_t bspline_bwd_smem(int K, int T) {
-  return sizeof(float) * (size_t)T * 12 + sizeof(int) * (size_t)(K - 2);
+size_t bspline_bwd_smem(int Kx, int T) {
+  return sizeof(float) * (size_t)T * 12 + sizeof(int) * (size_t)(Kx - 2);
 }
 
-cudaError_t launch_bspline_bwd(int64_t n_traj, int d, int K, int T, float dt, const float* gq,
-                               const float* gqd, const float* gqdd, const float* gqd2,
-                               const float* gqdd2, float* gU, cudaStream_t s) {
-  const size_t smem = bspline_bwd_smem(K, T);
+cudaError_t launch_bspline_bwd(int64_t n_traj, int d, int K, int T, float dt, int has_start,
+                               int end_static, const float* gq, const float* gqd,
+                               const float* gqdd, const float* gqd2, const float* gqdd2,
+                               float* gU, float* gstart, cudaStream_t s) {
+  const int hs = has_start ? 1 : 0, es = end_static ? 1 : 0;
+  const size_t smem = bspline_bwd_smem(K + 3 * hs + 3 * es, T);
   cudaError_t e = cudaFuncSetAttribute(bspline_bwd_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int64_t n = n_traj * d * K;
-  bspline_bwd_kernel<<<(unsigned)((n + 255) / 256), 256, smem, s>>>(n_traj, d, K, T, dt, gq, gqd,
-                                                                   gqdd, gqd2, gqdd2, gU);
+  const int64_t n = n_traj * d * (K + hs);
+  bspline_bwd_kernel<<<(unsigned)((n + 255) / 256), 256, smem, s>>>(
+      n_traj, d, K, T, dt, hs, es, gq, gqd, gqdd, gqd2, gqdd2, gU, gstart);
   return cudaGetLastError();
 }
 

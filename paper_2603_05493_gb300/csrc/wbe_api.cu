@@ -1380,41 +1380,61 @@ static int check_buf(const void* p, const char* name, bool required, int* device
   return WB_OK;
 }
 
-static int check_spline(int64_t n_traj, int32_t d, int32_t K, int32_t T, float dt) {
+// K control points extended by 3 ghost knots (has_start) and 3 repeats of
+// the last one (end_static) must give at least one cubic segment
+static int check_spline(int64_t n_traj, int32_t d, int32_t K, int32_t T, float dt,
+                        int has_start = 0, int end_static = 0) {
   if (n_traj < 0 || d < 1 || d > WB_MAX_LINKS) return fail(WB_EINVAL, "bad n_traj or d");
-  if (K < 4 || K > 4096)
-    return fail(WB_EINVAL, "K = %d outside [4, 4096] (a cubic B-spline needs 4 control points)", K);
+  const int Kx = K + (has_start ? 3 : 0) + (end_static ? 3 : 0);
+  if (K < 1 || K > 4096 || Kx < 4)
+    return fail(WB_EINVAL,
+                "K = %d outside [1, 4096] or fewer than 4 knots with the boundary conditions "
+                "(a cubic B-spline needs 4)", K);
   if (T < 2 || T > 4096) return fail(WB_EINVAL, "T = %d outside [2, 4096]", T);
   if (!(dt > 0.0f) || !std::isfinite(dt)) return fail(WB_EINVAL, "dt must be positive");
   if (n_traj * T * (int64_t)d > ((int64_t)1 << 40)) return fail(WB_EINVAL, "too many samples");
   return WB_OK;
 }
 
-int wb_bspline_eval(int64_t n_traj, int32_t d, int32_t K, int32_t T, float dt, const float* U,
-                    float* q, float* qd, float* qdd, void* stream) {
+int wb_bspline_eval_bc(int64_t n_traj, int32_t d, int32_t K, int32_t T, float dt, const float* U,
+                       const float* start, int32_t end_static, float* q, float* qd, float* qdd,
+                       void* stream) {
   g_err.clear();
   int rc, dev = -1;
-  if ((rc = check_spline(n_traj, d, K, T, dt))) return rc;
+  if ((rc = check_spline(n_traj, d, K, T, dt, start != nullptr, end_static))) return rc;
   if ((rc = check_buf(U, "U", n_traj > 0, &dev))) return rc;
+  if ((rc = check_buf(start, "start", false, &dev))) return rc;
   if ((rc = check_buf(q, "q", false, &dev))) return rc;
   if ((rc = check_buf(qd, "qd", false, &dev))) return rc;
   if ((rc = check_buf(qdd, "qdd", false, &dev))) return rc;
   if (n_traj == 0 || (!q && !qd && !qdd)) return WB_OK;
   DeviceGuard guard(dev);
-  cudaError_t e = launch_bspline_fwd(n_traj, d, K, T, dt, U, q, qd, qdd,
+  cudaError_t e = launch_bspline_fwd(n_traj, d, K, T, dt, U, start, end_static, q, qd, qdd,
                                      static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "wb_bspline_eval launch");
   return WB_OK;
 }
 
-int wb_bspline_backward_ext(int64_t n_traj, int32_t d, int32_t K, int32_t T, float dt,
-                            const float* gq, const float* gqd, const float* gqdd,
-                            const float* gqd_add, const float* gqdd_add, float* gU,
-                            void* stream) {
+int wb_bspline_eval(int64_t n_traj, int32_t d, int32_t K, int32_t T, float dt, const float* U,
+                    float* q, float* qd, float* qdd, void* stream) {
+  if (K < 4) {
+    g_err.clear();
+    return fail(WB_EINVAL, "K = %d outside [4, 4096] (a cubic B-spline needs 4 control points)",
+                K);
+  }
+  return wb_bspline_eval_bc(n_traj, d, K, T, dt, U, nullptr, 0, q, qd, qdd, stream);
+}
+
+int wb_bspline_backward_bc(int64_t n_traj, int32_t d, int32_t K, int32_t T, float dt,
+                           int32_t has_start, int32_t end_static, const float* gq,
+                           const float* gqd, const float* gqdd, const float* gqd_add,
+                           const float* gqdd_add, float* gU, float* g_start, void* stream) {
   g_err.clear();
   int rc, dev = -1;
-  if ((rc = check_spline(n_traj, d, K, T, dt))) return rc;
+  if ((rc = check_spline(n_traj, d, K, T, dt, has_start, end_static))) return rc;
+  if (g_start && !has_start) return fail(WB_EINVAL, "g_start without has_start");
   if ((rc = check_buf(gU, "gU", n_traj > 0, &dev))) return rc;
+  if ((rc = check_buf(g_start, "g_start", false, &dev))) return rc;
   if ((rc = check_buf(gq, "gq", false, &dev))) return rc;
   if ((rc = check_buf(gqd, "gqd", false, &dev))) return rc;
   if ((rc = check_buf(gqdd, "gqdd", false, &dev))) return rc;
@@ -1422,10 +1442,24 @@ int wb_bspline_backward_ext(int64_t n_traj, int32_t d, int32_t K, int32_t T, flo
   if ((rc = check_buf(gqdd_add, "gqdd_add", false, &dev))) return rc;
   if (n_traj == 0) return WB_OK;
   DeviceGuard guard(dev);
-  cudaError_t e = launch_bspline_bwd(n_traj, d, K, T, dt, gq, gqd, gqdd, gqd_add, gqdd_add, gU,
+  cudaError_t e = launch_bspline_bwd(n_traj, d, K, T, dt, has_start, end_static, gq, gqd, gqdd,
+                                     gqd_add, gqdd_add, gU, g_start,
                                      static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "wb_bspline_backward launch");
   return WB_OK;
+}
+
+int wb_bspline_backward_ext(int64_t n_traj, int32_t d, int32_t K, int32_t T, float dt,
+                            const float* gq, const float* gqd, const float* gqdd,
+                            const float* gqd_add, const float* gqdd_add, float* gU,
+                            void* stream) {
+  if (K < 4) {
+    g_err.clear();
+    return fail(WB_EINVAL, "K = %d outside [4, 4096] (a cubic B-spline needs 4 control points)",
+                K);
+  }
+  return wb_bspline_backward_bc(n_traj, d, K, T, dt, 0, 0, gq, gqd, gqdd, gqd_add, gqdd_add, gU,
+                                nullptr, stream);
 }
 
 int wb_bspline_backward(int64_t n_traj, int32_t d, int32_t K, int32_t T, float dt,

@@ -229,11 +229,13 @@ cudaError_t hinge_max_blocks_per_sm(const DevRobot& r, int warps, int* out);
 
 // trajectory-optimisation ends (k_traj.cu)
 cudaError_t launch_bspline_fwd(int64_t n_traj, int d, int K, int T, float dt, const float* U,
-                               float* q, float* qd, float* qdd, cudaStream_t s);
-size_t bspline_bwd_smem(int K, int T);
-cudaError_t launch_bspline_bwd(int64_t n_traj, int d, int K, int T, float dt, const float* gq,
-                               const float* gqd, const float* gqdd, const float* gqd2,
-                               const float* gqdd2, float* gU, cudaStream_t s);
+                               const float* start, int end_static, float* q, float* qd,
+                               float* qdd, cudaStream_t s);
+size_t bspline_bwd_smem(int Kx, int T);
+cudaError_t launch_bspline_bwd(int64_t n_traj, int d, int K, int T, float dt, int has_start,
+                               int end_static, const float* gq, const float* gqd,
+                               const float* gqdd, const float* gqd2, const float* gqdd2,
+                               float* gU, float* gstart, cudaStream_t s);
 cudaError_t launch_trajopt_cost(int64_t B, int d, const float* tau, const float* d_min,
                                 const float* qd, const float* qdd, const float* lo,
                                 const float* hi, float w, float smooth, float length, float e,

@@ -332,17 +332,48 @@ class Batch:
                 "wb_batch_eval_backward")
 
 
-def bspline_eval(U, T: int, dt: float, q=None, qd=None, qdd=None, stream=None):
+def bspline_eval(U, T: int, dt: float, q=None, qd=None, qdd=None, stream=None, start=None,
+                 end_static: bool = False):
     """Joint states [d][n_traj*T] from B-spline control points U
-    [n_traj][d][K] (wb_bspline_eval); allocates the outputs it is not given."""
+    [n_traj][d][K] (wb_bspline_eval); allocates the outputs it is not given.
+    With ``start`` [n_traj][d][3] (theta_0, thetadot_0, thetaddot_0) the
+    ghost knots of that start state come first, and ``end_static`` repeats
+    the last control point for a static goal (wb_bspline_eval_bc)."""
     lib = L.load()
     n_traj, d, K = U.shape
     B = n_traj * T
     mk = lambda t: t if t is not None else torch.empty((d, B), device=U.device)  # noqa: E731
     q, qd, qdd = mk(q), mk(qd), mk(qdd)
-    L.check(lib.wb_bspline_eval(n_traj, d, K, int(T), float(dt), _ptr(U), _ptr(q), _ptr(qd),
-                                _ptr(qdd), _stream(stream)), "wb_bspline_eval")
+    if start is None and not end_static:
+        L.check(lib.wb_bspline_eval(n_traj, d, K, int(T), float(dt), _ptr(U), _ptr(q), _ptr(qd),
+                                    _ptr(qdd), _stream(stream)), "wb_bspline_eval")
+    else:
+        L.check(lib.wb_bspline_eval_bc(n_traj, d, K, int(T), float(dt), _ptr(U), _ptr(start),
+                                       1 if end_static else 0, _ptr(q), _ptr(qd), _ptr(qdd),
+                                       _stream(stream)), "wb_bspline_eval_bc")
     return q, qd, qdd
+
+
+def bspline_backward_bc(gq, gqd, gqdd, n_traj: int, K: int, T: int, dt: float,
+                        has_start: bool = False, end_static: bool = False, gU=None,
+                        g_start=None, want_start: bool = True, gqd_add=None, gqdd_add=None,
+                        stream=None):
+    """Gradients through bspline_eval with boundary conditions
+    (wb_bspline_backward_bc): the control-point gradient [n_traj][d][K] and,
+    with a start state (and want_start), the start-state gradient
+    [n_traj][d][3].  Returns (gU, g_start)."""
+    lib = L.load()
+    ref = next(t for t in (gq, gqd, gqdd, gqd_add, gqdd_add) if t is not None)
+    d = ref.shape[0]
+    if gU is None:
+        gU = torch.empty((n_traj, d, K), device=ref.device)
+    if g_start is None and has_start and want_start:
+        g_start = torch.empty((n_traj, d, 3), device=ref.device)
+    L.check(lib.wb_bspline_backward_bc(n_traj, d, K, int(T), float(dt), 1 if has_start else 0,
+                                       1 if end_static else 0, _ptr(gq), _ptr(gqd), _ptr(gqdd),
+                                       _ptr(gqd_add), _ptr(gqdd_add), _ptr(gU), _ptr(g_start),
+                                       _stream(stream)), "wb_bspline_backward_bc")
+    return gU, g_start
 
 
 def bspline_backward(gq, gqd, gqdd, n_traj: int, K: int, T: int, dt: float, gU=None,

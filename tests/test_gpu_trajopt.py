@@ -67,6 +67,85 @@ def test_bspline_forward_and_vjp(W, O, n_traj, d, K, T, dt):
     assert np.abs(gq_only.cpu().numpy() - ref_q).max() <= 1e-5 * max(1.0, np.abs(ref_q).max()) * T
 
 
+@pytest.mark.parametrize("n_traj,d,K,T,dt", [(4, 7, 16, 64, 0.25), (3, 5, 1, 9, 0.3),
+                                             (2, 3, 5, 40, 0.1), (1, 48, 13, 301, 0.05)])
+@pytest.mark.parametrize("has_start,end_static", [(True, False), (False, True), (True, True)])
+def test_bspline_boundary_conditions_match_oracle(W, O, n_traj, d, K, T, dt, has_start,
+                                                  end_static):
+    """Ghost knots from a start state and the static goal (Sec. 4.2): states,
+    control-point gradient and start-state gradient against the oracle."""
+    if K + 3 * has_start + 3 * end_static < 4:
+        pytest.skip("fewer than 4 knots")
+    rng = np.random.default_rng(K * 1000 + T + 7 * has_start + 3 * end_static)
+    U = rng.uniform(-np.pi / 2, np.pi / 2, size=(n_traj, d, K)).astype(np.float32)
+    start = rng.uniform(-1.0, 1.0, size=(n_traj, d, 3)).astype(np.float32) if has_start else None
+    q, qd, qdd = W.bspline_eval(cuda(U), T, dt, start=None if start is None else cuda(start),
+                                end_static=end_static)
+    torch.cuda.synchronize()
+    ref = O.bspline_bc(U.astype(np.float64), T, dt,
+                       start=None if start is None else start.astype(np.float64),
+                       end_static=end_static)
+    for got, r, order in zip((q, qd, qdd), ref, range(3)):
+        scale = np.pi / dt ** order
+        assert np.abs(got.cpu().numpy() - r).max() <= 2e-6 * scale
+    g = [rng.normal(size=(d, n_traj * T)).astype(np.float32) for _ in range(3)]
+    gU, gs = W.bspline_backward_bc(*[cuda(x) for x in g], n_traj, K, T, dt, has_start=has_start,
+                                   end_static=end_static)
+    torch.cuda.synchronize()
+    rU, rs = O.bspline_bc_vjp(*[x.astype(np.float64) for x in g], n_traj, K, T, dt,
+                              has_start=has_start, end_static=end_static)
+    Kx = K + 3 * has_start + 3 * end_static
+    tol = 1e-5 * (1 + T / Kx) * max(1.0, np.abs(rU).max())
+    assert np.abs(gU.cpu().numpy() - rU).max() <= tol * (4 if end_static else 1)
+    if has_start:
+        assert np.abs(gs.cpu().numpy() - rs).max() <= 1e-5 * (1 + T / Kx) * max(1.0, np.abs(rs).max())
+    else:
+        assert gs is None
+    # the additive q-dot / q-ddot gradients join before the transpose
+    gU2, _ = W.bspline_backward_bc(cuda(g[0]), None, None, n_traj, K, T, dt,
+                                   has_start=has_start, end_static=end_static,
+                                   gqd_add=cuda(g[1]), gqdd_add=cuda(g[2]), want_start=False)
+    torch.cuda.synchronize()
+    assert torch.equal(gU2, gU)
+
+
+def test_bspline_boundary_first_sample_and_static_end(W):
+    """Closed forms on the GPU: the first sample carries the start state one
+    interval forward with zero jerk; with a static goal the final sample is
+    the last control point at rest."""
+    rng = np.random.default_rng(77)
+    n_traj, d, K, T, dt = 8, 6, 10, 33, 0.25
+    U = rng.uniform(-1.0, 1.0, size=(n_traj, d, K)).astype(np.float32)
+    start = rng.uniform(-1.0, 1.0, size=(n_traj, d, 3)).astype(np.float32)
+    q, qd, qdd = W.bspline_eval(cuda(U), T, dt, start=cuda(start), end_static=True)
+    torch.cuda.synchronize()
+    q, qd, qdd = (x.cpu().numpy().astype(np.float64) for x in (q, qd, qdd))
+    th, v, a = (start[..., i].astype(np.float64) for i in range(3))
+    first, last = np.arange(n_traj) * T, np.arange(n_traj) * T + T - 1
+    assert np.allclose(q[:, first].T, th + v * dt + a * dt * dt / 2, atol=2e-6)
+    assert np.allclose(qd[:, first].T, v + a * dt, atol=2e-5)
+    assert np.allclose(qdd[:, first].T, a, atol=2e-4)
+    assert np.allclose(q[:, last].T, U[..., -1], atol=2e-6)
+    assert np.allclose(qd[:, last], 0.0, atol=2e-5) and np.allclose(qdd[:, last], 0.0, atol=2e-4)
+
+
+def test_bspline_boundary_errors_and_determinism(W):
+    rng = np.random.default_rng(5)
+    x = cuda(rng.normal(size=(2, 3, 3)))
+    with pytest.raises(W.L.WbError):  # 3 control points, no boundary knots
+        W.bspline_eval(x, 8, 0.1)
+    q, _, _ = W.bspline_eval(x, 8, 0.1, end_static=True)  # 6 knots: fine
+    assert torch.isfinite(q).all()
+    g = cuda(rng.normal(size=(3, 16)))
+    with pytest.raises(W.L.WbError):  # a start-state gradient without a start state
+        W.bspline_backward_bc(g, None, None, 2, 3, 8, 0.1, has_start=False, end_static=True,
+                              g_start=torch.empty((2, 3, 3), device="cuda"))
+    a = W.bspline_backward_bc(g, g, g, 2, 3, 8, 0.1, has_start=True, end_static=True)
+    b = W.bspline_backward_bc(g, g, g, 2, 3, 8, 0.1, has_start=True, end_static=True)
+    torch.cuda.synchronize()
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+
+
 def test_bspline_backward_is_deterministic(W):
     rng = np.random.default_rng(3)
     n_traj, d, K, T = 64, 48, 16, 64
