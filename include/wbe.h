@@ -139,7 +139,10 @@ typedef struct {
   int32_t configs_per_block; /* fused: configurations per CTA; tree: threads per block
                                 of the sweep kernels (32..256); 0 = default */
   int32_t blocks_per_sm;     /* fused: grid = blocks_per_sm * SMs (0 = occupancy);
-                                tree: warps per block of the pair kernel (0 = 8) */
+                                tree: warps per block of the pair kernel (0 = the
+                                most, up to 8, whose per-warp workspaces fit in a
+                                block's shared memory: 8 up to about 850 spheres,
+                                6 at 1020) */
 } wb_tune;
 
 typedef struct {
@@ -208,7 +211,8 @@ int wb_self_collision(wb_robot* robot, int64_t B, const float* link_pose, float*
 /* wb_self_collision with a launch choice: tune->kernel TREE (or AUTO, or a
  * NULL tune) culls 4x4 sphere-group blocks whose bounding-sphere lower bound
  * exceeds an exact upper bound on d_min (the default); TREE_NOCULL screens
- * every block.  tune->blocks_per_sm = warps per block (0 = 8).  Same outputs,
+ * every block.  tune->blocks_per_sm = warps per block (0 = the most, up to 8,
+ * that fit in shared memory).  Same outputs,
  * same tie rule. */
 int wb_self_collision_tuned(wb_robot* robot, int64_t B, const float* link_pose, float* sphere,
                             float* d_min, int32_t* worst_pair, uint32_t* pair_bits,

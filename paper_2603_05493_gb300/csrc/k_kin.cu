@@ -142,6 +142,8 @@ __global__ void __launch_bounds__(256) kin_kernel(DevRobot r, const __grid_const
   }
 }
 
+size_t kin_smem_per_warp(const DevRobot& r) { return sizeof(float) * kin_words(r.n); }
+
 cudaError_t launch_kin(const DevRobot& r, const KinArgs& a, int grid, int warps, cudaStream_t s) {
   const size_t smem = sizeof(float) * kin_words(r.n) * warps;
   cudaError_t e =

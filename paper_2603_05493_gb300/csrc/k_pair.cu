@@ -59,6 +59,8 @@ cudaError_t launch_pair(const DevRobot& r, const PairSchedule32& ps, const FwdAr
   return pair_dispatch(r, ps, a, grid, warps, s, nullptr, cull);
 }
 
+size_t pair_block_smem(const DevRobot& r, int warps, bool bits) { return pair_smem(r, warps, bits); }
+
 cudaError_t pair_max_blocks_per_sm(const DevRobot& r, int warps, bool bits, int* out) {
   FwdArgs a{};
   a.bits = bits ? reinterpret_cast<uint32_t*>(16) : nullptr;  // only selects the variant

@@ -844,6 +844,22 @@ static int fused_shape(const wb_robot* R, bool fwd, bool bits, const wb_tune* t,
 
 static bool plain_fits(const DevRobot& D) { return D.n <= 64 && D.S <= 256; }
 
+// The one-warp-per-configuration kernels (pair map-reduce, summed hinge,
+// kinematics) keep a per-warp workspace in shared memory; a block takes the
+// most warps, up to 8, whose workspaces fit in one CTA's shared memory
+// (0: not even one fits).
+constexpr size_t kMaxBlockSmem = 227 * 1024;
+static int warps_that_fit(size_t fixed_bytes, size_t per_warp_bytes) {
+  for (int w = 8; w >= 1; --w)
+    if (fixed_bytes + per_warp_bytes * w <= kMaxBlockSmem) return w;
+  return 0;
+}
+static int pair_warps(const DevRobot& D, bool bits, const wb_tune* tune) {
+  if (tune && tune->blocks_per_sm) return tune->blocks_per_sm;
+  const size_t one = pair_block_smem(D, 1, bits), none = pair_block_smem(D, 0, bits);
+  return warps_that_fit(none, one - none);
+}
+
 // Segments of the sweep kernels (wb_tune.lanes_per_config for TREE): 1, 2, 4
 // or 8; 0 = the fewest of the robot's plans that give about 12 warps per SM --
 // measured on the 48-DoF humanoid at 32768 configurations: both passes best
@@ -926,8 +942,12 @@ int wb_eval_ext(wb_robot* robot, int64_t B, const float* q, const float* qd, con
     const int tpb = (tune && tune->configs_per_block) ? tune->configs_per_block : 128;
     if (tpb < 32 || tpb > 256 || tpb % 32)
       return fail(WB_EINVAL, "tree threads per block must be a multiple of 32 in [32, 256]");
-    const int warps = (tune && tune->blocks_per_sm) ? tune->blocks_per_sm : 8;
-    if (warps < 1 || warps > 8) return fail(WB_EINVAL, "pair warps per block must be in [1, 8]");
+    const int warps = pair_warps(robot->dev, pair_bits != nullptr, tune);
+    if (tune && tune->blocks_per_sm && (warps < 1 || warps > 8))
+      return fail(WB_EINVAL, "pair warps per block must be in [1, 8]");
+    if (pairs_wanted && warps == 0) return fail(WB_ETOOBIG, "pair kernel does not fit on an SM");
+    if (pairs_wanted && pair_block_smem(robot->dev, warps, pair_bits != nullptr) > kMaxBlockSmem)
+      return fail(WB_ETOOBIG, "%d pair warps per block need too much shared memory", warps);
     int G = 1;
     if ((rc = tree_segments(robot, tune, B, tpb, true, &G))) return rc;
     e = launch_tree_fwd(robot->dev, a, tpb, G, s);
@@ -980,8 +1000,12 @@ int wb_self_collision_tuned(wb_robot* robot, int64_t B, const float* link_pose, 
   const int kernel = tune ? tune->kernel : WB_KERNEL_AUTO;
   if (kernel != WB_KERNEL_AUTO && kernel != WB_KERNEL_TREE && kernel != WB_KERNEL_TREE_NOCULL)
     return fail(WB_EINVAL, "the pair kernel takes TREE (culled) or TREE_NOCULL");
-  const int warps = (tune && tune->blocks_per_sm) ? tune->blocks_per_sm : 8;
-  if (warps < 1 || warps > 8) return fail(WB_EINVAL, "pair warps per block must be in [1, 8]");
+  const int warps = pair_warps(robot->dev, pair_bits != nullptr, tune);
+  if (tune && tune->blocks_per_sm && (warps < 1 || warps > 8))
+    return fail(WB_EINVAL, "pair warps per block must be in [1, 8]");
+  if (warps == 0) return fail(WB_ETOOBIG, "pair kernel does not fit on an SM");
+  if (pair_block_smem(robot->dev, warps, pair_bits != nullptr) > kMaxBlockSmem)
+    return fail(WB_ETOOBIG, "%d pair warps per block need too much shared memory", warps);
   int bps = 0;
   cudaError_t e = pair_max_blocks_per_sm(robot->dev, warps, pair_bits != nullptr, &bps);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
@@ -1016,7 +1040,8 @@ int wb_kinematics(wb_robot* robot, int64_t B, const float* link_pose, int32_t n_
   if ((rc = check_ptr(robot, com, "com", false))) return rc;
   if ((rc = check_ptr(robot, jac_com, "jac_com", false))) return rc;
   DeviceGuard guard(robot->device);
-  const int warps = 8;
+  const int warps = warps_that_fit(0, kin_smem_per_warp(robot->dev));
+  if (warps == 0) return fail(WB_ETOOBIG, "kinematics kernel does not fit on an SM");
   int bps = 0;
   cudaError_t e = kin_max_blocks_per_sm(robot->dev, warps, &bps);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
@@ -1046,7 +1071,8 @@ int wb_self_collision_hinge(wb_robot* robot, int64_t B, const float* link_pose, 
   if ((rc = check_ptr(robot, cost, "cost", false))) return rc;
   if ((rc = check_ptr(robot, g_sphere, "g_sphere", false))) return rc;
   DeviceGuard guard(robot->device);
-  const int warps = 8;
+  const int warps = warps_that_fit(0, hinge_smem_per_warp(robot->dev));
+  if (warps == 0) return fail(WB_ETOOBIG, "hinge kernel does not fit on an SM");
   int bps = 0;
   cudaError_t e = hinge_max_blocks_per_sm(robot->dev, warps, &bps);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
@@ -1308,7 +1334,8 @@ int wb_batch_eval(wb_batch* batch, const float* q, const float* qd, const float*
     if (e != cudaSuccess) return cuda_fail(e, "wb_batch_eval launch");
   }
   if (pairs && batch->n_pitems > 0) {
-    const int warps = 8;
+    const int warps = warps_that_fit(0, batch_pair_smem(batch->ws_words, batch->rad_words, 1));
+    if (warps == 0) return fail(WB_ETOOBIG, "batch pair kernel does not fit on an SM");
     int bps = 0;
     e = batch_pair_max_blocks_per_sm(warps, batch->ws_words, batch->rad_words, &bps);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
@@ -1621,7 +1648,8 @@ int wb_batch_eval_noalloc(wb_robot* const* robots, int32_t n_robots, const wb_pr
     if (e != cudaSuccess) return cuda_fail(e, "wb_batch_eval_noalloc launch");
   }
   if (pairs) {
-    const int warps = 8;
+    const int warps = warps_that_fit(0, batch_pair_smem(ws_words, rad_words, 1));
+    if (warps == 0) return fail(WB_ETOOBIG, "batch pair kernel does not fit on an SM");
     int bps = 0;
     e = batch_pair_max_blocks_per_sm(warps, ws_words, rad_words, &bps);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");

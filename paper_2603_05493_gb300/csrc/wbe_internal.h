@@ -168,6 +168,7 @@ cudaError_t launch_batch_pair(const DevRobot* robots, const PairSchedule32* sche
                               int* counter, const BatchIO& io, int grid, int warps, int ws_words,
                               int rad_words, cudaStream_t s);
 cudaError_t batch_pair_max_blocks_per_sm(int warps, int ws_words, int rad_words, int* out);
+size_t batch_pair_smem(int ws_words, int rad_words, int warps);
 
 // Forward batch evaluation on tables in a file-scope device array
 // (k_noalloc.cu).  The limits equal the public WB_NOALLOC_MAX_* values.
@@ -213,6 +214,7 @@ struct KinArgs {
 };
 cudaError_t launch_kin(const DevRobot& r, const KinArgs& a, int grid, int warps, cudaStream_t s);
 cudaError_t kin_max_blocks_per_sm(const DevRobot& r, int warps, int* out);
+size_t kin_smem_per_warp(const DevRobot& r);
 
 // all-pairs summed collision hinge (k_hinge.cu)
 struct HingeArgs {
@@ -251,6 +253,7 @@ cudaError_t launch_tree_bwd(const DevRobot& r, const BwdArgs& a, int threads, in
 size_t tree_seg_smem(const DevRobot& r, int segments, int threads, bool fwd);
 int tree_max_depth();
 size_t pair_smem(const DevRobot& r, int warps, bool bits);
+size_t pair_block_smem(const DevRobot& r, int warps, bool bits);  // the same, out of line
 cudaError_t launch_pair(const DevRobot& r, const PairSchedule32& ps, const FwdArgs& a, int grid,
                         int warps, cudaStream_t s, bool cull = true);
 cudaError_t pair_max_blocks_per_sm(const DevRobot& r, int warps, bool bits, int* out);

@@ -411,5 +411,26 @@ def mixed_joint_tree(seed: int = 11) -> Robot:
     return rob.with_pairs(mask_pairs(parent, sph_link, 2))
 
 
+def max_size(seed: int = 255, min_tree_dist: int = 24) -> Robot:
+    """The largest robot the library accepts: 255 links (a fixed base with 4
+    spheres and 254 revolute links: 8 chains of 31 and one of 6 hanging from
+    the base), 1020 spheres (4 per link), 32 tree levels (the deepest tree the
+    sweep kernels take); pairs on links >= `min_tree_dist` apart."""
+    parent = [-1]
+    for c in range(9):
+        length = 31 if c < 8 else 6
+        parent += _chain(0, length, len(parent))
+    jtype = [FIXED] + [REVOLUTE] * (len(parent) - 1)
+    return _build("max255", seed, parent, jtype, 4, 0.02, 0.06, min_tree_dist)
+
+
+def deep_chain(n: int = 33, seed: int = 33) -> Robot:
+    """A serial chain of n revolute links, 1 sphere each (one level deeper
+    than the sweep kernels take when n = 33)."""
+    parent = [-1] + list(range(n - 1))
+    return _build("chain%d" % n, seed, parent, [REVOLUTE] * n, 0, 0.02, 0.05, 2,
+                  spheres_per_link=1)
+
+
 def get(name: str) -> Robot:
     return {"R7": r7, "R23": r23, "R48": r48}[name]()

@@ -352,3 +352,81 @@ def test_tree_segments_parity(W, O, rname, G):
     torch.cuda.synchronize()
     for a, b in zip(g, g1):
         torch.testing.assert_close(a, b, rtol=1e-4, atol=1e-4 * float(b.abs().max()))
+
+
+def test_maximum_size_robot(W, O):
+    """The largest robot the library takes: 255 links, 1020 spheres, 32 tree
+    levels (the sweep kernels' limit) and 330,624 masked pairs.  Forward
+    (culled and full pair stage, with pair bits) and backward against the
+    oracle on a ragged batch; the plain kernel refuses it; the pair kernel
+    takes the 6 warps per block that fit in shared memory."""
+    from paper_2603_05493_gb300 import _lib as L
+    desc = R.max_size()
+    assert (desc.n, desc.S, int(desc.depth().max()) + 1) == (255, 1020, 32)
+    rob = W.Robot(desc, device=0)
+    B = 45
+    q, qd, qdd = I.uniform_states(desc.dof, B, seed=255)
+    ref = O.evaluate(desc, q, qd, qdd)
+    for tune in (W.TREE, W.TREE_NOCULL, None):
+        PY.check_forward(desc, run_fwd(rob, q, qd, qdd, tune, bits=True), ref)
+    with pytest.raises(L.WbError) as e:
+        rob.eval(cuda(q), cuda(qd), cuda(qdd), tune=W.PLAIN)
+    assert e.value.code == L.WB_ETOOBIG
+    with pytest.raises(L.WbError) as e:  # 8 pair warps do not fit at this size
+        rob.eval(cuda(q), cuda(qd), cuda(qdd), tune=W.Tune(kernel=3, blocks_per_sm=8))
+    assert e.value.code == L.WB_ETOOBIG
+    Bb = 7
+    gp, gs, gm, gt = I.upstream_grads(desc, Bb, seed=256)
+    o = rob.eval(cuda(q[:, :Bb]), cuda(qd[:, :Bb]), cuda(qdd[:, :Bb]))
+    g = rob.eval_backward(cuda(q[:, :Bb]), cuda(qd[:, :Bb]), cuda(qdd[:, :Bb]), o["worst"],
+                          cuda(gp), cuda(gs), cuda(gm), cuda(gt))
+    torch.cuda.synchronize()
+    gref = O.gradient(desc, q[:, :Bb], qd[:, :Bb], qdd[:, :Bb], gp, gs, gm, gt)
+    same = o["worst"].cpu().numpy() == ref["worst"][:Bb]
+    assert same.mean() >= 0.7
+    PY.check_gradient([x.cpu().numpy() for x in g], gref, mask=same)
+    # the summed hinge and the kinematics outputs at this size
+    pose = o["pose"]
+    cost, gsph = rob.self_collision_hinge(pose, 0.02, 1.0)
+    rc, rg = O.pair_hinge(desc, q[:, :Bb], 0.02, 1.0)
+    torch.cuda.synchronize()
+    assert np.allclose(cost.cpu().numpy(), rc, rtol=1e-4, atol=1e-3)
+    jac, com, jcom = rob.kinematics(pose, [desc.n - 1, 31])
+    rJ, rcom, rJc = O.kinematics(desc, q[:, :Bb], [desc.n - 1, 31])
+    torch.cuda.synchronize()
+    assert np.abs(com.cpu().numpy() - rcom).max() <= 1e-4
+    assert np.abs(jac.cpu().numpy() - rJ).max() <= 1e-4 * max(1.0, np.abs(rJ).max())
+    assert np.abs(jcom.cpu().numpy() - rJc).max() <= 1e-4 * max(1.0, np.abs(rJc).max())
+
+
+def test_too_large_robots_are_refused(W):
+    """One link, one sphere or one tree level past the limits: the first two
+    fail to load with WB_ETOOBIG; the 33-level chain loads, the tree kernels
+    refuse it and the automatic choice runs the fused kernels."""
+    from paper_2603_05493_gb300 import _lib as L
+    big = R.max_size()
+    from dataclasses import replace
+    more_links = replace(big, parent=np.append(big.parent, 0), jtype=np.append(big.jtype, 1),
+                         axis=np.vstack([big.axis, [[0, 0, 1]]]),
+                         T_fixed=np.vstack([big.T_fixed, big.T_fixed[1:2]]),
+                         jidx=np.append(big.jidx, big.dof), mimic_mult=np.append(big.mimic_mult, 1),
+                         mimic_off=np.append(big.mimic_off, 0), mass=np.append(big.mass, 1),
+                         com=np.vstack([big.com, [[0, 0, 0]]]),
+                         Icom=np.vstack([big.Icom, big.Icom[1:2]]))
+    with pytest.raises(L.WbError) as e:
+        W.Robot(more_links, device=0)
+    assert e.value.code == L.WB_ETOOBIG
+    more_sph = replace(big, sph_link=np.append(big.sph_link, 1),
+                       sph_c=np.vstack([big.sph_c, [[0, 0, 0]]]), sph_r=np.append(big.sph_r, 0.01))
+    with pytest.raises(L.WbError) as e:
+        W.Robot(more_sph, device=0)
+    assert e.value.code == L.WB_ETOOBIG
+    deep = R.deep_chain(33)
+    rob = W.Robot(deep, device=0)
+    q = torch.zeros((deep.dof, 40), device="cuda")
+    with pytest.raises(L.WbError) as e:
+        rob.eval(q, q, q, tune=W.TREE)
+    assert e.value.code == L.WB_ETOOBIG
+    o = rob.eval(q, q, q)
+    torch.cuda.synchronize()
+    assert torch.isfinite(o["tau"]).all()
