@@ -27,6 +27,8 @@
 
 #include "spatial.cuh"
 
+#include <cuda_fp16.h>
+
 #include <climits>
 
 namespace wbe {
@@ -35,6 +37,7 @@ __host__ __device__ constexpr int a32(int x) { return (x + 31) & ~31; }
 
 struct PairPlan {  // per warp, 32-bit words
   int xr, yr, zr, xc, yc, zc, nn, gb, q, bits, total;
+  __host__ __device__ int ra_words() const { return xc; }  // the row (and pose) region
   __host__ __device__ PairPlan(int n, int Sg, int P, bool with_bits) {
     const int m = a32(4 * Sg);
     const int ra = 3 * m > a32(12 * n) ? 3 * m : a32(12 * n);  // rows; poses while staging
@@ -296,11 +299,15 @@ __device__ __forceinline__ void pair_one(const DevRobot& r, const PairSchedule32
 // a block whose lb exceeds an upper bound on d_min holds no candidate for the
 // minimum (nor, with lb >= 0, a colliding pair).  Pass 1 finds the block of
 // smallest lb and the exact minimum of its pairs, a real pair distance and
-// so an upper bound on d_min; pass 2 walks the schedule again, keeps the
-// blocks with lb within the margin of the current bound (or below 0 when
-// the pair bits are wanted), queues them warp-wide (ballot + prefix count)
-// and screens 32 queued blocks at a time with the usual screen and exact
-// path.  The result -- d_min, the worst pair with its tie rule, the bits --
+// so an upper bound on d_min, and keeps every block's lb as a half, rounded
+// down below a margin for the approximate square root; pass 2 walks the
+// schedule again, keeps the blocks whose stored lb is within the margin of
+// the current bound (or below 0 when the pair bits are wanted) -- a superset
+// of the blocks an exact test would keep -- queues them warp-wide (ballot +
+// prefix count) and screens 32 queued blocks at a time with the usual screen
+// and exact path.  The culled path forms the row copies of a block's spheres
+// (-2 c) when it screens the block, and keeps the bounds where the full
+// map-reduce keeps those copies.  The result -- d_min, the worst pair with its tie rule, the bits --
 // is that of the full map-reduce; only blocks that cannot affect it are
 // skipped.
 template <bool FULL, bool BITS>
@@ -309,8 +316,6 @@ __device__ __forceinline__ void pair_one_culled(const DevRobot& r, const PairSch
                                                 const float4* radw, int lane) {
   const PairPlan pl(r.n, r.Sg, r.P, BITS);
   float* xr = ws + pl.xr;
-  float* yr = ws + pl.yr;
-  float* zr = ws + pl.zr;
   float* xc = ws + pl.xc;
   float* yc = ws + pl.yc;
   float* zc = ws + pl.zc;
@@ -318,9 +323,6 @@ __device__ __forceinline__ void pair_one_culled(const DevRobot& r, const PairSch
   float4* gb = reinterpret_cast<float4*>(ws + pl.gb);
   uint32_t* qu = reinterpret_cast<uint32_t*>(ws + pl.q);
   uint32_t* bm = reinterpret_cast<uint32_t*>(ws + pl.bits);
-  const char* cxr = reinterpret_cast<const char*>(xr);
-  const char* cyr = reinterpret_cast<const char*>(yr);
-  const char* czr = reinterpret_cast<const char*>(zr);
   const char* cxc = reinterpret_cast<const char*>(xc);
   const char* cyc = reinterpret_cast<const char*>(yc);
   const char* czc = reinterpret_cast<const char*>(zc);
@@ -363,11 +365,6 @@ __device__ __forceinline__ void pair_one_culled(const DevRobot& r, const PairSch
     nn[s] = fmaf(-rs, rs, fmaf(c[2], c[2], fmaf(c[1], c[1], c[0] * c[0])));  // |c|^2 - r^2
   }
   __syncwarp();
-  for (int s = lane; s < 4 * Sg; s += 32) {  // row copies, pre-scaled by -2
-    xr[s] = -2.0f * xc[s];
-    yr[s] = -2.0f * yc[s];
-    zr[s] = -2.0f * zc[s];
-  }
   for (int g = lane; g < Sg; g += 32) {  // group bounding spheres
     const int s0 = 4 * g, s1 = min(S, s0 + 4);
     float cx = 0.0f, cy = 0.0f, cz = 0.0f;
@@ -402,18 +399,29 @@ __device__ __forceinline__ void pair_one_culled(const DevRobot& r, const PairSch
   const float inf = __int_as_float(0x7f800000);
   // ---- pass 1: the block of smallest lower bound (approximately: any block
   // gives a valid bound), and the exact minimum of its pairs ----
+  // The lower bounds are kept for pass 2 as halves in the (now free) row
+  // region when they fit, rounded down after a widening that covers the
+  // approximate square root, so that pass 2 keeps every block its exact test
+  // would keep (and at most a few more, within the half's rounding).
+  const bool keep_lb = rounds * 32 <= 2 * pl.ra_words();
+  __half* lb16 = reinterpret_cast<__half*>(xr);
   float lbmin = inf;
   uint2 ebest = make_uint2(0u, 0u);
   for (int rr = 0; rr < rounds; ++rr) {
     const uint2 e = __ldg(ps.ent + rr * 32 + lane);
-    if ((e.y >> 16) == 0u) continue;  // null entry
-    const float4 P4 = gb[(e.x & 0xFFFF) >> 4], Q4 = gb[(e.x >> 16) >> 4];
-    const float D2 = fmaxf(dist2(P4.x, P4.y, P4.z, Q4.x, Q4.y, Q4.z), 1e-30f);
-    const float lb = D2 * rsqrtf(D2) - (P4.w + Q4.w);  // approximate square root
-    if (lb < lbmin) {
-      lbmin = lb;
-      ebest = e;
+    __half low = __float2half(inf);  // null entries are never kept
+    if ((e.y >> 16) != 0u) {  // a real block
+      const float4 P4 = gb[(e.x & 0xFFFF) >> 4], Q4 = gb[(e.x >> 16) >> 4];
+      const float D2 = fmaxf(dist2(P4.x, P4.y, P4.z, Q4.x, Q4.y, Q4.z), 1e-30f);
+      const float dist = D2 * rsqrtf(D2);  // approximate square root
+      const float lb = dist - (P4.w + Q4.w);
+      if (lb < lbmin) {
+        lbmin = lb;
+        ebest = e;
+      }
+      low = __float2half_rd(lb - fmaf(dist, 4e-6f, 4e-6f));
     }
+    if (keep_lb) lb16[rr * 32 + lane] = low;
   }
   float gbest;
   {
@@ -446,7 +454,10 @@ __device__ __forceinline__ void pair_one_culled(const DevRobot& r, const PairSch
   auto screen_block = [&](uint2 e) {
     const uint32_t ro = e.x & 0xFFFF, co = e.x >> 16;
     const uint32_t mask = e.y >> 16;
-    const float4 XR = lds4(cxr, ro), YR = lds4(cyr, ro), ZR = lds4(czr, ro);
+    const float4 XC = lds4(cxc, ro), YC = lds4(cyc, ro), ZC = lds4(czc, ro);
+    const float4 XR = make_float4(-2.0f * XC.x, -2.0f * XC.y, -2.0f * XC.z, -2.0f * XC.w);
+    const float4 YR = make_float4(-2.0f * YC.x, -2.0f * YC.y, -2.0f * YC.z, -2.0f * YC.w);
+    const float4 ZR = make_float4(-2.0f * ZC.x, -2.0f * ZC.y, -2.0f * ZC.z, -2.0f * ZC.w);
     const float4 RR = lds4(crad, ro), NI = lds4(cnn, ro);
     const float4 CC = make_float4(fmaf(RR.x, RR.x, NI.x), fmaf(RR.y, RR.y, NI.y),
                                   fmaf(RR.z, RR.z, NI.z), fmaf(RR.w, RR.w, NI.w));  // |c_i|^2
@@ -509,16 +520,21 @@ __device__ __forceinline__ void pair_one_culled(const DevRobot& r, const PairSch
   };
   for (int rr = 0; rr < rounds; ++rr) {
     const int idx = rr * 32 + lane;
-    const uint2 e = __ldg(ps.ent + idx);
     // lb <= bound + tol  <=>  |C_i - C_j| <= t := bound + tol + R_i + R_j,
     // tested on squares (t >= 0); the tolerance covers the float rounding
     bool keep = false;
-    if ((e.y >> 16) != 0u) {
-      const float4 P4 = gb[(e.x & 0xFFFF) >> 4], Q4 = gb[(e.x >> 16) >> 4];
-      const float D2 = dist2(P4.x, P4.y, P4.z, Q4.x, Q4.y, Q4.z);
-      const float RR2 = P4.w + Q4.w + reach_tol;
-      const float t = fminf(best, gbest) + RR2;
-      keep = (t >= 0.0f && D2 <= t * t) || (BITS && RR2 >= 0.0f && D2 <= RR2 * RR2);
+    if (keep_lb) {  // null entries hold +inf
+      const float lbv = __half2float(lb16[idx]);
+      keep = lbv <= fminf(best, gbest) + reach_tol || (BITS && lbv <= reach_tol);
+    } else {
+      const uint2 e = __ldg(ps.ent + idx);
+      if ((e.y >> 16) != 0u) {
+        const float4 P4 = gb[(e.x & 0xFFFF) >> 4], Q4 = gb[(e.x >> 16) >> 4];
+        const float D2 = dist2(P4.x, P4.y, P4.z, Q4.x, Q4.y, Q4.z);
+        const float RR2 = P4.w + Q4.w + reach_tol;
+        const float t = fminf(best, gbest) + RR2;
+        keep = (t >= 0.0f && D2 <= t * t) || (BITS && RR2 >= 0.0f && D2 <= RR2 * RR2);
+      }
     }
     const uint32_t ball = __ballot_sync(0xffffffffu, keep);
     if (keep) qu[qn + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)idx;
