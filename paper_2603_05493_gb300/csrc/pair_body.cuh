@@ -293,8 +293,10 @@ __device__ __forceinline__ void pair_one(const DevRobot& r, const PairSchedule32
 // ---------------------------------------------------------------------------
 // The same map-reduce with whole blocks culled by group bounding spheres.
 //
-// Every 4-sphere group gets a bounding sphere (C_g, R_g): the mean of its
-// centres and the largest |c - C_g| + r, widened for float rounding.  For any
+// Every 4-sphere group gets a bounding sphere (C_g, R_g): for a group on one
+// link, a host-made sphere in that link's frame moved with the link;
+// otherwise the mean of its centres and the largest |c - C_g| + r; both
+// widened for float rounding.  For any
 // pair (a in group i, b in group j), d_ab >= |C_i - C_j| - R_i - R_j =: lb, so
 // a block whose lb exceeds an upper bound on d_min holds no candidate for the
 // minimum (nor, with lb >= 0, a colliding pair).  Pass 1 finds the block of
@@ -366,6 +368,21 @@ __device__ __forceinline__ void pair_one_culled(const DevRobot& r, const PairSch
   }
   __syncwarp();
   for (int g = lane; g < Sg; g += 32) {  // group bounding spheres
+    const int gl = __ldg(r.grp_link + g);
+    if (gl >= 0) {  // one link: its host-made bound, moved with the link
+      const float4 L = __ldg(r.grp_loc + g);
+      const float* T = xr + 12 * gl;  // the staged pose
+      const float cl[3] = {L.x, L.y, L.z};
+      float c[3];
+      rot(T, cl, c);
+      // widened for the rounding of this transform and of the sphere
+      // placement (a few ulp of the coordinates' size each)
+      const float scale = fabsf(T[9]) + fabsf(T[10]) + fabsf(T[11]) + fabsf(L.x) + fabsf(L.y) +
+                          fabsf(L.z);
+      gb[g] = make_float4(c[0] + T[9], c[1] + T[10], c[2] + T[11],
+                          fmaf(scale, 1e-6f, fmaf(L.w, 1e-6f, L.w)) + 1e-6f);
+      continue;
+    }
     const int s0 = 4 * g, s1 = min(S, s0 + 4);
     float cx = 0.0f, cy = 0.0f, cz = 0.0f;
     for (int s = s0; s < s1; ++s) {

@@ -207,7 +207,8 @@ struct HostPlan {
       jl_links, ls_start, ls_sph, sph_link;
   std::vector<int8_t> jtype, rot_id;
   std::vector<float> axis, Tf, mimic, inert;
-  std::vector<float4> sp, grp_rad;
+  std::vector<float4> sp, grp_rad, grp_loc;
+  std::vector<int16_t> grp_link;
   std::vector<int2> pairs_dev;
   std::vector<int32_t> adj_start;
   std::vector<int16_t> adj;
@@ -452,6 +453,67 @@ static int plan_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs
   const int Sg = std::max((S + 3) / 4, 1);
   std::vector<float4> grp_rad(Sg, make_float4(0, 0, 0, 0));
   for (int s = 0; s < S; ++s) (&grp_rad[s / 4].x)[s % 4] = sp[s].w;
+  // A group whose spheres all sit on one link gets a bounding sphere in that
+  // link's frame, computed here once (the pair stage then moves it with the
+  // link); other groups are bounded per configuration.  Centre: the better
+  // of the centroid and a Badoiu-Clarkson minimax iteration; radius: the
+  // largest |c_s - C| + r_s from the float centre, rounded up.
+  std::vector<float4> grp_loc(Sg, make_float4(0, 0, 0, 0));
+  std::vector<int16_t> grp_link(Sg, -1);
+  for (int g = 0; g < Sg; ++g) {
+    const int s0 = 4 * g, s1 = std::min(S, s0 + 4);
+    if (s1 <= s0) continue;
+    bool one = true;
+    for (int q = s0 + 1; q < s1; ++q) one = one && sph_link[q] == sph_link[s0];
+    if (!one) continue;
+    auto radius = [&](const double* C) {
+      double R = 0.0;
+      for (int q = s0; q < s1; ++q) {
+        const double dx = sp[q].x - C[0], dy = sp[q].y - C[1], dz = sp[q].z - C[2];
+        R = std::max(R, std::sqrt(dx * dx + dy * dy + dz * dz) + (double)sp[q].w);
+      }
+      return R;
+    };
+    double cen[3] = {0, 0, 0};
+    for (int q = s0; q < s1; ++q) {
+      cen[0] += sp[q].x / (s1 - s0);
+      cen[1] += sp[q].y / (s1 - s0);
+      cen[2] += sp[q].z / (s1 - s0);
+    }
+    double best[3] = {cen[0], cen[1], cen[2]}, bestR = radius(cen);
+    double C[3] = {cen[0], cen[1], cen[2]};
+    for (int it = 0; it < 200; ++it) {  // step towards the far point of the farthest sphere
+      int far = s0;
+      double fd = -1.0;
+      for (int q = s0; q < s1; ++q) {
+        const double dx = sp[q].x - C[0], dy = sp[q].y - C[1], dz = sp[q].z - C[2];
+        const double dq = std::sqrt(dx * dx + dy * dy + dz * dz) + sp[q].w;
+        if (dq > fd) {
+          fd = dq;
+          far = q;
+        }
+      }
+      const double dx = sp[far].x - C[0], dy = sp[far].y - C[1], dz = sp[far].z - C[2];
+      const double nn = std::sqrt(dx * dx + dy * dy + dz * dz);
+      const double k = nn > 0.0 ? (nn + sp[far].w) / nn : 0.0;
+      const double step = 1.0 / (it + 2);
+      C[0] += step * dx * k;
+      C[1] += step * dy * k;
+      C[2] += step * dz * k;
+      const double R = radius(C);
+      if (R < bestR) {
+        bestR = R;
+        best[0] = C[0];
+        best[1] = C[1];
+        best[2] = C[2];
+      }
+    }
+    const float fc[3] = {(float)best[0], (float)best[1], (float)best[2]};
+    const double dc[3] = {fc[0], fc[1], fc[2]};
+    const float R = std::nextafter((float)radius(dc), INFINITY);
+    grp_loc[g] = make_float4(fc[0], fc[1], fc[2], R);
+    grp_link[g] = sph_link[s0];
+  }
   std::vector<int> blk_of((size_t)Sg * Sg, -1);
   std::vector<uint32_t> bx;  // gi | gj << 8 | mask << 16
   std::vector<int32_t> blk_pidx;
@@ -565,6 +627,8 @@ static int plan_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs
   H.inert.swap(inert);
   H.sp.swap(sp);
   H.grp_rad.swap(grp_rad);
+  H.grp_loc.swap(grp_loc);
+  H.grp_link.swap(grp_link);
   H.pairs_dev.swap(pairs_dev);
   H.bx.swap(bx);
   H.blk_pidx.swap(blk_pidx);
@@ -686,6 +750,8 @@ int wb_load_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs* pa
   pk.add_vec(H.adj_start, &D.adj_start);
   pk.add_vec(H.adj, &D.adj);
   pk.add_vec(H.grp_rad, &D.grp_rad);
+  pk.add_vec(H.grp_loc, &D.grp_loc);
+  pk.add_vec(H.grp_link, &D.grp_link);
   pk.add_vec(H.blk_pidx, &D.blk_pidx);
   std::vector<uint2> ents[4];
   for (int t = 0; t < 4; ++t) {

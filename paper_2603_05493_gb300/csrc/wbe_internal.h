@@ -64,6 +64,8 @@ struct DevRobot {
   const int16_t* sph_link;   // [S]
   const int2* pairs;         // [P] sorted row-major
   const float4* grp_rad;     // [Sg] radii of the 4 spheres of a group (0 pad)
+  const float4* grp_loc;     // [Sg] bounding sphere of a one-link group in its link frame
+  const int16_t* grp_link;   // [Sg] that link, or -1 (spheres on several links)
   const int32_t* blk_pidx;   // [nblk][16] pair index of (4gi+a, 4gj+b) or -1
   // sphere adjacency of the masked pairs, by partner group of 4: per sphere
   // (each pair listed at both spheres), entries group | mask << 8 with
