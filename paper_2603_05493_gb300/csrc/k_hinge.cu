@@ -8,7 +8,9 @@
 //
 // One warp per configuration (persistent grid): the warp stages the
 // configuration's link poses into shared memory, places its spheres
-// (Sec. 6.1.1) and bounds every group of 4 with a sphere (C_g, R_g), then each
+// (Sec. 6.1.1) and bounds every group of 4 with a sphere (C_g, R_g) (for a
+// group on one link, the host-made sphere in its link frame moved with the
+// link), then each
 // lane walks the partner groups of its spheres (s = lane, lane + 32, ...;
 // groups ascending).  A partner group whose bound is farther than eta,
 // |c_s - C_g| - r_s - R_g >= eta (every partner in it then has d >= eta),
@@ -61,6 +63,19 @@ __global__ void __launch_bounds__(256) hinge_kernel(DevRobot r, HingeArgs A) {
     }
     __syncwarp();
     for (int g = lane; g < Sg; g += 32) {  // group bounding spheres
+      const int gl = __ldg(r.grp_link + g);
+      if (gl >= 0) {  // one link: its host-made bound, moved with the link
+        const float4 L = __ldg(r.grp_loc + g);
+        const float* T = P + 12 * gl;
+        const float cl[3] = {L.x, L.y, L.z};
+        float c[3];
+        rot(T, cl, c);
+        const float scale = fabsf(T[9]) + fabsf(T[10]) + fabsf(T[11]) + fabsf(L.x) +
+                            fabsf(L.y) + fabsf(L.z);
+        gb[g] = make_float4(c[0] + T[9], c[1] + T[10], c[2] + T[11],
+                            fmaf(scale, 1e-6f, fmaf(L.w, 1e-6f, L.w)) + 1e-6f);
+        continue;
+      }
       const int s1 = min(S, 4 * g + 4);
       float cx = 0.0f, cy = 0.0f, cz = 0.0f;
       for (int s = 4 * g; s < s1; ++s) {
