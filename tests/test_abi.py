@@ -125,3 +125,27 @@ def test_load_on_missing_device_reports_edevice(lib):
                          C.byref(h))
     assert rc == lib.WB_EDEVICE
     assert b"device" in L.wb_last_error()
+
+
+def test_size_limits(lib):
+    """The largest robot the library takes plans on the host (255 links,
+    1020 spheres, 32 levels); one link or one sphere more is WB_ETOOBIG."""
+    from dataclasses import replace
+    big = R.max_size()
+    info, _ = _plan(big)
+    assert (info["n_links"], info["n_spheres"], info["n_levels"]) == (255, 1020, 32)
+    assert info["n_pairs"] == 330624 and info["n_pair_blocks"] <= 65535
+    more_sph = replace(big, sph_link=np.append(big.sph_link, 1),
+                       sph_c=np.vstack([big.sph_c, [[0, 0, 0]]]), sph_r=np.append(big.sph_r, 0.01))
+    assert _code(more_sph) == lib.WB_ETOOBIG
+    more_links = replace(big, parent=np.append(big.parent, 0), jtype=np.append(big.jtype, 1),
+                         axis=np.vstack([big.axis, [[0, 0, 1]]]),
+                         T_fixed=np.vstack([big.T_fixed, big.T_fixed[1:2]]),
+                         jidx=np.append(big.jidx, big.dof), mimic_mult=np.append(big.mimic_mult, 1),
+                         mimic_off=np.append(big.mimic_off, 0), mass=np.append(big.mass, 1),
+                         com=np.vstack([big.com, [[0, 0, 0]]]),
+                         Icom=np.vstack([big.Icom, big.Icom[1:2]]))
+    assert _code(more_links) == lib.WB_ETOOBIG
+    deep = R.deep_chain(33)  # plans; only the sweep kernels refuse it
+    info, _ = _plan(deep)
+    assert info["n_levels"] == 33
