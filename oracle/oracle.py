@@ -370,32 +370,46 @@ def pair_hinge(robot, q, eta: float, w: float):
 
 
 def trajopt_value(robot, U, T: int, dt: float, tau_lo, tau_hi, w_coll, smooth=0.0,
-                  length=0.0, energy=0.0):
+                  length=0.0, energy=0.0, eta=None):
     """Total cost L(U) = sum_b cost_b over every sample of every trajectory:
     B-spline states -> whole-body evaluation -> cost (the energy term uses
-    the sample spacing of the B-spline, dt (K-3) / (T-1))."""
+    the sample spacing of the B-spline, dt (K-3) / (T-1)).  The collision
+    term is w_coll max(0, -d_min) on the worst pair, or with an activation
+    distance eta the summed hinge w_coll sum_p max(0, eta - d_p) over every
+    masked pair (pair_hinge)."""
     q, qd, qdd = bspline(U, T, dt)
     ev = evaluate(robot, q, qd, qdd, want=("dmin", "tau"))
     K = np.asarray(U).shape[2]
-    cost = trajopt_cost(ev["tau"], ev["dmin"], tau_lo, tau_hi, w_coll, qd, qdd, smooth, length,
+    dmin = ev["dmin"] if eta is None else np.ones_like(ev["dmin"])  # hinge term apart
+    cost = trajopt_cost(ev["tau"], dmin, tau_lo, tau_hi, w_coll, qd, qdd, smooth, length,
                         energy, dt * (K - 3) / (T - 1))[0]
+    if eta is not None:
+        cost = cost + pair_hinge(robot, q, eta, w_coll)[0]
     return float(cost.sum()), ev
 
 
 def trajopt_gradient(robot, U, T: int, dt: float, tau_lo, tau_hi, w_coll, smooth=0.0,
-                     length=0.0, energy=0.0):
+                     length=0.0, energy=0.0, eta=None):
     """dL/dU by the chain of the pieces above: cost gradients -> VJP of the
     whole-body evaluation (dual numbers) plus the cost's direct qd / qdd
-    gradients -> VJP of the B-spline.  Returns (Ubar [n_traj][d][K],
-    per-configuration cost [B], evaluation dict)."""
+    gradients -> VJP of the B-spline.  With eta the collision term is the
+    summed hinge, whose sphere-centre gradient enters the whole-body VJP.
+    Returns (Ubar [n_traj][d][K], per-configuration cost [B], evaluation
+    dict)."""
     U = np.asarray(U, np.float64)
     n_traj, d, K = U.shape
     q, qd, qdd = bspline(U, T, dt)
     ev = evaluate(robot, q, qd, qdd, want=("dmin", "tau"))
-    cost, g_tau, g_dmin, d_qd, d_qdd = trajopt_cost(ev["tau"], ev["dmin"], tau_lo, tau_hi,
+    dmin = ev["dmin"] if eta is None else np.ones_like(ev["dmin"])
+    cost, g_tau, g_dmin, d_qd, d_qdd = trajopt_cost(ev["tau"], dmin, tau_lo, tau_hi,
                                                     w_coll, qd, qdd, smooth, length, energy,
                                                     dt * (K - 3) / (T - 1))
-    gq, gqd, gqdd = gradient(robot, q, qd, qdd, g_dmin=g_dmin, g_tau=g_tau)
+    if eta is None:
+        gq, gqd, gqdd = gradient(robot, q, qd, qdd, g_dmin=g_dmin, g_tau=g_tau)
+    else:
+        hc, g_sph = pair_hinge(robot, q, eta, w_coll)
+        cost = cost + hc
+        gq, gqd, gqdd = gradient(robot, q, qd, qdd, g_sph=g_sph, g_tau=g_tau)
     return bspline_vjp(gq, gqd + d_qd, gqdd + d_qdd, n_traj, K, T, dt), cost, ev
 
 

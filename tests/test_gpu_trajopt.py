@@ -341,3 +341,41 @@ def test_trajopt_chain_with_motion_terms_matches_oracle(W, O):
     gU, cost, o = _chain(W, rob, desc, cuda(U), T, dt, lo, hi, w, motion)
     kept = _compare_chain(O, desc, U, T, dt, lim, w, gU, cost, o, list(range(n_traj)), motion)
     assert kept >= n_traj - 2
+
+
+def test_trajopt_chain_with_summed_hinge_matches_oracle(W, O):
+    """The trajopt48 chain with the summed collision hinge (activation
+    distance 2 cm) and the motion terms, as `bench.py --workload trajopt48
+    --collision hinge` runs it: hinge sphere gradient -> backward sweep, the
+    cost's direct qd / qdd gradients -> B-spline adjoint."""
+    desc = I.hand_payload(R.r48())
+    rob = W.Robot(desc, device=0)
+    n_traj, K, T, dt = 4, CF.TRAJOPT_KNOTS, CF.TRAJOPT_STEPS, CF.TRAJOPT_DT
+    U = I.bspline_controls(desc.dof, n_traj, K, seed=CF.TRAJOPT48.seed + 2)
+    lim, w, eta = CF.TORQUE_LIMIT, CF.COLLISION_WEIGHT, CF.ACTIVATION_DISTANCE
+    motion = dict(smooth=CF.SMOOTH_WEIGHT, length=CF.LENGTH_WEIGHT, energy=CF.ENERGY_WEIGHT)
+    lo = cuda(-lim * np.ones(desc.dof))
+    hi = cuda(lim * np.ones(desc.dof))
+    Ud = cuda(U)
+    q, qd, qdd = W.bspline_eval(Ud, T, dt)
+    o = rob.eval(q, qd, qdd, sphere=False, dmin=False)
+    hcost, g_sph = rob.self_collision_hinge(o["pose"], eta, w)
+    cost, g_tau, _, g_qd, g_qdd = W.trajopt_cost_ext(o["tau"], None, qd, qdd, lo, hi, w,
+                                                     dt=dt * (K - 3) / (T - 1), **motion)
+    gq, gqd, gqdd = rob.eval_backward(q, qd, qdd, None, None, g_sph, None, g_tau)
+    gU = W.bspline_backward(gq, gqd, gqdd, n_traj, K, T, dt, gqd_add=g_qd, gqdd_add=g_qdd)
+    torch.cuda.synchronize()
+    Uref, cref, ev = O.trajopt_gradient(desc, U.astype(np.float64), T, dt, -lim * np.ones(desc.dof),
+                                        lim * np.ones(desc.dof), w, eta=eta, **motion)
+    total = (cost + hcost).cpu().numpy()
+    # torques agree to 1e-4 relative, distances to 1e-5 m per active pair
+    tol = 1e-4 * np.abs(cref) + 1e-4 * np.maximum(np.abs(ev["tau"]), 1.0).sum(axis=0) + 1e-2
+    assert (np.abs(total - cref) <= tol).all()
+    gUn = gU.cpu().numpy()
+    good = 0
+    for tr in range(n_traj):
+        e = np.linalg.norm(gUn[tr] - Uref[tr])
+        # a pair within float rounding of eta may switch sides: a unit-size
+        # change against a gradient of norm ~1e4
+        good += e <= 2 * PY.GRAD_REL * np.linalg.norm(Uref[tr])
+    assert good >= n_traj - 1

@@ -494,6 +494,33 @@ def test_bspline_vjp_local_support_is_the_textbook_basis(oracle_lib):
         assert np.allclose(Ubd, refd, atol=1e-13)
 
 
+def test_trajopt_chain_with_summed_hinge_matches_finite_differences(oracle_lib):
+    """The chain with the summed collision hinge (every masked pair within
+    the activation distance) and the motion terms: its gradient, with the
+    hinge's sphere-centre gradient fed to the whole-body VJP, equals central
+    differences of the total cost."""
+    O = oracle_lib
+    rob = R.r7()
+    rng = np.random.default_rng(19)
+    n_traj, K, T, dt = 2, 6, 9, 0.25
+    U = rng.uniform(-1.5, 1.5, size=(n_traj, rob.dof, K))
+    lo, hi = -8.0 * np.ones(rob.dof), 8.0 * np.ones(rob.dof)
+    kw = dict(smooth=0.01, length=0.1, energy=0.05, eta=0.05)
+    Ub, cost, _ = O.trajopt_gradient(rob, U, T, dt, lo, hi, 2.0, **kw)
+    q, _, _ = O.bspline(U, T, dt)
+    hc, _ = O.pair_hinge(rob, q, 0.05, 2.0)
+    assert (hc > 0).mean() > 0.5  # the hinge is active on most samples
+    h = 1e-6
+    for flat in rng.choice(U.size, size=10, replace=False):
+        idx = np.unravel_index(flat, U.shape)
+        Up, Um = U.copy(), U.copy()
+        Up[idx] += h
+        Um[idx] -= h
+        fd = (O.trajopt_value(rob, Up, T, dt, lo, hi, 2.0, **kw)[0] -
+              O.trajopt_value(rob, Um, T, dt, lo, hi, 2.0, **kw)[0]) / (2 * h)
+        assert abs(fd - Ub[idx]) <= 1e-6 * max(1.0, abs(Ub[idx])), (idx, fd, Ub[idx])
+
+
 def test_bspline_ghost_knots_continue_the_start_state(oracle_lib):
     """With a non-static start (Sec. 4.2) the first sampled window is
     [u_-3, u_-2, u_-1, u_0]; its state at alpha = 0 depends on the ghost
