@@ -494,13 +494,12 @@ def trajopt_work(desc, K, T):
         "bspline_fwd": {"flops": 84 * d, "bytes": 4 * 3 * d + 4 * d * K // T},
         "tree_fwd": {"flops": 150 * nm + 330 * n, "bytes": 4 * (3 * d + 12 * n + d)},
         "pair": {"flops": 18 * S + 11 * P, "bytes": 4 * (12 * n + 2)},
-        # hinges and motion terms: tau, qd, qdd, d_min in; cost, g_tau, g_qd,
-        # g_qdd, g_dmin out
-        "cost": {"flops": 22 * d + 3, "bytes": 4 * (6 * d + 3)},
-        "tree_bwd": {"flops": 150 * nm + 330 * n + 660 * n + 60 * n,
-                     "bytes": 4 * (3 * d + 2 + d + 3 * d)},
-        # five upstream gradients (three of the sweep, two direct ones of the cost)
-        "bspline_bwd": {"flops": 26 * d, "bytes": 4 * 5 * d + 4 * d * K // T},
+        # the whole adjoint with the cost in its prologue: q, qd, qdd, tau,
+        # d_min and worst in; gq, gqd, gqdd and the cost out (the hinges and
+        # motion terms add ~22 flops per joint)
+        "tree_bwd": {"flops": 150 * nm + 330 * n + 660 * n + 60 * n + 22 * d + 3,
+                     "bytes": 4 * (3 * d + d + 2 + 3 * d + 1)},
+        "bspline_bwd": {"flops": 24 * d, "bytes": 4 * 3 * d + 4 * d * K // T},
         # summed hinge: every pair screened from both spheres (sqrt-free, 8 flops)
         "hinge": {"flops": 18 * S + 16 * P, "bytes": 4 * (12 * n + 3 * S + 1)},
     }
@@ -511,9 +510,9 @@ def run_trajopt(args, rank=0, world=1, local_rank=0):
     hand payloads: 512 seeds x 16 control points per joint -> 64 B-spline
     samples each (32768 configurations) -> FK + RNEA sweep -> self-collision
     -> torque-limit + collision hinges and the smooth / length / energy
-    terms -> adjoint sweep -> dL/dU (the cost's direct qd / qdd gradients
-    join the sweep's in the B-spline adjoint).  Value = configurations per
-    second."""
+    terms, formed in the prologue of the adjoint sweep (which also adds the
+    cost's direct qd / qdd gradients) -> B-spline adjoint -> dL/dU.  Value =
+    configurations per second."""
     import torch
     from paper_2603_05493_gb300 import build
     build()
@@ -542,17 +541,14 @@ def run_trajopt(args, rank=0, world=1, local_rank=0):
                "tau": out["tau"], "bits": None}
     pair_out = {"sphere": None, "dmin": out["dmin"], "worst": out["worst"], "bits": None}
     cost = torch.empty((B,), device=dev)
-    g_tau = torch.empty((d, B), device=dev)
-    g_dmin = torch.empty((B,), device=dev)
-    g_qd, g_qdd = torch.empty((d, B), device=dev), torch.empty((d, B), device=dev)
     gout = tuple(torch.empty((d, B), device=dev) for _ in range(3))
     # the energy term's dt: the time between consecutive samples
     dt_sample = dt * (K - 3) / (T - 1)
     gU = torch.empty((n_traj, d, K), device=dev)
     stream = torch.cuda.current_stream()
     hinge = args.collision == "hinge"
-    names = ["bspline_fwd", "tree_fwd", "hinge" if hinge else "pair", "cost", "tree_bwd",
-             "bspline_bwd"]
+    # the cost runs in the backward sweep's prologue (wb_eval_backward_cost)
+    names = ["bspline_fwd", "tree_fwd", "hinge" if hinge else "pair", "tree_bwd", "bspline_bwd"]
     hinge_cost = torch.empty((B,), device=dev)
     g_sph = torch.empty((B, desc.S, 3), device=dev) if hinge else None
 
@@ -568,18 +564,14 @@ def run_trajopt(args, rank=0, world=1, local_rank=0):
         else:  # the worst pair
             rob.self_collision(out["pose"], out=pair_out)
         mark(3)
-        wbe.trajopt_cost_ext(out["tau"], None if hinge else out["dmin"], qd, qdd, lo, hi,
-                             CF.COLLISION_WEIGHT, CF.SMOOTH_WEIGHT, CF.LENGTH_WEIGHT,
-                             CF.ENERGY_WEIGHT, dt_sample,
-                             out=(cost, g_tau, None if hinge else g_dmin, g_qd, g_qdd))
+        rob.eval_backward_cost(q, qd, qdd, out["tau"], lo, hi, CF.COLLISION_WEIGHT,
+                               CF.SMOOTH_WEIGHT, CF.LENGTH_WEIGHT, CF.ENERGY_WEIGHT, dt_sample,
+                               d_min=None if hinge else out["dmin"],
+                               worst=None if hinge else out["worst"],
+                               g_sphere=g_sph if hinge else None, cost=cost, tune=btune,
+                               out=gout)
         mark(4)
-        if hinge:
-            rob.eval_backward(q, qd, qdd, None, None, g_sph, None, g_tau, tune=btune, out=gout)
-        else:
-            rob.eval_backward(q, qd, qdd, out["worst"], None, None, g_dmin, g_tau, tune=btune,
-                              out=gout)
-        mark(5)
-        wbe.bspline_backward(*gout, n_traj, K, T, dt, gU, gqd_add=g_qd, gqdd_add=g_qdd)
+        wbe.bspline_backward(*gout, n_traj, K, T, dt, gU)
 
     flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
     for _ in range(max(args.warmup, 3)):
@@ -588,17 +580,19 @@ def run_trajopt(args, rank=0, world=1, local_rank=0):
     barrier(world)
     clocks = ClockSampler(local_rank)
     clocks.start()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    nk = len(names)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(nk + 1)]
+           for _ in range(args.steps)]
     torch.cuda.nvtx.range_push("timed")
     for i in range(args.steps):
         flush.fill_(float(i))
         evs[i][0].record(stream)
         step(evs[i])
-        evs[i][6].record(stream)
+        evs[i][nk].record(stream)
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier(world)
-    step_ms = float(np.mean([e[0].elapsed_time(e[6]) for e in evs]))
+    step_ms = float(np.mean([e[0].elapsed_time(e[nk]) for e in evs]))
     k_ms = {nm: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in evs]))
             for i, nm in enumerate(names)}
     # end to end: control points in from pinned host memory, dL/dU and the
@@ -631,7 +625,6 @@ def run_trajopt(args, rank=0, world=1, local_rank=0):
     kernels = {}
     kn = {"bspline_fwd": "bspline_fwd_kernel", "pair": "pair_kernel", "hinge": "hinge_kernel",
           "tree_fwd": "tree_fwd_seg_kernel" if seg(ft) > 1 else "tree_fwd_kernel",
-          "cost": "trajopt_cost_kernel",
           "tree_bwd": "tree_bwd_seg_kernel" if seg(bt) > 1 else "tree_bwd_kernel",
           "bspline_bwd": "bspline_bwd_kernel"}
     for nm, ms in k_ms.items():
@@ -672,7 +665,7 @@ def run_trajopt(args, rank=0, world=1, local_rank=0):
         "e2e": {"value": job_value(world, B, e2e_ms), "unit": "evals/s",
                 "h2d_bytes_per_step": world * int(hU.numel() * 4),
                 "d2h_bytes_per_step": world * int(hgU.numel() * 4 + hcost.numel() * 4)},
-        "gpu_launches": 6 * args.steps * world,
+        "gpu_launches": len(names) * args.steps * world,
         "clocks": clocks.summary(),
     }
     print(json.dumps(line), flush=True)

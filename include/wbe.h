@@ -448,6 +448,33 @@ int wb_trajopt_cost_ext(int64_t B, int32_t d, const float* tau, const float* d_m
                         const float* tau_hi, const wb_cost_weights* w, float* cost,
                         float* g_tau, float* g_dmin, float* g_qd, float* g_qdd, void* stream);
 
+/* The trajectory cost folded into the backward sweep (the cost's gradients
+ * formed in the sweep's prologue, without a separate cost pass).  Same
+ * results, up to float summation order, as
+ *   wb_trajopt_cost_ext(B, d, tau, d_min, qd, qdd, tau_lo, tau_hi, w,
+ *                       cost, g_tau, g_dmin, g_qd, g_qdd)
+ *   wb_eval_backward(robot, B, q, qd, qdd, worst_pair, g_pose, g_sphere,
+ *                    g_dmin, g_tau, gq, gqd, gqdd)
+ *   gqd += g_qd; gqdd += g_qdd
+ * i.e. gq, gqd, gqdd [d][B] are the total gradients of
+ *   sum_b cost_b + <g_pose, poses> + <g_sphere, sphere centres>
+ * with respect to q, qd, qdd (feed them to wb_bspline_backward for dL/dU),
+ * and cost [B] (nullable) is the per-configuration cost.  tau [d][B] are the
+ * forward torques at (q, qd, qdd); d_min [B] (nullable: no collision term)
+ * the forward's worst-pair distance with its worst_pair (then required);
+ * g_pose, g_sphere nullable.  Runs in the tree kernels only (tune NULL,
+ * AUTO or TREE with its segment and block choices).  The robot must drive
+ * each joint with one link (no shared mimic joints).
+ * Errors: WB_EINVAL (also a robot with shared mimic joints or another
+ * kernel), WB_EDEVICE, WB_ETOOBIG (tree deeper than the sweep kernels take),
+ * WB_ECUDA. */
+int wb_eval_backward_cost(wb_robot* robot, int64_t B, const float* q, const float* qd,
+                          const float* qdd, const int32_t* worst_pair, const float* g_pose,
+                          const float* g_sphere, const float* tau, const float* d_min,
+                          const float* tau_lo, const float* tau_hi, const wb_cost_weights* w,
+                          float* cost, float* gq, float* gqd, float* gqdd, const wb_tune* tune,
+                          void* stream);
+
 /* ---------------------------------------------------------------------------
  * Forward evaluation of an uneven batch without any device allocation.  The
  * paper has no counterpart to this entry point.

@@ -68,8 +68,54 @@ __global__ void __launch_bounds__(256, 2) tree_bwd_seg_kernel(const __grid_const
   for (int s = 0; s < ns; ++s)
     for (int q = 0; q < 3; ++q) sg.part[q * o + (s * G + sg.g) * 32 + sg.lane] = 0.0f;
   const int64_t b = ((int64_t)blockIdx.x * CG + cg) * 32 + sg.lane;
-  if (b < A.B) tree_bwd_seg(r, A, b, sg);
+  if (b < A.B) tree_bwd_seg<false>(r, A, FusedCost{}, b, sg);
   __syncthreads();
+  if (b < A.B) {
+    for (int s = sg.g; s < ns; s += G) {
+      float acc[3] = {0.0f, 0.0f, 0.0f};
+      for (int h = 0; h < G; ++h)
+        for (int q = 0; q < 3; ++q) acc[q] += sg.part[q * o + (s * G + h) * 32 + sg.lane];
+      const int k = __ldg(r.seg_slot_link + t * r.n + s);
+      const int64_t at = (int64_t)__ldg(r.jidx + k) * A.B + b;
+      A.gq[at] = acc[0];
+      A.gqd[at] = acc[1];
+      A.gqdd[at] = acc[2];
+    }
+  }
+}
+
+// The same sweeps with the trajectory cost in their prologue (FusedCost):
+// separate kernels, so that the plain ones keep their register allocation.
+// The segmented one adds each configuration's cost terms over the segments
+// in segment order (deterministic) after the barrier.
+__global__ void __launch_bounds__(256, 2) tree_bwd_cost_kernel(DevRobot r, BwdArgs A,
+                                                               FusedCost fc) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b < A.B) tree_bwd_cost_one(r, A, fc, b);
+}
+
+__global__ void __launch_bounds__(256, 2) tree_bwd_cost_seg_kernel(
+    const __grid_constant__ DevRobot r, BwdArgs A, FusedCost fc, int t) {
+  extern __shared__ float part[];
+  const int G = 2 << t;
+  const int CG = blockDim.x / (32 * G);
+  const int cg = (threadIdx.x >> 5) / G;
+  const int ns = r.seg_ns[t];
+  const size_t o = (size_t)ns * G * 32;  // one output's partials
+  Seg sg = seg_of(r, t, part + (size_t)cg * (3 * o + G * 32));
+  float* cpart = sg.part + 3 * o;  // [G][32] the segments' cost terms
+  for (int s = 0; s < ns; ++s)
+    for (int q = 0; q < 3; ++q) sg.part[q * o + (s * G + sg.g) * 32 + sg.lane] = 0.0f;
+  const int64_t b = ((int64_t)blockIdx.x * CG + cg) * 32 + sg.lane;
+  float c = 0.0f;
+  if (b < A.B) c = tree_bwd_seg<true>(r, A, fc, b, sg);
+  cpart[sg.g * 32 + sg.lane] = c;
+  __syncthreads();
+  if (b < A.B && sg.g == 0 && fc.cost) {
+    float acc = 0.0f;
+    for (int h = 0; h < G; ++h) acc += cpart[h * 32 + sg.lane];
+    fc.cost[b] = fc.d_min ? fmaf(fc.w, fmaxf(0.0f, -__ldg(fc.d_min + b)), acc) : acc;
+  }
   if (b < A.B) {
     for (int s = sg.g; s < ns; s += G) {
       float acc[3] = {0.0f, 0.0f, 0.0f};
@@ -91,6 +137,7 @@ static void prefer_l1() {
   if (!done) {
     cudaFuncSetAttribute(tree_fwd_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
     cudaFuncSetAttribute(tree_bwd_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    cudaFuncSetAttribute(tree_bwd_cost_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
     done = true;
   }
 }
@@ -98,10 +145,14 @@ static void prefer_l1() {
 static int seg_plan(int segments) { return segments == 2 ? 0 : segments == 4 ? 1 : 2; }
 static int seg_groups(int segments, int threads) { return std::max(1, threads / (32 * segments)); }
 
-size_t tree_seg_smem(const DevRobot& r, int segments, int threads, bool fwd) {
+// per group of G warps: the shared-slot partials of each output (tau in the
+// forward; gq, gqd, gqdd in the backward), plus, for the cost variant, one
+// cost term per segment
+size_t tree_seg_smem(const DevRobot& r, int segments, int threads, bool fwd, bool cost) {
   const int t = seg_plan(segments);
-  return (size_t)seg_groups(segments, threads) * (fwd ? 1 : 3) * r.seg_ns[t] * segments * 32 *
-         sizeof(float);
+  const size_t per =
+      (size_t)(fwd ? 1 : 3) * r.seg_ns[t] * segments * 32 + (cost ? segments * 32 : 0);
+  return (size_t)seg_groups(segments, threads) * per * sizeof(float);
 }
 
 template <class Args>
@@ -109,13 +160,27 @@ static cudaError_t launch_seg(void (*kern)(DevRobot, Args, int), const DevRobot&
                               int threads, int segments, bool fwd, cudaStream_t s) {
   const int t = seg_plan(segments);
   const int CG = seg_groups(segments, threads);
-  const size_t smem = tree_seg_smem(r, segments, threads, fwd);
+  const size_t smem = tree_seg_smem(r, segments, threads, fwd, false);
   cudaError_t e =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t groups = (a.B + 31) / 32;
   const int64_t grid = (groups + CG - 1) / CG;
   kern<<<(unsigned)grid, 32 * segments * CG, smem, s>>>(r, a, t);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_cost_seg(const DevRobot& r, const BwdArgs& a, const FusedCost& fc,
+                                   int threads, int segments, cudaStream_t s) {
+  const int t = seg_plan(segments);
+  const int CG = seg_groups(segments, threads);
+  const size_t smem = tree_seg_smem(r, segments, threads, false, true);
+  cudaError_t e = cudaFuncSetAttribute(tree_bwd_cost_seg_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t groups = (a.B + 31) / 32;
+  const int64_t grid = (groups + CG - 1) / CG;
+  tree_bwd_cost_seg_kernel<<<(unsigned)grid, 32 * segments * CG, smem, s>>>(r, a, fc, t);
   return cudaGetLastError();
 }
 
@@ -130,12 +195,17 @@ cudaError_t launch_tree_fwd(const DevRobot& r, const FwdArgs& a, int threads, in
 }
 
 cudaError_t launch_tree_bwd(const DevRobot& r, const BwdArgs& a, int threads, int segments,
-                            cudaStream_t s) {
+                            cudaStream_t s, const FusedCost* fc) {
   if (threads <= 0) threads = 128;
-  if (segments > 1) return launch_seg(tree_bwd_seg_kernel, r, a, threads, segments, false, s);
+  if (segments > 1)
+    return fc ? launch_cost_seg(r, a, *fc, threads, segments, s)
+              : launch_seg(tree_bwd_seg_kernel, r, a, threads, segments, false, s);
   prefer_l1();
   const int64_t grid = (a.B + threads - 1) / threads;
-  tree_bwd_kernel<<<(unsigned)grid, threads, 0, s>>>(r, a);
+  if (fc)
+    tree_bwd_cost_kernel<<<(unsigned)grid, threads, 0, s>>>(r, a, *fc);
+  else
+    tree_bwd_kernel<<<(unsigned)grid, threads, 0, s>>>(r, a);
   return cudaGetLastError();
 }
 

@@ -370,9 +370,19 @@ __device__ __forceinline__ void point_wrench(const float* R, float4 sp, const fl
   w[5] += f[2];
 }
 
-__device__ __forceinline__ void tree_bwd_seg(const DevRobot& r, const BwdArgs& A, int64_t b,
-                                             const Seg& sg) {
+// With a fused cost (FC, fc) the sweep computes g_tau = [tau > hi] -
+// [tau < lo] + 2 e qd^2 tau and g_dmin = -w [d_min < 0] itself, adds the
+// cost's direct qd / qdd gradients (2 length qd + 2 e qd tau^2, 2 smooth qdd)
+// to the outputs of the joint's link, and returns the cost terms of the joints
+// of the links it owns (the caller adds the collision term and the segments'
+// shares).  Needs one link per joint (no shared mimic joints).
+// FC: compiled with the fused cost (a separate instantiation, so that the
+// plain sweep keeps its register allocation).
+template <bool FC>
+__device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& A,
+                                              const FusedCost& fc, int64_t b, const Seg& sg) {
   const int64_t B = A.B;
+  float cost_part = 0.0f;
   const int n = r.n;
   BEnt stk[TMAXD];
   if (r.mimic_shared)
@@ -390,9 +400,9 @@ __device__ __forceinline__ void tree_bwd_seg(const DevRobot& r, const BwdArgs& A
   };
   int pl1 = -1, pl2 = -1, ps1 = 0, ps2 = 0;
   float u[3] = {0.0f, 0.0f, 0.0f};
-  if (A.g_dmin) {
+  if (A.g_dmin || (FC && fc.d_min)) {
     const int wp = A.worst[b];
-    const float gd = A.g_dmin[b];
+    const float gd = FC ? (__ldg(fc.d_min + b) < 0.0f ? -fc.w : 0.0f) : A.g_dmin[b];
     if (wp >= 0 && wp < r.P && gd != 0.0f) {
       const int2 ij = __ldg(r.pairs + wp);
       const int l1 = __ldg(r.sph_link + ij.x), l2 = __ldg(r.sph_link + ij.y);
@@ -553,7 +563,26 @@ __device__ __forceinline__ void tree_bwd_seg(const DevRobot& r, const BwdArgs& A
     crm(S, Xv, c6);
     gq -= dot6t(vb, c6);
     gq += dot6t(S, Wr);
-    if (j >= 0) {
+    if (FC && j >= 0) {
+      float dqd = 0.0f, dqdd = 0.0f;  // the cost's direct gradients, once per joint
+      if (!((replayed >> e) & 1u)) {
+        const int64_t at = (int64_t)j * B + b;
+        const float tj = __ldg(fc.tau + at), vj = __ldg(A.qd + at), aj = __ldg(A.qdd + at);
+        dqd = 2.0f * (fc.length * vj + fc.e * (vj * tj) * tj);
+        dqdd = 2.0f * fc.smooth * aj;
+      }
+      float* p0 = seg_part(sg, k, 0);
+      if (p0) {
+        const size_t o = (size_t)sg.ns * sg.G * 32;
+        p0[0] = mm * gq;
+        p0[o] = mm * gqd + dqd;
+        p0[2 * o] = mm * gqdd + dqdd;
+      } else {
+        A.gq[(int64_t)j * B + b] = mm * gq;
+        A.gqd[(int64_t)j * B + b] = mm * gqd + dqd;
+        A.gqdd[(int64_t)j * B + b] = mm * gqdd + dqdd;
+      }
+    } else if (j >= 0) {
       float* p0 = seg_part(sg, k, 0);
       if (p0) {
         const size_t o = (size_t)sg.ns * sg.G * 32;
@@ -668,7 +697,25 @@ __device__ __forceinline__ void tree_bwd_seg(const DevRobot& r, const BwdArgs& A
     // adjoint of the force sweep: Fbar_k = S m taubar + X Fbar_pa
     float S[6];
     motion_S6t(jt, ax, S);
-    const float tb = (j >= 0 && A.g_tau) ? mm * __ldg(A.g_tau + (int64_t)j * B + b) : 0.0f;
+    float tb = 0.0f;
+    if (FC && j >= 0) {  // the cost's torque gradient, as the cost kernel forms it
+      const float t = __ldg(fc.tau + (int64_t)j * B + b), l = __ldg(fc.lo + j),
+                  h = __ldg(fc.hi + j);
+      const float v = __ldg(A.qd + (int64_t)j * B + b), a = __ldg(A.qdd + (int64_t)j * B + b);
+      const float vt = v * t;
+      float gt = 2.0f * fc.e * v * vt;
+      gt += (t > h ? 1.0f : 0.0f) - (t < l ? 1.0f : 0.0f);
+      tb = mm * gt;
+      if (own) {
+        float c = fmaf(fc.smooth * a, a, 0.0f);
+        c = fmaf(fc.length * v, v, c);
+        c = fmaf(fc.e * vt, vt, c);
+        c += fmaxf(0.0f, t - h) + fmaxf(0.0f, l - t);
+        cost_part += c;
+      }
+    } else if (!FC && j >= 0 && A.g_tau) {
+      tb = mm * __ldg(A.g_tau + (int64_t)j * B + b);
+    }
     float XF[6];
     xf_motion(L, L + 9, Fbp, XF);
 #pragma unroll
@@ -748,6 +795,7 @@ __device__ __forceinline__ void tree_bwd_seg(const DevRobot& r, const BwdArgs& A
         pf(A.qd + (int64_t)jn * B + b);
         pf(A.qdd + (int64_t)jn * B + b);
         if (A.g_tau) pf(A.g_tau + (int64_t)jn * B + b);
+        if (FC) pf(fc.tau + (int64_t)jn * B + b);
       }
       if (A.g_pose) {
         const float* gpn = A.g_pose + (b * n + kn) * 12;
@@ -769,10 +817,19 @@ __device__ __forceinline__ void tree_bwd_seg(const DevRobot& r, const BwdArgs& A
   }
   while (sp > 0) close(--sp);
   flush();
+  return cost_part;
 }
 
+// the whole sweep of one configuration; with a fused cost it also writes the
+// configuration's cost (joint terms, then the collision term)
 __device__ __forceinline__ void tree_bwd_one(const DevRobot& r, const BwdArgs& A, int64_t b) {
-  tree_bwd_seg(r, A, b, whole_sweep(r));
+  tree_bwd_seg<false>(r, A, FusedCost{}, b, whole_sweep(r));
+}
+
+__device__ __forceinline__ void tree_bwd_cost_one(const DevRobot& r, const BwdArgs& A,
+                                                  const FusedCost& fc, int64_t b) {
+  const float c = tree_bwd_seg<true>(r, A, fc, b, whole_sweep(r));
+  if (fc.cost) fc.cost[b] = fc.d_min ? fmaf(fc.w, fmaxf(0.0f, -__ldg(fc.d_min + b)), c) : c;
 }
 
 }  // namespace wbe

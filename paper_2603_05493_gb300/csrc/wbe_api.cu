@@ -949,7 +949,7 @@ static int tree_segments(const wb_robot* R, const wb_tune* tune, int64_t B, int 
     for (int t = 0; t < 3 && warps * G < target; ++t)
       if (ok >> t & 1) G = 2 << t;
   }
-  if (G > 1 && tree_seg_smem(R->dev, G, threads, fwd) > 227 * 1024)
+  if (G > 1 && tree_seg_smem(R->dev, G, threads, fwd, !fwd) > 227 * 1024)
     return fail(WB_ETOOBIG, "segmented sweep needs too much shared memory");
   *out = G;
   return WB_OK;
@@ -1220,6 +1220,69 @@ int wb_eval_backward_ext(wb_robot* robot, int64_t B, const float* q, const float
     return fail(WB_EINVAL, "unknown kernel %d", kernel);
   }
   if (e != cudaSuccess) return cuda_fail(e, "wb_eval_backward launch");
+  return WB_OK;
+}
+
+int wb_eval_backward_cost(wb_robot* robot, int64_t B, const float* q, const float* qd,
+                          const float* qdd, const int32_t* worst_pair, const float* g_pose,
+                          const float* g_sphere, const float* tau, const float* d_min,
+                          const float* tau_lo, const float* tau_hi, const wb_cost_weights* w,
+                          float* cost, float* gq, float* gqd, float* gqdd, const wb_tune* tune,
+                          void* stream) {
+  g_err.clear();
+  if (!robot) return fail(WB_EINVAL, "robot is NULL");
+  if (!w) return fail(WB_EINVAL, "weights are NULL");
+  const wb_cost_weights W = *w;
+  if (!std::isfinite(W.collision) || !std::isfinite(W.smooth) || !std::isfinite(W.length) ||
+      !std::isfinite(W.energy) || !std::isfinite(W.dt) || !(W.dt > 0.0f) ||
+      !std::isfinite(W.energy * W.dt * W.dt))
+    return fail(WB_EINVAL, "weights must be finite and dt > 0");
+  if (B < 0) return fail(WB_EINVAL, "B < 0");
+  if (B == 0) return WB_OK;
+  if (B > (int64_t)1 << 40) return fail(WB_EINVAL, "B too large");
+  if (robot->dev.mimic_shared)
+    return fail(WB_EINVAL, "the fused cost needs one link per joint (no shared mimic joints)");
+  int rc;
+  if ((rc = check_ptr(robot, q, "q", true))) return rc;
+  if ((rc = check_ptr(robot, qd, "qd", true))) return rc;
+  if ((rc = check_ptr(robot, qdd, "qdd", true))) return rc;
+  if ((rc = check_ptr(robot, tau, "tau", true))) return rc;
+  if ((rc = check_ptr(robot, tau_lo, "tau_lo", true))) return rc;
+  if ((rc = check_ptr(robot, tau_hi, "tau_hi", true))) return rc;
+  if ((rc = check_ptr(robot, d_min, "d_min", false))) return rc;
+  if ((rc = check_ptr(robot, worst_pair, "worst_pair", d_min != nullptr))) return rc;
+  if ((rc = check_ptr(robot, g_pose, "g_pose", false))) return rc;
+  if ((rc = check_ptr(robot, g_sphere, "g_sphere", false))) return rc;
+  if ((rc = check_ptr(robot, cost, "cost", false))) return rc;
+  if ((rc = check_ptr(robot, gq, "gq", true))) return rc;
+  if ((rc = check_ptr(robot, gqd, "gqd", true))) return rc;
+  if ((rc = check_ptr(robot, gqdd, "gqdd", true))) return rc;
+  int kernel = tune ? tune->kernel : WB_KERNEL_AUTO;
+  if (kernel == WB_KERNEL_TREE_NOCULL) kernel = WB_KERNEL_TREE;
+  if (kernel != WB_KERNEL_AUTO && kernel != WB_KERNEL_TREE)
+    return fail(WB_EINVAL, "the fused cost runs in the tree kernels (kernel AUTO or TREE)");
+  if (robot->dev.maxdepth > tree_max_depth())
+    return fail(WB_ETOOBIG, "tree deeper than %d levels", tree_max_depth());
+  DeviceGuard guard(robot->device);
+  BwdArgs a{B, q, qd, qdd, worst_pair, g_pose, g_sphere, nullptr, nullptr, gq, gqd, gqdd};
+  FusedCost fc;
+  fc.tau = tau;
+  fc.d_min = d_min;
+  fc.lo = tau_lo;
+  fc.hi = tau_hi;
+  fc.w = W.collision;
+  fc.smooth = W.smooth;
+  fc.length = W.length;
+  fc.e = W.energy * W.dt * W.dt;
+  fc.cost = cost;
+  const int tpb = (tune && tune->configs_per_block) ? tune->configs_per_block : 128;
+  if (tpb < 32 || tpb > 256 || tpb % 32)
+    return fail(WB_EINVAL, "tree threads per block must be a multiple of 32 in [32, 256]");
+  int G = 1;
+  if ((rc = tree_segments(robot, tune, B, tpb, false, &G))) return rc;
+  const cudaError_t e =
+      launch_tree_bwd(robot->dev, a, tpb, G, static_cast<cudaStream_t>(stream), &fc);
+  if (e != cudaSuccess) return cuda_fail(e, "wb_eval_backward_cost launch");
   return WB_OK;
 }
 

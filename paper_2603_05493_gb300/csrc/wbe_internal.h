@@ -116,6 +116,19 @@ struct FwdArgs {
   const float* fext = nullptr;  // [B][n][6] external link wrenches, link coordinates
 };
 
+// The trajectory cost folded into the backward sweep (a separate kernel
+// argument of the cost variants of the sweep kernels): the sweep computes
+// g_tau, g_dmin and the cost's direct qd / qdd gradients itself, adds the
+// latter to its gqd / gqdd outputs and writes the cost.
+struct FusedCost {
+  const float* tau = nullptr;    // [d][B] forward torques
+  const float* d_min = nullptr;  // [B] worst-pair distance, or nullptr (no collision term)
+  const float* lo = nullptr;     // [d] torque limits
+  const float* hi = nullptr;
+  float w = 0.0f, smooth = 0.0f, length = 0.0f, e = 0.0f;  // e = energy dt^2
+  float* cost = nullptr;         // [B] out, or nullptr
+};
+
 struct BwdArgs {
   int64_t B;
   const float* q;
@@ -251,8 +264,8 @@ cudaError_t launch_trajopt_cost(int64_t B, int d, const float* tau, const float*
 cudaError_t launch_tree_fwd(const DevRobot& r, const FwdArgs& a, int threads, int segments,
                             cudaStream_t s);
 cudaError_t launch_tree_bwd(const DevRobot& r, const BwdArgs& a, int threads, int segments,
-                            cudaStream_t s);
-size_t tree_seg_smem(const DevRobot& r, int segments, int threads, bool fwd);
+                            cudaStream_t s, const FusedCost* fc = nullptr);
+size_t tree_seg_smem(const DevRobot& r, int segments, int threads, bool fwd, bool cost = false);
 int tree_max_depth();
 size_t pair_smem(const DevRobot& r, int warps, bool bits);
 size_t pair_block_smem(const DevRobot& r, int warps, bool bits);  // the same, out of line

@@ -266,6 +266,35 @@ class Robot:
                 "wb_eval_backward")
         return gq, gqd, gqdd
 
+    def eval_backward_cost(self, q, qd, qdd, tau, tau_lo, tau_hi, w_coll: float,
+                           smooth: float = 0.0, length: float = 0.0, energy: float = 0.0,
+                           dt: float = 1.0, *, d_min=None, worst=None, g_pose=None,
+                           g_sphere=None, cost=None, want_cost: bool = True,
+                           tune: Tune | None = None, out=None, stream=None):
+        """The trajectory cost folded into the backward sweep
+        (wb_eval_backward_cost): total gradients (gq, gqd, gqdd) of the
+        per-configuration cost (torque hinges, worst-pair hinge when d_min
+        is given, smooth / length / energy terms) plus <g_pose, poses> +
+        <g_sphere, centres>, and the cost [B].  Returns (gq, gqd, gqdd,
+        cost)."""
+        B = q.shape[1]
+        if out is None:
+            out = tuple(torch.empty((self.dof, B), device=self.device, dtype=torch.float32)
+                        for _ in range(3))
+        gq, gqd, gqdd = out
+        if cost is None and want_cost:
+            cost = torch.empty((B,), device=self.device, dtype=torch.float32)
+        w = L.wb_cost_weights(float(w_coll), float(smooth), float(length), float(energy),
+                              float(dt))
+        t = (tune or Tune()).c()
+        L.check(self.lib.wb_eval_backward_cost(self.handle, B, _ptr(q), _ptr(qd), _ptr(qdd),
+                                               _ptr(worst), _ptr(g_pose), _ptr(g_sphere),
+                                               _ptr(tau), _ptr(d_min), _ptr(tau_lo),
+                                               _ptr(tau_hi), C.byref(w), _ptr(cost), _ptr(gq),
+                                               _ptr(gqd), _ptr(gqdd), C.byref(t),
+                                               _stream(stream)), "wb_eval_backward_cost")
+        return gq, gqd, gqdd, cost
+
 
 class Batch:
     """An uneven batch: problems (robot index, horizon) over several loaded

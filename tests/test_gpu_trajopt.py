@@ -379,3 +379,78 @@ def test_trajopt_chain_with_summed_hinge_matches_oracle(W, O):
         # change against a gradient of norm ~1e4
         good += e <= 2 * PY.GRAD_REL * np.linalg.norm(Uref[tr])
     assert good >= n_traj - 1
+
+
+@pytest.mark.parametrize("G", [1, 2, 4])
+@pytest.mark.parametrize("collision,kin", [(True, False), (False, True)])
+def test_fused_cost_matches_separate_calls(W, G, collision, kin):
+    """wb_eval_backward_cost against wb_trajopt_cost_ext + wb_eval_backward +
+    adding the direct q-dot / q-ddot gradients, for every sweep segment
+    count, with the worst-pair term or with pose / sphere gradients."""
+    desc = I.hand_payload(R.r48())
+    rob = W.Robot(desc, device=0)
+    B = 301
+    q, qd, qdd = (cuda(x) for x in I.uniform_states(desc.dof, B, seed=PY.stable_seed("fc", G)))
+    gp, gs, _, _ = I.upstream_grads(desc, B, seed=12)
+    gp, gs = (cuda(gp), cuda(gs)) if kin else (None, None)
+    lim = CF.TORQUE_LIMIT
+    lo, hi = cuda(-lim * np.ones(desc.dof)), cuda(lim * np.ones(desc.dof))
+    wts = dict(smooth=CF.SMOOTH_WEIGHT, length=CF.LENGTH_WEIGHT, energy=CF.ENERGY_WEIGHT,
+               dt=0.05)
+    tune = W.Tune(kernel=3, lanes_per_config=G)
+    o = rob.eval(q, qd, qdd, tune=tune)
+    dmin = o["dmin"] if collision else None
+    worst = o["worst"] if collision else None
+    c1, g_tau, g_dmin, g_qd, g_qdd = W.trajopt_cost_ext(o["tau"], dmin, qd, qdd, lo, hi, 1.5,
+                                                        **wts)
+    a = rob.eval_backward(q, qd, qdd, worst, gp, gs, g_dmin, g_tau, tune=tune)
+    ref = (a[0], a[1] + g_qd, a[2] + g_qdd)
+    b = rob.eval_backward_cost(q, qd, qdd, o["tau"], lo, hi, 1.5, d_min=dmin, worst=worst,
+                               g_pose=gp, g_sphere=gs, tune=tune, **wts)
+    torch.cuda.synchronize()
+    for x, y in zip(b[:3], ref):
+        x, y = x.cpu().numpy(), y.cpu().numpy()
+        assert np.abs(x - y).max() <= 1e-5 * max(1.0, np.abs(y).max())
+    assert np.allclose(b[3].cpu().numpy(), c1.cpu().numpy(), rtol=1e-5, atol=1e-4)
+
+
+def test_fused_cost_chain_matches_oracle(W, O):
+    """The trajopt48 chain through the fused cost: U -> B-spline -> forward
+    + worst pair -> backward sweep with the cost in its prologue -> dL/dU."""
+    desc = I.hand_payload(R.r48())
+    rob = W.Robot(desc, device=0)
+    n_traj, K, T, dt = 6, CF.TRAJOPT_KNOTS, CF.TRAJOPT_STEPS, CF.TRAJOPT_DT
+    U = I.bspline_controls(desc.dof, n_traj, K, seed=CF.TRAJOPT48.seed + 3)
+    lim, w = CF.TORQUE_LIMIT, CF.COLLISION_WEIGHT
+    motion = dict(smooth=CF.SMOOTH_WEIGHT, length=CF.LENGTH_WEIGHT, energy=CF.ENERGY_WEIGHT)
+    lo, hi = cuda(-lim * np.ones(desc.dof)), cuda(lim * np.ones(desc.dof))
+    q, qd, qdd = W.bspline_eval(cuda(U), T, dt)
+    o = rob.eval(q, qd, qdd)
+    gq, gqd, gqdd, cost = rob.eval_backward_cost(q, qd, qdd, o["tau"], lo, hi, w, d_min=o["dmin"],
+                                                 worst=o["worst"], dt=dt * (K - 3) / (T - 1),
+                                                 **motion)
+    gU = W.bspline_backward(gq, gqd, gqdd, n_traj, K, T, dt)
+    torch.cuda.synchronize()
+    kept = _compare_chain(O, desc, U, T, dt, lim, w, gU, cost, o, list(range(n_traj)), motion)
+    assert kept >= n_traj - 2
+
+
+def test_fused_cost_refusals(W):
+    from paper_2603_05493_gb300 import _lib as L
+    desc = R.mixed_joint_tree()  # a joint drives two links
+    rob = W.Robot(desc, device=0)
+    x = torch.zeros((desc.dof, 8), device="cuda")
+    lim = torch.ones(desc.dof, device="cuda")
+    with pytest.raises(L.WbError) as e:
+        rob.eval_backward_cost(x, x, x, x, -lim, lim, 1.0)
+    assert e.value.code == L.WB_EINVAL
+    d7 = R.r7()
+    r7 = W.Robot(d7, device=0)
+    x = torch.zeros((d7.dof, 8), device="cuda")
+    lim = torch.ones(d7.dof, device="cuda")
+    with pytest.raises(L.WbError) as e:
+        r7.eval_backward_cost(x, x, x, x, -lim, lim, 1.0, tune=W.PLAIN)
+    assert e.value.code == L.WB_EINVAL
+    with pytest.raises(L.WbError) as e:  # d_min without its worst pair
+        r7.eval_backward_cost(x, x, x, x, -lim, lim, 1.0, d_min=torch.zeros(8, device="cuda"))
+    assert e.value.code == L.WB_EINVAL
