@@ -5,12 +5,13 @@
 // [d_p][H_p] blocks for q, qd, qdd, tau and their gradients (offset jo_p),
 // [H_p][n_p][12] link poses (po_p), [H_p][S_p][3] sphere centres (so_p) and
 // [H_p] d_min / worst pair (co_p).  The host cuts the problems into work
-// items and sorts them by cost, longest first; warps of a persistent grid
-// pull items through an atomic counter (a 4-byte scratch word per pass,
-// cleared on the stream before the launch) until the list is exhausted, and
-// each item runs the single-robot per-configuration code (tree_sweep.cuh,
-// pair_body.cuh) with its own robot's descriptor.  There are no waits on
-// other blocks: a warp that finds the list exhausted returns.
+// items and sorts them by cost, longest first; warps (pairs of warps for the
+// sweeps) of a persistent grid pull items through an atomic counter (a
+// 4-byte scratch word per pass, cleared on the stream before the launch)
+// until the list is exhausted, and each item runs the single-robot
+// per-configuration code (tree_sweep.cuh, pair_body.cuh) with its own
+// robot's descriptor.  There are no waits on other blocks: a warp (pair)
+// that finds the list exhausted returns.
 #include "pair_body.cuh"
 #include "tree_sweep.cuh"
 
@@ -22,14 +23,40 @@ __device__ __forceinline__ int warp_pull(int* counter, int lane) {
   return __shfl_sync(0xffffffffu, it, 0);
 }
 
-// tree items: x = problem, y = first configuration, z = count (<= 32)
+// Tree items (x = problem, y = first configuration, z = count <= 32) are
+// taken by pairs of warps: a block holds two pairs, and the two warps of a
+// pair sweep the two segments of the item's robot's 2-segment plan (the
+// segmented sweeps of tree_sweep.cuh: warp g replays the ancestors of its
+// first link, then sweeps its links).  The outputs of links both segments
+// hold go to the pair's shared-memory partials and are summed in segment
+// order after the pair's barrier.  A robot without a 2-segment plan (a joint
+// driving several links) is swept whole by the pair's first warp.  The pair
+// shares the pulled item through shared memory; its barriers are named
+// barriers of 64 threads, and both warps leave the loop on the same item.
+__device__ __forceinline__ void pair_bar(int id) {
+  asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
+}
+
+// shared memory: one item slot per pair (32 words), then per pair the
+// partials [nout][ns_max][2][32]
+__host__ __device__ inline size_t batch_tree_words(int nout, int ns_max) {
+  return 32 + 2 * (size_t)nout * ns_max * 64;
+}
+
 __global__ void __launch_bounds__(128) batch_tree_fwd_kernel(const DevRobot* robots,
                                                              const BatchProblemDev* probs,
                                                              const int4* items, int n_items,
-                                                             int* counter, BatchIO io) {
-  const int lane = threadIdx.x & 31;
+                                                             int* counter, BatchIO io,
+                                                             int ns_max) {
+  extern __shared__ float sm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int pi = warp >> 1, g = warp & 1, bar = 1 + pi;
+  int* slot = reinterpret_cast<int*>(sm) + pi;
+  float* part = sm + 32 + (size_t)pi * ns_max * 64;
   for (;;) {
-    const int it = warp_pull(counter, lane);
+    if (g == 0 && lane == 0) *slot = atomicAdd(counter, 1);
+    pair_bar(bar);
+    const int it = *slot;
     if (it >= n_items) return;
     const int4 w = items[it];
     const BatchProblemDev pb = probs[w.x];
@@ -44,7 +71,21 @@ __global__ void __launch_bounds__(128) batch_tree_fwd_kernel(const DevRobot* rob
               nullptr,
               io.tau ? io.tau + pb.jo : nullptr,
               nullptr};
-    if (lane < w.z) tree_fwd_one(r, A, (int64_t)w.y + lane);
+    const int64_t b = (int64_t)w.y + lane;
+    const bool seg = r.seg_ok & 1;
+    const int ns = seg ? r.seg_ns[0] : 0;
+    // one call site for both cases (a second inlined sweep would cost registers)
+    const Seg sg = seg ? Seg{r.seg_pos[0][g], r.seg_pos[0][g + 1], g, 2, r.seg_slot, part, ns, lane}
+                       : whole_sweep(r);
+    for (int q = 0; q < ns; ++q) part[(q * 2 + g) * 32 + lane] = 0.0f;
+    if ((seg || g == 0) && lane < w.z) tree_fwd_seg(r, A, b, sg);
+    pair_bar(bar);
+    if (lane < w.z && A.tau)
+      for (int q = g; q < ns; q += 2) {
+        const float acc = part[(q * 2) * 32 + lane] + part[(q * 2 + 1) * 32 + lane];
+        A.tau[(int64_t)__ldg(r.jidx + __ldg(r.seg_slot_link + q)) * A.B + b] = acc;
+      }
+    pair_bar(bar);  // the slot and the partials are free again
   }
 }
 
@@ -52,10 +93,17 @@ __global__ void __launch_bounds__(128) batch_tree_fwd_kernel(const DevRobot* rob
 __global__ void __launch_bounds__(128, 4) batch_tree_bwd_kernel(const DevRobot* robots,
                                                              const BatchProblemDev* probs,
                                                              const int4* items, int n_items,
-                                                             int* counter, BatchIO io) {
-  const int lane = threadIdx.x & 31;
+                                                             int* counter, BatchIO io,
+                                                             int ns_max) {
+  extern __shared__ float sm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int pi = warp >> 1, g = warp & 1, bar = 1 + pi;
+  int* slot = reinterpret_cast<int*>(sm) + pi;
+  float* part = sm + 32 + (size_t)pi * 3 * ns_max * 64;
   for (;;) {
-    const int it = warp_pull(counter, lane);
+    if (g == 0 && lane == 0) *slot = atomicAdd(counter, 1);
+    pair_bar(bar);
+    const int it = *slot;
     if (it >= n_items) return;
     const int4 w = items[it];
     const BatchProblemDev pb = probs[w.x];
@@ -72,7 +120,27 @@ __global__ void __launch_bounds__(128, 4) batch_tree_bwd_kernel(const DevRobot* 
               io.gq + pb.jo,
               io.gqd + pb.jo,
               io.gqdd + pb.jo};
-    if (lane < w.z) tree_bwd_one(r, A, (int64_t)w.y + lane);
+    const int64_t b = (int64_t)w.y + lane;
+    const bool seg = r.seg_ok & 1;
+    const int ns = seg ? r.seg_ns[0] : 0;
+    const size_t o = (size_t)ns * 64;  // one output's partials
+    const Seg sg = seg ? Seg{r.seg_pos[0][g], r.seg_pos[0][g + 1], g, 2, r.seg_slot, part, ns, lane}
+                       : whole_sweep(r);
+    for (int q = 0; q < ns; ++q)
+      for (int k = 0; k < 3; ++k) part[k * o + (q * 2 + g) * 32 + lane] = 0.0f;
+    if ((seg || g == 0) && lane < w.z) tree_bwd_seg<false>(r, A, FusedCost{}, b, sg);
+    pair_bar(bar);
+    if (lane < w.z)
+      for (int q = g; q < ns; q += 2) {
+        float acc[3];
+        for (int k = 0; k < 3; ++k)
+          acc[k] = part[k * o + (q * 2) * 32 + lane] + part[k * o + (q * 2 + 1) * 32 + lane];
+        const int64_t at = (int64_t)__ldg(r.jidx + __ldg(r.seg_slot_link + q)) * A.B + b;
+        A.gq[at] = acc[0];
+        A.gqd[at] = acc[1];
+        A.gqdd[at] = acc[2];
+      }
+    pair_bar(bar);  // the slot and the partials are free again
   }
 }
 
@@ -116,23 +184,35 @@ __global__ void __launch_bounds__(256, 3) batch_pair_kernel(const DevRobot* robo
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+size_t batch_tree_smem(bool fwd, int ns_max) {
+  return sizeof(float) * batch_tree_words(fwd ? 1 : 3, ns_max);
+}
+
 cudaError_t launch_batch_tree_fwd(const DevRobot* robots, const BatchProblemDev* probs, const int4* items,
                                   int n_items, int* counter, const BatchIO& io, int grid,
-                                  cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+                                  int ns_max, cudaStream_t s) {
+  const size_t smem = batch_tree_smem(true, ns_max);
+  cudaError_t e = cudaFuncSetAttribute(batch_tree_fwd_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  batch_tree_fwd_kernel<<<grid, 128, 0, s>>>(
-      robots, probs, items, n_items, counter, io);
+  e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  batch_tree_fwd_kernel<<<grid, 128, smem, s>>>(robots, probs, items, n_items, counter, io,
+                                                ns_max);
   return cudaGetLastError();
 }
 
 cudaError_t launch_batch_tree_bwd(const DevRobot* robots, const BatchProblemDev* probs, const int4* items,
                                   int n_items, int* counter, const BatchIO& io, int grid,
-                                  cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+                                  int ns_max, cudaStream_t s) {
+  const size_t smem = batch_tree_smem(false, ns_max);
+  cudaError_t e = cudaFuncSetAttribute(batch_tree_bwd_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  batch_tree_bwd_kernel<<<grid, 128, 0, s>>>(
-      robots, probs, items, n_items, counter, io);
+  e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  batch_tree_bwd_kernel<<<grid, 128, smem, s>>>(robots, probs, items, n_items, counter, io,
+                                                ns_max);
   return cudaGetLastError();
 }
 
@@ -165,9 +245,13 @@ cudaError_t batch_pair_max_blocks_per_sm(int warps, int ws_words, int rad_words,
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_pair_kernel, warps * 32, smem);
 }
 
-cudaError_t batch_tree_max_blocks_per_sm(bool fwd, int* out) {
-  return fwd ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_tree_fwd_kernel, 128, 0)
-             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_tree_bwd_kernel, 128, 0);
+cudaError_t batch_tree_max_blocks_per_sm(bool fwd, int ns_max, int* out) {
+  const size_t smem = batch_tree_smem(fwd, ns_max);
+  cudaError_t e = cudaFuncSetAttribute(fwd ? batch_tree_fwd_kernel : batch_tree_bwd_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return fwd ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_tree_fwd_kernel, 128, smem)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_tree_bwd_kernel, 128, smem);
 }
 
 int pair_plan_words(const DevRobot& r) { return PairPlan(r.n, r.Sg, r.P, false).total; }

@@ -1305,8 +1305,12 @@ struct wb_batch {
   const int* d_counters = nullptr;
   int n_titems = 0, n_pitems = 0;
   int ws_words = 0, rad_words = 0;
+  int ns_max = 0;  // most shared slots among the robots' 2-segment sweep plans
   wb_batch_sizes sizes{};
 };
+
+// the most shared output slots among these robots' 2-segment sweep plans
+static int seg2_slots(const DevRobot& D) { return (D.seg_ok & 1) ? D.seg_ns[0] : 0; }
 
 extern "C" {
 
@@ -1351,6 +1355,7 @@ int wb_batch_create(wb_robot* const* robots, int32_t n_robots, const wb_problem*
     for (int c = 0; c < H; ++c) pitems.push_back(make_int2(p, c));
     Bt->ws_words = std::max(Bt->ws_words, pair_plan_words(D));
     Bt->rad_words = std::max(Bt->rad_words, (4 * D.Sg + 31) & ~31);
+    Bt->ns_max = std::max(Bt->ns_max, seg2_slots(D));
   }
   // longest work first
   auto tcost = [&](const int4& w) { return robots[w.w]->dev.n; };
@@ -1424,9 +1429,9 @@ void wb_free_batch(wb_batch* batch) {
 
 static int batch_grid_tree(const wb_batch* Bt, bool fwd, int* grid) {
   int bps = 0;
-  cudaError_t e = batch_tree_max_blocks_per_sm(fwd, &bps);
+  cudaError_t e = batch_tree_max_blocks_per_sm(fwd, Bt->ns_max, &bps);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
-  const int need = (Bt->n_titems + 3) / 4;  // 4 warps per block
+  const int need = (Bt->n_titems + 1) / 2;  // two pairs of warps per block, an item per pair
   *grid = std::max(1, std::min(need, std::max(bps, 1) * Bt->num_sms));
   return WB_OK;
 }
@@ -1459,7 +1464,7 @@ int wb_batch_eval(wb_batch* batch, const float* q, const float* qd, const float*
     int grid = 1;
     if ((rc = batch_grid_tree(batch, true, &grid))) return rc;
     e = launch_batch_tree_fwd(batch->d_robots, batch->d_probs, batch->d_titems, batch->n_titems,
-                              counters, io, grid, s);
+                              counters, io, grid, batch->ns_max, s);
     if (e != cudaSuccess) return cuda_fail(e, "wb_batch_eval launch");
   }
   if (pairs && batch->n_pitems > 0) {
@@ -1506,7 +1511,8 @@ int wb_batch_eval_backward(wb_batch* batch, const float* q, const float* qd, con
   if ((rc = batch_grid_tree(batch, false, &grid))) return rc;
   cudaError_t e = launch_batch_tree_bwd(batch->d_robots, batch->d_probs, batch->d_titems,
                                         batch->n_titems, const_cast<int*>(batch->d_counters) + 2,
-                                        io, grid, static_cast<cudaStream_t>(stream));
+                                        io, grid, batch->ns_max,
+                                        static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "wb_batch_eval_backward launch");
   return WB_OK;
 }
@@ -1769,11 +1775,14 @@ int wb_batch_eval_noalloc(wb_robot* const* robots, int32_t n_robots, const wb_pr
   BatchIO io{q, qd, qdd, link_pose, sphere, d_min, worst_pair, tau,
              nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   if (link_pose || tau) {
+    int ns_max = 0;
+    for (int i = 0; i < n_robots; ++i) ns_max = std::max(ns_max, seg2_slots(robots[i]->dev));
     int bps = 0;
-    e = batch_tree_max_blocks_per_sm(true, &bps);
+    e = batch_tree_max_blocks_per_sm(true, ns_max, &bps);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
-    const int grid = std::max(1, std::min((n_titems + 3) / 4, std::max(bps, 1) * R0->num_sms));
-    e = launch_batch_tree_fwd(T.robots, T.probs, T.titems, n_titems, T.counters, io, grid, s);
+    const int grid = std::max(1, std::min((n_titems + 1) / 2, std::max(bps, 1) * R0->num_sms));
+    e = launch_batch_tree_fwd(T.robots, T.probs, T.titems, n_titems, T.counters, io, grid, ns_max,
+                              s);
     if (e != cudaSuccess) return cuda_fail(e, "wb_batch_eval_noalloc launch");
   }
   if (pairs) {

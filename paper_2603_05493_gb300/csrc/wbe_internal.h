@@ -172,12 +172,13 @@ struct BatchIO {
   float* gqdd;
 };
 
+// ns_max: the most shared output slots among the robots' 2-segment plans
 cudaError_t launch_batch_tree_fwd(const DevRobot* robots, const BatchProblemDev* probs,
                                   const int4* items, int n_items, int* counter, const BatchIO& io,
-                                  int grid, cudaStream_t s);
+                                  int grid, int ns_max, cudaStream_t s);
 cudaError_t launch_batch_tree_bwd(const DevRobot* robots, const BatchProblemDev* probs,
                                   const int4* items, int n_items, int* counter, const BatchIO& io,
-                                  int grid, cudaStream_t s);
+                                  int grid, int ns_max, cudaStream_t s);
 cudaError_t launch_batch_pair(const DevRobot* robots, const PairSchedule32* scheds,
                               const BatchProblemDev* probs, const int2* items, int n_items,
                               int* counter, const BatchIO& io, int grid, int warps, int ws_words,
@@ -212,7 +213,7 @@ __host__ __device__ NoAllocTables noalloc_tables(unsigned char* base);
 cudaError_t noalloc_scratch(int device, unsigned char** out);
 cudaError_t launch_noalloc_setup(const NoAllocPlan& plan, unsigned char* base, int grid,
                                  cudaStream_t s);
-cudaError_t batch_tree_max_blocks_per_sm(bool fwd, int* out);
+cudaError_t batch_tree_max_blocks_per_sm(bool fwd, int ns_max, int* out);
 int pair_plan_words(const DevRobot& r);
 
 // launchers (return cudaGetLastError())
