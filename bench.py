@@ -625,7 +625,7 @@ def run_trajopt(args, rank=0, world=1, local_rank=0):
     kernels = {}
     kn = {"bspline_fwd": "bspline_fwd_kernel", "pair": "pair_kernel", "hinge": "hinge_kernel",
           "tree_fwd": "tree_fwd_seg_kernel" if seg(ft) > 1 else "tree_fwd_kernel",
-          "tree_bwd": "tree_bwd_seg_kernel" if seg(bt) > 1 else "tree_bwd_kernel",
+          "tree_bwd": "tree_bwd_cost_seg_kernel" if seg(bt) > 1 else "tree_bwd_cost_kernel",
           "bspline_bwd": "bspline_bwd_kernel"}
     for nm, ms in k_ms.items():
         w = work[nm]
