@@ -5,7 +5,8 @@
 // One warp per configuration (persistent grid).  The warp stages the poses
 // and, at every depth-first position, the link's mass moment m_k x_k =
 // m_k p_k + R_k h_k (h_k = m_k c_k, payload point masses included in the
-// compact inertia).  A lane per joint j then walks the links the joint
+// compact inertia), kept as exclusive prefix sums over the depth-first order
+// so that any subtree's moment is one difference.  A lane per joint j then walks the links the joint
 // drives (connectedLinks of Alg. 2, several for a mimic joint):
 //   Jacobian of target e: a driven link l contributes when it is an ancestor
 //     of e or e itself -- an O(1) test on depth-first ranges (l's subtree is
@@ -14,15 +15,20 @@
 //     (w = R_l a_l) and m_l [R_l a_l; 0] for a prismatic one;
 //   centre of mass: sum_k m_k x_k / M, and column j of its Jacobian
 //     sum_l m_l (w x (S_l - M_l p_l)) / M (revolute) or M_l R_l a_l / M
-//     (prismatic), with S_l and M_l the mass moment and mass of l's subtree,
-//     summed over its contiguous depth-first range.
+//     (prismatic), with S_l and M_l the mass moment and mass of l's subtree:
+//     the difference of the prefix sums at the ends of its contiguous
+//     depth-first range.
 // Rows of a link Jacobian: velocity of the world origin, then angular
 // velocity, both in world coordinates.
 #include "spatial.cuh"
 
 namespace wbe {
 
-static __host__ __device__ int kin_words(int n) { return ((12 * n + 31) & ~31) + ((4 * n + 31) & ~31); }
+// per warp: link poses, then the exclusive prefix sums of the mass moments
+// over the depth-first order (n + 1 float4)
+static __host__ __device__ int kin_words(int n) {
+  return ((12 * n + 31) & ~31) + ((4 * (n + 1) + 31) & ~31);
+}
 
 __global__ void __launch_bounds__(256) kin_kernel(DevRobot r, const __grid_constant__ KinArgs A) {
   extern __shared__ __align__(16) float smem[];
@@ -38,37 +44,54 @@ __global__ void __launch_bounds__(256) kin_kernel(DevRobot r, const __grid_const
     const bool want_com = A.com || A.jac_com;
     float M = 0.0f;
     if (want_com) {
-      float cx = 0.0f, cy = 0.0f, cz = 0.0f, m = 0.0f;
-      for (int pos = lane; pos < n; pos += 32) {
-        const int k = __ldg(r.dfs + pos).x;
-        const float* I = r.inert + 10 * k;
-        const float mk = __ldg(I), h[3] = {__ldg(I + 1), __ldg(I + 2), __ldg(I + 3)};
-        const float* T = P + 12 * k;
-        float Rh[3];
-        rot(T, h, Rh);
-        const float4 v = make_float4(fmaf(mk, T[9], Rh[0]), fmaf(mk, T[10], Rh[1]),
-                                     fmaf(mk, T[11], Rh[2]), mk);
-        mom[pos] = v;
-        cx += v.x;
-        cy += v.y;
-        cz += v.z;
-        m += v.w;
-      }
+      // mass moments by DFS position and their exclusive prefix sums
+      // mom[pos] = sum of the first pos moments (warp scans, 32 at a time):
+      // a subtree is a DFS range [pos_l, end_l), so its moment is
+      // mom[end_l] - mom[pos_l], and the whole body's is mom[n]
+      float4 carry = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if (lane == 0) mom[0] = carry;
+      for (int p0 = 0; p0 < n; p0 += 32) {
+        const int pos = p0 + lane;
+        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (pos < n) {
+          const int k = __ldg(r.dfs + pos).x;
+          const float* I = r.inert + 10 * k;
+          const float mk = __ldg(I), h[3] = {__ldg(I + 1), __ldg(I + 2), __ldg(I + 3)};
+          const float* T = P + 12 * k;
+          float Rh[3];
+          rot(T, h, Rh);
+          v = make_float4(fmaf(mk, T[9], Rh[0]), fmaf(mk, T[10], Rh[1]), fmaf(mk, T[11], Rh[2]),
+                          mk);
+        }
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        cx += __shfl_xor_sync(0xffffffffu, cx, off);
-        cy += __shfl_xor_sync(0xffffffffu, cy, off);
-        cz += __shfl_xor_sync(0xffffffffu, cz, off);
-        m += __shfl_xor_sync(0xffffffffu, m, off);
-      }
-      M = m;
-      if (A.com && lane == 0) {
-        const float iM = m > 0.0f ? 1.0f / m : 0.0f;
-        A.com[3 * b] = cx * iM;
-        A.com[3 * b + 1] = cy * iM;
-        A.com[3 * b + 2] = cz * iM;
+        for (int off = 1; off < 32; off <<= 1) {  // inclusive scan
+          const float x = __shfl_up_sync(0xffffffffu, v.x, off);
+          const float y = __shfl_up_sync(0xffffffffu, v.y, off);
+          const float z = __shfl_up_sync(0xffffffffu, v.z, off);
+          const float w = __shfl_up_sync(0xffffffffu, v.w, off);
+          if (lane >= off) {
+            v.x += x;
+            v.y += y;
+            v.z += z;
+            v.w += w;
+          }
+        }
+        if (pos < n)
+          mom[pos + 1] = make_float4(carry.x + v.x, carry.y + v.y, carry.z + v.z, carry.w + v.w);
+        carry.x += __shfl_sync(0xffffffffu, v.x, 31);
+        carry.y += __shfl_sync(0xffffffffu, v.y, 31);
+        carry.z += __shfl_sync(0xffffffffu, v.z, 31);
+        carry.w += __shfl_sync(0xffffffffu, v.w, 31);
       }
       __syncwarp();
+      const float4 tot = mom[n];
+      M = tot.w;
+      if (A.com && lane == 0) {
+        const float iM = M > 0.0f ? 1.0f / M : 0.0f;
+        A.com[3 * b] = tot.x * iM;
+        A.com[3 * b + 1] = tot.y * iM;
+        A.com[3 * b + 2] = tot.z * iM;
+      }
     }
     for (int j = lane; j < d; j += 32) {
       const int l0 = __ldg(r.jl_start + j), l1 = __ldg(r.jl_start + j + 1);
@@ -83,15 +106,9 @@ __global__ void __launch_bounds__(256) kin_kernel(DevRobot r, const __grid_const
           float wv[3];
           rot(T, a, wv);  // R_l a_l
           const float mm = __ldg(reinterpret_cast<const float2*>(r.mimic) + l).x;
-          float S[3] = {0.0f, 0.0f, 0.0f}, Ms = 0.0f;
-          const int e0 = __ldg(r.dfs_pos + l), e1 = __ldg(r.dfs_end + l);
-          for (int pos = e0; pos < e1; ++pos) {
-            const float4 v = mom[pos];
-            S[0] += v.x;
-            S[1] += v.y;
-            S[2] += v.z;
-            Ms += v.w;
-          }
+          const float4 hi = mom[__ldg(r.dfs_end + l)], lo = mom[__ldg(r.dfs_pos + l)];
+          const float S[3] = {hi.x - lo.x, hi.y - lo.y, hi.z - lo.z};
+          const float Ms = hi.w - lo.w;
           if (__ldg(r.jtype + l) == 1) {
             const float rel[3] = {fmaf(-Ms, T[9], S[0]), fmaf(-Ms, T[10], S[1]),
                                   fmaf(-Ms, T[11], S[2])};
