@@ -155,3 +155,51 @@ def test_streamed_step_matches_direct_calls(W):
                    "gqd": g[1][:, sl], "gqdd": g[2][:, sl]}
             for k, v in ref.items():
                 assert torch.equal(hout[c][k], v.cpu()), (c, k)
+
+
+def test_uneven_full_size_sampled(W, O):
+    """The bench's uneven workload (256 x R7 + 256 x R23 + 256 x R48, horizons
+    U{16..64}, 30,398 configurations) in one batch, with the bench's input
+    seeds; five problems of each robot checked against the oracle."""
+    mix = I.uneven_mix()
+    robs = [W.Robot(d, device=0) for d in mix.robots]
+    problems = list(zip(mix.robot_of.tolist(), mix.horizon.tolist()))
+    batch = W.Batch(robs, problems)
+    raw = {}
+
+    def packed(kind, k, make):
+        out = batch.empty(kind)
+        for p, (ri, H) in enumerate(problems):
+            x = make(mix.robots[ri], H, 7000 + p)
+            raw.setdefault(p, {})[k] = x
+            o = int(batch.offsets[kind][p])
+            t = torch.from_numpy(np.ascontiguousarray(x)).reshape(-1).cuda()
+            out[o:o + t.numel()] = t
+        return out
+    q = packed("joint", "q", lambda d, H, s: I.uniform_states(d.dof, H, s)[0])
+    qd = packed("joint", "qd", lambda d, H, s: I.uniform_states(d.dof, H, s)[1])
+    qdd = packed("joint", "qdd", lambda d, H, s: I.uniform_states(d.dof, H, s)[2])
+    gp = packed("pose", "gp", lambda d, H, s: I.upstream_grads(d, H, s)[0])
+    gs = packed("sphere", "gs", lambda d, H, s: I.upstream_grads(d, H, s)[1])
+    gm = packed("config", "gm", lambda d, H, s: I.upstream_grads(d, H, s)[2])
+    gt = packed("joint", "gt", lambda d, H, s: I.upstream_grads(d, H, s)[3])
+    x = dict(q=q, qd=qd, qdd=qdd, g_pose=gp, g_sph=gs, g_dmin=gm, g_tau=gt)
+    o, g = run(batch, x)
+    torch.cuda.synchronize()
+    assert int(mix.horizon.sum()) == 30398
+    for ri in range(len(mix.robots)):
+        ps = [p for p, (r, _) in enumerate(problems) if r == ri][:5]
+        for p in ps:
+            d, H, rp = mix.robots[ri], problems[p][1], raw[p]
+            got = {"pose": batch.view(o["pose"], "pose", p, (H, d.n, 12)).cpu().numpy(),
+                   "sphere": batch.view(o["sphere"], "sphere", p, (H, d.S, 3)).cpu().numpy(),
+                   "dmin": batch.view(o["dmin"], "config", p, (H,)).cpu().numpy(),
+                   "worst": batch.view(o["worst"], "config", p, (H,)).cpu().numpy(),
+                   "tau": batch.view(o["tau"], "joint", p, (d.dof, H)).cpu().numpy()}
+            ref = O.evaluate(d, rp["q"], rp["qd"], rp["qdd"])
+            PY.check_forward(d, got, ref)
+            gref = O.gradient(d, rp["q"], rp["qd"], rp["qdd"], rp["gp"], rp["gs"], rp["gm"],
+                              rp["gt"])
+            same = got["worst"] == ref["worst"]
+            PY.check_gradient([batch.view(t, "joint", p, (d.dof, H)).cpu().numpy() for t in g],
+                              gref, mask=same)

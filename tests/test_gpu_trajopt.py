@@ -454,3 +454,31 @@ def test_fused_cost_refusals(W):
     with pytest.raises(L.WbError) as e:  # d_min without its worst pair
         r7.eval_backward_cost(x, x, x, x, -lim, lim, 1.0, d_min=torch.zeros(8, device="cuda"))
     assert e.value.code == L.WB_EINVAL
+
+
+def test_trajopt48_full_size_fused_cost_sampled(W, O):
+    """The full 512 x 64 launch as the bench runs it (the cost in the
+    backward sweep's prologue, autotuned shapes); three trajectories checked
+    against the oracle."""
+    desc = I.hand_payload(R.r48())
+    rob = W.Robot(desc, device=0)
+    n_traj, K, T, dt = CF.TRAJOPT_SEEDS, CF.TRAJOPT_KNOTS, CF.TRAJOPT_STEPS, CF.TRAJOPT_DT
+    B = n_traj * T
+    ft, bt, _, _ = rob.autotune(B)
+    U = I.bspline_controls(desc.dof, n_traj, K, seed=CF.TRAJOPT48.seed)
+    lim, w = CF.TORQUE_LIMIT, CF.COLLISION_WEIGHT
+    motion = dict(smooth=CF.SMOOTH_WEIGHT, length=CF.LENGTH_WEIGHT, energy=CF.ENERGY_WEIGHT)
+    lo, hi = cuda(-lim * np.ones(desc.dof)), cuda(lim * np.ones(desc.dof))
+    q, qd, qdd = W.bspline_eval(cuda(U), T, dt)
+    tree = lambda t: W.Tune(kernel=3, lanes_per_config=t.lanes_per_config if t.kernel == 3 else 0,  # noqa: E731
+                            configs_per_block=t.configs_per_block if t.kernel == 3 else 0)
+    o = rob.eval(q, qd, qdd, tune=tree(ft))
+    gq, gqd, gqdd, cost = rob.eval_backward_cost(q, qd, qdd, o["tau"], lo, hi, w, d_min=o["dmin"],
+                                                 worst=o["worst"], dt=dt * (K - 3) / (T - 1),
+                                                 tune=tree(bt), **motion)
+    gU = W.bspline_backward(gq, gqd, gqdd, n_traj, K, T, dt)
+    torch.cuda.synchronize()
+    assert torch.isfinite(gU).all() and torch.isfinite(cost).all()
+    trajs = [0, 257, n_traj - 1]
+    kept = _compare_chain(O, desc, U[trajs], T, dt, lim, w, gU, cost, o, trajs, motion)
+    assert kept >= 2
