@@ -492,13 +492,17 @@ def trajopt_work(desc, K, T):
     S, P, d = desc.S, desc.P, desc.dof
     return {
         "bspline_fwd": {"flops": 84 * d, "bytes": 4 * 3 * d + 4 * d * K // T},
-        "tree_fwd": {"flops": 150 * nm + 330 * n, "bytes": 4 * (3 * d + 12 * n + d)},
+        # the states evaluated from the trajectory's control points in the sweep
+        # (4 control points and 7 flops per state read; the K d control points of
+        # a trajectory are read once for its T samples)
+        "tree_fwd": {"flops": 150 * nm + 330 * n + 28 * d,
+                     "bytes": 4 * (d * K // T + 12 * n + d)},
         "pair": {"flops": 18 * S + 11 * P, "bytes": 4 * (12 * n + 2)},
-        # the whole adjoint with the cost in its prologue: q, qd, qdd, tau,
-        # d_min and worst in; gq, gqd, gqdd and the cost out (the hinges and
-        # motion terms add ~22 flops per joint)
-        "tree_bwd": {"flops": 150 * nm + 330 * n + 660 * n + 60 * n + 22 * d + 3,
-                     "bytes": 4 * (3 * d + d + 2 + 3 * d + 1)},
+        # the whole adjoint with the cost in its prologue: the control points,
+        # tau, d_min and worst in; gq, gqd, gqdd and the cost out (the hinges
+        # and motion terms add ~22 flops per joint, the states ~56)
+        "tree_bwd": {"flops": 150 * nm + 330 * n + 660 * n + 60 * n + 22 * d + 3 + 56 * d,
+                     "bytes": 4 * (d * K // T + d + 2 + 3 * d + 1)},
         "bspline_bwd": {"flops": 24 * d, "bytes": 4 * 3 * d + 4 * d * K // T},
         # summed hinge: every pair screened from both spheres (sqrt-free, 8 flops)
         "hinge": {"flops": 18 * S + 16 * P, "bytes": 4 * (12 * n + 3 * S + 1)},
@@ -508,10 +512,11 @@ def trajopt_work(desc, K, T):
 def run_trajopt(args, rank=0, world=1, local_rank=0):
     """Trajectory-optimisation gradient step on the 48-DoF humanoid with 3 kg
     hand payloads: 512 seeds x 16 control points per joint -> 64 B-spline
-    samples each (32768 configurations) -> FK + RNEA sweep -> self-collision
-    -> torque-limit + collision hinges and the smooth / length / energy
-    terms, formed in the prologue of the adjoint sweep (which also adds the
-    cost's direct qd / qdd gradients) -> B-spline adjoint -> dL/dU.  Value =
+    samples each (32768 configurations), the states evaluated from the
+    control points inside the sweeps -> FK + RNEA sweep -> self-collision ->
+    torque-limit + collision hinges and the smooth / length / energy terms,
+    formed in the prologue of the adjoint sweep (which also adds the cost's
+    direct qd / qdd gradients) -> B-spline adjoint -> dL/dU.  Value =
     configurations per second."""
     import torch
     from paper_2603_05493_gb300 import build
@@ -535,7 +540,6 @@ def run_trajopt(args, rank=0, world=1, local_rank=0):
     U = hU.to(dev)
     lo = torch.full((d,), -CF.TORQUE_LIMIT, device=dev)
     hi = torch.full((d,), CF.TORQUE_LIMIT, device=dev)
-    q, qd, qdd = (torch.empty((d, B), device=dev) for _ in range(3))
     out = rob.empty_outputs(B, sphere=False)
     fwd_out = {"pose": out["pose"], "sphere": None, "dmin": None, "worst": None,
                "tau": out["tau"], "bits": None}
@@ -547,30 +551,30 @@ def run_trajopt(args, rank=0, world=1, local_rank=0):
     gU = torch.empty((n_traj, d, K), device=dev)
     stream = torch.cuda.current_stream()
     hinge = args.collision == "hinge"
-    # the cost runs in the backward sweep's prologue (wb_eval_backward_cost)
-    names = ["bspline_fwd", "tree_fwd", "hinge" if hinge else "pair", "tree_bwd", "bspline_bwd"]
+    # the states come from the control points inside the sweeps
+    # (wb_eval_spline, wb_eval_backward_spline_cost); the cost runs in the
+    # backward sweep's prologue
+    names = ["tree_fwd", "hinge" if hinge else "pair", "tree_bwd", "bspline_bwd"]
     hinge_cost = torch.empty((B,), device=dev)
     g_sph = torch.empty((B, desc.S, 3), device=dev) if hinge else None
 
     def step(ev=None):
         mark = (lambda i: ev[i].record(stream)) if ev else (lambda i: None)
-        wbe.bspline_eval(U, T, dt, q, qd, qdd)
+        rob.eval_spline(U, T, dt, tune=ftune, out=fwd_out)
         mark(1)
-        rob.eval(q, qd, qdd, tune=ftune, out=fwd_out, dmin=False, sphere=False)
-        mark(2)
         if hinge:  # every pair within the activation distance
             rob.self_collision_hinge(out["pose"], CF.ACTIVATION_DISTANCE, CF.COLLISION_WEIGHT,
                                      cost=hinge_cost, g_sphere=g_sph)
         else:  # the worst pair
             rob.self_collision(out["pose"], out=pair_out)
+        mark(2)
+        rob.eval_backward_spline_cost(U, T, dt, out["tau"], lo, hi, CF.COLLISION_WEIGHT,
+                                      CF.SMOOTH_WEIGHT, CF.LENGTH_WEIGHT, CF.ENERGY_WEIGHT,
+                                      dt_sample, d_min=None if hinge else out["dmin"],
+                                      worst=None if hinge else out["worst"],
+                                      g_sphere=g_sph if hinge else None, cost=cost, tune=btune,
+                                      out=gout)
         mark(3)
-        rob.eval_backward_cost(q, qd, qdd, out["tau"], lo, hi, CF.COLLISION_WEIGHT,
-                               CF.SMOOTH_WEIGHT, CF.LENGTH_WEIGHT, CF.ENERGY_WEIGHT, dt_sample,
-                               d_min=None if hinge else out["dmin"],
-                               worst=None if hinge else out["worst"],
-                               g_sphere=g_sph if hinge else None, cost=cost, tune=btune,
-                               out=gout)
-        mark(4)
         wbe.bspline_backward(*gout, n_traj, K, T, dt, gU)
 
     flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
@@ -624,8 +628,9 @@ def run_trajopt(args, rank=0, world=1, local_rank=0):
     ridge = alu_peak * 1e12 / (hbm_peak * 1e9)
     kernels = {}
     kn = {"bspline_fwd": "bspline_fwd_kernel", "pair": "pair_kernel", "hinge": "hinge_kernel",
-          "tree_fwd": "tree_fwd_seg_kernel" if seg(ft) > 1 else "tree_fwd_kernel",
-          "tree_bwd": "tree_bwd_cost_seg_kernel" if seg(bt) > 1 else "tree_bwd_cost_kernel",
+          "tree_fwd": "tree_fwd_spline_seg_kernel" if seg(ft) > 1 else "tree_fwd_spline_kernel",
+          "tree_bwd": ("tree_bwd_spline_cost_seg_kernel" if seg(bt) > 1
+                       else "tree_bwd_spline_cost_kernel"),
           "bspline_bwd": "bspline_bwd_kernel"}
     for nm, ms in k_ms.items():
         w = work[nm]

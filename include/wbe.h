@@ -475,6 +475,40 @@ int wb_eval_backward_cost(wb_robot* robot, int64_t B, const float* q, const floa
                           float* cost, float* gq, float* gqd, float* gqdd, const wb_tune* tune,
                           void* stream);
 
+/* The whole-body evaluation with the joint states evaluated from uniform
+ * cubic B-spline control points inside the sweeps (Sec. 4, Eq.
+ * bspline-cubic, fused with the evaluation): no q, qd, qdd arrays.
+ * U [n_traj][d][K] control points (device, caller-owned); configuration
+ * b = traj * T + s is sample s of trajectory traj, laid out as in
+ * wb_bspline_eval.  Limits: 4 <= K <= 4096, 2 <= T <= 4096, dt > 0.  The
+ * states are the same bits as wb_bspline_eval's, so the results equal those
+ * of wb_bspline_eval followed by wb_eval (and wb_eval_backward_cost). */
+typedef struct {
+  const float* U;
+  int64_t n_traj;
+  int32_t K, T;
+  float dt;
+} wb_spline;
+
+/* wb_eval on B = n_traj * T configurations from control points: link poses,
+ * spheres, d_min / worst pair (each nullable; spheres and pairs need the
+ * poses) and tau.  Tree kernels only (tune NULL, AUTO, TREE, TREE_NOCULL);
+ * no pair bits.  Errors as wb_eval. */
+int wb_eval_spline(wb_robot* robot, const wb_spline* spline, float* link_pose, float* sphere,
+                   float* d_min, int32_t* worst_pair, float* tau, const wb_tune* tune,
+                   void* stream);
+
+/* wb_eval_backward_cost on the same configurations from control points: the
+ * cost in the backward sweep's prologue, gq, gqd, gqdd [d][n_traj*T] (feed
+ * them to wb_bspline_backward for dL/dU) and the cost [n_traj*T].  Arguments
+ * and errors as wb_eval_backward_cost. */
+int wb_eval_backward_spline_cost(wb_robot* robot, const wb_spline* spline,
+                                 const int32_t* worst_pair, const float* g_pose,
+                                 const float* g_sphere, const float* tau, const float* d_min,
+                                 const float* tau_lo, const float* tau_hi,
+                                 const wb_cost_weights* w, float* cost, float* gq, float* gqd,
+                                 float* gqdd, const wb_tune* tune, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Forward evaluation of an uneven batch without any device allocation.  The
  * paper has no counterpart to this entry point.

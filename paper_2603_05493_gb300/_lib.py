@@ -58,6 +58,11 @@ class wb_cost_weights(C.Structure):
                 ("energy", C.c_float), ("dt", C.c_float)]
 
 
+class wb_spline(C.Structure):
+    _fields_ = [("U", C.c_void_p), ("n_traj", C.c_int64), ("K", C.c_int32), ("T", C.c_int32),
+                ("dt", C.c_float)]
+
+
 class wb_problem(C.Structure):
     _fields_ = [("robot", C.c_int32), ("horizon", C.c_int32)]
 
@@ -107,6 +112,11 @@ SIGNATURES = {
     "wb_trajopt_cost": (C.c_int, [C.c_int64, C.c_int32, p, p, p, p, C.c_float, p, p, p, p]),
     "wb_bspline_backward_ext": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_float,
                                           p, p, p, p, p, p, p]),
+    "wb_eval_spline": (C.c_int, [p, C.POINTER(wb_spline), p, p, p, p, p, C.POINTER(wb_tune),
+                                 p]),
+    "wb_eval_backward_spline_cost": (C.c_int, [p, C.POINTER(wb_spline), p, p, p, p, p, p, p,
+                                               C.POINTER(wb_cost_weights), p, p, p, p,
+                                               C.POINTER(wb_tune), p]),
     "wb_eval_backward_cost": (C.c_int, [p, C.c_int64, p, p, p, p, p, p, p, p, p, p,
                                         C.POINTER(wb_cost_weights), p, p, p, p,
                                         C.POINTER(wb_tune), p]),

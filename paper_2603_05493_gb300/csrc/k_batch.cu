@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(128) batch_tree_fwd_kernel(const DevRobot* rob
     const Seg sg = seg ? Seg{r.seg_pos[0][g], r.seg_pos[0][g + 1], g, 2, r.seg_slot, part, ns, lane}
                        : whole_sweep(r);
     for (int q = 0; q < ns; ++q) part[(q * 2 + g) * 32 + lane] = 0.0f;
-    if ((seg || g == 0) && lane < w.z) tree_fwd_seg(r, A, b, sg);
+    if ((seg || g == 0) && lane < w.z) tree_fwd_seg(r, A, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b, sg);
     pair_bar(bar);
     if (lane < w.z && A.tau)
       for (int q = g; q < ns; q += 2) {
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(128, 4) batch_tree_bwd_kernel(const DevRobot* 
                        : whole_sweep(r);
     for (int q = 0; q < ns; ++q)
       for (int k = 0; k < 3; ++k) part[k * o + (q * 2 + g) * 32 + lane] = 0.0f;
-    if ((seg || g == 0) && lane < w.z) tree_bwd_seg<false>(r, A, FusedCost{}, b, sg);
+    if ((seg || g == 0) && lane < w.z) tree_bwd_seg<false>(r, A, FusedCost{}, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b, sg);
     pair_bar(bar);
     if (lane < w.z)
       for (int q = g; q < ns; q += 2) {

@@ -13,36 +13,9 @@
 // exact quotient, the same integer a double-precision floor gives, since an
 // integer quotient is exact in double and a non-integer one is at least
 // 1/(T-1) away from the next integer) and alpha = remainder / (T-1).
-#include "wbe_internal.h"
+#include "spline_basis.cuh"
 
 namespace wbe {
-
-__device__ __forceinline__ void bs_sample(int s, int K, int T, int& k, float& al) {
-  const int nseg = K - 3;
-  const int num = s * nseg;
-  int kk = num / (T - 1);
-  if (kk > nseg - 1) kk = nseg - 1;
-  k = kk;
-  al = (float)(num - kk * (T - 1)) / (float)(T - 1);
-}
-
-// rows of B(alpha) = T P(alpha) C for theta, theta_dot, theta_ddot, with
-// C = (1/6) [[-1, 3, -3, 1], [3, -6, 3, 0], [-3, 0, 3, 0], [1, 4, 1, 0]]
-__device__ __forceinline__ void bs_basis(float a, float dt, float Bm[3][4]) {
-  const float idt = 1.0f / dt;
-  const float P[3][4] = {{a * a * a, a * a, a, 1.0f},
-                         {3.0f * a * a * idt, 2.0f * a * idt, idt, 0.0f},
-                         {6.0f * a * idt * idt, 2.0f * idt * idt, 0.0f, 0.0f}};
-  const float c = 1.0f / 6.0f;
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    const float* p = P[r];
-    Bm[r][0] = c * (-p[0] + 3.0f * p[1] - 3.0f * p[2] + p[3]);
-    Bm[r][1] = c * (3.0f * p[0] - 6.0f * p[1] + 4.0f * p[3]);
-    Bm[r][2] = c * (-3.0f * p[0] + 3.0f * p[1] + 3.0f * p[2] + p[3]);
-    Bm[r][3] = c * p[0];
-  }
-}
 
 // Boundary conditions (Sec. 4.2).  The spline is evaluated on an extended
 // knot sequence of Kx = K + 3 hs + 3 es knots: with a start state (hs = 1)

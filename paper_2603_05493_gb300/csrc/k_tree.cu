@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(256) tree_fwd_seg_kernel(const __grid_constant
   Seg sg = seg_of(r, t, part + (size_t)cg * ns * G * 32);
   for (int s = 0; s < ns; ++s) sg.part[(s * G + sg.g) * 32 + sg.lane] = 0.0f;
   const int64_t b = ((int64_t)blockIdx.x * CG + cg) * 32 + sg.lane;
-  if (b < A.B) tree_fwd_seg(r, A, b, sg);
+  if (b < A.B) tree_fwd_seg(r, A, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b, sg);
   __syncthreads();
   if (b < A.B && A.tau) {
     for (int s = sg.g; s < ns; s += G) {
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(256, 2) tree_bwd_seg_kernel(const __grid_const
   for (int s = 0; s < ns; ++s)
     for (int q = 0; q < 3; ++q) sg.part[q * o + (s * G + sg.g) * 32 + sg.lane] = 0.0f;
   const int64_t b = ((int64_t)blockIdx.x * CG + cg) * 32 + sg.lane;
-  if (b < A.B) tree_bwd_seg<false>(r, A, FusedCost{}, b, sg);
+  if (b < A.B) tree_bwd_seg<false>(r, A, FusedCost{}, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b, sg);
   __syncthreads();
   if (b < A.B) {
     for (int s = sg.g; s < ns; s += G) {
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(256, 2) tree_bwd_seg_kernel(const __grid_const
 __global__ void __launch_bounds__(256, 2) tree_bwd_cost_kernel(DevRobot r, BwdArgs A,
                                                                FusedCost fc) {
   const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (b < A.B) tree_bwd_cost_one(r, A, fc, b);
+  if (b < A.B) tree_bwd_cost_one(r, A, fc, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b);
 }
 
 __global__ void __launch_bounds__(256, 2) tree_bwd_cost_seg_kernel(
@@ -108,7 +108,105 @@ __global__ void __launch_bounds__(256, 2) tree_bwd_cost_seg_kernel(
     for (int q = 0; q < 3; ++q) sg.part[q * o + (s * G + sg.g) * 32 + sg.lane] = 0.0f;
   const int64_t b = ((int64_t)blockIdx.x * CG + cg) * 32 + sg.lane;
   float c = 0.0f;
-  if (b < A.B) c = tree_bwd_seg<true>(r, A, fc, b, sg);
+  if (b < A.B) c = tree_bwd_seg<true>(r, A, fc, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b, sg);
+  cpart[sg.g * 32 + sg.lane] = c;
+  __syncthreads();
+  if (b < A.B && sg.g == 0 && fc.cost) {
+    float acc = 0.0f;
+    for (int h = 0; h < G; ++h) acc += cpart[h * 32 + sg.lane];
+    fc.cost[b] = fc.d_min ? fmaf(fc.w, fmaxf(0.0f, -__ldg(fc.d_min + b)), acc) : acc;
+  }
+  if (b < A.B) {
+    for (int s = sg.g; s < ns; s += G) {
+      float acc[3] = {0.0f, 0.0f, 0.0f};
+      for (int h = 0; h < G; ++h)
+        for (int q = 0; q < 3; ++q) acc[q] += sg.part[q * o + (s * G + h) * 32 + sg.lane];
+      const int k = __ldg(r.seg_slot_link + t * r.n + s);
+      const int64_t at = (int64_t)__ldg(r.jidx + k) * A.B + b;
+      A.gq[at] = acc[0];
+      A.gqd[at] = acc[1];
+      A.gqdd[at] = acc[2];
+    }
+  }
+}
+
+// The sweeps with the joint states evaluated from B-spline control points
+// where they need them (SplineStates): no state arrays are read or written.
+// Each thread keeps its sample's basis rows in shared memory, in front of the
+// segments' partials.
+__device__ __forceinline__ SplineStates spline_states(const DevRobot& r, const SplineArgs& sp,
+                                                      int64_t b, float* bs) {
+  const int64_t tr = b / sp.T;
+  int k;
+  float al;
+  bs_sample((int)(b - tr * sp.T), sp.K, sp.T, k, al);
+  float Bm[3][4];
+  bs_basis(al, sp.dt, Bm);
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int l = 0; l < 4; ++l) bs[4 * q + l] = Bm[q][l];
+  return SplineStates{sp.U + (tr * r.d) * sp.K + k, sp.K, bs};
+}
+
+__global__ void __launch_bounds__(256) tree_fwd_spline_kernel(DevRobot r, FwdArgs A,
+                                                              SplineArgs sp) {
+  extern __shared__ float sm[];
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= A.B) return;
+  const SplineStates st = spline_states(r, sp, b, sm + 12 * threadIdx.x);
+  tree_fwd_seg(r, A, st, b, whole_sweep(r));
+}
+
+__global__ void __launch_bounds__(256) tree_fwd_spline_seg_kernel(
+    const __grid_constant__ DevRobot r, FwdArgs A, SplineArgs sp, int t) {
+  extern __shared__ float sm[];
+  float* part = sm + 12 * blockDim.x;
+  const int G = 2 << t;
+  const int CG = blockDim.x / (32 * G);
+  const int cg = (threadIdx.x >> 5) / G;
+  const int ns = r.seg_ns[t];
+  Seg sg = seg_of(r, t, part + (size_t)cg * ns * G * 32);
+  for (int s = 0; s < ns; ++s) sg.part[(s * G + sg.g) * 32 + sg.lane] = 0.0f;
+  const int64_t b = ((int64_t)blockIdx.x * CG + cg) * 32 + sg.lane;
+  if (b < A.B) tree_fwd_seg(r, A, spline_states(r, sp, b, sm + 12 * threadIdx.x), b, sg);
+  __syncthreads();
+  if (b < A.B && A.tau) {
+    for (int s = sg.g; s < ns; s += G) {
+      float acc = 0.0f;
+      for (int h = 0; h < G; ++h) acc += sg.part[(s * G + h) * 32 + sg.lane];
+      const int k = __ldg(r.seg_slot_link + t * r.n + s);
+      A.tau[(int64_t)__ldg(r.jidx + k) * A.B + b] = acc;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256, 2) tree_bwd_spline_cost_kernel(DevRobot r, BwdArgs A,
+                                                                      FusedCost fc,
+                                                                      SplineArgs sp) {
+  extern __shared__ float sm[];
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= A.B) return;
+  tree_bwd_cost_one(r, A, fc, spline_states(r, sp, b, sm + 12 * threadIdx.x), b);
+}
+
+__global__ void __launch_bounds__(256, 2) tree_bwd_spline_cost_seg_kernel(
+    const __grid_constant__ DevRobot r, BwdArgs A, FusedCost fc, SplineArgs sp, int t) {
+  extern __shared__ float sm[];
+  float* base = sm + 12 * blockDim.x;
+  const int G = 2 << t;
+  const int CG = blockDim.x / (32 * G);
+  const int cg = (threadIdx.x >> 5) / G;
+  const int ns = r.seg_ns[t];
+  const size_t o = (size_t)ns * G * 32;  // one output's partials
+  Seg sg = seg_of(r, t, base + (size_t)cg * (3 * o + G * 32));
+  float* cpart = sg.part + 3 * o;  // [G][32] the segments' cost terms
+  for (int s = 0; s < ns; ++s)
+    for (int q = 0; q < 3; ++q) sg.part[q * o + (s * G + sg.g) * 32 + sg.lane] = 0.0f;
+  const int64_t b = ((int64_t)blockIdx.x * CG + cg) * 32 + sg.lane;
+  float c = 0.0f;
+  if (b < A.B)
+    c = tree_bwd_seg<true>(r, A, fc, spline_states(r, sp, b, sm + 12 * threadIdx.x), b, sg);
   cpart[sg.g * 32 + sg.lane] = c;
   __syncthreads();
   if (b < A.B && sg.g == 0 && fc.cost) {
@@ -206,6 +304,49 @@ cudaError_t launch_tree_bwd(const DevRobot& r, const BwdArgs& a, int threads, in
     tree_bwd_cost_kernel<<<(unsigned)grid, threads, 0, s>>>(r, a, *fc);
   else
     tree_bwd_kernel<<<(unsigned)grid, threads, 0, s>>>(r, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tree_fwd_spline(const DevRobot& r, const FwdArgs& a, const SplineArgs& sp,
+                                   int threads, int segments, cudaStream_t s) {
+  if (threads <= 0) threads = 128;
+  if (segments > 1) {
+    const int t = seg_plan(segments);
+    const int CG = seg_groups(segments, threads);
+    const int block = 32 * segments * CG;
+    const size_t smem = tree_seg_smem(r, segments, threads, true, false) + 12 * sizeof(float) * block;
+    cudaError_t e = cudaFuncSetAttribute(tree_fwd_spline_seg_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = ((a.B + 31) / 32 + CG - 1) / CG;
+    tree_fwd_spline_seg_kernel<<<(unsigned)grid, block, smem, s>>>(r, a, sp, t);
+    return cudaGetLastError();
+  }
+  const size_t smem = 12 * sizeof(float) * threads;
+  const int64_t grid = (a.B + threads - 1) / threads;
+  tree_fwd_spline_kernel<<<(unsigned)grid, threads, smem, s>>>(r, a, sp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tree_bwd_spline_cost(const DevRobot& r, const BwdArgs& a, const FusedCost& fc,
+                                        const SplineArgs& sp, int threads, int segments,
+                                        cudaStream_t s) {
+  if (threads <= 0) threads = 128;
+  if (segments > 1) {
+    const int t = seg_plan(segments);
+    const int CG = seg_groups(segments, threads);
+    const int block = 32 * segments * CG;
+    const size_t smem = tree_seg_smem(r, segments, threads, false, true) + 12 * sizeof(float) * block;
+    cudaError_t e = cudaFuncSetAttribute(tree_bwd_spline_cost_seg_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = ((a.B + 31) / 32 + CG - 1) / CG;
+    tree_bwd_spline_cost_seg_kernel<<<(unsigned)grid, block, smem, s>>>(r, a, fc, sp, t);
+    return cudaGetLastError();
+  }
+  const size_t smem = 12 * sizeof(float) * threads;
+  const int64_t grid = (a.B + threads - 1) / threads;
+  tree_bwd_spline_cost_kernel<<<(unsigned)grid, threads, smem, s>>>(r, a, fc, sp);
   return cudaGetLastError();
 }
 

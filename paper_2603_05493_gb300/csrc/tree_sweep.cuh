@@ -51,6 +51,7 @@
 #pragma once
 
 #include "spatial.cuh"
+#include "spline_basis.cuh"
 
 namespace wbe {
 
@@ -76,6 +77,45 @@ __device__ __forceinline__ Seg whole_sweep(const DevRobot& r) {
 // humanoid: 11 % off the one-thread sweeps; an L1 hint gives the same).
 // Only called on addresses inside the caller's buffers.
 __device__ __forceinline__ void pf(const void* p) { asm volatile("prefetch.L2 [%0];" ::"l"(p)); }
+
+// The joint states (q, qd, qdd of joint j) of the sweep's configuration b,
+// from [d][B] arrays ...
+struct ArrayStates {
+  const float* q;
+  const float* qd;
+  const float* qdd;
+  int64_t B, b;
+  __device__ __forceinline__ float pos(int j) const { return __ldg(q + (int64_t)j * B + b); }
+  __device__ __forceinline__ float vel(int j) const { return __ldg(qd + (int64_t)j * B + b); }
+  __device__ __forceinline__ float acc(int j) const { return __ldg(qdd + (int64_t)j * B + b); }
+  __device__ __forceinline__ void prefetch(int j, bool rates) const {
+    pf(q + (int64_t)j * B + b);
+    if (rates) {
+      pf(qd + (int64_t)j * B + b);
+      pf(qdd + (int64_t)j * B + b);
+    }
+  }
+};
+
+// ... or evaluated from uniform cubic B-spline control points (Sec. 4,
+// Eq. bspline-cubic) where the sweep needs them: the configuration is sample
+// s of trajectory tr, u points at that trajectory's first window knot of
+// joint 0 (control points [d][K]) and bs at the sample's basis rows [3][4]
+// (q, qd, qdd), computed once per configuration.  Same arithmetic as the
+// B-spline forward kernel, so the states are the same bits.
+struct SplineStates {
+  const float* u;
+  int K;
+  const float* bs;
+  __device__ __forceinline__ float row(int j, int r) const {
+    const float* p = u + (int64_t)j * K;
+    return bs_row(bs + 4 * r, __ldg(p), __ldg(p + 1), __ldg(p + 2), __ldg(p + 3));
+  }
+  __device__ __forceinline__ float pos(int j) const { return row(j, 0); }
+  __device__ __forceinline__ float vel(int j) const { return row(j, 1); }
+  __device__ __forceinline__ float acc(int j) const { return row(j, 2); }
+  __device__ __forceinline__ void prefetch(int j, bool) const { pf(u + (int64_t)j * K); }
+};
 
 // where the partial output o of link k goes, or nullptr for a direct write
 __device__ __forceinline__ float* seg_part(const Seg& sg, int k, int o) {
@@ -111,10 +151,10 @@ __device__ __forceinline__ void compose(const float* P, const float* L, float* W
   W[11] = P[11] + t[2];
 }
 
-__device__ __forceinline__ void link_local(const DevRobot& r, int k, const float* q, int64_t B,
-                                           int64_t b, float* L) {
+template <class St>
+__device__ __forceinline__ void link_local(const DevRobot& r, int k, const St& st, float* L) {
   const int j = __ldg(r.jidx + k);
-  const float th = j >= 0 ? joint_var(r, k, __ldg(q + (int64_t)j * B + b)) : 0.0f;
+  const float th = j >= 0 ? joint_var(r, k, st.pos(j)) : 0.0f;
   local_xf(r, k, th, L, L + 9);
 }
 
@@ -131,8 +171,9 @@ struct FEnt {
   float v[6], a[6], F[6];
 };
 
-__device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A, int64_t b,
-                                             const Seg& sg) {
+template <class St>
+__device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A, const St& st,
+                                             int64_t b, const Seg& sg) {
   const int64_t B = A.B;
   const int n = r.n;
   const bool dyn = A.tau != nullptr;
@@ -178,7 +219,7 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
     }
     if (e > 0) {
       float L[12], up[6];
-      link_local(r, k, A.q, B, b, L);
+      link_local(r, k, st, L);
       xf_force_T(L, L + 9, F, up);
 #pragma unroll
       for (int i = 0; i < 6; ++i) pF[i] = stk[e - 1].F[i] + up[i];
@@ -199,7 +240,7 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
     if (dyn) flush();  // the parent's force, when it is still pending
     FEnt& E = stk[dep];
     float L[12];
-    link_local(r, k, A.q, B, b, L);
+    link_local(r, k, st, L);
     float PW[12], vp[6], ap[6];
     if (dep > 0) {
       if (dep == cdep + 1) {
@@ -248,8 +289,8 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
       const float4 a4 = __ldg(reinterpret_cast<const float4*>(r.axis) + k);
       const float ax[3] = {a4.x, a4.y, a4.z};
       const float mm = __ldg(reinterpret_cast<const float2*>(r.mimic) + k).x;
-      const float vq = j >= 0 ? mm * __ldg(A.qd + (int64_t)j * B + b) : 0.0f;
-      const float aq = j >= 0 ? mm * __ldg(A.qdd + (int64_t)j * B + b) : 0.0f;
+      const float vq = j >= 0 ? mm * st.vel(j) : 0.0f;
+      const float aq = j >= 0 ? mm * st.acc(j) : 0.0f;
       rnea_va(L, L + 9, vp, ap, __ldg(r.jtype + k), ax, vq, aq, cv, ca);
       float F[6];
       if (own) {
@@ -291,13 +332,7 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
     const int dep = kd.y;
     if (pos + 1 < sg.p1) {  // the next link's joint inputs
       const int jn = __ldg(r.jidx + __ldg(r.dfs + pos + 1).x);
-      if (jn >= 0) {
-        pf(A.q + (int64_t)jn * B + b);
-        if (dyn) {
-          pf(A.qd + (int64_t)jn * B + b);
-          pf(A.qdd + (int64_t)jn * B + b);
-        }
-      }
+      if (jn >= 0) st.prefetch(jn, dyn);
     }
     if (dyn) {
       while (sp > dep) close(--sp);
@@ -313,7 +348,7 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
 }
 
 __device__ __forceinline__ void tree_fwd_one(const DevRobot& r, const FwdArgs& A, int64_t b) {
-  tree_fwd_seg(r, A, b, whole_sweep(r));
+  tree_fwd_seg(r, A, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b, whole_sweep(r));
 }
 
 // ---------------------------------------------------------------------------
@@ -339,12 +374,12 @@ struct BEnt {
 };
 
 // world pose of link l by composing its ancestor chain (topology cache)
-__device__ __forceinline__ void chain_pose(const DevRobot& r, int l, const float* q, int64_t B,
-                                           int64_t b, float* P) {
+template <class St>
+__device__ __forceinline__ void chain_pose(const DevRobot& r, int l, const St& st, float* P) {
   const int c0 = __ldg(r.chain_start + l), c1 = __ldg(r.chain_start + l + 1);
   for (int c = c0; c < c1; ++c) {
     float L[12];
-    link_local(r, __ldg(r.chain + c), q, B, b, L);
+    link_local(r, __ldg(r.chain + c), st, L);
     if (c == c0) {
 #pragma unroll
       for (int i = 0; i < 12; ++i) P[i] = L[i];
@@ -378,9 +413,10 @@ __device__ __forceinline__ void point_wrench(const float* R, float4 sp, const fl
 // shares).  Needs one link per joint (no shared mimic joints).
 // FC: compiled with the fused cost (a separate instantiation, so that the
 // plain sweep keeps its register allocation).
-template <bool FC>
+template <bool FC, class St>
 __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& A,
-                                              const FusedCost& fc, int64_t b, const Seg& sg) {
+                                              const FusedCost& fc, const St& st, int64_t b,
+                                              const Seg& sg) {
   const int64_t B = A.B;
   float cost_part = 0.0f;
   const int n = r.n;
@@ -412,8 +448,8 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
         pl1 = l1;
         pl2 = l2;
         float P1[12], P2[12], c1[3], c2[3];
-        chain_pose(r, pl1, A.q, B, b, P1);
-        chain_pose(r, pl2, A.q, B, b, P2);
+        chain_pose(r, pl1, st, P1);
+        chain_pose(r, pl2, st, P2);
         const float4 s1 = __ldg(r.sph + ps1), s2 = __ldg(r.sph + ps2);
         const float q1[3] = {s1.x, s1.y, s1.z}, q2[3] = {s2.x, s2.y, s2.z};
         rot(P1, q1, c1);
@@ -525,9 +561,9 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
     float S[6];
     motion_S6t(jt, ax, S);
     const float mm = __ldg(reinterpret_cast<const float2*>(r.mimic) + k).x;
-    const float vq = j >= 0 ? mm * __ldg(A.qd + (int64_t)j * B + b) : 0.0f;
+    const float vq = j >= 0 ? mm * st.vel(j) : 0.0f;
     float L[12];
-    link_local(r, k, A.q, B, b, L);
+    link_local(r, k, st, L);
     float XF[6], vp[6], ap[6], Fbp[6];  // X_k Fbar_pa, and the parent's v, a, Fbar
     if (e > 0) {
       const BEnt& P = stk[e - 1];
@@ -567,7 +603,7 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
       float dqd = 0.0f, dqdd = 0.0f;  // the cost's direct gradients, once per joint
       if (!((replayed >> e) & 1u)) {
         const int64_t at = (int64_t)j * B + b;
-        const float tj = __ldg(fc.tau + at), vj = __ldg(A.qd + at), aj = __ldg(A.qdd + at);
+        const float tj = __ldg(fc.tau + at), vj = st.vel(j), aj = st.acc(j);
         dqd = 2.0f * (fc.length * vj + fc.e * (vj * tj) * tj);
         dqdd = 2.0f * fc.smooth * aj;
       }
@@ -645,7 +681,7 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
   auto push = [&](int k, int dep, bool own) {
     BEnt& E = stk[dep];
     float L[12];
-    link_local(r, k, A.q, B, b, L);
+    link_local(r, k, st, L);
     float PW[12], vp[6], ap[6], Fbp[6];
     if (dep > 0) {
       if (dep == cdep + 1) {
@@ -690,8 +726,8 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
     const float4 a4 = __ldg(reinterpret_cast<const float4*>(r.axis) + k);
     const float ax[3] = {a4.x, a4.y, a4.z};
     const float mm = __ldg(reinterpret_cast<const float2*>(r.mimic) + k).x;
-    const float vq = j >= 0 ? mm * __ldg(A.qd + (int64_t)j * B + b) : 0.0f;
-    const float aq = j >= 0 ? mm * __ldg(A.qdd + (int64_t)j * B + b) : 0.0f;
+    const float vq = j >= 0 ? mm * st.vel(j) : 0.0f;
+    const float aq = j >= 0 ? mm * st.acc(j) : 0.0f;
     // dynamics forward: v, a
     rnea_va(L, L + 9, vp, ap, jt, ax, vq, aq, cv, ca);
     // adjoint of the force sweep: Fbar_k = S m taubar + X Fbar_pa
@@ -701,7 +737,7 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
     if (FC && j >= 0) {  // the cost's torque gradient, as the cost kernel forms it
       const float t = __ldg(fc.tau + (int64_t)j * B + b), l = __ldg(fc.lo + j),
                   h = __ldg(fc.hi + j);
-      const float v = __ldg(A.qd + (int64_t)j * B + b), a = __ldg(A.qdd + (int64_t)j * B + b);
+      const float v = st.vel(j), a = st.acc(j);
       const float vt = v * t;
       float gt = 2.0f * fc.e * v * vt;
       gt += (t > h ? 1.0f : 0.0f) - (t < l ? 1.0f : 0.0f);
@@ -791,9 +827,7 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
       const int kn = __ldg(r.dfs + pos + 1).x;
       const int jn = __ldg(r.jidx + kn);
       if (jn >= 0) {
-        pf(A.q + (int64_t)jn * B + b);
-        pf(A.qd + (int64_t)jn * B + b);
-        pf(A.qdd + (int64_t)jn * B + b);
+        st.prefetch(jn, true);
         if (A.g_tau) pf(A.g_tau + (int64_t)jn * B + b);
         if (FC) pf(fc.tau + (int64_t)jn * B + b);
       }
@@ -823,12 +857,14 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
 // the whole sweep of one configuration; with a fused cost it also writes the
 // configuration's cost (joint terms, then the collision term)
 __device__ __forceinline__ void tree_bwd_one(const DevRobot& r, const BwdArgs& A, int64_t b) {
-  tree_bwd_seg<false>(r, A, FusedCost{}, b, whole_sweep(r));
+  tree_bwd_seg<false>(r, A, FusedCost{}, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b,
+                      whole_sweep(r));
 }
 
+template <class St>
 __device__ __forceinline__ void tree_bwd_cost_one(const DevRobot& r, const BwdArgs& A,
-                                                  const FusedCost& fc, int64_t b) {
-  const float c = tree_bwd_seg<true>(r, A, fc, b, whole_sweep(r));
+                                                  const FusedCost& fc, const St& st, int64_t b) {
+  const float c = tree_bwd_seg<true>(r, A, fc, st, b, whole_sweep(r));
   if (fc.cost) fc.cost[b] = fc.d_min ? fmaf(fc.w, fmaxf(0.0f, -__ldg(fc.d_min + b)), c) : c;
 }
 

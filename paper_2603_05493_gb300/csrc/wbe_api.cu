@@ -1223,6 +1223,138 @@ int wb_eval_backward_ext(wb_robot* robot, int64_t B, const float* q, const float
   return WB_OK;
 }
 
+// the spline source of the _spline entry points: validated, on the robot's device
+static int check_spline_src(const wb_robot* robot, const wb_spline* sp, SplineArgs* out,
+                            int64_t* B) {
+  if (!sp) return fail(WB_EINVAL, "spline is NULL");
+  if (sp->n_traj < 0) return fail(WB_EINVAL, "n_traj < 0");
+  if (sp->K < 4 || sp->K > 4096)
+    return fail(WB_EINVAL, "K = %d outside [4, 4096] (a cubic B-spline needs 4 control points)",
+                sp->K);
+  if (sp->T < 2 || sp->T > 4096) return fail(WB_EINVAL, "T = %d outside [2, 4096]", sp->T);
+  if (!(sp->dt > 0.0f) || !std::isfinite(sp->dt)) return fail(WB_EINVAL, "dt must be positive");
+  if (sp->n_traj * sp->T > ((int64_t)1 << 40)) return fail(WB_EINVAL, "too many samples");
+  int rc;
+  if ((rc = check_ptr(robot, sp->U, "U", sp->n_traj > 0))) return rc;
+  out->U = sp->U;
+  out->K = sp->K;
+  out->T = sp->T;
+  out->dt = sp->dt;
+  *B = sp->n_traj * sp->T;
+  return WB_OK;
+}
+
+int wb_eval_spline(wb_robot* robot, const wb_spline* spline, float* link_pose, float* sphere,
+                   float* d_min, int32_t* worst_pair, float* tau, const wb_tune* tune,
+                   void* stream) {
+  g_err.clear();
+  if (!robot) return fail(WB_EINVAL, "robot is NULL");
+  SplineArgs sp;
+  int64_t B = 0;
+  int rc;
+  if ((rc = check_spline_src(robot, spline, &sp, &B))) return rc;
+  if (B == 0) return WB_OK;
+  const bool pairs_wanted = d_min || sphere;
+  if (pairs_wanted && !link_pose) return fail(WB_EINVAL, "spheres or pairs need link_pose");
+  if (d_min && !worst_pair) return fail(WB_EINVAL, "d_min without worst_pair");
+  if ((rc = check_ptr(robot, link_pose, "link_pose", false))) return rc;
+  if ((rc = check_ptr(robot, sphere, "sphere", false))) return rc;
+  if ((rc = check_ptr(robot, d_min, "d_min", false))) return rc;
+  if ((rc = check_ptr(robot, worst_pair, "worst_pair", false))) return rc;
+  if ((rc = check_ptr(robot, tau, "tau", false))) return rc;
+  int kernel = tune ? tune->kernel : WB_KERNEL_AUTO;
+  if (kernel != WB_KERNEL_AUTO && kernel != WB_KERNEL_TREE && kernel != WB_KERNEL_TREE_NOCULL)
+    return fail(WB_EINVAL, "the spline sweeps are tree kernels (kernel AUTO, TREE or TREE_NOCULL)");
+  if (robot->dev.maxdepth > tree_max_depth())
+    return fail(WB_ETOOBIG, "tree deeper than %d levels", tree_max_depth());
+  DeviceGuard guard(robot->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  FwdArgs a{B, nullptr, nullptr, nullptr, link_pose, sphere, d_min, worst_pair, tau, nullptr};
+  const int tpb = (tune && tune->configs_per_block) ? tune->configs_per_block : 128;
+  if (tpb < 32 || tpb > 256 || tpb % 32)
+    return fail(WB_EINVAL, "tree threads per block must be a multiple of 32 in [32, 256]");
+  int G = 1;
+  if ((rc = tree_segments(robot, tune, B, tpb, true, &G))) return rc;
+  cudaError_t e = launch_tree_fwd_spline(robot->dev, a, sp, tpb, G, s);
+  if (e == cudaSuccess && pairs_wanted) {
+    const int warps = pair_warps(robot->dev, false, tune);
+    if (warps < 1 || warps > 8) return fail(WB_ETOOBIG, "pair kernel does not fit on an SM");
+    int bps = 0;
+    e = pair_max_blocks_per_sm(robot->dev, warps, false, &bps);
+    if (e == cudaSuccess) {
+      if (bps < 1) return fail(WB_ETOOBIG, "pair kernel does not fit on an SM");
+      const int64_t need = (B + warps - 1) / warps;
+      const int grid = (int)std::min<int64_t>(need, (int64_t)bps * robot->num_sms);
+      e = launch_pair(robot->dev, robot->sched32, a, grid, warps, s,
+                      kernel != WB_KERNEL_TREE_NOCULL);
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "wb_eval_spline launch");
+  return WB_OK;
+}
+
+int wb_eval_backward_spline_cost(wb_robot* robot, const wb_spline* spline,
+                                 const int32_t* worst_pair, const float* g_pose,
+                                 const float* g_sphere, const float* tau, const float* d_min,
+                                 const float* tau_lo, const float* tau_hi,
+                                 const wb_cost_weights* w, float* cost, float* gq, float* gqd,
+                                 float* gqdd, const wb_tune* tune, void* stream) {
+  g_err.clear();
+  if (!robot) return fail(WB_EINVAL, "robot is NULL");
+  if (!w) return fail(WB_EINVAL, "weights are NULL");
+  const wb_cost_weights W = *w;
+  if (!std::isfinite(W.collision) || !std::isfinite(W.smooth) || !std::isfinite(W.length) ||
+      !std::isfinite(W.energy) || !std::isfinite(W.dt) || !(W.dt > 0.0f) ||
+      !std::isfinite(W.energy * W.dt * W.dt))
+    return fail(WB_EINVAL, "weights must be finite and dt > 0");
+  SplineArgs sp;
+  int64_t B = 0;
+  int rc;
+  if ((rc = check_spline_src(robot, spline, &sp, &B))) return rc;
+  if (B == 0) return WB_OK;
+  if (robot->dev.mimic_shared)
+    return fail(WB_EINVAL, "the fused cost needs one link per joint (no shared mimic joints)");
+  if ((rc = check_ptr(robot, tau, "tau", true))) return rc;
+  if ((rc = check_ptr(robot, tau_lo, "tau_lo", true))) return rc;
+  if ((rc = check_ptr(robot, tau_hi, "tau_hi", true))) return rc;
+  if ((rc = check_ptr(robot, d_min, "d_min", false))) return rc;
+  if ((rc = check_ptr(robot, worst_pair, "worst_pair", d_min != nullptr))) return rc;
+  if ((rc = check_ptr(robot, g_pose, "g_pose", false))) return rc;
+  if ((rc = check_ptr(robot, g_sphere, "g_sphere", false))) return rc;
+  if ((rc = check_ptr(robot, cost, "cost", false))) return rc;
+  if ((rc = check_ptr(robot, gq, "gq", true))) return rc;
+  if ((rc = check_ptr(robot, gqd, "gqd", true))) return rc;
+  if ((rc = check_ptr(robot, gqdd, "gqdd", true))) return rc;
+  int kernel = tune ? tune->kernel : WB_KERNEL_AUTO;
+  if (kernel == WB_KERNEL_TREE_NOCULL) kernel = WB_KERNEL_TREE;
+  if (kernel != WB_KERNEL_AUTO && kernel != WB_KERNEL_TREE)
+    return fail(WB_EINVAL, "the fused cost runs in the tree kernels (kernel AUTO or TREE)");
+  if (robot->dev.maxdepth > tree_max_depth())
+    return fail(WB_ETOOBIG, "tree deeper than %d levels", tree_max_depth());
+  DeviceGuard guard(robot->device);
+  BwdArgs a{B, nullptr, nullptr, nullptr, worst_pair, g_pose, g_sphere, nullptr, nullptr,
+            gq, gqd, gqdd};
+  FusedCost fc;
+  fc.tau = tau;
+  fc.d_min = d_min;
+  fc.lo = tau_lo;
+  fc.hi = tau_hi;
+  fc.w = W.collision;
+  fc.smooth = W.smooth;
+  fc.length = W.length;
+  fc.e = W.energy * W.dt * W.dt;
+  fc.cost = cost;
+  const int tpb = (tune && tune->configs_per_block) ? tune->configs_per_block : 128;
+  if (tpb < 32 || tpb > 256 || tpb % 32)
+    return fail(WB_EINVAL, "tree threads per block must be a multiple of 32 in [32, 256]");
+  int G = 1;
+  if ((rc = tree_segments(robot, tune, B, tpb, false, &G))) return rc;
+  const cudaError_t e = launch_tree_bwd_spline_cost(robot->dev, a, fc, sp, tpb, G,
+                                                    static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "wb_eval_backward_spline_cost launch");
+  return WB_OK;
+}
+
 int wb_eval_backward_cost(wb_robot* robot, int64_t B, const float* q, const float* qd,
                           const float* qdd, const int32_t* worst_pair, const float* g_pose,
                           const float* g_sphere, const float* tau, const float* d_min,

@@ -129,6 +129,14 @@ struct FusedCost {
   float* cost = nullptr;         // [B] out, or nullptr
 };
 
+// Joint states from uniform cubic B-spline control points U [n_traj][d][K]:
+// configuration b is sample b mod T of trajectory b / T (Sec. 4).
+struct SplineArgs {
+  const float* U = nullptr;
+  int K = 0, T = 0;
+  float dt = 0.0f;
+};
+
 struct BwdArgs {
   int64_t B;
   const float* q;
@@ -266,6 +274,12 @@ cudaError_t launch_tree_fwd(const DevRobot& r, const FwdArgs& a, int threads, in
                             cudaStream_t s);
 cudaError_t launch_tree_bwd(const DevRobot& r, const BwdArgs& a, int threads, int segments,
                             cudaStream_t s, const FusedCost* fc = nullptr);
+// the sweeps with the joint states evaluated from control points
+cudaError_t launch_tree_fwd_spline(const DevRobot& r, const FwdArgs& a, const SplineArgs& sp,
+                                   int threads, int segments, cudaStream_t s);
+cudaError_t launch_tree_bwd_spline_cost(const DevRobot& r, const BwdArgs& a, const FusedCost& fc,
+                                        const SplineArgs& sp, int threads, int segments,
+                                        cudaStream_t s);
 size_t tree_seg_smem(const DevRobot& r, int segments, int threads, bool fwd, bool cost = false);
 int tree_max_depth();
 size_t pair_smem(const DevRobot& r, int warps, bool bits);

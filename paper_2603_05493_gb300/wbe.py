@@ -266,6 +266,49 @@ class Robot:
                 "wb_eval_backward")
         return gq, gqd, gqdd
 
+    def _spline(self, U, T: int, dt: float):
+        n_traj, d, K = U.shape
+        return L.wb_spline(U.data_ptr(), int(n_traj), int(K), int(T), float(dt)), int(n_traj) * int(T)
+
+    def eval_spline(self, U, T: int, dt: float, *, pose=True, sphere=True, dmin=True, tau=True,
+                    tune: Tune | None = None, out=None, stream=None):
+        """Forward evaluation with the joint states evaluated from B-spline
+        control points U [n_traj][d][K] inside the sweep (wb_eval_spline);
+        returns the output dict of eval (no pair bits)."""
+        sp, B = self._spline(U, T, dt)
+        o = out if out is not None else self.empty_outputs(B, pose, sphere, dmin, tau, False)
+        t = (tune or Tune()).c()
+        L.check(self.lib.wb_eval_spline(self.handle, C.byref(sp), _ptr(o.get("pose")),
+                                        _ptr(o.get("sphere")), _ptr(o.get("dmin")),
+                                        _ptr(o.get("worst")), _ptr(o.get("tau")), C.byref(t),
+                                        _stream(stream)), "wb_eval_spline")
+        return o
+
+    def eval_backward_spline_cost(self, U, T: int, dt: float, tau, tau_lo, tau_hi,
+                                  w_coll: float, smooth: float = 0.0, length: float = 0.0,
+                                  energy: float = 0.0, dt_cost: float = 1.0, *, d_min=None,
+                                  worst=None, g_pose=None, g_sphere=None, cost=None,
+                                  want_cost: bool = True, tune: Tune | None = None, out=None,
+                                  stream=None):
+        """eval_backward_cost with the joint states evaluated from control
+        points (wb_eval_backward_spline_cost).  dt_cost is the energy term's
+        dt.  Returns (gq, gqd, gqdd, cost)."""
+        sp, B = self._spline(U, T, dt)
+        if out is None:
+            out = tuple(torch.empty((self.dof, B), device=self.device, dtype=torch.float32)
+                        for _ in range(3))
+        gq, gqd, gqdd = out
+        if cost is None and want_cost:
+            cost = torch.empty((B,), device=self.device, dtype=torch.float32)
+        w = L.wb_cost_weights(float(w_coll), float(smooth), float(length), float(energy),
+                              float(dt_cost))
+        t = (tune or Tune()).c()
+        L.check(self.lib.wb_eval_backward_spline_cost(
+            self.handle, C.byref(sp), _ptr(worst), _ptr(g_pose), _ptr(g_sphere), _ptr(tau),
+            _ptr(d_min), _ptr(tau_lo), _ptr(tau_hi), C.byref(w), _ptr(cost), _ptr(gq),
+            _ptr(gqd), _ptr(gqdd), C.byref(t), _stream(stream)), "wb_eval_backward_spline_cost")
+        return gq, gqd, gqdd, cost
+
     def eval_backward_cost(self, q, qd, qdd, tau, tau_lo, tau_hi, w_coll: float,
                            smooth: float = 0.0, length: float = 0.0, energy: float = 0.0,
                            dt: float = 1.0, *, d_min=None, worst=None, g_pose=None,

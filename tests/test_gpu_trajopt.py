@@ -482,3 +482,81 @@ def test_trajopt48_full_size_fused_cost_sampled(W, O):
     trajs = [0, 257, n_traj - 1]
     kept = _compare_chain(O, desc, U[trajs], T, dt, lim, w, gU, cost, o, trajs, motion)
     assert kept >= 2
+
+
+@pytest.mark.parametrize("G", [1, 2, 4])
+@pytest.mark.parametrize("kin", [False, True])
+def test_spline_sourced_sweeps_equal_the_two_step_path(W, G, kin):
+    """The sweeps with the joint states evaluated from control points
+    (wb_eval_spline, wb_eval_backward_spline_cost) against wb_bspline_eval
+    followed by wb_eval and wb_eval_backward_cost: the states are the same
+    bits, so every output is too, for every sweep segment count."""
+    desc = I.hand_payload(R.r48())
+    rob = W.Robot(desc, device=0)
+    n_traj, K, T, dt = 5, 16, 45, 0.25  # 225 configurations: a ragged tail
+    U = cuda(I.bspline_controls(desc.dof, n_traj, K, seed=PY.stable_seed("spl", G)))
+    tune = W.Tune(kernel=3, lanes_per_config=G)
+    q, qd, qdd = W.bspline_eval(U, T, dt)
+    a = rob.eval(q, qd, qdd, tune=tune)
+    b = rob.eval_spline(U, T, dt, tune=tune)
+    torch.cuda.synchronize()
+    for k in ("pose", "sphere", "dmin", "worst", "tau"):
+        assert torch.equal(a[k], b[k]), k
+    lim = CF.TORQUE_LIMIT
+    lo, hi = cuda(-lim * np.ones(desc.dof)), cuda(lim * np.ones(desc.dof))
+    motion = dict(smooth=CF.SMOOTH_WEIGHT, length=CF.LENGTH_WEIGHT, energy=CF.ENERGY_WEIGHT)
+    gp, gs, _, _ = I.upstream_grads(desc, n_traj * T, seed=31)
+    gp, gs = (cuda(gp), cuda(gs)) if kin else (None, None)
+    dtc = dt * (K - 3) / (T - 1)
+    ga = rob.eval_backward_cost(q, qd, qdd, a["tau"], lo, hi, 1.0, dt=dtc, d_min=a["dmin"],
+                                worst=a["worst"], g_pose=gp, g_sphere=gs, tune=tune, **motion)
+    gb = rob.eval_backward_spline_cost(U, T, dt, b["tau"], lo, hi, 1.0, dt_cost=dtc,
+                                       d_min=b["dmin"], worst=b["worst"], g_pose=gp, g_sphere=gs,
+                                       tune=tune, **motion)
+    torch.cuda.synchronize()
+    for x, y in zip(ga, gb):
+        assert torch.equal(x, y)
+
+
+def test_trajopt48_full_size_spline_sampled(W, O):
+    """The full 512 x 64 launch as the bench runs it: states from control
+    points inside the sweeps, the cost in the backward's prologue, autotuned
+    shapes; three trajectories against the oracle."""
+    desc = I.hand_payload(R.r48())
+    rob = W.Robot(desc, device=0)
+    n_traj, K, T, dt = CF.TRAJOPT_SEEDS, CF.TRAJOPT_KNOTS, CF.TRAJOPT_STEPS, CF.TRAJOPT_DT
+    ft, bt, _, _ = rob.autotune(n_traj * T)
+    U = I.bspline_controls(desc.dof, n_traj, K, seed=CF.TRAJOPT48.seed)
+    lim, w = CF.TORQUE_LIMIT, CF.COLLISION_WEIGHT
+    motion = dict(smooth=CF.SMOOTH_WEIGHT, length=CF.LENGTH_WEIGHT, energy=CF.ENERGY_WEIGHT)
+    lo, hi = cuda(-lim * np.ones(desc.dof)), cuda(lim * np.ones(desc.dof))
+    tree = lambda t: W.Tune(kernel=3, lanes_per_config=t.lanes_per_config if t.kernel == 3 else 0,  # noqa: E731
+                            configs_per_block=t.configs_per_block if t.kernel == 3 else 0)
+    Ud = cuda(U)
+    o = rob.eval_spline(Ud, T, dt, tune=tree(ft))
+    gq, gqd, gqdd, cost = rob.eval_backward_spline_cost(
+        Ud, T, dt, o["tau"], lo, hi, w, dt_cost=dt * (K - 3) / (T - 1), d_min=o["dmin"],
+        worst=o["worst"], tune=tree(bt), **motion)
+    gU = W.bspline_backward(gq, gqd, gqdd, n_traj, K, T, dt)
+    torch.cuda.synchronize()
+    assert torch.isfinite(gU).all() and torch.isfinite(cost).all()
+    trajs = [0, 300, n_traj - 1]
+    kept = _compare_chain(O, desc, U[trajs], T, dt, lim, w, gU, cost, o, trajs, motion)
+    assert kept >= 2
+
+
+def test_spline_sourced_refusals(W):
+    from paper_2603_05493_gb300 import _lib as L
+    desc = R.r7()
+    rob = W.Robot(desc, device=0)
+    U3 = torch.zeros((2, desc.dof, 3), device="cuda")
+    with pytest.raises(L.WbError) as e:  # 3 control points
+        rob.eval_spline(U3, 8, 0.1)
+    assert e.value.code == L.WB_EINVAL
+    U = torch.zeros((2, desc.dof, 6), device="cuda")
+    with pytest.raises(L.WbError) as e:
+        rob.eval_spline(U, 8, 0.1, tune=W.PLAIN)
+    assert e.value.code == L.WB_EINVAL
+    o = rob.eval_spline(U, 8, 0.1, sphere=False, dmin=False)
+    torch.cuda.synchronize()
+    assert torch.isfinite(o["tau"]).all()
