@@ -63,12 +63,12 @@ TREE_SRC = ["paper_2603_05493_gb300/csrc/k_tree.cu", "paper_2603_05493_gb300/csr
 PAIR_SRC = ["paper_2603_05493_gb300/csrc/k_pair.cu", "paper_2603_05493_gb300/csrc/pair_body.cuh",
             "paper_2603_05493_gb300/csrc/spatial.cuh"]
 MEASURED_TRAFFIC = {  # profiles/humanoid48_kernel_traffic.md
-    "tree_fwd": {"src": TREE_SRC, "sha256": "cb2b92d8bba0b7342ec8f2363659b9e3fea5344d0f6c6c38be2eb803b88952ca",
-                 "bytes_per_eval": (17.06e6 + 41.60e6) / 24576},
+    "tree_fwd": {"src": TREE_SRC, "sha256": "9a29546cb6200045ddfb0fa80d0ee152c58dc7934a6cc17805ee0f96ac738f98",
+                 "bytes_per_eval": (17.05e6 + 41.67e6) / 24576},
     "pair": {"src": PAIR_SRC, "sha256": "1b13086cd2699f0b277577a854f835d9ca425fc9ac020564113acfaecdc67567",
-             "bytes_per_eval": (59.60e6 + 21.14e6) / 24576},
-    "tree_bwd": {"src": TREE_SRC, "sha256": "cb2b92d8bba0b7342ec8f2363659b9e3fea5344d0f6c6c38be2eb803b88952ca",
-                 "bytes_per_eval": (213.75e6 + 94.27e6) / 24576},
+             "bytes_per_eval": (59.62e6 + 21.09e6) / 24576},
+    "tree_bwd": {"src": TREE_SRC, "sha256": "9a29546cb6200045ddfb0fa80d0ee152c58dc7934a6cc17805ee0f96ac738f98",
+                 "bytes_per_eval": (213.86e6 + 94.04e6) / 24576},
 }
 
 
