@@ -59,15 +59,15 @@ def work_per_eval(desc):
 # the hash of the sources that kernel is built from: a changed source makes the
 # figure stale, and it is reported as null until captured again.
 TREE_SRC = ["paper_2603_05493_gb300/csrc/k_tree.cu", "paper_2603_05493_gb300/csrc/tree_sweep.cuh",
-            "paper_2603_05493_gb300/csrc/spatial.cuh"]
+            "paper_2603_05493_gb300/csrc/spatial.cuh", "paper_2603_05493_gb300/csrc/spline_basis.cuh"]
 PAIR_SRC = ["paper_2603_05493_gb300/csrc/k_pair.cu", "paper_2603_05493_gb300/csrc/pair_body.cuh",
             "paper_2603_05493_gb300/csrc/spatial.cuh"]
 MEASURED_TRAFFIC = {  # profiles/humanoid48_kernel_traffic.md
-    "tree_fwd": {"src": TREE_SRC, "sha256": "9a29546cb6200045ddfb0fa80d0ee152c58dc7934a6cc17805ee0f96ac738f98",
+    "tree_fwd": {"src": TREE_SRC, "sha256": "ebbc6eb0cba46e934189b25b09314ae0f9cec05a31e5b2391a856d073a71733f",
                  "bytes_per_eval": (17.05e6 + 41.67e6) / 24576},
     "pair": {"src": PAIR_SRC, "sha256": "1b13086cd2699f0b277577a854f835d9ca425fc9ac020564113acfaecdc67567",
              "bytes_per_eval": (59.62e6 + 21.09e6) / 24576},
-    "tree_bwd": {"src": TREE_SRC, "sha256": "9a29546cb6200045ddfb0fa80d0ee152c58dc7934a6cc17805ee0f96ac738f98",
+    "tree_bwd": {"src": TREE_SRC, "sha256": "ebbc6eb0cba46e934189b25b09314ae0f9cec05a31e5b2391a856d073a71733f",
                  "bytes_per_eval": (213.86e6 + 94.04e6) / 24576},
 }
 
