@@ -63,12 +63,12 @@ TREE_SRC = ["paper_2603_05493_gb300/csrc/k_tree.cu", "paper_2603_05493_gb300/csr
 PAIR_SRC = ["paper_2603_05493_gb300/csrc/k_pair.cu", "paper_2603_05493_gb300/csrc/pair_body.cuh",
             "paper_2603_05493_gb300/csrc/spatial.cuh"]
 MEASURED_TRAFFIC = {  # profiles/humanoid48_kernel_traffic.md
-    "tree_fwd": {"src": TREE_SRC, "sha256": "ebbc6eb0cba46e934189b25b09314ae0f9cec05a31e5b2391a856d073a71733f",
-                 "bytes_per_eval": (17.05e6 + 41.67e6) / 24576},
+    "tree_fwd": {"src": TREE_SRC, "sha256": "bbb3c684f90e677446f70efdea5abea535395149c3113a7965139f4790dcd361",
+                 "bytes_per_eval": (17.13e6 + 42.01e6) / 24576},
     "pair": {"src": PAIR_SRC, "sha256": "1b13086cd2699f0b277577a854f835d9ca425fc9ac020564113acfaecdc67567",
-             "bytes_per_eval": (59.62e6 + 21.09e6) / 24576},
-    "tree_bwd": {"src": TREE_SRC, "sha256": "ebbc6eb0cba46e934189b25b09314ae0f9cec05a31e5b2391a856d073a71733f",
-                 "bytes_per_eval": (213.86e6 + 94.04e6) / 24576},
+             "bytes_per_eval": (59.68e6 + 21.17e6) / 24576},
+    "tree_bwd": {"src": TREE_SRC, "sha256": "bbb3c684f90e677446f70efdea5abea535395149c3113a7965139f4790dcd361",
+                 "bytes_per_eval": (214.81e6 + 94.50e6) / 24576},
 }
 
 
@@ -86,6 +86,21 @@ def traffic_per_eval(name):
     if not t or not t["sha256"] or source_hash(t["src"]) != t["sha256"]:
         return None
     return t["bytes_per_eval"]
+
+
+def sweep_shapes(rob, B, args):
+    """Forward and backward sweep launch shapes: the library's autotuner at
+    batch B, or the ones --sweep-shape pins (segments and configurations per
+    block of each sweep), so that a profiler run, whose slowed launches would
+    sway the autotuner, times the same launches as the plain run."""
+    from paper_2603_05493_gb300 import wbe
+    if not args.sweep_shape:
+        ft, bt, _, _ = rob.autotune(B)
+        return ft, bt
+    fs, fc, bs, bc = (int(x) for x in args.sweep_shape.split(","))
+    mk = lambda g, c: wbe.Tune(kernel=wbe.L.WB_KERNEL_TREE, lanes_per_config=g,  # noqa: E731
+                               configs_per_block=c)
+    return mk(fs, fc), mk(bs, bc)
 
 
 # ---------------------------------------------------------------------------
@@ -273,7 +288,7 @@ def run_ours(args, rank, world, local_rank):
     if args.kernel == "tree":
         # sweep launch shape (segments, threads per block) from the library's
         # autotuner at this batch size
-        ft, bt, fms, bms = rob.autotune(B)
+        ft, bt = sweep_shapes(rob, B, args)
         seg = lambda t: t.lanes_per_config if t.kernel == wbe.L.WB_KERNEL_TREE else 0  # noqa
         tpb = lambda t: t.configs_per_block if t.kernel == wbe.L.WB_KERNEL_TREE else 0  # noqa
         tune = wbe.Tune(kernel=wbe.L.WB_KERNEL_TREE, lanes_per_config=seg(ft),
@@ -528,7 +543,7 @@ def run_trajopt(args, rank=0, world=1, local_rank=0):
     rob = wbe.Robot(desc, device=local_rank)
     n_traj, K, T, dt = CF.TRAJOPT_SEEDS, CF.TRAJOPT_KNOTS, CF.TRAJOPT_STEPS, CF.TRAJOPT_DT
     B, d = n_traj * T, desc.dof
-    ft, bt, _, _ = rob.autotune(B)
+    ft, bt = sweep_shapes(rob, B, args)
     seg = lambda t: t.lanes_per_config if t.kernel == wbe.L.WB_KERNEL_TREE else 0  # noqa
     tpb = lambda t: t.configs_per_block if t.kernel == wbe.L.WB_KERNEL_TREE else 0  # noqa
     ftune = wbe.Tune(kernel=wbe.L.WB_KERNEL_TREE, lanes_per_config=seg(ft),
@@ -862,6 +877,9 @@ def main():
                     default="humanoid48")
     ap.add_argument("--collision", choices=["worst", "hinge"], default="worst",
                     help="trajopt48 collision cost: worst-pair hinge or summed hinge")
+    ap.add_argument("--sweep-shape", default="",
+                    help="pin the sweep launch shapes instead of autotuning: "
+                         "fwd segments,fwd configs per block,bwd segments,bwd configs per block")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

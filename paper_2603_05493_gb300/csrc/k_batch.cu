@@ -195,6 +195,7 @@ cudaError_t launch_batch_tree_fwd(const DevRobot* robots, const BatchProblemDev*
   cudaError_t e = cudaFuncSetAttribute(batch_tree_fwd_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  fit_carveout((const void*)batch_tree_fwd_kernel, 128, smem);
   e = cudaMemsetAsync(counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   batch_tree_fwd_kernel<<<grid, 128, smem, s>>>(robots, probs, items, n_items, counter, io,
@@ -209,6 +210,7 @@ cudaError_t launch_batch_tree_bwd(const DevRobot* robots, const BatchProblemDev*
   cudaError_t e = cudaFuncSetAttribute(batch_tree_bwd_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  fit_carveout((const void*)batch_tree_bwd_kernel, 128, smem);
   e = cudaMemsetAsync(counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   batch_tree_bwd_kernel<<<grid, 128, smem, s>>>(robots, probs, items, n_items, counter, io,

@@ -240,6 +240,39 @@ static void prefer_l1() {
   }
 }
 
+// Shared memory and L1 are one array per SM.  Without a preference the
+// driver gave the segmented sweeps, whose blocks hold 14-22 KB of partials, a
+// 132 KB shared carveout (measured), and the L1 that caches their depth-first
+// stacks shrank to match.  fit_carveout asks for the smallest carveout that
+// still holds every block the registers, warps and block limit let one SM
+// keep (a hint: the driver rounds it up to a carveout it supports).
+void fit_carveout(const void* kern, int threads, size_t smem) {
+  static int smem_sm = 0, regs_sm = 0, threads_sm = 0, blocks_sm = 0, reserved = 0;
+  if (!smem_sm) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    if (cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) ||
+        cudaDeviceGetAttribute(&threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) ||
+        cudaDeviceGetAttribute(&blocks_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev) ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) {
+      smem_sm = 0;
+      return;
+    }
+  }
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return;
+  const int warps = (threads + 31) / 32;
+  const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;  // 256-register allocation unit
+  int nb = std::min(threads_sm / (32 * warps), blocks_sm);
+  if (regs_warp > 0) nb = std::min(nb, (regs_sm / regs_warp) / warps);
+  const size_t per = smem + fa.sharedSizeBytes + (size_t)reserved;
+  nb = std::min<int>(nb, (int)((size_t)smem_sm / per));
+  const size_t need = (size_t)std::max(nb, 1) * per;
+  const int pct = (int)std::min<size_t>(100, (need * 100 + smem_sm - 1) / smem_sm);
+  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+}
+
 static int seg_plan(int segments) { return segments == 2 ? 0 : segments == 4 ? 1 : 2; }
 static int seg_groups(int segments, int threads) { return std::max(1, threads / (32 * segments)); }
 
@@ -262,6 +295,7 @@ static cudaError_t launch_seg(void (*kern)(DevRobot, Args, int), const DevRobot&
   cudaError_t e =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  fit_carveout((const void*)kern, 32 * segments * CG, smem);
   const int64_t groups = (a.B + 31) / 32;
   const int64_t grid = (groups + CG - 1) / CG;
   kern<<<(unsigned)grid, 32 * segments * CG, smem, s>>>(r, a, t);
@@ -276,6 +310,7 @@ static cudaError_t launch_cost_seg(const DevRobot& r, const BwdArgs& a, const Fu
   cudaError_t e = cudaFuncSetAttribute(tree_bwd_cost_seg_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  fit_carveout((const void*)tree_bwd_cost_seg_kernel, 32 * segments * CG, smem);
   const int64_t groups = (a.B + 31) / 32;
   const int64_t grid = (groups + CG - 1) / CG;
   tree_bwd_cost_seg_kernel<<<(unsigned)grid, 32 * segments * CG, smem, s>>>(r, a, fc, t);
@@ -318,11 +353,13 @@ cudaError_t launch_tree_fwd_spline(const DevRobot& r, const FwdArgs& a, const Sp
     cudaError_t e = cudaFuncSetAttribute(tree_fwd_spline_seg_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    fit_carveout((const void*)tree_fwd_spline_seg_kernel, block, smem);
     const int64_t grid = ((a.B + 31) / 32 + CG - 1) / CG;
     tree_fwd_spline_seg_kernel<<<(unsigned)grid, block, smem, s>>>(r, a, sp, t);
     return cudaGetLastError();
   }
   const size_t smem = 12 * sizeof(float) * threads;
+  fit_carveout((const void*)tree_fwd_spline_kernel, threads, smem);
   const int64_t grid = (a.B + threads - 1) / threads;
   tree_fwd_spline_kernel<<<(unsigned)grid, threads, smem, s>>>(r, a, sp);
   return cudaGetLastError();
@@ -340,11 +377,13 @@ cudaError_t launch_tree_bwd_spline_cost(const DevRobot& r, const BwdArgs& a, con
     cudaError_t e = cudaFuncSetAttribute(tree_bwd_spline_cost_seg_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    fit_carveout((const void*)tree_bwd_spline_cost_seg_kernel, block, smem);
     const int64_t grid = ((a.B + 31) / 32 + CG - 1) / CG;
     tree_bwd_spline_cost_seg_kernel<<<(unsigned)grid, block, smem, s>>>(r, a, fc, sp, t);
     return cudaGetLastError();
   }
   const size_t smem = 12 * sizeof(float) * threads;
+  fit_carveout((const void*)tree_bwd_spline_cost_kernel, threads, smem);
   const int64_t grid = (a.B + threads - 1) / threads;
   tree_bwd_spline_cost_kernel<<<(unsigned)grid, threads, smem, s>>>(r, a, fc, sp);
   return cudaGetLastError();
