@@ -444,6 +444,63 @@ def test_bspline_reproduces_polynomials(oracle_lib):
     assert np.allclose(qdd[2], 2 / dt ** 2, atol=1e-10)
 
 
+def _golden_bspline():
+    """The paper's printed B-spline tables (tests/golden/bspline_cubic.txt)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "bspline_cubic.txt")
+    blocks, cur = {}, None
+    with open(path) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            if line[0].isalpha():  # a table name
+                cur = blocks.setdefault(line, [])
+                continue
+            cur.append([float(x) for x in line.split()])
+    return np.array(blocks["C6"]) / 6.0, np.array(blocks["GHOST"])
+
+
+def test_bspline_matches_the_printed_coefficients(oracle_lib):
+    """Eq. bspline-cubic with the C matrix the paper prints: probing the
+    oracle with unit control vectors on one segment recovers, for every
+    sample, the 3 x 4 map from the window's control points to (q, qd, qdd),
+    and it equals the first three rows of T P(alpha) C."""
+    O = oracle_lib
+    C, _ = _golden_bspline()
+    assert C.shape == (4, 4)
+    K, T, dt = 4, 9, 0.37
+    cols = []
+    for l in range(K):
+        U = np.zeros((1, 1, K))
+        U[0, 0, l] = 1.0
+        q, qd, qdd = O.bspline(U, T, dt)
+        cols.append(np.stack([q[0], qd[0], qdd[0]]))  # [3][T]
+    M = np.stack(cols, axis=-1)  # [3][T][4]
+    for s in range(T):
+        a = s / (T - 1)  # one segment: t = alpha
+        P = np.array([[a ** 3, a ** 2, a, 1.0],
+                      [3 * a ** 2, 2 * a, 1.0, 0.0],
+                      [6 * a, 2.0, 0.0, 0.0]])
+        Tm = np.diag([1.0, 1.0 / dt, 1.0 / dt ** 2])
+        assert np.allclose(M[:, s, :], Tm @ P @ C, atol=1e-13)
+
+
+def test_bspline_ghost_knots_match_the_printed_coefficients(oracle_lib):
+    """Eqs. fixed_3, fixed_2, fixed_1 as printed: probing ghost_knots with a
+    unit theta_0, thetadot_0 and thetaddot_0 recovers the coefficients of
+    each ghost control point."""
+    O = oracle_lib
+    _, G = _golden_bspline()
+    dt = 0.29
+    for i, cv, num, den in G:
+        slot = 3 - int(i)  # u_-3, u_-2, u_-1 in order
+        for comp, want in ((0, 1.0), (1, cv * dt), (2, num / den * dt * dt)):
+            st = np.zeros((1, 1, 3))
+            st[0, 0, comp] = 1.0
+            assert abs(O.ghost_knots(st, dt)[0, 0, slot] - want) < 1e-15
+
+
 def test_bspline_vjp_is_the_adjoint(oracle_lib):
     """The B-spline map U -> (q, qd, qdd) is linear, so its VJP must satisfy
     <bspline(U), g> = <U, vjp(g)> for every U and g (Eq. backward_grad is the
