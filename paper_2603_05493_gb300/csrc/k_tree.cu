@@ -34,6 +34,26 @@ __device__ __forceinline__ Seg seg_of(const DevRobot& r, int t, float* part) {
              part, r.seg_ns[t], (int)(threadIdx.x & 31)};
 }
 
+// The sweeps read a link's fixed transform, axis, mimic factors and inertia
+// at its push (and the backward again at its close).  The segmented ones
+// stage these once per block in shared memory, behind the partials
+// (kParamWords floats a link), where they no longer compete with the
+// depth-first stacks for L1.
+constexpr int kParamWords = 28;  // Tf 12, axis 4, inertia 10, mimic 2
+__device__ __forceinline__ DevRobot stage_params(const DevRobot& r, float* dst) {
+  const int n = r.n;
+  for (int i = threadIdx.x; i < 12 * n; i += blockDim.x) dst[i] = __ldg(r.Tf + i);
+  for (int i = threadIdx.x; i < 4 * n; i += blockDim.x) dst[12 * n + i] = __ldg(r.axis + i);
+  for (int i = threadIdx.x; i < 10 * n; i += blockDim.x) dst[16 * n + i] = __ldg(r.inert + i);
+  for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) dst[26 * n + i] = __ldg(r.mimic + i);
+  DevRobot s = r;
+  s.Tf = dst;
+  s.axis = dst + 12 * n;
+  s.inert = dst + 16 * n;
+  s.mimic = dst + 26 * n;
+  return s;
+}
+
 __global__ void __launch_bounds__(256) tree_fwd_seg_kernel(const __grid_constant__ DevRobot r,
                                                            FwdArgs A, int t) {
   extern __shared__ float part[];
@@ -43,8 +63,10 @@ __global__ void __launch_bounds__(256) tree_fwd_seg_kernel(const __grid_constant
   const int ns = r.seg_ns[t];
   Seg sg = seg_of(r, t, part + (size_t)cg * ns * G * 32);
   for (int s = 0; s < ns; ++s) sg.part[(s * G + sg.g) * 32 + sg.lane] = 0.0f;
+  const DevRobot rs = stage_params(r, part + (size_t)CG * ns * G * 32);
+  __syncthreads();
   const int64_t b = ((int64_t)blockIdx.x * CG + cg) * 32 + sg.lane;
-  if (b < A.B) tree_fwd_seg(r, A, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b, sg);
+  if (b < A.B) tree_fwd_seg(rs, A, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b, sg);
   __syncthreads();
   if (b < A.B && A.tau) {
     for (int s = sg.g; s < ns; s += G) {
@@ -67,8 +89,10 @@ __global__ void __launch_bounds__(256, 2) tree_bwd_seg_kernel(const __grid_const
   Seg sg = seg_of(r, t, part + (size_t)cg * 3 * o);
   for (int s = 0; s < ns; ++s)
     for (int q = 0; q < 3; ++q) sg.part[q * o + (s * G + sg.g) * 32 + sg.lane] = 0.0f;
+  const DevRobot rs = stage_params(r, part + (size_t)CG * 3 * o);
+  __syncthreads();
   const int64_t b = ((int64_t)blockIdx.x * CG + cg) * 32 + sg.lane;
-  if (b < A.B) tree_bwd_seg<false>(r, A, FusedCost{}, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b, sg);
+  if (b < A.B) tree_bwd_seg<false>(rs, A, FusedCost{}, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b, sg);
   __syncthreads();
   if (b < A.B) {
     for (int s = sg.g; s < ns; s += G) {
@@ -106,9 +130,11 @@ __global__ void __launch_bounds__(256, 2) tree_bwd_cost_seg_kernel(
   float* cpart = sg.part + 3 * o;  // [G][32] the segments' cost terms
   for (int s = 0; s < ns; ++s)
     for (int q = 0; q < 3; ++q) sg.part[q * o + (s * G + sg.g) * 32 + sg.lane] = 0.0f;
+  const DevRobot rs = stage_params(r, part + (size_t)CG * (3 * o + G * 32));
+  __syncthreads();
   const int64_t b = ((int64_t)blockIdx.x * CG + cg) * 32 + sg.lane;
   float c = 0.0f;
-  if (b < A.B) c = tree_bwd_seg<true>(r, A, fc, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b, sg);
+  if (b < A.B) c = tree_bwd_seg<true>(rs, A, fc, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b, sg);
   cpart[sg.g * 32 + sg.lane] = c;
   __syncthreads();
   if (b < A.B && sg.g == 0 && fc.cost) {
@@ -168,8 +194,10 @@ __global__ void __launch_bounds__(256) tree_fwd_spline_seg_kernel(
   const int ns = r.seg_ns[t];
   Seg sg = seg_of(r, t, part + (size_t)cg * ns * G * 32);
   for (int s = 0; s < ns; ++s) sg.part[(s * G + sg.g) * 32 + sg.lane] = 0.0f;
+  const DevRobot rs = stage_params(r, part + (size_t)CG * ns * G * 32);
+  __syncthreads();
   const int64_t b = ((int64_t)blockIdx.x * CG + cg) * 32 + sg.lane;
-  if (b < A.B) tree_fwd_seg(r, A, spline_states(r, sp, b, sm + 12 * threadIdx.x), b, sg);
+  if (b < A.B) tree_fwd_seg(rs, A, spline_states(r, sp, b, sm + 12 * threadIdx.x), b, sg);
   __syncthreads();
   if (b < A.B && A.tau) {
     for (int s = sg.g; s < ns; s += G) {
@@ -203,10 +231,12 @@ __global__ void __launch_bounds__(256, 2) tree_bwd_spline_cost_seg_kernel(
   float* cpart = sg.part + 3 * o;  // [G][32] the segments' cost terms
   for (int s = 0; s < ns; ++s)
     for (int q = 0; q < 3; ++q) sg.part[q * o + (s * G + sg.g) * 32 + sg.lane] = 0.0f;
+  const DevRobot rs = stage_params(r, base + (size_t)CG * (3 * o + G * 32));
+  __syncthreads();
   const int64_t b = ((int64_t)blockIdx.x * CG + cg) * 32 + sg.lane;
   float c = 0.0f;
   if (b < A.B)
-    c = tree_bwd_seg<true>(r, A, fc, spline_states(r, sp, b, sm + 12 * threadIdx.x), b, sg);
+    c = tree_bwd_seg<true>(rs, A, fc, spline_states(r, sp, b, sm + 12 * threadIdx.x), b, sg);
   cpart[sg.g * 32 + sg.lane] = c;
   __syncthreads();
   if (b < A.B && sg.g == 0 && fc.cost) {
@@ -278,12 +308,12 @@ static int seg_groups(int segments, int threads) { return std::max(1, threads / 
 
 // per group of G warps: the shared-slot partials of each output (tau in the
 // forward; gq, gqd, gqdd in the backward), plus, for the cost variant, one
-// cost term per segment
+// cost term per segment; per block, the staged link parameters
 size_t tree_seg_smem(const DevRobot& r, int segments, int threads, bool fwd, bool cost) {
   const int t = seg_plan(segments);
   const size_t per =
       (size_t)(fwd ? 1 : 3) * r.seg_ns[t] * segments * 32 + (cost ? segments * 32 : 0);
-  return (size_t)seg_groups(segments, threads) * per * sizeof(float);
+  return ((size_t)seg_groups(segments, threads) * per + (size_t)kParamWords * r.n) * sizeof(float);
 }
 
 template <class Args>

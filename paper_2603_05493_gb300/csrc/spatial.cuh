@@ -48,6 +48,14 @@ __device__ __forceinline__ void matmul3(const float* A, const float* B, float* C
       C[3 * i + j] = fmaf(A[3 * i + 2], B[6 + j], fmaf(A[3 * i + 1], B[3 + j], A[3 * i] * B[j]));
 }
 
+// Robot parameters (fixed transforms, axes, mimic factors, inertias) are read
+// with plain loads, not __ldg: the segmented backward sweeps stage them in
+// shared memory and hand the sweep pointers into it.
+template <class T>
+__device__ __forceinline__ T ldp(const T* p) {
+  return *p;
+}
+
 __device__ __forceinline__ float joint_var(const DevRobot& r, int k, float qj) {
   const float2 mm = reinterpret_cast<const float2*>(r.mimic)[k];
   return fmaf(mm.x, qj, mm.y);
@@ -58,7 +66,7 @@ __device__ __forceinline__ float joint_var(const DevRobot& r, int k, float qj) {
 // rotation R_J = c I + s [a]^ + (1-c) a a^T.  Prismatic: p = p_f + R_f a th.
 __device__ __forceinline__ void local_xf(const DevRobot& r, int k, float th, float* R, float* p) {
   const float4* T4 = reinterpret_cast<const float4*>(r.Tf + 12 * k);
-  const float4 t0 = __ldg(T4), t1 = __ldg(T4 + 1), t2 = __ldg(T4 + 2);
+  const float4 t0 = ldp(T4), t1 = ldp(T4 + 1), t2 = ldp(T4 + 2);
   const float Rf[9] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w, t2.x};
   p[0] = t2.y;
   p[1] = t2.z;
@@ -66,7 +74,7 @@ __device__ __forceinline__ void local_xf(const DevRobot& r, int k, float th, flo
   const int jt = __ldg(r.jtype + k);
   const bool ident = __ldg(r.rot_id + k) != 0;
   if (jt == 1) {
-    const float4 a = __ldg(reinterpret_cast<const float4*>(r.axis) + k);
+    const float4 a = ldp(reinterpret_cast<const float4*>(r.axis) + k);
     float s, c;
     sincosf(th, &s, &c);
     const float t = 1.0f - c;
@@ -92,7 +100,7 @@ __device__ __forceinline__ void local_xf(const DevRobot& r, int k, float th, flo
 #pragma unroll
     for (int i = 0; i < 9; ++i) R[i] = Rf[i];
     if (jt == 2) {
-      const float4 a = __ldg(reinterpret_cast<const float4*>(r.axis) + k);
+      const float4 a = ldp(reinterpret_cast<const float4*>(r.axis) + k);
       const float s[3] = {a.x * th, a.y * th, a.z * th};
       float Rs[3];
       rot(Rf, s, Rs);
@@ -170,7 +178,7 @@ __device__ __forceinline__ void inertia_mul(const float* I, const float* v, floa
 __device__ __forceinline__ void load_inertia(const DevRobot& r, int k, float* I) {
   const float* src = r.inert + 10 * k;
 #pragma unroll
-  for (int i = 0; i < 10; ++i) I[i] = __ldg(src + i);
+  for (int i = 0; i < 10; ++i) I[i] = ldp(src + i);
 }
 
 // Joint motion subspace S of link k as (jt, axis): revolute [a;0],

@@ -205,9 +205,9 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
     pdep = -1;
     const int j = __ldg(r.jidx + k);
     if (j >= 0) {
-      const float4 a4 = __ldg(reinterpret_cast<const float4*>(r.axis) + k);
+      const float4 a4 = ldp(reinterpret_cast<const float4*>(r.axis) + k);
       const float ax[3] = {a4.x, a4.y, a4.z};
-      const float mm = __ldg(reinterpret_cast<const float2*>(r.mimic) + k).x;
+      const float mm = ldp(reinterpret_cast<const float2*>(r.mimic) + k).x;
       const float t = mm * St_dot(__ldg(r.jtype + k), ax, F);
       float* pt = seg_part(sg, k, 0);
       if (pt) {
@@ -286,9 +286,9 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
     }
     if (dyn) {
       const int j = __ldg(r.jidx + k);
-      const float4 a4 = __ldg(reinterpret_cast<const float4*>(r.axis) + k);
+      const float4 a4 = ldp(reinterpret_cast<const float4*>(r.axis) + k);
       const float ax[3] = {a4.x, a4.y, a4.z};
-      const float mm = __ldg(reinterpret_cast<const float2*>(r.mimic) + k).x;
+      const float mm = ldp(reinterpret_cast<const float2*>(r.mimic) + k).x;
       const float vq = j >= 0 ? mm * st.vel(j) : 0.0f;
       const float aq = j >= 0 ? mm * st.acc(j) : 0.0f;
       rnea_va(L, L + 9, vp, ap, __ldg(r.jtype + k), ax, vq, aq, cv, ca);
@@ -556,11 +556,11 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
     pdep = -1;
     const int j = __ldg(r.jidx + k);
     const int jt = __ldg(r.jtype + k);
-    const float4 a4 = __ldg(reinterpret_cast<const float4*>(r.axis) + k);
+    const float4 a4 = ldp(reinterpret_cast<const float4*>(r.axis) + k);
     const float ax[3] = {a4.x, a4.y, a4.z};
     float S[6];
     motion_S6t(jt, ax, S);
-    const float mm = __ldg(reinterpret_cast<const float2*>(r.mimic) + k).x;
+    const float mm = ldp(reinterpret_cast<const float2*>(r.mimic) + k).x;
     const float vq = j >= 0 ? mm * st.vel(j) : 0.0f;
     float L[12];
     link_local(r, k, st, L);
@@ -723,9 +723,9 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
     replayed = own ? (replayed & ~bit) : (replayed | bit);
     const int j = __ldg(r.jidx + k);
     const int jt = __ldg(r.jtype + k);
-    const float4 a4 = __ldg(reinterpret_cast<const float4*>(r.axis) + k);
+    const float4 a4 = ldp(reinterpret_cast<const float4*>(r.axis) + k);
     const float ax[3] = {a4.x, a4.y, a4.z};
-    const float mm = __ldg(reinterpret_cast<const float2*>(r.mimic) + k).x;
+    const float mm = ldp(reinterpret_cast<const float2*>(r.mimic) + k).x;
     const float vq = j >= 0 ? mm * st.vel(j) : 0.0f;
     const float aq = j >= 0 ? mm * st.acc(j) : 0.0f;
     // dynamics forward: v, a
