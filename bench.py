@@ -88,14 +88,23 @@ def traffic_per_eval(name):
     return t["bytes_per_eval"]
 
 
-def sweep_shapes(rob, B, args):
+def sweep_shapes(rob, B, args, spline=None):
     """Forward and backward sweep launch shapes: the library's autotuner at
-    batch B, or the ones --sweep-shape pins (segments and configurations per
-    block of each sweep), so that a profiler run, whose slowed launches would
-    sway the autotuner, times the same launches as the plain run."""
+    batch B (the control-point path's own autotuner when spline = (n_traj, K,
+    T, dt) is given, timed with the trajectory cost's weights), or the ones
+    --sweep-shape pins (segments and configurations per block of each sweep),
+    so that a profiler run, whose slowed launches would sway the autotuner,
+    times the same launches as the plain run."""
     from paper_2603_05493_gb300 import wbe
     if not args.sweep_shape:
-        ft, bt, _, _ = rob.autotune(B)
+        if spline is not None:
+            ft, bt, _, _ = rob.autotune_spline(*spline, w_coll=CF.COLLISION_WEIGHT,
+                                               smooth=CF.SMOOTH_WEIGHT,
+                                               length=CF.LENGTH_WEIGHT,
+                                               energy=CF.ENERGY_WEIGHT,
+                                               dt_cost=spline[3] * (spline[1] - 3) / (spline[2] - 1))
+        else:
+            ft, bt, _, _ = rob.autotune(B)
         return ft, bt
     fs, fc, bs, bc = (int(x) for x in args.sweep_shape.split(","))
     mk = lambda g, c: wbe.Tune(kernel=wbe.L.WB_KERNEL_TREE, lanes_per_config=g,  # noqa: E731
@@ -543,7 +552,7 @@ def run_trajopt(args, rank=0, world=1, local_rank=0):
     rob = wbe.Robot(desc, device=local_rank)
     n_traj, K, T, dt = CF.TRAJOPT_SEEDS, CF.TRAJOPT_KNOTS, CF.TRAJOPT_STEPS, CF.TRAJOPT_DT
     B, d = n_traj * T, desc.dof
-    ft, bt = sweep_shapes(rob, B, args)
+    ft, bt = sweep_shapes(rob, B, args, spline=(n_traj, K, T, dt))
     seg = lambda t: t.lanes_per_config if t.kernel == wbe.L.WB_KERNEL_TREE else 0  # noqa
     tpb = lambda t: t.configs_per_block if t.kernel == wbe.L.WB_KERNEL_TREE else 0  # noqa
     ftune = wbe.Tune(kernel=wbe.L.WB_KERNEL_TREE, lanes_per_config=seg(ft),

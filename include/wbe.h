@@ -288,7 +288,8 @@ int wb_eval_backward_ext(wb_robot* robot, int64_t B, const float* q, const float
  * kernels with 4, 8, 16 and 32 lanes per configuration, the plain kernels --
  * on random states with all outputs (forward) and all upstream gradients
  * (backward), and returns the fastest choice for each pass with its median
- * time (ms, nullable). */
+ * time (ms, nullable).  Each candidate is timed 5 times, each run after an
+ * L2 flush (a memset of twice the L2 size), and ranked by the median. */
 int wb_autotune(wb_robot* robot, int64_t B, wb_tune* fwd, wb_tune* bwd, float* fwd_ms,
                 float* bwd_ms);
 
@@ -508,6 +509,25 @@ int wb_eval_backward_spline_cost(wb_robot* robot, const wb_spline* spline,
                                  const float* tau_lo, const float* tau_hi,
                                  const wb_cost_weights* w, float* cost, float* gq, float* gqd,
                                  float* gqdd, const wb_tune* tune, void* stream);
+
+/* Autotuner of the control-point path (a setup-time call like wb_autotune:
+ * it allocates scratch buffers for n_traj * T configurations, synchronises the
+ * device and must not be captured).  Times the depth-first sweep shapes
+ * (1 / 2 / 4 / 8 segments, 64 / 128 / 256 threads per block, as the robot's
+ * segment plans allow) of the two kernels this path runs -- wb_eval_spline
+ * with link poses and torques (the forward sweep), and
+ * wb_eval_backward_spline_cost with the cost weights w (host pointer) and
+ * torque limits of +-30 -- on deterministic control points in [-pi/2, pi/2],
+ * 5 runs per candidate, each after an L2 flush, and returns the fastest shape
+ * for each with its median time (ms, nullable).  Its choices differ from
+ * wb_autotune's where the spline-cost backward kernel prefers another block
+ * size than the plain backward sweep.  n_traj >= 1 and K, T, dt as
+ * wb_spline.
+ * Errors: WB_EINVAL (NULL argument, sizes, shared mimic joints), WB_ETOOBIG
+ * (tree deeper than the sweep kernels take), WB_ECUDA. */
+int wb_autotune_spline(wb_robot* robot, int64_t n_traj, int32_t K, int32_t T, float dt,
+                       const wb_cost_weights* w, wb_tune* fwd, wb_tune* bwd, float* fwd_ms,
+                       float* bwd_ms);
 
 /* ---------------------------------------------------------------------------
  * Forward evaluation of an uneven batch without any device allocation.  The

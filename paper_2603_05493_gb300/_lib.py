@@ -117,6 +117,10 @@ SIGNATURES = {
     "wb_eval_backward_spline_cost": (C.c_int, [p, C.POINTER(wb_spline), p, p, p, p, p, p, p,
                                                C.POINTER(wb_cost_weights), p, p, p, p,
                                                C.POINTER(wb_tune), p]),
+    "wb_autotune_spline": (C.c_int, [p, C.c_int64, C.c_int32, C.c_int32, C.c_float,
+                                     C.POINTER(wb_cost_weights), C.POINTER(wb_tune),
+                                     C.POINTER(wb_tune), C.POINTER(C.c_float),
+                                     C.POINTER(C.c_float)]),
     "wb_eval_backward_cost": (C.c_int, [p, C.c_int64, p, p, p, p, p, p, p, p, p, p,
                                         C.POINTER(wb_cost_weights), p, p, p, p,
                                         C.POINTER(wb_tune), p]),

@@ -7,38 +7,11 @@
 
 namespace wbe {
 
-__global__ void __launch_bounds__(256) tree_fwd_kernel(DevRobot r, FwdArgs A) {
-  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (b < A.B) tree_fwd_one(r, A, b);
-}
-
-// The backward sweeps are capped at 128 registers (two 256-thread blocks per
-// SM): with the register copies of the stack top they would take ~165, and
-// the occupancy lost costs more than the few spills (measured on the
-// 48-DoF humanoid: 0.29 ms capped vs 0.36 ms uncapped at 2 segments).
-__global__ void __launch_bounds__(256, 2) tree_bwd_kernel(DevRobot r, BwdArgs A) {
-  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (b < A.B) tree_bwd_one(r, A, b);
-}
-
-// Segmented sweeps, plan t (G = 2 << t segments).  A block holds CG groups of
-// G warps; warp w sweeps segment w % G of the 32 configurations of group
-// w / G.  Shared memory per group: the partial outputs [nout][ns][G][32] of
-// the ns links that several segments hold, summed in segment order after the
-// barrier by the group's warps (slot s by warp s % G).
-__device__ __forceinline__ Seg seg_of(const DevRobot& r, int t, float* part) {
-  const int G = 2 << t;
-  const int w = threadIdx.x >> 5;
-  const int g = w % G;
-  return Seg{r.seg_pos[t][g], r.seg_pos[t][g + 1], g, G, r.seg_slot + t * r.n,
-             part, r.seg_ns[t], (int)(threadIdx.x & 31)};
-}
-
 // The sweeps read a link's fixed transform, axis, mimic factors and inertia
-// at its push (and the backward again at its close).  The segmented ones
-// stage these once per block in shared memory, behind the partials
-// (kParamWords floats a link), where they no longer compete with the
-// depth-first stacks for L1.
+// at its push (and the backward again at its close).  Every sweep kernel
+// stages these once per block in shared memory (kParamWords floats a link,
+// behind the partials or basis rows it also keeps there), where they no
+// longer compete with the depth-first stacks for L1.
 constexpr int kParamWords = 28;  // Tf 12, axis 4, inertia 10, mimic 2
 __device__ __forceinline__ DevRobot stage_params(const DevRobot& r, float* dst) {
   const int n = r.n;
@@ -52,6 +25,41 @@ __device__ __forceinline__ DevRobot stage_params(const DevRobot& r, float* dst) 
   s.inert = dst + 16 * n;
   s.mimic = dst + 26 * n;
   return s;
+}
+
+__global__ void __launch_bounds__(256) tree_fwd_kernel(const __grid_constant__ DevRobot r,
+                                                       FwdArgs A) {
+  extern __shared__ float prm[];
+  const DevRobot rs = stage_params(r, prm);
+  __syncthreads();
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b < A.B) tree_fwd_one(rs, A, b);
+}
+
+// The backward sweeps are capped at 128 registers (two 256-thread blocks per
+// SM): with the register copies of the stack top they would take ~165, and
+// the occupancy lost costs more than the few spills (measured on the
+// 48-DoF humanoid: 0.29 ms capped vs 0.36 ms uncapped at 2 segments).
+__global__ void __launch_bounds__(256, 2) tree_bwd_kernel(const __grid_constant__ DevRobot r,
+                                                          BwdArgs A) {
+  extern __shared__ float prm[];
+  const DevRobot rs = stage_params(r, prm);
+  __syncthreads();
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b < A.B) tree_bwd_one(rs, A, b);
+}
+
+// Segmented sweeps, plan t (G = 2 << t segments).  A block holds CG groups of
+// G warps; warp w sweeps segment w % G of the 32 configurations of group
+// w / G.  Shared memory per group: the partial outputs [nout][ns][G][32] of
+// the ns links that several segments hold, summed in segment order after the
+// barrier by the group's warps (slot s by warp s % G).
+__device__ __forceinline__ Seg seg_of(const DevRobot& r, int t, float* part) {
+  const int G = 2 << t;
+  const int w = threadIdx.x >> 5;
+  const int g = w % G;
+  return Seg{r.seg_pos[t][g], r.seg_pos[t][g + 1], g, G, r.seg_slot + t * r.n,
+             part, r.seg_ns[t], (int)(threadIdx.x & 31)};
 }
 
 __global__ void __launch_bounds__(256) tree_fwd_seg_kernel(const __grid_constant__ DevRobot r,
@@ -112,10 +120,13 @@ __global__ void __launch_bounds__(256, 2) tree_bwd_seg_kernel(const __grid_const
 // separate kernels, so that the plain ones keep their register allocation.
 // The segmented one adds each configuration's cost terms over the segments
 // in segment order (deterministic) after the barrier.
-__global__ void __launch_bounds__(256, 2) tree_bwd_cost_kernel(DevRobot r, BwdArgs A,
-                                                               FusedCost fc) {
+__global__ void __launch_bounds__(256, 2) tree_bwd_cost_kernel(
+    const __grid_constant__ DevRobot r, BwdArgs A, FusedCost fc) {
+  extern __shared__ float prm[];
+  const DevRobot rs = stage_params(r, prm);
+  __syncthreads();
   const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (b < A.B) tree_bwd_cost_one(r, A, fc, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b);
+  if (b < A.B) tree_bwd_cost_one(rs, A, fc, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b);
 }
 
 __global__ void __launch_bounds__(256, 2) tree_bwd_cost_seg_kernel(
@@ -175,13 +186,15 @@ __device__ __forceinline__ SplineStates spline_states(const DevRobot& r, const S
   return SplineStates{sp.U + (tr * r.d) * sp.K + k, sp.K, bs};
 }
 
-__global__ void __launch_bounds__(256) tree_fwd_spline_kernel(DevRobot r, FwdArgs A,
-                                                              SplineArgs sp) {
+__global__ void __launch_bounds__(256) tree_fwd_spline_kernel(const __grid_constant__ DevRobot r,
+                                                              FwdArgs A, SplineArgs sp) {
   extern __shared__ float sm[];
+  const DevRobot rs = stage_params(r, sm + 12 * blockDim.x);
+  __syncthreads();
   const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (b >= A.B) return;
   const SplineStates st = spline_states(r, sp, b, sm + 12 * threadIdx.x);
-  tree_fwd_seg(r, A, st, b, whole_sweep(r));
+  tree_fwd_seg(rs, A, st, b, whole_sweep(r));
 }
 
 __global__ void __launch_bounds__(256) tree_fwd_spline_seg_kernel(
@@ -209,13 +222,14 @@ __global__ void __launch_bounds__(256) tree_fwd_spline_seg_kernel(
   }
 }
 
-__global__ void __launch_bounds__(256, 2) tree_bwd_spline_cost_kernel(DevRobot r, BwdArgs A,
-                                                                      FusedCost fc,
-                                                                      SplineArgs sp) {
+__global__ void __launch_bounds__(256, 2) tree_bwd_spline_cost_kernel(
+    const __grid_constant__ DevRobot r, BwdArgs A, FusedCost fc, SplineArgs sp) {
   extern __shared__ float sm[];
+  const DevRobot rs = stage_params(r, sm + 12 * blockDim.x);
+  __syncthreads();
   const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (b >= A.B) return;
-  tree_bwd_cost_one(r, A, fc, spline_states(r, sp, b, sm + 12 * threadIdx.x), b);
+  tree_bwd_cost_one(rs, A, fc, spline_states(r, sp, b, sm + 12 * threadIdx.x), b);
 }
 
 __global__ void __launch_bounds__(256, 2) tree_bwd_spline_cost_seg_kernel(
@@ -258,18 +272,6 @@ __global__ void __launch_bounds__(256, 2) tree_bwd_spline_cost_seg_kernel(
   }
 }
 
-// The one-thread sweep kernels use no shared memory: give the whole unified
-// L1/shared array to L1, where the stacks live.
-static void prefer_l1() {
-  static bool done = false;
-  if (!done) {
-    cudaFuncSetAttribute(tree_fwd_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-    cudaFuncSetAttribute(tree_bwd_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-    cudaFuncSetAttribute(tree_bwd_cost_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-    done = true;
-  }
-}
-
 // Shared memory and L1 are one array per SM.  Without a preference the
 // driver gave the segmented sweeps, whose blocks hold 14-22 KB of partials, a
 // 132 KB shared carveout (measured), and the L1 that caches their depth-first
@@ -303,6 +305,8 @@ void fit_carveout(const void* kern, int threads, size_t smem) {
   cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
 }
 
+static size_t param_smem(const DevRobot& r) { return sizeof(float) * kParamWords * (size_t)r.n; }
+
 static int seg_plan(int segments) { return segments == 2 ? 0 : segments == 4 ? 1 : 2; }
 static int seg_groups(int segments, int threads) { return std::max(1, threads / (32 * segments)); }
 
@@ -313,7 +317,7 @@ size_t tree_seg_smem(const DevRobot& r, int segments, int threads, bool fwd, boo
   const int t = seg_plan(segments);
   const size_t per =
       (size_t)(fwd ? 1 : 3) * r.seg_ns[t] * segments * 32 + (cost ? segments * 32 : 0);
-  return ((size_t)seg_groups(segments, threads) * per + (size_t)kParamWords * r.n) * sizeof(float);
+  return (size_t)seg_groups(segments, threads) * per * sizeof(float) + param_smem(r);
 }
 
 template <class Args>
@@ -351,9 +355,10 @@ cudaError_t launch_tree_fwd(const DevRobot& r, const FwdArgs& a, int threads, in
                             cudaStream_t s) {
   if (threads <= 0) threads = 128;
   if (segments > 1) return launch_seg(tree_fwd_seg_kernel, r, a, threads, segments, true, s);
-  prefer_l1();
+  const size_t smem = param_smem(r);
+  fit_carveout((const void*)tree_fwd_kernel, threads, smem);
   const int64_t grid = (a.B + threads - 1) / threads;
-  tree_fwd_kernel<<<(unsigned)grid, threads, 0, s>>>(r, a);
+  tree_fwd_kernel<<<(unsigned)grid, threads, smem, s>>>(r, a);
   return cudaGetLastError();
 }
 
@@ -363,12 +368,14 @@ cudaError_t launch_tree_bwd(const DevRobot& r, const BwdArgs& a, int threads, in
   if (segments > 1)
     return fc ? launch_cost_seg(r, a, *fc, threads, segments, s)
               : launch_seg(tree_bwd_seg_kernel, r, a, threads, segments, false, s);
-  prefer_l1();
+  const size_t smem = param_smem(r);
+  fit_carveout(fc ? (const void*)tree_bwd_cost_kernel : (const void*)tree_bwd_kernel, threads,
+               smem);
   const int64_t grid = (a.B + threads - 1) / threads;
   if (fc)
-    tree_bwd_cost_kernel<<<(unsigned)grid, threads, 0, s>>>(r, a, *fc);
+    tree_bwd_cost_kernel<<<(unsigned)grid, threads, smem, s>>>(r, a, *fc);
   else
-    tree_bwd_kernel<<<(unsigned)grid, threads, 0, s>>>(r, a);
+    tree_bwd_kernel<<<(unsigned)grid, threads, smem, s>>>(r, a);
   return cudaGetLastError();
 }
 
@@ -388,7 +395,7 @@ cudaError_t launch_tree_fwd_spline(const DevRobot& r, const FwdArgs& a, const Sp
     tree_fwd_spline_seg_kernel<<<(unsigned)grid, block, smem, s>>>(r, a, sp, t);
     return cudaGetLastError();
   }
-  const size_t smem = 12 * sizeof(float) * threads;
+  const size_t smem = 12 * sizeof(float) * threads + param_smem(r);
   fit_carveout((const void*)tree_fwd_spline_kernel, threads, smem);
   const int64_t grid = (a.B + threads - 1) / threads;
   tree_fwd_spline_kernel<<<(unsigned)grid, threads, smem, s>>>(r, a, sp);
@@ -412,7 +419,7 @@ cudaError_t launch_tree_bwd_spline_cost(const DevRobot& r, const BwdArgs& a, con
     tree_bwd_spline_cost_seg_kernel<<<(unsigned)grid, block, smem, s>>>(r, a, fc, sp, t);
     return cudaGetLastError();
   }
-  const size_t smem = 12 * sizeof(float) * threads;
+  const size_t smem = 12 * sizeof(float) * threads + param_smem(r);
   fit_carveout((const void*)tree_bwd_spline_cost_kernel, threads, smem);
   const int64_t grid = (a.B + threads - 1) / threads;
   tree_bwd_spline_cost_kernel<<<(unsigned)grid, threads, smem, s>>>(r, a, fc, sp);

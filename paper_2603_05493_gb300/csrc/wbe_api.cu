@@ -1952,9 +1952,67 @@ struct Scratch {
   }
 };
 
-float median3(std::vector<float> v) {
+float median_of(std::vector<float> v) {
   std::sort(v.begin(), v.end());
   return v[v.size() / 2];
+}
+
+// The autotuners' clock: the median of kTuneReps runs of f on stream s, each
+// after an L2 flush (a memset of flush_bytes, outside the events), as a step
+// over a batch that does not stay in L2 sees it.
+constexpr int kTuneReps = 5;
+struct TuneClock {
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  void* flush = nullptr;
+  size_t flush_bytes = 0;
+  bool init(Scratch& sc, int device) {
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+      return false;
+    int l2 = 0;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device) == cudaSuccess && l2 > 0) {
+      flush_bytes = 2 * (size_t)l2;
+      flush = sc.get<char>(flush_bytes);  // no flush if it cannot be had
+      if (!flush) cudaGetLastError();
+    }
+    return true;
+  }
+  template <class F>
+  float time(F&& f) {
+    std::vector<float> ts;
+    for (int rep = 0; rep < kTuneReps; ++rep) {
+      if (flush) cudaMemsetAsync(flush, rep & 0xFF, flush_bytes, s);
+      cudaEventRecord(e0, s);
+      f();
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ts.push_back(ms);
+    }
+    return median_of(ts);
+  }
+  ~TuneClock() {
+    if (s) cudaStreamSynchronize(s);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+  }
+};
+
+// the depth-first sweep shapes a robot takes: segments x threads per block
+std::vector<wb_tune> sweep_shapes(const DevRobot& D, bool pair_warps) {
+  std::vector<wb_tune> c;
+  if (D.maxdepth > tree_max_depth()) return c;
+  for (int seg : {1, 2, 4, 8})
+    for (int tpb : {64, 128, 256})
+      for (int pw : {4, 8}) {
+        if (!pair_warps && pw == 8) continue;
+        if (seg == 1 || (tpb >= 128 && (D.seg_ok >> (seg == 2 ? 0 : seg == 4 ? 1 : 2) & 1)))
+          c.push_back(wb_tune{WB_KERNEL_TREE, seg, tpb, pair_warps ? pw : 0});
+      }
+  return c;
 }
 }  // namespace
 
@@ -2003,18 +2061,10 @@ extern "C" int wb_autotune(wb_robot* robot, int64_t B, wb_tune* fwd, wb_tune* bw
     if (e == cudaSuccess) e = fill(gtau, nj, 1.0f);
     if (e != cudaSuccess) return cuda_fail(e, "autotune inputs");
   }
-  cudaStream_t s = nullptr;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
-    return fail(WB_ECUDA, "autotune stream/events");
-  std::vector<wb_tune> cands;
-  if (D.maxdepth <= tree_max_depth())
-    for (int seg : {1, 2, 4, 8})
-      for (int tpb : {64, 128, 256})
-        for (int pw : {4, 8})
-          if (seg == 1 || (tpb >= 128 && (D.seg_ok >> (seg == 2 ? 0 : seg == 4 ? 1 : 2) & 1)))
-            cands.push_back(wb_tune{WB_KERNEL_TREE, seg, tpb, pw});
+  TuneClock clk;
+  if (!clk.init(sc, robot->device)) return fail(WB_ECUDA, "autotune stream/events");
+  cudaStream_t s = clk.s;
+  std::vector<wb_tune> cands = sweep_shapes(D, true);
   for (int G : {4, 8, 16, 32}) cands.push_back(wb_tune{WB_KERNEL_FUSED, G, 0, 0});
   if (plain_fits(D)) cands.push_back(wb_tune{WB_KERNEL_PLAIN, 0, 0, 0});
   float best_f = 1e30f, best_b = 1e30f;
@@ -2029,17 +2079,7 @@ extern "C" int wb_autotune(wb_robot* robot, int64_t B, wb_tune* fwd, wb_tune* bw
                                             gtau, gq, gqd, gqdd, &t, s);
       };
       if (run() != WB_OK) continue;  // shape not applicable to this robot
-      std::vector<float> ts;
-      for (int rep = 0; rep < 3; ++rep) {
-        cudaEventRecord(e0, s);
-        run();
-        cudaEventRecord(e1, s);
-        cudaEventSynchronize(e1);
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        ts.push_back(ms);
-      }
-      const float m = median3(ts);
+      const float m = clk.time(run);
       if (pass == 0 && m < best_f) {
         best_f = m;
         bf = t;
@@ -2051,9 +2091,95 @@ extern "C" int wb_autotune(wb_robot* robot, int64_t B, wb_tune* fwd, wb_tune* bw
     }
   }
   cudaStreamSynchronize(s);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cudaStreamDestroy(s);
+  g_err.clear();
+  *fwd = bf;
+  *bwd = bb;
+  if (fwd_ms) *fwd_ms = best_f;
+  if (bwd_ms) *bwd_ms = best_b;
+  return WB_OK;
+}
+
+extern "C" int wb_autotune_spline(wb_robot* robot, int64_t n_traj, int32_t K, int32_t T, float dt,
+                                  const wb_cost_weights* w, wb_tune* fwd, wb_tune* bwd,
+                                  float* fwd_ms, float* bwd_ms) {
+  g_err.clear();
+  if (!robot || !fwd || !bwd || !w) return fail(WB_EINVAL, "NULL argument");
+  if (n_traj <= 0 || K < 4 || K > 4096 || T < 2 || T > 4096 || !(dt > 0.0f))
+    return fail(WB_EINVAL, "spline sizes out of range");
+  DeviceGuard guard(robot->device);
+  const DevRobot& D = robot->dev;
+  std::vector<wb_tune> cands = sweep_shapes(D, false);
+  if (cands.empty()) return fail(WB_ETOOBIG, "tree deeper than the sweep kernels take");
+  const int64_t B = n_traj * T;
+  const size_t nj = (size_t)D.d * B;
+  Scratch sc;
+  float* U = sc.get<float>((size_t)n_traj * D.d * K);
+  float* pose = sc.get<float>((size_t)B * D.n * 12);
+  float* sph = sc.get<float>((size_t)B * D.S * 3);
+  float* dmin = sc.get<float>(B);
+  int32_t* worst = sc.get<int32_t>(B);
+  float* tau = sc.get<float>(nj);
+  float* cost = sc.get<float>(B);
+  float* gq = sc.get<float>(nj);
+  float* gqd = sc.get<float>(nj);
+  float* gqdd = sc.get<float>(nj);
+  float* lim = sc.get<float>(2 * (size_t)D.d);
+  if (!U || !pose || !sph || !dmin || !worst || !tau || !cost || !gq || !gqd || !gqdd || !lim)
+    return fail(WB_ECUDA, "autotune scratch");
+  {  // deterministic control points in [-pi/2, pi/2]; torque limits +-30
+    const size_t nu = (size_t)n_traj * D.d * K;
+    std::vector<float> h(std::max(nu, 2 * (size_t)D.d));
+    uint64_t st = 0x9E3779B97F4A7C15ull;
+    for (size_t i = 0; i < nu; ++i) {
+      st = st * 6364136223846793005ull + 1442695040888963407ull;
+      h[i] = 1.57079633f * ((float)((st >> 40) * (1.0 / 16777216.0)) * 2.0f - 1.0f);
+    }
+    cudaError_t e = cudaMemcpy(U, h.data(), nu * sizeof(float), cudaMemcpyHostToDevice);
+    for (int j = 0; j < D.d; ++j) {
+      h[j] = -30.0f;
+      h[D.d + j] = 30.0f;
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpy(lim, h.data(), 2 * (size_t)D.d * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune inputs");
+  }
+  TuneClock clk;
+  if (!clk.init(sc, robot->device)) return fail(WB_ECUDA, "autotune stream/events");
+  cudaStream_t s = clk.s;
+  const wb_spline sp{U, n_traj, K, T, dt};
+  // the worst pairs and torques the backward reads
+  int rc = wb_eval_spline(robot, &sp, pose, sph, dmin, worst, tau, nullptr, s);
+  if (rc != WB_OK) return rc;
+  float best_f = 1e30f, best_b = 1e30f;
+  wb_tune bf = cands[0], bb = cands[0];
+  for (const wb_tune& t : cands) {
+    auto run_f = [&]() {
+      return wb_eval_spline(robot, &sp, pose, nullptr, nullptr, nullptr, tau, &t, s);
+    };
+    auto run_b = [&]() {
+      return wb_eval_backward_spline_cost(robot, &sp, worst, nullptr, nullptr, tau, dmin, lim,
+                                          lim + D.d, w, cost, gq, gqd, gqdd, &t, s);
+    };
+    if (run_f() == WB_OK) {
+      const float m = clk.time(run_f);
+      if (m < best_f) {
+        best_f = m;
+        bf = t;
+      }
+    }
+    if (run_b() == WB_OK) {
+      const float m = clk.time(run_b);
+      if (m < best_b) {
+        best_b = m;
+        bb = t;
+      }
+    }
+  }
+  cudaStreamSynchronize(s);
+  if (best_f >= 1e30f || best_b >= 1e30f) {
+    const std::string why = g_err.empty() ? std::string("no sweep shape applies") : g_err;
+    return fail(WB_EINVAL, "%s", why.c_str());
+  }
   g_err.clear();
   *fwd = bf;
   *bwd = bb;

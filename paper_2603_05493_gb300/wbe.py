@@ -162,6 +162,24 @@ class Robot:
         mk = lambda t: Tune(t.kernel, t.lanes_per_config, t.configs_per_block, t.blocks_per_sm)
         return mk(f), mk(b), fm.value, bm.value
 
+    def autotune_spline(self, n_traj: int, K: int, T: int, dt: float, w_coll: float = 1.0,
+                        smooth: float = 0.0, length: float = 0.0, energy: float = 0.0,
+                        dt_cost: float = 1.0):
+        """Time the sweep shapes of the control-point path (eval_spline's
+        forward sweep and eval_backward_spline_cost with these cost weights)
+        for n_traj trajectories of T samples from K control points
+        (wb_autotune_spline); returns (forward Tune, backward Tune, forward
+        ms, backward ms)."""
+        f, b = L.wb_tune(), L.wb_tune()
+        fm, bm = C.c_float(), C.c_float()
+        w = L.wb_cost_weights(float(w_coll), float(smooth), float(length), float(energy),
+                              float(dt_cost))
+        L.check(self.lib.wb_autotune_spline(self.handle, int(n_traj), int(K), int(T), float(dt),
+                                            C.byref(w), C.byref(f), C.byref(b), C.byref(fm),
+                                            C.byref(bm)), "wb_autotune_spline")
+        mk = lambda t: Tune(t.kernel, t.lanes_per_config, t.configs_per_block, t.blocks_per_sm)
+        return mk(f), mk(b), fm.value, bm.value
+
     # ------------------------------------------------------------------
     def empty_outputs(self, B, pose=True, sphere=True, dmin=True, tau=True, bits=False):
         dev = self.device

@@ -525,10 +525,11 @@ def test_trajopt48_full_size_spline_sampled(W, O):
     desc = I.hand_payload(R.r48())
     rob = W.Robot(desc, device=0)
     n_traj, K, T, dt = CF.TRAJOPT_SEEDS, CF.TRAJOPT_KNOTS, CF.TRAJOPT_STEPS, CF.TRAJOPT_DT
-    ft, bt, _, _ = rob.autotune(n_traj * T)
-    U = I.bspline_controls(desc.dof, n_traj, K, seed=CF.TRAJOPT48.seed)
     lim, w = CF.TORQUE_LIMIT, CF.COLLISION_WEIGHT
     motion = dict(smooth=CF.SMOOTH_WEIGHT, length=CF.LENGTH_WEIGHT, energy=CF.ENERGY_WEIGHT)
+    ft, bt, _, _ = rob.autotune_spline(n_traj, K, T, dt, w, dt_cost=dt * (K - 3) / (T - 1),
+                                       **motion)
+    U = I.bspline_controls(desc.dof, n_traj, K, seed=CF.TRAJOPT48.seed)
     lo, hi = cuda(-lim * np.ones(desc.dof)), cuda(lim * np.ones(desc.dof))
     tree = lambda t: W.Tune(kernel=3, lanes_per_config=t.lanes_per_config if t.kernel == 3 else 0,  # noqa: E731
                             configs_per_block=t.configs_per_block if t.kernel == 3 else 0)
@@ -560,3 +561,51 @@ def test_spline_sourced_refusals(W):
     o = rob.eval_spline(U, 8, 0.1, sphere=False, dmin=False)
     torch.cuda.synchronize()
     assert torch.isfinite(o["tau"]).all()
+
+
+def test_autotune_spline_shapes_run_and_agree(W):
+    """wb_autotune_spline returns depth-first sweep shapes the robot takes,
+    with positive times; the chosen shapes give the one-segment sweep's
+    results up to the rounding of the segments' partial sums."""
+    desc = I.hand_payload(R.r48())
+    rob = W.Robot(desc, device=0)
+    n_traj, K, T, dt = 16, 16, 64, 0.25
+    dtc = dt * (K - 3) / (T - 1)
+    motion = dict(smooth=CF.SMOOTH_WEIGHT, length=CF.LENGTH_WEIGHT, energy=CF.ENERGY_WEIGHT)
+    ft, bt, fm, bm = rob.autotune_spline(n_traj, K, T, dt, 1.0, dt_cost=dtc, **motion)
+    for t in (ft, bt):
+        assert t.kernel == 3 and t.lanes_per_config in (1, 2, 4, 8)
+        assert t.configs_per_block in (64, 128, 256)
+    assert 0.0 < fm < 1e3 and 0.0 < bm < 1e3
+    U = cuda(I.bspline_controls(desc.dof, n_traj, K, seed=PY.stable_seed("ats", 0)))
+    one = W.Tune(kernel=3, lanes_per_config=1)
+    lo = cuda(-CF.TORQUE_LIMIT * np.ones(desc.dof))
+    hi = cuda(CF.TORQUE_LIMIT * np.ones(desc.dof))
+    res = []
+    for ftune, btune in ((one, one), (ft, bt)):
+        o = rob.eval_spline(U, T, dt, tune=ftune)
+        g = rob.eval_backward_spline_cost(U, T, dt, o["tau"], lo, hi, 1.0, dt_cost=dtc,
+                                          d_min=o["dmin"], worst=o["worst"], tune=btune,
+                                          **motion)
+        res.append((o, g))
+    torch.cuda.synchronize()
+    (o1, g1), (o2, g2) = res
+    assert torch.equal(o1["worst"], o2["worst"])
+    for k in ("pose", "dmin", "tau"):
+        assert torch.allclose(o1[k], o2[k], rtol=1e-4, atol=1e-4), k
+    for x, y in zip(g1, g2):
+        assert torch.allclose(x, y, rtol=1e-4, atol=1e-3 * float(x.abs().max()))
+
+
+def test_autotune_spline_refusals(W):
+    from paper_2603_05493_gb300 import _lib as L
+    rob = W.Robot(R.r7(), device=0)
+    for args in ((0, 8, 16, 0.1), (2, 3, 16, 0.1), (2, 8, 1, 0.1), (2, 8, 16, 0.0)):
+        with pytest.raises(L.WbError) as e:
+            rob.autotune_spline(*args)
+        assert e.value.code == L.WB_EINVAL, args
+    deep = W.Robot(R.deep_chain(33), device=0)
+    with pytest.raises(L.WbError) as e:
+        deep.autotune_spline(2, 8, 16, 0.1)
+    assert e.value.code == L.WB_ETOOBIG
+
