@@ -137,7 +137,8 @@ typedef struct {
                                 joint drives several links); 0 = the fewest that
                                 give about 12 warps per SM */
   int32_t configs_per_block; /* fused: configurations per CTA; tree: threads per block
-                                of the sweep kernels (32..256); 0 = default */
+                                of the sweep kernels (32..256, up to 512 for
+                                G > 1 segments); 0 = default */
   int32_t blocks_per_sm;     /* fused: grid = blocks_per_sm * SMs (0 = occupancy);
                                 tree: warps per block of the pair kernel (0 = the
                                 most, up to 8, whose per-warp workspaces fit in a

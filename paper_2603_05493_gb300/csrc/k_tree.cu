@@ -37,9 +37,12 @@ __global__ void __launch_bounds__(256) tree_fwd_kernel(const __grid_constant__ D
 }
 
 // The backward sweeps are capped at 128 registers (two 256-thread blocks per
-// SM): with the register copies of the stack top they would take ~165, and
-// the occupancy lost costs more than the few spills (measured on the
-// 48-DoF humanoid: 0.29 ms capped vs 0.36 ms uncapped at 2 segments).
+// SM, or one 512-thread block of a segmented sweep): with the register copies
+// of the stack top they would take ~165, and the occupancy lost costs more
+// than the few spills (measured on the 48-DoF humanoid: 0.29 ms capped vs
+// 0.36 ms uncapped at 2 segments).  The segmented sweeps take blocks of up to
+// 512 threads, so that one block per SM holds the staged link parameters once
+// and the shared-memory carveout stays small.
 __global__ void __launch_bounds__(256, 2) tree_bwd_kernel(const __grid_constant__ DevRobot r,
                                                           BwdArgs A) {
   extern __shared__ float prm[];
@@ -62,7 +65,7 @@ __device__ __forceinline__ Seg seg_of(const DevRobot& r, int t, float* part) {
              part, r.seg_ns[t], (int)(threadIdx.x & 31)};
 }
 
-__global__ void __launch_bounds__(256) tree_fwd_seg_kernel(const __grid_constant__ DevRobot r,
+__global__ void __launch_bounds__(512) tree_fwd_seg_kernel(const __grid_constant__ DevRobot r,
                                                            FwdArgs A, int t) {
   extern __shared__ float part[];
   const int G = 2 << t;
@@ -86,7 +89,7 @@ __global__ void __launch_bounds__(256) tree_fwd_seg_kernel(const __grid_constant
   }
 }
 
-__global__ void __launch_bounds__(256, 2) tree_bwd_seg_kernel(const __grid_constant__ DevRobot r,
+__global__ void __launch_bounds__(512, 1) tree_bwd_seg_kernel(const __grid_constant__ DevRobot r,
                                                            BwdArgs A, int t) {
   extern __shared__ float part[];
   const int G = 2 << t;
@@ -129,7 +132,7 @@ __global__ void __launch_bounds__(256, 2) tree_bwd_cost_kernel(
   if (b < A.B) tree_bwd_cost_one(rs, A, fc, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b);
 }
 
-__global__ void __launch_bounds__(256, 2) tree_bwd_cost_seg_kernel(
+__global__ void __launch_bounds__(512, 1) tree_bwd_cost_seg_kernel(
     const __grid_constant__ DevRobot r, BwdArgs A, FusedCost fc, int t) {
   extern __shared__ float part[];
   const int G = 2 << t;
@@ -197,7 +200,7 @@ __global__ void __launch_bounds__(256) tree_fwd_spline_kernel(const __grid_const
   tree_fwd_seg(rs, A, st, b, whole_sweep(r));
 }
 
-__global__ void __launch_bounds__(256) tree_fwd_spline_seg_kernel(
+__global__ void __launch_bounds__(512) tree_fwd_spline_seg_kernel(
     const __grid_constant__ DevRobot r, FwdArgs A, SplineArgs sp, int t) {
   extern __shared__ float sm[];
   float* part = sm + 12 * blockDim.x;
@@ -232,7 +235,7 @@ __global__ void __launch_bounds__(256, 2) tree_bwd_spline_cost_kernel(
   tree_bwd_cost_one(rs, A, fc, spline_states(r, sp, b, sm + 12 * threadIdx.x), b);
 }
 
-__global__ void __launch_bounds__(256, 2) tree_bwd_spline_cost_seg_kernel(
+__global__ void __launch_bounds__(512, 1) tree_bwd_spline_cost_seg_kernel(
     const __grid_constant__ DevRobot r, BwdArgs A, FusedCost fc, SplineArgs sp, int t) {
   extern __shared__ float sm[];
   float* base = sm + 12 * blockDim.x;

@@ -949,6 +949,8 @@ static int tree_segments(const wb_robot* R, const wb_tune* tune, int64_t B, int 
     for (int t = 0; t < 3 && warps * G < target; ++t)
       if (ok >> t & 1) G = 2 << t;
   }
+  if (G == 1 && threads > 256)
+    return fail(WB_EINVAL, "one-segment sweeps take at most 256 threads per block");
   if (G > 1 && tree_seg_smem(R->dev, G, threads, fwd, !fwd) > 227 * 1024)
     return fail(WB_ETOOBIG, "segmented sweep needs too much shared memory");
   *out = G;
@@ -1006,8 +1008,8 @@ int wb_eval_ext(wb_robot* robot, int64_t B, const float* q, const float* qd, con
     if (pairs_wanted && !link_pose)
       return fail(WB_EINVAL, "the tree kernel needs link_pose when spheres or pairs are wanted");
     const int tpb = (tune && tune->configs_per_block) ? tune->configs_per_block : 128;
-    if (tpb < 32 || tpb > 256 || tpb % 32)
-      return fail(WB_EINVAL, "tree threads per block must be a multiple of 32 in [32, 256]");
+    if (tpb < 32 || tpb > 512 || tpb % 32)
+      return fail(WB_EINVAL, "tree threads per block must be a multiple of 32 in [32, 512]");
     const int warps = pair_warps(robot->dev, pair_bits != nullptr, tune);
     if (tune && tune->blocks_per_sm && (warps < 1 || warps > 8))
       return fail(WB_EINVAL, "pair warps per block must be in [1, 8]");
@@ -1206,8 +1208,8 @@ int wb_eval_backward_ext(wb_robot* robot, int64_t B, const float* q, const float
   } else if (kernel == WB_KERNEL_TREE) {
     if (!tree_ok) return fail(WB_ETOOBIG, "tree deeper than %d levels", tree_max_depth());
     const int tpb = (tune && tune->configs_per_block) ? tune->configs_per_block : 128;
-    if (tpb < 32 || tpb > 256 || tpb % 32)
-      return fail(WB_EINVAL, "tree threads per block must be a multiple of 32 in [32, 256]");
+    if (tpb < 32 || tpb > 512 || tpb % 32)
+      return fail(WB_EINVAL, "tree threads per block must be a multiple of 32 in [32, 512]");
     int G = 1;
     if ((rc = tree_segments(robot, tune, B, tpb, false, &G))) return rc;
     e = launch_tree_bwd(robot->dev, a, tpb, G, s);
@@ -1271,8 +1273,8 @@ int wb_eval_spline(wb_robot* robot, const wb_spline* spline, float* link_pose, f
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   FwdArgs a{B, nullptr, nullptr, nullptr, link_pose, sphere, d_min, worst_pair, tau, nullptr};
   const int tpb = (tune && tune->configs_per_block) ? tune->configs_per_block : 128;
-  if (tpb < 32 || tpb > 256 || tpb % 32)
-    return fail(WB_EINVAL, "tree threads per block must be a multiple of 32 in [32, 256]");
+  if (tpb < 32 || tpb > 512 || tpb % 32)
+    return fail(WB_EINVAL, "tree threads per block must be a multiple of 32 in [32, 512]");
   int G = 1;
   if ((rc = tree_segments(robot, tune, B, tpb, true, &G))) return rc;
   cudaError_t e = launch_tree_fwd_spline(robot->dev, a, sp, tpb, G, s);
@@ -1345,8 +1347,8 @@ int wb_eval_backward_spline_cost(wb_robot* robot, const wb_spline* spline,
   fc.e = W.energy * W.dt * W.dt;
   fc.cost = cost;
   const int tpb = (tune && tune->configs_per_block) ? tune->configs_per_block : 128;
-  if (tpb < 32 || tpb > 256 || tpb % 32)
-    return fail(WB_EINVAL, "tree threads per block must be a multiple of 32 in [32, 256]");
+  if (tpb < 32 || tpb > 512 || tpb % 32)
+    return fail(WB_EINVAL, "tree threads per block must be a multiple of 32 in [32, 512]");
   int G = 1;
   if ((rc = tree_segments(robot, tune, B, tpb, false, &G))) return rc;
   const cudaError_t e = launch_tree_bwd_spline_cost(robot->dev, a, fc, sp, tpb, G,
@@ -1408,8 +1410,8 @@ int wb_eval_backward_cost(wb_robot* robot, int64_t B, const float* q, const floa
   fc.e = W.energy * W.dt * W.dt;
   fc.cost = cost;
   const int tpb = (tune && tune->configs_per_block) ? tune->configs_per_block : 128;
-  if (tpb < 32 || tpb > 256 || tpb % 32)
-    return fail(WB_EINVAL, "tree threads per block must be a multiple of 32 in [32, 256]");
+  if (tpb < 32 || tpb > 512 || tpb % 32)
+    return fail(WB_EINVAL, "tree threads per block must be a multiple of 32 in [32, 512]");
   int G = 1;
   if ((rc = tree_segments(robot, tune, B, tpb, false, &G))) return rc;
   const cudaError_t e =
@@ -2002,14 +2004,17 @@ struct TuneClock {
 };
 
 // the depth-first sweep shapes a robot takes: segments x threads per block
+// (512-thread blocks for the segmented sweeps only: one block per SM then
+// holds the link parameters once)
 std::vector<wb_tune> sweep_shapes(const DevRobot& D, bool pair_warps) {
   std::vector<wb_tune> c;
   if (D.maxdepth > tree_max_depth()) return c;
   for (int seg : {1, 2, 4, 8})
-    for (int tpb : {64, 128, 256})
+    for (int tpb : {64, 128, 256, 512})
       for (int pw : {4, 8}) {
         if (!pair_warps && pw == 8) continue;
-        if (seg == 1 || (tpb >= 128 && (D.seg_ok >> (seg == 2 ? 0 : seg == 4 ? 1 : 2) & 1)))
+        if ((seg == 1 && tpb <= 256) ||
+            (seg > 1 && tpb >= 128 && (D.seg_ok >> (seg == 2 ? 0 : seg == 4 ? 1 : 2) & 1)))
           c.push_back(wb_tune{WB_KERNEL_TREE, seg, tpb, pair_warps ? pw : 0});
       }
   return c;

@@ -317,13 +317,14 @@ def _segments_available(desc, G):
 
 
 @pytest.mark.parametrize("rname", list(ROBOTS))
-@pytest.mark.parametrize("G", [1, 2, 4, 8])
-def test_tree_segments_parity(W, O, rname, G):
+@pytest.mark.parametrize("G,tpb", [(1, 0), (2, 0), (4, 0), (8, 0), (2, 512), (4, 512)])
+def test_tree_segments_parity(W, O, rname, G, tpb):
     """Segmented depth-first sweeps (G warps per 32 configurations, shared
     ancestors' outputs summed across segments) against the oracle, forward
-    and backward, on a ragged batch."""
+    and backward, on a ragged batch; also in 512-thread blocks (several
+    groups of G warps sharing one block's staged link parameters)."""
     desc, rob = robot(W, rname)
-    tune = W.Tune(kernel=3, lanes_per_config=G)
+    tune = W.Tune(kernel=3, lanes_per_config=G, configs_per_block=tpb)
     B = 77 if rname == "R48" else 203
     q, qd, qdd = I.uniform_states(desc.dof, B, seed=PY.stable_seed(rname, 5, G))
     if not _segments_available(desc, G):
@@ -352,6 +353,17 @@ def test_tree_segments_parity(W, O, rname, G):
     torch.cuda.synchronize()
     for a, b in zip(g, g1):
         torch.testing.assert_close(a, b, rtol=1e-4, atol=1e-4 * float(b.abs().max()))
+
+
+def test_one_segment_sweeps_refuse_512_threads(W):
+    desc, rob = robot(W, "R7")
+    q = cuda(np.zeros((desc.dof, 40)))
+    with pytest.raises(W.L.WbError) as ei:
+        rob.eval(q, q, q, tune=W.Tune(kernel=3, lanes_per_config=1, configs_per_block=512))
+    assert ei.value.code == W.L.WB_EINVAL
+    with pytest.raises(W.L.WbError) as ei:
+        rob.eval(q, q, q, tune=W.Tune(kernel=3, lanes_per_config=2, configs_per_block=544))
+    assert ei.value.code == W.L.WB_EINVAL
 
 
 def test_maximum_size_robot(W, O):
