@@ -55,20 +55,27 @@ def work_per_eval(desc):
 
 
 # DRAM bytes (read + write) per evaluation from one ncu capture of each
-# kernel at the bench's launch configuration on 24576 configurations, tied to
-# the hash of the sources that kernel is built from: a changed source makes the
-# figure stale, and it is reported as null until captured again.
+# kernel at the bench's launch configuration (humanoid48 and trajopt48, both
+# on their 32768 configurations), tied to the kernel launched and to
+# the hash of the sources it is built from: a changed source or another
+# kernel makes the figure stale, and it is reported as null until captured
+# again.
 TREE_SRC = ["paper_2603_05493_gb300/csrc/k_tree.cu", "paper_2603_05493_gb300/csrc/tree_sweep.cuh",
             "paper_2603_05493_gb300/csrc/spatial.cuh", "paper_2603_05493_gb300/csrc/spline_basis.cuh"]
 PAIR_SRC = ["paper_2603_05493_gb300/csrc/k_pair.cu", "paper_2603_05493_gb300/csrc/pair_body.cuh",
             "paper_2603_05493_gb300/csrc/spatial.cuh"]
-MEASURED_TRAFFIC = {  # profiles/humanoid48_kernel_traffic.md
-    "tree_fwd": {"src": TREE_SRC, "sha256": "bbb3c684f90e677446f70efdea5abea535395149c3113a7965139f4790dcd361",
-                 "bytes_per_eval": (17.13e6 + 42.01e6) / 24576},
-    "pair": {"src": PAIR_SRC, "sha256": "1b13086cd2699f0b277577a854f835d9ca425fc9ac020564113acfaecdc67567",
-             "bytes_per_eval": (59.68e6 + 21.17e6) / 24576},
-    "tree_bwd": {"src": TREE_SRC, "sha256": "bbb3c684f90e677446f70efdea5abea535395149c3113a7965139f4790dcd361",
-                 "bytes_per_eval": (214.81e6 + 94.50e6) / 24576},
+SPLINE_SRC = ["paper_2603_05493_gb300/csrc/k_traj.cu", "paper_2603_05493_gb300/csrc/spline_basis.cuh"]
+TREE_SHA = "ac75317bcb46a234d7b96495d9413974d7338a02888b313a4531e372720ca258"
+PAIR_SHA = "24eba79b1a9ec4a4fcf9f325d5e1c7e8a31c5b229392800e1bee28cbaa6dd384"
+SPLINE_SHA = "c108dcde01f4aae419c550035ef5f5a4bbbc87970a1f481e1261585a2097194d"
+MEASURED_TRAFFIC = {  # profiles/humanoid48_kernel_traffic.md, profiles/trajopt48_kernel_traffic.md
+    "tree_fwd_seg_kernel": (TREE_SRC, TREE_SHA, (29.86e6 + 79.77e6) / 32768),
+    "pair_kernel": (PAIR_SRC, PAIR_SHA, (79.02e6 + 41.27e6) / 32768),
+    "tree_bwd_seg_kernel": (TREE_SRC, TREE_SHA, (341.06e6 + 162.12e6) / 32768),
+    "tree_fwd_spline_seg_kernel": (TREE_SRC, TREE_SHA, (8.41e6 + 80.03e6) / 32768),
+    "pair_kernel@trajopt48": (PAIR_SRC, PAIR_SHA, (77.81e6 + 0.20e6) / 32768),
+    "tree_bwd_spline_cost_kernel": (TREE_SRC, TREE_SHA, (15.23e6 + 20.83e6) / 32768),
+    "bspline_bwd_kernel": (SPLINE_SRC, SPLINE_SHA, (18.89e6 + 0.0) / 32768),
 }
 
 
@@ -81,11 +88,13 @@ def source_hash(files):
     return h.hexdigest()
 
 
-def traffic_per_eval(name):
-    t = MEASURED_TRAFFIC.get(name)
-    if not t or not t["sha256"] or source_hash(t["src"]) != t["sha256"]:
+def traffic_per_eval(kernel, workload=""):
+    """Measured DRAM bytes per evaluation of this kernel (in this workload,
+    where it has its own figure), or None when stale or never captured."""
+    t = MEASURED_TRAFFIC.get("%s@%s" % (kernel, workload)) or MEASURED_TRAFFIC.get(kernel)
+    if not t or source_hash(t[0]) != t[1]:
         return None
-    return t["bytes_per_eval"]
+    return t[2]
 
 
 def sweep_shapes(rob, B, args, spline=None):
@@ -449,7 +458,7 @@ def run_ours(args, rank, world, local_rank):
             ach = w["bytes"] * B / (ms * 1e-3) / 1e9
             kernels[name] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                              "frac": ach / hbm_peak}
-        tr = traffic_per_eval(name)
+        tr = traffic_per_eval(names[name])
         kernels[name].update({"kernel": names[name], "ms": ms, "flops_per_eval": w["flops"],
                               "bytes_per_eval": w["bytes"],
                               "traffic": None if tr is None else tr * B})
@@ -666,8 +675,10 @@ def run_trajopt(args, rank=0, world=1, local_rank=0):
             ach = w["bytes"] * B / (ms * 1e-3) / 1e9
             kernels[nm] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                            "frac": ach / hbm_peak}
+        tr = traffic_per_eval(kn[nm], "trajopt48")
         kernels[nm].update({"kernel": kn[nm], "ms": ms, "flops_per_eval": w["flops"],
-                            "bytes_per_eval": w["bytes"], "traffic": None})
+                            "bytes_per_eval": w["bytes"],
+                            "traffic": None if tr is None else tr * B})
     dom = max(k_ms, key=k_ms.get)
     line = {
         "metric": "trajopt48 evals/s (B-spline -> FK+self-coll+RNEA -> hinge + motion cost "

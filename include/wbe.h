@@ -285,7 +285,9 @@ int wb_eval_backward_ext(wb_robot* robot, int64_t B, const float* q, const float
 /* Autotuner (a setup-time call: it allocates scratch buffers for B
  * configurations, synchronises the device and must not be captured).  Times
  * every applicable kernel family and launch shape -- depth-first sweep kernels
- * with 64 / 128 / 256 threads per block and 4 / 8 warps per pair block, fused
+ * with 64 / 128 / 256 threads per block (512 and the block that deals B
+ * evenly over the SMs in one wave for segmented sweeps; the latter for one
+ * segment too) and 4 / 8 warps per pair block, fused
  * kernels with 4, 8, 16 and 32 lanes per configuration, the plain kernels --
  * on random states with all outputs (forward) and all upstream gradients
  * (backward), and returns the fastest choice for each pass with its median
@@ -514,8 +516,8 @@ int wb_eval_backward_spline_cost(wb_robot* robot, const wb_spline* spline,
 /* Autotuner of the control-point path (a setup-time call like wb_autotune:
  * it allocates scratch buffers for n_traj * T configurations, synchronises the
  * device and must not be captured).  Times the depth-first sweep shapes
- * (1 / 2 / 4 / 8 segments, 64 / 128 / 256 threads per block, as the robot's
- * segment plans allow) of the two kernels this path runs -- wb_eval_spline
+ * (1 / 2 / 4 / 8 segments as the robot's segment plans allow, and the block
+ * sizes wb_autotune tries) of the two kernels this path runs -- wb_eval_spline
  * with link poses and torques (the forward sweep), and
  * wb_eval_backward_spline_cost with the cost weights w (host pointer) and
  * torque limits of +-30 -- on deterministic control points in [-pi/2, pi/2],

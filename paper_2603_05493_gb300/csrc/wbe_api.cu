@@ -2003,20 +2003,35 @@ struct TuneClock {
   }
 };
 
-// the depth-first sweep shapes a robot takes: segments x threads per block
-// (512-thread blocks for the segmented sweeps only: one block per SM then
-// holds the link parameters once)
-std::vector<wb_tune> sweep_shapes(const DevRobot& D, bool pair_warps) {
+// the depth-first sweep shapes a robot takes for B configurations: segments
+// x threads per block -- 64 / 128 / 256, 512 for the segmented sweeps (one
+// block per SM then holds the link parameters once), and the balanced block
+// that deals the batch's 32-configuration groups evenly over the SMs in one
+// wave (448 threads at 2 segments for 32768 configurations on 152 SMs: 147
+// blocks of 14 warps, where 512-thread blocks leave 24 SMs idle)
+std::vector<wb_tune> sweep_shapes(const DevRobot& D, bool pair_warps, int64_t B, int num_sms) {
   std::vector<wb_tune> c;
   if (D.maxdepth > tree_max_depth()) return c;
-  for (int seg : {1, 2, 4, 8})
-    for (int tpb : {64, 128, 256, 512})
+  const int64_t groups = (B + 31) / 32;
+  for (int seg : {1, 2, 4, 8}) {
+    const bool ok = seg == 1 || (D.seg_ok >> (seg == 2 ? 0 : seg == 4 ? 1 : 2) & 1);
+    if (!ok) continue;
+    const int lim = seg == 1 ? 256 : 512;
+    const int64_t per_sm = num_sms > 0 ? (seg == 1 ? (B + num_sms - 1) / num_sms
+                                                   : (groups + num_sms - 1) / num_sms)
+                                       : 0;
+    const int64_t bal = seg == 1 ? (per_sm + 31) / 32 * 32 : 32 * seg * per_sm;
+    std::vector<int> tpbs = {64, 128, 256, 512};
+    if (bal >= 32 && bal <= lim && bal != 64 && bal != 128 && bal != 256 && bal != 512)
+      tpbs.push_back((int)bal);
+    for (int tpb : tpbs) {
+      if (tpb > lim || (seg > 1 && tpb < 128)) continue;
       for (int pw : {4, 8}) {
         if (!pair_warps && pw == 8) continue;
-        if ((seg == 1 && tpb <= 256) ||
-            (seg > 1 && tpb >= 128 && (D.seg_ok >> (seg == 2 ? 0 : seg == 4 ? 1 : 2) & 1)))
-          c.push_back(wb_tune{WB_KERNEL_TREE, seg, tpb, pair_warps ? pw : 0});
+        c.push_back(wb_tune{WB_KERNEL_TREE, seg, tpb, pair_warps ? pw : 0});
       }
+    }
+  }
   return c;
 }
 }  // namespace
@@ -2069,7 +2084,7 @@ extern "C" int wb_autotune(wb_robot* robot, int64_t B, wb_tune* fwd, wb_tune* bw
   TuneClock clk;
   if (!clk.init(sc, robot->device)) return fail(WB_ECUDA, "autotune stream/events");
   cudaStream_t s = clk.s;
-  std::vector<wb_tune> cands = sweep_shapes(D, true);
+  std::vector<wb_tune> cands = sweep_shapes(D, true, B, robot->num_sms);
   for (int G : {4, 8, 16, 32}) cands.push_back(wb_tune{WB_KERNEL_FUSED, G, 0, 0});
   if (plain_fits(D)) cands.push_back(wb_tune{WB_KERNEL_PLAIN, 0, 0, 0});
   float best_f = 1e30f, best_b = 1e30f;
@@ -2113,9 +2128,9 @@ extern "C" int wb_autotune_spline(wb_robot* robot, int64_t n_traj, int32_t K, in
     return fail(WB_EINVAL, "spline sizes out of range");
   DeviceGuard guard(robot->device);
   const DevRobot& D = robot->dev;
-  std::vector<wb_tune> cands = sweep_shapes(D, false);
-  if (cands.empty()) return fail(WB_ETOOBIG, "tree deeper than the sweep kernels take");
   const int64_t B = n_traj * T;
+  std::vector<wb_tune> cands = sweep_shapes(D, false, B, robot->num_sms);
+  if (cands.empty()) return fail(WB_ETOOBIG, "tree deeper than the sweep kernels take");
   const size_t nj = (size_t)D.d * B;
   Scratch sc;
   float* U = sc.get<float>((size_t)n_traj * D.d * K);
