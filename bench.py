@@ -313,6 +313,10 @@ def run_ours(args, rank, world, local_rank):
                         configs_per_block=tpb(ft))
         btune = wbe.Tune(kernel=wbe.L.WB_KERNEL_TREE, lanes_per_config=seg(bt),
                          configs_per_block=tpb(bt))
+        # the pair stage's warps per block as the autotuner timed them with
+        # the forward (0 when pinned: the library's default)
+        ptune = wbe.Tune(kernel=wbe.L.WB_KERNEL_TREE,
+                         blocks_per_sm=ft.blocks_per_sm if ft.kernel == wbe.L.WB_KERNEL_TREE else 0)
         chosen = {"fwd": dict(ft.__dict__), "bwd": dict(bt.__dict__)}
         names = {"tree_fwd": "tree_fwd_seg_kernel" if seg(ft) > 1 else "tree_fwd_kernel",
                  "pair": "pair_kernel",
@@ -344,7 +348,7 @@ def run_ours(args, rank, world, local_rank):
             rob.eval(tq, tqd, tqdd, tune=tune, out=fwd_out, dmin=False, sphere=False)
             if events:
                 events[1].record(stream)
-            rob.self_collision(out["pose"], out=pair_out)
+            rob.self_collision(out["pose"], out=pair_out, tune=ptune)
             if events:
                 events[2].record(stream)
         rob.eval_backward(tq, tqd, tqdd, out["worst"], tgp, tgs, tgm, tgt, tune=btune, out=gout)

@@ -140,10 +140,13 @@ typedef struct {
                                 of the sweep kernels (32..256, up to 512 for
                                 G > 1 segments); 0 = default */
   int32_t blocks_per_sm;     /* fused: grid = blocks_per_sm * SMs (0 = occupancy);
-                                tree: warps per block of the pair kernel (0 = the
-                                most, up to 8, whose per-warp workspaces fit in a
-                                block's shared memory: 8 up to about 850 spheres,
-                                6 at 1020) */
+                                tree: warps per block of the pair kernel, 1..8
+                                (0 = of the counts 4..8 whose per-warp
+                                workspaces fit in a block's shared memory, the
+                                one whose blocks keep the most warps resident
+                                on an SM, the fewest on a tie: 4 for the 48-DoF
+                                humanoid; fewer than 4 only for robots where
+                                no more fit) */
 } wb_tune;
 
 typedef struct {
