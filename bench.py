@@ -230,11 +230,11 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline leg and --impl reference)
 # ---------------------------------------------------------------------------
-def time_oracle(desc, target_s=15.0, seed=CF.HUMANOID48.seed):
+def time_oracle(desc, target_s=15.0, seed=CF.HUMANOID48.seed, orob=None):
     """Forward + exact (dual-number) gradient of the FP64 oracle on the host
     cores, on a sample sized to take about target_s seconds."""
     from oracle import oracle as O
-    orob = O.OracleRobot(desc)
+    orob = orob or O.OracleRobot(desc)
     cores = O.max_threads()
     n_cal = max(cores, 8)
     q, qd, qdd = I.uniform_states(desc.dof, n_cal, seed)
@@ -255,15 +255,29 @@ def time_oracle(desc, target_s=15.0, seed=CF.HUMANOID48.seed):
                       "gradient, OpenMP over configurations), %.1f s" % (n, desc.name, dt)}
 
 
+def reference_step_targets(steps, warmup, total_s, step_cap_s):
+    """Seconds of oracle work for each warm-up and each timed step of the
+    reference arm: the whole run stays within about total_s whatever the
+    step counts (a timed step takes at most step_cap_s and at least 0.1 s;
+    the warm-up gets a tenth of the budget)."""
+    warm = min(2.0, max(0.05, 0.1 * total_s / max(1, warmup)))
+    step = min(step_cap_s, max(0.1, 0.9 * total_s / max(1, steps)))
+    return warm, step
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
+    from oracle import oracle as O
     desc = R.r48()
+    orob = O.OracleRobot(desc)
+    warm_s, step_s = reference_step_targets(args.steps, args.warmup, args.ref_total_s,
+                                            args.ref_step_s)
     steps = []
     for _ in range(args.warmup):
-        time_oracle(desc, target_s=2.0)
+        time_oracle(desc, target_s=warm_s, orob=orob)
     for _ in range(args.steps):
-        steps.append(time_oracle(desc, target_s=args.ref_step_s))
+        steps.append(time_oracle(desc, target_s=step_s, orob=orob))
     vals = [s["value"] for s in steps]
     value = float(np.mean(vals))
     line = {
@@ -896,7 +910,10 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--cpu-s", type=float, default=15.0)
-    ap.add_argument("--ref-step-s", type=float, default=10.0)
+    ap.add_argument("--ref-step-s", type=float, default=10.0,
+                    help="reference arm: at most this many seconds of oracle work a step")
+    ap.add_argument("--ref-total-s", type=float, default=120.0,
+                    help="reference arm: about this many seconds for the whole run")
     ap.add_argument("--workload", choices=["humanoid48", "uneven", "trajopt48", "kinematics"],
                     default="humanoid48")
     ap.add_argument("--collision", choices=["worst", "hinge"], default="worst",

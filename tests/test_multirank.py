@@ -60,3 +60,33 @@ def test_single_rank_needs_no_process_group():
     assert bench.rank_seed(7, 0) == 7
     assert len({bench.rank_seed(7, r) for r in range(8)}) == 8
     assert np.isfinite(bench.job_value(8, 32768, 0.8))
+
+
+@pytest.mark.parametrize("steps,warmup", [(1, 3), (20, 5), (300, 5), (1000, 10)])
+def test_reference_arm_fits_its_time_budget(steps, warmup):
+    """bench.py --impl reference times the oracle in bounded samples: however
+    many steps it is asked for, the whole run stays within about its budget
+    (120 s by default), and no step is longer than the per-step cap."""
+    import bench
+    total, cap = 120.0, 10.0
+    warm, step = bench.reference_step_targets(steps, warmup, total, cap)
+    assert 0.0 < warm <= 2.0 and 0.0 < step <= cap
+    planned = warmup * warm + steps * step
+    assert planned <= 1.05 * total or step == 0.1  # the floor: 0.1 s a step
+    assert planned <= 240.0
+
+
+def test_reference_arm_runs_end_to_end_quickly():
+    """The reference arm's JSON line on a tiny budget (a few seconds of the
+    FP64 oracle on the host cores)."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "4",
+                          "--warmup", "1", "--ref-total-s", "2"], cwd=root, capture_output=True,
+                         text=True, timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["steps"] == 4
