@@ -8,8 +8,14 @@ configurations of the 48-DoF humanoid-shaped tree (1024 seeds x 32 timesteps
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--kernel tree|fused|plain] [--batch B] [--skip-cpu] [--skip-plain]
+                  [--workload humanoid48|trajopt48|uneven|kinematics]
+                  [--collision worst|hinge] [--sweep-shape FS,FC,BS,BC]
+                  [--ref-total-s T] [--ref-step-s S]
 
---impl reference times the FP64 CPU oracle on the host cores instead.
+--impl reference times the FP64 CPU oracle on the host cores instead, in
+bounded samples that keep the whole run within about --ref-total-s seconds.
+--sweep-shape pins the sweeps' launch shapes (segments and threads per block
+of the forward and the backward) instead of autotuning, for profiler runs.
 Under torchrun (N > 1) every rank evaluates its own batch (weak scaling);
 the step time is the maximum over ranks.
 """
