@@ -193,7 +193,7 @@ static void build_schedule(int G, const std::vector<uint32_t>& bx, std::vector<u
 
 extern "C" {
 
-int wb_version(void) { return 101; }
+int wb_version(void) { return 102; }
 
 const char* wb_last_error(void) { return g_err.c_str(); }
 
