@@ -269,7 +269,10 @@ cudaError_t launch_trajopt_cost(int64_t B, int d, const float* tau, const float*
                                 float* g_qdd, cudaStream_t s);
 
 // segments: 1 = one thread per configuration; 2, 4, 8 = segmented sweep
-// (requires the robot's plan for it, bit log2(segments) - 1 of seg_ok)
+// (requires the robot's plan for it, bit log2(segments) - 1 of seg_ok).
+// threads: threads per block, a multiple of 32, at most 256 for one segment
+// and 512 for a segmented sweep (its launch bounds); every sweep block also
+// stages the robot's link parameters in shared memory
 cudaError_t launch_tree_fwd(const DevRobot& r, const FwdArgs& a, int threads, int segments,
                             cudaStream_t s);
 cudaError_t launch_tree_bwd(const DevRobot& r, const BwdArgs& a, int threads, int segments,
