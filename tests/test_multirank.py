@@ -90,3 +90,27 @@ def test_reference_arm_runs_end_to_end_quickly():
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["steps"] == 4
+
+
+def test_work_model_matches_the_documented_figures():
+    """bench.py's algorithmic flops and bytes per evaluation, on the bench's
+    robots, are the closed forms of the design notes' work table."""
+    import bench
+    from synthetic import inputs as I
+    from synthetic import robots as R
+    r48 = R.r48()
+    n, nm, S, P, d = r48.n, 48, r48.S, r48.P, r48.dof
+    assert (n, S, P, d) == (49, 200, 15392, 48)
+    w = bench.work_per_eval(r48)
+    assert w["tree_fwd"] == {"flops": 150 * nm + 330 * n, "bytes": 4 * (3 * d + 12 * n + d)}
+    assert w["pair"] == {"flops": 18 * S + 11 * P, "bytes": 4 * (12 * n + 3 * S + 2)}
+    assert w["tree_bwd"] == {"flops": 150 * nm + 1050 * n + 15 * S,
+                             "bytes": 4 * (7 * d + 12 * n + 3 * S + 2)}
+    assert [w[k]["flops"] for k in ("tree_fwd", "pair", "tree_bwd")] == [23370, 172912, 61650]
+    assert [w[k]["bytes"] for k in ("tree_fwd", "pair", "tree_bwd")] == [3120, 4760, 6104]
+    t = bench.trajopt_work(I.hand_payload(r48), 16, 64)
+    assert t["tree_fwd"] == {"flops": 24714, "bytes": 2592}
+    assert t["pair"] == {"flops": 172912, "bytes": 2360}
+    assert t["tree_bwd"] == {"flops": 62397, "bytes": 828}
+    assert t["bspline_bwd"] == {"flops": 1152, "bytes": 624}
+    assert t["hinge"] == {"flops": 249872, "bytes": 4756}
