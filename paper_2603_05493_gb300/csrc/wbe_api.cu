@@ -922,19 +922,22 @@ static int warps_that_fit(size_t fixed_bytes, size_t per_warp_bytes) {
   return 0;
 }
 // Warps per block of the pair kernel (wb_tune.blocks_per_sm for TREE): the
-// tuned count, else the count in 4..8 (of those whose workspaces fit a block)
-// whose blocks keep the most warps resident on an SM, the fewest on a tie --
-// smaller blocks let the persistent grid deal its configurations in finer
-// pieces.  Measured on the 48-DoF humanoid at 32768 configurations: 4 warps
-// (7 blocks, 28 warps an SM) 0.176 ms, 7 warps (4 blocks) 0.183 ms, 8 warps
-// (3 blocks, 24 warps) 0.185 ms.
-static int pair_warps(wb_robot* R, bool bits, const wb_tune* tune) {
+// tuned count; else, for the culled kernel, the count in 4..8 (of those whose
+// workspaces fit a block) whose blocks keep the most warps resident on an SM,
+// the fewest on a tie -- smaller blocks let the persistent grid deal its
+// configurations in finer pieces; for the full map-reduce (TREE_NOCULL) the
+// most that fit.  Measured on the 48-DoF humanoid at 32768 configurations,
+// culled: 4 warps (7 blocks, 28 warps an SM) 0.176 ms, 7 warps (4 blocks)
+// 0.183 ms, 8 warps (3 blocks, 24 warps) 0.185 ms; the full map-reduce
+// 0.33 ms at 8 warps, 0.40 ms at 4.
+static int pair_warps(wb_robot* R, bool bits, const wb_tune* tune, bool cull = true) {
   if (tune && tune->blocks_per_sm) return tune->blocks_per_sm;
-  int& cached = R->pair_warps_default[bits ? 1 : 0];
-  if (cached) return cached;
   const DevRobot& D = R->dev;
   const size_t one = pair_block_smem(D, 1, bits), none = pair_block_smem(D, 0, bits);
   const int most = warps_that_fit(none, one - none);
+  if (!cull) return most;
+  int& cached = R->pair_warps_default[bits ? 1 : 0];
+  if (cached) return cached;
   int best = most, best_res = -1;
   for (int w = 4; w <= most; ++w) {
     int bps = 0;
@@ -1036,7 +1039,7 @@ int wb_eval_ext(wb_robot* robot, int64_t B, const float* q, const float* qd, con
     const int tpb = (tune && tune->configs_per_block) ? tune->configs_per_block : 128;
     if (tpb < 32 || tpb > 512 || tpb % 32)
       return fail(WB_EINVAL, "tree threads per block must be a multiple of 32 in [32, 512]");
-    const int warps = pair_warps(robot, pair_bits != nullptr, tune);
+    const int warps = pair_warps(robot, pair_bits != nullptr, tune, cull);
     if (tune && tune->blocks_per_sm && (warps < 1 || warps > 8))
       return fail(WB_EINVAL, "pair warps per block must be in [1, 8]");
     if (pairs_wanted && warps == 0) return fail(WB_ETOOBIG, "pair kernel does not fit on an SM");
@@ -1094,7 +1097,7 @@ int wb_self_collision_tuned(wb_robot* robot, int64_t B, const float* link_pose, 
   const int kernel = tune ? tune->kernel : WB_KERNEL_AUTO;
   if (kernel != WB_KERNEL_AUTO && kernel != WB_KERNEL_TREE && kernel != WB_KERNEL_TREE_NOCULL)
     return fail(WB_EINVAL, "the pair kernel takes TREE (culled) or TREE_NOCULL");
-  const int warps = pair_warps(robot, pair_bits != nullptr, tune);
+  const int warps = pair_warps(robot, pair_bits != nullptr, tune, kernel != WB_KERNEL_TREE_NOCULL);
   if (tune && tune->blocks_per_sm && (warps < 1 || warps > 8))
     return fail(WB_EINVAL, "pair warps per block must be in [1, 8]");
   if (warps == 0) return fail(WB_ETOOBIG, "pair kernel does not fit on an SM");
@@ -1305,7 +1308,7 @@ int wb_eval_spline(wb_robot* robot, const wb_spline* spline, float* link_pose, f
   if ((rc = tree_segments(robot, tune, B, tpb, true, &G))) return rc;
   cudaError_t e = launch_tree_fwd_spline(robot->dev, a, sp, tpb, G, s);
   if (e == cudaSuccess && pairs_wanted) {
-    const int warps = pair_warps(robot, false, tune);
+    const int warps = pair_warps(robot, false, tune, kernel != WB_KERNEL_TREE_NOCULL);
     if (warps < 1 || warps > 8) return fail(WB_ETOOBIG, "pair kernel does not fit on an SM");
     int bps = 0;
     e = pair_max_blocks_per_sm(robot->dev, warps, false, &bps);
