@@ -62,19 +62,23 @@ def work_per_eval(desc):
 
 # DRAM bytes (read + write) per evaluation from one ncu capture of each
 # kernel at the bench's launch configuration (humanoid48 and trajopt48, both
-# on their 32768 configurations), tied to the kernel launched and to
-# the hash of the sources it is built from: a changed source or another
-# kernel makes the figure stale, and it is reported as null until captured
-# again.
+# on their 32768 configurations), tied to the kernel launched and to the
+# hash of the sources it is built from, including the host code that picks
+# its launch shape (wbe_api.cu): a changed source, another launch-shape
+# default or another kernel makes the figure stale, and it is reported as
+# null until captured again.
+API_SRC = ["paper_2603_05493_gb300/csrc/wbe_api.cu"]
 TREE_SRC = ["paper_2603_05493_gb300/csrc/k_tree.cu", "paper_2603_05493_gb300/csrc/tree_sweep.cuh",
-            "paper_2603_05493_gb300/csrc/spatial.cuh", "paper_2603_05493_gb300/csrc/spline_basis.cuh"]
+            "paper_2603_05493_gb300/csrc/spatial.cuh",
+            "paper_2603_05493_gb300/csrc/spline_basis.cuh"] + API_SRC
 PAIR_SRC = ["paper_2603_05493_gb300/csrc/k_pair.cu", "paper_2603_05493_gb300/csrc/pair_body.cuh",
-            "paper_2603_05493_gb300/csrc/spatial.cuh"]
-SPLINE_SRC = ["paper_2603_05493_gb300/csrc/k_traj.cu", "paper_2603_05493_gb300/csrc/spline_basis.cuh"]
+            "paper_2603_05493_gb300/csrc/spatial.cuh"] + API_SRC
+SPLINE_SRC = ["paper_2603_05493_gb300/csrc/k_traj.cu",
+              "paper_2603_05493_gb300/csrc/spline_basis.cuh"] + API_SRC
 TREE_SHA = "ac75317bcb46a234d7b96495d9413974d7338a02888b313a4531e372720ca258"
 PAIR_SHA = "24eba79b1a9ec4a4fcf9f325d5e1c7e8a31c5b229392800e1bee28cbaa6dd384"
 SPLINE_SHA = "c108dcde01f4aae419c550035ef5f5a4bbbc87970a1f481e1261585a2097194d"
-MEASURED_TRAFFIC = {  # profiles/humanoid48_kernel_traffic.md, profiles/trajopt48_kernel_traffic.md
+MEASURED_TRAFFIC = {  # kernel[@workload]: (sources, their hash, bytes / evaluation)
     "tree_fwd_seg_kernel": (TREE_SRC, TREE_SHA, (29.86e6 + 79.77e6) / 32768),
     "pair_kernel": (PAIR_SRC, PAIR_SHA, (79.02e6 + 41.27e6) / 32768),
     "tree_bwd_seg_kernel": (TREE_SRC, TREE_SHA, (341.06e6 + 162.12e6) / 32768),
@@ -125,6 +129,76 @@ def sweep_shapes(rob, B, args, spline=None):
     mk = lambda g, c: wbe.Tune(kernel=wbe.L.WB_KERNEL_TREE, lanes_per_config=g,  # noqa: E731
                                configs_per_block=c)
     return mk(fs, fc), mk(bs, bc)
+
+
+# ---------------------------------------------------------------------------
+# the humanoid48 step: its launch shapes and its launches (the GPU parity
+# tests run the same two functions at the full batch)
+# ---------------------------------------------------------------------------
+def humanoid48_launch(rob, B, kernel="tree", sweep_shape=""):
+    """Launch choices of the humanoid48 step at batch B: for the tree kernels
+    the sweep shapes (segments, threads per block) and the pair stage's warps
+    per block from the library's autotuner at this batch size (or the sweep
+    shapes --sweep-shape pins); for fused / plain one kernel family.  Returns
+    {"fwd", "pair", "bwd": Tune, "names": kernel names, "chosen": the
+    autotuner's picks or None}."""
+    from paper_2603_05493_gb300 import wbe
+    if kernel != "tree":
+        t = {"plain": wbe.PLAIN, "fused": wbe.FUSED}[kernel]
+        pre = "fused" if kernel == "fused" else "plain"
+        return {"fwd": t, "pair": None, "bwd": t, "chosen": None,
+                "names": {"tree_fwd": pre + "_fwd_kernel", "pair": "-",
+                          "tree_bwd": pre + "_bwd_kernel"}}
+
+    class _Pin:  # the argparse namespace sweep_shapes reads
+        pass
+    pin = _Pin()
+    pin.sweep_shape = sweep_shape
+    ft, bt = sweep_shapes(rob, B, pin)
+    is_tree = lambda t: t.kernel == wbe.L.WB_KERNEL_TREE  # noqa: E731
+    seg = lambda t: t.lanes_per_config if is_tree(t) else 0  # noqa: E731
+    tpb = lambda t: t.configs_per_block if is_tree(t) else 0  # noqa: E731
+    fwd = wbe.Tune(kernel=wbe.L.WB_KERNEL_TREE, lanes_per_config=seg(ft),
+                   configs_per_block=tpb(ft))
+    bwd = wbe.Tune(kernel=wbe.L.WB_KERNEL_TREE, lanes_per_config=seg(bt),
+                   configs_per_block=tpb(bt))
+    # the pair stage's warps per block as the autotuner timed them with the
+    # forward (0 when pinned: the library's default)
+    pair = wbe.Tune(kernel=wbe.L.WB_KERNEL_TREE, blocks_per_sm=ft.blocks_per_sm if is_tree(ft) else 0)
+    return {"fwd": fwd, "pair": pair, "bwd": bwd,
+            "chosen": {"fwd": dict(ft.__dict__), "bwd": dict(bt.__dict__)},
+            "names": {"tree_fwd": "tree_fwd_seg_kernel" if seg(ft) > 1 else "tree_fwd_kernel",
+                      "pair": "pair_kernel",
+                      "tree_bwd": "tree_bwd_seg_kernel" if seg(bt) > 1 else "tree_bwd_kernel"}}
+
+
+def humanoid48_step(rob, shapes, states, grads, out, gout, events=None, stream=None):
+    """One humanoid48 step with the launch choices of humanoid48_launch:
+    forward (FK + RNEA sweep, then spheres + self-collision; one launch for
+    fused / plain) and backward with the upstream gradients grads = (g_pose,
+    g_sphere, g_dmin, g_tau).  out: rob.empty_outputs(B); gout: (gq, gqd,
+    gqdd).  events[1], events[2] are recorded after the forward sweep and
+    after the pair stage."""
+    tq, tqd, tqdd = states
+    tgp, tgs, tgm, tgt = grads
+    if shapes["pair"] is None:  # one forward launch
+        rob.eval(tq, tqd, tqdd, tune=shapes["fwd"], out=out, stream=stream)
+        if events:
+            events[1].record(stream)
+            events[2].record(stream)
+    else:
+        rob.eval(tq, tqd, tqdd, tune=shapes["fwd"], dmin=False, sphere=False, stream=stream,
+                 out={"pose": out["pose"], "sphere": None, "dmin": None, "worst": None,
+                      "tau": out["tau"], "bits": None})
+        if events:
+            events[1].record(stream)
+        rob.self_collision(out["pose"], tune=shapes["pair"], stream=stream,
+                           out={"sphere": out["sphere"], "dmin": out["dmin"],
+                                "worst": out["worst"], "bits": None})
+        if events:
+            events[2].record(stream)
+    rob.eval_backward(tq, tqd, tqdd, out["worst"], tgp, tgs, tgm, tgt, tune=shapes["bwd"],
+                      out=gout, stream=stream)
 
 
 # ---------------------------------------------------------------------------
@@ -236,29 +310,96 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline leg and --impl reference)
 # ---------------------------------------------------------------------------
-def time_oracle(desc, target_s=15.0, seed=CF.HUMANOID48.seed, orob=None):
-    """Forward + exact (dual-number) gradient of the FP64 oracle on the host
-    cores, on a sample sized to take about target_s seconds."""
-    from oracle import oracle as O
-    orob = orob or O.OracleRobot(desc)
-    cores = O.max_threads()
-    n_cal = max(cores, 8)
-    q, qd, qdd = I.uniform_states(desc.dof, n_cal, seed)
-    gp, gs, gm, gt = I.upstream_grads(desc, n_cal, seed + 1)
-    t0 = time.perf_counter()
-    O.evaluate(orob, q, qd, qdd)
-    O.gradient(orob, q, qd, qdd, gp, gs, gm, gt)
-    per = (time.perf_counter() - t0) / n_cal
-    n = int(max(n_cal, min(200000, target_s / max(per, 1e-9))))
-    q, qd, qdd = I.uniform_states(desc.dof, n, seed + 7)
-    gp, gs, gm, gt = I.upstream_grads(desc, n, seed + 8)
-    t0 = time.perf_counter()
-    O.evaluate(orob, q, qd, qdd)
-    O.gradient(orob, q, qd, qdd, gp, gs, gm, gt)
-    dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "evals/s", "cores": cores, "kind": "oracle",
-            "sample": "%d configurations of the %s workload (FP64 forward + dual-number "
-                      "gradient, OpenMP over configurations), %.1f s" % (n, desc.name, dt)}
+FD_PASS = ("forward + central-difference gradient (2*3d+1 forward evaluations per "
+           "configuration: the oracle has no reverse mode; its dual-number gradient is for "
+           "correctness only and is not timed)")
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or the machine type."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
+
+
+class OracleTimer:
+    """The FP64 oracle (g++ -O3, plain double, OpenMP over configurations) on
+    the humanoid48 workload, timed on the host cores: the forward evaluation
+    (FK, spheres, brute-force pairs, RNEA), and forward + backward as the
+    forward plus a central-difference gradient of the same upstream loss as
+    the GPU step."""
+
+    def __init__(self, desc, seed=CF.HUMANOID48.seed):
+        from oracle import oracle as O
+        self.O = O
+        self.desc = desc
+        self.orob = O.OracleRobot(desc)
+        self.seed = seed
+        self.threads = O.max_threads()
+        self._inputs = {}
+
+    def inputs(self, n):
+        if n not in self._inputs:
+            q, qd, qdd = I.uniform_states(self.desc.dof, n, self.seed + 7)
+            self._inputs = {n: (q, qd, qdd) + tuple(I.upstream_grads(self.desc, n,
+                                                                      self.seed + 8))}
+        return self._inputs[n]
+
+    def run(self, n, threads, backward):
+        """Wall seconds of one pass over n configurations."""
+        q, qd, qdd, gp, gs, gm, gt = self.inputs(n)
+        t0 = time.perf_counter()
+        self.O.evaluate(self.orob, q, qd, qdd, nthreads=threads)
+        if backward:
+            self.O.gradient_fd(self.orob, q, qd, qdd, gp, gs, gm, gt, nthreads=threads)
+        return time.perf_counter() - t0
+
+    def size_for(self, target_s, threads, backward, cap):
+        """Configurations that take about target_s (calibrated on a small run)."""
+        n0 = max(threads, 4) if backward else max(16 * threads, 64)
+        per = self.run(n0, threads, backward) / n0
+        return int(max(n0, min(cap, target_s / max(per, 1e-9))))
+
+    def rate(self, target_s, threads, backward, cap=200000):
+        n = self.size_for(target_s, threads, backward, cap)
+        dt = self.run(n, threads, backward)
+        return n / dt, n, dt
+
+
+def time_oracle(desc, target_s=15.0):
+    """cpu_baseline: the oracle's forward + backward (forward + central
+    differences) on all host cores over a sample sized to take about half of
+    target_s, with the single-thread figure and the forward-only rates (all
+    cores, and one thread on at most a 4096-configuration subset) beside it."""
+    t = OracleTimer(desc)
+    fb_n, n_fb, s_fb = t.rate(0.5 * target_s, t.threads, True)
+    fb_1, n_fb1, s_fb1 = t.rate(0.2 * target_s, 1, True)
+    f_n, n_f, s_f = t.rate(0.1 * target_s, t.threads, False)
+    f_1, n_f1, s_f1 = t.rate(0.2 * target_s, 1, False, cap=4096)
+    return {"value": fb_n, "unit": "evals/s", "cores": t.threads, "kind": "oracle",
+            "pass": FD_PASS,
+            "sample": "%d configurations of the %s workload on %d threads in %.1f s "
+                      "(1 thread: %d in %.1f s)" % (n_fb, desc.name, t.threads, s_fb, n_fb1,
+                                                     s_fb1),
+            "threads_1": fb_1,
+            "forward": {"threads_N": f_n, "threads_1": f_1, "unit": "evals/s",
+                        "sample": "%d configurations on %d threads in %.2f s; %d on 1 thread "
+                                  "in %.2f s" % (n_f, t.threads, s_f, n_f1, s_f1)},
+            "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+            "build": "g++ -O3 -fopenmp, plain double"}
 
 
 def reference_step_targets(steps, warmup, total_s, step_cap_s):
@@ -271,30 +412,44 @@ def reference_step_targets(steps, warmup, total_s, step_cap_s):
     return warm, step
 
 
+HUMANOID48_WORKLOAD = ("humanoid48: 48-DoF tree, 200 spheres, 15392 pairs, 1024 x 32 "
+                       "configurations, fwd + bwd (upstream grads on poses, spheres, d_min, tau)")
+
+
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle's forward + backward (forward +
+    central differences) on all host cores.  Every timed step evaluates the
+    same bounded sample of the humanoid48 workload, sized in the warm-up so
+    that the run keeps to about --ref-total-s; ms_per_step is the measured
+    wall time of a step."""
     if rank != 0:
         return
-    from oracle import oracle as O
     desc = R.r48()
-    orob = O.OracleRobot(desc)
+    t = OracleTimer(desc)
     warm_s, step_s = reference_step_targets(args.steps, args.warmup, args.ref_total_s,
                                             args.ref_step_s)
-    steps = []
+    n = t.size_for(step_s, t.threads, True, cap=CF.HUMANOID48.batch)
     for _ in range(args.warmup):
-        time_oracle(desc, target_s=warm_s, orob=orob)
-    for _ in range(args.steps):
-        steps.append(time_oracle(desc, target_s=step_s, orob=orob))
-    vals = [s["value"] for s in steps]
-    value = float(np.mean(vals))
+        t.run(max(t.threads, int(n * warm_s / step_s)), t.threads, True)
+    secs = [t.run(n, t.threads, True) for _ in range(args.steps)]
+    mean_s = float(np.mean(secs))
+    value = n / mean_s
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * CF.HUMANOID48.batch / value, "higher_is_better": True,
+        "ms_per_step": 1e3 * mean_s, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "humanoid48: 48-DoF tree, 200 spheres, 15392 pairs, "
-                               "1024 x 32 configurations, fwd + bwd",
-                   "batch": CF.HUMANOID48.batch},
-        "cpu_baseline": dict(steps[-1], value=value),
+        "config": {"workload": HUMANOID48_WORKLOAD, "batch": CF.HUMANOID48.batch,
+                   "sample_configs_per_step": n,
+                   "step": "each timed step evaluates the same %d-configuration sample of "
+                           "the batch (forward + backward); value = sample / measured step "
+                           "time" % n},
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": t.threads, "kind": "oracle",
+                         "pass": FD_PASS,
+                         "sample": "%d configurations per step, %d timed steps of %.2f s "
+                                   "mean" % (n, args.steps, mean_s),
+                         "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+                         "build": "g++ -O3 -fopenmp, plain double"},
         "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -317,30 +472,9 @@ def run_ours(args, rank, world, local_rank):
     desc = R.r48()
     B = args.batch or CF.HUMANOID48.batch
     rob = wbe.Robot(desc, device=local_rank)
-    tune = {"plain": wbe.PLAIN, "fused": wbe.FUSED, "tree": wbe.TREE}[args.kernel]
-    btune = tune
-    names = {"tree_fwd": "fused_fwd_kernel" if args.kernel == "fused" else "plain_fwd_kernel",
-             "pair": "-", "tree_bwd": "fused_bwd_kernel" if args.kernel == "fused"
-             else "plain_bwd_kernel"}
-    chosen = None
-    if args.kernel == "tree":
-        # sweep launch shape (segments, threads per block) from the library's
-        # autotuner at this batch size
-        ft, bt = sweep_shapes(rob, B, args)
-        seg = lambda t: t.lanes_per_config if t.kernel == wbe.L.WB_KERNEL_TREE else 0  # noqa
-        tpb = lambda t: t.configs_per_block if t.kernel == wbe.L.WB_KERNEL_TREE else 0  # noqa
-        tune = wbe.Tune(kernel=wbe.L.WB_KERNEL_TREE, lanes_per_config=seg(ft),
-                        configs_per_block=tpb(ft))
-        btune = wbe.Tune(kernel=wbe.L.WB_KERNEL_TREE, lanes_per_config=seg(bt),
-                         configs_per_block=tpb(bt))
-        # the pair stage's warps per block as the autotuner timed them with
-        # the forward (0 when pinned: the library's default)
-        ptune = wbe.Tune(kernel=wbe.L.WB_KERNEL_TREE,
-                         blocks_per_sm=ft.blocks_per_sm if ft.kernel == wbe.L.WB_KERNEL_TREE else 0)
-        chosen = {"fwd": dict(ft.__dict__), "bwd": dict(bt.__dict__)}
-        names = {"tree_fwd": "tree_fwd_seg_kernel" if seg(ft) > 1 else "tree_fwd_kernel",
-                 "pair": "pair_kernel",
-                 "tree_bwd": "tree_bwd_seg_kernel" if seg(bt) > 1 else "tree_bwd_kernel"}
+    shapes = humanoid48_launch(rob, B, args.kernel, args.sweep_shape)
+    tune, btune = shapes["fwd"], shapes["bwd"]
+    names, chosen = shapes["names"], shapes["chosen"]
     seed = rank_seed(CF.HUMANOID48.seed, rank)
     q, qd, qdd = I.uniform_states(desc.dof, B, seed)
     gp, gs, gm, gt = I.upstream_grads(desc, B, seed + 1)
@@ -352,26 +486,9 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
     stream = torch.cuda.current_stream()
 
-    fwd_out = {"pose": out["pose"], "sphere": None, "dmin": None, "worst": None,
-               "tau": out["tau"], "bits": None}
-    pair_out = {"sphere": out["sphere"], "dmin": out["dmin"], "worst": out["worst"],
-                "bits": None}
-
     def step(events=None):
-        # forward: FK + RNEA sweep, then spheres + self-collision; backward
-        if args.kernel != "tree":  # one forward launch
-            rob.eval(tq, tqd, tqdd, tune=tune, out=out)
-            if events:
-                events[1].record(stream)
-                events[2].record(stream)
-        else:
-            rob.eval(tq, tqd, tqdd, tune=tune, out=fwd_out, dmin=False, sphere=False)
-            if events:
-                events[1].record(stream)
-            rob.self_collision(out["pose"], out=pair_out, tune=ptune)
-            if events:
-                events[2].record(stream)
-        rob.eval_backward(tq, tqd, tqdd, out["worst"], tgp, tgs, tgm, tgt, tune=btune, out=gout)
+        humanoid48_step(rob, shapes, (tq, tqd, tqdd), (tgp, tgs, tgm, tgt), out, gout,
+                        events=events, stream=stream)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -494,9 +611,7 @@ def run_ours(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "humanoid48: 48-DoF tree, 200 spheres, 15392 pairs, "
-                               "1024 x 32 configurations, fwd + bwd (upstream grads on "
-                               "poses, spheres, d_min, tau)",
+        "config": {"workload": HUMANOID48_WORKLOAD,
                    "batch_per_gpu": B, "kernel": args.kernel, "autotuned": chosen,
                    "l2": "flushed between timed steps (512 MB write outside the events)"},
         "fwd_ms": fwd_mean, "bwd_ms": bwd_mean,

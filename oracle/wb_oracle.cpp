@@ -564,6 +564,77 @@ int or_grad(const or_robot* r, int B, const double* q, const double* qd, const d
   return 0;
 }
 
+// L (see loss) from one full forward evaluation in double: FK, sphere
+// centres, the brute-force minimum over every masked pair and the RNEA
+// torques, as or_eval computes them.
+static double full_loss(const or_robot& r, const double* q, const double* qd, const double* qdd,
+                        const double* fext, const double* gpose, const double* gsph,
+                        double gdmin, const double* gtau) {
+  std::vector<M3<double>> Rw;
+  std::vector<double> pw, c, tau(r.d);
+  fk(r, q, Rw, pw);
+  spheres(r, Rw, pw, c);
+  double dm = 0.0;
+  int w = -1;
+  self_collision(r, c, &dm, &w, nullptr);
+  rnea(r, q, qd, qdd, fext, tau.data());
+  double L = 0.0;
+  if (gpose)
+    for (int k = 0; k < r.n; ++k) {
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) L += gpose[12 * k + 3 * i + j] * Rw[k].a[i][j];
+      for (int i = 0; i < 3; ++i) L += gpose[12 * k + 9 + i] * pw[3 * k + i];
+    }
+  if (gsph)
+    for (int s = 0; s < 3 * r.S; ++s) L += gsph[s] * c[s];
+  if (gdmin != 0.0 && w >= 0) L += gdmin * dm;
+  if (gtau)
+    for (int j = 0; j < r.d; ++j) L += gtau[j] * tau[j];
+  return L;
+}
+
+// The same gradient as or_grad by central differences of full forward
+// evaluations: two at x +- h e_i for each of the 3d inputs per configuration
+// (with the forward evaluation at the point itself, 2*3d + 1 evaluations:
+// the gradient a CPU program without an adjoint would compute).  d_min
+// enters as the minimum over all pairs, so the difference is valid where no
+// other pair takes over the minimum within +-h.  Outputs gq, gqd, gqdd [B][d].
+int or_grad_fd(const or_robot* r, int B, const double* q, const double* qd, const double* qdd,
+               const double* fext, const double* gpose, const double* gsph, const double* gdmin,
+               const double* gtau, double h, double* gq, double* gqd, double* gqdd,
+               int nthreads) {
+  if (!(h > 0.0)) return -1;
+  int nt = threads_for(nthreads);
+  const int d = r->d;
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 1)
+  for (int b = 0; b < B; ++b) {
+    std::vector<double> x[3] = {std::vector<double>(q + (size_t)b * d, q + (size_t)(b + 1) * d),
+                                std::vector<double>(qd + (size_t)b * d, qd + (size_t)(b + 1) * d),
+                                std::vector<double>(qdd + (size_t)b * d,
+                                                    qdd + (size_t)(b + 1) * d)};
+    const double* gp = gpose ? gpose + (size_t)b * r->n * 12 : nullptr;
+    const double* gs = gsph ? gsph + (size_t)b * r->S * 3 : nullptr;
+    const double gdm = gdmin ? gdmin[b] : 0.0;
+    const double* gt = gtau ? gtau + (size_t)b * d : nullptr;
+    const double* fe = fext ? fext + (size_t)b * r->n * 6 : nullptr;
+    auto L = [&]() {
+      return full_loss(*r, x[0].data(), x[1].data(), x[2].data(), fe, gp, gs, gdm, gt);
+    };
+    double* out[3] = {gq, gqd, gqdd};
+    for (int which = 0; which < 3; ++which)
+      for (int j = 0; j < d; ++j) {
+        const double x0 = x[which][j];
+        x[which][j] = x0 + h;
+        const double lp = L();
+        x[which][j] = x0 - h;
+        const double lm = L();
+        x[which][j] = x0;
+        out[which][(size_t)b * d + j] = (lp - lm) / (2.0 * h);
+      }
+  }
+  return 0;
+}
+
 // Uniform cubic B-spline (Sec. 4, Eq. bspline-cubic).  U [n_traj][d][K]
 // control points; each trajectory is sampled at T uniformly spaced points over
 // its K-3 valid segments: t_s = s*(K-3)/(T-1), segment k = min(floor(t_s), K-4),

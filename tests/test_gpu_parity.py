@@ -166,6 +166,58 @@ def test_humanoid48_full_size_sampled(W, O):
         assert torch.isfinite(x).all()
 
 
+def _bench_step_sample(B, block_configs, k, seed):
+    """Sampled configurations of a full-size launch: the first and last 32
+    (the first and last warp groups), the last sweep block's tail, the
+    configurations on both sides of the first few block boundaries and k
+    random ones."""
+    rng = np.random.default_rng(seed)
+    last_block = (B - 1) // block_configs * block_configs
+    edges = [i * block_configs + o for i in range(1, 4) for o in (-1, 0)]
+    s = np.concatenate([np.arange(32), np.arange(B - 32, B), np.arange(last_block, B), edges,
+                        rng.choice(B, k, replace=False)])
+    return np.unique(s[(s >= 0) & (s < B)])
+
+
+@pytest.mark.parametrize("shape", ["autotuned", "fwd2x256_bwd2x448_pair4"])
+def test_humanoid48_bench_step_parity(W, O, shape):
+    """The humanoid48 step exactly as bench.py times it: 32768
+    configurations, forward sweep, pair stage and backward sweep with the
+    launch shapes bench.py takes (the library's autotuner at this batch, or
+    the shapes it picked on GB300: forward 2 segments x 256 threads, backward
+    2 segments x 448 threads = 147 blocks of 7 groups, 4 pair warps a block),
+    through bench.py's own launch functions; >= 256 sampled configurations
+    against the oracle (forward outputs and the three gradients)."""
+    import bench
+    desc, rob = robot(W, "R48")
+    B = CF.HUMANOID48.batch
+    if shape == "autotuned":
+        shapes = bench.humanoid48_launch(rob, B)
+    else:
+        shapes = bench.humanoid48_launch(rob, B, sweep_shape="2,256,2,448")
+        shapes["pair"] = W.Tune(kernel=3, blocks_per_sm=4)
+    q, qd, qdd = I.uniform_states(desc.dof, B, CF.HUMANOID48.seed)
+    gp, gs, gm, gt = I.upstream_grads(desc, B, seed=CF.HUMANOID48.seed + 1)
+    out = rob.empty_outputs(B)
+    gout = tuple(torch.empty((desc.dof, B), device="cuda") for _ in range(3))
+    bwd = shapes["bwd"]
+    groups_per_block = max(1, bwd.configs_per_block // 32 // max(1, bwd.lanes_per_config))
+    bench.humanoid48_step(rob, shapes, (cuda(q), cuda(qd), cuda(qdd)),
+                          (cuda(gp), cuda(gs), cuda(gm), cuda(gt)), out, gout)
+    torch.cuda.synchronize()
+    got = host(out)
+    s = _bench_step_sample(B, 32 * groups_per_block, 200, 12)
+    assert len(s) >= 256
+    ref = O.evaluate(desc, q[:, s], qd[:, s], qdd[:, s])
+    PY.check_forward(desc, got, ref, sample=s)
+    gref = O.gradient(desc, q[:, s], qd[:, s], qdd[:, s], gp[s], gs[s], gm[s], gt[:, s])
+    same = got["worst"][s] == ref["worst"]
+    assert same.mean() >= 0.95
+    PY.check_gradient([x.cpu().numpy()[:, s] for x in gout], gref, mask=same)
+    for x in gout:
+        assert torch.isfinite(x).all()
+
+
 def test_payload_via_set_inertials(W, O):
     """Runtime payload: 3 kg on each hand through wb_set_inertials."""
     desc = R.r48()

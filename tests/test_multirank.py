@@ -82,19 +82,42 @@ def test_reference_arm_runs_end_to_end_quickly():
     import json
     import subprocess
     import sys
+    import time
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    t0 = time.perf_counter()
     out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "4",
                           "--warmup", "1", "--ref-total-s", "2"], cwd=root, capture_output=True,
                          text=True, timeout=300)
+    wall = time.perf_counter() - t0
     assert out.returncode == 0, out.stderr[-2000:]
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["steps"] == 4
+    # ms_per_step is the measured time of a step's sample, not an extrapolation
+    n = line["config"]["sample_configs_per_step"]
+    assert 0 < n <= line["config"]["batch"]
+    assert line["steps"] * line["ms_per_step"] * 1e-3 < wall
+    assert line["value"] == pytest.approx(n / (line["ms_per_step"] * 1e-3), rel=1e-9)
+    assert line["e2e"]["value"] == line["value"]
+
+
+def test_cpu_baseline_reports_forward_and_fd_rates():
+    """cpu_baseline: forward + central-difference rate on all cores (value),
+    on one thread, the forward-only rates, the thread count, nproc and the
+    CPU model."""
+    import bench
+    from synthetic import robots as R
+    cb = bench.time_oracle(R.r7(), target_s=1.0)
+    assert cb["kind"] == "oracle" and cb["value"] > 0 and cb["threads_1"] > 0
+    assert cb["forward"]["threads_N"] > cb["value"] and cb["forward"]["threads_1"] > 0
+    assert cb["cores"] >= 1 and cb["nproc"] >= 1 and cb["cpu_model"]
+    assert "central-difference" in cb["pass"]
 
 
 def test_work_model_matches_the_documented_figures():
     """bench.py's algorithmic flops and bytes per evaluation, on the bench's
-    robots, are the closed forms of the design notes' work table."""
+    robots, are the closed forms of the work table (per kernel, in the link,
+    joint, sphere and pair counts)."""
     import bench
     from synthetic import inputs as I
     from synthetic import robots as R

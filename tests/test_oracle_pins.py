@@ -418,6 +418,26 @@ def test_dual_gradient_matches_central_differences(oracle_lib, mk):
             assert np.abs(g[:, b] - fd).max() <= 1e-7 * max(1.0, np.abs(fd).max())
 
 
+@pytest.mark.parametrize("mk", [R.r7, R.mixed_joint_tree, R.r23])
+def test_fd_gradient_matches_dual_gradient(oracle_lib, mk):
+    """The central-difference gradient of full forward evaluations (the CPU
+    fwd + bwd the benchmark times) equals the dual-number gradient, with
+    d_min as the minimum over every pair, at configurations whose worst pair
+    stays the minimum within the step."""
+    O = oracle_lib
+    rob = mk()
+    B = 4
+    q, qd, qdd = states(rob, B, 81)
+    gp, gs, gm, gt = I.upstream_grads(rob, B, 82)
+    dual = O.gradient(rob, q, qd, qdd, gp, gs, gm, gt, nthreads=1)
+    fd = O.gradient_fd(rob, q, qd, qdd, gp, gs, gm, gt, h=1e-6, nthreads=2)
+    for g, f in zip(dual, fd):
+        scale = np.maximum(np.abs(g).max(axis=0), 1.0)
+        assert (np.abs(g - f).max(axis=0) <= 1e-7 * scale).all()
+    with pytest.raises(ValueError):
+        O.gradient_fd(rob, q, qd, qdd, gp, gs, gm, gt, h=0.0)
+
+
 # ---------------------------------------------------------------------------
 # B-spline (Sec. 4)
 # ---------------------------------------------------------------------------
