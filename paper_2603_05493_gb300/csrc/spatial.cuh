@@ -123,6 +123,19 @@ __device__ __forceinline__ void xf_motion(const float* R, const float* p, const 
   rotT(R, t, out + 3);
 }
 
+// motion vector m (child coords) -> parent coords, the inverse of xf_motion:
+// X^-1 [w; u] = [R w ; R u + p x (R w)]
+__device__ __forceinline__ void xf_motion_inv(const float* R, const float* p, const float* m,
+                                              float* out) {
+  float pxw[3];
+  rot(R, m, out);
+  rot(R, m + 3, out + 3);
+  cross3(p, out, pxw);
+  out[3] += pxw[0];
+  out[4] += pxw[1];
+  out[5] += pxw[2];
+}
+
 // force vector f (child coords) -> parent coords (X^T f); the same map
 // carries adjoints of motion vectors back to the parent.
 __device__ __forceinline__ void xf_force_T(const float* R, const float* p, const float* f,

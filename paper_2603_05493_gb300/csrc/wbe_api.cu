@@ -737,6 +737,16 @@ int wb_load_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs* pa
     for (uint32_t x : H.bx)
       if ((x >> 16) != 0xFFFFu) full = 0;
     D.all_full = full;
+    int v4 = H.S % 4 == 0 ? 1 : 0;
+    for (int k = 0; k < n && v4; ++k) {
+      const int e0 = H.ls_start[k], e1 = H.ls_start[k + 1];
+      if ((e1 - e0) % 4) v4 = 0;
+      for (int e = e0; e < e1 && v4; ++e)
+        if (H.ls_sph[e] != H.ls_sph[e0 + (e - e0) / 4 * 4] + (e - e0) % 4 ||
+            H.ls_sph[e0 + (e - e0) / 4 * 4] % 4)
+          v4 = 0;
+    }
+    D.sph_vec4 = v4;
   }
   D.mimic_shared = H.mimic_shared;
   pk.add_vec(H.child_start, &D.child_start);

@@ -23,6 +23,9 @@ struct DevRobot {
   float etol;                // pair filter tolerance on the squared form (m^2)
   float rmin;                // smallest sphere radius
   int all_full;              // every pair block holds all 16 pairs
+  int sph_vec4;              // S % 4 == 0 and every link's spheres are runs of 4
+                             // consecutive indices from a multiple of 4: a link's
+                             // [B][S][3] rows load as float4 triples
   float abase[3];            // base acceleration = -gravity
 
   // per link
