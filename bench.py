@@ -8,6 +8,7 @@ configurations of the 48-DoF humanoid-shaped tree (1024 seeds x 32 timesteps
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--kernel tree|fused|plain] [--batch B] [--skip-cpu] [--skip-plain]
+                  [--skip-uneven]
                   [--workload humanoid48|trajopt48|uneven|kinematics]
                   [--collision worst|hinge] [--sweep-shape FS,FC,BS,BC]
                   [--ref-total-s T] [--ref-step-s S]
@@ -652,6 +653,18 @@ def run_ours(args, rank, world, local_rank):
             pb.append(b.elapsed_time(c))
         line["plain"] = {"value": B / ((np.mean(pf) + np.mean(pb)) * 1e-3), "unit": "evals/s",
                          "fwd_ms": float(np.mean(pf)), "bwd_ms": float(np.mean(pb))}
+    if args.kernel == "tree" and not args.skip_uneven:
+        # the uneven-batch workload (one GPU, rank 0): graph-replayed forward +
+        # backward with the batch's default and its autotuned launch choices
+        u = uneven_measure(rank, dev, 50, 3)
+        line["uneven"] = {
+            "workload": "256 x R7 + 256 x R23 + 256 x R48, horizons U{16..64}, fwd + bwd, "
+                        "one CUDA graph",
+            "value": u["configurations"] / (u["ms"] * 1e-3), "unit": "evals/s",
+            "ms_per_step": u["ms"], "configurations": u["configurations"],
+            "default_launch_value": u["configurations"] / (u["default_ms"] * 1e-3),
+            "default_launch_ms": u["default_ms"], "autotuned": u["autotuned"],
+            "default_launch": u["default"]}
     print(json.dumps(line), flush=True)
 
 
@@ -930,19 +943,17 @@ def run_kinematics(args, rank=0, world=1, local_rank=0):
         "gpu_launches": 2 * args.steps * world, "clocks": clocks.summary()}), flush=True)
 
 
-def run_uneven(args, rank=0, world=1, local_rank=0):
-    """Uneven batch: 256 x R7 + 256 x R23 + 256 x R48 problems with horizons
-    U{16..64}, forward (FK + RNEA, spheres + self-collision) and backward in
-    one persistent launch per pass, captured once in a CUDA graph and
-    replayed.  Value = configurations per second (sum of horizons / step)."""
+def uneven_measure(rank, dev, steps, warmup, clocks=None):
+    """The uneven workload: 256 x R7 + 256 x R23 + 256 x R48 problems with
+    horizons U{16..64}, forward (FK + RNEA, spheres + self-collision) and
+    backward in one persistent launch per pass, captured in a CUDA graph and
+    replayed; timed with the batch's default launch choices and again after
+    wb_batch_autotune (a graph captured anew for each).  Returns the times
+    and choices."""
     import torch
-    from paper_2603_05493_gb300 import build
-    build()
     from paper_2603_05493_gb300 import wbe
-    dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
     mix = I.uneven_mix()  # the same problem mix on every rank; states differ
-    robs = [wbe.Robot(d, device=local_rank) for d in mix.robots]
+    robs = [wbe.Robot(d, device=dev.index) for d in mix.robots]
     problems = list(zip(mix.robot_of.tolist(), mix.horizon.tolist()))
     batch = wbe.Batch(robs, problems)
     total = int(mix.horizon.sum())
@@ -970,43 +981,69 @@ def run_uneven(args, rank=0, world=1, local_rank=0):
     def step():
         batch.eval(q, qd, qdd, pose, sph, dmin, worst, tau)
         batch.eval_backward(q, qd, qdd, worst, gp, gs, gm, gt, *g)
-    side = torch.cuda.Stream()
-    side.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(side):
-        for _ in range(3):
-            step()
-    torch.cuda.current_stream().wait_stream(side)
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        step()
     flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
-    for _ in range(max(args.warmup, 3)):
-        graph.replay()
-    torch.cuda.synchronize()
+
+    def timed(n, clk=None):
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(3):
+                step()
+        torch.cuda.current_stream().wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        for _ in range(max(warmup, 3)):
+            graph.replay()
+        torch.cuda.synchronize()
+        if clk is not None:
+            clk.start()
+        ts = []
+        torch.cuda.nvtx.range_push("timed")
+        for i in range(n):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            graph.replay()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        torch.cuda.nvtx.range_pop()
+        if clk is not None:
+            clk.stop()
+        return float(np.mean(ts))
+    default = batch.get_tune()
+    ms_default = timed(max(3, steps // 2))
+    tune, fseg, bseg, fms, bms = batch.autotune()
+    ms = timed(steps, clocks)
+    names = [d.name for d in mix.robots]
+    return {"ms": ms, "configurations": total, "problems": len(problems),
+            "default_ms": ms_default,
+            "default": {"tune": default[0], "fwd_segments": dict(zip(names, default[1])),
+                        "bwd_segments": dict(zip(names, default[2]))},
+            "autotuned": {"tune": tune, "fwd_segments": dict(zip(names, fseg)),
+                          "bwd_segments": dict(zip(names, bseg)),
+                          "fwd_ms": fms, "bwd_ms": bms}}
+
+
+def run_uneven(args, rank=0, world=1, local_rank=0):
+    """Uneven batch: 256 x R7 + 256 x R23 + 256 x R48 problems with horizons
+    U{16..64}, forward and backward in one persistent launch per pass with the
+    launch choices of wb_batch_autotune, captured once in a CUDA graph and
+    replayed.  Value = configurations per second (sum of horizons / step)."""
+    import torch
+    from paper_2603_05493_gb300 import build
+    build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
     barrier(world)
     clocks = ClockSampler(local_rank)
-    clocks.start()
-    ts = []
-    torch.cuda.nvtx.range_push("timed")
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        graph.replay()
-        b.record()
-        torch.cuda.synchronize()
-        ts.append(a.elapsed_time(b))
-    torch.cuda.nvtx.range_pop()
-    clocks.stop()
+    u = uneven_measure(rank, dev, args.steps, args.warmup, clocks)
     barrier(world)
-    ms = reduce_max([float(np.mean(ts))], world, dev)[0]
+    ms, ms_default = reduce_max([u["ms"], u["default_ms"]], world, dev)
     if rank != 0:
         return
-    tunes = {}
-    for d, rob in zip(mix.robots, robs):
-        f, bw, fm, bm = rob.autotune(2048)
-        tunes[d.name] = {"fwd": f.__dict__, "bwd": bw.__dict__, "fwd_ms_2048": fm,
-                         "bwd_ms_2048": bm}
+    total = u["configurations"]
     print(json.dumps({
         "metric": "uneven-batch evals/s (R7/R23/R48 problems, fwd+bwd, one graph)",
         "value": job_value(world, total, ms), "unit": "evals/s", "n_gpus": world,
@@ -1014,10 +1051,12 @@ def run_uneven(args, rank=0, world=1, local_rank=0):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": "uneven: 256 x R7 + 256 x R23 + 256 x R48, horizons U{16..64}",
-                   "configurations": total, "problems": len(problems),
+                   "configurations": total, "problems": u["problems"],
                    "l2": "flushed between timed steps"},
-        "gpu_launches": 3 * args.steps * world, "clocks": clocks.summary(),
-        "autotune_single_robot_b2048": tunes}), flush=True)
+        "autotuned": u["autotuned"],
+        "default_launch": dict(u["default"], value=job_value(world, total, ms_default),
+                               ms_per_step=ms_default),
+        "gpu_launches": 3 * args.steps * world, "clocks": clocks.summary()}), flush=True)
 
 
 def main():
@@ -1030,6 +1069,8 @@ def main():
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-uneven", action="store_true",
+                    help="humanoid48: leave out the uneven-batch sub-result")
     ap.add_argument("--cpu-s", type=float, default=15.0)
     ap.add_argument("--ref-step-s", type=float, default=10.0,
                     help="reference arm: at most this many seconds of oracle work a step")

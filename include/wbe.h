@@ -341,6 +341,46 @@ int wb_batch_eval_backward(wb_batch* batch, const float* q, const float* qd, con
                            float* gqdd, void* stream);
 void wb_free_batch(wb_batch* batch);
 
+/* Launch choices of an uneven batch (Sec. 7, batched evaluation: the
+ * threads per configuration and the block shapes of the persistent launches,
+ * chosen per robot and per batch).  Per robot and pass, the sweep takes 1 or 2
+ * segments: 2 = the two warps of a pair sweep the two halves of the robot's
+ * depth-first order over the same 32 configurations (robots with a
+ * 2-segment plan only), 1 = each warp sweeps its own 32 configurations whole.
+ * Outputs do not depend on the choice beyond float summation order (the
+ * segments' shares of a shared ancestor are added in segment order). */
+typedef struct {
+  int32_t fwd_threads; /* threads per block of the forward sweep pass: 64, 128 or 256 (0 = 128) */
+  int32_t bwd_threads; /* the same for the backward sweep pass */
+  int32_t pair_warps;  /* warps per block of the pair pass, 1..8 (0 = the most that fit) */
+} wb_batch_tune;
+
+/* Set the batch's launch choices; fwd_segments and bwd_segments are host
+ * arrays of n_robots values (1 or 2), each nullable (= 2 where the robot has a
+ * 2-segment plan, else 1: wb_batch_create's defaults).  A set-up call: it
+ * uploads the batch's work lists with a synchronous copy; do not call it while
+ * the batch's work is in flight or during stream capture.  Errors: WB_EINVAL
+ * (bad value, 2 segments for a robot without a plan), WB_ETOOBIG (more pair
+ * warps than fit), WB_ECUDA. */
+int wb_batch_set_tune(wb_batch* batch, const wb_batch_tune* tune, const int32_t* fwd_segments,
+                      const int32_t* bwd_segments);
+/* The batch's current choices (each output nullable; segments: n_robots). */
+int wb_batch_get_tune(const wb_batch* batch, wb_batch_tune* tune, int32_t* fwd_segments,
+                      int32_t* bwd_segments);
+/* Autotuner of the batch (a set-up call like wb_autotune: it allocates scratch
+ * buffers of the batch's packed sizes, synchronises the device and must not
+ * be captured).  On deterministic states and upstream gradients it times the
+ * forward and backward sweep passes for every per-robot choice of 1 or 2
+ * segments (all combinations over the robots that have a 2-segment plan and a
+ * problem when there are at most 4, else one pass of coordinate descent from
+ * the defaults) in blocks of 64, 128 and 256 threads, and the pair pass with
+ * 2, 4 and 8 warps a block (those that fit), 5 runs per candidate after an L2
+ * flush (median); the fastest become the batch's choices for later calls and
+ * are returned (each output nullable), with the forward (sweep + pair) and
+ * backward times in ms.  Errors: WB_EINVAL, WB_ETOOBIG, WB_ECUDA. */
+int wb_batch_autotune(wb_batch* batch, wb_batch_tune* tune, int32_t* fwd_segments,
+                      int32_t* bwd_segments, float* fwd_ms, float* bwd_ms);
+
 /* ---------------------------------------------------------------------------
  * Trajectory-optimisation ends of the evaluation.  These calls take no robot:
  * every buffer must live on one device (the first non-NULL buffer fixes it),

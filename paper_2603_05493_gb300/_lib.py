@@ -73,6 +73,11 @@ class wb_batch_sizes(C.Structure):
                 ("n_problems", C.c_int32), ("n_robots", C.c_int32)]
 
 
+class wb_batch_tune(C.Structure):
+    _fields_ = [("fwd_threads", C.c_int32), ("bwd_threads", C.c_int32),
+                ("pair_warps", C.c_int32)]
+
+
 class wb_robot_info(C.Structure):
     _fields_ = [("n_links", C.c_int32), ("dof", C.c_int32), ("n_spheres", C.c_int32),
                 ("n_pairs", C.c_int32), ("n_levels", C.c_int32), ("max_level_width", C.c_int32),
@@ -104,6 +109,10 @@ SIGNATURES = {
     "wb_batch_eval": (C.c_int, [p, p, p, p, p, p, p, p, p, p]),
     "wb_batch_eval_backward": (C.c_int, [p, p, p, p, p, p, p, p, p, p, p, p, p]),
     "wb_free_batch": (None, [p]),
+    "wb_batch_set_tune": (C.c_int, [p, C.POINTER(wb_batch_tune), p, p]),
+    "wb_batch_get_tune": (C.c_int, [p, C.POINTER(wb_batch_tune), p, p]),
+    "wb_batch_autotune": (C.c_int, [p, C.POINTER(wb_batch_tune), p, p, C.POINTER(C.c_float),
+                                    C.POINTER(C.c_float)]),
     "wb_batch_eval_noalloc": (C.c_int, [p, C.c_int32, p, C.c_int32, p, p, p, p, p, p, p, p, p]),
     "wb_bspline_eval": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_float, p, p, p,
                                   p, p]),

@@ -23,27 +23,43 @@ __device__ __forceinline__ int warp_pull(int* counter, int lane) {
   return __shfl_sync(0xffffffffu, it, 0);
 }
 
-// Tree items (x = problem, y = first configuration, z = count <= 32) are
-// taken by pairs of warps: a block holds two pairs, and the two warps of a
-// pair sweep the two segments of the item's robot's 2-segment plan (the
+// Tree items (x = problem, y = first configuration, z = count, w = mode) are
+// taken by pairs of warps; a block holds blockDim.x / 64 pairs (1, 2 or 4,
+// chosen by the batch's tune).  Mode 0 (z <= 32): the two warps of the pair
+// sweep the two segments of the item's robot's 2-segment plan (the
 // segmented sweeps of tree_sweep.cuh: warp g replays the ancestors of its
-// first link, then sweeps its links).  The outputs of links both segments
+// first link, then sweeps its links); the outputs of links both segments
 // hold go to the pair's shared-memory partials and are summed in segment
 // order after the pair's barrier.  A robot without a 2-segment plan (a joint
-// driving several links) is swept whole by the pair's first warp.  The pair
-// shares the pulled item through shared memory; its barriers are named
-// barriers of 64 threads, and both warps leave the loop on the same item.
+// driving several links) is swept whole by the pair's first warp in mode 0.
+// Mode 1 (z <= 64): each warp sweeps its own 32 configurations of the item
+// whole (warp g takes configurations y + 32 g ...), the one-segment choice.
+// The mode is per robot (the batch's tune).  The pair shares the pulled item
+// through shared memory; its barriers are named barriers of 64 threads, and
+// both warps leave the loop on the same item.
 __device__ __forceinline__ void pair_bar(int id) {
   asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
 }
 
-// shared memory: one item slot per pair (32 words), then per pair the
-// partials [nout][ns_max][2][32]
-__host__ __device__ inline size_t batch_tree_words(int nout, int ns_max) {
-  return 32 + 2 * (size_t)nout * ns_max * 64;
+// shared memory: one item slot per pair (32 words, up to 32 pairs), then per
+// pair the partials [nout][ns_max][2][32]
+__host__ __device__ inline size_t batch_tree_words(int nout, int ns_max, int pairs) {
+  return 32 + (size_t)pairs * nout * ns_max * 64;
 }
 
-__global__ void __launch_bounds__(128) batch_tree_fwd_kernel(const DevRobot* robots,
+// the configuration a lane sweeps in item w, and whether it sweeps one:
+// mode 0 -- lane of the 32; the second warp only with a segment plan;
+// mode 1 -- configuration 32 g + lane of the 64
+__device__ __forceinline__ bool batch_lane(const int4& w, bool seg, int g, int lane, int64_t* b) {
+  if (w.w == 1) {
+    *b = (int64_t)w.y + 32 * g + lane;
+    return 32 * g + lane < w.z;
+  }
+  *b = (int64_t)w.y + lane;
+  return (seg || g == 0) && lane < w.z;
+}
+
+__global__ void __launch_bounds__(256) batch_tree_fwd_kernel(const DevRobot* robots,
                                                              const BatchProblemDev* probs,
                                                              const int4* items, int n_items,
                                                              int* counter, BatchIO io,
@@ -71,14 +87,15 @@ __global__ void __launch_bounds__(128) batch_tree_fwd_kernel(const DevRobot* rob
               nullptr,
               io.tau ? io.tau + pb.jo : nullptr,
               nullptr};
-    const int64_t b = (int64_t)w.y + lane;
-    const bool seg = r.seg_ok & 1;
+    const bool seg = w.w == 0 && (r.seg_ok & 1);
+    int64_t b;
+    const bool act = batch_lane(w, seg, g, lane, &b);
     const int ns = seg ? r.seg_ns[0] : 0;
     // one call site for both cases (a second inlined sweep would cost registers)
     const Seg sg = seg ? Seg{r.seg_pos[0][g], r.seg_pos[0][g + 1], g, 2, r.seg_slot, part, ns, lane}
                        : whole_sweep(r);
     for (int q = 0; q < ns; ++q) part[(q * 2 + g) * 32 + lane] = 0.0f;
-    if ((seg || g == 0) && lane < w.z) tree_fwd_seg(r, A, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b, sg);
+    if (act) tree_fwd_seg(r, A, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b, sg);
     pair_bar(bar);
     if (lane < w.z && A.tau)
       for (int q = g; q < ns; q += 2) {
@@ -90,7 +107,7 @@ __global__ void __launch_bounds__(128) batch_tree_fwd_kernel(const DevRobot* rob
 }
 
 // capped at 128 registers, as the single-robot backward sweeps
-__global__ void __launch_bounds__(128, 4) batch_tree_bwd_kernel(const DevRobot* robots,
+__global__ void __launch_bounds__(256, 2) batch_tree_bwd_kernel(const DevRobot* robots,
                                                              const BatchProblemDev* probs,
                                                              const int4* items, int n_items,
                                                              int* counter, BatchIO io,
@@ -120,15 +137,16 @@ __global__ void __launch_bounds__(128, 4) batch_tree_bwd_kernel(const DevRobot* 
               io.gq + pb.jo,
               io.gqd + pb.jo,
               io.gqdd + pb.jo};
-    const int64_t b = (int64_t)w.y + lane;
-    const bool seg = r.seg_ok & 1;
+    const bool seg = w.w == 0 && (r.seg_ok & 1);
+    int64_t b;
+    const bool act = batch_lane(w, seg, g, lane, &b);
     const int ns = seg ? r.seg_ns[0] : 0;
     const size_t o = (size_t)ns * 64;  // one output's partials
     const Seg sg = seg ? Seg{r.seg_pos[0][g], r.seg_pos[0][g + 1], g, 2, r.seg_slot, part, ns, lane}
                        : whole_sweep(r);
     for (int q = 0; q < ns; ++q)
       for (int k = 0; k < 3; ++k) part[k * o + (q * 2 + g) * 32 + lane] = 0.0f;
-    if ((seg || g == 0) && lane < w.z) tree_bwd_seg<false>(r, A, FusedCost{}, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b, sg);
+    if (act) tree_bwd_seg<false>(r, A, FusedCost{}, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b, sg);
     pair_bar(bar);
     if (lane < w.z)
       for (int q = g; q < ns; q += 2) {
@@ -184,37 +202,37 @@ __global__ void __launch_bounds__(256, 3) batch_pair_kernel(const DevRobot* robo
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-size_t batch_tree_smem(bool fwd, int ns_max) {
-  return sizeof(float) * batch_tree_words(fwd ? 1 : 3, ns_max);
+size_t batch_tree_smem(bool fwd, int ns_max, int threads) {
+  return sizeof(float) * batch_tree_words(fwd ? 1 : 3, ns_max, threads / 64);
 }
 
 cudaError_t launch_batch_tree_fwd(const DevRobot* robots, const BatchProblemDev* probs, const int4* items,
                                   int n_items, int* counter, const BatchIO& io, int grid,
-                                  int ns_max, cudaStream_t s) {
-  const size_t smem = batch_tree_smem(true, ns_max);
+                                  int ns_max, int threads, cudaStream_t s) {
+  const size_t smem = batch_tree_smem(true, ns_max, threads);
   cudaError_t e = cudaFuncSetAttribute(batch_tree_fwd_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  fit_carveout((const void*)batch_tree_fwd_kernel, 128, smem);
+  fit_carveout((const void*)batch_tree_fwd_kernel, threads, smem);
   e = cudaMemsetAsync(counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  batch_tree_fwd_kernel<<<grid, 128, smem, s>>>(robots, probs, items, n_items, counter, io,
-                                                ns_max);
+  batch_tree_fwd_kernel<<<grid, threads, smem, s>>>(robots, probs, items, n_items, counter, io,
+                                                    ns_max);
   return cudaGetLastError();
 }
 
 cudaError_t launch_batch_tree_bwd(const DevRobot* robots, const BatchProblemDev* probs, const int4* items,
                                   int n_items, int* counter, const BatchIO& io, int grid,
-                                  int ns_max, cudaStream_t s) {
-  const size_t smem = batch_tree_smem(false, ns_max);
+                                  int ns_max, int threads, cudaStream_t s) {
+  const size_t smem = batch_tree_smem(false, ns_max, threads);
   cudaError_t e = cudaFuncSetAttribute(batch_tree_bwd_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  fit_carveout((const void*)batch_tree_bwd_kernel, 128, smem);
+  fit_carveout((const void*)batch_tree_bwd_kernel, threads, smem);
   e = cudaMemsetAsync(counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  batch_tree_bwd_kernel<<<grid, 128, smem, s>>>(robots, probs, items, n_items, counter, io,
-                                                ns_max);
+  batch_tree_bwd_kernel<<<grid, threads, smem, s>>>(robots, probs, items, n_items, counter, io,
+                                                    ns_max);
   return cudaGetLastError();
 }
 
@@ -247,13 +265,15 @@ cudaError_t batch_pair_max_blocks_per_sm(int warps, int ws_words, int rad_words,
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_pair_kernel, warps * 32, smem);
 }
 
-cudaError_t batch_tree_max_blocks_per_sm(bool fwd, int ns_max, int* out) {
-  const size_t smem = batch_tree_smem(fwd, ns_max);
+cudaError_t batch_tree_max_blocks_per_sm(bool fwd, int ns_max, int threads, int* out) {
+  const size_t smem = batch_tree_smem(fwd, ns_max, threads);
   cudaError_t e = cudaFuncSetAttribute(fwd ? batch_tree_fwd_kernel : batch_tree_bwd_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return fwd ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_tree_fwd_kernel, 128, smem)
-             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_tree_bwd_kernel, 128, smem);
+  return fwd ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_tree_fwd_kernel, threads,
+                                                             smem)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_tree_bwd_kernel, threads,
+                                                             smem);
 }
 
 int pair_plan_words(const DevRobot& r) { return PairPlan(r.n, r.Sg, r.P, false).total; }

@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(1024) noalloc_setup_kernel(const __grid_consta
     const int qh = plan.prob[q] & 0xFFFFFF;
     T.pitems[plan.pstart[q] + c] = make_int2(q, c);
     if ((c & 31) == 0)
-      T.titems[plan.tstart[q] + (c >> 5)] = make_int4(q, c, min(32, qh - c), plan.prob[q] >> 24);
+      T.titems[plan.tstart[q] + (c >> 5)] = make_int4(q, c, min(32, qh - c), 0);  // mode 0
   }
 }
 

@@ -1473,17 +1473,68 @@ struct wb_batch {
   const DevRobot* d_robots = nullptr;
   const PairSchedule32* d_scheds = nullptr;
   const BatchProblemDev* d_probs = nullptr;
-  const int4* d_titems = nullptr;
+  int4* d_titems[2] = {nullptr, nullptr};  // sweep items of the forward, backward pass
   const int2* d_pitems = nullptr;
   const int* d_counters = nullptr;
-  int n_titems = 0, n_pitems = 0;
+  int n_titems[2] = {0, 0};
+  int cap_titems = 0;  // capacity of each sweep item list
+  int n_pitems = 0;
   int ws_words = 0, rad_words = 0;
-  int ns_max = 0;  // most shared slots among the robots' 2-segment sweep plans
+  int ns_max = 0;  // most shared slots among the used robots' 2-segment sweep plans
   wb_batch_sizes sizes{};
+  // launch choices (wb_batch_set_tune / wb_batch_autotune): threads per block
+  // of the forward and backward sweep passes, warps per block of the pair
+  // pass (0 = the most that fit) and, per robot and pass, the sweep segments
+  int threads[2] = {128, 128};
+  int pair_warps = 0;
+  std::vector<int> seg[2];
 };
 
 // the most shared output slots among these robots' 2-segment sweep plans
 static int seg2_slots(const DevRobot& D) { return (D.seg_ok & 1) ? D.seg_ns[0] : 0; }
+
+// default sweep segments of a robot: its 2-segment plan where it has one
+static int default_segments(const DevRobot& D) { return (D.seg_ok & 1) ? 2 : 1; }
+
+// Sweep items of a batch for per-robot segments (1 or 2), longest first: two
+// segments sweep items of up to 32 configurations (mode 0), one segment
+// items of up to 64 (mode 1, a warp each for 32); a robot without a
+// 2-segment plan swept in mode 0 leaves the pair's second warp idle, so it
+// always takes mode 1.
+static std::vector<int4> batch_sweep_items(const wb_batch* Bt, const std::vector<int>& seg) {
+  std::vector<int4> items;
+  std::vector<int> cost;
+  for (size_t p = 0; p < Bt->probs.size(); ++p) {
+    const int ri = Bt->probs[p].robot, H = Bt->probs[p].H;
+    const DevRobot& D = Bt->robots[ri]->dev;
+    const bool two = seg[ri] == 2 && (D.seg_ok & 1);
+    const int per = two ? 32 : 64;
+    for (int c = 0; c < H; c += per) {
+      items.push_back(make_int4((int)p, c, std::min(per, H - c), two ? 0 : 1));
+      // links a warp walks: half the tree plus the replayed ancestors, or all
+      cost.push_back(two ? (D.n + 1) / 2 + D.maxdepth / 2 : D.n);
+    }
+  }
+  std::vector<int> order(items.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<int4> out;
+  for (int i : order) out.push_back(items[i]);
+  return out;
+}
+
+// upload the sweep items of pass (0 forward, 1 backward) for the batch's
+// current segments (a setup-time copy)
+static int batch_upload_items(wb_batch* Bt, int pass) {
+  std::vector<int4> it = batch_sweep_items(Bt, Bt->seg[pass]);
+  if ((int)it.size() > Bt->cap_titems) return fail(WB_ECUDA, "sweep items exceed capacity");
+  Bt->n_titems[pass] = Bt->sizes.configs > 0 ? (int)it.size() : 0;
+  if (it.empty()) return WB_OK;
+  DeviceGuard guard(Bt->device);
+  cudaError_t e =
+      cudaMemcpy(Bt->d_titems[pass], it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? WB_OK : cuda_fail(e, "batch item upload");
+}
 
 extern "C" {
 
@@ -1505,8 +1556,9 @@ int wb_batch_create(wb_robot* const* robots, int32_t n_robots, const wb_problem*
   Bt->device = dev;
   Bt->num_sms = robots[0]->num_sms;
   Bt->robots.assign(robots, robots + n_robots);
+  for (int pass = 0; pass < 2; ++pass)
+    for (int i = 0; i < n_robots; ++i) Bt->seg[pass].push_back(default_segments(robots[i]->dev));
   int64_t jo = 0, po = 0, so = 0, co = 0;
-  std::vector<int4> titems;
   std::vector<int2> pitems;
   for (int p = 0; p < n_problems; ++p) {
     const int ri = problems[p].robot, H = problems[p].horizon;
@@ -1524,16 +1576,14 @@ int wb_batch_create(wb_robot* const* robots, int32_t n_robots, const wb_problem*
     po += (int64_t)H * D.n * 12;
     so += (int64_t)H * D.S * 3;
     co += H;
-    for (int c = 0; c < H; c += 32) titems.push_back(make_int4(p, c, std::min(32, H - c), ri));
+    Bt->cap_titems += (H + 31) / 32;
     for (int c = 0; c < H; ++c) pitems.push_back(make_int2(p, c));
     Bt->ws_words = std::max(Bt->ws_words, pair_plan_words(D));
     Bt->rad_words = std::max(Bt->rad_words, (4 * D.Sg + 31) & ~31);
     Bt->ns_max = std::max(Bt->ns_max, seg2_slots(D));
   }
+  Bt->sizes = wb_batch_sizes{jo, po, so, co, n_problems, n_robots};
   // longest work first
-  auto tcost = [&](const int4& w) { return robots[w.w]->dev.n; };
-  std::stable_sort(titems.begin(), titems.end(),
-                   [&](const int4& a, const int4& b) { return tcost(a) > tcost(b); });
   auto pcost = [&](const int2& w) { return robots[Bt->probs[w.x].robot]->dev.P; };
   std::stable_sort(pitems.begin(), pitems.end(),
                    [&](const int2& a, const int2& b) { return pcost(a) > pcost(b); });
@@ -1544,18 +1594,18 @@ int wb_batch_create(wb_robot* const* robots, int32_t n_robots, const wb_problem*
     dss.push_back(robots[i]->sched32);
   }
   std::vector<int> counters(4, 0);
-  if (titems.empty()) titems.push_back(make_int4(0, 0, 0, 0));
+  std::vector<int4> titems(std::max(Bt->cap_titems, 1), make_int4(0, 0, 0, 0));
   if (pitems.empty()) pitems.push_back(make_int2(0, 0));
   std::vector<BatchProblemDev> probs_dev = Bt->probs;
   if (probs_dev.empty()) probs_dev.push_back(BatchProblemDev{0, 0, 0, 0, 0, 0});
-  Bt->n_titems = n_problems ? (int)titems.size() : 0;
   Bt->n_pitems = co > 0 ? (int)pitems.size() : 0;
-  if (co == 0) Bt->n_titems = 0;
+  const int4* tslot[2] = {nullptr, nullptr};
   Packer pk;
   pk.add_vec(drs, &Bt->d_robots);
   pk.add_vec(dss, &Bt->d_scheds);
   pk.add_vec(probs_dev, &Bt->d_probs);
-  pk.add_vec(titems, &Bt->d_titems);
+  pk.add_vec(titems, &tslot[0]);
+  pk.add_vec(titems, &tslot[1]);
   pk.add_vec(pitems, &Bt->d_pitems);
   pk.add_vec(counters, &Bt->d_counters);
   DeviceGuard guard(dev);
@@ -1568,7 +1618,15 @@ int wb_batch_create(wb_robot* const* robots, int32_t n_robots, const wb_problem*
     return cuda_fail(e, "batch upload");
   }
   for (auto& it : pk.items) *it.slot = static_cast<char*>(Bt->dmem) + it.off;
-  Bt->sizes = wb_batch_sizes{jo, po, so, co, n_problems, n_robots};
+  Bt->d_titems[0] = const_cast<int4*>(tslot[0]);
+  Bt->d_titems[1] = const_cast<int4*>(tslot[1]);
+  for (int pass = 0; pass < 2; ++pass) {
+    const int rc = batch_upload_items(Bt, pass);
+    if (rc) {
+      wb_free_batch(Bt);
+      return rc;
+    }
+  }
   *out = Bt;
   return WB_OK;
 }
@@ -1601,12 +1659,21 @@ void wb_free_batch(wb_batch* batch) {
 }
 
 static int batch_grid_tree(const wb_batch* Bt, bool fwd, int* grid) {
+  const int pass = fwd ? 0 : 1, threads = Bt->threads[pass];
   int bps = 0;
-  cudaError_t e = batch_tree_max_blocks_per_sm(fwd, Bt->ns_max, &bps);
+  cudaError_t e = batch_tree_max_blocks_per_sm(fwd, Bt->ns_max, threads, &bps);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
-  const int need = (Bt->n_titems + 1) / 2;  // two pairs of warps per block, an item per pair
-  *grid = std::max(1, std::min(need, std::max(bps, 1) * Bt->num_sms));
+  if (bps < 1) return fail(WB_ETOOBIG, "batch sweep block of %d threads does not fit", threads);
+  const int pairs = threads / 64;  // an item per pair of warps
+  const int need = (Bt->n_titems[pass] + pairs - 1) / pairs;
+  *grid = std::max(1, std::min(need, bps * Bt->num_sms));
   return WB_OK;
+}
+
+// the pair pass's warps per block: the batch's choice, or the most that fit
+static int batch_pair_warps(const wb_batch* Bt) {
+  const int most = warps_that_fit(0, batch_pair_smem(Bt->ws_words, Bt->rad_words, 1));
+  return Bt->pair_warps > 0 ? std::min(Bt->pair_warps, most) : most;
 }
 
 int wb_batch_eval(wb_batch* batch, const float* q, const float* qd, const float* qdd,
@@ -1636,12 +1703,13 @@ int wb_batch_eval(wb_batch* batch, const float* q, const float* qd, const float*
   if (link_pose || tau) {
     int grid = 1;
     if ((rc = batch_grid_tree(batch, true, &grid))) return rc;
-    e = launch_batch_tree_fwd(batch->d_robots, batch->d_probs, batch->d_titems, batch->n_titems,
-                              counters, io, grid, batch->ns_max, s);
+    e = launch_batch_tree_fwd(batch->d_robots, batch->d_probs, batch->d_titems[0],
+                              batch->n_titems[0], counters, io, grid, batch->ns_max,
+                              batch->threads[0], s);
     if (e != cudaSuccess) return cuda_fail(e, "wb_batch_eval launch");
   }
   if (pairs && batch->n_pitems > 0) {
-    const int warps = warps_that_fit(0, batch_pair_smem(batch->ws_words, batch->rad_words, 1));
+    const int warps = batch_pair_warps(batch);
     if (warps == 0) return fail(WB_ETOOBIG, "batch pair kernel does not fit on an SM");
     int bps = 0;
     e = batch_pair_max_blocks_per_sm(warps, batch->ws_words, batch->rad_words, &bps);
@@ -1682,11 +1750,58 @@ int wb_batch_eval_backward(wb_batch* batch, const float* q, const float* qd, con
              g_pose, g_sphere, g_dmin, g_tau, gq, gqd, gqdd};
   int grid = 1;
   if ((rc = batch_grid_tree(batch, false, &grid))) return rc;
-  cudaError_t e = launch_batch_tree_bwd(batch->d_robots, batch->d_probs, batch->d_titems,
-                                        batch->n_titems, const_cast<int*>(batch->d_counters) + 2,
-                                        io, grid, batch->ns_max,
+  cudaError_t e = launch_batch_tree_bwd(batch->d_robots, batch->d_probs, batch->d_titems[1],
+                                        batch->n_titems[1], const_cast<int*>(batch->d_counters) + 2,
+                                        io, grid, batch->ns_max, batch->threads[1],
                                         static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "wb_batch_eval_backward launch");
+  return WB_OK;
+}
+
+int wb_batch_set_tune(wb_batch* batch, const wb_batch_tune* tune, const int32_t* fwd_segments,
+                      const int32_t* bwd_segments) {
+  g_err.clear();
+  if (!batch) return fail(WB_EINVAL, "batch is NULL");
+  const int nr = (int)batch->robots.size();
+  wb_batch_tune t = tune ? *tune : wb_batch_tune{0, 0, 0};
+  for (int x : {t.fwd_threads, t.bwd_threads})
+    if (x != 0 && x != 64 && x != 128 && x != 256)
+      return fail(WB_EINVAL, "sweep threads per block %d: 0, 64, 128 or 256", x);
+  if (t.pair_warps < 0 || t.pair_warps > 8)
+    return fail(WB_EINVAL, "pair warps per block %d: 0..8", t.pair_warps);
+  const int most = warps_that_fit(0, batch_pair_smem(batch->ws_words, batch->rad_words, 1));
+  if (t.pair_warps > most)
+    return fail(WB_ETOOBIG, "%d pair warps per block do not fit (at most %d)", t.pair_warps, most);
+  const int32_t* segs[2] = {fwd_segments, bwd_segments};
+  std::vector<int> next[2];
+  for (int pass = 0; pass < 2; ++pass)
+    for (int i = 0; i < nr; ++i) {
+      const DevRobot& D = batch->robots[i]->dev;
+      const int g = segs[pass] ? segs[pass][i] : default_segments(D);
+      if (g != 1 && g != 2) return fail(WB_EINVAL, "robot %d: %d segments (1 or 2)", i, g);
+      if (g == 2 && !(D.seg_ok & 1))
+        return fail(WB_EINVAL, "robot %d has no 2-segment sweep plan", i);
+      next[pass].push_back(g);
+    }
+  batch->threads[0] = t.fwd_threads ? t.fwd_threads : 128;
+  batch->threads[1] = t.bwd_threads ? t.bwd_threads : 128;
+  batch->pair_warps = t.pair_warps;
+  for (int pass = 0; pass < 2; ++pass) {
+    batch->seg[pass] = next[pass];
+    const int rc = batch_upload_items(batch, pass);
+    if (rc) return rc;
+  }
+  return WB_OK;
+}
+
+int wb_batch_get_tune(const wb_batch* batch, wb_batch_tune* tune, int32_t* fwd_segments,
+                      int32_t* bwd_segments) {
+  if (!batch) return fail(WB_EINVAL, "batch is NULL");
+  if (tune) *tune = wb_batch_tune{batch->threads[0], batch->threads[1], batch->pair_warps};
+  for (size_t i = 0; i < batch->robots.size(); ++i) {
+    if (fwd_segments) fwd_segments[i] = batch->seg[0][i];
+    if (bwd_segments) bwd_segments[i] = batch->seg[1][i];
+  }
   return WB_OK;
 }
 
@@ -1902,16 +2017,19 @@ int wb_batch_eval_noalloc(wb_robot* const* robots, int32_t n_robots, const wb_pr
   plan.n_robots = n_robots;
   plan.n_problems = n_problems;
   plan.n_configs = (int)configs;
-  int ws_words = 0, rad_words = 0;
+  int ws_words = 0, rad_words = 0, ns_max = 0;
   for (int i = 0; i < n_robots; ++i) {
     plan.robots[i] = robots[i]->dev;
     plan.scheds[i] = robots[i]->sched32;
   }
+  // shared-memory sizes over the robots that some problem uses, as
+  // wb_batch_create takes them
   for (int p = 0; p < n_problems; ++p) {
     const DevRobot& D = robots[problems[p].robot]->dev;
     plan.prob[p] = problems[p].robot << 24 | problems[p].horizon;
     ws_words = std::max(ws_words, pair_plan_words(D));
     rad_words = std::max(rad_words, (4 * D.Sg + 31) & ~31);
+    ns_max = std::max(ns_max, seg2_slots(D));
   }
   // longest work first: robots by cost (stable), problems in order within one
   int n_titems = 0, n_pitems = 0;
@@ -1948,14 +2066,12 @@ int wb_batch_eval_noalloc(wb_robot* const* robots, int32_t n_robots, const wb_pr
   BatchIO io{q, qd, qdd, link_pose, sphere, d_min, worst_pair, tau,
              nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   if (link_pose || tau) {
-    int ns_max = 0;
-    for (int i = 0; i < n_robots; ++i) ns_max = std::max(ns_max, seg2_slots(robots[i]->dev));
     int bps = 0;
-    e = batch_tree_max_blocks_per_sm(true, ns_max, &bps);
+    e = batch_tree_max_blocks_per_sm(true, ns_max, 128, &bps);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     const int grid = std::max(1, std::min((n_titems + 1) / 2, std::max(bps, 1) * R0->num_sms));
     e = launch_batch_tree_fwd(T.robots, T.probs, T.titems, n_titems, T.counters, io, grid, ns_max,
-                              s);
+                              128, s);
     if (e != cudaSuccess) return cuda_fail(e, "wb_batch_eval_noalloc launch");
   }
   if (pairs) {
@@ -2244,5 +2360,175 @@ extern "C" int wb_autotune_spline(wb_robot* robot, int64_t n_traj, int32_t K, in
   *bwd = bb;
   if (fwd_ms) *fwd_ms = best_f;
   if (bwd_ms) *bwd_ms = best_b;
+  return WB_OK;
+}
+
+// Autotuner of an uneven batch: times, on the batch's own packed sizes with
+// deterministic states and upstream gradients, the sweep passes for every
+// per-robot choice of 1 or 2 segments (all combinations of the robots that
+// have a 2-segment plan and a problem, up to 4 of them; beyond that one pass
+// of coordinate descent from the defaults) in blocks of 64, 128 and 256
+// threads, and the pair pass with 2, 4 and 8 warps a block (as many as fit),
+// each 5 times after an L2 flush (median), and keeps the fastest for the
+// batch's later calls.
+extern "C" int wb_batch_autotune(wb_batch* batch, wb_batch_tune* tune, int32_t* fwd_segments,
+                                 int32_t* bwd_segments, float* fwd_ms, float* bwd_ms) {
+  g_err.clear();
+  if (!batch) return fail(WB_EINVAL, "batch is NULL");
+  const wb_batch_sizes z = batch->sizes;
+  const int nr = (int)batch->robots.size();
+  float best[2] = {0.0f, 0.0f}, best_pair = 0.0f;
+  if (z.configs > 0) {
+    DeviceGuard guard(batch->device);
+    Scratch sc;
+    float* q = sc.get<float>(z.joint_elems);
+    float* qd = sc.get<float>(z.joint_elems);
+    float* qdd = sc.get<float>(z.joint_elems);
+    float* tau = sc.get<float>(z.joint_elems);
+    float* gtau = sc.get<float>(z.joint_elems);
+    float* gq = sc.get<float>(z.joint_elems);
+    float* gqd = sc.get<float>(z.joint_elems);
+    float* gqdd = sc.get<float>(z.joint_elems);
+    float* pose = sc.get<float>(z.pose_elems);
+    float* gpose = sc.get<float>(z.pose_elems);
+    float* sph = sc.get<float>(z.sphere_elems);
+    float* gsph = sc.get<float>(z.sphere_elems);
+    float* dmin = sc.get<float>(z.configs);
+    float* gdmin = sc.get<float>(z.configs);
+    int32_t* worst = sc.get<int32_t>(z.configs);
+    if (!q || !qd || !qdd || !tau || !gtau || !gq || !gqd || !gqdd || !pose || !gpose || !sph ||
+        !gsph || !dmin || !gdmin || !worst)
+      return fail(WB_ECUDA, "batch autotune scratch");
+    {  // deterministic states: q in [-pi, pi], rates in [-2, 2] and [-5, 5], grads in [-1, 1]
+      const int64_t most = std::max({z.joint_elems, z.pose_elems, z.sphere_elems, z.configs});
+      std::vector<float> h((size_t)most);
+      uint64_t st = 0xD1B54A32D192ED03ull;
+      auto fill = [&](float* dst, int64_t n, float scale) {
+        for (int64_t i = 0; i < n; ++i) {
+          st = st * 6364136223846793005ull + 1442695040888963407ull;
+          h[(size_t)i] = scale * ((float)((st >> 40) * (1.0 / 16777216.0)) * 2.0f - 1.0f);
+        }
+        return cudaMemcpy(dst, h.data(), (size_t)n * sizeof(float), cudaMemcpyHostToDevice);
+      };
+      cudaError_t e = fill(q, z.joint_elems, 3.14159265f);
+      if (e == cudaSuccess) e = fill(qd, z.joint_elems, 2.0f);
+      if (e == cudaSuccess) e = fill(qdd, z.joint_elems, 5.0f);
+      if (e == cudaSuccess) e = fill(gtau, z.joint_elems, 1.0f);
+      if (e == cudaSuccess) e = fill(gpose, z.pose_elems, 1.0f);
+      if (e == cudaSuccess) e = fill(gsph, z.sphere_elems, 1.0f);
+      if (e == cudaSuccess) e = fill(gdmin, z.configs, 1.0f);
+      if (e != cudaSuccess) return cuda_fail(e, "batch autotune inputs");
+    }
+    TuneClock clk;
+    if (!clk.init(sc, batch->device)) return fail(WB_ECUDA, "batch autotune stream/events");
+    cudaStream_t s = clk.s;
+    int* counters = const_cast<int*>(batch->d_counters);
+    BatchIO io{q, qd, qdd, pose, sph, dmin, worst, tau, gpose, gsph, gdmin, gtau, gq, gqd, gqdd};
+    auto sweep = [&](int pass) -> int {
+      int grid = 1, rc;
+      if ((rc = batch_grid_tree(batch, pass == 0, &grid))) return rc;
+      cudaError_t e =
+          pass == 0
+              ? launch_batch_tree_fwd(batch->d_robots, batch->d_probs, batch->d_titems[0],
+                                      batch->n_titems[0], counters, io, grid, batch->ns_max,
+                                      batch->threads[0], s)
+              : launch_batch_tree_bwd(batch->d_robots, batch->d_probs, batch->d_titems[1],
+                                      batch->n_titems[1], counters + 2, io, grid, batch->ns_max,
+                                      batch->threads[1], s);
+      return e == cudaSuccess ? WB_OK : cuda_fail(e, "batch autotune launch");
+    };
+    // robots whose segments are a choice: a 2-segment plan and some problem
+    std::vector<int> used(nr, 0), free_r;
+    for (const BatchProblemDev& pb : batch->probs)
+      if (pb.H > 0) used[pb.robot] = 1;
+    for (int i = 0; i < nr; ++i)
+      if (used[i] && (batch->robots[i]->dev.seg_ok & 1)) free_r.push_back(i);
+    for (int pass = 0; pass < 2; ++pass) {
+      std::vector<int> cur = batch->seg[pass], bseg = cur;
+      int bthr = batch->threads[pass];
+      float bt = 1e30f;
+      auto trial = [&](const std::vector<int>& seg) -> int {
+        batch->seg[pass] = seg;
+        int rc = batch_upload_items(batch, pass);
+        if (rc) return rc;
+        for (int thr : {64, 128, 256}) {
+          batch->threads[pass] = thr;
+          if (sweep(pass) != WB_OK) {  // a block that does not fit is not a candidate
+            g_err.clear();
+            cudaGetLastError();
+            continue;
+          }
+          const float m = clk.time([&]() { return sweep(pass); });
+          if (m < bt) {
+            bt = m;
+            bseg = seg;
+            bthr = thr;
+          }
+        }
+        return WB_OK;
+      };
+      int rc;
+      if (free_r.size() <= 4) {
+        for (int mask = 0; mask < (1 << free_r.size()); ++mask) {
+          std::vector<int> seg = cur;
+          for (size_t k = 0; k < free_r.size(); ++k) seg[free_r[k]] = (mask >> k) & 1 ? 2 : 1;
+          if ((rc = trial(seg))) return rc;
+        }
+      } else {
+        if ((rc = trial(cur))) return rc;
+        for (int i : free_r) {
+          std::vector<int> seg = bseg;
+          seg[i] = 3 - seg[i];
+          if ((rc = trial(seg))) return rc;
+        }
+      }
+      if (bt >= 1e30f) return fail(WB_ETOOBIG, "no batch sweep shape fits");
+      batch->seg[pass] = bseg;
+      batch->threads[pass] = bthr;
+      if ((rc = batch_upload_items(batch, pass))) return rc;
+      best[pass] = bt;
+    }
+    // the pair pass on the poses of the tuned forward sweep
+    int rc;
+    if ((rc = sweep(0))) return rc;
+    if (batch->n_pitems > 0) {
+      const int most = warps_that_fit(0, batch_pair_smem(batch->ws_words, batch->rad_words, 1));
+      float bp = 1e30f;
+      int bw = 0;
+      for (int w : {2, 4, 8}) {
+        if (w > most) continue;
+        int bps = 0;
+        if (batch_pair_max_blocks_per_sm(w, batch->ws_words, batch->rad_words, &bps) !=
+                cudaSuccess ||
+            bps < 1) {
+          cudaGetLastError();
+          continue;
+        }
+        const int grid = std::min((batch->n_pitems + w - 1) / w, bps * batch->num_sms);
+        auto run = [&]() {
+          return launch_batch_pair(batch->d_robots, batch->d_scheds, batch->d_probs,
+                                   batch->d_pitems, batch->n_pitems, counters + 1, io, grid, w,
+                                   batch->ws_words, batch->rad_words, s);
+        };
+        if (run() != cudaSuccess) {
+          cudaGetLastError();
+          continue;
+        }
+        const float m = clk.time(run);
+        if (m < bp) {
+          bp = m;
+          bw = w;
+        }
+      }
+      batch->pair_warps = bw;
+      best_pair = bp < 1e30f ? bp : 0.0f;
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "batch autotune");
+  }
+  g_err.clear();
+  wb_batch_get_tune(batch, tune, fwd_segments, bwd_segments);
+  if (fwd_ms) *fwd_ms = best[0] + best_pair;
+  if (bwd_ms) *bwd_ms = best[1];
   return WB_OK;
 }

@@ -183,13 +183,19 @@ struct BatchIO {
   float* gqdd;
 };
 
-// ns_max: the most shared output slots among the robots' 2-segment plans
+// Sweep items of an uneven batch: x = problem, y = first configuration,
+// z = count, w = mode (0: the two warps of a pair sweep the two segments of
+// the robot's 2-segment plan over <= 32 configurations, or the first warp the
+// whole tree when the robot has no plan; 1: each warp of the pair sweeps its
+// own 32 of <= 64 configurations whole).  ns_max: the most shared output
+// slots among the robots' 2-segment plans; threads: 64, 128 or 256 (pairs of
+// warps per block).
 cudaError_t launch_batch_tree_fwd(const DevRobot* robots, const BatchProblemDev* probs,
                                   const int4* items, int n_items, int* counter, const BatchIO& io,
-                                  int grid, int ns_max, cudaStream_t s);
+                                  int grid, int ns_max, int threads, cudaStream_t s);
 cudaError_t launch_batch_tree_bwd(const DevRobot* robots, const BatchProblemDev* probs,
                                   const int4* items, int n_items, int* counter, const BatchIO& io,
-                                  int grid, int ns_max, cudaStream_t s);
+                                  int grid, int ns_max, int threads, cudaStream_t s);
 cudaError_t launch_batch_pair(const DevRobot* robots, const PairSchedule32* scheds,
                               const BatchProblemDev* probs, const int2* items, int n_items,
                               int* counter, const BatchIO& io, int grid, int warps, int ws_words,
@@ -224,7 +230,7 @@ __host__ __device__ NoAllocTables noalloc_tables(unsigned char* base);
 cudaError_t noalloc_scratch(int device, unsigned char** out);
 cudaError_t launch_noalloc_setup(const NoAllocPlan& plan, unsigned char* base, int grid,
                                  cudaStream_t s);
-cudaError_t batch_tree_max_blocks_per_sm(bool fwd, int ns_max, int* out);
+cudaError_t batch_tree_max_blocks_per_sm(bool fwd, int ns_max, int threads, int* out);
 int pair_plan_words(const DevRobot& r);
 
 // launchers (return cudaGetLastError())

@@ -408,6 +408,40 @@ class Batch:
         n = int(np.prod(shape))
         return packed[o:o + n].view(*shape)
 
+    def set_tune(self, fwd_threads=0, bwd_threads=0, pair_warps=0, fwd_segments=None,
+                 bwd_segments=None):
+        """Launch choices of the batch's passes (wb_batch_set_tune): sweep
+        threads per block, pair warps per block, and per robot 1 or 2 sweep
+        segments for each pass (None = the defaults)."""
+        t = L.wb_batch_tune(int(fwd_threads), int(bwd_threads), int(pair_warps))
+        segs = [None if x is None else np.ascontiguousarray(x, dtype=np.int32)
+                for x in (fwd_segments, bwd_segments)]
+        L.check(self.lib.wb_batch_set_tune(self.handle, C.byref(t),
+                                           *[None if x is None else x.ctypes.data for x in segs]),
+                "wb_batch_set_tune")
+
+    def get_tune(self):
+        """(wb_batch_tune as a dict, forward segments, backward segments)."""
+        t = L.wb_batch_tune()
+        f = np.zeros(len(self.robots), np.int32)
+        b = np.zeros(len(self.robots), np.int32)
+        L.check(self.lib.wb_batch_get_tune(self.handle, C.byref(t), f.ctypes.data, b.ctypes.data),
+                "wb_batch_get_tune")
+        return {k: getattr(t, k) for k, _ in L.wb_batch_tune._fields_}, f.tolist(), b.tolist()
+
+    def autotune(self):
+        """Time the batch's launch choices and keep the fastest
+        (wb_batch_autotune); returns (tune dict, forward segments, backward
+        segments, forward ms, backward ms)."""
+        t = L.wb_batch_tune()
+        f = np.zeros(len(self.robots), np.int32)
+        b = np.zeros(len(self.robots), np.int32)
+        fm, bm = C.c_float(), C.c_float()
+        L.check(self.lib.wb_batch_autotune(self.handle, C.byref(t), f.ctypes.data, b.ctypes.data,
+                                           C.byref(fm), C.byref(bm)), "wb_batch_autotune")
+        return ({k: getattr(t, k) for k, _ in L.wb_batch_tune._fields_}, f.tolist(), b.tolist(),
+                fm.value, bm.value)
+
     def eval(self, q, qd, qdd, pose, sphere=None, dmin=None, worst=None, tau=None, stream=None):
         L.check(self.lib.wb_batch_eval(self.handle, _ptr(q), _ptr(qd), _ptr(qdd), _ptr(pose),
                                        _ptr(sphere), _ptr(dmin), _ptr(worst), _ptr(tau),

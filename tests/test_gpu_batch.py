@@ -203,3 +203,107 @@ def test_uneven_full_size_sampled(W, O):
             same = got["worst"] == ref["worst"]
             PY.check_gradient([batch.view(t, "joint", p, (d.dof, H)).cpu().numpy() for t in g],
                               gref, mask=same)
+
+
+def _per_problem(batch, o, g, p, d, H):
+    return {"pose": batch.view(o["pose"], "pose", p, (H, d.n, 12)),
+            "sphere": batch.view(o["sphere"], "sphere", p, (H, d.S, 3)),
+            "dmin": batch.view(o["dmin"], "config", p, (H,)),
+            "worst": batch.view(o["worst"], "config", p, (H,)),
+            "tau": batch.view(o["tau"], "joint", p, (d.dof, H)),
+            "g": [batch.view(t, "joint", p, (d.dof, H)) for t in g]}
+
+
+def _check_against_single_robot(W, batch, robs, descs, problems, x, o, g, fseg, bseg, base):
+    """Sweep outputs bit for bit those of the single-robot depth-first kernels
+    with the same segment count on the same inputs (and the batch's worst
+    pair); pair outputs bit for bit those of `base` (another tune of the same
+    batch: the pair warps change the schedule, not the arithmetic)."""
+    qs, qds, qdds, gps, gss, gms, gts = x["raw"]
+    cuda = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    bo, bg = base
+    for p, (ri, H) in enumerate(problems):
+        if H == 0:
+            continue
+        d, rob = descs[ri], robs[ri]
+        got = _per_problem(batch, o, g, p, d, H)
+        ref = _per_problem(batch, bo, bg, p, d, H)
+        for k in ("sphere", "dmin", "worst"):
+            assert torch.equal(got[k], ref[k]), (p, k)
+        f = rob.eval(cuda(qs[p]), cuda(qds[p]), cuda(qdds[p]), sphere=False, dmin=False,
+                     tune=W.Tune(kernel=3, lanes_per_config=fseg[ri]))
+        assert torch.equal(got["pose"], f["pose"]) and torch.equal(got["tau"], f["tau"]), p
+        gr = rob.eval_backward(cuda(qs[p]), cuda(qds[p]), cuda(qdds[p]), got["worst"].clone(),
+                               cuda(gps[p]), cuda(gss[p]), cuda(gms[p]), cuda(gts[p]),
+                               tune=W.Tune(kernel=3, lanes_per_config=bseg[ri]))
+        for a, b in zip(got["g"], gr):
+            assert torch.equal(a, b), p
+
+
+@pytest.mark.parametrize("threads,pair_warps", [(64, 2), (128, 4), (256, 8)])
+def test_batch_tunes_match_single_robot_sweeps(W, threads, pair_warps):
+    """Every launch choice of an uneven batch -- sweep blocks of 64 / 128 /
+    256 threads, 2 / 4 / 8 pair warps, and per robot and pass 1 or 2 sweep
+    segments (the mimic robot has no 2-segment plan) -- gives the
+    single-robot kernels' results bit for bit."""
+    descs, robs, batch, problems = make_batch(W, horizons_seed=5)
+    x = fill(batch, descs, problems, 700)
+    base = run(batch, x)
+    for fseg, bseg in (([1, 1, 1, 1], [2, 2, 2, 1]), ([2, 2, 2, 1], [1, 1, 1, 1]),
+                       ([2, 1, 2, 1], [1, 2, 1, 1])):
+        batch.set_tune(threads, threads, pair_warps, fseg, bseg)
+        t, f, b = batch.get_tune()
+        assert (t["fwd_threads"], t["bwd_threads"], t["pair_warps"]) == (threads, threads,
+                                                                          pair_warps)
+        assert (f, b) == (fseg, bseg)
+        o, g = run(batch, x)
+        torch.cuda.synchronize()
+        _check_against_single_robot(W, batch, robs, descs, problems, x, o, g, fseg, bseg, base)
+
+
+def test_batch_autotune_choice_is_applied_and_exact(W, O):
+    """wb_batch_autotune: valid choices, kept by the batch, results equal to
+    the single-robot kernels with the chosen segments and to the oracle."""
+    descs, robs, batch, problems = make_batch(W, horizons_seed=9)
+    x = fill(batch, descs, problems, 800)
+    base = run(batch, x)
+    t, f, b, fm, bm = batch.autotune()
+    assert fm > 0 and bm > 0
+    assert t["fwd_threads"] in (64, 128, 256) and t["bwd_threads"] in (64, 128, 256)
+    assert t["pair_warps"] in (2, 4, 8)
+    assert all(s in (1, 2) for s in f + b) and f[3] == 1 and b[3] == 1
+    assert batch.get_tune() == (t, f, b)
+    o, g = run(batch, x)
+    torch.cuda.synchronize()
+    _check_against_single_robot(W, batch, robs, descs, problems, x, o, g, f, b, base)
+    qs, qds, qdds, gps, gss, gms, gts = x["raw"]
+    for p, (ri, H) in enumerate(problems[:6]):
+        if H == 0:
+            continue
+        d = descs[ri]
+        got = {k: v.cpu().numpy() for k, v in _per_problem(batch, o, g, p, d, H).items()
+               if k != "g"}
+        ref = O.evaluate(d, qs[p], qds[p], qdds[p])
+        PY.check_forward(d, got, ref)
+        gref = O.gradient(d, qs[p], qds[p], qdds[p], gps[p], gss[p], gms[p], gts[p])
+        gg = [t_.cpu().numpy() for t_ in _per_problem(batch, o, g, p, d, H)["g"]]
+        PY.check_gradient(gg, gref, mask=got["worst"] == ref["worst"])
+
+
+def test_batch_set_tune_refusals(W):
+    descs, robs, batch, problems = make_batch(W)
+    for bad in (dict(fwd_threads=96), dict(bwd_threads=512), dict(pair_warps=9),
+                dict(pair_warps=-1)):
+        with pytest.raises(W.L.WbError) as ei:
+            batch.set_tune(**bad)
+        assert ei.value.code == W.L.WB_EINVAL
+    with pytest.raises(W.L.WbError) as ei:  # the mimic robot has no 2-segment plan
+        batch.set_tune(fwd_segments=[2, 2, 2, 2])
+    assert ei.value.code == W.L.WB_EINVAL
+    with pytest.raises(W.L.WbError):
+        batch.set_tune(bwd_segments=[3, 1, 1, 1])
+    # the defaults: 2 segments where a plan exists, 128 threads, the most pair warps
+    batch.set_tune()
+    t, f, b = batch.get_tune()
+    assert (t["fwd_threads"], t["bwd_threads"], t["pair_warps"]) == (128, 128, 0)
+    assert f == b == [2, 2, 2, 1]
