@@ -9,16 +9,18 @@ configurations of the 48-DoF humanoid-shaped tree (1024 seeds x 32 timesteps
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--kernel tree|fused|plain] [--batch B] [--skip-cpu] [--skip-plain]
                   [--skip-uneven]
-                  [--workload humanoid48|trajopt48|uneven|kinematics]
+                  [--workload humanoid48|arm7|trajopt48|uneven|kinematics]
                   [--collision worst|hinge] [--sweep-shape FS,FC,BS,BC]
-                  [--ref-total-s T] [--ref-step-s S]
+                  [--ref-total-s T] [--ref-step-s S] [--split]
 
 --impl reference times the FP64 CPU oracle on the host cores instead, in
 bounded samples that keep the whole run within about --ref-total-s seconds.
 --sweep-shape pins the sweeps' launch shapes (segments and threads per block
 of the forward and the backward) instead of autotuning, for profiler runs.
-Under torchrun (N > 1) every rank evaluates its own batch (weak scaling);
-the step time is the maximum over ranks.
+Under torchrun (N > 1) the humanoid48 workload is one seeded global batch
+partitioned into contiguous column ranges, one per rank: N x --batch
+configurations (weak scaling, the default) or --batch split over the ranks
+(--split, strong scaling).  The step time is the maximum over ranks.
 """
 from __future__ import annotations
 
@@ -207,8 +209,25 @@ def humanoid48_step(rob, shapes, states, grads, out, gout, events=None, stream=N
 # (weak scaling); no collective touches the data path, only the timing
 # ---------------------------------------------------------------------------
 def rank_seed(base, rank):
-    """Each rank draws its own inputs."""
+    """Each rank draws its own inputs (the trajopt48, kinematics and uneven
+    workloads)."""
     return base + 101 * rank
+
+
+def rank_columns(world, rank, B, split=False):
+    """The columns of one global batch that rank `rank` of `world` evaluates,
+    a contiguous partition: weak scaling (default) makes the global batch
+    world x B and gives rank r columns [r B, (r + 1) B); split keeps the
+    global batch at B and gives rank r columns [r B / world, (r + 1) B /
+    world).  Returns (lo, hi, global batch size)."""
+    total = B if split else world * B
+    return rank * total // world, (rank + 1) * total // world, total
+
+
+def humanoid48_inputs(desc, lo, hi):
+    """Columns [lo, hi) of the humanoid48 workload's one seeded batch:
+    (q, qd, qdd, g_pose, g_sphere, g_dmin, g_tau)."""
+    return I.batch_columns(desc, lo, hi, CF.HUMANOID48.seed)
 
 
 def reduce_max(values, world, device):
@@ -473,12 +492,13 @@ def run_ours(args, rank, world, local_rank):
     desc = R.r48()
     B = args.batch or CF.HUMANOID48.batch
     rob = wbe.Robot(desc, device=local_rank)
+    # this rank's contiguous slice of the one seeded global batch
+    lo, hi, total = rank_columns(world, rank, B, args.split)
+    B = hi - lo
     shapes = humanoid48_launch(rob, B, args.kernel, args.sweep_shape)
     tune, btune = shapes["fwd"], shapes["bwd"]
     names, chosen = shapes["names"], shapes["chosen"]
-    seed = rank_seed(CF.HUMANOID48.seed, rank)
-    q, qd, qdd = I.uniform_states(desc.dof, B, seed)
-    gp, gs, gm, gt = I.upstream_grads(desc, B, seed + 1)
+    q, qd, qdd, gp, gs, gm, gt = humanoid48_inputs(desc, lo, hi)
     h_in = [torch.from_numpy(x).pin_memory() for x in (q, qd, qdd, gp, gs, gm, gt)]
     d_in = [x.to(dev) for x in h_in]
     tq, tqd, tqdd, tgp, tgs, tgm, tgt = d_in
@@ -578,8 +598,8 @@ def run_ours(args, rank, world, local_rank):
     fwd_mean, bwd_mean = kmean["tree_fwd"] + kmean["pair"], kmean["tree_bwd"]
     if rank != 0:
         return
-    value = job_value(world, B, step_ms)
-    e2e_value = job_value(world, B, e2e_ms)
+    value = total / (step_ms * 1e-3)  # the whole global batch / the slowest rank's time
+    e2e_value = total * (Bc * e2e_chunks / B) / (e2e_ms * 1e-3)  # the chunks cover Bc each
     work = work_per_eval(desc)
     peaks = measured_peaks()
     num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -610,10 +630,12 @@ def run_ours(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic",
+        "higher_is_better": True, "scaling": "strong" if args.split else "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": HUMANOID48_WORKLOAD,
-                   "batch_per_gpu": B, "kernel": args.kernel, "autotuned": chosen,
+                   "batch_per_gpu": B, "global_batch": total,
+                   "partition": "contiguous columns of one seeded batch, rank 0 first",
+                   "kernel": args.kernel, "autotuned": chosen,
                    "l2": "flushed between timed steps (512 MB write outside the events)"},
         "fwd_ms": fwd_mean, "bwd_ms": bwd_mean,
         "roofline": dict(kernel=names[dom], **{k: kernels[dom][k] for k in
@@ -632,27 +654,30 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu,
     }
     if args.kernel == "tree" and not args.skip_plain:
-        # the plain one-thread-per-configuration kernels on the same inputs
-        for _ in range(2):
-            rob.eval(tq, tqd, tqdd, tune=wbe.PLAIN, out=out)
-            rob.eval_backward(tq, tqd, tqdd, out["worst"], tgp, tgs, tgm, tgt, tune=wbe.PLAIN,
-                              out=gout)
-        torch.cuda.synchronize()
-        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        pf, pb = [], []
-        for i in range(3):
-            flush.fill_(float(i))
-            a.record(stream)
-            rob.eval(tq, tqd, tqdd, tune=wbe.PLAIN, out=out)
-            b.record(stream)
-            rob.eval_backward(tq, tqd, tqdd, out["worst"], tgp, tgs, tgm, tgt, tune=wbe.PLAIN,
-                              out=gout)
-            c.record(stream)
+        # the plain one-thread-per-configuration kernels and the fused
+        # (CTA-tiled, level-synchronous) kernels on the same inputs
+        for key, kt, reps in (("plain", wbe.PLAIN, 3), ("fused", wbe.FUSED, 10)):
+            for _ in range(2):
+                rob.eval(tq, tqd, tqdd, tune=kt, out=out)
+                rob.eval_backward(tq, tqd, tqdd, out["worst"], tgp, tgs, tgm, tgt, tune=kt,
+                                  out=gout)
             torch.cuda.synchronize()
-            pf.append(a.elapsed_time(b))
-            pb.append(b.elapsed_time(c))
-        line["plain"] = {"value": B / ((np.mean(pf) + np.mean(pb)) * 1e-3), "unit": "evals/s",
-                         "fwd_ms": float(np.mean(pf)), "bwd_ms": float(np.mean(pb))}
+            a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            pf, pb = [], []
+            for i in range(reps):
+                flush.fill_(float(i))
+                a.record(stream)
+                rob.eval(tq, tqd, tqdd, tune=kt, out=out)
+                b.record(stream)
+                rob.eval_backward(tq, tqd, tqdd, out["worst"], tgp, tgs, tgm, tgt, tune=kt,
+                                  out=gout)
+                c.record(stream)
+                torch.cuda.synchronize()
+                pf.append(a.elapsed_time(b))
+                pb.append(b.elapsed_time(c))
+            line[key] = {"value": B / ((np.mean(pf) + np.mean(pb)) * 1e-3), "unit": "evals/s",
+                         "fwd_ms": float(np.mean(pf)), "bwd_ms": float(np.mean(pb)),
+                         "kernels": "%s_fwd_kernel, %s_bwd_kernel" % (key, key)}
     if args.kernel == "tree" and not args.skip_uneven:
         # the uneven-batch workload (one GPU, rank 0): graph-replayed forward +
         # backward with the batch's default and its autotuned launch choices
@@ -943,6 +968,118 @@ def run_kinematics(args, rank=0, world=1, local_rank=0):
         "gpu_launches": 2 * args.steps * world, "clocks": clocks.summary()}), flush=True)
 
 
+def run_arm7(args, rank=0, world=1, local_rank=0):
+    """The 7-DoF chain at 4096 seeds x 32 timesteps (131072 configurations),
+    forward only: FK, sphere placement, self-collision and RNEA with every
+    output written (poses, sphere centres, d_min / worst pair, torques).  The
+    HBM-bound workload.  Times the default path (the forward sweep with the
+    autotuner's shape, then the pair kernel), the fused kernel and the plain
+    single-robot kernel on the same inputs; value = configurations per second
+    of the default path."""
+    import torch
+    from paper_2603_05493_gb300 import build
+    build()
+    from paper_2603_05493_gb300 import wbe
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    desc = R.r7()
+    rob = wbe.Robot(desc, device=local_rank)
+    lo, hi, total = rank_columns(world, rank, args.batch or CF.ARM7.batch, args.split)
+    B = hi - lo
+    q, qd, qdd = (torch.from_numpy(x).to(dev) for x in
+                  I.batch_columns(desc, lo, hi, CF.ARM7.seed)[:3])
+    out = rob.empty_outputs(B)
+    ft, _, _, _ = rob.autotune(B)
+    is_tree = ft.kernel == wbe.L.WB_KERNEL_TREE
+    seg = ft.lanes_per_config if is_tree else 0
+    sweep = wbe.Tune(kernel=wbe.L.WB_KERNEL_TREE, lanes_per_config=seg,
+                     configs_per_block=ft.configs_per_block if is_tree else 0)
+    pair = wbe.Tune(kernel=wbe.L.WB_KERNEL_TREE, blocks_per_sm=ft.blocks_per_sm if is_tree else 0)
+    stream = torch.cuda.current_stream()
+    fwd_out = {"pose": out["pose"], "sphere": None, "dmin": None, "worst": None,
+               "tau": out["tau"], "bits": None}
+    pair_out = {"sphere": out["sphere"], "dmin": out["dmin"], "worst": out["worst"],
+                "bits": None}
+
+    def tree_step(ev=None):
+        rob.eval(q, qd, qdd, tune=sweep, out=fwd_out, sphere=False, dmin=False)
+        if ev:
+            ev.record(stream)
+        rob.self_collision(out["pose"], tune=pair, out=pair_out)
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
+
+    def timed(f, n, split_event=False, clk=None):
+        for _ in range(max(args.warmup, 3)):
+            f()
+        torch.cuda.synchronize()
+        barrier(world)
+        if clk is not None:
+            clk.start()
+        tot, first = [], []
+        for i in range(n):
+            flush.fill_(float(i))
+            a, m, b = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a.record(stream)
+            f(m) if split_event else f()
+            b.record(stream)
+            torch.cuda.synchronize()
+            tot.append(a.elapsed_time(b))
+            if split_event:
+                first.append(a.elapsed_time(m))
+        if clk is not None:
+            clk.stop()
+        barrier(world)
+        return float(np.mean(tot)), (float(np.mean(first)) if first else None)
+    clocks = ClockSampler(local_rank)
+    ms, sweep_ms = timed(tree_step, args.steps, split_event=True, clk=clocks)
+    n_other = max(5, min(args.steps, 50))
+    fused_ms, _ = timed(lambda: rob.eval(q, qd, qdd, tune=wbe.FUSED, out=out), n_other)
+    plain_ms, _ = timed(lambda: rob.eval(q, qd, qdd, tune=wbe.PLAIN, out=out), n_other)
+    ms, sweep_ms, fused_ms, plain_ms = reduce_max([ms, sweep_ms, fused_ms, plain_ms], world, dev)
+    if rank != 0:
+        return
+    d, n, S = desc.dof, desc.n, desc.S
+    w = work_per_eval(desc)
+    bytes_fwd = 4 * (3 * d + 12 * n + 3 * S + 2 + d)  # states in; poses, spheres, d_min, worst, tau out
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+
+    def hbm(bytes_per_eval, t_ms):
+        ach = bytes_per_eval * B / (t_ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak}
+    pair_ms = ms - sweep_ms
+    kernels = {
+        "tree_fwd": dict(hbm(w["tree_fwd"]["bytes"], sweep_ms), ms=sweep_ms,
+                         kernel="tree_fwd_seg_kernel" if seg > 1 else "tree_fwd_kernel",
+                         bytes_per_eval=w["tree_fwd"]["bytes"]),
+        "pair": dict(hbm(w["pair"]["bytes"], pair_ms), ms=pair_ms, kernel="pair_kernel",
+                     bytes_per_eval=w["pair"]["bytes"]),
+    }
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    print(json.dumps({
+        "metric": "arm7 whole-body forward evals/s (FK+self-coll+RNEA, 7-DoF chain)",
+        "value": total / (ms * 1e-3), "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "strong" if args.split else "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "arm7: 7-DoF chain, 28 spheres, 240 pairs, 4096 x 32 "
+                               "configurations, forward with every output",
+                   "batch_per_gpu": B, "global_batch": total,
+                   "autotuned": dict(ft.__dict__), "l2": "flushed between timed steps"},
+        "step_roofline": dict(hbm(bytes_fwd, ms), bytes_per_eval=bytes_fwd),
+        "roofline": dict(kernel=kernels[dom]["kernel"], traffic=None,
+                         **{k: kernels[dom][k] for k in ("bound", "achieved", "peak", "unit",
+                                                         "frac")}),
+        "kernels": kernels,
+        "fused": dict(hbm(bytes_fwd, fused_ms), value=B / (fused_ms * 1e-3), ms=fused_ms,
+                      kernel="fused_fwd_kernel"),
+        "plain": dict(hbm(bytes_fwd, plain_ms), value=B / (plain_ms * 1e-3), ms=plain_ms,
+                      kernel="plain_fwd_kernel"),
+        "gpu_launches": 2 * args.steps * world, "clocks": clocks.summary()}), flush=True)
+
+
 def uneven_measure(rank, dev, steps, warmup, clocks=None):
     """The uneven workload: 256 x R7 + 256 x R23 + 256 x R48 problems with
     horizons U{16..64}, forward (FK + RNEA, spheres + self-collision) and
@@ -1069,6 +1206,9 @@ def main():
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--split", action="store_true",
+                    help="humanoid48 under torchrun: split the --batch configurations over "
+                         "the ranks (strong scaling) instead of --batch per rank")
     ap.add_argument("--skip-uneven", action="store_true",
                     help="humanoid48: leave out the uneven-batch sub-result")
     ap.add_argument("--cpu-s", type=float, default=15.0)
@@ -1076,7 +1216,8 @@ def main():
                     help="reference arm: at most this many seconds of oracle work a step")
     ap.add_argument("--ref-total-s", type=float, default=120.0,
                     help="reference arm: about this many seconds for the whole run")
-    ap.add_argument("--workload", choices=["humanoid48", "uneven", "trajopt48", "kinematics"],
+    ap.add_argument("--workload", choices=["humanoid48", "arm7", "uneven", "trajopt48",
+                                           "kinematics"],
                     default="humanoid48")
     ap.add_argument("--collision", choices=["worst", "hinge"], default="worst",
                     help="trajopt48 collision cost: worst-pair hinge or summed hinge")
@@ -1096,8 +1237,8 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     try:
-        run = {"humanoid48": run_ours, "uneven": run_uneven, "trajopt48": run_trajopt,
-               "kinematics": run_kinematics}
+        run = {"humanoid48": run_ours, "arm7": run_arm7, "uneven": run_uneven,
+               "trajopt48": run_trajopt, "kinematics": run_kinematics}
         run[args.workload](args, rank, world, local_rank)
     finally:
         if world > 1:

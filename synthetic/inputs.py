@@ -41,6 +41,44 @@ def upstream_grads(robot: R.Robot, B: int, seed: int, pose=True, sph=True, dmin=
     return g_pose, g_sph, g_dmin, g_tau
 
 
+def batch_columns(robot: R.Robot, lo: int, hi: int, seed: int, block: int = 32):
+    """Columns [lo, hi) of one seeded batch of configurations: the states of
+    uniform_states (same ranges) and the standard-normal upstream gradients of
+    upstream_grads, drawn in blocks of `block` consecutive columns (one seed's
+    timesteps), block k from the generator seeded with (seed, k).  Any
+    contiguous slice is therefore the same whoever draws it: ranks that split
+    one batch draw only their own columns.  Returns (q, qd, qdd, g_pose,
+    g_sph, g_dmin, g_tau) in the library's layouts."""
+    if not 0 <= lo <= hi:
+        raise ValueError("bad column range [%d, %d)" % (lo, hi))
+    k0, k1 = lo // block, (hi + block - 1) // block
+    parts = [[] for _ in range(7)]
+    for k in range(k0, k1):
+        rng = np.random.default_rng([seed, k])
+        d = robot.dof
+        draws = (rng.uniform(-np.pi, np.pi, size=(d, block)),
+                 rng.uniform(-2.0, 2.0, size=(d, block)),
+                 rng.uniform(-5.0, 5.0, size=(d, block)),
+                 rng.standard_normal((block, robot.n, 12)),
+                 rng.standard_normal((block, robot.S, 3)),
+                 rng.standard_normal(block),
+                 rng.standard_normal((d, block)))
+        for lst, x in zip(parts, draws):
+            lst.append(x.astype(np.float32))
+    a, b = lo - k0 * block, hi - k0 * block
+    out = []
+    for i, lst in enumerate(parts):
+        if not lst:
+            shape = {0: (robot.dof, 0), 1: (robot.dof, 0), 2: (robot.dof, 0),
+                     3: (0, robot.n, 12), 4: (0, robot.S, 3), 5: (0,), 6: (robot.dof, 0)}[i]
+            out.append(np.zeros(shape, np.float32))
+            continue
+        joint = i in (0, 1, 2, 6)
+        x = np.concatenate(lst, axis=1 if joint else 0)
+        out.append(np.ascontiguousarray(x[:, a:b] if joint else x[a:b]))
+    return tuple(out)
+
+
 def bspline_controls(dof: int, n_traj: int, K: int, seed: int, lim=np.pi / 2):
     """Control points U ~ U(-pi/2, pi/2), layout [n_traj][d][K]."""
     rng = np.random.default_rng(seed)

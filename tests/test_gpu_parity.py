@@ -186,8 +186,9 @@ def test_humanoid48_bench_step_parity(W, O, shape):
     launch shapes bench.py takes (the library's autotuner at this batch, or
     the shapes it picked on GB300: forward 2 segments x 256 threads, backward
     2 segments x 448 threads = 147 blocks of 7 groups, 4 pair warps a block),
-    through bench.py's own launch functions; >= 256 sampled configurations
-    against the oracle (forward outputs and the three gradients)."""
+    through bench.py's own launch functions and on its inputs; >= 256 sampled
+    configurations against the oracle (forward outputs and the three
+    gradients)."""
     import bench
     desc, rob = robot(W, "R48")
     B = CF.HUMANOID48.batch
@@ -196,8 +197,7 @@ def test_humanoid48_bench_step_parity(W, O, shape):
     else:
         shapes = bench.humanoid48_launch(rob, B, sweep_shape="2,256,2,448")
         shapes["pair"] = W.Tune(kernel=3, blocks_per_sm=4)
-    q, qd, qdd = I.uniform_states(desc.dof, B, CF.HUMANOID48.seed)
-    gp, gs, gm, gt = I.upstream_grads(desc, B, seed=CF.HUMANOID48.seed + 1)
+    q, qd, qdd, gp, gs, gm, gt = bench.humanoid48_inputs(desc, 0, B)  # the bench's inputs
     out = rob.empty_outputs(B)
     gout = tuple(torch.empty((desc.dof, B), device="cuda") for _ in range(3))
     bwd = shapes["bwd"]

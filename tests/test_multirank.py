@@ -1,7 +1,9 @@
 """The multi-rank host logic of bench.py on CPU: two gloo ranks on
-127.0.0.1, each with its own batch (weak scaling).  The slowest rank's time
-sets the step, the whole-job value counts every rank's configurations, and
-the ranks draw different inputs.  No GPU, no collective on the data path."""
+127.0.0.1.  The humanoid48 workload is one seeded batch partitioned into
+contiguous column ranges (weak or strong scaling); the other workloads draw
+per-rank inputs.  The slowest rank's time sets the step and the whole-job
+value counts every rank's configurations.  No GPU, no collective on the data
+path."""
 import os
 import socket
 
@@ -51,6 +53,68 @@ def test_two_gloo_ranks_weak_scaling():
     assert st0 == st1 == 2.0                 # max over ranks
     assert e0 == e1 == 4.0
     assert v0 == v1 == pytest.approx(2 * 32768 / 2e-3)   # all ranks' work / slowest time
+
+
+def _split_rank_main(rank, world, port, B, split, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import bench
+        from synthetic import robots as R
+        lo, hi, total = bench.rank_columns(world, rank, B, split)
+        mine = bench.humanoid48_inputs(R.r7(), lo, hi)
+        got = [None] * world
+        dist.all_gather_object(got, (rank, lo, hi, total, mine))
+        if rank == 0:
+            out.put(got)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("split", [False, True])
+def test_two_gloo_ranks_partition_one_batch(split):
+    """Each rank evaluates a contiguous slice of one seeded batch: the slices
+    cover the global batch exactly once, in rank order, and each rank's
+    inputs are the one-rank batch's columns, bit for bit (host arrays only)."""
+    import bench
+    from synthetic import robots as R
+    world, port, B = 2, _free_port(), 70
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    procs = [ctx.Process(target=_split_rank_main, args=(r, world, port, B, split, out))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    got = out.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    total = got[0][3]
+    assert total == (B if split else world * B)
+    cols = sorted((lo, hi) for _, lo, hi, _, _ in got)
+    assert cols[0][0] == 0 and cols[-1][1] == total
+    assert all(a[1] == b[0] for a, b in zip(cols, cols[1:]))    # no gap, no overlap
+    whole = bench.humanoid48_inputs(R.r7(), 0, total)
+    for rank, lo, hi, _, mine in got:
+        assert (lo, hi) == cols[rank]
+        for part, ref in zip(mine, whole):
+            want = ref[:, lo:hi] if ref.ndim == 2 and ref.shape[1] == total else ref[lo:hi]
+            assert np.array_equal(part, want)
+
+
+def test_rank_columns_partition_uneven_sizes():
+    import bench
+    for world in (1, 2, 3, 8):
+        for B in (1, 7, 100, 32768):
+            for split in (False, True):
+                cols = [bench.rank_columns(world, r, B, split) for r in range(world)]
+                total = cols[0][2]
+                assert total == (B if split else world * B)
+                assert cols[0][0] == 0 and cols[-1][1] == total
+                assert all(a[1] == b[0] for a, b in zip(cols, cols[1:]))
+                sizes = [hi - lo for lo, hi, _ in cols]
+                assert max(sizes) - min(sizes) <= 1
 
 
 def test_single_rank_needs_no_process_group():
