@@ -608,7 +608,9 @@ int wb_autotune_spline(wb_robot* robot, int64_t n_traj, int32_t K, int32_t T, fl
  * Setup: the first call on a device looks up the scratch array's device
  * address (cudaGetSymbolAddress, with that device current), which may load
  * the library's device code there; make that first call on each device before
- * any stream capture begins, e.g. as a warm-up.
+ * any stream capture begins, e.g. as a warm-up.  The address is kept for the
+ * life of the process: after a cudaDeviceReset of that device it is stale,
+ * and this call must not be used on that device again.
  *
  * The statement on graph capture in the conventions at the top of this file
  * does not cover this call.

@@ -28,9 +28,11 @@ static constexpr size_t NA_BYTES = NA_OFF_COUNTERS + 256;
 
 static_assert(sizeof(NoAllocPlan) + sizeof(void*) <= 32764, "setup parameters exceed the launch limit");
 
-static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+// the public header promises about 0.6 MiB per device (618,240 bytes with
+// the present layouts)
+static_assert(NA_BYTES <= 640 * 1024, "no-alloc scratch larger than the header states");
 
-size_t noalloc_scratch_bytes() { return NA_BYTES; }
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
 __host__ __device__ NoAllocTables noalloc_tables(unsigned char* base) {
   NoAllocTables t;

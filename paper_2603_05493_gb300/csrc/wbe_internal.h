@@ -225,7 +225,6 @@ struct NoAllocTables {
   int2* pitems;
   int* counters;
 };
-size_t noalloc_scratch_bytes();
 __host__ __device__ NoAllocTables noalloc_tables(unsigned char* base);
 cudaError_t noalloc_scratch(int device, unsigned char** out);
 cudaError_t launch_noalloc_setup(const NoAllocPlan& plan, unsigned char* base, int grid,

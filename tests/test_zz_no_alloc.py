@@ -12,7 +12,6 @@ import torch
 
 from synthetic import inputs as I
 from synthetic import robots as R
-from tests import parity as PY
 
 pytestmark = pytest.mark.gpu
 
@@ -79,10 +78,10 @@ def call(W, robs, problems, x, o, n_robots=None):
 
 
 def same(o, ref):
-    for k in ("pose", "sphere", "dmin"):
-        torch.testing.assert_close(o[k], ref[k], rtol=0, atol=PY.POS_TOL, equal_nan=False)
-    torch.testing.assert_close(o["tau"], ref["tau"], rtol=PY.TAU_REL, atol=PY.TAU_REL)
-    assert torch.equal(o["worst"], ref["worst"])
+    """Identical to the allocating entry point's outputs, bit for bit (the
+    same kernels on the same work items)."""
+    for k in ("pose", "sphere", "dmin", "tau", "worst"):
+        assert torch.equal(o[k], ref[k]), k
 
 
 def test_matches_allocating_entry_point_on_consecutive_calls(W, robots):
@@ -146,3 +145,43 @@ def test_python_binding_matches(W, robots):
                          o["dmin"], o["worst"], o["tau"])
     torch.cuda.synchronize()
     same(o, rb)
+
+
+def limit_mix(total, seed):
+    """1024 problems over the four robots, empty ones first, in the middle and
+    last, horizons summing to `total` configurations."""
+    rng = np.random.default_rng(seed)
+    n = 1024
+    H = rng.integers(1, 2 * total // n, size=n)
+    H[[0, n // 2, n - 1]] = 0
+    H = (H * (total / H.sum())).astype(np.int64)
+    H[[0, n // 2, n - 1]] = 0
+    i = 1
+    while H.sum() < total:  # exact total, spread over the non-empty problems
+        if i not in (n // 2,):
+            H[i] += 1
+        i = i % (n - 2) + 1
+    robot = rng.integers(0, 4, size=n)
+    return [(int(r), int(h)) for r, h in zip(robot, H)]
+
+
+def test_matches_allocating_entry_point_at_the_limits(W, robots):
+    """1024 problems (empty ones first, in the middle and last) and exactly
+    65536 configurations: the setup kernel runs 64 blocks, each rescanning
+    every problem's offsets and searching all of them; outputs identical to
+    wb_batch_eval's.  One configuration more is refused."""
+    descs, robs = robots
+    mix = limit_mix(65536, 3)
+    assert len(mix) == 1024 and sum(h for _, h in mix) == 65536
+    assert mix[0][1] == mix[512][1] == mix[1023][1] == 0
+    b, x, ref = case(W, descs, robs, mix, 1300)
+    o = outputs(b)
+    assert call(W, robs, mix, x, o) == W.L.WB_OK
+    torch.cuda.synchronize()
+    same(o, ref)
+    over = list(mix)
+    over[5] = (over[5][0], over[5][1] + 1)
+    o2 = outputs(b)
+    assert call(W, robs, over, x, o2) == W.L.WB_ETOOBIG
+    torch.cuda.synchronize()
+    assert torch.isnan(o2["pose"]).all()
