@@ -46,7 +46,6 @@ extern "C" {
 #define WB_ETOOBIG (-4)  /* robot larger than the kernels' limits */
 #define WB_EDEVICE (-5)  /* pointer not on the robot's device */
 #define WB_ECUDA (-6)    /* CUDA runtime error (allocation, copy or launch) */
-#define WB_ETIMEOUT (-7) /* a bounded device wait expired */
 
 /* limits of the kernels (checked at load) */
 #define WB_MAX_LINKS 255

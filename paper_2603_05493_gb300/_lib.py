@@ -16,9 +16,8 @@ WB_ERANGE = -3
 WB_ETOOBIG = -4
 WB_EDEVICE = -5
 WB_ECUDA = -6
-WB_ETIMEOUT = -7
 ERRNAMES = {0: "WB_OK", -1: "WB_EINVAL", -2: "WB_ETOPO", -3: "WB_ERANGE", -4: "WB_ETOOBIG",
-            -5: "WB_EDEVICE", -6: "WB_ECUDA", -7: "WB_ETIMEOUT"}
+            -5: "WB_EDEVICE", -6: "WB_ECUDA"}
 
 WB_KERNEL_AUTO = 0
 WB_KERNEL_PLAIN = 1

@@ -4,6 +4,7 @@
 #include "tree_sweep.cuh"
 
 #include <algorithm>
+#include <mutex>
 
 namespace wbe {
 
@@ -281,30 +282,55 @@ __global__ void __launch_bounds__(512, 1) tree_bwd_spline_cost_seg_kernel(
 // stacks shrank to match.  fit_carveout asks for the smallest carveout that
 // still holds every block the registers, warps and block limit let one SM
 // keep (a hint: the driver rounds it up to a carveout it supports).
+// the SM limits fit_carveout needs, queried once per device (host threads may
+// launch on several devices at once)
+struct SmLimits {
+  int smem_sm, regs_sm, threads_sm, blocks_sm, reserved;
+};
+static bool sm_limits(int dev, SmLimits* out) {
+  constexpr int kDevices = 64;
+  static std::mutex mu;
+  static SmLimits cache[kDevices];
+  static bool have[kDevices] = {};
+  auto query = [](int d, SmLimits* l) {
+    return cudaDeviceGetAttribute(&l->regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, d) ==
+               cudaSuccess &&
+           cudaDeviceGetAttribute(&l->threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, d) ==
+               cudaSuccess &&
+           cudaDeviceGetAttribute(&l->blocks_sm, cudaDevAttrMaxBlocksPerMultiprocessor, d) ==
+               cudaSuccess &&
+           cudaDeviceGetAttribute(&l->reserved, cudaDevAttrReservedSharedMemoryPerBlock, d) ==
+               cudaSuccess &&
+           cudaDeviceGetAttribute(&l->smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, d) ==
+               cudaSuccess;
+  };
+  if (dev < 0 || dev >= kDevices) return query(dev, out);
+  std::lock_guard<std::mutex> lock(mu);
+  if (!have[dev]) {
+    if (!query(dev, &cache[dev])) return false;
+    have[dev] = true;
+  }
+  *out = cache[dev];
+  return true;
+}
+
 void fit_carveout(const void* kern, int threads, size_t smem) {
-  static int smem_sm = 0, regs_sm = 0, threads_sm = 0, blocks_sm = 0, reserved = 0;
-  if (!smem_sm) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return;
-    if (cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) ||
-        cudaDeviceGetAttribute(&threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) ||
-        cudaDeviceGetAttribute(&blocks_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev) ||
-        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) ||
-        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) {
-      smem_sm = 0;
-      return;
-    }
+  int dev = 0;
+  SmLimits L;
+  if (cudaGetDevice(&dev) != cudaSuccess || !sm_limits(dev, &L)) {
+    cudaGetLastError();
+    return;
   }
   cudaFuncAttributes fa;
   if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return;
   const int warps = (threads + 31) / 32;
   const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;  // 256-register allocation unit
-  int nb = std::min(threads_sm / (32 * warps), blocks_sm);
-  if (regs_warp > 0) nb = std::min(nb, (regs_sm / regs_warp) / warps);
-  const size_t per = smem + fa.sharedSizeBytes + (size_t)reserved;
-  nb = std::min<int>(nb, (int)((size_t)smem_sm / per));
+  int nb = std::min(L.threads_sm / (32 * warps), L.blocks_sm);
+  if (regs_warp > 0) nb = std::min(nb, (L.regs_sm / regs_warp) / warps);
+  const size_t per = smem + fa.sharedSizeBytes + (size_t)L.reserved;
+  nb = std::min<int>(nb, (int)((size_t)L.smem_sm / per));
   const size_t need = (size_t)std::max(nb, 1) * per;
-  const int pct = (int)std::min<size_t>(100, (need * 100 + smem_sm - 1) / smem_sm);
+  const int pct = (int)std::min<size_t>(100, (need * 100 + L.smem_sm - 1) / L.smem_sm);
   cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
 }
 

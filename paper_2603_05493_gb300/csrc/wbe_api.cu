@@ -14,6 +14,7 @@
 #include "wbe_internal.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -74,7 +75,8 @@ struct wb_robot {
   float* h_stage = nullptr;   // pinned staging buffer for inertia uploads
   cudaEvent_t stage_evt = nullptr;
   bool stage_pending = false;
-  int pair_warps_default[2] = {0, 0};  // without / with pair bits, set on first use
+  // without / with pair bits, set on first use (any host thread may be first)
+  std::atomic<int> pair_warps_default[2] = {0, 0};
 };
 
 static int sched_slot(int G) { return G == 4 ? 0 : G == 8 ? 1 : G == 16 ? 2 : G == 32 ? 3 : -1; }
@@ -946,8 +948,8 @@ static int pair_warps(wb_robot* R, bool bits, const wb_tune* tune, bool cull = t
   const size_t one = pair_block_smem(D, 1, bits), none = pair_block_smem(D, 0, bits);
   const int most = warps_that_fit(none, one - none);
   if (!cull) return most;
-  int& cached = R->pair_warps_default[bits ? 1 : 0];
-  if (cached) return cached;
+  std::atomic<int>& cached = R->pair_warps_default[bits ? 1 : 0];
+  if (const int c = cached.load(std::memory_order_relaxed)) return c;
   int best = most, best_res = -1;
   for (int w = 4; w <= most; ++w) {
     int bps = 0;
@@ -961,7 +963,7 @@ static int pair_warps(wb_robot* R, bool bits, const wb_tune* tune, bool cull = t
       best = w;
     }
   }
-  cached = best;
+  cached.store(best, std::memory_order_relaxed);
   return best;
 }
 
