@@ -78,16 +78,16 @@ PAIR_SRC = ["paper_2603_05493_gb300/csrc/k_pair.cu", "paper_2603_05493_gb300/csr
             "paper_2603_05493_gb300/csrc/spatial.cuh"] + API_SRC
 SPLINE_SRC = ["paper_2603_05493_gb300/csrc/k_traj.cu",
               "paper_2603_05493_gb300/csrc/spline_basis.cuh"] + API_SRC
-TREE_SHA = "ac75317bcb46a234d7b96495d9413974d7338a02888b313a4531e372720ca258"
-PAIR_SHA = "24eba79b1a9ec4a4fcf9f325d5e1c7e8a31c5b229392800e1bee28cbaa6dd384"
-SPLINE_SHA = "c108dcde01f4aae419c550035ef5f5a4bbbc87970a1f481e1261585a2097194d"
+TREE_SHA = "9dfc827f64d34d9a4c8807d3135fb153c968e66dcbd2d159fa6f713dd0d81234"
+PAIR_SHA = "9461984026f76ba35a978ed8c21c58525b61a946bd61fd4511937fa2cc7bc632"
+SPLINE_SHA = "67fd8ed4cfa1b35e9693ecee907ae3b451b28eaa8a491575e4c6a075ebf2e655"
 MEASURED_TRAFFIC = {  # kernel[@workload]: (sources, their hash, bytes / evaluation)
-    "tree_fwd_seg_kernel": (TREE_SRC, TREE_SHA, (29.86e6 + 79.77e6) / 32768),
-    "pair_kernel": (PAIR_SRC, PAIR_SHA, (79.02e6 + 41.27e6) / 32768),
-    "tree_bwd_seg_kernel": (TREE_SRC, TREE_SHA, (341.06e6 + 162.12e6) / 32768),
-    "tree_fwd_spline_seg_kernel": (TREE_SRC, TREE_SHA, (8.41e6 + 80.03e6) / 32768),
-    "pair_kernel@trajopt48": (PAIR_SRC, PAIR_SHA, (77.81e6 + 0.20e6) / 32768),
-    "tree_bwd_spline_cost_kernel": (TREE_SRC, TREE_SHA, (15.23e6 + 20.83e6) / 32768),
+    "tree_fwd_seg_kernel": (TREE_SRC, TREE_SHA, (29.71e6 + 80.28e6) / 32768),
+    "pair_kernel": (PAIR_SRC, PAIR_SHA, (80.49e6 + 46.52e6) / 32768),
+    "tree_bwd_seg_kernel": (TREE_SRC, TREE_SHA, (244.46e6 + 36.89e6) / 32768),
+    "tree_fwd_spline_seg_kernel": (TREE_SRC, TREE_SHA, (8.46e6 + 80.84e6) / 32768),
+    "pair_kernel@trajopt48": (PAIR_SRC, PAIR_SHA, (78.59e6 + 2.95e6) / 32768),
+    "tree_bwd_spline_cost_seg_kernel": (TREE_SRC, TREE_SHA, (8.33e6 + 1.78e6) / 32768),
     "bspline_bwd_kernel": (SPLINE_SRC, SPLINE_SHA, (18.89e6 + 0.0) / 32768),
 }
 
