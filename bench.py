@@ -179,8 +179,8 @@ def humanoid48_step(rob, shapes, states, grads, out, gout, events=None, stream=N
     """One humanoid48 step with the launch choices of humanoid48_launch:
     forward (FK + RNEA sweep, then spheres + self-collision; one launch for
     fused / plain) and backward with the upstream gradients grads = (g_pose,
-    g_sphere, g_dmin, g_tau).  out: rob.empty_outputs(B); gout: (gq, gqd,
-    gqdd).  events[1], events[2] are recorded after the forward sweep and
+    g_sphere, g_dmin, g_tau).  out: rob.empty_outputs(B), with a "diff" (B, 3)
+    buffer for the worst pair's centre difference; gout: (gq, gqd, gqdd).  events[1], events[2] are recorded after the forward sweep and
     after the pair stage."""
     tq, tqd, tqdd = states
     tgp, tgs, tgm, tgt = grads
@@ -197,11 +197,14 @@ def humanoid48_step(rob, shapes, states, grads, out, gout, events=None, stream=N
             events[1].record(stream)
         rob.self_collision(out["pose"], tune=shapes["pair"], stream=stream,
                            out={"sphere": out["sphere"], "dmin": out["dmin"],
-                                "worst": out["worst"], "bits": None})
+                                "worst": out["worst"], "diff": out.get("diff"), "bits": None})
         if events:
             events[2].record(stream)
+    # the pair stage's worst-pair centre difference spares the backward the
+    # forward kinematics of the pair's two links
     rob.eval_backward(tq, tqd, tqdd, out["worst"], tgp, tgs, tgm, tgt, tune=shapes["bwd"],
-                      out=gout, stream=stream)
+                      out=gout, stream=stream,
+                      worst_diff=out.get("diff") if shapes["pair"] is not None else None)
 
 
 # ---------------------------------------------------------------------------
@@ -503,6 +506,7 @@ def run_ours(args, rank, world, local_rank):
     d_in = [x.to(dev) for x in h_in]
     tq, tqd, tqdd, tgp, tgs, tgm, tgt = d_in
     out = rob.empty_outputs(B)
+    out["diff"] = torch.empty((B, 3), device=dev)
     gout = tuple(torch.empty((desc.dof, B), device=dev) for _ in range(3))
     flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
     stream = torch.cuda.current_stream()

@@ -221,6 +221,15 @@ int wb_self_collision_tuned(wb_robot* robot, int64_t B, const float* link_pose, 
                             float* d_min, int32_t* worst_pair, uint32_t* pair_bits,
                             const wb_tune* tune, void* stream);
 
+/* wb_self_collision_tuned that also writes worst_diff [B][3] (nullable;
+ * needs d_min): c_i - c_j of the worst pair's sphere centres (zero when the
+ * robot has no pairs), the direction of d_min's gradient on the spheres.
+ * Hand it to wb_eval_backward_dir: the backward then needs no forward
+ * kinematics of the worst pair's links of its own.  Errors as wb_eval. */
+int wb_self_collision_dir(wb_robot* robot, int64_t B, const float* link_pose, float* sphere,
+                          float* d_min, int32_t* worst_pair, float* worst_diff,
+                          uint32_t* pair_bits, const wb_tune* tune, void* stream);
+
 /* Kinematic Jacobians of chosen links and the whole-body centre of mass,
  * from world link poses [B][n][12] (from wb_eval): the second-kernel outputs
  * of the split forward kinematics (Sec. 6.1.1), columns as in Alg. 2 (a joint
@@ -283,6 +292,17 @@ int wb_eval_backward_ext(wb_robot* robot, int64_t B, const float* q, const float
                          const float* g_pose, const float* g_sphere, const float* g_dmin,
                          const float* g_tau, float* gq, float* gqd, float* gqdd, float* g_fext,
                          const wb_tune* tune, void* stream);
+
+/* wb_eval_backward_ext with the worst pair's centre difference worst_diff
+ * [B][3] from wb_self_collision_dir on the same poses (nullable: the sweep
+ * places the two spheres itself).  The tree kernels use it in place of the
+ * forward kinematics of the pair's two links and give the same results bit
+ * for bit; the fused and plain kernels ignore it.  Errors as wb_eval. */
+int wb_eval_backward_dir(wb_robot* robot, int64_t B, const float* q, const float* qd,
+                         const float* qdd, const float* f_ext, const int32_t* worst_pair,
+                         const float* worst_diff, const float* g_pose, const float* g_sphere,
+                         const float* g_dmin, const float* g_tau, float* gq, float* gqd,
+                         float* gqdd, float* g_fext, const wb_tune* tune, void* stream);
 
 /* Autotuner (a setup-time call: it allocates scratch buffers for B
  * configurations, synchronises the device and must not be captured).  Times

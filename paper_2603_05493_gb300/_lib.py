@@ -141,6 +141,9 @@ SIGNATURES = {
     "wb_self_collision_hinge": (C.c_int, [p, C.c_int64, p, C.c_float, C.c_float, p, p, p]),
     "wb_kinematics": (C.c_int, [p, C.c_int64, p, C.c_int32, p, p, p, p, p]),
     "wb_self_collision_tuned": (C.c_int, [p, C.c_int64, p, p, p, p, p, C.POINTER(wb_tune), p]),
+    "wb_self_collision_dir": (C.c_int, [p, C.c_int64, p, p, p, p, p, p, C.POINTER(wb_tune), p]),
+    "wb_eval_backward_dir": (C.c_int, [p, C.c_int64, p, p, p, p, p, p, p, p, p, p, p, p, p, p,
+                                       C.POINTER(wb_tune), p]),
     "wb_eval_ext": (C.c_int, [p, C.c_int64, p, p, p, p, p, p, p, p, p, p, C.POINTER(wb_tune), p]),
     "wb_eval_backward_ext": (C.c_int, [p, C.c_int64, p, p, p, p, p, p, p, p, p, p, p, p, p,
                                        C.POINTER(wb_tune), p]),

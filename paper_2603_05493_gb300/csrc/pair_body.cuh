@@ -74,6 +74,22 @@ __device__ __forceinline__ float pick(const float4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
 
+// c_i - c_j of pair p from the placed sphere centres (zero when there is no
+// pair): the vector the backward sweep needs for the worst pair's gradient
+__device__ __forceinline__ void pair_diff(const DevRobot& r, const FwdArgs& A, int64_t b, int p,
+                                          const float* xc, const float* yc, const float* zc) {
+  float d[3] = {0.0f, 0.0f, 0.0f};
+  if (p >= 0) {
+    const int2 ij = __ldg(r.pairs + p);
+    d[0] = xc[ij.x] - xc[ij.y];
+    d[1] = yc[ij.x] - yc[ij.y];
+    d[2] = zc[ij.x] - zc[ij.y];
+  }
+  A.wdiff[3 * b] = d[0];
+  A.wdiff[3 * b + 1] = d[1];
+  A.wdiff[3 * b + 2] = d[2];
+}
+
 template <bool FULL, bool BITS>
 __device__ __forceinline__ void pair_one(const DevRobot& r, const PairSchedule32& ps,
                                          const FwdArgs& A, int64_t b, float* ws,
@@ -145,6 +161,7 @@ __device__ __forceinline__ void pair_one(const DevRobot& r, const PairSchedule32
     if (lane == 0 && A.dmin) {
       A.dmin[b] = __int_as_float(0x7f800000);
       A.worst[b] = -1;
+      if (A.wdiff) pair_diff(r, A, b, -1, xc, yc, zc);
     }
     if (BITS)
       for (int w = lane; w < W; w += 32) A.bits[b * (int64_t)W + w] = 0u;
@@ -282,6 +299,7 @@ __device__ __forceinline__ void pair_one(const DevRobot& r, const PairSchedule32
     const bool none = bidx == INT_MAX;
     A.dmin[b] = none ? __int_as_float(0x7f800000) : best;
     A.worst[b] = none ? -1 : bidx;
+    if (A.wdiff) pair_diff(r, A, b, none ? -1 : bidx, xc, yc, zc);
   }
   if (BITS) {
     __syncwarp();
@@ -408,6 +426,7 @@ __device__ __forceinline__ void pair_one_culled(const DevRobot& r, const PairSch
     if (lane == 0 && A.dmin) {
       A.dmin[b] = __int_as_float(0x7f800000);
       A.worst[b] = -1;
+      if (A.wdiff) pair_diff(r, A, b, -1, xc, yc, zc);
     }
     if (BITS)
       for (int w = lane; w < W; w += 32) A.bits[b * (int64_t)W + w] = 0u;
@@ -583,6 +602,7 @@ __device__ __forceinline__ void pair_one_culled(const DevRobot& r, const PairSch
     const bool none = bidx == INT_MAX;
     A.dmin[b] = none ? __int_as_float(0x7f800000) : best;
     A.worst[b] = none ? -1 : bidx;
+    if (A.wdiff) pair_diff(r, A, b, none ? -1 : bidx, xc, yc, zc);
   }
   if (BITS) {
     __syncwarp();

@@ -476,16 +476,23 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
         ps2 = ij.y;
         pl1 = l1;
         pl2 = l2;
-        float P1[12], P2[12], c1[3], c2[3];
-        chain_pose(r, pl1, st, P1);
-        chain_pose(r, pl2, st, P2);
-        const float4 s1 = __ldg(r.sph + ps1), s2 = __ldg(r.sph + ps2);
-        const float q1[3] = {s1.x, s1.y, s1.z}, q2[3] = {s2.x, s2.y, s2.z};
-        rot(P1, q1, c1);
-        rot(P2, q2, c2);
-        const float dx = (c1[0] + P1[9]) - (c2[0] + P2[9]);
-        const float dy = (c1[1] + P1[10]) - (c2[1] + P2[10]);
-        const float dz = (c1[2] + P1[11]) - (c2[2] + P2[11]);
+        float dx, dy, dz;
+        if (A.wdiff) {  // from the pair stage: the same arithmetic on the same poses
+          dx = __ldg(A.wdiff + 3 * b);
+          dy = __ldg(A.wdiff + 3 * b + 1);
+          dz = __ldg(A.wdiff + 3 * b + 2);
+        } else {  // place the two spheres from their links' ancestor chains
+          float P1[12], P2[12], c1[3], c2[3];
+          chain_pose(r, pl1, st, P1);
+          chain_pose(r, pl2, st, P2);
+          const float4 s1 = __ldg(r.sph + ps1), s2 = __ldg(r.sph + ps2);
+          const float q1[3] = {s1.x, s1.y, s1.z}, q2[3] = {s2.x, s2.y, s2.z};
+          rot(P1, q1, c1);
+          rot(P2, q2, c2);
+          dx = (c1[0] + P1[9]) - (c2[0] + P2[9]);
+          dy = (c1[1] + P1[10]) - (c2[1] + P2[10]);
+          dz = (c1[2] + P1[11]) - (c2[2] + P2[11]);
+        }
         const float nrm = sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
         const float sc = nrm > 0.0f ? gd / nrm : 0.0f;
         u[0] = dx * sc;

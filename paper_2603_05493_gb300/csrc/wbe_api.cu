@@ -1091,6 +1091,13 @@ int wb_self_collision(wb_robot* robot, int64_t B, const float* link_pose, float*
 int wb_self_collision_tuned(wb_robot* robot, int64_t B, const float* link_pose, float* sphere,
                             float* d_min, int32_t* worst_pair, uint32_t* pair_bits,
                             const wb_tune* tune, void* stream) {
+  return wb_self_collision_dir(robot, B, link_pose, sphere, d_min, worst_pair, nullptr, pair_bits,
+                               tune, stream);
+}
+
+int wb_self_collision_dir(wb_robot* robot, int64_t B, const float* link_pose, float* sphere,
+                          float* d_min, int32_t* worst_pair, float* worst_diff,
+                          uint32_t* pair_bits, const wb_tune* tune, void* stream) {
   g_err.clear();
   if (!robot) return fail(WB_EINVAL, "robot is NULL");
   if (B < 0) return fail(WB_EINVAL, "B < 0");
@@ -1100,12 +1107,15 @@ int wb_self_collision_tuned(wb_robot* robot, int64_t B, const float* link_pose, 
   if ((rc = check_ptr(robot, sphere, "sphere", false))) return rc;
   if ((rc = check_ptr(robot, d_min, "d_min", false))) return rc;
   if ((rc = check_ptr(robot, worst_pair, "worst_pair", d_min != nullptr))) return rc;
+  if ((rc = check_ptr(robot, worst_diff, "worst_diff", false))) return rc;
   if ((rc = check_ptr(robot, pair_bits, "pair_bits", false))) return rc;
   if (!d_min && worst_pair) return fail(WB_EINVAL, "worst_pair without d_min");
+  if (!d_min && worst_diff) return fail(WB_EINVAL, "worst_diff without d_min");
   if (!d_min && !sphere && !pair_bits) return WB_OK;
   DeviceGuard guard(robot->device);
   FwdArgs a{B, nullptr, nullptr, nullptr, const_cast<float*>(link_pose), sphere, d_min,
             worst_pair, nullptr, pair_bits};
+  a.wdiff = worst_diff;
   const int kernel = tune ? tune->kernel : WB_KERNEL_AUTO;
   if (kernel != WB_KERNEL_AUTO && kernel != WB_KERNEL_TREE && kernel != WB_KERNEL_TREE_NOCULL)
     return fail(WB_EINVAL, "the pair kernel takes TREE (culled) or TREE_NOCULL");
@@ -1207,6 +1217,15 @@ int wb_eval_backward_ext(wb_robot* robot, int64_t B, const float* q, const float
                          const float* g_pose, const float* g_sphere, const float* g_dmin,
                          const float* g_tau, float* gq, float* gqd, float* gqdd, float* g_fext,
                          const wb_tune* tune, void* stream) {
+  return wb_eval_backward_dir(robot, B, q, qd, qdd, f_ext, worst_pair, nullptr, g_pose, g_sphere,
+                              g_dmin, g_tau, gq, gqd, gqdd, g_fext, tune, stream);
+}
+
+int wb_eval_backward_dir(wb_robot* robot, int64_t B, const float* q, const float* qd,
+                         const float* qdd, const float* f_ext, const int32_t* worst_pair,
+                         const float* worst_diff, const float* g_pose, const float* g_sphere,
+                         const float* g_dmin, const float* g_tau, float* gq, float* gqd,
+                         float* gqdd, float* g_fext, const wb_tune* tune, void* stream) {
   g_err.clear();
   if (!robot) return fail(WB_EINVAL, "robot is NULL");
   if (B < 0) return fail(WB_EINVAL, "B < 0");
@@ -1226,10 +1245,12 @@ int wb_eval_backward_ext(wb_robot* robot, int64_t B, const float* q, const float
   if ((rc = check_ptr(robot, gqdd, "gqdd", true))) return rc;
   if ((rc = check_ptr(robot, f_ext, "f_ext", false))) return rc;
   if ((rc = check_ptr(robot, g_fext, "g_fext", false))) return rc;
+  if ((rc = check_ptr(robot, worst_diff, "worst_diff", false))) return rc;
   DeviceGuard guard(robot->device);
   BwdArgs a{B, q, qd, qdd, worst_pair, g_pose, g_sphere, g_dmin, g_tau, gq, gqd, gqdd};
   a.fext = f_ext;
   a.g_fext = g_fext;
+  a.wdiff = worst_diff;
   if (g_fext && !g_tau) {  // nothing depends on the external forces but tau
     cudaError_t e0 = cudaMemsetAsync(g_fext, 0, sizeof(float) * 6 * robot->dev.n * B,
                                      static_cast<cudaStream_t>(stream));

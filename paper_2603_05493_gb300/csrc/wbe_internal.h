@@ -117,6 +117,7 @@ struct FwdArgs {
   float* tau;
   uint32_t* bits;
   const float* fext = nullptr;  // [B][n][6] external link wrenches, link coordinates
+  float* wdiff = nullptr;       // [B][3] c_i - c_j of the worst pair (pair stage), or nullptr
 };
 
 // The trajectory cost folded into the backward sweep (a separate kernel
@@ -155,6 +156,8 @@ struct BwdArgs {
   float* gqdd;
   const float* fext = nullptr;  // [B][n][6]
   float* g_fext = nullptr;      // [B][n][6]: -Fbar_k
+  const float* wdiff = nullptr; // [B][3] c_i - c_j of the worst pair from the pair stage, or
+                                // nullptr: the sweep places the two spheres itself
 };
 
 // One problem of an uneven batch: robot index and horizon, and the offsets

@@ -208,19 +208,24 @@ class Robot:
                 "wb_eval")
         return o
 
-    def self_collision(self, link_pose, *, sphere=True, dmin=True, bits=False, out=None,
-                       tune: Tune | None = None, stream=None):
+    def self_collision(self, link_pose, *, sphere=True, dmin=True, bits=False, diff=False,
+                       out=None, tune: Tune | None = None, stream=None):
         """Spheres and the pair map-reduce from given world link poses
-        (B, n, 12); returns a dict with sphere, dmin, worst, bits.  tune:
-        TREE (default, culled blocks) or Tune(kernel=TREE_NOCULL)."""
+        (B, n, 12); returns a dict with sphere, dmin, worst, bits and, with
+        diff=True (or a "diff" tensor in `out`), the worst pair's centre
+        difference (B, 3) for eval_backward's worst_diff
+        (wb_self_collision_dir).  tune: TREE (default, culled blocks) or
+        Tune(kernel=TREE_NOCULL)."""
         B = link_pose.shape[0]
         o = out if out is not None else self.empty_outputs(B, pose=False, sphere=sphere,
                                                            dmin=dmin, tau=False, bits=bits)
+        if out is None and diff:
+            o["diff"] = torch.empty((B, 3), device=self.device, dtype=torch.float32)
         t = (tune or Tune()).c()
-        L.check(self.lib.wb_self_collision_tuned(self.handle, B, _ptr(link_pose),
-                                                 _ptr(o.get("sphere")), _ptr(o.get("dmin")),
-                                                 _ptr(o.get("worst")), _ptr(o.get("bits")),
-                                                 C.byref(t), _stream(stream)),
+        L.check(self.lib.wb_self_collision_dir(self.handle, B, _ptr(link_pose),
+                                               _ptr(o.get("sphere")), _ptr(o.get("dmin")),
+                                               _ptr(o.get("worst")), _ptr(o.get("diff")),
+                                               _ptr(o.get("bits")), C.byref(t), _stream(stream)),
                 "wb_self_collision")
         return o
 
@@ -265,22 +270,23 @@ class Robot:
 
     def eval_backward(self, q, qd, qdd, worst=None, g_pose=None, g_sphere=None, g_dmin=None,
                       g_tau=None, *, tune: Tune | None = None, out=None, f_ext=None,
-                      g_fext=None, stream=None):
+                      g_fext=None, worst_diff=None, stream=None):
         """Gradient of <g_pose,pose> + <g_sphere,sphere> + g_dmin.d_min +
         <g_tau,tau> w.r.t. (q, qd, qdd); with f_ext given (the forward's
-        external wrenches) and a g_fext buffer [B][n][6], also w.r.t. f_ext
-        (wb_eval_backward_ext)."""
+        external wrenches) and a g_fext buffer [B][n][6], also w.r.t. f_ext;
+        worst_diff: the pair stage's centre difference of the worst pair (B, 3)
+        (wb_eval_backward_dir)."""
         B = q.shape[1]
         if out is None:
             out = tuple(torch.empty((self.dof, B), device=self.device, dtype=torch.float32)
                         for _ in range(3))
         gq, gqd, gqdd = out
         t = (tune or Tune()).c()
-        L.check(self.lib.wb_eval_backward_ext(self.handle, B, _ptr(q), _ptr(qd), _ptr(qdd),
-                                              _ptr(f_ext), _ptr(worst), _ptr(g_pose),
-                                              _ptr(g_sphere), _ptr(g_dmin), _ptr(g_tau),
-                                              _ptr(gq), _ptr(gqd), _ptr(gqdd), _ptr(g_fext),
-                                              C.byref(t), _stream(stream)),
+        L.check(self.lib.wb_eval_backward_dir(self.handle, B, _ptr(q), _ptr(qd), _ptr(qdd),
+                                              _ptr(f_ext), _ptr(worst), _ptr(worst_diff),
+                                              _ptr(g_pose), _ptr(g_sphere), _ptr(g_dmin),
+                                              _ptr(g_tau), _ptr(gq), _ptr(gqd), _ptr(gqdd),
+                                              _ptr(g_fext), C.byref(t), _stream(stream)),
                 "wb_eval_backward")
         return gq, gqd, gqdd
 
@@ -617,7 +623,8 @@ class StreamedStep:
                              "g_tau": torch.empty((d, Bc), **f)})
             o = robot.empty_outputs(Bc)
             o.update(gq=torch.empty((d, Bc), **f), gqd=torch.empty((d, Bc), **f),
-                     gqdd=torch.empty((d, Bc), **f))
+                     gqdd=torch.empty((d, Bc), **f),
+                     diff=torch.empty((Bc, 3), **f))  # the worst pair's, stays on the device
             self.dout.append(o)
         self.s_in, self.s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
         # chunks alternate over run_streams compute streams, so that the kernels
@@ -654,7 +661,8 @@ class StreamedStep:
                 rob.self_collision(do["pose"], out=do, stream=sr)
                 rob.eval_backward(di["q"], di["qd"], di["qdd"], do["worst"], di["g_pose"],
                                   di["g_sphere"], di["g_dmin"], di["g_tau"], tune=self.bt,
-                                  out=(do["gq"], do["gqd"], do["gqdd"]), stream=sr)
+                                  out=(do["gq"], do["gqd"], do["gqdd"]), stream=sr,
+                                  worst_diff=do["diff"])
                 self.ev_run[c].record(sr)
             self.s_out.wait_event(self.ev_run[c])
             with torch.cuda.stream(self.s_out):

@@ -199,6 +199,7 @@ def test_humanoid48_bench_step_parity(W, O, shape):
         shapes["pair"] = W.Tune(kernel=3, blocks_per_sm=4)
     q, qd, qdd, gp, gs, gm, gt = bench.humanoid48_inputs(desc, 0, B)  # the bench's inputs
     out = rob.empty_outputs(B)
+    out["diff"] = torch.empty((B, 3), device="cuda")  # as bench.py allocates it
     gout = tuple(torch.empty((desc.dof, B), device="cuda") for _ in range(3))
     bwd = shapes["bwd"]
     groups_per_block = max(1, bwd.configs_per_block // 32 // max(1, bwd.lanes_per_config))
@@ -494,3 +495,40 @@ def test_too_large_robots_are_refused(W):
     o = rob.eval(q, q, q)
     torch.cuda.synchronize()
     assert torch.isfinite(o["tau"]).all()
+
+
+@pytest.mark.parametrize("rname", ["R7", "R48", "mixed"])
+def test_worst_diff_spares_the_backward_its_pair_kinematics(W, O, rname):
+    """wb_self_collision_dir's worst-pair centre difference: c_i - c_j of the
+    oracle's spheres for the reported pair, and wb_eval_backward_dir with it
+    gives the tree kernels' gradients bit for bit as without it, for every
+    segment count the robot takes."""
+    desc, rob = robot(W, rname)
+    B = 203
+    q, qd, qdd = I.uniform_states(desc.dof, B, seed=PY.stable_seed(rname, 71))
+    gp, gs, gm, gt = I.upstream_grads(desc, B, seed=72)
+    tq, tqd, tqdd = cuda(q), cuda(qd), cuda(qdd)
+    o = rob.eval(tq, tqd, tqdd, tune=W.TREE, sphere=False, dmin=False)
+    c = rob.self_collision(o["pose"], diff=True)
+    torch.cuda.synchronize()
+    ref = O.evaluate(desc, q, qd, qdd, want=("sph", "dmin"))
+    worst = c["worst"].cpu().numpy()
+    i, j = desc.pairs[worst, 0], desc.pairs[worst, 1]
+    want = ref["sph"][np.arange(B), i] - ref["sph"][np.arange(B), j]
+    assert np.abs(c["diff"].cpu().numpy() - want).max() <= 2 * PY.POS_TOL
+    for G in (1, 2, 4):
+        if not _segments_available(desc, G):
+            continue
+        tune = W.Tune(kernel=3, lanes_per_config=G)
+        args = (tq, tqd, tqdd, c["worst"], cuda(gp), cuda(gs), cuda(gm), cuda(gt))
+        a = rob.eval_backward(*args, tune=tune)
+        b = rob.eval_backward(*args, tune=tune, worst_diff=c["diff"])
+        torch.cuda.synchronize()
+        for x, y in zip(a, b):
+            assert torch.equal(x, y), G
+    # no pairs: a zero difference
+    nop = desc.with_pairs(np.zeros((0, 2), np.int32))
+    r0 = W.Robot(nop, device=0)
+    c0 = r0.self_collision(o["pose"], diff=True)
+    torch.cuda.synchronize()
+    assert (c0["diff"] == 0).all() and (c0["worst"] == -1).all()
