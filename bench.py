@@ -757,7 +757,9 @@ def run_trajopt(args, rank=0, world=1, local_rank=0):
     out = rob.empty_outputs(B, sphere=False)
     fwd_out = {"pose": out["pose"], "sphere": None, "dmin": None, "worst": None,
                "tau": out["tau"], "bits": None}
-    pair_out = {"sphere": None, "dmin": out["dmin"], "worst": out["worst"], "bits": None}
+    wdiff = torch.empty((B, 3), device=dev)  # the worst pair's centre difference
+    pair_out = {"sphere": None, "dmin": out["dmin"], "worst": out["worst"], "diff": wdiff,
+                "bits": None}
     cost = torch.empty((B,), device=dev)
     gout = tuple(torch.empty((d, B), device=dev) for _ in range(3))
     # the energy term's dt: the time between consecutive samples
@@ -786,6 +788,7 @@ def run_trajopt(args, rank=0, world=1, local_rank=0):
                                       CF.SMOOTH_WEIGHT, CF.LENGTH_WEIGHT, CF.ENERGY_WEIGHT,
                                       dt_sample, d_min=None if hinge else out["dmin"],
                                       worst=None if hinge else out["worst"],
+                                      worst_diff=None if hinge else wdiff,
                                       g_sphere=g_sph if hinge else None, cost=cost, tune=btune,
                                       out=gout)
         mark(3)

@@ -312,7 +312,9 @@ int wb_eval_backward_dir(wb_robot* robot, int64_t B, const float* q, const float
  * segment too) and 4 / 8 warps per pair block, fused
  * kernels with 4, 8, 16 and 32 lanes per configuration, the plain kernels --
  * on random states with all outputs (forward) and all upstream gradients
- * (backward), and returns the fastest choice for each pass with its median
+ * (backward; the tree kernels with the worst pair's centre difference from
+ * wb_self_collision_dir, as wb_eval_backward_dir takes it), and returns the
+ * fastest choice for each pass with its median
  * time (ms, nullable).  Each candidate is timed 5 times, each run after an
  * L2 flush (a memset of twice the L2 size), and ranked by the median. */
 int wb_autotune(wb_robot* robot, int64_t B, wb_tune* fwd, wb_tune* bwd, float* fwd_ms,
@@ -541,6 +543,18 @@ int wb_eval_backward_cost(wb_robot* robot, int64_t B, const float* q, const floa
                           float* cost, float* gq, float* gqd, float* gqdd, const wb_tune* tune,
                           void* stream);
 
+/* wb_eval_backward_cost with the worst pair's centre difference worst_diff
+ * [B][3] from wb_self_collision_dir on the same poses (nullable), as
+ * wb_eval_backward_dir takes it: the same results, without the forward
+ * kinematics of the pair's two links in the sweep. */
+int wb_eval_backward_cost_dir(wb_robot* robot, int64_t B, const float* q, const float* qd,
+                              const float* qdd, const int32_t* worst_pair,
+                              const float* worst_diff, const float* g_pose,
+                              const float* g_sphere, const float* tau, const float* d_min,
+                              const float* tau_lo, const float* tau_hi, const wb_cost_weights* w,
+                              float* cost, float* gq, float* gqd, float* gqdd,
+                              const wb_tune* tune, void* stream);
+
 /* The whole-body evaluation with the joint states evaluated from uniform
  * cubic B-spline control points inside the sweeps (Sec. 4, Eq.
  * bspline-cubic, fused with the evaluation): no q, qd, qdd arrays.
@@ -575,14 +589,25 @@ int wb_eval_backward_spline_cost(wb_robot* robot, const wb_spline* spline,
                                  const wb_cost_weights* w, float* cost, float* gq, float* gqd,
                                  float* gqdd, const wb_tune* tune, void* stream);
 
+/* wb_eval_backward_spline_cost with the worst pair's centre difference
+ * worst_diff [n_traj*T][3] (nullable), as wb_eval_backward_cost_dir. */
+int wb_eval_backward_spline_cost_dir(wb_robot* robot, const wb_spline* spline,
+                                     const int32_t* worst_pair, const float* worst_diff,
+                                     const float* g_pose, const float* g_sphere,
+                                     const float* tau, const float* d_min, const float* tau_lo,
+                                     const float* tau_hi, const wb_cost_weights* w, float* cost,
+                                     float* gq, float* gqd, float* gqdd, const wb_tune* tune,
+                                     void* stream);
+
 /* Autotuner of the control-point path (a setup-time call like wb_autotune:
  * it allocates scratch buffers for n_traj * T configurations, synchronises the
  * device and must not be captured).  Times the depth-first sweep shapes
  * (1 / 2 / 4 / 8 segments as the robot's segment plans allow, and the block
  * sizes wb_autotune tries) of the two kernels this path runs -- wb_eval_spline
  * with link poses and torques (the forward sweep), and
- * wb_eval_backward_spline_cost with the cost weights w (host pointer) and
- * torque limits of +-30 -- on deterministic control points in [-pi/2, pi/2],
+ * wb_eval_backward_spline_cost_dir with the cost weights w (host pointer),
+ * torque limits of +-30 and the worst pairs' centre differences -- on
+ * deterministic control points in [-pi/2, pi/2],
  * 5 runs per candidate, each after an L2 flush, and returns the fastest shape
  * for each with its median time (ms, nullable).  Its choices differ from
  * wb_autotune's where the spline-cost backward kernel prefers another block

@@ -132,6 +132,12 @@ SIGNATURES = {
     "wb_eval_backward_cost": (C.c_int, [p, C.c_int64, p, p, p, p, p, p, p, p, p, p,
                                         C.POINTER(wb_cost_weights), p, p, p, p,
                                         C.POINTER(wb_tune), p]),
+    "wb_eval_backward_cost_dir": (C.c_int, [p, C.c_int64, p, p, p, p, p, p, p, p, p, p, p,
+                                            C.POINTER(wb_cost_weights), p, p, p, p,
+                                            C.POINTER(wb_tune), p]),
+    "wb_eval_backward_spline_cost_dir": (C.c_int, [p, C.POINTER(wb_spline), p, p, p, p, p, p,
+                                                   p, p, C.POINTER(wb_cost_weights), p, p, p,
+                                                   p, C.POINTER(wb_tune), p]),
     "wb_bspline_eval_bc": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_float, p, p,
                                      C.c_int32, p, p, p, p]),
     "wb_bspline_backward_bc": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_float,

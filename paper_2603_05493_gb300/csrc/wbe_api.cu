@@ -1363,6 +1363,18 @@ int wb_eval_backward_spline_cost(wb_robot* robot, const wb_spline* spline,
                                  const float* tau_lo, const float* tau_hi,
                                  const wb_cost_weights* w, float* cost, float* gq, float* gqd,
                                  float* gqdd, const wb_tune* tune, void* stream) {
+  return wb_eval_backward_spline_cost_dir(robot, spline, worst_pair, nullptr, g_pose, g_sphere,
+                                          tau, d_min, tau_lo, tau_hi, w, cost, gq, gqd, gqdd,
+                                          tune, stream);
+}
+
+int wb_eval_backward_spline_cost_dir(wb_robot* robot, const wb_spline* spline,
+                                     const int32_t* worst_pair, const float* worst_diff,
+                                     const float* g_pose, const float* g_sphere,
+                                     const float* tau, const float* d_min, const float* tau_lo,
+                                     const float* tau_hi, const wb_cost_weights* w, float* cost,
+                                     float* gq, float* gqd, float* gqdd, const wb_tune* tune,
+                                     void* stream) {
   g_err.clear();
   if (!robot) return fail(WB_EINVAL, "robot is NULL");
   if (!w) return fail(WB_EINVAL, "weights are NULL");
@@ -1389,6 +1401,7 @@ int wb_eval_backward_spline_cost(wb_robot* robot, const wb_spline* spline,
   if ((rc = check_ptr(robot, gq, "gq", true))) return rc;
   if ((rc = check_ptr(robot, gqd, "gqd", true))) return rc;
   if ((rc = check_ptr(robot, gqdd, "gqdd", true))) return rc;
+  if ((rc = check_ptr(robot, worst_diff, "worst_diff", false))) return rc;
   int kernel = tune ? tune->kernel : WB_KERNEL_AUTO;
   if (kernel == WB_KERNEL_TREE_NOCULL) kernel = WB_KERNEL_TREE;
   if (kernel != WB_KERNEL_AUTO && kernel != WB_KERNEL_TREE)
@@ -1398,6 +1411,7 @@ int wb_eval_backward_spline_cost(wb_robot* robot, const wb_spline* spline,
   DeviceGuard guard(robot->device);
   BwdArgs a{B, nullptr, nullptr, nullptr, worst_pair, g_pose, g_sphere, nullptr, nullptr,
             gq, gqd, gqdd};
+  a.wdiff = worst_diff;
   FusedCost fc;
   fc.tau = tau;
   fc.d_min = d_min;
@@ -1425,6 +1439,18 @@ int wb_eval_backward_cost(wb_robot* robot, int64_t B, const float* q, const floa
                           const float* tau_lo, const float* tau_hi, const wb_cost_weights* w,
                           float* cost, float* gq, float* gqd, float* gqdd, const wb_tune* tune,
                           void* stream) {
+  return wb_eval_backward_cost_dir(robot, B, q, qd, qdd, worst_pair, nullptr, g_pose, g_sphere,
+                                   tau, d_min, tau_lo, tau_hi, w, cost, gq, gqd, gqdd, tune,
+                                   stream);
+}
+
+int wb_eval_backward_cost_dir(wb_robot* robot, int64_t B, const float* q, const float* qd,
+                              const float* qdd, const int32_t* worst_pair,
+                              const float* worst_diff, const float* g_pose,
+                              const float* g_sphere, const float* tau, const float* d_min,
+                              const float* tau_lo, const float* tau_hi, const wb_cost_weights* w,
+                              float* cost, float* gq, float* gqd, float* gqdd,
+                              const wb_tune* tune, void* stream) {
   g_err.clear();
   if (!robot) return fail(WB_EINVAL, "robot is NULL");
   if (!w) return fail(WB_EINVAL, "weights are NULL");
@@ -1453,6 +1479,7 @@ int wb_eval_backward_cost(wb_robot* robot, int64_t B, const float* q, const floa
   if ((rc = check_ptr(robot, gq, "gq", true))) return rc;
   if ((rc = check_ptr(robot, gqd, "gqd", true))) return rc;
   if ((rc = check_ptr(robot, gqdd, "gqdd", true))) return rc;
+  if ((rc = check_ptr(robot, worst_diff, "worst_diff", false))) return rc;
   int kernel = tune ? tune->kernel : WB_KERNEL_AUTO;
   if (kernel == WB_KERNEL_TREE_NOCULL) kernel = WB_KERNEL_TREE;
   if (kernel != WB_KERNEL_AUTO && kernel != WB_KERNEL_TREE)
@@ -1461,6 +1488,7 @@ int wb_eval_backward_cost(wb_robot* robot, int64_t B, const float* q, const floa
     return fail(WB_ETOOBIG, "tree deeper than %d levels", tree_max_depth());
   DeviceGuard guard(robot->device);
   BwdArgs a{B, q, qd, qdd, worst_pair, g_pose, g_sphere, nullptr, nullptr, gq, gqd, gqdd};
+  a.wdiff = worst_diff;
   FusedCost fc;
   fc.tau = tau;
   fc.d_min = d_min;
@@ -2262,6 +2290,26 @@ extern "C" int wb_autotune(wb_robot* robot, int64_t B, wb_tune* fwd, wb_tune* bw
   TuneClock clk;
   if (!clk.init(sc, robot->device)) return fail(WB_ECUDA, "autotune stream/events");
   cudaStream_t s = clk.s;
+  // the worst pairs and their centre differences the backward candidates
+  // read, from the split forward (sweep, then the pair stage) as a step hands
+  // them over; the forward candidates write their own worst pairs
+  int32_t* worst_f = sc.get<int32_t>(B);
+  float* dmin_f = sc.get<float>(B);
+  float* wdiff = sc.get<float>(3 * (size_t)B);
+  if (!worst_f || !dmin_f || !wdiff) return fail(WB_ECUDA, "autotune scratch");
+  bool have_diff = false;
+  if (D.maxdepth <= tree_max_depth()) {
+    const wb_tune tt{WB_KERNEL_TREE, 0, 0, 0};
+    have_diff = wb_eval(robot, B, q, qd, qdd, pose, nullptr, nullptr, nullptr, nullptr,
+                        nullptr, &tt, s) == WB_OK &&
+                wb_self_collision_dir(robot, B, pose, nullptr, dmin, worst, wdiff, nullptr,
+                                      nullptr, s) == WB_OK;
+  }
+  if (!have_diff) {  // the fused fallback: its own forward's worst pairs
+    const int rc0 = wb_eval(robot, B, q, qd, qdd, pose, nullptr, dmin, worst, nullptr, nullptr,
+                            nullptr, s);
+    if (rc0 != WB_OK) return rc0;
+  }
   std::vector<wb_tune> cands = sweep_shapes(D, true, B, robot->num_sms);
   for (int G : {4, 8, 16, 32}) cands.push_back(wb_tune{WB_KERNEL_FUSED, G, 0, 0});
   if (plain_fits(D)) cands.push_back(wb_tune{WB_KERNEL_PLAIN, 0, 0, 0});
@@ -2271,10 +2319,11 @@ extern "C" int wb_autotune(wb_robot* robot, int64_t B, wb_tune* fwd, wb_tune* bw
     for (int pass = 0; pass < 2; ++pass) {
       if (pass == 1 && t.kernel == WB_KERNEL_TREE && t.blocks_per_sm != 8) continue;
       auto run = [&]() {
-        return pass == 0 ? wb_eval(robot, B, q, qd, qdd, pose, sph, dmin, worst, tau, nullptr,
-                                   &t, s)
-                         : wb_eval_backward(robot, B, q, qd, qdd, worst, gpose, gsph, gdmin,
-                                            gtau, gq, gqd, gqdd, &t, s);
+        return pass == 0 ? wb_eval(robot, B, q, qd, qdd, pose, sph, dmin_f, worst_f, tau,
+                                   nullptr, &t, s)
+                         : wb_eval_backward_dir(robot, B, q, qd, qdd, nullptr, worst,
+                                                have_diff ? wdiff : nullptr, gpose, gsph, gdmin,
+                                                gtau, gq, gqd, gqdd, nullptr, &t, s);
       };
       if (run() != WB_OK) continue;  // shape not applicable to this robot
       const float m = clk.time(run);
@@ -2345,8 +2394,13 @@ extern "C" int wb_autotune_spline(wb_robot* robot, int64_t n_traj, int32_t K, in
   if (!clk.init(sc, robot->device)) return fail(WB_ECUDA, "autotune stream/events");
   cudaStream_t s = clk.s;
   const wb_spline sp{U, n_traj, K, T, dt};
-  // the worst pairs and torques the backward reads
-  int rc = wb_eval_spline(robot, &sp, pose, sph, dmin, worst, tau, nullptr, s);
+  // the worst pairs, their centre differences and the torques the backward
+  // reads, as the split forward (sweep, then the pair stage) hands them over
+  float* wdiff = sc.get<float>(3 * (size_t)B);
+  if (!wdiff) return fail(WB_ECUDA, "autotune scratch");
+  int rc = wb_eval_spline(robot, &sp, pose, nullptr, nullptr, nullptr, tau, nullptr, s);
+  if (rc == WB_OK)
+    rc = wb_self_collision_dir(robot, B, pose, sph, dmin, worst, wdiff, nullptr, nullptr, s);
   if (rc != WB_OK) return rc;
   float best_f = 1e30f, best_b = 1e30f;
   wb_tune bf = cands[0], bb = cands[0];
@@ -2355,8 +2409,9 @@ extern "C" int wb_autotune_spline(wb_robot* robot, int64_t n_traj, int32_t K, in
       return wb_eval_spline(robot, &sp, pose, nullptr, nullptr, nullptr, tau, &t, s);
     };
     auto run_b = [&]() {
-      return wb_eval_backward_spline_cost(robot, &sp, worst, nullptr, nullptr, tau, dmin, lim,
-                                          lim + D.d, w, cost, gq, gqd, gqdd, &t, s);
+      return wb_eval_backward_spline_cost_dir(robot, &sp, worst, wdiff, nullptr, nullptr, tau,
+                                              dmin, lim, lim + D.d, w, cost, gq, gqd, gqdd, &t,
+                                              s);
     };
     if (run_f() == WB_OK) {
       const float m = clk.time(run_f);

@@ -313,10 +313,11 @@ class Robot:
                                   energy: float = 0.0, dt_cost: float = 1.0, *, d_min=None,
                                   worst=None, g_pose=None, g_sphere=None, cost=None,
                                   want_cost: bool = True, tune: Tune | None = None, out=None,
-                                  stream=None):
+                                  worst_diff=None, stream=None):
         """eval_backward_cost with the joint states evaluated from control
-        points (wb_eval_backward_spline_cost).  dt_cost is the energy term's
-        dt.  Returns (gq, gqd, gqdd, cost)."""
+        points (wb_eval_backward_spline_cost_dir).  dt_cost is the energy
+        term's dt; worst_diff: the pair stage's worst-pair centre difference.
+        Returns (gq, gqd, gqdd, cost)."""
         sp, B = self._spline(U, T, dt)
         if out is None:
             out = tuple(torch.empty((self.dof, B), device=self.device, dtype=torch.float32)
@@ -327,19 +328,21 @@ class Robot:
         w = L.wb_cost_weights(float(w_coll), float(smooth), float(length), float(energy),
                               float(dt_cost))
         t = (tune or Tune()).c()
-        L.check(self.lib.wb_eval_backward_spline_cost(
-            self.handle, C.byref(sp), _ptr(worst), _ptr(g_pose), _ptr(g_sphere), _ptr(tau),
-            _ptr(d_min), _ptr(tau_lo), _ptr(tau_hi), C.byref(w), _ptr(cost), _ptr(gq),
-            _ptr(gqd), _ptr(gqdd), C.byref(t), _stream(stream)), "wb_eval_backward_spline_cost")
+        L.check(self.lib.wb_eval_backward_spline_cost_dir(
+            self.handle, C.byref(sp), _ptr(worst), _ptr(worst_diff), _ptr(g_pose),
+            _ptr(g_sphere), _ptr(tau), _ptr(d_min), _ptr(tau_lo), _ptr(tau_hi), C.byref(w),
+            _ptr(cost), _ptr(gq), _ptr(gqd), _ptr(gqdd), C.byref(t), _stream(stream)),
+            "wb_eval_backward_spline_cost")
         return gq, gqd, gqdd, cost
 
     def eval_backward_cost(self, q, qd, qdd, tau, tau_lo, tau_hi, w_coll: float,
                            smooth: float = 0.0, length: float = 0.0, energy: float = 0.0,
                            dt: float = 1.0, *, d_min=None, worst=None, g_pose=None,
                            g_sphere=None, cost=None, want_cost: bool = True,
-                           tune: Tune | None = None, out=None, stream=None):
+                           tune: Tune | None = None, out=None, worst_diff=None, stream=None):
         """The trajectory cost folded into the backward sweep
-        (wb_eval_backward_cost): total gradients (gq, gqd, gqdd) of the
+        (wb_eval_backward_cost_dir; worst_diff as eval_backward takes it):
+        total gradients (gq, gqd, gqdd) of the
         per-configuration cost (torque hinges, worst-pair hinge when d_min
         is given, smooth / length / energy terms) plus <g_pose, poses> +
         <g_sphere, centres>, and the cost [B].  Returns (gq, gqd, gqdd,
@@ -354,12 +357,13 @@ class Robot:
         w = L.wb_cost_weights(float(w_coll), float(smooth), float(length), float(energy),
                               float(dt))
         t = (tune or Tune()).c()
-        L.check(self.lib.wb_eval_backward_cost(self.handle, B, _ptr(q), _ptr(qd), _ptr(qdd),
-                                               _ptr(worst), _ptr(g_pose), _ptr(g_sphere),
-                                               _ptr(tau), _ptr(d_min), _ptr(tau_lo),
-                                               _ptr(tau_hi), C.byref(w), _ptr(cost), _ptr(gq),
-                                               _ptr(gqd), _ptr(gqdd), C.byref(t),
-                                               _stream(stream)), "wb_eval_backward_cost")
+        L.check(self.lib.wb_eval_backward_cost_dir(self.handle, B, _ptr(q), _ptr(qd),
+                                                   _ptr(qdd), _ptr(worst), _ptr(worst_diff),
+                                                   _ptr(g_pose), _ptr(g_sphere), _ptr(tau),
+                                                   _ptr(d_min), _ptr(tau_lo), _ptr(tau_hi),
+                                                   C.byref(w), _ptr(cost), _ptr(gq), _ptr(gqd),
+                                                   _ptr(gqdd), C.byref(t), _stream(stream)),
+                "wb_eval_backward_cost")
         return gq, gqd, gqdd, cost
 
 
@@ -715,24 +719,37 @@ def _c(t):
 
 class WholeBodyEval(torch.autograd.Function):
     """(q, qd, qdd) -> (link_pose, sphere, d_min, tau) with the hand-written
-    adjoint kernel as backward.  Saves q, qd, qdd and the worst pair, not the
-    transforms (they are recomputed)."""
+    adjoint kernel as backward.  Saves q, qd, qdd, the worst pair and its
+    centre difference (3 floats a configuration), not the transforms (they
+    are recomputed).  With the default or the tree kernels the forward runs
+    as the sweep, then the pair stage, which also hands the backward the
+    worst pair's centre difference."""
 
     @staticmethod
     def forward(ctx, robot: Robot, q, qd, qdd, tune=None):
         q, qd, qdd = q.contiguous(), qd.contiguous(), qdd.contiguous()
-        o = robot.eval(q, qd, qdd, tune=tune)
+        kern = (tune or Tune()).kernel
+        if kern in (L.WB_KERNEL_AUTO, L.WB_KERNEL_TREE, L.WB_KERNEL_TREE_NOCULL):
+            o = robot.eval(q, qd, qdd, tune=tune, sphere=False, dmin=False)
+            o.update({k: v for k, v in robot.self_collision(o["pose"], diff=True).items()
+                      if k in ("sphere", "dmin", "worst", "diff")})
+        else:
+            o = robot.eval(q, qd, qdd, tune=tune)
+            o["diff"] = None
         ctx.robot = robot
         ctx.tune = tune
-        ctx.save_for_backward(q, qd, qdd, o["worst"])
+        ctx.has_diff = o["diff"] is not None
+        ctx.save_for_backward(q, qd, qdd, o["worst"],
+                              o["diff"] if ctx.has_diff else o["worst"])
         ctx.mark_non_differentiable(o["worst"])
         return o["pose"], o["sphere"], o["dmin"], o["tau"], o["worst"]
 
     @staticmethod
     def backward(ctx, g_pose, g_sph, g_dmin, g_tau, _g_worst):
-        q, qd, qdd, worst = ctx.saved_tensors
+        q, qd, qdd, worst, diff = ctx.saved_tensors
         gq, gqd, gqdd = ctx.robot.eval_backward(q, qd, qdd, worst, _c(g_pose), _c(g_sph),
-                                                _c(g_dmin), _c(g_tau), tune=ctx.tune)
+                                                _c(g_dmin), _c(g_tau), tune=ctx.tune,
+                                                worst_diff=diff if ctx.has_diff else None)
         return None, gq, gqd, gqdd, None
 
 

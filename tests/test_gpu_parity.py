@@ -299,13 +299,18 @@ def test_errors_are_reported(W):
     assert np.isfinite(o["dmin"]).all()
 
 
-def test_autograd_function(W, O):
+@pytest.mark.parametrize("kname", ["default", "fused", "plain"])
+def test_autograd_function(W, O, kname):
+    """The torch.autograd.Function: the default path (sweep, then the pair
+    stage handing the backward its worst-pair difference) and the fused and
+    plain kernels, against the oracle's gradient."""
     desc, rob = robot(W, "R23")
     B = 24
     q, qd, qdd = I.uniform_states(desc.dof, B, 31)
     gp, gs, gm, gt = I.upstream_grads(desc, B, 32)
     tq, tqd, tqdd = (cuda(x).requires_grad_(True) for x in (q, qd, qdd))
-    pose, sph, dmin, tau, worst = W.whole_body_eval(rob, tq, tqd, tqdd)
+    tune = {"default": None, "fused": W.FUSED, "plain": W.PLAIN}[kname]
+    pose, sph, dmin, tau, worst = W.whole_body_eval(rob, tq, tqd, tqdd, tune=tune)
     loss = (pose * cuda(gp)).sum() + (sph * cuda(gs)).sum() + (dmin * cuda(gm)).sum() + \
         (tau * cuda(gt)).sum()
     loss.backward()

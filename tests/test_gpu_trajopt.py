@@ -609,3 +609,36 @@ def test_autotune_spline_refusals(W):
         deep.autotune_spline(2, 8, 16, 0.1)
     assert e.value.code == L.WB_ETOOBIG
 
+
+
+@pytest.mark.parametrize("G", [1, 2, 4])
+def test_fused_cost_with_worst_diff_is_bit_identical(W, G):
+    """The cost-fused backward with the pair stage's worst-pair centre
+    difference (wb_eval_backward_cost_dir, wb_eval_backward_spline_cost_dir)
+    gives the same bits as without it, for array and control-point states."""
+    desc = I.hand_payload(R.r48())
+    rob = W.Robot(desc, device=0)
+    n_traj, K, T, dt = 4, 16, 37, 0.25
+    U = cuda(I.bspline_controls(desc.dof, n_traj, K, seed=PY.stable_seed("wd", G)))
+    tune = W.Tune(kernel=3, lanes_per_config=G)
+    o = rob.eval_spline(U, T, dt, tune=tune, sphere=False, dmin=False)
+    c = rob.self_collision(o["pose"], diff=True)
+    lim = CF.TORQUE_LIMIT
+    lo, hi = cuda(-lim * np.ones(desc.dof)), cuda(lim * np.ones(desc.dof))
+    motion = dict(smooth=CF.SMOOTH_WEIGHT, length=CF.LENGTH_WEIGHT, energy=CF.ENERGY_WEIGHT)
+    dtc = dt * (K - 3) / (T - 1)
+    kw = dict(d_min=c["dmin"], worst=c["worst"], tune=tune)
+    a = rob.eval_backward_spline_cost(U, T, dt, o["tau"], lo, hi, 1.0, dt_cost=dtc, **motion,
+                                      **kw)
+    b = rob.eval_backward_spline_cost(U, T, dt, o["tau"], lo, hi, 1.0, dt_cost=dtc, **motion,
+                                      worst_diff=c["diff"], **kw)
+    q, qd, qdd = W.bspline_eval(U, T, dt)
+    e = rob.eval_backward_cost(q, qd, qdd, o["tau"], lo, hi, 1.0, dt=dtc, **motion, **kw)
+    f = rob.eval_backward_cost(q, qd, qdd, o["tau"], lo, hi, 1.0, dt=dtc, **motion,
+                               worst_diff=c["diff"], **kw)
+    torch.cuda.synchronize()
+    assert (c["dmin"] < 0).float().mean() > 0.5  # most configurations take the pair term
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    for x, y in zip(e, f):
+        assert torch.equal(x, y)
