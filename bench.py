@@ -1061,8 +1061,11 @@ def run_arm7(args, rank=0, world=1, local_rank=0):
         "tree_fwd": dict(hbm(w["tree_fwd"]["bytes"], sweep_ms), ms=sweep_ms,
                          kernel="tree_fwd_seg_kernel" if seg > 1 else "tree_fwd_kernel",
                          bytes_per_eval=w["tree_fwd"]["bytes"]),
-        "pair": dict(hbm(w["pair"]["bytes"], pair_ms), ms=pair_ms, kernel="pair_kernel",
-                     bytes_per_eval=w["pair"]["bytes"]),
+        # robots of at most 32 spheres and 1024 pairs take the library's
+        # one-thread-per-configuration pair kernel
+        "pair": dict(hbm(w["pair"]["bytes"], pair_ms), ms=pair_ms,
+                     kernel="pair_thread_kernel" if desc.S <= 32 and desc.P <= 1024
+                     else "pair_kernel", bytes_per_eval=w["pair"]["bytes"]),
     }
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     print(json.dumps({
