@@ -102,9 +102,12 @@ __global__ void __launch_bounds__(512, 1) tree_bwd_seg_kernel(const __grid_const
   for (int s = 0; s < ns; ++s)
     for (int q = 0; q < 3; ++q) sg.part[q * o + (s * G + sg.g) * 32 + sg.lane] = 0.0f;
   const DevRobot rs = stage_params(r, part + (size_t)CG * 3 * o);
+  // the gradient-row slots behind the link parameters (reserved by the
+  // launch when there are upstream pose or sphere gradients)
+  const GradSlot gs = grad_slot_of(part + (size_t)CG * 3 * o + kParamWords * (size_t)r.n);
   __syncthreads();
   const int64_t b = ((int64_t)blockIdx.x * CG + cg) * 32 + sg.lane;
-  if (b < A.B) tree_bwd_seg<false>(rs, A, FusedCost{}, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b, sg);
+  if (b < A.B) tree_bwd_seg<false>(rs, A, FusedCost{}, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b, sg, gs);
   __syncthreads();
   if (b < A.B) {
     for (int s = sg.g; s < ns; s += G) {
@@ -146,10 +149,11 @@ __global__ void __launch_bounds__(512, 1) tree_bwd_cost_seg_kernel(
   for (int s = 0; s < ns; ++s)
     for (int q = 0; q < 3; ++q) sg.part[q * o + (s * G + sg.g) * 32 + sg.lane] = 0.0f;
   const DevRobot rs = stage_params(r, part + (size_t)CG * (3 * o + G * 32));
+  const GradSlot gs = grad_slot_of(part + (size_t)CG * (3 * o + G * 32) + kParamWords * (size_t)r.n);
   __syncthreads();
   const int64_t b = ((int64_t)blockIdx.x * CG + cg) * 32 + sg.lane;
   float c = 0.0f;
-  if (b < A.B) c = tree_bwd_seg<true>(rs, A, fc, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b, sg);
+  if (b < A.B) c = tree_bwd_seg<true>(rs, A, fc, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b, sg, gs);
   cpart[sg.g * 32 + sg.lane] = c;
   __syncthreads();
   if (b < A.B && sg.g == 0 && fc.cost) {
@@ -349,12 +353,19 @@ size_t tree_seg_smem(const DevRobot& r, int segments, int threads, bool fwd, boo
   return (size_t)seg_groups(segments, threads) * per * sizeof(float) + param_smem(r);
 }
 
+// a backward block's gradient-row slots (GradSlot), when it has upstream pose
+// or sphere gradients to read
+size_t grad_slot_smem(int segments, int threads) {
+  return 16 + (size_t)kGradSlotBytes * 32 * segments * seg_groups(segments, threads);
+}
+
 template <class Args>
 static cudaError_t launch_seg(void (*kern)(DevRobot, Args, int), const DevRobot& r, const Args& a,
-                              int threads, int segments, bool fwd, cudaStream_t s) {
+                              int threads, int segments, bool fwd, size_t extra,
+                              cudaStream_t s) {
   const int t = seg_plan(segments);
   const int CG = seg_groups(segments, threads);
-  const size_t smem = tree_seg_smem(r, segments, threads, fwd, false);
+  const size_t smem = tree_seg_smem(r, segments, threads, fwd, false) + extra;
   cudaError_t e =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -369,7 +380,8 @@ static cudaError_t launch_cost_seg(const DevRobot& r, const BwdArgs& a, const Fu
                                    int threads, int segments, cudaStream_t s) {
   const int t = seg_plan(segments);
   const int CG = seg_groups(segments, threads);
-  const size_t smem = tree_seg_smem(r, segments, threads, false, true);
+  const size_t smem = tree_seg_smem(r, segments, threads, false, true) +
+                      (a.g_pose || a.g_sph ? grad_slot_smem(segments, threads) : 0);
   cudaError_t e = cudaFuncSetAttribute(tree_bwd_cost_seg_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -383,7 +395,7 @@ static cudaError_t launch_cost_seg(const DevRobot& r, const BwdArgs& a, const Fu
 cudaError_t launch_tree_fwd(const DevRobot& r, const FwdArgs& a, int threads, int segments,
                             cudaStream_t s) {
   if (threads <= 0) threads = 128;
-  if (segments > 1) return launch_seg(tree_fwd_seg_kernel, r, a, threads, segments, true, s);
+  if (segments > 1) return launch_seg(tree_fwd_seg_kernel, r, a, threads, segments, true, 0, s);
   const size_t smem = param_smem(r);
   fit_carveout((const void*)tree_fwd_kernel, threads, smem);
   const int64_t grid = (a.B + threads - 1) / threads;
@@ -396,7 +408,8 @@ cudaError_t launch_tree_bwd(const DevRobot& r, const BwdArgs& a, int threads, in
   if (threads <= 0) threads = 128;
   if (segments > 1)
     return fc ? launch_cost_seg(r, a, *fc, threads, segments, s)
-              : launch_seg(tree_bwd_seg_kernel, r, a, threads, segments, false, s);
+              : launch_seg(tree_bwd_seg_kernel, r, a, threads, segments, false,
+                           a.g_pose || a.g_sph ? grad_slot_smem(segments, threads) : 0, s);
   const size_t smem = param_smem(r);
   fit_carveout(fc ? (const void*)tree_bwd_cost_kernel : (const void*)tree_bwd_kernel, threads,
                smem);

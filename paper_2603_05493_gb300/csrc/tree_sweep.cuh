@@ -434,6 +434,32 @@ __device__ __forceinline__ void point_wrench(const float* R, float4 sp, const fl
   w[5] += f[2];
 }
 
+// A thread's slot in shared memory for the upstream gradient rows that the
+// next close reads: 6 float4 at p[q * stride], the link's pose gradient row
+// (12 floats), then its first run of 4 sphere gradients.  Asynchronous copies
+// (cp.async, bypassing L1) fill it while the sweep computes the link's push
+// (a leaf) or its child's close, and the close waits for them: the rows' global
+// latency no longer sits on the close's critical path.
+struct GradSlot {
+  float4* p = nullptr;
+  int stride = 0;
+};
+constexpr int kGradSlotBytes = 6 * 16;  // a thread's slot
+// the slots of a block behind `after` (any float address in dynamic shared
+// memory), rounded up to 16 bytes; the block reserves kGradSlotBytes a thread
+// plus 16 bytes for the rounding
+__device__ __forceinline__ GradSlot grad_slot_of(float* after) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(after);
+  GradSlot g;
+  g.p = reinterpret_cast<float4*>(after + ((16 - (a & 15)) & 15) / 4) + threadIdx.x;
+  g.stride = blockDim.x;
+  return g;
+}
+__device__ __forceinline__ void cp16(float4* dst, const void* src) {
+  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(a), "l"(src));
+}
+
 // With a fused cost (FC, fc) the sweep computes g_tau = [tau > hi] -
 // [tau < lo] + 2 e qd^2 tau and g_dmin = -w [d_min < 0] itself, adds the
 // cost's direct qd / qdd gradients (2 length qd + 2 e qd tau^2, 2 smooth qdd)
@@ -441,11 +467,12 @@ __device__ __forceinline__ void point_wrench(const float* R, float4 sp, const fl
 // of the links it owns (the caller adds the collision term and the segments'
 // shares).  Needs one link per joint (no shared mimic joints).
 // FC: compiled with the fused cost (a separate instantiation, so that the
-// plain sweep keeps its register allocation).
+// plain sweep keeps its register allocation).  gs: the thread's gradient-row
+// slot, or none (the rows are then read with plain loads at each close).
 template <bool FC, class St>
 __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& A,
                                               const FusedCost& fc, const St& st, int64_t b,
-                                              const Seg& sg) {
+                                              const Seg& sg, GradSlot gs = GradSlot{}) {
   const int64_t B = A.B;
   float cost_part = 0.0f;
   const int n = r.n;
@@ -522,15 +549,41 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
   // a packed batch, possibly) is 16-byte aligned
   const bool sph4 = A.g_sph != nullptr && r.sph_vec4 &&
                     (reinterpret_cast<uintptr_t>(A.g_sph) & 15u) == 0;
+  // the link whose gradient rows are on their way into the slot (-1: none)
+  int pend = -1;
+  const bool use_slot = gs.p != nullptr && kin_grad;
+  auto issue = [&](int k) {
+    if (A.g_pose) {
+      const float4* g4 = reinterpret_cast<const float4*>(A.g_pose + (b * n + k) * 12);
+      cp16(gs.p, g4);
+      cp16(gs.p + gs.stride, g4 + 1);
+      cp16(gs.p + 2 * gs.stride, g4 + 2);
+    }
+    if (sph4) {
+      const int e0 = __ldg(r.ls_start + k);
+      if (__ldg(r.ls_start + k + 1) > e0) {
+        const float4* g4 = reinterpret_cast<const float4*>(A.g_sph + (b * r.S + __ldg(r.ls_sph + e0)) * 3);
+        cp16(gs.p + 3 * gs.stride, g4);
+        cp16(gs.p + 4 * gs.stride, g4 + 1);
+        cp16(gs.p + 5 * gs.stride, g4 + 2);
+      }
+    }
+    asm volatile("cp.async.commit_group;");
+    pend = k;
+  };
 
   // link-frame gradient wrench of link k's kinematic outputs (pose, spheres,
   // the worst pair's spheres), from its world pose in cW
   auto wrench = [&](int k, float* w) {
 #pragma unroll
     for (int i = 0; i < 6; ++i) w[i] = 0.0f;
+    const bool slot = pend == k;
+    if (slot) asm volatile("cp.async.wait_group 0;" ::: "memory");
+    pend = -1;
     if (A.g_pose) {
       const float4* g4 = reinterpret_cast<const float4*>(A.g_pose + (b * n + k) * 12);
-      const float4 x0 = __ldg(g4), x1 = __ldg(g4 + 1), x2 = __ldg(g4 + 2);
+      const float4 x0 = slot ? gs.p[0] : __ldg(g4), x1 = slot ? gs.p[gs.stride] : __ldg(g4 + 1),
+                   x2 = slot ? gs.p[2 * gs.stride] : __ldg(g4 + 2);
       const float gg[12] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w, x2.x, x2.y, x2.z, x2.w};
       const float* R = cW;
       float Gm[9];  // R^T Rbar
@@ -546,10 +599,14 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
     }
     if (sph4) {  // runs of 4 spheres: three float4 loads a run
       const int e1 = __ldg(r.ls_start + k + 1);
-      for (int e = __ldg(r.ls_start + k); e < e1; e += 4) {
+      const int ef = __ldg(r.ls_start + k);
+      for (int e = ef; e < e1; e += 4) {
         const int s = __ldg(r.ls_sph + e);
         const float4* g4 = reinterpret_cast<const float4*>(A.g_sph + (b * r.S + s) * 3);
-        const float4 x0 = __ldg(g4), x1 = __ldg(g4 + 1), x2 = __ldg(g4 + 2);
+        const bool fs = slot && e == ef;
+        const float4 x0 = fs ? gs.p[3 * gs.stride] : __ldg(g4),
+                     x1 = fs ? gs.p[4 * gs.stride] : __ldg(g4 + 1),
+                     x2 = fs ? gs.p[5 * gs.stride] : __ldg(g4 + 2);
         const float gg[12] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w, x2.x, x2.y, x2.z, x2.w};
 #pragma unroll
         for (int i = 0; i < 4; ++i) point_wrench(cW, __ldg(r.sph + s + i), gg + 3 * i, w);
@@ -570,8 +627,9 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
     }
   };
 
-  // post-order of the link at depth e; the registers hold its state
-  auto close = [&](int e) {
+  // post-order of the link at depth e; the registers hold its state; tgt:
+  // the closes go on down to depth tgt
+  auto close = [&](int e, int tgt) {
     const int k = __ldg(r.chain + __ldg(r.chain_start + lastk) + e);
     const bool own = !((replayed >> e) & 1u);
     // own terms: f = I a + v x* I v - f_ext, abar = I Fbar,
@@ -596,6 +654,9 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
       for (int i = 0; i < 6; ++i) vb[i] = -t1[i] - t3[i];
       if (kin_grad || k == pl1 || k == pl2) {
         wrench(k, Wr);
+        // the next close's rows, while this one computes
+        if (use_slot && e - 1 >= tgt && !((replayed >> (e - 1)) & 1u))
+          issue(__ldg(r.chain + __ldg(r.chain_start + lastk) + e - 1));
       } else {
 #pragma unroll
         for (int i = 0; i < 6; ++i) Wr[i] = 0.0f;
@@ -849,13 +910,17 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
         if (FC) pf(fc.tau + (int64_t)jn * B + b);
       }
     }
-    while (sp > dep) close(--sp);
+    while (sp > dep) close(--sp, dep);
     flush();
     sp = dep + 1;
+    // a link closed right after its push (a leaf, or the segment's last
+    // link): its rows start on their way now
+    if (use_slot && (pos + 1 >= sg.p1 || __ldg(r.dfs + pos + 1).y <= dep)) issue(kd.x);
     push(kd.x, dep, true);
   }
-  while (sp > 0) close(--sp);
+  while (sp > 0) close(--sp, 0);
   flush();
+  if (pend >= 0) asm volatile("cp.async.wait_group 0;" ::: "memory");
   return cost_part;
 }
 

@@ -992,7 +992,9 @@ static int tree_segments(const wb_robot* R, const wb_tune* tune, int64_t B, int 
   }
   if (G == 1 && threads > 256)
     return fail(WB_EINVAL, "one-segment sweeps take at most 256 threads per block");
-  if (G > 1 && tree_seg_smem(R->dev, G, threads, fwd, !fwd) > 227 * 1024)
+  if (G > 1 && tree_seg_smem(R->dev, G, threads, fwd, !fwd) +
+                       (fwd ? 0 : grad_slot_smem(G, threads)) >
+                   227 * 1024)
     return fail(WB_ETOOBIG, "segmented sweep needs too much shared memory");
   *out = G;
   return WB_OK;

@@ -295,6 +295,8 @@ cudaError_t launch_tree_bwd_spline_cost(const DevRobot& r, const BwdArgs& a, con
                                         const SplineArgs& sp, int threads, int segments,
                                         cudaStream_t s);
 size_t tree_seg_smem(const DevRobot& r, int segments, int threads, bool fwd, bool cost = false);
+// the backward's per-thread gradient-row slots of a segmented block
+size_t grad_slot_smem(int segments, int threads);
 // shared-memory carveout hint: the smallest that holds every block of `threads`
 // threads and `smem` dynamic bytes one SM can keep, leaving the rest to L1
 void fit_carveout(const void* kern, int threads, size_t smem);
