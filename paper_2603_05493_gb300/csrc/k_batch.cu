@@ -117,6 +117,8 @@ __global__ void __launch_bounds__(256, 2) batch_tree_bwd_kernel(const DevRobot* 
   const int pi = warp >> 1, g = warp & 1, bar = 1 + pi;
   int* slot = reinterpret_cast<int*>(sm) + pi;
   float* part = sm + 32 + (size_t)pi * 3 * ns_max * 64;
+  // the gradient-row slots behind every pair's partials
+  const GradSlot gs = grad_slot_of(sm + batch_tree_words(3, ns_max, blockDim.x / 64));
   for (;;) {
     if (g == 0 && lane == 0) *slot = atomicAdd(counter, 1);
     pair_bar(bar);
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(256, 2) batch_tree_bwd_kernel(const DevRobot* 
                        : whole_sweep(r);
     for (int q = 0; q < ns; ++q)
       for (int k = 0; k < 3; ++k) part[k * o + (q * 2 + g) * 32 + lane] = 0.0f;
-    if (act) tree_bwd_seg<false>(r, A, FusedCost{}, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b, sg);
+    if (act) tree_bwd_seg<false>(r, A, FusedCost{}, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b, sg, gs);
     pair_bar(bar);
     if (lane < w.z)
       for (int q = g; q < ns; q += 2) {
@@ -202,8 +204,10 @@ __global__ void __launch_bounds__(256, 3) batch_pair_kernel(const DevRobot* robo
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+// the backward adds each thread's gradient-row slot (GradSlot)
 size_t batch_tree_smem(bool fwd, int ns_max, int threads) {
-  return sizeof(float) * batch_tree_words(fwd ? 1 : 3, ns_max, threads / 64);
+  return sizeof(float) * batch_tree_words(fwd ? 1 : 3, ns_max, threads / 64) +
+         (fwd ? 0 : 16 + (size_t)kGradSlotBytes * threads);
 }
 
 cudaError_t launch_batch_tree_fwd(const DevRobot* robots, const BatchProblemDev* probs, const int4* items,
