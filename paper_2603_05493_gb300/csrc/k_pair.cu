@@ -6,7 +6,8 @@
 namespace wbe {
 
 template <bool FULL, bool BITS, bool CULL>
-__global__ void __launch_bounds__(256, 3) pair_kernel(DevRobot r, PairSchedule32 ps, FwdArgs A) {
+__device__ __forceinline__ void pair_warps(const DevRobot& r, const PairSchedule32& ps,
+                                           const FwdArgs& A) {
   extern __shared__ __align__(128) float smem[];
   const PairPlan pl(r.n, r.Sg, r.P, BITS);
   float4* radw = reinterpret_cast<float4*>(smem);
@@ -21,6 +22,21 @@ __global__ void __launch_bounds__(256, 3) pair_kernel(DevRobot r, PairSchedule32
       pair_one_culled<FULL, BITS>(r, ps, A, b, ws, radw, lane);
     else
       pair_one<FULL, BITS>(r, ps, A, b, ws, radw, lane);
+}
+
+// The culled map-reduce is capped at 72 registers: 7 blocks of 4 warps then
+// fit an SM's registers, and its shared memory holds 7 (the humanoid's culled
+// pair stage: 0.162 ms at 79 registers and 6 blocks, 0.155 ms at 72 and 7,
+// without spills).  The full map-reduce keeps its own allocation (it would
+// spill at 72).
+template <bool FULL, bool BITS>
+__global__ void __maxnreg__(72) pair_kernel(DevRobot r, PairSchedule32 ps, FwdArgs A) {
+  pair_warps<FULL, BITS, true>(r, ps, A);
+}
+template <bool FULL, bool BITS>
+__global__ void __launch_bounds__(256, 3) pair_full_kernel(DevRobot r, PairSchedule32 ps,
+                                                          FwdArgs A) {
+  pair_warps<FULL, BITS, false>(r, ps, A);
 }
 
 // Small robots (at most kThreadMaxS spheres and kThreadMaxP pairs, e.g. a
@@ -160,7 +176,7 @@ static cudaError_t launch_pair_thread(const DevRobot& r, const FwdArgs& a, cudaS
 template <bool FULL, bool BITS, bool CULL>
 static cudaError_t pair_launch_t(const DevRobot& r, const PairSchedule32& ps, const FwdArgs& a,
                                  int grid, int warps, size_t smem, cudaStream_t s, int* occ) {
-  auto kern = pair_kernel<FULL, BITS, CULL>;
+  auto kern = CULL ? pair_kernel<FULL, BITS> : pair_full_kernel<FULL, BITS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;

@@ -521,8 +521,16 @@ __device__ __forceinline__ void pair_one_culled(const DevRobot& r, const PairSch
       const int t = __ffs(cand) - 1;
       cand &= cand - 1u;
       const int a = t >> 2, c = t & 3;
-      const float d2 = dist2(-0.5f * xr4[a], -0.5f * yr4[a], -0.5f * zr4[a], xj[c], yj[c], zj[c]);
-      const float dd = sqrtf(d2) - (pick(RR, a) + rj[c]);
+      // the candidate's centres and radii from shared memory (a dynamic index
+      // into the register copies would put those in local memory)
+      const float d2 = dist2(reinterpret_cast<const float*>(cxc + ro)[a],
+                             reinterpret_cast<const float*>(cyc + ro)[a],
+                             reinterpret_cast<const float*>(czc + ro)[a],
+                             reinterpret_cast<const float*>(cxc + co)[c],
+                             reinterpret_cast<const float*>(cyc + co)[c],
+                             reinterpret_cast<const float*>(czc + co)[c]);
+      const float dd = sqrtf(d2) - (reinterpret_cast<const float*>(crad + ro)[a] +
+                                    reinterpret_cast<const float*>(crad + co)[c]);
       const int slot = 16 * (e.y & 0xFFFF) + t;  // row of blk_pidx: resolved at the end
       if (dd < best) {
         best = dd;
