@@ -78,16 +78,16 @@ PAIR_SRC = ["paper_2603_05493_gb300/csrc/k_pair.cu", "paper_2603_05493_gb300/csr
             "paper_2603_05493_gb300/csrc/spatial.cuh"] + API_SRC
 SPLINE_SRC = ["paper_2603_05493_gb300/csrc/k_traj.cu",
               "paper_2603_05493_gb300/csrc/spline_basis.cuh"] + API_SRC
-TREE_SHA = "9dfc827f64d34d9a4c8807d3135fb153c968e66dcbd2d159fa6f713dd0d81234"
-PAIR_SHA = "9461984026f76ba35a978ed8c21c58525b61a946bd61fd4511937fa2cc7bc632"
-SPLINE_SHA = "67fd8ed4cfa1b35e9693ecee907ae3b451b28eaa8a491575e4c6a075ebf2e655"
+TREE_SHA = "880675b8db6a9db5a03fc5c1fa87d44ba1389009efbdceccb221c26b0a47b9ee"
+PAIR_SHA = "c68b6c43952284e074d55c204d96bdf4eb54c9291f3342badd778a9a24ae744b"
+SPLINE_SHA = "a83f5787bb09e6caeda1fe7efeda7d94c5fb196340261147c0df5fd1d72e00c1"
 MEASURED_TRAFFIC = {  # kernel[@workload]: (sources, their hash, bytes / evaluation)
-    "tree_fwd_seg_kernel": (TREE_SRC, TREE_SHA, (29.71e6 + 80.28e6) / 32768),
-    "pair_kernel": (PAIR_SRC, PAIR_SHA, (80.49e6 + 46.52e6) / 32768),
-    "tree_bwd_seg_kernel": (TREE_SRC, TREE_SHA, (244.46e6 + 36.89e6) / 32768),
-    "tree_fwd_spline_seg_kernel": (TREE_SRC, TREE_SHA, (8.46e6 + 80.84e6) / 32768),
-    "pair_kernel@trajopt48": (PAIR_SRC, PAIR_SHA, (78.59e6 + 2.95e6) / 32768),
-    "tree_bwd_spline_cost_seg_kernel": (TREE_SRC, TREE_SHA, (8.33e6 + 1.78e6) / 32768),
+    "tree_fwd_seg_kernel": (TREE_SRC, TREE_SHA, (29.72e6 + 79.91e6) / 32768),
+    "pair_kernel": (PAIR_SRC, PAIR_SHA, (77.29e6 + 35.13e6) / 32768),
+    "tree_bwd_seg_kernel": (TREE_SRC, TREE_SHA, (240.26e6 + 37.63e6) / 32768),
+    "tree_fwd_spline_seg_kernel": (TREE_SRC, TREE_SHA, (8.45e6 + 80.43e6) / 32768),
+    "pair_kernel@trajopt48": (PAIR_SRC, PAIR_SHA, (77.25e6 + 0.48e6) / 32768),
+    "tree_bwd_spline_cost_seg_kernel": (TREE_SRC, TREE_SHA, (8.72e6 + 1.71e6) / 32768),
     "bspline_bwd_kernel": (SPLINE_SRC, SPLINE_SHA, (18.89e6 + 0.0) / 32768),
 }
 
