@@ -128,7 +128,10 @@ __device__ __forceinline__ void pair_one(const DevRobot& r, const PairSchedule32
     float rs = 0.0f;
     if (s < S) {
       const float4 sp = __ldg(r.sph + s);
-      const float* P = xr + 12 * __ldg(r.sph_link + s);
+      // the link's staged pose as three vector loads (48-byte rows)
+      const float4* P4 = reinterpret_cast<const float4*>(xr) + 3 * __ldg(r.sph_link + s);
+      const float4 p0 = P4[0], p1 = P4[1], p2 = P4[2];
+      const float P[12] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w, p2.x, p2.y, p2.z, p2.w};
       const float cl[3] = {sp.x, sp.y, sp.z};
       rot(P, cl, c);
       c[0] += P[9];
@@ -365,7 +368,10 @@ __device__ __forceinline__ void pair_one_culled(const DevRobot& r, const PairSch
     float rs = 0.0f;
     if (s < S) {
       const float4 sp = __ldg(r.sph + s);
-      const float* P = xr + 12 * __ldg(r.sph_link + s);
+      // the link's staged pose as three vector loads (48-byte rows)
+      const float4* P4 = reinterpret_cast<const float4*>(xr) + 3 * __ldg(r.sph_link + s);
+      const float4 p0 = P4[0], p1 = P4[1], p2 = P4[2];
+      const float P[12] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w, p2.x, p2.y, p2.z, p2.w};
       const float cl[3] = {sp.x, sp.y, sp.z};
       rot(P, cl, c);
       c[0] += P[9];
@@ -389,7 +395,9 @@ __device__ __forceinline__ void pair_one_culled(const DevRobot& r, const PairSch
     const int gl = __ldg(r.grp_link + g);
     if (gl >= 0) {  // one link: its host-made bound, moved with the link
       const float4 L = __ldg(r.grp_loc + g);
-      const float* T = xr + 12 * gl;  // the staged pose
+      const float4* T4 = reinterpret_cast<const float4*>(xr) + 3 * gl;  // the staged pose
+      const float4 t0 = T4[0], t1 = T4[1], t2 = T4[2];
+      const float T[12] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w, t2.x, t2.y, t2.z, t2.w};
       const float cl[3] = {L.x, L.y, L.z};
       float c[3];
       rot(T, cl, c);

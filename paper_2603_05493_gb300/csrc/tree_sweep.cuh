@@ -238,12 +238,17 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
   };
 
   // pre-order of link k at depth dep; own = false replays an ancestor of
-  // the segment (pose, v, a only; no output, no force of its own)
-  auto push = [&](int k, int dep, bool own) {
+  // the segment (pose, v, a only; no output, no force of its own); pre: the
+  // joint states (pq, pqd, pqdd) were loaded ahead by the caller
+  auto push = [&](int k, int dep, bool own, bool pre, float pq, float pqd, float pqdd) {
     if (dyn) flush();  // the parent's force, when it is still pending
     FEnt& E = stk[dep];
     float L[12];
-    link_local(r, k, st, L);
+    {
+      const int jj = __ldg(r.jidx + k);
+      const float th = jj >= 0 ? joint_var(r, k, pre ? pq : st.pos(jj)) : 0.0f;
+      local_xf(r, k, th, L, L + 9);
+    }
     float PW[12], vp[6], ap[6];
     if (dep > 0) {
       if (dep == cdep + 1) {
@@ -292,8 +297,8 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
       const float4 a4 = ldp(reinterpret_cast<const float4*>(r.axis) + k);
       const float ax[3] = {a4.x, a4.y, a4.z};
       const float mm = ldp(reinterpret_cast<const float2*>(r.mimic) + k).x;
-      const float vq = j >= 0 ? mm * st.vel(j) : 0.0f;
-      const float aq = j >= 0 ? mm * st.acc(j) : 0.0f;
+      const float vq = j >= 0 ? mm * (pre ? pqd : st.vel(j)) : 0.0f;
+      const float aq = j >= 0 ? mm * (pre ? pqdd : st.acc(j)) : 0.0f;
       rnea_va(L, L + 9, vp, ap, __ldg(r.jtype + k), ax, vq, aq, cv, ca);
       float F[6];
       if (own) {
@@ -327,22 +332,45 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
   if (sg.p0 > 0) {  // replay the proper ancestors of the first link
     const int k0 = __ldg(r.dfs + sg.p0).x;
     const int c0 = __ldg(r.chain_start + k0), c1 = __ldg(r.chain_start + k0 + 1);
-    for (int c = c0; c < c1 - 1; ++c) push(__ldg(r.chain + c), c - c0, false);
+    for (int c = c0; c < c1 - 1; ++c)
+      push(__ldg(r.chain + c), c - c0, false, false, 0.0f, 0.0f, 0.0f);
     sp = c1 - 1 - c0;
+  }
+  // The joint states of the link pushed next, loaded one link ahead into
+  // registers, so that their latency overlaps the current link's closes and
+  // push (measured on the 48-DoF humanoid at 2 segments x 448 threads:
+  // 0.0985 -> 0.0970 ms against the L2 prefetch hint it replaces).
+  float nq = 0.0f, nqd = 0.0f, nqdd = 0.0f;
+  {
+    const int j0 = sg.p0 < sg.p1 ? __ldg(r.jidx + __ldg(r.dfs + sg.p0).x) : -1;
+    if (j0 >= 0) {
+      nq = st.pos(j0);
+      if (dyn) {
+        nqd = st.vel(j0);
+        nqdd = st.acc(j0);
+      }
+    }
   }
   for (int pos = sg.p0; pos < sg.p1; ++pos) {
     const int2 kd = __ldg(r.dfs + pos);
     const int dep = kd.y;
+    const float cq = nq, cqd = nqd, cqdd = nqdd;
     if (pos + 1 < sg.p1) {  // the next link's joint inputs
       const int jn = __ldg(r.jidx + __ldg(r.dfs + pos + 1).x);
-      if (jn >= 0) st.prefetch(jn, dyn);
+      if (jn >= 0) {
+        nq = st.pos(jn);
+        if (dyn) {
+          nqd = st.vel(jn);
+          nqdd = st.acc(jn);
+        }
+      }
     }
     if (dyn) {
       while (sp > dep) close(--sp);
       flush();
     }
     sp = dep + 1;
-    push(kd.x, dep, true);
+    push(kd.x, dep, true, true, cq, cqd, cqdd);
   }
   if (dyn) {
     while (sp > 0) close(--sp);
