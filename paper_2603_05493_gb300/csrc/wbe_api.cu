@@ -748,6 +748,10 @@ int wb_load_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs* pa
             H.ls_sph[e0 + (e - e0) / 4 * 4] % 4)
           v4 = 0;
     }
+    // then every group of 4 lies on one link (the pair stage places a group
+    // from its link's pose); checked, not assumed
+    for (size_t g = 0; g < H.grp_link.size() && v4; ++g)
+      if (H.grp_link[g] < 0) v4 = 0;
     D.sph_vec4 = v4;
   }
   D.mimic_shared = H.mimic_shared;

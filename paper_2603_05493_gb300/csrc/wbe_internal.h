@@ -25,7 +25,8 @@ struct DevRobot {
   int all_full;              // every pair block holds all 16 pairs
   int sph_vec4;              // S % 4 == 0 and every link's spheres are runs of 4
                              // consecutive indices from a multiple of 4: a link's
-                             // [B][S][3] rows load as float4 triples
+                             // [B][S][3] rows load as float4 triples, and every
+                             // group of 4 spheres lies on one link
   float abase[3];            // base acceleration = -gravity
 
   // per link
