@@ -504,19 +504,23 @@ __device__ __forceinline__ void pair_one_culled(const DevRobot& r, const PairSch
   // would keep (and at most a few more, within the half's rounding).
   const bool keep_lb = rounds * 32 <= 2 * pl.ra_words();
   __half* lb16 = reinterpret_cast<__half*>(xr);
+  // the schedule's byte offsets of a block's two groups in the per-warp
+  // sphere arrays (16 bytes a group) are also their offsets in gb
+  const char* cgb = reinterpret_cast<const char*>(gb);
   float lbmin = inf;
-  uint2 ebest = make_uint2(0u, 0u);
+  int rbest = 0;  // the round of the lane's smallest bound (its entry is
+                  // reloaded once at the end: 0.1408 -> 0.1375 ms on humanoid48)
   for (int rr = 0; rr < rounds; ++rr) {
     const uint2 e = __ldg(ps.ent + rr * 32 + lane);
     __half low = __float2half(inf);  // null entries are never kept
     if ((e.y >> 16) != 0u) {  // a real block
-      const float4 P4 = gb[(e.x & 0xFFFF) >> 4], Q4 = gb[(e.x >> 16) >> 4];
+      const float4 P4 = lds4(cgb, e.x & 0xFFFF), Q4 = lds4(cgb, e.x >> 16);
       const float D2 = fmaxf(dist2(P4.x, P4.y, P4.z, Q4.x, Q4.y, Q4.z), 1e-30f);
       const float dist = D2 * rsqrtf(D2);  // approximate square root
       const float lb = dist - (P4.w + Q4.w);
       if (lb < lbmin) {
         lbmin = lb;
-        ebest = e;
+        rbest = rr;
       }
       low = __float2half_rd(lb - fmaf(dist, 4e-6f, 4e-6f));
     }
@@ -526,8 +530,7 @@ __device__ __forceinline__ void pair_one_culled(const DevRobot& r, const PairSch
   {
     const int kmin = __reduce_min_sync(0xffffffffu, fkey(lbmin));
     const int src = __ffs(__ballot_sync(0xffffffffu, fkey(lbmin) == kmin)) - 1;
-    const uint2 e = make_uint2(__shfl_sync(0xffffffffu, ebest.x, src),
-                               __shfl_sync(0xffffffffu, ebest.y, src));
+    const uint2 e = __ldg(ps.ent + __shfl_sync(0xffffffffu, rbest, src) * 32 + src);
     float d = inf;
     const int t = lane & 15, a = t >> 2, c = t & 3;
     if (lane < 16 && ((e.y >> 16) >> t) & 1u) {
