@@ -631,41 +631,79 @@ __device__ __forceinline__ void pair_one_culled(const DevRobot& r, const PairSch
     if ((e.y >> 16) != 0u) screen_block(e);
     gbest = fminf(gbest, fkey_inv(__reduce_min_sync(0xffffffffu, fkey(best))));
   };
-  for (int rr = 0; rr < rounds; ++rr) {
-    const int idx = rr * 32 + lane;
-    // lb <= bound + tol  <=>  |C_i - C_j| <= t := bound + tol + R_i + R_j,
-    // tested on squares (t >= 0); the tolerance covers the float rounding
-    bool keep = false;
-    if (keep_lb) {  // null entries hold +inf
-      const float lbv = __half2float(lb16[idx]);
-      keep = lbv <= thr || (BITS && lbv <= reach_tol);
-    } else {
-      const uint2 e = __ldg(ps.ent + idx);
-      if ((e.y >> 16) != 0u) {
-        const float4 P4 = gb[(e.x & 0xFFFF) >> 4], Q4 = gb[(e.x >> 16) >> 4];
-        const float D2 = dist2(P4.x, P4.y, P4.z, Q4.x, Q4.y, Q4.z);
-        const float RR2 = P4.w + Q4.w + reach_tol;
-        const float t = fminf(best, gbest) + RR2;
-        keep = (t >= 0.0f && D2 <= t * t) || (BITS && RR2 >= 0.0f && D2 <= RR2 * RR2);
+  if (keep_lb) {
+    // Per chunk of 32 rounds, each lane first marks its surviving blocks in a
+    // bit mask (one half load and one compare a round), then the survivors are
+    // queued in lane order, positions from a warp scan of the lanes' counts,
+    // and screened 32 at a time.  The threshold is refreshed per chunk; the
+    // order of the screening does not change the result (the exact path keeps
+    // the lexicographic (d, index) minimum).
+    for (int r0 = 0; r0 < rounds; r0 += 32) {
+      const int r1 = min(rounds, r0 + 32);
+      const float th = fminf(best, gbest) + reach_tol;
+      uint32_t km = 0u;
+      for (int rr = r0; rr < r1; ++rr) {  // null entries hold +inf
+        const float lbv = __half2float(lb16[rr * 32 + lane]);
+        km |= (lbv <= th || (BITS && lbv <= reach_tol) ? 1u : 0u) << (rr - r0);
+      }
+      const int cnt = __popc(km);
+      int off = cnt;  // inclusive scan of the counts over the lanes
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, off, o);
+        if (lane >= o) off += v;
+      }
+      const int tot = __shfl_sync(0xffffffffu, off, 31);
+      int pos = off - cnt;
+      for (int w0 = 0; w0 < tot; w0 += 32) {
+        while (km && pos < w0 + 32) {
+          const int rr = r0 + __ffs(km) - 1;
+          km &= km - 1u;
+          qu[pos - w0] = (uint32_t)(rr * 32 + lane);
+          ++pos;
+        }
+        __syncwarp();
+        drain(min(32, tot - w0));
+        __syncwarp();
       }
     }
-    const uint32_t ball = __ballot_sync(0xffffffffu, keep);
-    if (keep) qu[qn + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)idx;
-    qn += __popc(ball);
-    if (qn >= 32) {
-      __syncwarp();
-      drain(32);
-      thr = fminf(best, gbest) + reach_tol;
-      __syncwarp();
-      const uint32_t moved = lane + 32 < qn ? qu[lane + 32] : 0u;  // at most 31 left
-      __syncwarp();
-      if (lane + 32 < qn) qu[lane] = moved;
-      qn -= 32;
-      __syncwarp();
+  } else {
+    for (int rr = 0; rr < rounds; ++rr) {
+      const int idx = rr * 32 + lane;
+      // lb <= bound + tol  <=>  |C_i - C_j| <= t := bound + tol + R_i + R_j,
+      // tested on squares (t >= 0); the tolerance covers the float rounding
+      bool keep = false;
+      if (keep_lb) {  // null entries hold +inf
+        const float lbv = __half2float(lb16[idx]);
+        keep = lbv <= thr || (BITS && lbv <= reach_tol);
+      } else {
+        const uint2 e = __ldg(ps.ent + idx);
+        if ((e.y >> 16) != 0u) {
+          const float4 P4 = gb[(e.x & 0xFFFF) >> 4], Q4 = gb[(e.x >> 16) >> 4];
+          const float D2 = dist2(P4.x, P4.y, P4.z, Q4.x, Q4.y, Q4.z);
+          const float RR2 = P4.w + Q4.w + reach_tol;
+          const float t = fminf(best, gbest) + RR2;
+          keep = (t >= 0.0f && D2 <= t * t) || (BITS && RR2 >= 0.0f && D2 <= RR2 * RR2);
+        }
+      }
+      const uint32_t ball = __ballot_sync(0xffffffffu, keep);
+      if (keep) qu[qn + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)idx;
+      qn += __popc(ball);
+      if (qn >= 32) {
+        __syncwarp();
+        drain(32);
+        thr = fminf(best, gbest) + reach_tol;
+        __syncwarp();
+        const uint32_t moved = lane + 32 < qn ? qu[lane + 32] : 0u;  // at most 31 left
+        __syncwarp();
+        if (lane + 32 < qn) qu[lane] = moved;
+        qn -= 32;
+        __syncwarp();
+      }
     }
+    __syncwarp();
+    if (qn > 0) drain(qn);
   }
-  __syncwarp();
-  if (qn > 0) drain(qn);
   bidx = bidx == INT_MAX ? INT_MAX : __ldg(r.blk_pidx + bidx);  // slot -> pair index
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
