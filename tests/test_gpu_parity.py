@@ -254,6 +254,29 @@ def test_edge_cases(W, O):
         PY.check_forward(nop, o, O.evaluate(nop, q, want=("pose", "sph")))
 
 
+def test_joint_angles_far_from_zero(W, O):
+    """The joint sine and cosine (a Cody-Waite reduction to [-pi, pi], then
+    the fast intrinsic) stay within 1e-6 of the FP64 values of the same float
+    angles up to |q| = 1e4 rad, multiples of pi / 2 included; link poses of
+    the planar arm match the oracle there at the usual 1e-5."""
+    desc = R.planar_2link()
+    rob = W.Robot(desc, device=0)
+    rng = np.random.default_rng(2024)
+    half_pi = np.arange(-6366, 6367, 97) * (np.pi / 2)  # up to +-1e4 rad
+    q1 = np.concatenate([np.linspace(-1e4, 1e4, 2001), half_pi, rng.uniform(-50, 50, 500),
+                         [0.0, np.pi, -np.pi, 2 * np.pi, 4e4, -4e4]]).astype(np.float32)
+    B = q1.size
+    q = np.stack([q1, rng.uniform(-np.pi, np.pi, B).astype(np.float32)])
+    ref = O.evaluate(desc, q.astype(np.float64), want=("pose",))
+    c, s = np.cos(q1.astype(np.float64)), np.sin(q1.astype(np.float64))
+    for tune in (W.TREE, W.PLAIN):
+        o = host(rob.eval(cuda(q), tau=False, tune=tune))
+        R0 = o["pose"][:, 0, :9]  # link 1: R_z(q1), row-major
+        assert np.abs(R0[:, 0] - c).max() <= 1e-6 and np.abs(R0[:, 4] - c).max() <= 1e-6
+        assert np.abs(R0[:, 3] - s).max() <= 1e-6 and np.abs(R0[:, 1] + s).max() <= 1e-6
+        assert np.abs(o["pose"] - ref["pose"]).max() <= 1e-5
+
+
 def test_exact_touching_and_ties(W, O):
     """Sliders with exact dyadic positions: touching spheres are not
     colliding, exact ties pick the smallest pair index."""
