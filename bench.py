@@ -78,16 +78,16 @@ PAIR_SRC = ["paper_2603_05493_gb300/csrc/k_pair.cu", "paper_2603_05493_gb300/csr
             "paper_2603_05493_gb300/csrc/spatial.cuh"] + API_SRC
 SPLINE_SRC = ["paper_2603_05493_gb300/csrc/k_traj.cu",
               "paper_2603_05493_gb300/csrc/spline_basis.cuh"] + API_SRC
-TREE_SHA = "880675b8db6a9db5a03fc5c1fa87d44ba1389009efbdceccb221c26b0a47b9ee"
-PAIR_SHA = "c68b6c43952284e074d55c204d96bdf4eb54c9291f3342badd778a9a24ae744b"
-SPLINE_SHA = "a83f5787bb09e6caeda1fe7efeda7d94c5fb196340261147c0df5fd1d72e00c1"
+TREE_SHA = "22b958d8339adbe47cd5a90bffbcbdd185dea54c0876fa60385ba038ff9c5860"
+PAIR_SHA = "ed4157749f8820fbf639b6c280848dcd6853a6a8b947c7c215a88f12fc63e6b9"
+SPLINE_SHA = "3a315575ebaa592361e79aa82b0f73dbff31492182d80a05927c020c19d2cf81"
 MEASURED_TRAFFIC = {  # kernel[@workload]: (sources, their hash, bytes / evaluation)
-    "tree_fwd_seg_kernel": (TREE_SRC, TREE_SHA, (29.72e6 + 79.91e6) / 32768),
-    "pair_kernel": (PAIR_SRC, PAIR_SHA, (77.29e6 + 35.13e6) / 32768),
-    "tree_bwd_seg_kernel": (TREE_SRC, TREE_SHA, (240.26e6 + 37.63e6) / 32768),
-    "tree_fwd_spline_seg_kernel": (TREE_SRC, TREE_SHA, (8.45e6 + 80.43e6) / 32768),
-    "pair_kernel@trajopt48": (PAIR_SRC, PAIR_SHA, (77.25e6 + 0.48e6) / 32768),
-    "tree_bwd_spline_cost_seg_kernel": (TREE_SRC, TREE_SHA, (8.72e6 + 1.71e6) / 32768),
+    "tree_fwd_seg_kernel": (TREE_SRC, TREE_SHA, (30.57e6 + 80.06e6) / 32768),
+    "pair_kernel": (PAIR_SRC, PAIR_SHA, (77.34e6 + 31.51e6) / 32768),
+    "tree_bwd_seg_kernel": (TREE_SRC, TREE_SHA, (240.35e6 + 37.62e6) / 32768),
+    "tree_fwd_spline_seg_kernel": (TREE_SRC, TREE_SHA, (8.57e6 + 80.62e6) / 32768),
+    "pair_kernel@trajopt48": (PAIR_SRC, PAIR_SHA, (77.26e6 + 0.57e6) / 32768),
+    "tree_bwd_spline_cost_seg_kernel": (TREE_SRC, TREE_SHA, (8.71e6 + 1.76e6) / 32768),
     "bspline_bwd_kernel": (SPLINE_SRC, SPLINE_SHA, (18.89e6 + 0.0) / 32768),
 }
 
