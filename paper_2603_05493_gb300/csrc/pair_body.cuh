@@ -414,7 +414,7 @@ __device__ __forceinline__ void pair_one_culled(const DevRobot& r, const PairSch
       const float scale = fabsf(T[9]) + fabsf(T[10]) + fabsf(T[11]) + fabsf(L.x) + fabsf(L.y) +
                           fabsf(L.z);
       gb[g] = make_float4(c[0] + T[9], c[1] + T[10], c[2] + T[11],
-                          fmaf(scale, 1e-6f, fmaf(L.w, 1e-6f, L.w)) + 1e-6f);
+                          fmaf(scale, 1e-6f, fmaf(L.w, 1e-6f, L.w)) + 3e-6f);
     }
   } else {
     for (int s = lane; s < 4 * Sg; s += 32) {
@@ -460,7 +460,7 @@ __device__ __forceinline__ void pair_one_culled(const DevRobot& r, const PairSch
         const float scale = fabsf(T[9]) + fabsf(T[10]) + fabsf(T[11]) + fabsf(L.x) + fabsf(L.y) +
                             fabsf(L.z);
         gb[g] = make_float4(c[0] + T[9], c[1] + T[10], c[2] + T[11],
-                            fmaf(scale, 1e-6f, fmaf(L.w, 1e-6f, L.w)) + 1e-6f);
+                            fmaf(scale, 1e-6f, fmaf(L.w, 1e-6f, L.w)) + 3e-6f);
         continue;
       }
       const int s0 = 4 * g, s1 = min(S, s0 + 4);
@@ -478,7 +478,7 @@ __device__ __forceinline__ void pair_one_culled(const DevRobot& r, const PairSch
       float R = 0.0f;
       for (int s = s0; s < s1; ++s)
         R = fmaxf(R, sqrtf(dist2(cx, cy, cz, xc[s], yc[s], zc[s])) + pick(rad, s - s0));
-      gb[g] = make_float4(cx, cy, cz, fmaf(R, 1e-6f, R) + 1e-6f);  // widened for rounding
+      gb[g] = make_float4(cx, cy, cz, fmaf(R, 1e-6f, R) + 3e-6f);  // widened for rounding
     }
   }
   if (BITS)
@@ -517,12 +517,14 @@ __device__ __forceinline__ void pair_one_culled(const DevRobot& r, const PairSch
       const float4 P4 = lds4(cgb, e.x & 0xFFFF), Q4 = lds4(cgb, e.x >> 16);
       const float D2 = fmaxf(dist2(P4.x, P4.y, P4.z, Q4.x, Q4.y, Q4.z), 1e-30f);
       const float dist = D2 * rsqrtf(D2);  // approximate square root
-      const float lb = dist - (P4.w + Q4.w);
+      // the lower bound widened for the approximate square root: 4e-6 of
+      // the distance here, 2 x 2e-6 in the group radii
+      const float lb = fmaf(dist, 0.999996f, -(P4.w + Q4.w));
       if (lb < lbmin) {
         lbmin = lb;
         rbest = rr;
       }
-      low = __float2half_rd(lb - fmaf(dist, 4e-6f, 4e-6f));
+      low = __float2half_rd(lb);
     }
     if (keep_lb) lb16[rr * 32 + lane] = low;
   }

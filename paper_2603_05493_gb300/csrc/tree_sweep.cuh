@@ -137,6 +137,113 @@ __device__ __forceinline__ void motion_S6t(int jt, const float* ax, float* S) {
   }
 }
 
+// The close's terms with the joint's motion subspace S = [a; 0] (JT = 1,
+// revolute), [0; a] (JT = 2, prismatic) or 0 (JT = 0, fixed), written per
+// joint type so that S's zero half costs nothing (the joint type is
+// warp-uniform: every lane closes the same link).  The same operations, in
+// the same order, as the dense 6-vector forms on the nonzero half.
+//   parent terms: X_k v_pa = v - S qd, X_k a_pa = a - S qdd - v x_m (S qd),
+//                 X_k Fbar_pa = Fbar - S taubar;
+//   gradients:    gq = XF . crf(S) F - ab . crm(S) Xa - vb . crm(S) Xv + S . W,
+//                 vb += qd crf(S) ab (before gq and gqd), gqdd = S . ab,
+//                 gqd = S . vb - S . crf(v) ab.
+template <int JT>
+__device__ __forceinline__ void close_parent_terms(const float* a, float vq, float aq, float tb,
+                                                   const float* cv, const float* ca,
+                                                   const float* cFb, float* Xv, float* Xa,
+                                                   float* XF) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    Xv[i] = cv[i];
+    Xa[i] = ca[i];
+    XF[i] = cFb[i];
+  }
+  if (JT == 0) return;
+  const float s[3] = {a[0] * vq, a[1] * vq, a[2] * vq};
+  float c[3];
+  if (JT == 1) {  // v x_m [s; 0] = [w x s; u x s]
+    float cu[3];
+    cross3(cv, s, c);
+    cross3(cv + 3, s, cu);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      Xv[i] = cv[i] - s[i];
+      Xa[i] = ca[i] - fmaf(a[i], aq, c[i]);
+      Xa[3 + i] = ca[3 + i] - cu[i];
+      XF[i] = fmaf(-a[i], tb, cFb[i]);
+    }
+  } else {  // v x_m [0; s] = [0; w x s]
+    cross3(cv, s, c);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      Xv[3 + i] = cv[3 + i] - s[i];
+      Xa[3 + i] = ca[3 + i] - fmaf(a[i], aq, c[i]);
+      XF[3 + i] = fmaf(-a[i], tb, cFb[3 + i]);
+    }
+  }
+}
+
+template <int JT>
+__device__ __forceinline__ void close_joint_grads(const float* a, float vq, const float* F,
+                                                  const float* ab, float* vb, const float* Wr,
+                                                  const float* cv, const float* Xv,
+                                                  const float* Xa, const float* XF, float& gq,
+                                                  float& gqd, float& gqdd) {
+  gq = gqd = gqdd = 0.0f;
+  if (JT == 0) return;
+  constexpr int w = JT == 1 ? 0 : 3;  // the half of a 6-vector S lives in
+  float t[3], t2[3];
+  if (JT == 1) {  // crf([a; 0]) f = [a x f_n; a x f_f]
+    cross3(a, F, t);
+    cross3(a, F + 3, t2);
+    gq = fmaf(XF[5], t2[2], fmaf(XF[4], t2[1], fmaf(XF[3], t2[0],
+         fmaf(XF[2], t[2], fmaf(XF[1], t[1], XF[0] * t[0])))));
+    cross3(a, ab, t);
+    cross3(a, ab + 3, t2);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      vb[i] = fmaf(vq, t[i], vb[i]);
+      vb[3 + i] = fmaf(vq, t2[i], vb[3 + i]);
+    }
+  } else {  // crf([0; a]) f = [a x f_f; 0]
+    cross3(a, F + 3, t);
+    gq = fmaf(XF[2], t[2], fmaf(XF[1], t[1], XF[0] * t[0]));
+    cross3(a, ab + 3, t);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) vb[i] = fmaf(vq, t[i], vb[i]);
+  }
+  gqdd = dot3(a, ab + w);
+  // the half of crf(v) ab that S picks: [w x ab_n + u x ab_f] or [w x ab_f]
+  float cr[3];
+  if (JT == 1) {
+    float c1[3], c2[3];
+    cross3(cv, ab, c1);
+    cross3(cv + 3, ab + 3, c2);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) cr[i] = c1[i] + c2[i];
+  } else {
+    cross3(cv, ab + 3, cr);
+  }
+  gqd = dot3(a, vb + w) - dot3(a, cr);
+  // crm([a; 0]) m = [a x m_w; a x m_u],  crm([0; a]) m = [0; a x m_w]
+  if (JT == 1) {
+    cross3(a, Xa, t);
+    cross3(a, Xa + 3, t2);
+    gq -= fmaf(ab[5], t2[2], fmaf(ab[4], t2[1], fmaf(ab[3], t2[0],
+          fmaf(ab[2], t[2], fmaf(ab[1], t[1], ab[0] * t[0])))));
+    cross3(a, Xv, t);
+    cross3(a, Xv + 3, t2);
+    gq -= fmaf(vb[5], t2[2], fmaf(vb[4], t2[1], fmaf(vb[3], t2[0],
+          fmaf(vb[2], t[2], fmaf(vb[1], t[1], vb[0] * t[0])))));
+  } else {
+    cross3(a, Xa, t);
+    gq -= fmaf(ab[5], t[2], fmaf(ab[4], t[1], ab[3] * t[0]));
+    cross3(a, Xv, t);
+    gq -= fmaf(vb[5], t[2], fmaf(vb[4], t[1], vb[3] * t[0]));
+  }
+  gq += dot3(a, Wr + w);
+}
+
 __device__ __forceinline__ float dot6t(const float* a, const float* b) {
   float s = 0.0f;
 #pragma unroll
@@ -717,8 +824,6 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
     const int jt = __ldg(r.jtype + k);
     const float4 a4 = ldp(reinterpret_cast<const float4*>(r.axis) + k);
     const float ax[3] = {a4.x, a4.y, a4.z};
-    float S[6];
-    motion_S6t(jt, ax, S);
     const float mm = ldp(reinterpret_cast<const float2*>(r.mimic) + k).x;
     const float vq = j >= 0 ? mm * st.vel(j) : 0.0f;
     float L[12];
@@ -728,37 +833,25 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
     if (e > 0) {
       const float aq = j >= 0 ? mm * st.acc(j) : 0.0f;
       const float tb = fresh ? ctb : stk[e].tb;
-      float sv[6], c6[6];
-#pragma unroll
-      for (int i = 0; i < 6; ++i) sv[i] = S[i] * vq;
-      crm(cv, sv, c6);
-#pragma unroll
-      for (int i = 0; i < 6; ++i) {
-        Xv[i] = cv[i] - sv[i];
-        Xa[i] = ca[i] - fmaf(S[i], aq, c6[i]);
-        XF[i] = fmaf(-S[i], tb, cFb[i]);
-      }
+      if (jt == 1)
+        close_parent_terms<1>(ax, vq, aq, tb, cv, ca, cFb, Xv, Xa, XF);
+      else if (jt == 2)
+        close_parent_terms<2>(ax, vq, aq, tb, cv, ca, cFb, Xv, Xa, XF);
+      else
+        close_parent_terms<0>(ax, vq, aq, tb, cv, ca, cFb, Xv, Xa, XF);
     } else {  // the root: v_pa = 0, a_pa = the base acceleration, Fbar_pa = 0
       const float ap[6] = {0.0f, 0.0f, 0.0f, r.abase[0], r.abase[1], r.abase[2]};
       xf_motion(L, L + 9, ap, Xa);
 #pragma unroll
       for (int i = 0; i < 6; ++i) Xv[i] = XF[i] = 0.0f;
     }
-    float t[6];
-    crf(S, F, t);
-    float gq = dot6t(XF, t);
-    crf(S, ab, t);
-#pragma unroll
-    for (int i = 0; i < 6; ++i) vb[i] = fmaf(vq, t[i], vb[i]);
-    const float gqdd = dot6t(S, ab);
-    crf(cv, ab, t);
-    const float gqd = dot6t(S, vb) - dot6t(S, t);
-    float c6[6];
-    crm(S, Xa, c6);
-    gq -= dot6t(ab, c6);
-    crm(S, Xv, c6);
-    gq -= dot6t(vb, c6);
-    gq += dot6t(S, Wr);
+    float gq, gqd, gqdd;
+    if (jt == 1)
+      close_joint_grads<1>(ax, vq, F, ab, vb, Wr, cv, Xv, Xa, XF, gq, gqd, gqdd);
+    else if (jt == 2)
+      close_joint_grads<2>(ax, vq, F, ab, vb, Wr, cv, Xv, Xa, XF, gq, gqd, gqdd);
+    else
+      close_joint_grads<0>(ax, vq, F, ab, vb, Wr, cv, Xv, Xa, XF, gq, gqd, gqdd);
     if (FC && j >= 0) {
       float dqd = 0.0f, dqdd = 0.0f;  // the cost's direct gradients, once per joint
       if (own) {
