@@ -1196,7 +1196,7 @@ int wb_self_collision_hinge(wb_robot* robot, int64_t B, const float* link_pose, 
   if ((rc = check_ptr(robot, cost, "cost", false))) return rc;
   if ((rc = check_ptr(robot, g_sphere, "g_sphere", false))) return rc;
   DeviceGuard guard(robot->device);
-  const int warps = warps_that_fit(0, hinge_smem_per_warp(robot->dev));
+  const int warps = warps_that_fit(hinge_smem_fixed(robot->dev), hinge_smem_per_warp(robot->dev));
   if (warps == 0) return fail(WB_ETOOBIG, "hinge kernel does not fit on an SM");
   int bps = 0;
   cudaError_t e = hinge_max_blocks_per_sm(robot->dev, warps, &bps);
@@ -1205,7 +1205,7 @@ int wb_self_collision_hinge(wb_robot* robot, int64_t B, const float* link_pose, 
   const int64_t need = (B + warps - 1) / warps;
   const int grid = (int)std::min<int64_t>(need, (int64_t)bps * robot->num_sms);
   HingeArgs a{B, link_pose, eta, w, cost, g_sphere};
-  e = launch_hinge(robot->dev, a, grid, warps, static_cast<cudaStream_t>(stream));
+  e = launch_hinge(robot->dev, robot->sched32, a, grid, warps, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "wb_self_collision_hinge launch");
   return WB_OK;
 }

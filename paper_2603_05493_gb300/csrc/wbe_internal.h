@@ -261,8 +261,9 @@ struct HingeArgs {
   float* g_sph;       // [B][S][3] or nullptr
 };
 size_t hinge_smem_per_warp(const DevRobot& r);
-cudaError_t launch_hinge(const DevRobot& r, const HingeArgs& a, int grid, int warps,
-                         cudaStream_t s);
+size_t hinge_smem_fixed(const DevRobot& r);  // per block, besides the warps' workspaces
+cudaError_t launch_hinge(const DevRobot& r, const PairSchedule32& ps, const HingeArgs& a,
+                         int grid, int warps, cudaStream_t s);
 cudaError_t hinge_max_blocks_per_sm(const DevRobot& r, int warps, int* out);
 
 // trajectory-optimisation ends (k_traj.cu)

@@ -368,6 +368,29 @@ def test_self_collision_from_poses(W, O, rname):
     PY.check_forward(desc, sc, O.evaluate(desc, q, want=("pose", "sph", "dmin")))
 
 
+def test_pair_stage_over_several_pass2_chunks(W, O):
+    """The humanoid with every pair of links at least one joint apart masked
+    in: 1224 pair blocks, 39 rounds of 32, so the culled kernel's pass 2 marks
+    its survivors in two chunks of rounds (32 + 7) with the bounds kept as
+    halves.  Against the oracle (pair bits included) and, d_min and the worst
+    pair, bit for bit against the full map-reduce."""
+    desc = R.r48(min_tree_dist=1)
+    info, rounds = W.plan_info(desc)
+    assert rounds[3] == 39  # lanes of 32: more than one chunk of 32 rounds
+    rob = W.Robot(desc, device=0)
+    B = 157
+    q, qd, qdd = I.uniform_states(desc.dof, B, seed=44)
+    o = rob.eval(cuda(q), cuda(qd), cuda(qdd), sphere=False, dmin=False, tau=False,
+                 tune=W.TREE)
+    ref = O.evaluate(desc, q, want=("pose", "sph", "dmin"))
+    for bits in (True, False):
+        sc = host(rob.self_collision(o["pose"], bits=bits, tune=W.TREE))
+        full = host(rob.self_collision(o["pose"], bits=bits, tune=W.TREE_NOCULL))
+        assert np.array_equal(sc["dmin"], full["dmin"]) and np.array_equal(sc["worst"], full["worst"])
+        sc["pose"] = o["pose"].cpu().numpy()
+        PY.check_forward(desc, sc, ref)
+
+
 @pytest.mark.parametrize("rname", ["R7", "R48"])
 def test_autotune_choice_is_valid_and_exact(W, O, rname, tmp_path):
     desc, rob = robot(W, rname)
