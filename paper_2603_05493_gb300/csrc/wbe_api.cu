@@ -213,8 +213,6 @@ struct HostPlan {
   std::vector<float4> sp, grp_rad, grp_loc;
   std::vector<int16_t> grp_link;
   std::vector<int2> pairs_dev;
-  std::vector<int32_t> adj_start;
-  std::vector<int16_t> adj;
   std::vector<uint32_t> bx;
   std::vector<int32_t> blk_pidx;
   std::vector<int4> lvm;
@@ -430,27 +428,6 @@ static int plan_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs
   const int P = (int)pl.size();
   std::vector<int2> pairs_dev(std::max(P, 1), int2{0, 0});
   for (int p = 0; p < P; ++p) pairs_dev[p] = int2{pl[p].first, pl[p].second};
-  {  // adjacency: per sphere, its partner groups of 4 (ascending) with a
-     // 4-bit mask of the partners in the group: entry = group | mask << 8
-    std::vector<std::vector<int>> nb(S);
-    for (int p = 0; p < P; ++p) {
-      nb[pl[p].first].push_back(pl[p].second);
-      nb[pl[p].second].push_back(pl[p].first);
-    }
-    H.adj_start.assign(S + 1, 0);
-    for (int s2 = 0; s2 < S; ++s2) {
-      std::sort(nb[s2].begin(), nb[s2].end());
-      H.adj_start[s2] = (int32_t)H.adj.size();
-      for (size_t i = 0; i < nb[s2].size();) {
-        const int g = nb[s2][i] >> 2;
-        int mask = 0;
-        while (i < nb[s2].size() && (nb[s2][i] >> 2) == g) mask |= 1 << (nb[s2][i++] & 3);
-        H.adj.push_back((int16_t)(g | mask << 8));
-      }
-    }
-    H.adj_start[S] = (int32_t)H.adj.size();
-    if (H.adj.empty()) H.adj.push_back(0);
-  }
 
   // ---- 4x4 group blocks ----
   const int Sg = std::max((S + 3) / 4, 1);
@@ -764,8 +741,6 @@ int wb_load_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs* pa
   pk.add_vec(H.sp, &D.sph);
   pk.add_vec(H.sph_link, &D.sph_link);
   pk.add_vec(H.pairs_dev, &D.pairs);
-  pk.add_vec(H.adj_start, &D.adj_start);
-  pk.add_vec(H.adj, &D.adj);
   pk.add_vec(H.grp_rad, &D.grp_rad);
   pk.add_vec(H.grp_loc, &D.grp_loc);
   pk.add_vec(H.grp_link, &D.grp_link);

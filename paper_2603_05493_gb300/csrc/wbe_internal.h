@@ -71,12 +71,6 @@ struct DevRobot {
   const float4* grp_loc;     // [Sg] bounding sphere of a one-link group in its link frame
   const int16_t* grp_link;   // [Sg] that link, or -1 (spheres on several links)
   const int32_t* blk_pidx;   // [nblk][16] pair index of (4gi+a, 4gj+b) or -1
-  // sphere adjacency of the masked pairs, by partner group of 4: per sphere
-  // (each pair listed at both spheres), entries group | mask << 8 with
-  // ascending groups and bit a of mask = sphere 4 group + a is a partner; the
-  // summed collision hinge walks it per sphere
-  const int32_t* adj_start;  // [S+1]
-  const int16_t* adj;
 };
 
 // A per-lane schedule of pair blocks for the fused kernel with G lanes per
