@@ -17,23 +17,25 @@
 // survivors are queued from a warp scan of the counts and worked 32 at a
 // time, one block a lane, every masked pair exactly (sqrt distance).  A
 // block's lane sums its pairs' cost and each of its 8 spheres' gradient in
-// pair order into a slot of shared memory; the slots are then added into the
-// per-sphere gradient in a fixed order -- first the row groups, then the
-// column groups, each by the lowest lane of the slots sharing that group,
-// in lane order -- and the lanes' costs by a fixed shuffle tree: no atomics,
-// the same result on every run.
+// pair order; the row spheres' gradients, then (a second phase) the column
+// spheres', go to a slot of shared memory and are added into the per-sphere
+// gradient in a fixed order -- each group's slots by the lowest lane holding
+// that group, in lane order -- and the lanes' costs meet in a fixed shuffle
+// tree: no atomics, the same result on every run.
 #include "spatial.cuh"
 
 namespace wbe {
 
-// per warp, 32-bit words: link poses (staging), the sphere SoA rows x, y, z,
-// the group bounds (float4), the gradient SoA rows gx, gy, gz, 32 block slots
-// and the queue of surviving schedule entries
+// per warp, 32-bit words: link poses while the spheres are placed, then the
+// 32 block slots in the same region; the sphere SoA rows x, y, z, the group
+// bounds (float4), the gradient SoA rows gx, gy, gz and the queue of
+// surviving schedule entries
 struct HingePlan {
-  int xc, yc, zc, gb, gx, gy, gz, slot, q, total;
+  int xc, yc, zc, gb, gx, gy, gz, q, total;
   __host__ __device__ HingePlan(int n, int S) {
     const int s4 = (S + 3) & ~3, m = (s4 + 31) & ~31;
-    const int p = (12 * n + 31) & ~31;
+    const int p0 = (12 * n + 31) & ~31, ps = (32 * kSlotWords + 31) & ~31;
+    const int p = p0 > ps ? p0 : ps;
     xc = p;
     yc = xc + m;
     zc = yc + m;
@@ -41,13 +43,13 @@ struct HingePlan {
     gx = gb + m;  // m >= 4 x groups
     gy = gx + m;
     gz = gy + m;
-    slot = gz + m;
-    q = slot + 32 * kSlotWords;
+    q = gz + m;
     total = q + 64;
   }
-  // a block's slot: its two groups' byte offsets, 12 row and 12 column
-  // gradient floats (an odd stride: the lanes' writes hit distinct banks)
-  static constexpr int kSlotWords = 25;
+  // a block's slot: the 12 gradient floats of its row spheres, then (a second
+  // phase) of its column spheres (an odd stride: the lanes' writes hit
+  // distinct banks)
+  static constexpr int kSlotWords = 13;
 };
 
 size_t hinge_smem_per_warp(const DevRobot& r) {
@@ -65,7 +67,10 @@ __device__ __forceinline__ float p4(const float4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
 
-__global__ void __launch_bounds__(256) hinge_kernel(DevRobot r, PairSchedule32 ps, HingeArgs A) {
+// Three 8-warp blocks an SM (24 warps; the slots share the pose region, so
+// three blocks' workspaces fit): 80 registers a thread (humanoid trajopt48
+// hinge 0.337 -> 0.281 ms against two blocks at 122 registers).
+__global__ void __launch_bounds__(256, 3) hinge_kernel(DevRobot r, PairSchedule32 ps, HingeArgs A) {
   extern __shared__ __align__(16) float smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const int n = r.n, S = r.S, Sg = r.Sg;
@@ -78,7 +83,7 @@ __global__ void __launch_bounds__(256) hinge_kernel(DevRobot r, PairSchedule32 p
   float *xc = ws + pl.xc, *yc = ws + pl.yc, *zc = ws + pl.zc;
   float4* gb = reinterpret_cast<float4*>(ws + pl.gb);
   float *gx = ws + pl.gx, *gy = ws + pl.gy, *gz = ws + pl.gz;
-  float* slot = ws + pl.slot;
+  float* slot = ws;  // over the poses, once the spheres are placed
   uint32_t* qu = reinterpret_cast<uint32_t*>(ws + pl.q);
   const char *cxc = reinterpret_cast<const char*>(xc), *cyc = reinterpret_cast<const char*>(yc),
              *czc = reinterpret_cast<const char*>(zc), *crad = reinterpret_cast<const char*>(radw),
@@ -204,13 +209,14 @@ __global__ void __launch_bounds__(256) hinge_kernel(DevRobot r, PairSchedule32 p
         const int count = min(32, tot - w0);
         // one block a lane: every masked pair exactly, in pair order
         uint32_t key = 0xFFFFFFFFu;  // no block
+        float gr[12];  // the lane's block: its row spheres' gradients, then its columns'
         if (lane < count) {
           const uint2 e = __ldg(ps.ent + qu[lane]);
           const uint32_t ro = e.x & 0xFFFF, co = e.x >> 16, mask = e.y >> 16;
           key = e.x;
           const float4 XR = ld4(cxc, ro), YR = ld4(cyc, ro), ZR = ld4(czc, ro), RR = ld4(crad, ro);
           const float4 XC = ld4(cxc, co), YC = ld4(cyc, co), ZC = ld4(czc, co), RC = ld4(crad, co);
-          float gr[12], gc[12];
+          float gc[12];
 #pragma unroll
           for (int k = 0; k < 12; ++k) gr[k] = gc[k] = 0.0f;
 #pragma unroll
@@ -236,16 +242,20 @@ __global__ void __launch_bounds__(256) hinge_kernel(DevRobot r, PairSchedule32 p
           }
           float* sl = slot + lane * SW;
 #pragma unroll
-          for (int k = 0; k < 12; ++k) {
-            sl[1 + k] = gr[k];
-            sl[13 + k] = gc[k];
-          }
+          for (int k = 0; k < 12; ++k) sl[k] = gr[k];
+#pragma unroll
+          for (int k = 0; k < 12; ++k) gr[k] = gc[k];  // the column side, written next
         }
-        __syncwarp();
         // add the slots into the spheres' gradients: the row groups, then the
         // column groups, each group's slots by their lowest lane in lane order
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
+          if (side == 1 && lane < count) {
+            float* sl = slot + lane * SW;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) sl[k] = gr[k];
+          }
+          __syncwarp();
           const uint32_t grp = side == 0 ? (key & 0xFFFFu) : (key >> 16);  // byte offset
           const uint32_t same = __match_any_sync(0xffffffffu, lane < count ? grp : 0xFFFFFFFFu);
           if (lane < count && (__ffs(same) - 1) == lane) {
@@ -254,7 +264,7 @@ __global__ void __launch_bounds__(256) hinge_kernel(DevRobot r, PairSchedule32 p
             float4* Z4 = reinterpret_cast<float4*>(reinterpret_cast<char*>(gz) + grp);
             float4 ax = *X4, ay = *Y4, az = *Z4;
             for (uint32_t m = same; m; m &= m - 1u) {
-              const float* sl = slot + (__ffs(m) - 1) * SW + 1 + 12 * side;
+              const float* sl = slot + (__ffs(m) - 1) * SW;
               ax.x += sl[0]; ay.x += sl[1]; az.x += sl[2];
               ax.y += sl[3]; ay.y += sl[4]; az.y += sl[5];
               ax.z += sl[6]; ay.z += sl[7]; az.z += sl[8];
