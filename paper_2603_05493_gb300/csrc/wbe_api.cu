@@ -216,7 +216,7 @@ struct HostPlan {
   std::vector<uint32_t> bx;
   std::vector<int32_t> blk_pidx;
   std::vector<int4> lvm;
-  std::vector<int2> dfs;
+  std::vector<int2> dfs, dfs_kj;
   std::vector<int16_t> chain_start, chain;
   int maxdepth = 0;
   int mimic_shared = 0;
@@ -576,6 +576,12 @@ static int plan_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs
   H.jidx.swap(jidx);
   H.dfs_pos.assign(n, 0);
   for (int p = 0; p < n; ++p) H.dfs_pos[H.dfs[p].x] = (int16_t)p;
+  H.dfs_kj.resize(n);
+  for (int p = 0; p < n; ++p) {
+    const int k = H.dfs[p].x;
+    H.dfs_kj[p] = make_int2(k | (H.dfs[p].y << 16),
+                            (H.jidx[k] + 1) | ((child_start[k + 1] - child_start[k]) << 16));
+  }
   // a subtree is the contiguous DFS range up to the next position at the
   // same or a smaller depth
   H.dfs_end.assign(n, (int16_t)n);
@@ -696,6 +702,7 @@ int wb_load_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs* pa
   pk.add_vec(H.lev_links, &D.lev_links);
   pk.add_vec(H.lvm, &D.lvm);
   pk.add_vec(H.dfs, &D.dfs);
+  pk.add_vec(H.dfs_kj, &D.dfs_kj);
   pk.add_vec(H.chain_start, &D.chain_start);
   pk.add_vec(H.chain, &D.chain);
   D.maxdepth = H.maxdepth;

@@ -42,6 +42,8 @@ struct DevRobot {
   const int16_t* lev_start;  // [nlev+1]
   const int16_t* lev_links;  // [n] links grouped by level
   const int2* dfs;           // [n] depth-first pre-order: link, depth
+  const int2* dfs_kj;        // [n] the same positions packed for the forward sweep:
+                             //   link | depth << 16, (joint + 1) | children << 16
   int maxdepth;              // deepest link depth + 1
   int mimic_shared;          // 1 if some joint drives more than one link
   const int16_t* chain_start;// [n+1] ancestor chains (Alg. 1 "linkChain")
