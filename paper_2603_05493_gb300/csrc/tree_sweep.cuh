@@ -952,10 +952,12 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
   // pre-order of link k at depth dep (the registers hold its parent's state);
   // own = false replays an ancestor of the segment (its own contributions
   // are zero)
-  auto push = [&](int k, int dep, bool own) {
+  auto push = [&](int k, int dep, bool own, int j, int nch) {
     float L[12];
-    link_local(r, k, st, L);
-    const int j = __ldg(r.jidx + k);
+    {
+      const float th = j >= 0 ? joint_var(r, k, st.pos(j)) : 0.0f;
+      local_xf(r, k, th, L, L + 9);
+    }
     const int jt = __ldg(r.jtype + k);
     const float4 a4 = ldp(reinterpret_cast<const float4*>(r.axis) + k);
     const float ax[3] = {a4.x, a4.y, a4.z};
@@ -1013,7 +1015,6 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
     const uint32_t bit = 1u << dep;
     accv &= ~bit;
     replayed = own ? (replayed & ~bit) : (replayed | bit);
-    const int nch = __ldg(r.child_start + k + 1) - __ldg(r.child_start + k);
     if (nch > 0) stk[dep].tb = tb;
     if (own && A.g_fext) {  // dL/df_ext,k = -Fbar_k
       float* o = A.g_fext + (b * n + k) * 6;
@@ -1026,17 +1027,22 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
   if (sg.p0 > 0) {  // replay the proper ancestors of the first link
     const int k0 = __ldg(r.dfs + sg.p0).x;
     const int c0 = __ldg(r.chain_start + k0), c1 = __ldg(r.chain_start + k0 + 1);
-    for (int c = c0; c < c1 - 1; ++c) push(__ldg(r.chain + c), c - c0, false);
+    for (int c = c0; c < c1 - 1; ++c) {
+      const int a = __ldg(r.chain + c);
+      push(a, c - c0, false, __ldg(r.jidx + a),
+           __ldg(r.child_start + a + 1) - __ldg(r.child_start + a));
+    }
     sp = c1 - 1 - c0;
   }
   for (int pos = sg.p0; pos < sg.p1; ++pos) {
-    const int2 kd = __ldg(r.dfs + pos);
-    const int dep = kd.y;
+    const int2 kd = __ldg(r.dfs_kj + pos);  // link | depth << 16, (joint + 1) | children << 16
+    const int k = kd.x & 0xFFFF, dep = kd.x >> 16;
+    const int2 kn = pos + 1 < sg.p1 ? __ldg(r.dfs_kj + pos + 1) : make_int2(0, 0);
     // L2 prefetch of the next link's joint inputs.  The gradient rows its
     // close reads are not prefetched: measured slower (the humanoid's
     // backward 0.218 -> 0.210 ms without)
     if (pos + 1 < sg.p1) {
-      const int jn = __ldg(r.jidx + __ldg(r.dfs + pos + 1).x);
+      const int jn = (kn.y & 0xFFFF) - 1;
       if (jn >= 0) {
         st.prefetch(jn, true);
         if (A.g_tau) pf(A.g_tau + (int64_t)jn * B + b);
@@ -1048,8 +1054,8 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
     sp = dep + 1;
     // a link closed right after its push (a leaf, or the segment's last
     // link): its rows start on their way now
-    if (use_slot && (pos + 1 >= sg.p1 || __ldg(r.dfs + pos + 1).y <= dep)) issue(kd.x);
-    push(kd.x, dep, true);
+    if (use_slot && (pos + 1 >= sg.p1 || (kn.x >> 16) <= dep)) issue(k);
+    push(k, dep, true, (kd.y & 0xFFFF) - 1, kd.y >> 16);
   }
   while (sp > 0) close(--sp, 0);
   flush();
