@@ -82,15 +82,16 @@ __device__ __forceinline__ void joint_sincos(float th, float* s, float* c) {
 // Local transform of link k (parent joint frame -> link frame) for joint
 // variable th: T_fixed * J(th).  Revolute: R = R_f R_J(th) with Rodrigues'
 // rotation R_J = c I + s [a]^ + (1-c) a a^T.  Prismatic: p = p_f + R_f a th.
-__device__ __forceinline__ void local_xf(const DevRobot& r, int k, float th, float* R, float* p) {
+// (jt, ident: the link's joint type and whether its fixed rotation is the
+// identity, from a packed table the caller holds)
+__device__ __forceinline__ void local_xf_m(const DevRobot& r, int k, float th, int jt, bool ident,
+                                           float* R, float* p) {
   const float4* T4 = reinterpret_cast<const float4*>(r.Tf + 12 * k);
   const float4 t0 = ldp(T4), t1 = ldp(T4 + 1), t2 = ldp(T4 + 2);
   const float Rf[9] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w, t2.x};
   p[0] = t2.y;
   p[1] = t2.z;
   p[2] = t2.w;
-  const int jt = __ldg(r.jtype + k);
-  const bool ident = __ldg(r.rot_id + k) != 0;
   if (jt == 1) {
     const float4 a = ldp(reinterpret_cast<const float4*>(r.axis) + k);
     float s, c;
@@ -127,6 +128,10 @@ __device__ __forceinline__ void local_xf(const DevRobot& r, int k, float th, flo
       p[2] += Rs[2];
     }
   }
+}
+
+__device__ __forceinline__ void local_xf(const DevRobot& r, int k, float th, float* R, float* p) {
+  local_xf_m(r, k, th, __ldg(r.jtype + k), __ldg(r.rot_id + k) != 0, R, p);
 }
 
 // motion vector m (parent coords) -> child coords

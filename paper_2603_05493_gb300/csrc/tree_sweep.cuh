@@ -262,10 +262,25 @@ __device__ __forceinline__ void compose(const float* P, const float* L, float* W
 }
 
 template <class St>
+__device__ __forceinline__ void link_local_m(const DevRobot& r, int k, int meta, const St& st,
+                                             float* L) {  // meta: lmeta[k]
+  const int j = (meta & 0xFFFF) - 1;
+  const float th = j >= 0 ? joint_var(r, k, st.pos(j)) : 0.0f;
+  local_xf_m(r, k, th, (meta >> 16) & 0xFF, ((meta >> 24) & 1) != 0, L, L + 9);
+}
+template <class St>
 __device__ __forceinline__ void link_local(const DevRobot& r, int k, const St& st, float* L) {
   const int j = __ldg(r.jidx + k);
   const float th = j >= 0 ? joint_var(r, k, st.pos(j)) : 0.0f;
   local_xf(r, k, th, L, L + 9);
+}
+
+// the dfs_kj word of link k, built from the per-link arrays (for the
+// replayed ancestors of a segment, which are not at its DFS positions)
+__device__ __forceinline__ int packed_link(const DevRobot& r, int k) {
+  const int nch = min(__ldg(r.child_start + k + 1) - __ldg(r.child_start + k), 255);
+  return (__ldg(r.lmeta + k) & 0xFFFF) | (nch << 16) | ((int)__ldg(r.jtype + k) << 24) |
+         ((int)__ldg(r.rot_id + k) << 26);
 }
 
 // ---------------------------------------------------------------------------
@@ -319,12 +334,13 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
       for (int i = 0; i < 6; ++i) F[i] = E.F[i];
     }
     pdep = -1;
-    const int j = __ldg(r.jidx + k);
+    const int meta = __ldg(r.lmeta + k);
+    const int j = (meta & 0xFFFF) - 1;
     if (j >= 0) {
       const float4 a4 = ldp(reinterpret_cast<const float4*>(r.axis) + k);
       const float ax[3] = {a4.x, a4.y, a4.z};
       const float mm = ldp(reinterpret_cast<const float2*>(r.mimic) + k).x;
-      const float t = mm * St_dot(__ldg(r.jtype + k), ax, F);
+      const float t = mm * St_dot((meta >> 16) & 0xFF, ax, F);
       float* pt = seg_part(sg, k, 0);
       if (pt) {
         *pt = t;
@@ -335,7 +351,7 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
     }
     if (e > 0) {
       float L[12], up[6];
-      link_local(r, k, st, L);
+      link_local_m(r, k, meta, st, L);
       xf_force_T(L, L + 9, F, up);
 #pragma unroll
       for (int i = 0; i < 6; ++i) pF[i] = stk[e - 1].F[i] + up[i];
@@ -353,14 +369,14 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
   // pre-order of link k at depth dep; own = false replays an ancestor of
   // the segment (pose, v, a only; no output, no force of its own); pre: the
   // joint states (pq, pqd, pqdd) were loaded ahead by the caller
-  auto push = [&](int k, int dep, bool own, bool pre, float pq, float pqd, float pqdd, int jk,
-                  int nch) {
+  auto push = [&](int k, int dep, bool own, bool pre, float pq, float pqd, float pqdd, int ky) {
+    const int jk = (ky & 0xFFFF) - 1, nch = (ky >> 16) & 0xFF, jtk = (ky >> 24) & 3;
     if (dyn) flush();  // the parent's force, when it is still pending
     FEnt& E = stk[dep];
     float L[12];
     {
       const float th = jk >= 0 ? joint_var(r, k, pre ? pq : st.pos(jk)) : 0.0f;
-      local_xf(r, k, th, L, L + 9);
+      local_xf_m(r, k, th, jtk, ((ky >> 26) & 1) != 0, L, L + 9);
     }
     float PW[12], vp[6], ap[6];
     if (dep > 0) {
@@ -412,7 +428,7 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
       const float mm = ldp(reinterpret_cast<const float2*>(r.mimic) + k).x;
       const float vq = j >= 0 ? mm * (pre ? pqd : st.vel(j)) : 0.0f;
       const float aq = j >= 0 ? mm * (pre ? pqdd : st.acc(j)) : 0.0f;
-      rnea_va(L, L + 9, vp, ap, __ldg(r.jtype + k), ax, vq, aq, cv, ca);
+      rnea_va(L, L + 9, vp, ap, jtk, ax, vq, aq, cv, ca);
       float F[6];
       if (own) {
         float I[10];
@@ -447,8 +463,7 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
     const int c0 = __ldg(r.chain_start + k0), c1 = __ldg(r.chain_start + k0 + 1);
     for (int c = c0; c < c1 - 1; ++c) {
       const int a = __ldg(r.chain + c);
-      push(a, c - c0, false, false, 0.0f, 0.0f, 0.0f, __ldg(r.jidx + a),
-           __ldg(r.child_start + a + 1) - __ldg(r.child_start + a));
+      push(a, c - c0, false, false, 0.0f, 0.0f, 0.0f, packed_link(r, a));
     }
     sp = c1 - 1 - c0;
   }
@@ -489,7 +504,7 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
       flush();
     }
     sp = dep + 1;
-    push(k, dep, true, true, cq, cqd, cqdd, (kd.y & 0xFFFF) - 1, kd.y >> 16);
+    push(k, dep, true, true, cq, cqd, cqdd, kd.y);
   }
   if (dyn) {
     while (sp > 0) close(--sp);
@@ -832,14 +847,15 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
       }
     }
     pdep = -1;
-    const int j = __ldg(r.jidx + k);
-    const int jt = __ldg(r.jtype + k);
+    const int meta = __ldg(r.lmeta + k);
+    const int j = (meta & 0xFFFF) - 1;
+    const int jt = (meta >> 16) & 0xFF;
     const float4 a4 = ldp(reinterpret_cast<const float4*>(r.axis) + k);
     const float ax[3] = {a4.x, a4.y, a4.z};
     const float mm = ldp(reinterpret_cast<const float2*>(r.mimic) + k).x;
     const float vq = j >= 0 ? mm * st.vel(j) : 0.0f;
     float L[12];
-    link_local(r, k, st, L);
+    link_local_m(r, k, meta, st, L);
     // the parent terms X_k v_pa, X_k a_pa, X_k Fbar_pa from the link's state
     float Xv[6], Xa[6], XF[6];
     if (e > 0) {
@@ -952,13 +968,13 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
   // pre-order of link k at depth dep (the registers hold its parent's state);
   // own = false replays an ancestor of the segment (its own contributions
   // are zero)
-  auto push = [&](int k, int dep, bool own, int j, int nch) {
+  auto push = [&](int k, int dep, bool own, int ky) {
+    const int j = (ky & 0xFFFF) - 1, nch = (ky >> 16) & 0xFF, jt = (ky >> 24) & 3;
     float L[12];
     {
       const float th = j >= 0 ? joint_var(r, k, st.pos(j)) : 0.0f;
-      local_xf(r, k, th, L, L + 9);
+      local_xf_m(r, k, th, jt, ((ky >> 26) & 1) != 0, L, L + 9);
     }
-    const int jt = __ldg(r.jtype + k);
     const float4 a4 = ldp(reinterpret_cast<const float4*>(r.axis) + k);
     const float ax[3] = {a4.x, a4.y, a4.z};
     const float mm = ldp(reinterpret_cast<const float2*>(r.mimic) + k).x;
@@ -1029,8 +1045,7 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
     const int c0 = __ldg(r.chain_start + k0), c1 = __ldg(r.chain_start + k0 + 1);
     for (int c = c0; c < c1 - 1; ++c) {
       const int a = __ldg(r.chain + c);
-      push(a, c - c0, false, __ldg(r.jidx + a),
-           __ldg(r.child_start + a + 1) - __ldg(r.child_start + a));
+      push(a, c - c0, false, packed_link(r, a));
     }
     sp = c1 - 1 - c0;
   }
@@ -1055,7 +1070,7 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
     // a link closed right after its push (a leaf, or the segment's last
     // link): its rows start on their way now
     if (use_slot && (pos + 1 >= sg.p1 || (kn.x >> 16) <= dep)) issue(k);
-    push(k, dep, true, (kd.y & 0xFFFF) - 1, kd.y >> 16);
+    push(k, dep, true, kd.y);
   }
   while (sp > 0) close(--sp, 0);
   flush();

@@ -217,6 +217,7 @@ struct HostPlan {
   std::vector<int32_t> blk_pidx;
   std::vector<int4> lvm;
   std::vector<int2> dfs, dfs_kj;
+  std::vector<int> lmeta;
   std::vector<int16_t> chain_start, chain;
   int maxdepth = 0;
   int mimic_shared = 0;
@@ -579,9 +580,14 @@ static int plan_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs
   H.dfs_kj.resize(n);
   for (int p = 0; p < n; ++p) {
     const int k = H.dfs[p].x;
-    H.dfs_kj[p] = make_int2(k | (H.dfs[p].y << 16),
-                            (H.jidx[k] + 1) | ((child_start[k + 1] - child_start[k]) << 16));
+    const int nch = std::min(child_start[k + 1] - child_start[k], 255);
+    H.dfs_kj[p] = make_int2(k | (H.dfs[p].y << 16), (H.jidx[k] + 1) | (nch << 16) |
+                                                        ((int)jtype[k] << 24) |
+                                                        ((int)rot_id[k] << 26));
   }
+  H.lmeta.resize(n);
+  for (int k = 0; k < n; ++k)
+    H.lmeta[k] = (H.jidx[k] + 1) | ((int)jtype[k] << 16) | ((int)rot_id[k] << 24);
   // a subtree is the contiguous DFS range up to the next position at the
   // same or a smaller depth
   H.dfs_end.assign(n, (int16_t)n);
@@ -703,6 +709,7 @@ int wb_load_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs* pa
   pk.add_vec(H.lvm, &D.lvm);
   pk.add_vec(H.dfs, &D.dfs);
   pk.add_vec(H.dfs_kj, &D.dfs_kj);
+  pk.add_vec(H.lmeta, &D.lmeta);
   pk.add_vec(H.chain_start, &D.chain_start);
   pk.add_vec(H.chain, &D.chain);
   D.maxdepth = H.maxdepth;
