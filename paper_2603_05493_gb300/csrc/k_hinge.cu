@@ -95,7 +95,12 @@ __global__ void __launch_bounds__(256, 3) hinge_kernel(DevRobot r, PairSchedule3
     {
       const float4* src = reinterpret_cast<const float4*>(A.pose + b * (int64_t)n * 12);
       float4* dst = reinterpret_cast<float4*>(P);
-      for (int i = lane; i < 3 * n; i += 32) dst[i] = __ldg(src + i);
+      for (int i = lane; i < 3 * n; i += 32) {  // asynchronous copies into shared memory
+        const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(dst + i));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(a), "l"(src + i));
+      }
+      asm volatile("cp.async.commit_group;");
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
     __syncwarp();
     if (r.sph_vec4) {  // every group of 4 on one link: a lane a group
