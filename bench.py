@@ -78,17 +78,17 @@ PAIR_SRC = ["paper_2603_05493_gb300/csrc/k_pair.cu", "paper_2603_05493_gb300/csr
             "paper_2603_05493_gb300/csrc/spatial.cuh"] + API_SRC
 SPLINE_SRC = ["paper_2603_05493_gb300/csrc/k_traj.cu",
               "paper_2603_05493_gb300/csrc/spline_basis.cuh"] + API_SRC
-TREE_SHA = "44b93f9bb9837819ed1648f1bc271c0abdb3aa8f018a1cb2ad0badb6731aad77"
-PAIR_SHA = "86ba7b8f5141e453462af060b5908cf4c2b0dc2f059745d975737b4e1e06b15e"
-SPLINE_SHA = "3a315575ebaa592361e79aa82b0f73dbff31492182d80a05927c020c19d2cf81"
+TREE_SHA = "f31d787b4ea96f5863634071a654b6bfc564688d080995f9024cb751c5aac711"
+PAIR_SHA = "40e7e5a0a4b08633bf07ce9a4f70adf76ed93a9a0520ff54123c35b3ad4ab052"
+SPLINE_SHA = "c213996357ba77815134538fdd745f18c358acd23b858546555e750d118b8b43"
 MEASURED_TRAFFIC = {  # kernel[@workload]: (sources, their hash, bytes / evaluation)
-    "tree_fwd_seg_kernel": (TREE_SRC, TREE_SHA, (30.47e6 + 80.09e6) / 32768),
-    "pair_kernel": (PAIR_SRC, PAIR_SHA, (77.29e6 + 32.11e6) / 32768),
-    "tree_bwd_seg_kernel": (TREE_SRC, TREE_SHA, (239.54e6 + 37.19e6) / 32768),
-    "tree_fwd_spline_seg_kernel": (TREE_SRC, TREE_SHA, (8.59e6 + 80.49e6) / 32768),
-    "pair_kernel@trajopt48": (PAIR_SRC, PAIR_SHA, (77.26e6 + 0.50e6) / 32768),
-    "tree_bwd_spline_cost_seg_kernel": (TREE_SRC, TREE_SHA, (8.71e6 + 2.32e6) / 32768),
-    "bspline_bwd_kernel": (SPLINE_SRC, SPLINE_SHA, (18.89e6 + 0.0) / 32768),
+    "tree_fwd_seg_kernel": (TREE_SRC, TREE_SHA, (29.54e6 + 79.11e6) / 32768),
+    "pair_kernel": (PAIR_SRC, PAIR_SHA, (77.30e6 + 32.57e6) / 32768),
+    "tree_bwd_seg_kernel": (TREE_SRC, TREE_SHA, (240.54e6 + 38.36e6) / 32768),
+    "tree_fwd_spline_seg_kernel": (TREE_SRC, TREE_SHA, (8.44e6 + 80.68e6) / 32768),
+    "pair_kernel@trajopt48": (PAIR_SRC, PAIR_SHA, (77.26e6 + 0.67e6) / 32768),
+    "tree_bwd_spline_cost_seg_kernel": (TREE_SRC, TREE_SHA, (8.72e6 + 2.30e6) / 32768),
+    "bspline_bwd_kernel": (SPLINE_SRC, SPLINE_SHA, (18.90e6 + 0.0) / 32768),
 }
 
 
