@@ -152,3 +152,28 @@ def test_hinge_full_size_humanoid_sampled_and_deterministic(W, O):
     ref_cost, ref_g = O.pair_hinge(desc, q[:, idx], eta, w)
     d, P = pair_distances(O, desc, q[:, idx])
     check(desc, cost.cpu().numpy()[idx], g.cpu().numpy()[idx], ref_cost, ref_g, d, P, eta, w)
+
+
+def test_hinge_without_pairs_and_over_two_chunks(W, O):
+    """No masked pairs: zero cost and gradient.  The humanoid with every pair
+    of links a joint apart masked in (39 rounds of 32 pair blocks, two
+    chunks of the block walk) against the oracle."""
+    desc = R.r7().with_pairs(np.zeros((0, 2), np.int32))
+    rob = W.Robot(desc, device=0)
+    q, qd, qdd = I.uniform_states(desc.dof, 45, seed=12)
+    o = rob.eval(cuda(q), tau=False)
+    cost, g = rob.self_collision_hinge(o["pose"], 0.05, 1.0)
+    torch.cuda.synchronize()
+    assert (cost.cpu().numpy() == 0.0).all() and (g.cpu().numpy() == 0.0).all()
+    desc = R.r48(min_tree_dist=1)
+    rob = W.Robot(desc, device=0)
+    assert W.plan_info(desc)[1][3] == 39
+    q, qd, qdd = I.uniform_states(desc.dof, 53, seed=13)
+    o = rob.eval(cuda(q), tau=False)
+    eta, w = 0.02, 0.7
+    cost, g = rob.self_collision_hinge(o["pose"], eta, w)
+    torch.cuda.synchronize()
+    ref_cost, ref_g = O.pair_hinge(desc, q, eta, w)
+    d, P = pair_distances(O, desc, q)
+    kept = check(desc, cost.cpu().numpy(), g.cpu().numpy(), ref_cost, ref_g, d, P, eta, w)
+    assert kept > 0.75
