@@ -483,11 +483,11 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
     }
   }
   for (int pos = sg.p0; pos < sg.p1; ++pos) {
-    // link | depth << 16, (joint + 1) | children << 16 of this position: one
+    // link | depth << 8, (joint + 1) | children << 16 of this position: one
     // load for what the DFS order, the joint index and the child table gave
     // in four (humanoid48 forward 0.0898 -> 0.0885 ms)
     const int2 kd = __ldg(r.dfs_kj + pos);
-    const int k = kd.x & 0xFFFF, dep = kd.x >> 16;
+    const int k = kd.x & 0xFF, dep = (kd.x >> 8) & 0xFF;
     const float cq = nq, cqd = nqd, cqdd = nqdd;
     if (pos + 1 < sg.p1) {  // the next link's joint inputs
       const int jn = (__ldg(r.dfs_kj + pos + 1).y & 0xFFFF) - 1;
@@ -704,7 +704,7 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
   // bit e: entry e is an ancestor replayed for this segment (no own terms),
   // its acc holds children's sums
   uint32_t replayed = 0u, accv = 0u;
-  int lastk = 0;  // last pushed link; the stack holds its ancestor chain
+  int lcs = 0;  // where the last pushed link's ancestor chain starts (the stack holds it)
   const bool kin_grad = A.g_pose != nullptr || A.g_sph != nullptr;
   // sphere gradients of a link as float4 triples: the robot's spheres come
   // in runs of 4 (then b S + s is a multiple of 4) and the array (a slice of
@@ -792,7 +792,7 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
   // post-order of the link at depth e; the registers hold its state; tgt:
   // the closes go on down to depth tgt
   auto close = [&](int e, int tgt) {
-    const int k = __ldg(r.chain + __ldg(r.chain_start + lastk) + e);
+    const int k = __ldg(r.chain + lcs + e);
     const bool own = !((replayed >> e) & 1u);
     // own terms: f = I a + v x* I v - f_ext, abar = I Fbar,
     // vbar = -crf(Fbar) I v - I crm(v) Fbar, and the gradient wrench
@@ -818,7 +818,7 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
         wrench(k, Wr);
         // the next close's rows, while this one computes
         if (use_slot && e - 1 >= tgt && !((replayed >> (e - 1)) & 1u))
-          issue(__ldg(r.chain + __ldg(r.chain_start + lastk) + e - 1));
+          issue(__ldg(r.chain + lcs + e - 1));
       } else {
 #pragma unroll
         for (int i = 0; i < 6; ++i) Wr[i] = 0.0f;
@@ -968,7 +968,7 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
   // pre-order of link k at depth dep (the registers hold its parent's state);
   // own = false replays an ancestor of the segment (its own contributions
   // are zero)
-  auto push = [&](int k, int dep, bool own, int ky) {
+  auto push = [&](int k, int dep, bool own, int ky, int cs) {
     const int j = (ky & 0xFFFF) - 1, nch = (ky >> 16) & 0xFF, jt = (ky >> 24) & 3;
     float L[12];
     {
@@ -1027,7 +1027,7 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
     }
     ctb = tb;
     fresh = true;
-    lastk = k;
+    lcs = cs;
     const uint32_t bit = 1u << dep;
     accv &= ~bit;
     replayed = own ? (replayed & ~bit) : (replayed | bit);
@@ -1045,13 +1045,13 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
     const int c0 = __ldg(r.chain_start + k0), c1 = __ldg(r.chain_start + k0 + 1);
     for (int c = c0; c < c1 - 1; ++c) {
       const int a = __ldg(r.chain + c);
-      push(a, c - c0, false, packed_link(r, a));
+      push(a, c - c0, false, packed_link(r, a), __ldg(r.chain_start + a));
     }
     sp = c1 - 1 - c0;
   }
   for (int pos = sg.p0; pos < sg.p1; ++pos) {
-    const int2 kd = __ldg(r.dfs_kj + pos);  // link | depth << 16, (joint + 1) | children << 16
-    const int k = kd.x & 0xFFFF, dep = kd.x >> 16;
+    const int2 kd = __ldg(r.dfs_kj + pos);  // link | depth << 8 | chain start << 16, joint word
+    const int k = kd.x & 0xFF, dep = (kd.x >> 8) & 0xFF;
     const int2 kn = pos + 1 < sg.p1 ? __ldg(r.dfs_kj + pos + 1) : make_int2(0, 0);
     // L2 prefetch of the next link's joint inputs.  The gradient rows its
     // close reads are not prefetched: measured slower (the humanoid's
@@ -1069,8 +1069,8 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
     sp = dep + 1;
     // a link closed right after its push (a leaf, or the segment's last
     // link): its rows start on their way now
-    if (use_slot && (pos + 1 >= sg.p1 || (kn.x >> 16) <= dep)) issue(k);
-    push(k, dep, true, kd.y);
+    if (use_slot && (pos + 1 >= sg.p1 || ((kn.x >> 8) & 0xFF) <= dep)) issue(k);
+    push(k, dep, true, kd.y, kd.x >> 16);
   }
   while (sp > 0) close(--sp, 0);
   flush();

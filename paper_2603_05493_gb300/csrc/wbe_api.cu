@@ -581,9 +581,9 @@ static int plan_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs
   for (int p = 0; p < n; ++p) {
     const int k = H.dfs[p].x;
     const int nch = std::min(child_start[k + 1] - child_start[k], 255);
-    H.dfs_kj[p] = make_int2(k | (H.dfs[p].y << 16), (H.jidx[k] + 1) | (nch << 16) |
-                                                        ((int)jtype[k] << 24) |
-                                                        ((int)rot_id[k] << 26));
+    H.dfs_kj[p] = make_int2(k | (H.dfs[p].y << 8) | ((int)H.chain_start[k] << 16),
+                            (H.jidx[k] + 1) | (nch << 16) | ((int)jtype[k] << 24) |
+                                ((int)rot_id[k] << 26));
   }
   H.lmeta.resize(n);
   for (int k = 0; k < n; ++k)

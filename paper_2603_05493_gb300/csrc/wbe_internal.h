@@ -43,8 +43,8 @@ struct DevRobot {
   const int16_t* lev_links;  // [n] links grouped by level
   const int2* dfs;           // [n] depth-first pre-order: link, depth
   const int2* dfs_kj;        // [n] the same positions packed for the sweeps: link |
-                             //   depth << 16, (joint + 1) | min(children, 255) << 16 |
-                             //   joint type << 24 | rot_id << 26
+                             //   depth << 8 | chain_start[link] << 16, (joint + 1) |
+                             //   min(children, 255) << 16 | joint type << 24 | rot_id << 26
   const int* lmeta;          // [n] per link: (joint + 1) | joint type << 16 | rot_id << 24
   int maxdepth;              // deepest link depth + 1
   int mimic_shared;          // 1 if some joint drives more than one link
