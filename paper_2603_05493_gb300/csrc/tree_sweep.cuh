@@ -792,7 +792,9 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
   // post-order of the link at depth e; the registers hold its state; tgt:
   // the closes go on down to depth tgt
   auto close = [&](int e, int tgt) {
-    const int k = __ldg(r.chain + lcs + e);
+    // the link at depth e with its joint, type and rotation flag, one load
+    const int cm = __ldg(r.chain_m + lcs + e);
+    const int k = cm & 0xFF;
     const bool own = !((replayed >> e) & 1u);
     // own terms: f = I a + v x* I v - f_ext, abar = I Fbar,
     // vbar = -crf(Fbar) I v - I crm(v) Fbar, and the gradient wrench
@@ -818,7 +820,7 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
         wrench(k, Wr);
         // the next close's rows, while this one computes
         if (use_slot && e - 1 >= tgt && !((replayed >> (e - 1)) & 1u))
-          issue(__ldg(r.chain + lcs + e - 1));
+          issue(__ldg(r.chain_m + lcs + e - 1) & 0xFF);
       } else {
 #pragma unroll
         for (int i = 0; i < 6; ++i) Wr[i] = 0.0f;
@@ -847,15 +849,17 @@ __device__ __forceinline__ float tree_bwd_seg(const DevRobot& r, const BwdArgs& 
       }
     }
     pdep = -1;
-    const int meta = __ldg(r.lmeta + k);
-    const int j = (meta & 0xFFFF) - 1;
-    const int jt = (meta >> 16) & 0xFF;
+    const int j = ((cm >> 8) & 0x1FF) - 1;
+    const int jt = (cm >> 17) & 3;
     const float4 a4 = ldp(reinterpret_cast<const float4*>(r.axis) + k);
     const float ax[3] = {a4.x, a4.y, a4.z};
     const float mm = ldp(reinterpret_cast<const float2*>(r.mimic) + k).x;
     const float vq = j >= 0 ? mm * st.vel(j) : 0.0f;
     float L[12];
-    link_local_m(r, k, meta, st, L);
+    {
+      const float th = j >= 0 ? joint_var(r, k, st.pos(j)) : 0.0f;
+      local_xf_m(r, k, th, jt, ((cm >> 19) & 1) != 0, L, L + 9);
+    }
     // the parent terms X_k v_pa, X_k a_pa, X_k Fbar_pa from the link's state
     float Xv[6], Xa[6], XF[6];
     if (e > 0) {

@@ -217,7 +217,7 @@ struct HostPlan {
   std::vector<int32_t> blk_pidx;
   std::vector<int4> lvm;
   std::vector<int2> dfs, dfs_kj;
-  std::vector<int> lmeta;
+  std::vector<int> lmeta, chain_m;
   std::vector<int16_t> chain_start, chain;
   int maxdepth = 0;
   int mimic_shared = 0;
@@ -712,6 +712,12 @@ int wb_load_robot(const wb_tree* tree, const wb_spheres* sph, const wb_pairs* pa
   pk.add_vec(H.lmeta, &D.lmeta);
   pk.add_vec(H.chain_start, &D.chain_start);
   pk.add_vec(H.chain, &D.chain);
+  H.chain_m.resize(H.chain.size());
+  for (size_t c = 0; c < H.chain.size(); ++c) {
+    const int k = H.chain[c];
+    H.chain_m[c] = k | ((H.jidx[k] + 1) << 8) | ((int)H.jtype[k] << 17) | ((int)H.rot_id[k] << 19);
+  }
+  pk.add_vec(H.chain_m, &D.chain_m);
   D.maxdepth = H.maxdepth;
   pk.add_vec(H.dfs_pos, &D.dfs_pos);
   pk.add_vec(H.dfs_end, &D.dfs_end);

@@ -50,6 +50,8 @@ struct DevRobot {
   int mimic_shared;          // 1 if some joint drives more than one link
   const int16_t* chain_start;// [n+1] ancestor chains (Alg. 1 "linkChain")
   const int16_t* chain;      // root -> link, link included
+  const int* chain_m;        // the chain's entries packed: link | (joint + 1) << 8 |
+                             //   joint type << 17 | rot_id << 19
   const int16_t* dfs_pos;    // [n] DFS position of each link
   const int16_t* dfs_end;    // [n] one past the last DFS position of its subtree
   // segmented sweeps with G = 2 << t segments, t = 0, 1, 2 (tree_sweep.cuh)
