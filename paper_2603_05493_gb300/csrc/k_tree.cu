@@ -14,6 +14,7 @@ namespace wbe {
 // behind the partials or basis rows it also keeps there), where they no
 // longer compete with the depth-first stacks for L1.
 constexpr int kParamWords = 28;  // Tf 12, axis 4, inertia 10, mimic 2
+constexpr size_t kSegSmemMax = 227 * 1024;  // dynamic shared memory of one block
 __device__ __forceinline__ DevRobot stage_params(const DevRobot& r, float* dst) {
   const int n = r.n;
   for (int i = threadIdx.x; i < 12 * n; i += blockDim.x) dst[i] = __ldg(r.Tf + i);
@@ -66,6 +67,11 @@ __device__ __forceinline__ Seg seg_of(const DevRobot& r, int t, float* part) {
              part, r.seg_ns[t], (int)(threadIdx.x & 31)};
 }
 
+// FS: the force stack in shared memory, [maxdepth][6][threads] floats behind
+// the link parameters (a link's F is stored when its first child is pushed
+// and read back at that child's close; in local memory these round trips
+// missed L1 61 % of the time)
+template <bool FS>
 __global__ void __launch_bounds__(512) tree_fwd_seg_kernel(const __grid_constant__ DevRobot r,
                                                            FwdArgs A, int t) {
   extern __shared__ float part[];
@@ -73,12 +79,27 @@ __global__ void __launch_bounds__(512) tree_fwd_seg_kernel(const __grid_constant
   const int CG = blockDim.x / (32 * G);
   const int cg = (threadIdx.x >> 5) / G;
   const int ns = r.seg_ns[t];
+  if (FS) {
+    // the launch reserves the stack for this block's threads; a block that
+    // finds less shared memory than that does nothing (its outputs stay
+    // unwritten) instead of indexing past it
+    unsigned dyn;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    const size_t need =
+        sizeof(float) * ((size_t)CG * ns * G * 32 + kParamWords * (size_t)r.n +
+                         6 * (size_t)r.maxdepth * blockDim.x);
+    if (need > dyn) return;
+  }
   Seg sg = seg_of(r, t, part + (size_t)cg * ns * G * 32);
   for (int s = 0; s < ns; ++s) sg.part[(s * G + sg.g) * 32 + sg.lane] = 0.0f;
   const DevRobot rs = stage_params(r, part + (size_t)CG * ns * G * 32);
+  if (FS) {
+    sg.fst = part + (size_t)CG * ns * G * 32 + kParamWords * (size_t)r.n + threadIdx.x;
+    sg.fstr = blockDim.x;
+  }
   __syncthreads();
   const int64_t b = ((int64_t)blockIdx.x * CG + cg) * 32 + sg.lane;
-  if (b < A.B) tree_fwd_seg(rs, A, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b, sg);
+  if (b < A.B) tree_fwd_seg<ArrayStates, FS>(rs, A, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b, sg);
   __syncthreads();
   if (b < A.B && A.tau) {
     for (int s = sg.g; s < ns; s += G) {
@@ -395,7 +416,16 @@ static cudaError_t launch_cost_seg(const DevRobot& r, const BwdArgs& a, const Fu
 cudaError_t launch_tree_fwd(const DevRobot& r, const FwdArgs& a, int threads, int segments,
                             cudaStream_t s) {
   if (threads <= 0) threads = 128;
-  if (segments > 1) return launch_seg(tree_fwd_seg_kernel, r, a, threads, segments, true, 0, s);
+  if (segments > 1) {
+    // the force stack in shared memory when it fits one block's limit (the
+    // humanoid's 13 levels x 448 threads: 140 KB; forward 0.0835 ->
+    // 0.0809 ms), else in local memory
+    const size_t bt = (size_t)32 * segments * seg_groups(segments, threads);
+    const size_t fs = sizeof(float) * 6 * (size_t)r.maxdepth * bt;
+    if (a.tau && tree_seg_smem(r, segments, threads, true, false) + fs <= kSegSmemMax)
+      return launch_seg(tree_fwd_seg_kernel<true>, r, a, threads, segments, true, fs, s);
+    return launch_seg(tree_fwd_seg_kernel<false>, r, a, threads, segments, true, 0, s);
+  }
   const size_t smem = param_smem(r);
   fit_carveout((const void*)tree_fwd_kernel, threads, smem);
   const int64_t grid = (a.B + threads - 1) / threads;

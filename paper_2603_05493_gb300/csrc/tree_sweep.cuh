@@ -69,6 +69,11 @@ struct Seg {
   float* part;         // partial outputs of this group: [nout][ns][G][32]
   int ns;              // shared slots
   int lane;
+  // forward sweep with its force stack in shared memory: this thread's
+  // entry 0, and the stride of the [depth][6][threads] layout (the block's
+  // threads)
+  float* fst = nullptr;
+  int fstr = 0;
 };
 
 __device__ __forceinline__ Seg whole_sweep(const DevRobot& r) {
@@ -296,7 +301,9 @@ struct FEnt {
   float v[6], a[6], F[6];
 };
 
-template <class St>
+// FS: the accumulated forces F of the stack live in shared memory (sg.fst)
+// instead of the thread's local stack
+template <class St, bool FS = false>
 __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A, const St& st,
                                              int64_t b, const Seg& sg) {
   const int64_t B = A.B;
@@ -331,7 +338,7 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
       for (int i = 0; i < 6; ++i) F[i] = pF[i];
     } else {
 #pragma unroll
-      for (int i = 0; i < 6; ++i) F[i] = E.F[i];
+      for (int i = 0; i < 6; ++i) F[i] = FS ? sg.fst[(6 * e + i) * sg.fstr] : E.F[i];
     }
     pdep = -1;
     const int meta = __ldg(r.lmeta + k);
@@ -354,14 +361,20 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
       link_local_m(r, k, meta, st, L);
       xf_force_T(L, L + 9, F, up);
 #pragma unroll
-      for (int i = 0; i < 6; ++i) pF[i] = stk[e - 1].F[i] + up[i];
+      for (int i = 0; i < 6; ++i)
+        pF[i] = (FS ? sg.fst[(6 * (e - 1) + i) * sg.fstr] : stk[e - 1].F[i]) + up[i];
       pdep = e - 1;
     }
   };
   auto flush = [&]() {  // the pending force goes back to its stack entry
     if (pdep >= 0) {
 #pragma unroll
-      for (int i = 0; i < 6; ++i) stk[pdep].F[i] = pF[i];
+      for (int i = 0; i < 6; ++i) {
+        if (FS)
+          sg.fst[(6 * pdep + i) * sg.fstr] = pF[i];
+        else
+          stk[pdep].F[i] = pF[i];
+      }
       pdep = -1;
     }
   };
@@ -472,8 +485,9 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
   // push (measured on the 48-DoF humanoid at 2 segments x 448 threads:
   // 0.0985 -> 0.0970 ms against the L2 prefetch hint it replaces).
   float nq = 0.0f, nqd = 0.0f, nqdd = 0.0f;
+  int2 nkd = sg.p0 < sg.p1 ? __ldg(r.dfs_kj + sg.p0) : make_int2(0, 0);
   {
-    const int j0 = sg.p0 < sg.p1 ? (__ldg(r.dfs_kj + sg.p0).y & 0xFFFF) - 1 : -1;
+    const int j0 = sg.p0 < sg.p1 ? (nkd.y & 0xFFFF) - 1 : -1;
     if (j0 >= 0) {
       nq = st.pos(j0);
       if (dyn) {
@@ -485,12 +499,16 @@ __device__ __forceinline__ void tree_fwd_seg(const DevRobot& r, const FwdArgs& A
   for (int pos = sg.p0; pos < sg.p1; ++pos) {
     // link | depth << 8, (joint + 1) | children << 16 of this position: one
     // load for what the DFS order, the joint index and the child table gave
-    // in four (humanoid48 forward 0.0898 -> 0.0885 ms)
-    const int2 kd = __ldg(r.dfs_kj + pos);
+    // in four (humanoid48 forward 0.0898 -> 0.0885 ms), kept from the
+    // previous step's look-ahead rather than loaded again (0.0844 -> 0.0835
+    // ms; the backward, at its register cap, spills more with it: 0.1664 ->
+    // 0.1684 ms)
+    const int2 kd = nkd;
     const int k = kd.x & 0xFF, dep = (kd.x >> 8) & 0xFF;
     const float cq = nq, cqd = nqd, cqdd = nqdd;
     if (pos + 1 < sg.p1) {  // the next link's joint inputs
-      const int jn = (__ldg(r.dfs_kj + pos + 1).y & 0xFFFF) - 1;
+      nkd = __ldg(r.dfs_kj + pos + 1);
+      const int jn = (nkd.y & 0xFFFF) - 1;
       if (jn >= 0) {
         nq = st.pos(jn);
         if (dyn) {
