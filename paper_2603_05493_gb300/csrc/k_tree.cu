@@ -29,13 +29,30 @@ __device__ __forceinline__ DevRobot stage_params(const DevRobot& r, float* dst) 
   return s;
 }
 
+// the block's dynamic shared memory covers `words` floats
+__device__ __forceinline__ bool smem_holds(size_t words) {
+  unsigned dyn;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+  return sizeof(float) * words <= dyn;
+}
+
+// FS: the force stack in shared memory behind the link parameters, as in the
+// segmented forward below
+template <bool FS>
 __global__ void __launch_bounds__(256) tree_fwd_kernel(const __grid_constant__ DevRobot r,
                                                        FwdArgs A) {
   extern __shared__ float prm[];
+  if (FS && !smem_holds(kParamWords * (size_t)r.n + 6 * (size_t)r.maxdepth * blockDim.x)) return;
   const DevRobot rs = stage_params(r, prm);
   __syncthreads();
   const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (b < A.B) tree_fwd_one(rs, A, b);
+  if (b >= A.B) return;
+  Seg sg = whole_sweep(r);
+  if (FS) {
+    sg.fst = prm + kParamWords * (size_t)r.n + threadIdx.x;
+    sg.fstr = blockDim.x;
+  }
+  tree_fwd_seg<ArrayStates, FS>(rs, A, ArrayStates{A.q, A.qd, A.qdd, A.B, b}, b, sg);
 }
 
 // The backward sweeps are capped at 128 registers (two 256-thread blocks per
@@ -79,17 +96,12 @@ __global__ void __launch_bounds__(512) tree_fwd_seg_kernel(const __grid_constant
   const int CG = blockDim.x / (32 * G);
   const int cg = (threadIdx.x >> 5) / G;
   const int ns = r.seg_ns[t];
-  if (FS) {
-    // the launch reserves the stack for this block's threads; a block that
-    // finds less shared memory than that does nothing (its outputs stay
-    // unwritten) instead of indexing past it
-    unsigned dyn;
-    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
-    const size_t need =
-        sizeof(float) * ((size_t)CG * ns * G * 32 + kParamWords * (size_t)r.n +
-                         6 * (size_t)r.maxdepth * blockDim.x);
-    if (need > dyn) return;
-  }
+  // the launch reserves the stack for this block's threads; a block that
+  // finds less shared memory than that does nothing (its outputs stay
+  // unwritten) instead of indexing past it
+  if (FS && !smem_holds((size_t)CG * ns * G * 32 + kParamWords * (size_t)r.n +
+                        6 * (size_t)r.maxdepth * blockDim.x))
+    return;
   Seg sg = seg_of(r, t, part + (size_t)cg * ns * G * 32);
   for (int s = 0; s < ns; ++s) sg.part[(s * G + sg.g) * 32 + sg.lane] = 0.0f;
   const DevRobot rs = stage_params(r, part + (size_t)CG * ns * G * 32);
@@ -226,6 +238,8 @@ __global__ void __launch_bounds__(256) tree_fwd_spline_kernel(const __grid_const
   tree_fwd_seg(rs, A, st, b, whole_sweep(r));
 }
 
+// FS as for tree_fwd_seg_kernel; the force stack follows the link parameters
+template <bool FS>
 __global__ void __launch_bounds__(512) tree_fwd_spline_seg_kernel(
     const __grid_constant__ DevRobot r, FwdArgs A, SplineArgs sp, int t) {
   extern __shared__ float sm[];
@@ -234,12 +248,20 @@ __global__ void __launch_bounds__(512) tree_fwd_spline_seg_kernel(
   const int CG = blockDim.x / (32 * G);
   const int cg = (threadIdx.x >> 5) / G;
   const int ns = r.seg_ns[t];
+  if (FS && !smem_holds(12 * (size_t)blockDim.x + (size_t)CG * ns * G * 32 +
+                        kParamWords * (size_t)r.n + 6 * (size_t)r.maxdepth * blockDim.x))
+    return;
   Seg sg = seg_of(r, t, part + (size_t)cg * ns * G * 32);
   for (int s = 0; s < ns; ++s) sg.part[(s * G + sg.g) * 32 + sg.lane] = 0.0f;
   const DevRobot rs = stage_params(r, part + (size_t)CG * ns * G * 32);
+  if (FS) {
+    sg.fst = part + (size_t)CG * ns * G * 32 + kParamWords * (size_t)r.n + threadIdx.x;
+    sg.fstr = blockDim.x;
+  }
   __syncthreads();
   const int64_t b = ((int64_t)blockIdx.x * CG + cg) * 32 + sg.lane;
-  if (b < A.B) tree_fwd_seg(rs, A, spline_states(r, sp, b, sm + 12 * threadIdx.x), b, sg);
+  if (b < A.B)
+    tree_fwd_seg<SplineStates, FS>(rs, A, spline_states(r, sp, b, sm + 12 * threadIdx.x), b, sg);
   __syncthreads();
   if (b < A.B && A.tau) {
     for (int s = sg.g; s < ns; s += G) {
@@ -426,10 +448,16 @@ cudaError_t launch_tree_fwd(const DevRobot& r, const FwdArgs& a, int threads, in
       return launch_seg(tree_fwd_seg_kernel<true>, r, a, threads, segments, true, fs, s);
     return launch_seg(tree_fwd_seg_kernel<false>, r, a, threads, segments, true, 0, s);
   }
-  const size_t smem = param_smem(r);
-  fit_carveout((const void*)tree_fwd_kernel, threads, smem);
+  const size_t fs = sizeof(float) * 6 * (size_t)r.maxdepth * threads;  // the force stack
+  const bool use_fs = a.tau && param_smem(r) + fs <= kSegSmemMax;
+  const size_t smem = param_smem(r) + (use_fs ? fs : 0);
+  auto kern = use_fs ? tree_fwd_kernel<true> : tree_fwd_kernel<false>;
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  fit_carveout((const void*)kern, threads, smem);
   const int64_t grid = (a.B + threads - 1) / threads;
-  tree_fwd_kernel<<<(unsigned)grid, threads, smem, s>>>(r, a);
+  kern<<<(unsigned)grid, threads, smem, s>>>(r, a);
   return cudaGetLastError();
 }
 
@@ -458,13 +486,17 @@ cudaError_t launch_tree_fwd_spline(const DevRobot& r, const FwdArgs& a, const Sp
     const int t = seg_plan(segments);
     const int CG = seg_groups(segments, threads);
     const int block = 32 * segments * CG;
-    const size_t smem = tree_seg_smem(r, segments, threads, true, false) + 12 * sizeof(float) * block;
-    cudaError_t e = cudaFuncSetAttribute(tree_fwd_spline_seg_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t base = tree_seg_smem(r, segments, threads, true, false) + 12 * sizeof(float) * block;
+    const size_t fs = sizeof(float) * 6 * (size_t)r.maxdepth * block;  // the force stack
+    const bool use_fs = a.tau && base + fs <= kSegSmemMax;
+    const size_t smem = use_fs ? base + fs : base;
+    auto kern = use_fs ? tree_fwd_spline_seg_kernel<true> : tree_fwd_spline_seg_kernel<false>;
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fit_carveout((const void*)tree_fwd_spline_seg_kernel, block, smem);
+    fit_carveout((const void*)kern, block, smem);
     const int64_t grid = ((a.B + 31) / 32 + CG - 1) / CG;
-    tree_fwd_spline_seg_kernel<<<(unsigned)grid, block, smem, s>>>(r, a, sp, t);
+    kern<<<(unsigned)grid, block, smem, s>>>(r, a, sp, t);
     return cudaGetLastError();
   }
   const size_t smem = 12 * sizeof(float) * threads + param_smem(r);
