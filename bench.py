@@ -78,16 +78,16 @@ PAIR_SRC = ["paper_2603_05493_gb300/csrc/k_pair.cu", "paper_2603_05493_gb300/csr
             "paper_2603_05493_gb300/csrc/spatial.cuh"] + API_SRC
 SPLINE_SRC = ["paper_2603_05493_gb300/csrc/k_traj.cu",
               "paper_2603_05493_gb300/csrc/spline_basis.cuh"] + API_SRC
-TREE_SHA = "ebc353ac8c97d11b7778045dbc371c4f9e2cc398f8d2a7ecc3d86daf7aa69060"
+TREE_SHA = "13fce0a2be8cf42eb33fa5529711aa281bae59d0fe63b21a362a64dc984e8bad"
 PAIR_SHA = "900fda00358a3c3401e8bfc374fd49a744d5a9b1a5973a586c1a513c69b38dc8"
 SPLINE_SHA = "c1894a77ac640df27a5c2c3b6b8de685b1c24f10bdf9f4b73cac6f90e00a9a19"
 MEASURED_TRAFFIC = {  # kernel[@workload]: (sources, their hash, bytes / evaluation)
-    "tree_fwd_seg_kernel": (TREE_SRC, TREE_SHA, (29.48e6 + 79.34e6) / 32768),
-    "pair_kernel": (PAIR_SRC, PAIR_SHA, (77.34e6 + 32.56e6) / 32768),
-    "tree_bwd_seg_kernel": (TREE_SRC, TREE_SHA, (239.01e6 + 37.14e6) / 32768),
-    "tree_fwd_spline_seg_kernel": (TREE_SRC, TREE_SHA, (8.54e6 + 80.81e6) / 32768),
-    "pair_kernel@trajopt48": (PAIR_SRC, PAIR_SHA, (77.26e6 + 0.78e6) / 32768),
-    "tree_bwd_spline_cost_seg_kernel": (TREE_SRC, TREE_SHA, (8.71e6 + 2.31e6) / 32768),
+    "tree_fwd_seg_kernel": (TREE_SRC, TREE_SHA, (23.94e6 + 50.73e6) / 32768),
+    "pair_kernel": (PAIR_SRC, PAIR_SHA, (77.29e6 + 32.66e6) / 32768),
+    "tree_bwd_seg_kernel": (TREE_SRC, TREE_SHA, (239.01e6 + 37.11e6) / 32768),
+    "tree_fwd_spline_seg_kernel": (TREE_SRC, TREE_SHA, (5.66e6 + 52.47e6) / 32768),
+    "pair_kernel@trajopt48": (PAIR_SRC, PAIR_SHA, (77.26e6 + 0.70e6) / 32768),
+    "tree_bwd_spline_cost_seg_kernel": (TREE_SRC, TREE_SHA, (8.72e6 + 2.22e6) / 32768),
     "bspline_bwd_kernel": (SPLINE_SRC, SPLINE_SHA, (18.89e6 + 0.00e6) / 32768),
 }
 

@@ -2166,24 +2166,48 @@ float median_of(std::vector<float> v) {
   return v[v.size() / 2];
 }
 
+// The autotuners' L2 flush: a read of n16 16-byte words of a zeroed buffer
+// twice the L2's size.  L2 then holds clean lines of that buffer, so the timed
+// launch starts with a cold cache, as a step over a batch that does not stay
+// in L2 sees it, but without the write-back of a flush by memset, whose
+// dirty lines drained while the candidate ran.  With the memset the
+// trajopt48 control-point backward's 2 x 512 and 1 x 256 shapes timed within
+// 1 % of each other and the choice flipped between runs (1 x 256 in 1 of 4),
+// where the trajectory step runs them at 0.127 and 0.132 ms; with the read
+// flush the tuner took 2 x 512 in 4 of 4 runs, medians within 0.03 %.
+__global__ void tune_flush_kernel(const uint4* __restrict__ buf, size_t n16, unsigned* sink) {
+  unsigned acc = 0u;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n16;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const uint4 v = buf[i];
+    acc ^= v.x ^ v.y ^ v.z ^ v.w;
+  }
+  if (acc == 0x9E3779B9u) *sink = acc;  // never true for the zeroed buffer; keeps the loads
+}
+
 // The autotuners' clock: the median of kTuneReps runs of f on stream s, each
-// after an L2 flush (a memset of flush_bytes, outside the events), as a step
-// over a batch that does not stay in L2 sees it.
+// after an L2 flush (tune_flush_kernel, outside the events).
 constexpr int kTuneReps = 5;
 struct TuneClock {
   cudaStream_t s = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   void* flush = nullptr;
   size_t flush_bytes = 0;
+  int sms = 0;
   bool init(Scratch& sc, int device) {
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
       return false;
     int l2 = 0;
-    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device) == cudaSuccess && l2 > 0) {
-      flush_bytes = 2 * (size_t)l2;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device) == cudaSuccess && l2 > 0 &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess &&
+        sms > 0) {
+      flush_bytes = 2 * (size_t)l2 / 16 * 16;
       flush = sc.get<char>(flush_bytes);  // no flush if it cannot be had
-      if (!flush) cudaGetLastError();
+      if (!flush || cudaMemsetAsync(flush, 0, flush_bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        flush = nullptr;
+      }
     }
     return true;
   }
@@ -2191,7 +2215,10 @@ struct TuneClock {
   float time(F&& f) {
     std::vector<float> ts;
     for (int rep = 0; rep < kTuneReps; ++rep) {
-      if (flush) cudaMemsetAsync(flush, rep & 0xFF, flush_bytes, s);
+      if (flush)
+        tune_flush_kernel<<<8 * sms, 256, 0, s>>>(static_cast<const uint4*>(flush),
+                                                 flush_bytes / 16,
+                                                 static_cast<unsigned*>(flush));
       cudaEventRecord(e0, s);
       f();
       cudaEventRecord(e1, s);
