@@ -78,9 +78,9 @@ PAIR_SRC = ["paper_2603_05493_gb300/csrc/k_pair.cu", "paper_2603_05493_gb300/csr
             "paper_2603_05493_gb300/csrc/spatial.cuh"] + API_SRC
 SPLINE_SRC = ["paper_2603_05493_gb300/csrc/k_traj.cu",
               "paper_2603_05493_gb300/csrc/spline_basis.cuh"] + API_SRC
-TREE_SHA = "13fce0a2be8cf42eb33fa5529711aa281bae59d0fe63b21a362a64dc984e8bad"
-PAIR_SHA = "900fda00358a3c3401e8bfc374fd49a744d5a9b1a5973a586c1a513c69b38dc8"
-SPLINE_SHA = "c1894a77ac640df27a5c2c3b6b8de685b1c24f10bdf9f4b73cac6f90e00a9a19"
+TREE_SHA = "b46a54ba96021c75e1c4474cafdbca3e67ba2114540e07f250a8038979fb4f53"
+PAIR_SHA = "ae2e5f87424c775787e9ca01706fa8faad39a88ebd836ef5240b0cbcc1f6f0a6"
+SPLINE_SHA = "4a8e81a07663680c60efd7bd447af10bfb0c062febaa7048329d2e73c65f5f27"
 MEASURED_TRAFFIC = {  # kernel[@workload]: (sources, their hash, bytes / evaluation)
     "tree_fwd_seg_kernel": (TREE_SRC, TREE_SHA, (23.94e6 + 50.73e6) / 32768),
     "pair_kernel": (PAIR_SRC, PAIR_SHA, (77.29e6 + 32.66e6) / 32768),
