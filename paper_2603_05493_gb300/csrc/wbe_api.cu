@@ -2166,59 +2166,39 @@ float median_of(std::vector<float> v) {
   return v[v.size() / 2];
 }
 
-// The autotuners' L2 flush: a read of n16 16-byte words of a zeroed buffer
-// twice the L2's size.  L2 then holds clean lines of that buffer, so the timed
-// launch starts with a cold cache, as a step over a batch that does not stay
-// in L2 sees it, but without the write-back of a flush by memset, whose
-// dirty lines drained while the candidate ran.  With the memset the
-// trajopt48 control-point backward's 2 x 512 and 1 x 256 shapes timed within
-// 1 % of each other and the choice flipped between runs (1 x 256 in 1 of 4),
-// where the trajectory step runs them at 0.127 and 0.132 ms; with the read
-// flush the tuner took 2 x 512 in 4 of 4 runs, medians within 0.03 %.
-__global__ void tune_flush_kernel(const uint4* __restrict__ buf, size_t n16, unsigned* sink) {
-  unsigned acc = 0u;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n16;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const uint4 v = buf[i];
-    acc ^= v.x ^ v.y ^ v.z ^ v.w;
-  }
-  if (acc == 0x9E3779B9u) *sink = acc;  // never true for the zeroed buffer; keeps the loads
-}
-
 // The autotuners' clock: the median of kTuneReps runs of f on stream s, each
-// after an L2 flush (tune_flush_kernel, outside the events).
+// after an L2 flush (a memset of flush_bytes, outside the events), as a step
+// over a batch that does not stay in L2 sees it.  pre() runs between the
+// flush and the timed region: a backward candidate is timed after the
+// forward sweep and the pair stage that precede it in a step, so that it
+// finds the cache as it does there (timed straight after the flush, the
+// control-point backward's 2 x 512 and 1 x 256 shapes ranked within 1 % of
+// each other and the choice flipped between runs, where the trajectory step
+// runs them at 0.127 and 0.132 ms).
 constexpr int kTuneReps = 5;
 struct TuneClock {
   cudaStream_t s = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   void* flush = nullptr;
   size_t flush_bytes = 0;
-  int sms = 0;
   bool init(Scratch& sc, int device) {
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
       return false;
     int l2 = 0;
-    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device) == cudaSuccess && l2 > 0 &&
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess &&
-        sms > 0) {
-      flush_bytes = 2 * (size_t)l2 / 16 * 16;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device) == cudaSuccess && l2 > 0) {
+      flush_bytes = 2 * (size_t)l2;
       flush = sc.get<char>(flush_bytes);  // no flush if it cannot be had
-      if (!flush || cudaMemsetAsync(flush, 0, flush_bytes, s) != cudaSuccess) {
-        cudaGetLastError();
-        flush = nullptr;
-      }
+      if (!flush) cudaGetLastError();
     }
     return true;
   }
-  template <class F>
-  float time(F&& f) {
+  template <class F, class P>
+  float time(F&& f, P&& pre) {
     std::vector<float> ts;
     for (int rep = 0; rep < kTuneReps; ++rep) {
-      if (flush)
-        tune_flush_kernel<<<8 * sms, 256, 0, s>>>(static_cast<const uint4*>(flush),
-                                                 flush_bytes / 16,
-                                                 static_cast<unsigned*>(flush));
+      if (flush) cudaMemsetAsync(flush, rep & 0xFF, flush_bytes, s);
+      pre();
       cudaEventRecord(e0, s);
       f();
       cudaEventRecord(e1, s);
@@ -2228,6 +2208,10 @@ struct TuneClock {
       ts.push_back(ms);
     }
     return median_of(ts);
+  }
+  template <class F>
+  float time(F&& f) {
+    return time(f, [] {});
   }
   ~TuneClock() {
     if (s) cudaStreamSynchronize(s);
@@ -2354,7 +2338,12 @@ extern "C" int wb_autotune(wb_robot* robot, int64_t B, wb_tune* fwd, wb_tune* bw
                                                 gtau, gq, gqd, gqdd, nullptr, &t, s);
       };
       if (run() != WB_OK) continue;  // shape not applicable to this robot
-      const float m = clk.time(run);
+      // a backward candidate after the forward sweep and pair stage of a step
+      auto pre = [&]() {
+        if (pass == 1)
+          wb_eval(robot, B, q, qd, qdd, pose, sph, dmin_f, worst_f, tau, nullptr, nullptr, s);
+      };
+      const float m = clk.time(run, pre);
       if (pass == 0 && m < best_f) {
         best_f = m;
         bf = t;
@@ -2449,7 +2438,14 @@ extern "C" int wb_autotune_spline(wb_robot* robot, int64_t n_traj, int32_t K, in
       }
     }
     if (run_b() == WB_OK) {
-      const float m = clk.time(run_b);
+      // after the forward sweep and the pair stage that precede it in a step
+      // (they rewrite the torques, minima, worst pairs and centre
+      // differences the backward reads with the same values)
+      auto pre_b = [&]() {
+        wb_eval_spline(robot, &sp, pose, nullptr, nullptr, nullptr, tau, nullptr, s);
+        wb_self_collision_dir(robot, B, pose, sph, dmin, worst, wdiff, nullptr, nullptr, s);
+      };
+      const float m = clk.time(run_b, pre_b);
       if (m < best_b) {
         best_b = m;
         bb = t;
