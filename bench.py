@@ -78,9 +78,9 @@ PAIR_SRC = ["paper_2603_05493_gb300/csrc/k_pair.cu", "paper_2603_05493_gb300/csr
             "paper_2603_05493_gb300/csrc/spatial.cuh"] + API_SRC
 SPLINE_SRC = ["paper_2603_05493_gb300/csrc/k_traj.cu",
               "paper_2603_05493_gb300/csrc/spline_basis.cuh"] + API_SRC
-TREE_SHA = "b46a54ba96021c75e1c4474cafdbca3e67ba2114540e07f250a8038979fb4f53"
-PAIR_SHA = "ae2e5f87424c775787e9ca01706fa8faad39a88ebd836ef5240b0cbcc1f6f0a6"
-SPLINE_SHA = "4a8e81a07663680c60efd7bd447af10bfb0c062febaa7048329d2e73c65f5f27"
+TREE_SHA = "07a09d1949da5479c370f929d6354a1a1d6eb27af843fdf8497217fff37dee14"
+PAIR_SHA = "400b679eaab398c46eb74122c4f202b9724b238f380a50da02b7c1e8b9f19d8f"
+SPLINE_SHA = "610be5112e547b9a8bcf82c0f8d7e914f09a59ad580bfa1685a3d0b32a3c09f4"
 MEASURED_TRAFFIC = {  # kernel[@workload]: (sources, their hash, bytes / evaluation)
     "tree_fwd_seg_kernel": (TREE_SRC, TREE_SHA, (23.94e6 + 50.73e6) / 32768),
     "pair_kernel": (PAIR_SRC, PAIR_SHA, (77.29e6 + 32.66e6) / 32768),
