@@ -1206,7 +1206,9 @@ def run_uneven(args, rank=0, world=1, local_rank=0):
         "gpu_launches": 3 * args.steps * world, "clocks": clocks.summary()}), flush=True)
 
 
-def main():
+def arg_parser():
+    """bench.py's command line (the profile summaries' commands are checked
+    against it)."""
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=300)
@@ -1234,7 +1236,11 @@ def main():
     ap.add_argument("--sweep-shape", default="",
                     help="pin the sweep launch shapes instead of autotuning: "
                          "fwd segments,fwd configs per block,bwd segments,bwd configs per block")
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = arg_parser().parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
