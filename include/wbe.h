@@ -316,7 +316,10 @@ int wb_eval_backward_dir(wb_robot* robot, int64_t B, const float* q, const float
  * wb_self_collision_dir, as wb_eval_backward_dir takes it), and returns the
  * fastest choice for each pass with its median
  * time (ms, nullable).  Each candidate is timed 5 times, each run after an
- * L2 flush (a memset of twice the L2 size), and ranked by the median. */
+ * L2 flush (a memset of twice the L2 size), and ranked by the median; a
+ * backward candidate runs after the flush and an untimed forward with the
+ * pair stage (default launch), so that it meets the cache as a step leaves
+ * it. */
 int wb_autotune(wb_robot* robot, int64_t B, wb_tune* fwd, wb_tune* bwd, float* fwd_ms,
                 float* bwd_ms);
 
@@ -608,8 +611,9 @@ int wb_eval_backward_spline_cost_dir(wb_robot* robot, const wb_spline* spline,
  * wb_eval_backward_spline_cost_dir with the cost weights w (host pointer),
  * torque limits of +-30 and the worst pairs' centre differences -- on
  * deterministic control points in [-pi/2, pi/2],
- * 5 runs per candidate, each after an L2 flush, and returns the fastest shape
- * for each with its median time (ms, nullable).  Its choices differ from
+ * 5 runs per candidate, each after an L2 flush (a backward candidate also
+ * after an untimed forward sweep and pair stage), and returns the fastest
+ * shape for each with its median time (ms, nullable).  Its choices differ from
  * wb_autotune's where the spline-cost backward kernel prefers another block
  * size than the plain backward sweep.  n_traj >= 1 and K, T, dt as
  * wb_spline.
